@@ -1,0 +1,410 @@
+"""Pins of the FP64 oracle against facts the paper and mathematics fix.
+
+Each test targets a plausible mistake: a dropped or mis-signed term of the
+ReLU back-substitution (Sec. 3.1), a transposed or mis-padded convolution, a
+wrong concretisation (Eq. minimum), a wrong x* (Sec. 3.1 upper bounding), an
+unsound multi-neuron constraint, a wrong gradient, or a wrong ACS formula
+(Sec. 3.2).  None of these tests calls the GPU library.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy.optimize import linprog
+
+import synth
+from oracle import bab, core, exact, mnc
+from oracle.core import DT
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+def _t(x):
+    return torch.as_tensor(np.asarray(x), dtype=DT)
+
+
+def _fc(W, b):
+    return dict(kind="fc", W=np.asarray(W, np.float32), b=np.asarray(b, np.float32))
+
+
+RELU = dict(kind="relu")
+
+
+# --------------------------------------------------------------------------
+# affine layers and concretisation
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("ci,h,co,k,s,p", [(1, 28, 16, 4, 2, 0), (16, 13, 32, 4, 2, 0),
+                                           (3, 9, 5, 3, 1, 1), (4, 8, 6, 4, 2, 1)])
+def test_conv_forward_and_adjoint(ci, h, co, k, s, p):
+    """Conv forward equals the direct definition (synth's numpy loops), and the
+    back-substitution is its exact adjoint: <L, conv x> = <conv^T L, x>."""
+    rng = np.random.default_rng(5)
+    ho = (h + 2 * p - k) // s + 1
+    L = dict(kind="conv", W=rng.standard_normal((co, ci, k, k)).astype(np.float32),
+             b=rng.standard_normal(co).astype(np.float32), stride=s, pad=p,
+             in_shape=(ci, h, h), out_shape=(co, ho, ho))
+    net = core.load_net([L])
+    A = net.aff[1]
+    x = rng.standard_normal(ci * h * h)
+    ref = synth.net_forward([L], x)
+    got = A.forward(_t(x)[None])[0].numpy()
+    assert np.allclose(got, ref, atol=1e-10)
+    lam = _t(rng.standard_normal((3, co * ho * ho)))
+    lin = A.forward(_t(x)[None]) - A.forward(torch.zeros(1, ci * h * h, dtype=DT))
+    lhs = (lam * lin).sum(1)
+    rhs = A.backsub(lam) @ _t(x)
+    assert torch.allclose(lhs, rhs, atol=1e-9)
+    bias_full = A.forward(torch.zeros(1, ci * h * h, dtype=DT))[0]
+    assert torch.allclose(A.bias_dot(lam), lam @ bias_full, atol=1e-10)
+
+
+def test_affine_only_is_exact_and_hoelder():
+    """One affine layer: the bound is the exact minimum over the box, and without
+    clipping it is the Hoelder form a x0 - ||a||_1 eps + c (Eq. minimum)."""
+    rng = np.random.default_rng(1)
+    W = rng.standard_normal((4, 6))
+    b = rng.standard_normal(4)
+    net = core.load_net([_fc(W, b)])
+    x0 = rng.uniform(0.3, 0.7, 6)
+    eps = 0.1
+    lo, hi = synth.input_box(x0, eps)
+    lb, xs, _ = core.backsub_rows(net, 1, torch.eye(4, dtype=DT), {}, _t(lo), _t(hi))
+    Wf, bf = W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
+    corners = np.array(list(itertools.product(*zip(lo, hi))), dtype=np.float64)
+    brute = (corners @ Wf.T + bf).min(0)
+    assert np.allclose(lb.numpy(), brute, atol=1e-12)
+    x0f = x0.astype(np.float32).astype(np.float64)
+    hoelder = Wf @ x0f - np.abs(Wf).sum(1) * np.float64(np.float32(eps)) + bf
+    assert np.allclose(lb.numpy(), hoelder, atol=1e-6)
+    # x* attains the bound
+    assert np.allclose((xs.numpy() * Wf).sum(1) + bf, lb.numpy(), atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# the single-neuron table by hand (Sec. 3.1)
+# --------------------------------------------------------------------------
+def _one_neuron(w, c):
+    return [_fc([[1.0]], [0.0]), RELU, _fc([[w]], [c])]
+
+
+def test_relu_table_positive_coefficient():
+    """f = 3 relu(x) + 1, x in [-1, 2]: DeepPoly slope 1 gives -2; the alpha
+    bound is 1 - 3 alpha, so Adam drives alpha to 0 and reaches the exact 1."""
+    L = _one_neuron(3.0, 1.0)
+    net, lo, hi, l, u, S, m, dense = bab.prepare(L, [[1.0]], [0.0], [-1.0], [2.0])
+    assert float(l[1][0]) == -1.0 and float(u[1][0]) == 2.0
+    node = bab.root_node(net, 0, l, u, S, None)
+    lb_dp, _ = core.deeppoly_final(net, node, lo, hi)
+    assert float(lb_dp) == pytest.approx(-2.0, abs=1e-12)
+    for a in (0.0, 0.25, 0.6):
+        lb, _, _ = core.final_bound(net, node, {1: _t([a])}, {1: _t([0.0])},
+                                    {1: torch.zeros(0, dtype=DT)}, None, lo, hi)
+        assert float(lb) == pytest.approx(1.0 - 3.0 * a, abs=1e-12)
+    best, _, a, _, _ = core.optimize(net, node, None, lo, hi, core.AdamHP())
+    assert best == pytest.approx(1.0, abs=1e-12)
+    assert float(a[1][0]) == 0.0
+
+
+def test_relu_table_negative_coefficient():
+    """f = -2 relu(x) + 5, x in [-1, 2]: the upper line u/(u-l)(x - l) with
+    intercept -ul/(u-l) = 2/3 gives the exact minimum 1."""
+    L = _one_neuron(-2.0, 5.0)
+    net, lo, hi, l, u, S, _, _ = bab.prepare(L, [[1.0]], [0.0], [-1.0], [2.0])
+    node = bab.root_node(net, 0, l, u, S, None)
+    lb, xs = core.deeppoly_final(net, node, lo, hi)
+    assert float(lb) == pytest.approx(1.0, abs=1e-12)
+    assert float(xs[0]) == 2.0
+
+
+def test_relu_table_two_neurons_and_splits():
+    """f = relu(x1+x2) + relu(x1-x2) on [-1,1]^2 has bound -2 max(alpha); the
+    negative objective -relu(x1+x2) is exact (-2); a negative split (S=+1)
+    gives -2 beta (best 0) and a positive split gives -2 (1 + beta)."""
+    W1 = [[1.0, 1.0], [1.0, -1.0]]
+    L = [_fc(W1, [0, 0]), RELU, _fc([[1.0, 1.0]], [0.0])]
+    net, lo, hi, l, u, S, _, _ = bab.prepare(L, [[1.0]], [0.0], [-1, -1], [1, 1])
+    node = bab.root_node(net, 0, l, u, S, None)
+    for a1, a2 in ((1, 1), (0.3, 0.7), (0, 0), (0.9, 0.1)):
+        lb, _, _ = core.final_bound(net, node, {1: _t([a1, a2])}, {1: _t([0, 0])},
+                                    {1: torch.zeros(0, dtype=DT)}, None, lo, hi)
+        assert float(lb) == pytest.approx(-2 * max(a1, a2), abs=1e-12)
+    L2 = [_fc(W1, [0, 0]), RELU, _fc([[-1.0, 0.0]], [0.0])]
+    net, lo, hi, l, u, S, _, _ = bab.prepare(L2, [[1.0]], [0.0], [-1, -1], [1, 1])
+    node = bab.root_node(net, 0, l, u, S, None)
+    lb, _ = core.deeppoly_final(net, node, lo, hi)
+    assert float(lb) == pytest.approx(-2.0, abs=1e-12)
+    for sgn, f_beta in ((1, lambda b: -2 * b), (-1, lambda b: -2 * (1 + b))):
+        n2 = bab.root_node(net, 0, l, u, S, None)
+        n2.S[1] = torch.tensor([sgn, 0], dtype=torch.int8)
+        if sgn == 1:
+            n2.u[1] = torch.minimum(n2.u[1], _t([0.0, 1e9]))
+        else:
+            n2.l[1] = torch.maximum(n2.l[1], _t([0.0, -1e9]))
+        for bval in (0.0, 0.5, 2.0):
+            lb, _, _ = core.final_bound(net, n2, {1: _t([0.5, 0.5])}, {1: _t([bval, 0])},
+                                        {1: torch.zeros(0, dtype=DT)}, None, lo, hi)
+            assert float(lb) == pytest.approx(f_beta(bval), abs=1e-12)
+
+
+# --------------------------------------------------------------------------
+# soundness, exactness and gradients on small nets
+# --------------------------------------------------------------------------
+def _small_case(seed, dims=(12, 10, 10, 3), eps=0.08, with_mnc=True):
+    L = synth.tiny_fc_net(seed, list(dims))
+    rng = np.random.default_rng(seed + 100)
+    x0 = rng.uniform(0.2, 0.8, dims[0]).astype(np.float32)
+    y = synth.net_forward(L, x0)
+    C, d = synth.property_rows(int(np.argmax(y)), dims[-1])
+    lo, hi = synth.input_box(x0, eps)
+    fn = mnc.mnc_fn() if with_mnc else None
+    prep = bab.prepare(L, C, d, lo, hi, fn)
+    return L, C, d, lo, hi, prep
+
+
+def _random_node(prep, rng, n_splits=2, row=0):
+    net, lo, hi, l, u, S, m, dense = prep
+    node = bab.root_node(net, row, l, u, S, m)
+    cands = [(i, j) for i in l for j in range(l[i].numel()) if l[i][j] < 0 < u[i][j]]
+    picks = [cands[k] for k in rng.choice(len(cands), size=min(n_splits, len(cands)), replace=False)]
+    low = min(p[0] for p in picks) if picks else net.R
+    for (i, j) in picks:
+        sgn = int(rng.choice([1, -1]))
+        node.S[i][j] = sgn
+        if sgn == 1:
+            node.u[i][j] = 0.0
+        else:
+            node.l[i][j] = 0.0
+    node.split_layer = low
+    core.rebound_node(net, node, lo, hi)
+    node.alpha = {i: _t(rng.uniform(0, 1, l[i].numel())) for i in l}
+    node.beta = {i: _t(rng.uniform(0, 1, l[i].numel())) * (node.S[i] != 0) for i in l}
+    node.gamma = {i: _t(rng.uniform(0, 0.2, node.gamma[i].numel())) for i in l}
+    return node
+
+
+def _in_subdomain(net, node, X):
+    """Rows of X satisfying the node's split signs."""
+    keep = np.ones(X.shape[0], bool)
+    h = _t(X)
+    for i in range(1, net.R + 1):
+        zh = net.aff[i].forward(h)
+        S = node.S[i].numpy()
+        z = zh.numpy()
+        keep &= np.all((S[None, :] != 1) | (z <= 0), axis=1)
+        keep &= np.all((S[None, :] != -1) | (z >= 0), axis=1)
+        h = torch.clamp(zh, min=0)
+    return keep
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_soundness_random_parameters(seed):
+    """Every 0 <= alpha <= 1, beta, gamma >= 0 gives a sound bound (Sec. 3.1):
+    lb <= f_r at 10^4 samples of the subdomain and at x*; root bounds contain
+    every sampled pre-activation."""
+    L, C, d, lo, hi, prep = _small_case(seed, eps=0.15)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    assert m, "expected multi-neuron constraints on this case"
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(lo, hi, size=(10000, lo.size))
+    h = _t(X)
+    for i in range(1, net.R + 1):
+        zh = net.aff[i].forward(h)
+        assert bool((zh >= l[i] - 1e-9).all()) and bool((zh <= u[i] + 1e-9).all())
+        h = torch.clamp(zh, min=0)
+    for trial in range(4):
+        node = _random_node(prep, rng, n_splits=trial)
+        lb, xs, _ = core.final_bound(net, node, node.alpha, node.beta, node.gamma, dense, lo_t, hi_t)
+        keep = _in_subdomain(net, node, X)
+        f = net.forward(_t(X[keep]))[:, node.row].numpy()
+        if f.size:
+            assert float(lb) <= f.min() + 1e-9
+        # intermediate bounds of the node contain the subdomain's pre-activations
+        h = _t(X[keep])
+        for i in range(1, net.R + 1):
+            zh = net.aff[i].forward(h)
+            assert bool((zh >= node.l[i] - 1e-9).all()) and bool((zh <= node.u[i] + 1e-9).all())
+            h = torch.clamp(zh, min=0)
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_lower_bounds_below_exact_minimum(seed):
+    """2->8->8->2: DeepPoly and optimised bounds never exceed the exact minimum
+    from activation-pattern enumeration with an LP per pattern."""
+    L, C, d, lo, hi, prep = _small_case(seed, dims=(2, 8, 8, 2), eps=0.15)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    ex, xarg = exact.exact_min(L, C, d, 0, lo, hi)
+    node = bab.root_node(net, 0, l, u, S, m)
+    lb_dp, _ = core.deeppoly_final(net, node, lo_t, hi_t)
+    best, bx, *_ = core.optimize(net, node, dense, lo_t, hi_t, core.AdamHP(steps=40))
+    assert float(lb_dp) <= ex + 1e-9
+    assert best <= ex + 1e-9
+    assert best >= float(lb_dp) - 1e-12
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_fully_split_leaf_reaches_lp_optimum(seed):
+    """Completeness limit (Sec. 3.3): once every unstable neuron is split the
+    relaxation is exact and optimising beta approaches the LP optimum of the
+    subproblem from below."""
+    L, C, d, lo, hi, prep = _small_case(seed, dims=(2, 6, 6, 2), eps=0.2, with_mnc=False)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(lo, hi, size=(1, 2))
+    # split every unstable neuron by the pattern of a sampled point (feasible leaf)
+    node = bab.root_node(net, 0, l, u, S, None)
+    h = _t(X)
+    splits = {}
+    for i in range(1, net.R + 1):
+        zh = net.aff[i].forward(h)[0]
+        for j in range(zh.numel()):
+            if node.l[i][j] < 0 < node.u[i][j]:
+                sgn = 1 if zh[j] <= 0 else -1
+                node.S[i][j] = sgn
+                splits[(i, j)] = sgn
+                if sgn == 1:
+                    node.u[i][j] = 0.0
+                else:
+                    node.l[i][j] = 0.0
+        h = torch.clamp(zh[None], min=0)
+    ex, _ = exact.exact_min(L, C, d, 0, lo, hi, splits=splits)
+    best, *_ = core.optimize(net, node, None, lo_t, hi_t, core.AdamHP(steps=600, lr_beta=0.02))
+    assert best <= ex + 1e-9
+    assert best >= ex - 2e-2 * (1 + abs(ex))
+
+
+def test_gradient_matches_finite_differences():
+    """Reverse-mode gradient of the bound w.r.t. alpha, beta, gamma equals
+    central finite differences (FP64, h = 1e-6) away from case switches."""
+    L, C, d, lo, hi, prep = _small_case(7)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    rng = np.random.default_rng(7)
+    node = _random_node(prep, rng, n_splits=2)
+    lb, _, ga, gb, gg = core.bound_and_grad(net, node, node.alpha, node.beta, node.gamma,
+                                            dense, lo_t, hi_t)
+
+    def f(al, be, gm):
+        v, _, _ = core.final_bound(net, node, al, be, gm, dense, lo_t, hi_t)
+        return float(v)
+
+    h = 1e-6
+    checked = 0
+    for grp, G in (("a", ga), ("b", gb), ("g", gg)):
+        for i in G:
+            nz = torch.nonzero(G[i]).reshape(-1)
+            for j in nz[:6].tolist():
+                P = [{k: v.clone() for k, v in D.items()} for D in (node.alpha, node.beta, node.gamma)]
+                M = [{k: v.clone() for k, v in D.items()} for D in (node.alpha, node.beta, node.gamma)]
+                gi = "abg".index(grp)
+                P[gi][i][j] += h
+                M[gi][i][j] -= h
+                fd = (f(*P) - f(*M)) / (2 * h)
+                assert fd == pytest.approx(float(G[i][j]), rel=1e-6, abs=1e-9)
+                checked += 1
+    assert checked >= 10
+
+
+# --------------------------------------------------------------------------
+# multi-neuron constraints
+# --------------------------------------------------------------------------
+def test_mnc_rows_are_sound_per_orthant():
+    """Every constraint row holds on {octahedron and orthant} (LP per orthant)
+    and at sampled network activations."""
+    L, C, d, lo, hi, prep = _small_case(8)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    t = sorted(m)[0]
+    rows = m[t]
+    groups = sorted(set(map(tuple, rows.idx.tolist())))[:3]
+    ob = mnc.octahedron_bounds(net, t, groups, l, u, S, lo_t, hi_t)
+    for G, lbs in zip(groups, ob):
+        sel = np.nonzero((rows.idx == np.array(G)).all(1))[0]
+        for e in sel[:40]:
+            for sig in itertools.product((-1.0, 1.0), repeat=3):
+                sig = np.array(sig)
+                # variables x (3); y = x on positive coordinates, 0 otherwise
+                cy = np.where(sig > 0, rows.P[e], 0.0)
+                obj = -(cy + rows.Ph[e])
+                A_ub = np.concatenate([-mnc.DIRS, -np.diag(sig)])
+                b_ub = np.concatenate([-lbs, np.zeros(3)])
+                r = linprog(obj, A_ub=A_ub, b_ub=b_ub, bounds=[(None, None)] * 3, method="highs")
+                if r.status == 0:
+                    assert -r.fun <= rows.p[e] + 1e-9
+    rng = np.random.default_rng(8)
+    X = _t(rng.uniform(lo, hi, size=(5000, lo.size)))
+    h = X
+    for i in range(1, t + 1):
+        zh = net.aff[i].forward(h)
+        h = torch.clamp(zh, min=0)
+    z, zh = h.numpy(), zh.numpy()
+    viol = (rows.P * z[:, rows.idx]).sum(-1) + (rows.Ph * zh[:, rows.idx]).sum(-1) - rows.p
+    assert viol.max() <= 1e-9
+
+
+# --------------------------------------------------------------------------
+# branching and counterexamples
+# --------------------------------------------------------------------------
+def test_acs_scores_by_hand():
+    """s_j = |(gamma^T P)_j| + |(gamma^T Phat)_j| over unstable unsplit neurons
+    (Sec. 3.2); ties go to the lowest (layer, index)."""
+    l = {1: _t([-1, -1, -1, 1]), 2: _t([-1, -1])}
+    u = {1: _t([1, 1, 1, 2]), 2: _t([1, 1])}
+    S = {1: torch.zeros(4, dtype=torch.int8), 2: torch.tensor([0, -1], dtype=torch.int8)}
+    m1 = core.MNC(np.array([[0, 1, 2], [0, 1, 2]]), np.array([[1.0, 0, 0], [0, -2.0, 0]]),
+                  np.array([[0, 0, 1.0], [0, 0, 0]]), np.array([0.0, 0.0]))
+    m2 = core.MNC(np.array([[0, 1, 0]]), np.array([[0.0, 3.0, 0]]), np.array([[0.1, 0, 0]]),
+                  np.array([0.0]))
+    dense = {1: m1.dense(4), 2: m2.dense(2)}
+    node = core.Node(0, l, u, S, {}, {}, {}, split_layer=2)
+    gamma = {1: _t([0.5, 0.3]), 2: _t([2.0])}
+    sc, fb = core.acs_scores(node, gamma, dense, None)
+    assert not fb
+    assert np.allclose(sc[1].numpy()[:3], [0.5, 0.6, 0.5])
+    assert sc[1][3] == -math.inf and sc[2][1] == -math.inf   # stable / split
+    assert float(sc[2][0]) == pytest.approx(0.2)
+    assert core.pick_split(sc)[:2] == (1, 1)
+    gamma = {1: _t([0.5, 0.25]), 2: _t([0.0])}
+    sc, _ = core.acs_scores(node, gamma, dense, None)
+    assert core.pick_split(sc)[:2] == (1, 0)    # three-way tie at 0.5
+    # no active constraint: intercept fallback |a'_j| (-l u / (u - l))
+    gamma = {1: _t([0.0, 0.0]), 2: _t([0.0])}
+    aps = {1: _t([[1.0, -3.0, 0.5, 9.0]]), 2: _t([[0.1, 5.0]])}
+    sc, fb = core.acs_scores(node, gamma, dense, aps)
+    assert fb and np.allclose(sc[1].numpy()[:3], [0.5, 1.5, 0.25])
+    assert core.pick_split(sc)[:2] == (1, 1)
+
+
+def test_counterexamples_are_real():
+    """Every FALSIFIED verdict carries x* in the box with f_r(x*) < 0 under an
+    independent float64 forward pass (Sec. 3.1, upper bounding)."""
+    L = synth.tiny_fc_net(11, [16, 12, 12, 4])
+    n_fals = 0
+    for p in range(6):
+        x0 = np.random.default_rng(200 + p).uniform(0.2, 0.8, 16).astype(np.float32)
+        y = synth.net_forward(L, x0)
+        C, d = synth.property_rows(int(np.argmax(y)), 4)
+        lo, hi = synth.input_box(x0, 0.25)
+        r = bab.verify(L, C, d, lo, hi, max_nodes=20, hp=core.AdamHP(steps=5))
+        if r.verdict == bab.FALSIFIED:
+            n_fals += 1
+            nr = r.nodes[-1]
+            assert np.all(nr.xstar >= lo - 1e-12) and np.all(nr.xstar <= hi + 1e-12)
+            m = C @ synth.net_forward(L, nr.xstar) + d
+            assert m[nr.row] < 0
+    assert n_fals >= 1
+
+
+def test_children_keep_earlier_bounds():
+    """Bounds of layers up to and including the split layer are not recomputed
+    (Sec. 3.2, enforcing splits); later layers only tighten."""
+    L, C, d, lo, hi, prep = _small_case(9, with_mnc=False)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    node = bab.root_node(net, 0, l, u, S, None)
+    j = int(torch.nonzero((l[1] < 0) & (u[1] > 0))[0])
+    kids = bab.children(node, (node.alpha, node.beta, node.gamma), (1, j, 0.0), 1)
+    for ch in kids:
+        core.rebound_node(net, ch, lo_t, hi_t)
+        assert torch.equal(ch.l[1][torch.arange(l[1].numel()) != j], l[1][torch.arange(l[1].numel()) != j])
+        assert bool((ch.l[2] >= l[2] - 1e-12).all()) and bool((ch.u[2] <= u[2] + 1e-12).all())
+    assert float(kids[0].u[1][j]) == 0.0 and int(kids[0].S[1][j]) == 1
+    assert float(kids[1].l[1][j]) == 0.0 and int(kids[1].S[1][j]) == -1
