@@ -1,0 +1,240 @@
+/*
+ * mnbab.h -- C ABI of the GB300 library for batched MN-BaB bounding.
+ *
+ * The library bounds branch-and-bound (BaB) subproblems of the neural-network
+ * verification problem min_{x in D} f(x) (Sec. 2.1, Eq. 1), with the linear
+ * property folded into a final affine layer so that the goal is f(x) > 0, by
+ * back-substitution through affine and ReLU layers with optimisable slopes
+ * alpha, split multipliers beta and multi-neuron-constraint multipliers gamma
+ * (Sec. 3.1), projected Adam ascent on those parameters (Sec. 3.1), Active
+ * Constraint Score branching (Sec. 3.2) and a FIFO BaB queue (Sec. 2.2).
+ *
+ * Conventions
+ *  - Every call returns an mnbab_status; nothing throws across the ABI.
+ *  - Host pointers passed in are read before the call returns and stay owned
+ *    by the caller; outputs go to caller-allocated host memory.
+ *  - Handles are opaque.  Device memory is owned by the context, allocated with
+ *    cudaMalloc within the context's HBM budget, and freed by mnbab_destroy.
+ *  - All work of a context runs on its stream (mnbab_options.stream, or a
+ *    stream the library creates); calls are synchronous with respect to the
+ *    host unless stated otherwise.  One context per host thread.
+ *  - Floating point is IEEE FP32 on the device; the library re-checks every
+ *    counterexample with an FP64 forward pass on the host.
+ *  - Errors: MNBAB_E_INVALID_ARG for bad handles, sizes or shapes;
+ *    MNBAB_E_BUDGET when the HBM budget or a pool capacity would be exceeded;
+ *    MNBAB_E_DEVICE for CUDA errors; MNBAB_E_UNSUPPORTED for layer kinds or
+ *    shapes this build does not handle.  mnbab_last_error() gives the text.
+ */
+#ifndef MNBAB_H
+#define MNBAB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mnbab_status;
+#define MNBAB_OK 0
+#define MNBAB_E_INVALID_ARG (-1)
+#define MNBAB_E_BUDGET (-2)
+#define MNBAB_E_DEVICE (-3)
+#define MNBAB_E_TIMEOUT (-4)
+#define MNBAB_E_UNSUPPORTED (-5)
+
+/* verdicts (Sec. 2.2): a lower bound > 0 on every subdomain verifies, an
+ * input with f_r(x) < 0 falsifies */
+#define MNBAB_UNKNOWN 0
+#define MNBAB_VERIFIED 1
+#define MNBAB_FALSIFIED (-1)
+
+typedef struct mnbab_ctx mnbab_ctx;
+typedef struct mnbab_net mnbab_net;
+typedef struct mnbab_prop mnbab_prop;
+
+/* A node id names one BaB subproblem held in the context's device node pool. */
+typedef int64_t mnbab_node_id;
+
+typedef struct {
+  int32_t device;              /* CUDA device ordinal */
+  uint64_t hbm_budget_bytes;   /* cap on the context's device allocations; 0 = 64 GiB */
+  void* stream;                /* cudaStream_t to run on; NULL = a stream of the library */
+  int32_t node_capacity;       /* node slots per network pool; 0 = 65536 */
+  int32_t max_mnc_rows;        /* gamma entries per node (sum over layers); 0 = none */
+  int32_t row_chunk;           /* max back-substitution rows per launch; 0 = 32768, at most 65534 */
+} mnbab_options;
+
+/* Layer kinds.  A network is a chain affine, RELU, affine, ..., affine. */
+#define MNBAB_FC 1
+#define MNBAB_CONV2D 2
+#define MNBAB_RELU 3
+#define MNBAB_ADD 4 /* residual sum; not supported by this build */
+
+typedef struct {
+  int32_t kind;
+  /* FC: in_c = in features, out_c = out features, spatial sizes 1.
+   * CONV2D: input in_c x in_h x in_w, output out_c x out_h x out_w,
+   *         square kernel k, stride, zero padding pad (all sides). */
+  int32_t in_c, in_h, in_w;
+  int32_t out_c, out_h, out_w;
+  int32_t k, stride, pad;
+  const float* W; /* FC [out_c][in_c]; CONV2D [out_c][in_c][k][k]; row-major */
+  const float* b; /* [out_c] */
+  int32_t src_a, src_b; /* ADD only */
+} mnbab_layer_desc;
+
+/* Projected Adam ascent on (alpha, beta, gamma) (Sec. 3.1). */
+typedef struct {
+  int32_t steps;   /* gradient steps; the bound is evaluated steps + 1 times */
+  float lr_alpha, lr_beta, lr_gamma;
+  float beta1, beta2, eps;
+} mnbab_adam;
+
+typedef struct {
+  int32_t nodes_bounded;   /* subproblems bounded in this step */
+  int32_t nodes_verified;  /* closed with lower bound > 0 */
+  int32_t nodes_falsified; /* closed with an FP64-confirmed counterexample */
+  int32_t nodes_branched;  /* split into two children */
+  int32_t nodes_leaf;      /* open but nothing left to split */
+  int32_t props_done;      /* properties with a final verdict after this step */
+  int64_t rows_rebounded;  /* intermediate-bound rows back-substituted */
+} mnbab_step_stats;
+
+/* One record per bounded node, in bounding order (for traces and tests). */
+typedef struct {
+  int64_t seq;           /* FIFO node number within the property */
+  int32_t row;           /* property row */
+  int32_t depth;
+  float lb;              /* node lower bound (best of DeepPoly pass and Adam iterates) */
+  float lb_deeppoly;
+  float f_xstar;         /* f_r at the minimiser x* (FP64 host value) */
+  int32_t verdict;       /* MNBAB_VERIFIED / _FALSIFIED / _UNKNOWN (branched or leaf) */
+  int32_t split_layer;   /* ReLU layer (1-based) of the chosen split, 0 if none */
+  int32_t split_neuron;
+  int32_t fallback;      /* 1 if the split came from the intercept fallback score */
+} mnbab_trace_rec;
+
+/* ---- context ---------------------------------------------------------- */
+/* Creates a context on opt->device.  opt may be NULL for defaults. */
+mnbab_status mnbab_create(const mnbab_options* opt, mnbab_ctx** out);
+/* Frees every device allocation, network and property of the context. */
+void mnbab_destroy(mnbab_ctx* ctx);
+/* Text of the last error of this context; valid until its next call. */
+const char* mnbab_last_error(const mnbab_ctx* ctx);
+
+/* ---- network and property (Sec. 2.1, Eq. 1) --------------------------- */
+/* Copies a chain network to the device.  The last layer must be FC; its
+ * outputs are the logits that properties fold into (Sec. 2.1). */
+mnbab_status mnbab_load_network(mnbab_ctx* ctx, const mnbab_layer_desc* layers, int32_t n_layers,
+                                mnbab_net** out);
+
+/* Sets a property: input box x_lo <= x <= x_hi (d0 floats each, the clipped
+ * L-inf ball of Sec. 2.1) and rows C f(x) + d > 0 (C [n_rows][n_out]
+ * row-major, d [n_rows]).  Folds C into the last layer, computes the DeepPoly
+ * intermediate bounds of every ReLU layer on the device (Sec. 3.1, one
+ * back-substitution per neuron and side), and queues one root node per row.
+ * *out stays valid until mnbab_destroy. */
+mnbab_status mnbab_set_property(mnbab_ctx* ctx, const mnbab_net* net, const float* x_lo,
+                                const float* x_hi, const float* C, const float* d,
+                                int32_t n_rows, mnbab_prop** out);
+
+/* Root bounds l, u of ReLU layer relu_layer (1-based), d_i floats each. */
+mnbab_status mnbab_get_root_bounds(const mnbab_ctx* ctx, const mnbab_prop* prop,
+                                   int32_t relu_layer, float* l_out, float* u_out);
+
+/* Uploads the multi-neuron constraints P z + Phat zhat - p <= 0 of one ReLU
+ * layer (Sec. 3.1, enforcing multi-neuron constraints), n_rows rows over k
+ * neurons each: idx [n_rows][k] neuron indices, P and Phat [n_rows][k], p
+ * [n_rows].  Called once per layer after mnbab_set_property and before any
+ * bounding; gamma of existing nodes starts at 0. */
+mnbab_status mnbab_set_mnc(mnbab_ctx* ctx, mnbab_prop* prop, int32_t relu_layer, int32_t n_rows,
+                           int32_t k, const int32_t* idx, const float* P, const float* Phat,
+                           const float* p);
+
+/* ---- nodes ------------------------------------------------------------- */
+/* A fresh root node of property row `row` outside the property's BaB queue
+ * (root bounds, DeepPoly slopes, beta = gamma = 0). */
+mnbab_status mnbab_node_root(mnbab_ctx* ctx, mnbab_prop* prop, int32_t row, mnbab_node_id* out);
+mnbab_status mnbab_node_free(mnbab_ctx* ctx, mnbab_node_id node);
+
+/* Parameter block of a node, little-endian, in this order:
+ *   int32 split_layer (0..R; layers > split_layer are re-bounded by the next
+ *         mnbab_bound_batch), int32 R, int32 SD = sum_i d_i, int32 E,
+ *   float l[SD], float u[SD], int8 S[SD], float alpha[SD], float beta[SD],
+ *   float gamma[E]
+ * where per-neuron arrays concatenate ReLU layers 1..R and S uses the split
+ * encoding of Sec. 3.1 (-1 positive split, +1 negative split, 0 none).
+ * With host_buf NULL, *bytes receives the size. */
+mnbab_status mnbab_export_params(const mnbab_ctx* ctx, mnbab_node_id node, void* host_buf,
+                                 size_t* bytes);
+mnbab_status mnbab_import_params(mnbab_ctx* ctx, mnbab_node_id node, const void* host_buf,
+                                 size_t bytes);
+
+/* ---- bounding (Sec. 3.1) --------------------------------------------- */
+/* For each node: re-bound the ReLU layers after its split layer (only its
+ * unstable, unsplit neurons, with DeepPoly slopes and beta = gamma = 0,
+ * intersected with its current bounds; Sec. 3.2 enforcing splits), then bound
+ * its objective row at its current (alpha, beta, gamma).  lb_out[i] gets the
+ * lower bound, ub_out[i] (nullable) f_r(x*) at the minimiser x* (FP32). */
+mnbab_status mnbab_bound_batch(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
+                               float* lb_out, float* ub_out);
+
+/* The DeepPoly pass of each node's objective (slopes from the area
+ * heuristic, beta = gamma = 0); nodes must already be re-bounded. */
+mnbab_status mnbab_deeppoly_batch(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
+                                  float* lb_out);
+
+/* The objective bound at the node's parameters and its gradient w.r.t.
+ * (alpha, beta, gamma) from the adjoint back-substitution: grad_out holds
+ * n * (2 * SD + E) floats, per node alpha[SD], beta[SD], gamma[E]. */
+mnbab_status mnbab_bound_grad(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
+                              float* lb_out, float* grad_out);
+
+/* cfg->steps projected Adam steps from each node's current parameters
+ * (alpha clamped to [0, 1], beta, gamma >= 0).  best_lb_out[i] = the best
+ * bound over the steps + 1 evaluated iterates; the node keeps the last
+ * iterate's parameters.  Nodes must already be re-bounded. */
+mnbab_status mnbab_optimize(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
+                            const mnbab_adam* cfg, float* best_lb_out);
+
+/* ACS branching score (Sec. 3.2) at each node's current parameters:
+ * s_j = |(gamma^T P)_j| + |(gamma^T Phat)_j| over unstable unsplit neurons,
+ * or, when every candidate scores 0, the intercept score
+ * |a'_j| (-l_j u_j / (u_j - l_j)).  Picks the lowest (layer, neuron) among
+ * scores within 1e-5 (relative) of the maximum.  layer_out is 0 when the
+ * node has no candidate. */
+mnbab_status mnbab_score_branches(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
+                                  int32_t* layer_out, int32_t* neuron_out, float* score_out);
+
+/* ---- branch and bound (Sec. 2.2, Sec. 3.2) ----------------------------- */
+/* One BaB step over the given properties (all of one network): pops up to
+ * max_nodes open nodes in FIFO order from their queues (within each
+ * property's node budget), re-bounds, runs the DeepPoly pass, optimises the
+ * nodes it does not verify, checks the minimiser for a counterexample,
+ * branches the rest by ACS and queues their two children.  cfg may be NULL
+ * (20 steps, default rates).  max_nodes is clamped to the context's batch
+ * capacity. */
+mnbab_status mnbab_bab_step(mnbab_ctx* ctx, mnbab_prop* const* props, int32_t n_props,
+                            int32_t max_nodes, const mnbab_adam* cfg, mnbab_step_stats* out);
+
+/* Per-property node budget (bounded nodes including roots); default 256. */
+mnbab_status mnbab_set_budget(mnbab_ctx* ctx, mnbab_prop* prop, int32_t max_nodes);
+
+/* Verdict of a property (row < 0) or of one row.  lb (nullable) = the lowest
+ * open or leaf lower bound seen (+inf if verified).  x_cex (nullable, d0
+ * floats) receives the counterexample when FALSIFIED. */
+mnbab_status mnbab_get_verdict(const mnbab_ctx* ctx, const mnbab_prop* prop, int32_t row,
+                               int32_t* verdict, float* lb, float* x_cex);
+
+/* Copies up to max_recs trace records of the property's bounded nodes. */
+mnbab_status mnbab_get_trace(const mnbab_ctx* ctx, const mnbab_prop* prop, mnbab_trace_rec* recs,
+                             int32_t max_recs, int32_t* n_out);
+
+/* Number of open nodes queued for the property. */
+mnbab_status mnbab_queue_size(const mnbab_ctx* ctx, const mnbab_prop* prop, int32_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MNBAB_H */

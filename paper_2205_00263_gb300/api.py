@@ -1,0 +1,272 @@
+"""Thin Python binding of libmnbab: argument marshalling only.
+
+Every step of the bounding path runs in the library's CUDA kernels; this
+module converts numpy arrays to C pointers, checks status codes and raises
+``MnbabError`` with the library's message.  The library owns its device
+memory; the optional torch stream handle is only passed through.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as L
+
+
+class MnbabError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libmnbab error {code}: {msg}")
+        self.code = code
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(L.FP)
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(L.IP)
+
+
+@dataclass
+class NodeParams:
+    """Parameter block of one node (mnbab_export_params layout)."""
+    split_layer: int
+    R: int
+    l: np.ndarray
+    u: np.ndarray
+    S: np.ndarray
+    alpha: np.ndarray
+    beta: np.ndarray
+    gamma: np.ndarray
+
+    def pack(self) -> bytes:
+        SD = self.l.size
+        hdr = np.array([self.split_layer, self.R, SD, self.gamma.size], dtype=np.int32)
+        return b"".join([hdr.tobytes(), _f32(self.l).tobytes(), _f32(self.u).tobytes(),
+                         np.asarray(self.S, np.int8).tobytes(), _f32(self.alpha).tobytes(),
+                         _f32(self.beta).tobytes(), _f32(self.gamma).tobytes()])
+
+    @staticmethod
+    def unpack(buf: bytes) -> "NodeParams":
+        hdr = np.frombuffer(buf[:16], dtype=np.int32)
+        split, R, SD, E = (int(v) for v in hdr)
+        o = 16
+        def take(dt, n, size):
+            nonlocal o
+            a = np.frombuffer(buf[o:o + n * size], dtype=dt).copy()
+            o += n * size
+            return a
+        l = take(np.float32, SD, 4)
+        u = take(np.float32, SD, 4)
+        S = take(np.int8, SD, 1)
+        al = take(np.float32, SD, 4)
+        be = take(np.float32, SD, 4)
+        ga = take(np.float32, E, 4)
+        return NodeParams(split, R, l, u, S, al, be, ga)
+
+
+class Net:
+    def __init__(self, ctx: "Context", handle, layers):
+        self.ctx, self.h = ctx, handle
+        self.dims = []
+        self.d0 = None
+        for Ly in layers:
+            if Ly["kind"] == "relu":
+                continue
+            if self.d0 is None:
+                self.d0 = int(np.prod(Ly["W"].shape[1:])) if Ly["kind"] == "fc" else int(np.prod(Ly["in_shape"]))
+            self.dims.append(Ly["W"].shape[0] if Ly["kind"] == "fc" else int(np.prod(Ly["out_shape"])))
+        self.relu_dims = self.dims[:-1]
+        self.R = len(self.relu_dims)
+        self.SD = int(sum(self.relu_dims))
+
+
+class Prop:
+    def __init__(self, ctx: "Context", handle, net: Net, n_rows: int):
+        self.ctx, self.h, self.net, self.n_rows = ctx, handle, net, n_rows
+
+
+class Context:
+    """One libmnbab context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, stream=None,
+                 node_capacity: int = 0, max_mnc_rows: int = 0, row_chunk: int = 0):
+        self.lib = L.load()
+        o = L.Options(device, hbm_budget_bytes, stream, node_capacity, max_mnc_rows, row_chunk)
+        h = C.c_void_p()
+        st = self.lib.mnbab_create(C.byref(o), C.byref(h))
+        if st != 0:
+            raise MnbabError(st, "mnbab_create failed (no CUDA device?)")
+        self.h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mnbab_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _ck(self, st):
+        if st != 0:
+            msg = self.lib.mnbab_last_error(self.h)
+            raise MnbabError(st, msg.decode() if msg else "")
+
+    # ---- network / property ------------------------------------------------
+    def load_network(self, layers: list[dict]) -> Net:
+        descs = (L.LayerDesc * len(layers))()
+        keep = []
+        for i, Ly in enumerate(layers):
+            d = descs[i]
+            if Ly["kind"] == "relu":
+                d.kind = L.RELU
+                continue
+            W = _f32(Ly["W"])
+            b = _f32(Ly["b"])
+            keep += [W, b]
+            d.W, d.b = _fp(W), _fp(b)
+            if Ly["kind"] == "fc":
+                d.kind = L.FC
+                d.in_c, d.in_h, d.in_w = W.shape[1], 1, 1
+                d.out_c, d.out_h, d.out_w = W.shape[0], 1, 1
+                d.k, d.stride, d.pad = 1, 1, 0
+            else:
+                d.kind = L.CONV2D
+                d.in_c, d.in_h, d.in_w = Ly["in_shape"]
+                d.out_c, d.out_h, d.out_w = Ly["out_shape"]
+                d.k, d.stride, d.pad = W.shape[2], Ly["stride"], Ly["pad"]
+        h = C.c_void_p()
+        self._ck(self.lib.mnbab_load_network(self.h, descs, len(layers), C.byref(h)))
+        return Net(self, h, layers)
+
+    def set_property(self, net: Net, lo, hi, Cm, d=None) -> Prop:
+        lo, hi, Cm = _f32(lo).reshape(-1), _f32(hi).reshape(-1), _f32(Cm)
+        d = np.zeros(Cm.shape[0], np.float32) if d is None else _f32(d)
+        h = C.c_void_p()
+        self._ck(self.lib.mnbab_set_property(self.h, net.h, _fp(lo), _fp(hi), _fp(Cm), _fp(d),
+                                             Cm.shape[0], C.byref(h)))
+        return Prop(self, h, net, Cm.shape[0])
+
+    def root_bounds(self, prop: Prop, layer: int):
+        d = prop.net.relu_dims[layer - 1]
+        l = np.empty(d, np.float32)
+        u = np.empty(d, np.float32)
+        self._ck(self.lib.mnbab_get_root_bounds(self.h, prop.h, layer, _fp(l), _fp(u)))
+        return l, u
+
+    def set_mnc(self, prop: Prop, layer: int, idx, P, Ph, p):
+        idx = np.ascontiguousarray(np.asarray(idx, np.int32))
+        P, Ph, p = _f32(P), _f32(Ph), _f32(p)
+        n_rows = idx.shape[0]
+        k = idx.shape[1] if idx.ndim == 2 else 3
+        self._ck(self.lib.mnbab_set_mnc(self.h, prop.h, layer, n_rows, k, _ip(idx), _fp(P),
+                                        _fp(Ph), _fp(p)))
+
+    def set_budget(self, prop: Prop, n: int):
+        self._ck(self.lib.mnbab_set_budget(self.h, prop.h, n))
+
+    # ---- nodes ------------------------------------------------------------
+    def node_root(self, prop: Prop, row: int) -> int:
+        out = L.node_id()
+        self._ck(self.lib.mnbab_node_root(self.h, prop.h, row, C.byref(out)))
+        return out.value
+
+    def node_free(self, node: int):
+        self._ck(self.lib.mnbab_node_free(self.h, node))
+
+    def export_params(self, node: int) -> NodeParams:
+        n = C.c_size_t()
+        self._ck(self.lib.mnbab_export_params(self.h, node, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._ck(self.lib.mnbab_export_params(self.h, node, buf, C.byref(n)))
+        return NodeParams.unpack(buf.raw)
+
+    def import_params(self, node: int, p: NodeParams):
+        b = p.pack()
+        self._ck(self.lib.mnbab_import_params(self.h, node, b, len(b)))
+
+    @staticmethod
+    def _ids(nodes):
+        a = (L.node_id * len(nodes))(*nodes)
+        return a, len(nodes)
+
+    def bound_batch(self, nodes, with_ub=True):
+        ids, n = self._ids(nodes)
+        lb = np.empty(n, np.float32)
+        ub = np.empty(n, np.float32) if with_ub else None
+        self._ck(self.lib.mnbab_bound_batch(self.h, ids, n, _fp(lb), _fp(ub) if with_ub else None))
+        return (lb, ub) if with_ub else lb
+
+    def deeppoly_batch(self, nodes):
+        ids, n = self._ids(nodes)
+        lb = np.empty(n, np.float32)
+        self._ck(self.lib.mnbab_deeppoly_batch(self.h, ids, n, _fp(lb)))
+        return lb
+
+    def bound_grad(self, nodes, SD: int, E: int):
+        ids, n = self._ids(nodes)
+        lb = np.empty(n, np.float32)
+        g = np.empty(n * (2 * SD + E), np.float32)
+        self._ck(self.lib.mnbab_bound_grad(self.h, ids, n, _fp(lb), _fp(g)))
+        g = g.reshape(n, 2 * SD + E)
+        return lb, g[:, :SD], g[:, SD:2 * SD], g[:, 2 * SD:]
+
+    def optimize(self, nodes, steps=20, lr_alpha=0.1, lr_beta=0.05, lr_gamma=0.05, beta1=0.9,
+                 beta2=0.999, eps=1e-8):
+        ids, n = self._ids(nodes)
+        a = L.Adam(steps, lr_alpha, lr_beta, lr_gamma, beta1, beta2, eps)
+        best = np.empty(n, np.float32)
+        self._ck(self.lib.mnbab_optimize(self.h, ids, n, C.byref(a), _fp(best)))
+        return best
+
+    def score_branches(self, nodes):
+        ids, n = self._ids(nodes)
+        lay = np.empty(n, np.int32)
+        neu = np.empty(n, np.int32)
+        sc = np.empty(n, np.float32)
+        self._ck(self.lib.mnbab_score_branches(self.h, ids, n, _ip(lay), _ip(neu), _fp(sc)))
+        return lay, neu, sc
+
+    # ---- branch and bound ----------------------------------------------------
+    def bab_step(self, props, max_nodes: int, steps: int = 20, adam: dict | None = None):
+        arr = (C.c_void_p * len(props))(*[p.h.value for p in props])
+        a = L.Adam(steps, *(adam or {}).get("rates", (0.1, 0.05, 0.05, 0.9, 0.999, 1e-8)))
+        st = L.StepStats()
+        self._ck(self.lib.mnbab_bab_step(self.h, arr, len(props), max_nodes, C.byref(a),
+                                         C.byref(st)))
+        return {k: getattr(st, k) for k, _ in L.StepStats._fields_}
+
+    def verdict(self, prop: Prop, row: int = -1):
+        v = C.c_int32()
+        lb = C.c_float()
+        x = np.zeros(prop.net.d0, np.float32)
+        self._ck(self.lib.mnbab_get_verdict(self.h, prop.h, row, C.byref(v), C.byref(lb), _fp(x)))
+        return v.value, lb.value, x
+
+    def trace(self, prop: Prop):
+        n = C.c_int32()
+        self._ck(self.lib.mnbab_get_trace(self.h, prop.h, None, 0, C.byref(n)))
+        recs = (L.TraceRec * max(1, n.value))()
+        self._ck(self.lib.mnbab_get_trace(self.h, prop.h, recs, n.value, C.byref(n)))
+        return [{k: getattr(recs[i], k) for k, _ in L.TraceRec._fields_} for i in range(n.value)]
+
+    def queue_size(self, prop: Prop) -> int:
+        n = C.c_int32()
+        self._ck(self.lib.mnbab_queue_size(self.h, prop.h, C.byref(n)))
+        return n.value

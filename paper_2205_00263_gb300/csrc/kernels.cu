@@ -1,0 +1,893 @@
+// Device kernels of libmnbab: back-substitution through affine and ReLU layers
+// with fused relaxation epilogues (Sec. 3.1), concretisation over the input box
+// (Eq. minimum), the adjoint sweep for d lb / d (alpha, beta, gamma), projected
+// Adam, ACS scoring (Sec. 3.2) and the BaB node bookkeeping (Sec. 3.2, enforcing
+// splits).  All arithmetic is IEEE FP32 with FMA accumulation.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "mnbab_internal.h"
+
+namespace mnbab {
+
+// ---------------------------------------------------------------------------
+// epilogues
+// ---------------------------------------------------------------------------
+// ReLU back-substitution of one coefficient a on z_j (Sec. 3.1, combined ReLU
+// step): a' = a + (gamma^T P)_j, D / blow from the single-neuron table with
+// split precedence, ahat = a' D + beta S + (gamma^T Phat)_j.  The offset
+// contribution a' blow + ahat b_j (bias of the consuming affine layer) goes to
+// the row partial sum.
+__device__ __forceinline__ float epi_relu(const Epi& e, int m, int j, float a, float& part) {
+  const int n = e.row_node[m];
+  const size_t q = (size_t)n * e.SD + e.off + j;
+  const size_t qm = (size_t)m * e.SD + e.off + j;
+  const float l = e.pool.L[q], u = e.pool.U[q];
+  const int s = e.pool.S[q];
+  float ap = a;
+  if (e.GP) ap += e.GP[qm];
+  float D, bl = 0.f;
+  if (s == -1) D = 1.f;
+  else if (s == 1) D = 0.f;
+  else if (l >= 0.f) D = 1.f;
+  else if (u <= 0.f) D = 0.f;
+  else if (ap >= 0.f) D = e.final_mode ? e.pool.ALPHA[q] : (u >= -l ? 1.f : 0.f);
+  else {
+    const float den = u - l;
+    D = u / den;
+    bl = (-u * l) / den;
+  }
+  float ah = ap * D;
+  if (e.final_mode) ah += e.pool.BETA[q] * (float)s;
+  if (e.GPh) ah += e.GPh[qm];
+  if (e.AP) e.AP[qm] = ap;
+  part += ap * bl + ah * e.bias[j / e.bias_div];
+  return ah;
+}
+
+// Concretisation of a coefficient on input x_j over [lo, hi] (Eq. minimum):
+// x*_j = lo_j if a >= 0 else hi_j, contribution a x*_j.
+__device__ __forceinline__ float epi_conc(const Epi& e, int m, int j, float a, float& part) {
+  const int n = e.row_node[m];
+  const PropDev& P = e.props[e.pool.prop[n]];
+  const float x = a >= 0.f ? P.lo[j] : P.hi[j];
+  part += a * x;
+  if (e.X) e.X[(size_t)m * e.d0 + j] = x;
+  return a;
+}
+
+// Adjoint of the ReLU step at pre-activation adjoint h = d lb / d ahat_j:
+// d lb / d alpha_j = h a'_j on the alpha branch, d lb / d beta_j = h S_j,
+// and d lb / d a'_j = h D_j + blow_j flows to the next layer.
+__device__ __forceinline__ float epi_adj(const Epi& e, int m, int j, float h) {
+  const int n = e.row_node[m];
+  const size_t q = (size_t)n * e.SD + e.off + j;
+  const size_t qm = (size_t)m * e.SD + e.off + j;
+  const float l = e.pool.L[q], u = e.pool.U[q];
+  const int s = e.pool.S[q];
+  const float ap = e.AP[qm];
+  float D, bl = 0.f;
+  bool abr = false;
+  if (s == -1) D = 1.f;
+  else if (s == 1) D = 0.f;
+  else if (l >= 0.f) D = 1.f;
+  else if (u <= 0.f) D = 0.f;
+  else if (ap >= 0.f) { D = e.pool.ALPHA[q]; abr = true; }
+  else {
+    const float den = u - l;
+    D = u / den;
+    bl = (-u * l) / den;
+  }
+  e.GA[qm] = abr ? h * ap : 0.f;
+  e.GB[qm] = h * (float)s;
+  const float g = h * D + bl;
+  if (e.Hz) {
+    e.Hz[qm] = h;
+    e.Gz[qm] = g;
+  }
+  return g;
+}
+
+__device__ __forceinline__ float epi_apply(const Epi& e, int m, int j, float v, float& part) {
+  switch (e.kind) {
+    case EPI_RELU: return epi_relu(e, m, j, v, part);
+    case EPI_CONC: return epi_conc(e, m, j, v, part);
+    case EPI_ADJ: return epi_adj(e, m, j, v);
+    case EPI_FWD_RELU: return fmaxf(v, 0.f);
+    default: return v;
+  }
+}
+
+__device__ __forceinline__ bool epi_has_part(const Epi& e) {
+  return e.part != nullptr && (e.kind == EPI_RELU || e.kind == EPI_CONC);
+}
+
+// block-wide sum; every thread gets the result
+__device__ float block_sum(float v) {
+  __shared__ float sh[32];
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  float r = 0.f;
+  for (int i = 0; i < nw; ++i) r += sh[i];
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// starting rows
+// ---------------------------------------------------------------------------
+__global__ void k_init_rows(NetDev net, int t, RowsDev rows, float* out, int ld, Epi e) {
+  const int m = blockIdx.x;
+  if (m >= rows.M) return;
+  const int n = rows.node[m];
+  const int j = rows.j[m];
+  const float sg = rows.sign ? rows.sign[m] : 1.f;
+  const int width = net.d[t - 1];
+  float c0 = 0.f;
+  float part = 0.f;
+  if (t == net.R + 1) {
+    const PropDev& P = e.props[e.pool.prop[n]];
+    const float* w = P.Wf + (size_t)j * width;
+    c0 = P.bf[j];
+    for (int col = threadIdx.x; col < width; col += blockDim.x) {
+      const float o = epi_apply(e, m, col, w[col], part);
+      if (out) out[(size_t)m * ld + col] = o;
+    }
+  } else {
+    const LayerDev& L = net.aff[t];
+    if (L.kind == 1) {
+      c0 = sg * L.b[j];
+      const float* w = L.W + (size_t)j * width;
+      for (int col = threadIdx.x; col < width; col += blockDim.x) {
+        const float o = epi_apply(e, m, col, sg * w[col], part);
+        if (out) out[(size_t)m * ld + col] = o;
+      }
+    } else {
+      // row j = (co, oh, ow) of the convolution's Toeplitz matrix
+      const int hw = L.ho * L.wo;
+      const int co = j / hw, oh = (j % hw) / L.wo, ow = j % L.wo;
+      c0 = sg * L.b[co];
+      const int h0 = oh * L.s - L.p, w0 = ow * L.s - L.p;
+      const int ihw = L.hi * L.wi;
+      for (int col = threadIdx.x; col < width; col += blockDim.x) {
+        const int ci = col / ihw, ih = (col % ihw) / L.wi, iw = col % L.wi;
+        const int kh = ih - h0, kw = iw - w0;
+        float a = 0.f;
+        if (kh >= 0 && kh < L.k && kw >= 0 && kw < L.k)
+          a = sg * L.W[(((size_t)co * L.ci + ci) * L.k + kh) * L.k + kw];
+        const float o = epi_apply(e, m, col, a, part);
+        if (out) out[(size_t)m * ld + col] = o;
+      }
+    }
+  }
+  const float tot = block_sum(part);
+  if (threadIdx.x == 0 && e.part) e.part[(size_t)m * e.nslot + 0] = tot + c0;
+}
+
+void launch_init_rows(const NetDev& net, int t, const RowsDev& rows, float* out, int ld,
+                      const Epi& e, cudaStream_t st) {
+  if (rows.M <= 0) return;
+  k_init_rows<<<rows.M, 128, 0, st>>>(net, t, rows, out, ld, e);
+}
+
+// ---------------------------------------------------------------------------
+// dense GEMM C = A B (+ bias) with a fused epilogue; SIMT FP32, 64x64x16 tiles
+// ---------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* __restrict__ A,
+                                              int lda, const float* __restrict__ B, int ldb,
+                                              const float* __restrict__ bias, int bias_div,
+                                              float* C, int ldc, Epi e) {
+  __shared__ float As[GBK][GBM + 4];
+  __shared__ float Bs[GBK][GBN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += GBK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = (tid >> 4) + 16 * i, c = tid & 15;
+      const int gm = m0 + r, gk = k0 + c;
+      As[c][r] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = (tid >> 6) + 4 * i, c = tid & 63;
+      const int gk = k0 + r, gn = n0 + c;
+      Bs[r][c] = (gk < K && gn < N) ? B[(size_t)gk * ldb + gn] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float part[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if (bias) v += bias[n / bias_div];
+      const float o = epi_apply(e, m, n, v, part[i]);
+      if (C) C[(size_t)m * ldc + n] = o;
+    }
+  }
+  if (epi_has_part(e)) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float p = part[i];
+      for (int o = 8; o; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o, 16);
+      const int m = m0 + ty + 16 * i;
+      if (tx == 0 && m < M) e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = p;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// convolution: transposed (back-substitution) and forward (adjoint / forward)
+// ---------------------------------------------------------------------------
+// Input positions are enumerated phase-major (ih mod s, iw mod s) so that the
+// threads of a warp share kernel taps and read the weights from shared memory
+// as broadcasts.
+__device__ __forceinline__ void decode_phase(int pidx, int hi, int wi, int s, int& ih, int& iw) {
+  for (int ph = 0; ph < s; ++ph) {
+    const int nh = (hi - ph + s - 1) / s;
+    for (int pw = 0; pw < s; ++pw) {
+      const int nw = (wi - pw + s - 1) / s;
+      const int cnt = nh * nw;
+      if (pidx < cnt) {
+        ih = ph + s * (pidx / nw);
+        iw = pw + s * (pidx % nw);
+        return;
+      }
+      pidx -= cnt;
+    }
+  }
+  ih = iw = -1;
+}
+
+template <int CB>
+__global__ void __launch_bounds__(128) k_convT(int M, const float* __restrict__ in, int ld_in,
+                                               float* out, int ld_out, LayerDev L, Epi e) {
+  extern __shared__ float Ws[];
+  const int nW = L.co * L.ci * L.k * L.k;
+  for (int i = threadIdx.x; i < nW; i += blockDim.x) Ws[i] = L.W[i];
+  __syncthreads();
+  const int m = blockIdx.y;
+  const int Pin = L.hi * L.wi;
+  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
+  float part = 0.f;
+  if (pidx < Pin) {
+    int ih, iw;
+    decode_phase(pidx, L.hi, L.wi, L.s, ih, iw);
+    const float* lam = in + (size_t)m * ld_in;
+    const int kk = L.k * L.k;
+    const int hwo = L.ho * L.wo;
+    const int kh0 = (ih + L.p) % L.s, kw0 = (iw + L.p) % L.s;
+    for (int cb = 0; cb < L.ci; cb += CB) {
+      float acc[CB];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) acc[c] = 0.f;
+      for (int kh = kh0; kh < L.k; kh += L.s) {
+        const int th = ih + L.p - kh;
+        if (th < 0) break;
+        const int oh = th / L.s;
+        if (oh >= L.ho) continue;
+        for (int kw = kw0; kw < L.k; kw += L.s) {
+          const int tw = iw + L.p - kw;
+          if (tw < 0) break;
+          const int ow = tw / L.s;
+          if (ow >= L.wo) continue;
+          const float* lp = lam + oh * L.wo + ow;
+          const float* wp = Ws + (size_t)cb * kk + kh * L.k + kw;
+          for (int co = 0; co < L.co; ++co) {
+            const float v = lp[(size_t)co * hwo];
+            const float* w = wp + (size_t)co * L.ci * kk;
+#pragma unroll
+            for (int c = 0; c < CB; ++c)
+              if (CB == 1 || cb + c < L.ci) acc[c] = fmaf(v, w[c * kk], acc[c]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        const int ci = cb + c;
+        if (ci >= L.ci) break;
+        const int j = ci * Pin + ih * L.wi + iw;
+        const float o = epi_apply(e, m, j, acc[c], part);
+        if (out) out[(size_t)m * ld_out + j] = o;
+      }
+    }
+  }
+  if (epi_has_part(e)) {
+    const float tot = block_sum(part);
+    if (threadIdx.x == 0) e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = tot;
+  }
+}
+
+template <int CB>
+__global__ void __launch_bounds__(128) k_conv_fwd(int M, const float* __restrict__ in, int ld_in,
+                                                  float* out, int ld_out, LayerDev L, Epi e) {
+  extern __shared__ float Ws[];
+  const int nW = L.co * L.ci * L.k * L.k;
+  for (int i = threadIdx.x; i < nW; i += blockDim.x) Ws[i] = L.W[i];
+  __syncthreads();
+  const int m = blockIdx.y;
+  const int Pout = L.ho * L.wo;
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  float part = 0.f;
+  if (pos < Pout) {
+    const int oh = pos / L.wo, ow = pos % L.wo;
+    const float* x = in + (size_t)m * ld_in;
+    const int kk = L.k * L.k;
+    const int hwi = L.hi * L.wi;
+    for (int cb = 0; cb < L.co; cb += CB) {
+      float acc[CB];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) acc[c] = 0.f;
+      for (int ci = 0; ci < L.ci; ++ci) {
+        for (int kh = 0; kh < L.k; ++kh) {
+          const int ih = oh * L.s - L.p + kh;
+          if (ih < 0 || ih >= L.hi) continue;
+          for (int kw = 0; kw < L.k; ++kw) {
+            const int iw = ow * L.s - L.p + kw;
+            if (iw < 0 || iw >= L.wi) continue;
+            const float v = x[(size_t)ci * hwi + ih * L.wi + iw];
+            const float* w = Ws + ((size_t)cb * L.ci + ci) * kk + kh * L.k + kw;
+#pragma unroll
+            for (int c = 0; c < CB; ++c)
+              if (CB == 1 || cb + c < L.co) acc[c] = fmaf(v, w[(size_t)c * L.ci * kk], acc[c]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        const int co = cb + c;
+        if (co >= L.co) break;
+        const int j = co * Pout + pos;
+        const float o = epi_apply(e, m, j, acc[c] + L.b[co], part);
+        if (out) out[(size_t)m * ld_out + j] = o;
+      }
+    }
+  }
+  if (epi_has_part(e)) {
+    const float tot = block_sum(part);
+    if (threadIdx.x == 0) e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = tot;
+  }
+}
+
+template <typename F>
+static void set_smem(F f, int bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+int backsub_slots(const LayerDev& L) {
+  if (L.kind == 1) return (L.d_in + GBN - 1) / GBN;
+  return (L.hi * L.wi + 127) / 128;
+}
+
+int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
+                   const Epi& e, cudaStream_t st) {
+  if (M <= 0) return backsub_slots(L);
+  if (L.kind == 1) {
+    // Lambda [M][d_out] x W [d_out][d_in]
+    dim3 grid((L.d_in + GBN - 1) / GBN, (M + GBM - 1) / GBM);
+    k_gemm<<<grid, 256, 0, st>>>(M, L.d_in, L.d_out, in, ld_in, L.W, L.d_in, nullptr, 1, out,
+                                 ld_out, e);
+    return grid.x;
+  }
+  const int smem = L.co * L.ci * L.k * L.k * 4;
+  dim3 grid((L.hi * L.wi + 127) / 128, M);
+  if (L.ci <= 1) {
+    set_smem(k_convT<1>, smem);
+    k_convT<1><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+  } else if (L.ci <= 4) {
+    set_smem(k_convT<4>, smem);
+    k_convT<4><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+  } else if (L.ci <= 16) {
+    set_smem(k_convT<16>, smem);
+    k_convT<16><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+  } else {
+    set_smem(k_convT<32>, smem);
+    k_convT<32><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+  }
+  return grid.x;
+}
+
+void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
+                    const Epi& e, cudaStream_t st) {
+  if (M <= 0) return;
+  if (L.kind == 1) {
+    dim3 grid((L.d_out + GBN - 1) / GBN, (M + GBM - 1) / GBM);
+    k_gemm<<<grid, 256, 0, st>>>(M, L.d_out, L.d_in, in, ld_in, L.Wt, L.d_out, L.b, 1, out,
+                                 ld_out, e);
+    return;
+  }
+  const int smem = L.co * L.ci * L.k * L.k * 4;
+  dim3 grid((L.ho * L.wo + 127) / 128, M);
+  if (L.co <= 16) {
+    set_smem(k_conv_fwd<16>, smem);
+    k_conv_fwd<16><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+  } else {
+    set_smem(k_conv_fwd<32>, smem);
+    k_conv_fwd<32><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// reductions and bookkeeping
+// ---------------------------------------------------------------------------
+__global__ void k_reduce_lb(int M, const float* part, int nslot, int used, const float* gp0,
+                            float* lb, int track, const int* row_node, PoolDev pool,
+                            const float* X, int d0) {
+  const int m = blockIdx.x;
+  __shared__ int imp;
+  __shared__ int node;
+  if (threadIdx.x == 0) {
+    float acc = 0.f;
+    const float* p = part + (size_t)m * nslot;
+    for (int i = 0; i < used; ++i) acc += p[i];
+    if (gp0) acc -= gp0[m];
+    lb[m] = acc;
+    imp = 0;
+    node = row_node ? row_node[m] : 0;
+    if (track && acc > pool.BEST[node]) {
+      pool.BEST[node] = acc;
+      imp = 1;
+    }
+  }
+  __syncthreads();
+  if (imp)
+    for (int k = threadIdx.x; k < d0; k += blockDim.x)
+      pool.BESTX[(size_t)node * d0 + k] = X[(size_t)m * d0 + k];
+}
+
+void launch_reduce_lb(int M, const float* part, int nslot, int used, const float* gp0, float* lb,
+                      bool track, const int* row_node, PoolDev pool, const float* X, int d0,
+                      cudaStream_t st) {
+  if (M <= 0) return;
+  k_reduce_lb<<<M, 128, 0, st>>>(M, part, nslot, used, gp0, lb, track ? 1 : 0, row_node, pool,
+                                  X, d0);
+}
+
+// Rows (+e_j, -e_j) for every unstable (l < 0 < u) unsplit neuron of a layer,
+// ascending j within a node.
+__global__ void k_collect_rows(const int* nodes, PoolDev pool, int off, int d, int* counter,
+                               int* row_node, int* row_j, float* row_sign) {
+  const int n = nodes[blockIdx.x];
+  const size_t base = (size_t)n * pool.SD + off;
+  int cnt = 0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    const float l = pool.L[base + j], u = pool.U[base + j];
+    cnt += (l < 0.f && u > 0.f && pool.S[base + j] == 0) ? 1 : 0;
+  }
+  const int tot = (int)block_sum((float)cnt);
+  __shared__ int start;
+  if (threadIdx.x == 0) start = atomicAdd(counter, 2 * tot);
+  __syncthreads();
+  __shared__ int wsum[32];
+  int run = 0;  // rows emitted before this chunk
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j0 = 0; j0 < d; j0 += blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    bool f = false;
+    if (j < d) {
+      const float l = pool.L[base + j], u = pool.U[base + j];
+      f = l < 0.f && u > 0.f && pool.S[base + j] == 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    const int before_lane = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    int before_warp = 0, chunk = 0;
+    for (int i = 0; i < nw; ++i) {
+      if (i < w) before_warp += wsum[i];
+      chunk += wsum[i];
+    }
+    if (f) {
+      const int r = start + 2 * (run + before_warp + before_lane);
+      row_node[r] = n; row_j[r] = j; row_sign[r] = 1.f;
+      row_node[r + 1] = n; row_j[r + 1] = j; row_sign[r + 1] = -1.f;
+    }
+    run += chunk;
+    __syncthreads();
+  }
+}
+
+void launch_collect_rows(int nb, const int* nodes, PoolDev pool, int off, int d, int* counter,
+                         int* row_node, int* row_j, float* row_sign, cudaStream_t st) {
+  if (nb <= 0) return;
+  k_collect_rows<<<nb, 256, 0, st>>>(nodes, pool, off, d, counter, row_node, row_j, row_sign);
+}
+
+__global__ void k_update_bounds(int npairs, const int* row_node, const int* row_j,
+                                const float* lb, PoolDev pool, int off) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= npairs) return;
+  const int n = row_node[2 * q], j = row_j[2 * q];
+  const size_t i = (size_t)n * pool.SD + off + j;
+  pool.L[i] = fmaxf(pool.L[i], lb[2 * q]);
+  pool.U[i] = fminf(pool.U[i], -lb[2 * q + 1]);
+}
+
+void launch_update_bounds(int npairs, const int* row_node, const int* row_j, const float* lb,
+                          PoolDev pool, int off, cudaStream_t st) {
+  if (npairs <= 0) return;
+  k_update_bounds<<<(npairs + 255) / 256, 256, 0, st>>>(npairs, row_node, row_j, lb, pool, off);
+}
+
+__device__ __forceinline__ int layer_of(const NetDev& net, int f) {
+  int i = 1;
+  while (i < net.R && f >= net.off[i + 1]) ++i;
+  return i;
+}
+
+// gamma^T P and gamma^T Phat per neuron (CSR by neuron), gamma^T p per row.
+__global__ void k_gamma_proj(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                             NetDev net, float* GP, float* GPh) {
+  const int m = blockIdx.y;
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= net.SD) return;
+  const int n = row_node[m];
+  const int i = layer_of(net, f);
+  const int j = f - net.off[i];
+  const MncDev& mc = props[pool.prop[n]].mnc[i];
+  float gp = 0.f, gph = 0.f;
+  if (mc.e > 0) {
+    const float* gam = pool.GAM + (size_t)n * pool.EC + mc.goff;
+    for (int q = mc.cptr[j]; q < mc.cptr[j + 1]; ++q) {
+      const float g = gam[mc.ce[q]];
+      gp = fmaf(g, mc.cP[q], gp);
+      gph = fmaf(g, mc.cPh[q], gph);
+    }
+  }
+  GP[(size_t)m * net.SD + f] = gp;
+  GPh[(size_t)m * net.SD + f] = gph;
+}
+
+__global__ void k_gamma_p(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                          NetDev net, float* gp0) {
+  const int m = blockIdx.x;
+  const int n = row_node[m];
+  const PropDev& P = props[pool.prop[n]];
+  float acc = 0.f;
+  for (int i = 1; i <= net.R; ++i) {
+    const MncDev& mc = P.mnc[i];
+    const float* gam = pool.GAM + (size_t)n * pool.EC + mc.goff;
+    for (int e = threadIdx.x; e < mc.e; e += blockDim.x) acc = fmaf(gam[e], mc.p[e], acc);
+  }
+  const float tot = block_sum(acc);
+  if (threadIdx.x == 0) gp0[m] = tot;
+}
+
+void launch_gamma_proj(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                       const NetDev& net, float* GP, float* GPh, float* gp0, cudaStream_t st) {
+  if (M <= 0) return;
+  dim3 grid((net.SD + 255) / 256, M);
+  k_gamma_proj<<<grid, 256, 0, st>>>(M, row_node, pool, props, net, GP, GPh);
+  k_gamma_p<<<M, 256, 0, st>>>(M, row_node, pool, props, net, gp0);
+}
+
+// d lb / d gamma_e = sum_k P_ek (d lb / d a')_idx + Phat_ek (d lb / d ahat)_idx - p_e
+__global__ void k_gamma_grad(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                             NetDev net, const float* Gz, const float* Hz, float* GG) {
+  const int m = blockIdx.y;
+  const int ef = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = row_node[m];
+  const PropDev& P = props[pool.prop[n]];
+  if (ef >= P.E) return;
+  int i = 0;
+  for (int t = 1; t <= net.R; ++t)
+    if (P.mnc[t].e > 0 && ef >= P.mnc[t].goff && ef < P.mnc[t].goff + P.mnc[t].e) i = t;
+  if (i == 0) return;
+  const MncDev& mc = P.mnc[i];
+  const int e = ef - mc.goff;
+  const float* gz = Gz + (size_t)m * net.SD + net.off[i];
+  const float* hz = Hz + (size_t)m * net.SD + net.off[i];
+  float g = -mc.p[e];
+  for (int k = 0; k < mc.k; ++k) {
+    const int j = mc.idx[(size_t)e * mc.k + k];
+    g = fmaf(mc.P[(size_t)e * mc.k + k], gz[j], g);
+    g = fmaf(mc.Ph[(size_t)e * mc.k + k], hz[j], g);
+  }
+  GG[(size_t)m * pool.EC + ef] = g;
+}
+
+void launch_gamma_grad(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                       const NetDev& net, const float* Gz, const float* Hz, float* GG,
+                       cudaStream_t st) {
+  if (M <= 0 || pool.EC <= 0) return;
+  dim3 grid((pool.EC + 255) / 256, M);
+  k_gamma_grad<<<grid, 256, 0, st>>>(M, row_node, pool, props, net, Gz, Hz, GG);
+}
+
+// Projected Adam ascent step (Sec. 3.1): alpha in [0, 1], beta, gamma >= 0.
+__device__ __forceinline__ void adam1(float& th, float& mo, float& ve, float g, float lr, float b1,
+                                      float b2, float eps, float bc1, float bc2) {
+  mo = b1 * mo + (1.f - b1) * g;
+  ve = b2 * ve + (1.f - b2) * g * g;
+  const float mh = mo / bc1;
+  const float vh = ve / bc2;
+  th = th + lr * mh / (sqrtf(vh) + eps);
+}
+
+__global__ void k_adam(int M, const int* row_node, PoolDev pool, const PropDev* props, int SD,
+                       const float* GA, const float* GB, const float* GG, float lr_a, float lr_b,
+                       float lr_g, float b1, float b2, float eps, float bc1, float bc2) {
+  const int m = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = row_node[m];
+  if (idx < SD) {
+    const size_t q = (size_t)n * SD + idx;
+    float th = pool.ALPHA[q], mo = pool.MA[q], ve = pool.VA[q];
+    adam1(th, mo, ve, GA[(size_t)m * SD + idx], lr_a, b1, b2, eps, bc1, bc2);
+    pool.ALPHA[q] = fminf(fmaxf(th, 0.f), 1.f);
+    pool.MA[q] = mo; pool.VA[q] = ve;
+  } else if (idx < 2 * SD) {
+    const int f = idx - SD;
+    const size_t q = (size_t)n * SD + f;
+    float th = pool.BETA[q], mo = pool.MB[q], ve = pool.VB[q];
+    adam1(th, mo, ve, GB[(size_t)m * SD + f], lr_b, b1, b2, eps, bc1, bc2);
+    pool.BETA[q] = fmaxf(th, 0.f);
+    pool.MB[q] = mo; pool.VB[q] = ve;
+  } else {
+    const int e = idx - 2 * SD;
+    if (e >= props[pool.prop[n]].E) return;
+    const size_t q = (size_t)n * pool.EC + e;
+    float th = pool.GAM[q], mo = pool.MG[q], ve = pool.VG[q];
+    adam1(th, mo, ve, GG[(size_t)m * pool.EC + e], lr_g, b1, b2, eps, bc1, bc2);
+    pool.GAM[q] = fmaxf(th, 0.f);
+    pool.MG[q] = mo; pool.VG[q] = ve;
+  }
+}
+
+void launch_adam(int M, const int* row_node, PoolDev pool, const PropDev* props, int SD,
+                 const float* GA, const float* GB, const float* GG, float lr_a, float lr_b,
+                 float lr_g, float b1, float b2, float eps, float bc1, float bc2,
+                 cudaStream_t st) {
+  if (M <= 0) return;
+  const int tot = 2 * SD + pool.EC;
+  dim3 grid((tot + 255) / 256, M);
+  k_adam<<<grid, 256, 0, st>>>(M, row_node, pool, props, SD, GA, GB, GG, lr_a, lr_b, lr_g, b1, b2,
+                               eps, bc1, bc2);
+}
+
+__global__ void k_zero_adam(const int* row_node, PoolDev pool) {
+  const int n = row_node[blockIdx.y];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < pool.SD) {
+    const size_t q = (size_t)n * pool.SD + idx;
+    pool.MA[q] = 0.f; pool.VA[q] = 0.f; pool.MB[q] = 0.f; pool.VB[q] = 0.f;
+  } else if (idx < pool.SD + pool.EC) {
+    const size_t q = (size_t)n * pool.EC + idx - pool.SD;
+    pool.MG[q] = 0.f; pool.VG[q] = 0.f;
+  }
+}
+
+void launch_zero_adam(int M, const int* row_node, PoolDev pool, cudaStream_t st) {
+  if (M <= 0) return;
+  dim3 grid((pool.SD + pool.EC + 255) / 256, M);
+  k_zero_adam<<<grid, 256, 0, st>>>(row_node, pool);
+}
+
+__global__ void k_set_best(int M, const int* row_node, PoolDev pool, float v) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < M) pool.BEST[row_node[m]] = v;
+}
+
+void launch_set_best(int M, const int* row_node, PoolDev pool, float v, cudaStream_t st) {
+  if (M <= 0) return;
+  k_set_best<<<(M + 255) / 256, 256, 0, st>>>(M, row_node, pool, v);
+}
+
+// ACS (Sec. 3.2) with the intercept fallback; ties within 1e-5 of the maximum
+// go to the lowest (layer, neuron).
+__global__ void k_acs(int M, const int* row_node, PoolDev pool, NetDev net, const float* GP,
+                      const float* GPh, const float* AP, int has_gamma, int* out_layer,
+                      int* out_neuron, float* out_score, int* out_fallback) {
+  const int m = blockIdx.x;
+  const int n = row_node[m];
+  const size_t nb = (size_t)n * pool.SD, mb = (size_t)m * net.SD;
+  __shared__ float smax[32];
+  __shared__ int sany[32];
+  __shared__ int smin[32];
+  float mx = -INFINITY;
+  int any = 0;
+  for (int f = threadIdx.x; f < net.SD; f += blockDim.x) {
+    const float l = pool.L[nb + f], u = pool.U[nb + f];
+    if (l < 0.f && u > 0.f && pool.S[nb + f] == 0) {
+      any = 1;
+      const float s = has_gamma ? fabsf(GP[mb + f]) + fabsf(GPh[mb + f]) : 0.f;
+      mx = fmaxf(mx, s);
+    }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  auto bmax = [&](float v) {
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) smax[w] = v;
+    __syncthreads();
+    float r = -INFINITY;
+    for (int i = 0; i < nw; ++i) r = fmaxf(r, smax[i]);
+    return r;
+  };
+  mx = bmax(mx);
+  for (int o = 16; o; o >>= 1) any |= __shfl_xor_sync(0xffffffffu, any, o);
+  if (lane == 0) sany[w] = any;
+  __syncthreads();
+  any = 0;
+  for (int i = 0; i < nw; ++i) any |= sany[i];
+  if (!any) {
+    if (threadIdx.x == 0) {
+      out_layer[m] = 0; out_neuron[m] = -1; out_score[m] = 0.f; out_fallback[m] = 0;
+    }
+    return;
+  }
+  const int fallback = !(mx > 0.f);
+  if (fallback) {
+    mx = -INFINITY;
+    for (int f = threadIdx.x; f < net.SD; f += blockDim.x) {
+      const float l = pool.L[nb + f], u = pool.U[nb + f];
+      if (l < 0.f && u > 0.f && pool.S[nb + f] == 0) {
+        const float s = fabsf(AP[mb + f]) * ((-l * u) / (u - l));
+        mx = fmaxf(mx, s);
+      }
+    }
+    mx = bmax(mx);
+  }
+  const float thr = mx - 1e-5f * fabsf(mx);
+  int best = 0x7fffffff;
+  for (int f = threadIdx.x; f < net.SD; f += blockDim.x) {
+    const float l = pool.L[nb + f], u = pool.U[nb + f];
+    if (l < 0.f && u > 0.f && pool.S[nb + f] == 0) {
+      const float s = fallback ? fabsf(AP[mb + f]) * ((-l * u) / (u - l))
+                               : fabsf(GP[mb + f]) + fabsf(GPh[mb + f]);
+      if (s >= thr && f < best) best = f;
+    }
+  }
+  for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+  __syncthreads();
+  if (lane == 0) smin[w] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int b = 0x7fffffff;
+    for (int i = 0; i < nw; ++i) b = min(b, smin[i]);
+    const int i = layer_of(net, b);
+    out_layer[m] = i;
+    out_neuron[m] = b - net.off[i];
+    out_score[m] = mx;
+    out_fallback[m] = fallback;
+  }
+}
+
+void launch_acs(int M, const int* row_node, PoolDev pool, const NetDev& net, const float* GP,
+                const float* GPh, const float* AP, int has_gamma, int* out_layer, int* out_neuron,
+                float* out_score, int* out_fallback, cudaStream_t st) {
+  if (M <= 0) return;
+  k_acs<<<M, 256, 0, st>>>(M, row_node, pool, net, GP, GPh, AP, has_gamma, out_layer, out_neuron,
+                            out_score, out_fallback);
+}
+
+// Children of a split (Sec. 3.2, enforcing splits): copies of the parent with
+// S = +1 (zhat <= 0, u <- min(u, 0)) for the first child and S = -1 (zhat >= 0,
+// l <- max(l, 0)) for the second; the split neuron's beta starts at 0.
+__global__ void k_children(const int* parents, const int* kids, const int* layer,
+                           const int* neuron, PoolDev pool, NetDev net) {
+  const int b = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int par = parents[b];
+  const int f_split = net.off[layer[b]] + neuron[b];
+  for (int c = 0; c < 2; ++c) {
+    const int kid = kids[2 * b + c];
+    if (idx < pool.SD) {
+      const size_t qs = (size_t)par * pool.SD + idx, qd = (size_t)kid * pool.SD + idx;
+      float l = pool.L[qs], u = pool.U[qs];
+      int8_t s = pool.S[qs];
+      float be = pool.BETA[qs];
+      if (idx == f_split) {
+        be = 0.f;
+        if (c == 0) { s = 1; u = fminf(u, 0.f); }
+        else { s = -1; l = fmaxf(l, 0.f); }
+      }
+      pool.L[qd] = l; pool.U[qd] = u; pool.S[qd] = s;
+      pool.ALPHA[qd] = pool.ALPHA[qs];
+      pool.BETA[qd] = be;
+    } else if (idx < pool.SD + pool.EC) {
+      const int e = idx - pool.SD;
+      pool.GAM[(size_t)kid * pool.EC + e] = pool.GAM[(size_t)par * pool.EC + e];
+    }
+    if (idx == 0) {
+      pool.prop[kid] = pool.prop[par];
+      pool.row[kid] = pool.row[par];
+    }
+  }
+}
+
+void launch_children(int nb, const int* parents, const int* kids, const int* layer,
+                     const int* neuron, PoolDev pool, const NetDev& net, cudaStream_t st) {
+  if (nb <= 0) return;
+  dim3 grid((pool.SD + pool.EC + 255) / 256, nb);
+  k_children<<<grid, 256, 0, st>>>(parents, kids, layer, neuron, pool, net);
+}
+
+// Root nodes from a property's root-bound slot: DeepPoly slopes
+// (alpha = 1 if u >= -l else 0), beta = gamma = 0, no splits.
+__global__ void k_root_init(const int* slots, int src, PoolDev pool) {
+  const int dst = slots[blockIdx.y];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < pool.SD) {
+    const size_t qs = (size_t)src * pool.SD + idx, qd = (size_t)dst * pool.SD + idx;
+    const float l = pool.L[qs], u = pool.U[qs];
+    pool.L[qd] = l; pool.U[qd] = u; pool.S[qd] = 0;
+    pool.ALPHA[qd] = (u >= -l) ? 1.f : 0.f;
+    pool.BETA[qd] = 0.f;
+  } else if (idx < pool.SD + pool.EC) {
+    pool.GAM[(size_t)dst * pool.EC + idx - pool.SD] = 0.f;
+  }
+  if (idx == 0) pool.prop[dst] = pool.prop[src];
+}
+
+void launch_root_init(int nb, const int* slots, int src_slot, PoolDev pool, cudaStream_t st) {
+  if (nb <= 0) return;
+  dim3 grid((pool.SD + pool.EC + 255) / 256, nb);
+  k_root_init<<<grid, 256, 0, st>>>(slots, src_slot, pool);
+}
+
+// f_r(z_R) through the property's folded last layer, one warp per row.
+__global__ void k_final_dot(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                            const float* z, int ld, int dR, float* f) {
+  const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (m >= M) return;
+  const int n = row_node[m];
+  const PropDev& P = props[pool.prop[n]];
+  const int r = pool.row[n];
+  const float* w = P.Wf + (size_t)r * dR;
+  const float* x = z + (size_t)m * ld;
+  float acc = 0.f;
+  for (int k = lane; k < dR; k += 32) acc = fmaf(w[k], x[k], acc);
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) f[m] = acc + P.bf[r];
+}
+
+void launch_final_dot(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                      const float* z, int ld, int dR, float* f, cudaStream_t st) {
+  if (M <= 0) return;
+  k_final_dot<<<(M + 7) / 8, 256, 0, st>>>(M, row_node, pool, props, z, ld, dR, f);
+}
+
+__global__ void k_fill(float* p, size_t n, float v) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+void launch_fill(float* p, size_t n, float v, cudaStream_t st) {
+  if (n == 0) return;
+  k_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, n, v);
+}
+
+}  // namespace mnbab

@@ -1,0 +1,144 @@
+// Internal device data layout and kernel launchers of libmnbab.
+//
+// Per-node state lives in a structure-of-arrays pool in HBM: every array has
+// one row of SD = sum_i d_i floats per node slot (ReLU layers concatenated,
+// layer i at offset off[i]), so an epilogue that walks a back-substitution
+// row j of layer i reads l, u, S, alpha, beta of its node contiguously.
+// Scratch arrays of a launch are indexed by the launch's row m instead.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MNBAB_MAXR 16
+
+namespace mnbab {
+
+struct LayerDev {
+  int kind;  // 1 fc, 2 conv
+  int d_in, d_out;
+  int ci, hi, wi, co, ho, wo, k, s, p;
+  const float* W;   // fc [d_out][d_in]; conv [co][ci][k][k]
+  const float* Wt;  // fc only: [d_in][d_out]
+  const float* b;   // [d_out] (fc) or [co] (conv)
+};
+
+struct NetDev {
+  int R;                         // ReLU layers
+  int d[MNBAB_MAXR + 2];         // d[0] input, d[i] ReLU layer i
+  int off[MNBAB_MAXR + 2];       // offset of ReLU layer i in a node row
+  int SD;                        // sum of d[1..R]
+  int n_out;                     // logits
+  LayerDev aff[MNBAB_MAXR + 2];  // 1..R+1
+};
+
+// Multi-neuron constraints of one property and ReLU layer.  Row form
+// (idx, P, Ph, p) for gradients, CSR by neuron for gamma^T P and gamma^T Phat.
+struct MncDev {
+  int e;          // rows
+  int k;          // neurons per row
+  int goff;       // offset of this layer's gamma entries in a node's gamma row
+  const int* idx; const float* P; const float* Ph; const float* p;
+  const int* cptr; const int* ce; const float* cP; const float* cPh;
+};
+
+struct PropDev {
+  const float* lo;
+  const float* hi;
+  const float* Wf;   // folded last layer [n_rows][d_R]
+  const float* bf;   // [n_rows]
+  int n_rows;
+  int E;             // gamma entries per node
+  MncDev mnc[MNBAB_MAXR + 1];  // 1..R
+};
+
+struct PoolDev {
+  int SD, EC, d0;
+  float *L, *U, *ALPHA, *BETA;
+  int8_t* S;
+  float *MA, *VA, *MB, *VB;
+  float *GAM, *MG, *VG;
+  float* BESTX;  // [cap][d0]
+  float* BEST;   // [cap]
+  int* prop;     // property index of each slot
+  int* row;      // objective row of each slot
+};
+
+// Rows of one back-substitution launch.
+struct RowsDev {
+  int M;
+  const int* node;    // pool slot per row
+  const int* j;       // start neuron (intermediate rows) or property row (objective rows)
+  const float* sign;  // +1 / -1 (intermediate rows); null for objective rows
+};
+
+enum EpiKind { EPI_RELU = 0, EPI_CONC = 1, EPI_ADJ = 2, EPI_FWD_RELU = 3, EPI_STORE = 4 };
+
+// Everything an epilogue may need; unused pointers are null.
+struct Epi {
+  int kind;
+  int layer;         // ReLU layer index (EPI_RELU / EPI_ADJ)
+  int off, SD, d0;
+  const int* row_node;
+  PoolDev pool;
+  const PropDev* props;
+  bool final_mode;   // objective rows: use alpha/beta of the node, store a'
+  const float* GP;   // [M][SD] gamma^T P
+  const float* GPh;  // [M][SD] gamma^T Phat
+  float* AP;         // [M][SD] a' checkpoints (written in EPI_RELU, read in EPI_ADJ)
+  const float* bias; // bias of the consuming affine layer (EPI_RELU)
+  int bias_div;      // neuron j uses bias[j / bias_div]
+  float* X;          // [M][d0] minimiser (EPI_CONC)
+  float* GA;         // [M][SD] d lb / d alpha (EPI_ADJ)
+  float* GB;         // [M][SD] d lb / d beta
+  float* Gz;         // [M][SD] d lb / d a' (for gamma gradients)
+  float* Hz;         // [M][SD] d lb / d ahat
+  float* part;       // [M][nslot] row partial sums of the offset c
+  int nslot;
+  int slot_base;
+};
+
+// ---- launchers (kernels.cu) --------------------------------------------
+// Starting rows: a = sign * W_t[j, :] (t <= R) or Wf[row, :] (t = R + 1) on
+// z^(t-1), with c = sign * b_t[j] into slot 0, through epilogue `e`.
+void launch_init_rows(const NetDev& net, int t, const RowsDev& rows, float* out, int ld,
+                      const Epi& e, cudaStream_t st);
+// Back-substitution through affine layer i: in [M][d_i] -> out [M][d_{i-1}].
+// Returns the number of partial-sum slots used.
+int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
+                   const Epi& e, cudaStream_t st);
+int backsub_slots(const LayerDev& L);
+// Forward through affine layer i (+ bias): in [M][d_{i-1}] -> out [M][d_i].
+void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
+                    const Epi& e, cudaStream_t st);
+// lb[m] = sum of partial slots - gp0[m]; with track, keep the best bound and
+// its minimiser per node.
+void launch_reduce_lb(int M, const float* part, int nslot, int used, const float* gp0,
+                      float* lb, bool track, const int* row_node, PoolDev pool, const float* X,
+                      int d0, cudaStream_t st);
+// Unstable unsplit neurons of layer t for each node -> rows (+, -).
+void launch_collect_rows(int nb, const int* nodes, PoolDev pool, int off, int d, int* counter,
+                         int* row_node, int* row_j, float* row_sign, cudaStream_t st);
+void launch_update_bounds(int npairs, const int* row_node, const int* row_j, const float* lb,
+                          PoolDev pool, int off, cudaStream_t st);
+void launch_gamma_proj(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                       const NetDev& net, float* GP, float* GPh, float* gp0, cudaStream_t st);
+void launch_gamma_grad(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                       const NetDev& net, const float* Gz, const float* Hz, float* GG,
+                       cudaStream_t st);
+void launch_adam(int M, const int* row_node, PoolDev pool, const PropDev* props, int SD,
+                 const float* GA, const float* GB, const float* GG, float lr_a, float lr_b,
+                 float lr_g, float b1, float b2, float eps, float bc1, float bc2,
+                 cudaStream_t st);
+void launch_zero_adam(int M, const int* row_node, PoolDev pool, cudaStream_t st);
+void launch_set_best(int M, const int* row_node, PoolDev pool, float v, cudaStream_t st);
+void launch_acs(int M, const int* row_node, PoolDev pool, const NetDev& net, const float* GP,
+                const float* GPh, const float* AP, int has_gamma, int* out_layer, int* out_neuron,
+                float* out_score, int* out_fallback, cudaStream_t st);
+void launch_children(int nb, const int* parents, const int* kids, const int* layer,
+                     const int* neuron, PoolDev pool, const NetDev& net, cudaStream_t st);
+void launch_root_init(int nb, const int* slots, int src_slot, PoolDev pool, cudaStream_t st);
+void launch_final_dot(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                      const float* z, int ld, int dR, float* f, cudaStream_t st);
+void launch_fill(float* p, size_t n, float v, cudaStream_t st);
+
+}  // namespace mnbab

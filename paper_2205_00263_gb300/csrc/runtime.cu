@@ -1,0 +1,1326 @@
+// Host runtime of libmnbab: the C ABI declared in include/mnbab.h.
+//
+// Owns device memory (within an HBM budget), the per-network node pools,
+// property tables and multi-neuron constraints, and drives the kernels of
+// kernels.cu: back-substitution sweeps (Sec. 3.1), re-bounding after a split
+// (Sec. 3.2, enforcing splits), the DeepPoly pass and projected-Adam
+// optimisation with the adjoint sweep (Sec. 3.1), ACS branching (Sec. 3.2) and
+// the FIFO branch-and-bound queue (Sec. 2.2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <limits>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "mnbab.h"
+#include "mnbab_internal.h"
+
+using namespace mnbab;
+
+namespace {
+
+struct Err {
+  mnbab_status code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(mnbab_status c, const std::string& m) { throw Err{c, m}; }
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(MNBAB_E_DEVICE, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct QNode {
+  int slot;
+  int64_t seq;
+  int row;
+  int depth;
+  int split_layer;
+};
+
+struct HostLayer {
+  int kind;
+  int ci, hi, wi, co, ho, wo, k, s, p;
+  std::vector<double> W, b;
+};
+
+}  // namespace
+
+struct mnbab_ctx;
+
+struct mnbab_net {
+  int id = 0;
+  mnbab_ctx* ctx = nullptr;
+  NetDev nd{};
+  std::vector<HostLayer> host;  // 1..R+1 (index 0 unused)
+  int R = 0, d0 = 0, SD = 0, n_out = 0, maxd = 0, maxd_relu = 0;
+  int nslot = 0;
+  // node pool
+  PoolDev pool{};
+  int cap = 0;
+  std::vector<int> free_slots;
+  std::vector<int> slot_split;  // host metadata per slot
+  std::vector<int> slot_row;
+  std::vector<int> slot_prop;
+  std::vector<char> slot_used;
+  // scratch
+  int B = 0;          // batch capacity (objective rows)
+  int chunk = 0;      // rows per back-substitution launch
+  float *LamA = nullptr, *LamB = nullptr, *part = nullptr, *lb = nullptr;
+  int *row_node = nullptr, *row_j = nullptr, *counter = nullptr;
+  float* row_sign = nullptr;
+  size_t rows_cap = 0;
+  float *AP = nullptr, *GA = nullptr, *GB = nullptr, *GP = nullptr, *GPh = nullptr;
+  float *Gz = nullptr, *Hz = nullptr, *X = nullptr, *Xb = nullptr, *GG = nullptr, *gp0 = nullptr;
+  float *fout = nullptr, *score = nullptr, *bestb = nullptr;
+  int *bslots = nullptr, *brows = nullptr, *acs_layer = nullptr, *acs_neuron = nullptr,
+      *acs_fb = nullptr, *kid_parent = nullptr, *kid_slots = nullptr, *kid_layer = nullptr,
+      *kid_neuron = nullptr;
+};
+
+struct mnbab_prop {
+  int index = 0;
+  mnbab_net* net = nullptr;
+  PropDev pd{};
+  int root_slot = -1;
+  int n_rows = 0;
+  std::vector<float> lo, hi;
+  std::vector<double> Wf, bf;  // folded last layer in FP64 (host check)
+  std::deque<QNode> queue;
+  int budget = 256;
+  int bounded = 0;
+  int64_t next_seq = 0;
+  int verdict = MNBAB_UNKNOWN;
+  bool done = false;
+  bool unknown_leaf = false;
+  std::vector<int> row_open, row_leaf, row_fals;
+  std::vector<float> row_lb;
+  std::vector<float> cex;
+  int cex_row = -1;
+  std::vector<mnbab_trace_rec> trace;
+  int mnc_set[MNBAB_MAXR + 1] = {0};
+};
+
+struct mnbab_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  uint64_t budget = 0, used = 0;
+  int node_cap = 65536, EC = 0, row_chunk = 32768;
+  std::string err;
+  std::vector<mnbab_net*> nets;
+  std::vector<mnbab_prop*> props;
+  PropDev* d_props = nullptr;
+  int props_cap = 0;
+  std::vector<std::pair<void*, size_t>> allocs;
+};
+
+namespace {
+
+void* dalloc(mnbab_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (c->used + bytes > c->budget)
+    fail(MNBAB_E_BUDGET, "HBM budget exceeded (" + std::to_string(c->used + bytes) + " > " +
+                             std::to_string(c->budget) + " bytes)");
+  void* p = nullptr;
+  ck(cudaMalloc(&p, bytes), "cudaMalloc");
+  c->used += bytes;
+  c->allocs.push_back({p, bytes});
+  return p;
+}
+
+template <typename T>
+T* dalloc_t(mnbab_ctx* c, size_t n) {
+  return static_cast<T*>(dalloc(c, n * sizeof(T)));
+}
+
+template <typename T>
+void h2d(mnbab_ctx* c, T* dst, const T* src, size_t n) {
+  if (n) ck(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, c->st), "H2D");
+}
+
+template <typename T>
+void d2h(mnbab_ctx* c, T* dst, const T* src, size_t n) {
+  if (n) ck(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToHost, c->st), "D2H");
+}
+
+void sync(mnbab_ctx* c) {
+  ck(cudaStreamSynchronize(c->st), "stream synchronize");
+  ck(cudaGetLastError(), "kernel launch");
+}
+
+// ---------------------------------------------------------------------------
+// node pool
+// ---------------------------------------------------------------------------
+int alloc_slot(mnbab_net* n) {
+  if (n->free_slots.empty()) fail(MNBAB_E_BUDGET, "node pool exhausted");
+  const int s = n->free_slots.back();
+  n->free_slots.pop_back();
+  n->slot_used[s] = 1;
+  return s;
+}
+
+void free_slot(mnbab_net* n, int s) {
+  if (s < 0 || s >= n->cap || !n->slot_used[s]) return;
+  n->slot_used[s] = 0;
+  n->free_slots.push_back(s);
+}
+
+void upload_props(mnbab_ctx* c) {
+  const int np = (int)c->props.size();
+  if (np > c->props_cap) {
+    const int nc = std::max(64, np * 2);
+    PropDev* nd = dalloc_t<PropDev>(c, nc);
+    c->d_props = nd;  // old table stays allocated until destroy (small)
+    c->props_cap = nc;
+  }
+  std::vector<PropDev> h(np);
+  for (int i = 0; i < np; ++i) h[i] = c->props[i]->pd;
+  h2d(c, c->d_props, h.data(), np);
+}
+
+Epi base_epi(mnbab_net* n, const int* row_node) {
+  Epi e{};
+  e.SD = n->SD;
+  e.d0 = n->d0;
+  e.row_node = row_node;
+  e.pool = n->pool;
+  e.props = n->ctx->d_props;
+  e.part = n->part;
+  e.nslot = n->nslot;
+  e.bias_div = 1;
+  return e;
+}
+
+void relu_epi(mnbab_net* n, Epi& e, int layer) {
+  e.kind = EPI_RELU;
+  e.layer = layer;
+  e.off = n->nd.off[layer];
+  const LayerDev& L = n->nd.aff[layer];
+  e.bias = L.b;
+  e.bias_div = L.kind == 2 ? L.ho * L.wo : 1;
+}
+
+struct SweepOpts {
+  bool final_mode = false;  // objective rows with the node's alpha, beta (gamma if has_gamma)
+  bool has_gamma = false;
+  bool store = false;       // keep a' checkpoints and x*
+  bool track = false;       // keep best bound / minimiser per node
+};
+
+// Back-substitutes rows that all start at zhat^(t) down to the input.
+void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
+  mnbab_ctx* c = n->ctx;
+  if (rows.M <= 0) return;
+  Epi e0 = base_epi(n, rows.node);
+  auto setup = [&](Epi& e, int layer) {
+    if (layer >= 1) {
+      relu_epi(n, e, layer);
+      e.final_mode = o.final_mode;
+      if (o.final_mode && o.has_gamma) {
+        e.GP = n->GP;
+        e.GPh = n->GPh;
+      }
+      if (o.store) e.AP = n->AP;
+    } else {
+      e.kind = EPI_CONC;
+      if (o.store || o.track) e.X = n->X;
+    }
+  };
+  int need = 1;
+  for (int i = t - 1; i >= 1; --i) need += backsub_slots(n->nd.aff[i]);
+  if (need > n->nslot) fail(MNBAB_E_DEVICE, "partial-sum slots overflow");
+  if (rows.M > n->chunk && rows.M > n->B) fail(MNBAB_E_DEVICE, "row block larger than scratch");
+  setup(e0, t - 1);
+  e0.slot_base = 0;
+  float* cur = n->LamA;
+  float* nxt = n->LamB;
+  launch_init_rows(n->nd, t, rows, t - 1 >= 1 ? cur : nullptr, n->maxd, e0, c->st);
+  int used = 1;
+  for (int i = t - 1; i >= 1; --i) {
+    Epi e = base_epi(n, rows.node);
+    setup(e, i - 1);
+    e.slot_base = used;
+    used += launch_backsub(n->nd.aff[i], rows.M, cur, n->maxd, i - 1 >= 1 ? nxt : nullptr,
+                           n->maxd, e, c->st);
+    std::swap(cur, nxt);
+  }
+  launch_reduce_lb(rows.M, n->part, n->nslot, used,
+                   (o.final_mode && o.has_gamma) ? n->gp0 : nullptr, n->lb, o.track, rows.node,
+                   n->pool, n->X, n->d0, c->st);
+}
+
+// Re-bounds ReLU layers t > split layer of each node (Sec. 3.2, enforcing
+// splits); rows are the node's unstable unsplit neurons, both sides.
+int64_t rebound(mnbab_net* n, const std::vector<int>& slots) {
+  mnbab_ctx* c = n->ctx;
+  int64_t total = 0;
+  std::vector<int> sel;
+  for (int t = 1; t <= n->R; ++t) {
+    sel.clear();
+    for (int s : slots)
+      if (n->slot_split[s] < t) sel.push_back(s);
+    if (sel.empty()) continue;
+    int done = 0;
+    while (done < (int)sel.size()) {
+      // nodes per collection pass bounded by the rows capacity
+      const int per = std::max(1, (int)(n->rows_cap / (2 * (size_t)n->nd.d[t])));
+      const int nb = std::min((int)sel.size() - done, std::min(per, n->B));
+      h2d(c, n->bslots, sel.data() + done, nb);
+      ck(cudaMemsetAsync(n->counter, 0, sizeof(int), c->st), "memset");
+      launch_collect_rows(nb, n->bslots, n->pool, n->nd.off[t], n->nd.d[t], n->counter,
+                          n->row_node, n->row_j, n->row_sign, c->st);
+      int M = 0;
+      d2h(c, &M, n->counter, 1);
+      sync(c);
+      total += M;
+      for (int s0 = 0; s0 < M; s0 += n->chunk) {
+        const int Mc = std::min(n->chunk, M - s0);
+        RowsDev r{Mc, n->row_node + s0, n->row_j + s0, n->row_sign + s0};
+        SweepOpts o;
+        sweep(n, t, r, o);
+        launch_update_bounds(Mc / 2, r.node, r.j, n->lb, n->pool, n->nd.off[t], c->st);
+      }
+      done += nb;
+    }
+  }
+  for (int s : slots) n->slot_split[s] = n->R;
+  return total;
+}
+
+bool batch_has_gamma(mnbab_net* n, const std::vector<int>& slots) {
+  for (int s : slots)
+    if (n->ctx->props[n->slot_prop[s]]->pd.E > 0) return true;
+  return false;
+}
+
+void upload_batch(mnbab_net* n, const std::vector<int>& slots) {
+  std::vector<int> rows(slots.size());
+  for (size_t i = 0; i < slots.size(); ++i) rows[i] = n->slot_row[slots[i]];
+  h2d(n->ctx, n->bslots, slots.data(), slots.size());
+  h2d(n->ctx, n->brows, rows.data(), rows.size());
+}
+
+RowsDev obj_rows(mnbab_net* n, int M) { return RowsDev{M, n->bslots, n->brows, nullptr}; }
+
+// adjoint sweep from x* up through the ReLU layers (d lb / d ahat_i is the
+// forward pass of the relaxed network at x*)
+void adjoint(mnbab_net* n, int M, bool has_gamma) {
+  mnbab_ctx* c = n->ctx;
+  const float* in = n->X;
+  int ld_in = n->d0;
+  float* bufs[2] = {n->LamA, n->LamB};
+  for (int i = 1; i <= n->R; ++i) {
+    Epi e = base_epi(n, n->bslots);
+    e.kind = EPI_ADJ;
+    e.layer = i;
+    e.off = n->nd.off[i];
+    e.AP = n->AP;
+    e.GA = n->GA;
+    e.GB = n->GB;
+    if (has_gamma) {
+      e.Gz = n->Gz;
+      e.Hz = n->Hz;
+    }
+    e.part = nullptr;
+    float* out = bufs[i & 1];
+    launch_forward(n->nd.aff[i], M, in, ld_in, out, n->maxd, e, c->st);
+    in = out;
+    ld_in = n->maxd;
+  }
+  if (has_gamma)
+    launch_gamma_grad(M, n->bslots, n->pool, c->d_props, n->nd, n->Gz, n->Hz, n->GG, c->st);
+}
+
+void run_optimize(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
+  mnbab_ctx* c = n->ctx;
+  launch_zero_adam(M, n->bslots, n->pool, c->st);
+  SweepOpts o;
+  o.final_mode = true;
+  o.has_gamma = has_gamma;
+  o.store = true;
+  o.track = true;
+  double b1t = 1.0, b2t = 1.0;
+  for (int step = 0; step <= a.steps; ++step) {
+    if (has_gamma)
+      launch_gamma_proj(M, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+    sweep(n, n->R + 1, obj_rows(n, M), o);
+    if (step == a.steps) break;
+    adjoint(n, M, has_gamma);
+    b1t *= a.beta1;
+    b2t *= a.beta2;
+    launch_adam(M, n->bslots, n->pool, c->d_props, n->SD, n->GA, n->GB, n->GG, a.lr_alpha,
+                a.lr_beta, a.lr_gamma, a.beta1, a.beta2, a.eps, (float)(1.0 - b1t),
+                (float)(1.0 - b2t), c->st);
+  }
+}
+
+// FP32 forward pass of rows of `x` ([M][d0]) -> f_r in n->fout
+void forward_rows(mnbab_net* n, int M, const float* x) {
+  mnbab_ctx* c = n->ctx;
+  const float* in = x;
+  int ld = n->d0;
+  float* bufs[2] = {n->LamA, n->LamB};
+  for (int i = 1; i <= n->R; ++i) {
+    Epi e = base_epi(n, n->bslots);
+    e.kind = EPI_FWD_RELU;
+    e.part = nullptr;
+    float* out = bufs[i & 1];
+    launch_forward(n->nd.aff[i], M, in, ld, out, n->maxd, e, c->st);
+    in = out;
+    ld = n->maxd;
+  }
+  launch_final_dot(M, n->bslots, n->pool, c->d_props, in, ld, n->nd.d[n->R], n->fout, c->st);
+}
+
+__global__ void k_gather_rows(int M, const int* idx, const float* src, int ld_src, float* dst,
+                              int ld_dst, int w) {
+  const int m = blockIdx.x;
+  const float* s = src + (size_t)idx[m] * ld_src;
+  for (int k = threadIdx.x; k < w; k += blockDim.x) dst[(size_t)m * ld_dst + k] = s[k];
+}
+
+__global__ void k_gather1(int M, const int* idx, const float* src, float* dst) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < M) dst[m] = src[idx[m]];
+}
+
+// FP64 forward pass on the host (counterexample confirmation)
+double host_forward(mnbab_net* n, mnbab_prop* p, int row, const float* x) {
+  std::vector<double> h(x, x + n->d0), g;
+  for (int i = 1; i <= n->R; ++i) {
+    const HostLayer& L = n->host[i];
+    if (L.kind == MNBAB_FC) {
+      const int din = L.ci, dout = L.co;
+      g.assign(dout, 0.0);
+      for (int o = 0; o < dout; ++o) {
+        double acc = L.b[o];
+        for (int k = 0; k < din; ++k) acc += L.W[(size_t)o * din + k] * h[k];
+        g[o] = acc;
+      }
+    } else {
+      g.assign((size_t)L.co * L.ho * L.wo, 0.0);
+      for (int co = 0; co < L.co; ++co)
+        for (int oh = 0; oh < L.ho; ++oh)
+          for (int ow = 0; ow < L.wo; ++ow) {
+            double acc = L.b[co];
+            for (int ci = 0; ci < L.ci; ++ci)
+              for (int kh = 0; kh < L.k; ++kh) {
+                const int ih = oh * L.s - L.p + kh;
+                if (ih < 0 || ih >= L.hi) continue;
+                for (int kw = 0; kw < L.k; ++kw) {
+                  const int iw = ow * L.s - L.p + kw;
+                  if (iw < 0 || iw >= L.wi) continue;
+                  acc += L.W[(((size_t)co * L.ci + ci) * L.k + kh) * L.k + kw] *
+                         h[((size_t)ci * L.hi + ih) * L.wi + iw];
+                }
+              }
+            g[((size_t)co * L.ho + oh) * L.wo + ow] = acc;
+          }
+    }
+    for (auto& v : g) v = v > 0.0 ? v : 0.0;
+    h.swap(g);
+  }
+  const int dR = (int)h.size();
+  double f = p->bf[row];
+  for (int k = 0; k < dR; ++k) f += p->Wf[(size_t)row * dR + k] * h[k];
+  return f;
+}
+
+mnbab_adam default_adam() {
+  mnbab_adam a;
+  a.steps = 20;
+  a.lr_alpha = 0.1f;
+  a.lr_beta = 0.05f;
+  a.lr_gamma = 0.05f;
+  a.beta1 = 0.9f;
+  a.beta2 = 0.999f;
+  a.eps = 1e-8f;
+  return a;
+}
+
+mnbab_net* net_of(mnbab_ctx* c, mnbab_node_id id, int* slot) {
+  const int ni = (int)(id >> 32);
+  const int s = (int)(id & 0xffffffff);
+  if (ni < 0 || ni >= (int)c->nets.size()) fail(MNBAB_E_INVALID_ARG, "bad node id");
+  mnbab_net* n = c->nets[ni];
+  if (s < 0 || s >= n->cap || !n->slot_used[s]) fail(MNBAB_E_INVALID_ARG, "node id not live");
+  *slot = s;
+  return n;
+}
+
+mnbab_net* slots_of(mnbab_ctx* c, const mnbab_node_id* nodes, int nn, std::vector<int>& slots) {
+  if (nn <= 0 || !nodes) fail(MNBAB_E_INVALID_ARG, "empty node list");
+  mnbab_net* net = nullptr;
+  slots.resize(nn);
+  for (int i = 0; i < nn; ++i) {
+    int s;
+    mnbab_net* n = net_of(c, nodes[i], &s);
+    if (net && n != net) fail(MNBAB_E_INVALID_ARG, "nodes of different networks in one batch");
+    net = n;
+    slots[i] = s;
+  }
+  if (nn > net->B) fail(MNBAB_E_INVALID_ARG, "batch larger than the context's batch capacity");
+  return net;
+}
+
+void gather_best(mnbab_net* n, int M, float* host_out) {
+  k_gather1<<<(M + 255) / 256, 256, 0, n->ctx->st>>>(M, n->bslots, n->pool.BEST, n->bestb);
+  d2h(n->ctx, host_out, n->bestb, M);
+}
+
+void setup_net(mnbab_ctx* c, mnbab_net* n) {
+  // dims
+  n->maxd = n->d0;
+  n->maxd_relu = 1;
+  for (int i = 1; i <= n->R; ++i) {
+    n->maxd = std::max(n->maxd, n->nd.d[i]);
+    n->maxd_relu = std::max(n->maxd_relu, n->nd.d[i]);
+  }
+  n->nslot = 1;
+  for (int i = 1; i <= n->R; ++i) n->nslot += backsub_slots(n->nd.aff[i]);
+  n->nslot = std::max(n->nslot, 8);
+  // pool
+  n->cap = c->node_cap;
+  const size_t SD = n->SD, EC = c->EC, cap = n->cap;
+  PoolDev& P = n->pool;
+  P.SD = n->SD;
+  P.EC = c->EC;
+  P.d0 = n->d0;
+  P.L = dalloc_t<float>(c, cap * SD);
+  P.U = dalloc_t<float>(c, cap * SD);
+  P.ALPHA = dalloc_t<float>(c, cap * SD);
+  P.BETA = dalloc_t<float>(c, cap * SD);
+  P.S = dalloc_t<int8_t>(c, cap * SD);
+  P.MA = dalloc_t<float>(c, cap * SD);
+  P.VA = dalloc_t<float>(c, cap * SD);
+  P.MB = dalloc_t<float>(c, cap * SD);
+  P.VB = dalloc_t<float>(c, cap * SD);
+  P.GAM = dalloc_t<float>(c, cap * EC);
+  P.MG = dalloc_t<float>(c, cap * EC);
+  P.VG = dalloc_t<float>(c, cap * EC);
+  P.BESTX = dalloc_t<float>(c, cap * n->d0);
+  P.BEST = dalloc_t<float>(c, cap);
+  P.prop = dalloc_t<int>(c, cap);
+  P.row = dalloc_t<int>(c, cap);
+  n->free_slots.resize(cap);
+  for (int i = 0; i < (int)cap; ++i) n->free_slots[i] = (int)cap - 1 - i;
+  n->slot_split.assign(cap, 0);
+  n->slot_row.assign(cap, 0);
+  n->slot_prop.assign(cap, 0);
+  n->slot_used.assign(cap, 0);
+  // scratch
+  n->B = std::min(1024, std::max(1, (int)cap / 2));
+  n->chunk = std::max(2, c->row_chunk & ~1);
+  const size_t chunk = n->chunk, B = n->B;
+  const size_t mrows = std::max(chunk, B);
+  n->LamA = dalloc_t<float>(c, mrows * n->maxd);
+  n->LamB = dalloc_t<float>(c, mrows * n->maxd);
+  n->part = dalloc_t<float>(c, mrows * n->nslot);
+  n->lb = dalloc_t<float>(c, mrows);
+  n->rows_cap = std::max(chunk, (size_t)2 * n->maxd_relu);
+  n->row_node = dalloc_t<int>(c, n->rows_cap);
+  n->row_j = dalloc_t<int>(c, n->rows_cap);
+  n->row_sign = dalloc_t<float>(c, n->rows_cap);
+  n->counter = dalloc_t<int>(c, 4);
+  n->AP = dalloc_t<float>(c, B * SD);
+  n->GA = dalloc_t<float>(c, B * SD);
+  n->GB = dalloc_t<float>(c, B * SD);
+  n->GP = dalloc_t<float>(c, B * SD);
+  n->GPh = dalloc_t<float>(c, B * SD);
+  n->Gz = dalloc_t<float>(c, B * SD);
+  n->Hz = dalloc_t<float>(c, B * SD);
+  n->X = dalloc_t<float>(c, mrows * n->d0);
+  n->Xb = dalloc_t<float>(c, B * n->d0);
+  n->GG = dalloc_t<float>(c, B * std::max<size_t>(EC, 1));
+  n->gp0 = dalloc_t<float>(c, B);
+  n->fout = dalloc_t<float>(c, B);
+  n->score = dalloc_t<float>(c, B);
+  n->bestb = dalloc_t<float>(c, B);
+  n->bslots = dalloc_t<int>(c, B);
+  n->brows = dalloc_t<int>(c, B);
+  n->acs_layer = dalloc_t<int>(c, B);
+  n->acs_neuron = dalloc_t<int>(c, B);
+  n->acs_fb = dalloc_t<int>(c, B);
+  n->kid_parent = dalloc_t<int>(c, B);
+  n->kid_slots = dalloc_t<int>(c, 2 * B);
+  n->kid_layer = dalloc_t<int>(c, B);
+  n->kid_neuron = dalloc_t<int>(c, B);
+  ck(cudaMemsetAsync(P.GAM, 0, cap * EC * sizeof(float) + 16, c->st), "memset");
+}
+
+// ---------------------------------------------------------------------------
+// BaB step (Sec. 2.2; Sec. 3.2)
+// ---------------------------------------------------------------------------
+struct Picked {
+  mnbab_prop* p;
+  QNode q;
+};
+
+void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_nodes,
+                   const mnbab_adam& adam, mnbab_step_stats* st) {
+  std::memset(st, 0, sizeof(*st));
+  if (n_props <= 0) return;
+  mnbab_net* n = props[0]->net;
+  for (int i = 0; i < n_props; ++i)
+    if (props[i]->net != n) fail(MNBAB_E_INVALID_ARG, "properties of different networks");
+  max_nodes = std::max(1, std::min(max_nodes, n->B));
+  // pop FIFO
+  std::vector<Picked> picked;
+  for (int i = 0; i < n_props && (int)picked.size() < max_nodes; ++i) {
+    mnbab_prop* p = props[i];
+    while (!p->done && !p->queue.empty() && p->bounded < p->budget &&
+           (int)picked.size() < max_nodes) {
+      picked.push_back({p, p->queue.front()});
+      p->queue.pop_front();
+      p->bounded++;
+      p->row_open[picked.back().q.row]--;
+    }
+  }
+  const int M = (int)picked.size();
+  st->nodes_bounded = M;
+  if (M > 0) {
+    std::vector<int> slots(M);
+    for (int i = 0; i < M; ++i) slots[i] = picked[i].q.slot;
+    // 1. re-bound layers after the split layer
+    st->rows_rebounded = rebound(n, slots);
+    // 2. DeepPoly pass of the objective
+    upload_batch(n, slots);
+    launch_set_best(M, n->bslots, n->pool, -INFINITY, c->st);
+    SweepOpts dp;
+    dp.track = true;
+    sweep(n, n->R + 1, obj_rows(n, M), dp);
+    std::vector<float> lb_dp(M);
+    d2h(c, lb_dp.data(), n->lb, M);
+    sync(c);
+    // 3. projected Adam on the nodes DeepPoly does not verify
+    std::vector<int> opt_idx;
+    for (int i = 0; i < M; ++i)
+      if (!(lb_dp[i] > 0.f)) opt_idx.push_back(i);
+    std::vector<int> oslots(opt_idx.size());
+    for (size_t i = 0; i < opt_idx.size(); ++i) oslots[i] = slots[opt_idx[i]];
+    const int Mo = (int)oslots.size();
+    std::vector<int> acs_l(Mo), acs_n(Mo), acs_fb(Mo);
+    std::vector<float> best(M);
+    std::vector<float> f32(Mo);
+    if (Mo > 0) {
+      upload_batch(n, oslots);
+      const bool g = batch_has_gamma(n, oslots);
+      run_optimize(n, Mo, g, adam);
+      // 5. ACS at the final parameters (a' and gamma^T P of the last sweep)
+      launch_acs(Mo, n->bslots, n->pool, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0, n->acs_layer,
+                 n->acs_neuron, n->score, n->acs_fb, c->st);
+      // 4. counterexample check at the best minimiser
+      k_gather_rows<<<Mo, 128, 0, c->st>>>(Mo, n->bslots, n->pool.BESTX, n->d0, n->Xb, n->d0,
+                                           n->d0);
+      forward_rows(n, Mo, n->Xb);
+      d2h(c, f32.data(), n->fout, Mo);
+      d2h(c, acs_l.data(), n->acs_layer, Mo);
+      d2h(c, acs_n.data(), n->acs_neuron, Mo);
+      d2h(c, acs_fb.data(), n->acs_fb, Mo);
+    }
+    // best bound of every node (DeepPoly value for the verified ones)
+    upload_batch(n, slots);
+    gather_best(n, M, best.data());
+    sync(c);
+    // host: verdicts, counterexample confirmation, children
+    std::vector<int> par, lay, neu;
+    std::vector<int> kidslots;
+    std::vector<std::pair<int, int>> branch_of;  // (picked index, opt index)
+    int oi = 0;
+    std::vector<float> xs(n->d0);
+    for (int i = 0; i < M; ++i) {
+      mnbab_prop* p = picked[i].p;
+      const QNode& q = picked[i].q;
+      mnbab_trace_rec rec{};
+      rec.seq = q.seq;
+      rec.row = q.row;
+      rec.depth = q.depth;
+      rec.lb_deeppoly = lb_dp[i];
+      rec.lb = best[i];
+      rec.f_xstar = NAN;
+      rec.verdict = MNBAB_UNKNOWN;
+      const bool optimised = oi < Mo && opt_idx[oi] == i;
+      const int o = optimised ? oi++ : -1;
+      bool release = true;
+      if (best[i] > 0.f) {
+        rec.verdict = MNBAB_VERIFIED;
+        st->nodes_verified++;
+      } else {
+        bool fals = false;
+        if (optimised) {
+          rec.f_xstar = f32[o];
+          if (f32[o] < 0.f) {
+            d2h(c, xs.data(), n->pool.BESTX + (size_t)q.slot * n->d0, n->d0);
+            sync(c);
+            const double f64 = host_forward(n, p, q.row, xs.data());
+            rec.f_xstar = (float)f64;
+            if (f64 < 0.0) {
+              fals = true;
+              if (!p->done) {
+                p->cex = xs;
+                p->cex_row = q.row;
+              }
+            }
+          }
+        }
+        if (fals) {
+          rec.verdict = MNBAB_FALSIFIED;
+          st->nodes_falsified++;
+          p->row_fals[q.row] = 1;
+          if (!p->done) {
+            p->verdict = MNBAB_FALSIFIED;
+            p->done = true;
+          }
+        } else {
+          p->row_lb[q.row] = std::min(p->row_lb[q.row], best[i]);
+          if (optimised && acs_l[o] > 0 && !p->done) {
+            rec.split_layer = acs_l[o];
+            rec.split_neuron = acs_n[o];
+            rec.fallback = acs_fb[o];
+            par.push_back(q.slot);
+            lay.push_back(acs_l[o]);
+            neu.push_back(acs_n[o]);
+            branch_of.push_back({i, o});
+            release = false;
+            st->nodes_branched++;
+          } else if (!p->done) {
+            p->unknown_leaf = true;
+            p->row_leaf[q.row] = 1;
+            st->nodes_leaf++;
+          }
+        }
+      }
+      p->trace.push_back(rec);
+      if (release) free_slot(n, q.slot);
+    }
+    // children
+    const int nb = (int)par.size();
+    if (nb > 0) {
+      kidslots.resize(2 * nb);
+      for (int b = 0; b < nb; ++b) {
+        kidslots[2 * b] = alloc_slot(n);
+        kidslots[2 * b + 1] = alloc_slot(n);
+      }
+      h2d(c, n->kid_parent, par.data(), nb);
+      h2d(c, n->kid_slots, kidslots.data(), 2 * nb);
+      h2d(c, n->kid_layer, lay.data(), nb);
+      h2d(c, n->kid_neuron, neu.data(), nb);
+      launch_children(nb, n->kid_parent, n->kid_slots, n->kid_layer, n->kid_neuron, n->pool,
+                      n->nd, c->st);
+      for (int b = 0; b < nb; ++b) {
+        const Picked& pk = picked[branch_of[b].first];
+        for (int k = 0; k < 2; ++k) {
+          const int s = kidslots[2 * b + k];
+          n->slot_split[s] = lay[b];
+          n->slot_row[s] = pk.q.row;
+          n->slot_prop[s] = n->slot_prop[pk.q.slot];
+          pk.p->queue.push_back(QNode{s, pk.p->next_seq++, pk.q.row, pk.q.depth + 1, lay[b]});
+          pk.p->row_open[pk.q.row]++;
+        }
+      }
+      sync(c);
+      for (int b = 0; b < nb; ++b) free_slot(n, par[b]);
+    }
+  }
+  // property completion
+  for (int i = 0; i < n_props; ++i) {
+    mnbab_prop* p = props[i];
+    if (p->done) {
+      for (auto& q : p->queue) free_slot(n, q.slot);
+      p->queue.clear();
+    } else if (p->queue.empty()) {
+      p->verdict = p->unknown_leaf ? MNBAB_UNKNOWN : MNBAB_VERIFIED;
+      p->done = true;
+    } else if (p->bounded >= p->budget) {
+      p->verdict = MNBAB_UNKNOWN;
+      p->done = true;
+      for (auto& q : p->queue) free_slot(n, q.slot);
+      p->queue.clear();
+    }
+    if (p->done) st->props_done++;
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+#define API_BEGIN(c)                                      \
+  if (!(c)) return MNBAB_E_INVALID_ARG;                   \
+  try {                                                   \
+    ck(cudaSetDevice((c)->device), "cudaSetDevice");
+#define API_END(c)                                        \
+  return MNBAB_OK;                                        \
+  }                                                       \
+  catch (const Err& e) {                                  \
+    (c)->err = e.msg;                                     \
+    return e.code;                                        \
+  }                                                       \
+  catch (const std::exception& e) {                       \
+    (c)->err = e.what();                                  \
+    return MNBAB_E_DEVICE;                                \
+  }
+
+extern "C" {
+
+mnbab_status mnbab_create(const mnbab_options* opt, mnbab_ctx** out) {
+  if (!out) return MNBAB_E_INVALID_ARG;
+  *out = nullptr;
+  mnbab_ctx* c = new mnbab_ctx();
+  mnbab_options o{};
+  if (opt) o = *opt;
+  c->device = o.device;
+  c->budget = o.hbm_budget_bytes ? o.hbm_budget_bytes : (64ull << 30);
+  c->node_cap = o.node_capacity > 0 ? o.node_capacity : 65536;
+  c->EC = std::max(0, o.max_mnc_rows);
+  c->row_chunk = std::min(o.row_chunk > 0 ? o.row_chunk : 32768, 65534);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
+    delete c;
+    return MNBAB_E_DEVICE;
+  }
+  if (cudaSetDevice(c->device) != cudaSuccess) {
+    delete c;
+    return MNBAB_E_DEVICE;
+  }
+  if (o.stream) {
+    c->st = (cudaStream_t)o.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return MNBAB_E_DEVICE;
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return MNBAB_OK;
+}
+
+void mnbab_destroy(mnbab_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->st);
+  for (auto& a : c->allocs) cudaFree(a.first);
+  for (auto* n : c->nets) delete n;
+  for (auto* p : c->props) delete p;
+  if (c->own_stream) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+const char* mnbab_last_error(const mnbab_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+mnbab_status mnbab_load_network(mnbab_ctx* c, const mnbab_layer_desc* layers, int32_t n_layers,
+                                mnbab_net** out) {
+  API_BEGIN(c)
+  if (!layers || n_layers <= 0 || !out) fail(MNBAB_E_INVALID_ARG, "no layers");
+  mnbab_net* n = new mnbab_net();
+  n->ctx = c;
+  n->id = (int)c->nets.size();
+  n->host.resize(1);
+  bool expect_aff = true;
+  int prev = -1;
+  for (int i = 0; i < n_layers; ++i) {
+    const mnbab_layer_desc& d = layers[i];
+    if (d.kind == MNBAB_RELU) {
+      if (expect_aff) fail(MNBAB_E_INVALID_ARG, "ReLU must follow an affine layer");
+      expect_aff = true;
+      continue;
+    }
+    if (d.kind == MNBAB_ADD) fail(MNBAB_E_UNSUPPORTED, "residual ADD layers are not supported");
+    if (d.kind != MNBAB_FC && d.kind != MNBAB_CONV2D) fail(MNBAB_E_INVALID_ARG, "bad layer kind");
+    if (!expect_aff) fail(MNBAB_E_INVALID_ARG, "two affine layers without a ReLU between");
+    if (!d.W || !d.b) fail(MNBAB_E_INVALID_ARG, "missing weights");
+    HostLayer h{};
+    h.kind = d.kind;
+    if (d.kind == MNBAB_FC) {
+      h.ci = d.in_c; h.co = d.out_c; h.hi = h.wi = h.ho = h.wo = 1; h.k = 1; h.s = 1; h.p = 0;
+    } else {
+      h.ci = d.in_c; h.hi = d.in_h; h.wi = d.in_w; h.co = d.out_c; h.ho = d.out_h; h.wo = d.out_w;
+      h.k = d.k; h.s = d.stride; h.p = d.pad;
+      if (h.k <= 0 || h.s <= 0 || h.p < 0 || h.ho != (h.hi + 2 * h.p - h.k) / h.s + 1 ||
+          h.wo != (h.wi + 2 * h.p - h.k) / h.s + 1)
+        fail(MNBAB_E_INVALID_ARG, "inconsistent convolution shape");
+    }
+    const int din = h.ci * h.hi * h.wi, dout = h.co * h.ho * h.wo;
+    if (din <= 0 || dout <= 0) fail(MNBAB_E_INVALID_ARG, "empty layer");
+    if (prev >= 0 && din != prev) fail(MNBAB_E_INVALID_ARG, "layer sizes do not chain");
+    prev = dout;
+    const size_t nW = d.kind == MNBAB_FC ? (size_t)dout * din : (size_t)h.co * h.ci * h.k * h.k;
+    h.W.assign(d.W, d.W + nW);
+    h.b.assign(d.b, d.b + h.co);
+    n->host.push_back(std::move(h));
+    expect_aff = false;
+  }
+  if (expect_aff) fail(MNBAB_E_INVALID_ARG, "network must end with an affine layer");
+  n->R = (int)n->host.size() - 2;
+  if (n->R < 0 || n->R > MNBAB_MAXR) fail(MNBAB_E_UNSUPPORTED, "too many ReLU layers");
+  if (n->host.back().kind != MNBAB_FC) fail(MNBAB_E_UNSUPPORTED, "last layer must be FC");
+  NetDev& nd = n->nd;
+  nd.R = n->R;
+  n->d0 = n->host[1].ci * n->host[1].hi * n->host[1].wi;
+  nd.d[0] = n->d0;
+  int off = 0;
+  for (int i = 1; i <= n->R + 1; ++i) {
+    const HostLayer& h = n->host[i];
+    LayerDev& L = nd.aff[i];
+    L.kind = h.kind;
+    L.ci = h.ci; L.hi = h.hi; L.wi = h.wi; L.co = h.co; L.ho = h.ho; L.wo = h.wo;
+    L.k = h.k; L.s = h.s; L.p = h.p;
+    L.d_in = h.ci * h.hi * h.wi;
+    L.d_out = h.co * h.ho * h.wo;
+    std::vector<float> W(h.W.begin(), h.W.end()), b(h.b.begin(), h.b.end());
+    float* dW = dalloc_t<float>(c, W.size());
+    float* db = dalloc_t<float>(c, b.size());
+    h2d(c, dW, W.data(), W.size());
+    h2d(c, db, b.data(), b.size());
+    L.W = dW;
+    L.b = db;
+    if (h.kind == MNBAB_FC) {
+      std::vector<float> Wt((size_t)L.d_in * L.d_out);
+      for (int o = 0; o < L.d_out; ++o)
+        for (int k = 0; k < L.d_in; ++k) Wt[(size_t)k * L.d_out + o] = W[(size_t)o * L.d_in + k];
+      float* dWt = dalloc_t<float>(c, Wt.size());
+      h2d(c, dWt, Wt.data(), Wt.size());
+      L.Wt = dWt;
+    } else {
+      if ((size_t)L.co * L.ci * L.k * L.k * 4 > 227 * 1024)
+        fail(MNBAB_E_UNSUPPORTED, "convolution weights exceed shared memory");
+    }
+    if (i <= n->R) {
+      nd.d[i] = L.d_out;
+      nd.off[i] = off;
+      off += L.d_out;
+    }
+  }
+  nd.off[n->R + 1] = off;
+  nd.SD = off;
+  n->SD = off;
+  n->n_out = nd.aff[n->R + 1].d_out;
+  nd.n_out = n->n_out;
+  setup_net(c, n);
+  sync(c);
+  c->nets.push_back(n);
+  *out = n;
+  API_END(c)
+}
+
+mnbab_status mnbab_set_property(mnbab_ctx* c, const mnbab_net* cnet, const float* x_lo,
+                                const float* x_hi, const float* C, const float* d, int32_t n_rows,
+                                mnbab_prop** out) {
+  API_BEGIN(c)
+  mnbab_net* n = const_cast<mnbab_net*>(cnet);
+  if (!n || n->ctx != c || !x_lo || !x_hi || !C || n_rows <= 0 || !out)
+    fail(MNBAB_E_INVALID_ARG, "bad property arguments");
+  for (int k = 0; k < n->d0; ++k)
+    if (!(x_lo[k] <= x_hi[k])) fail(MNBAB_E_INVALID_ARG, "empty input box");
+  mnbab_prop* p = new mnbab_prop();
+  p->net = n;
+  p->index = (int)c->props.size();
+  p->n_rows = n_rows;
+  p->lo.assign(x_lo, x_lo + n->d0);
+  p->hi.assign(x_hi, x_hi + n->d0);
+  // fold the property into the last layer (Sec. 2.1)
+  const HostLayer& last = n->host[n->R + 1];
+  const int dR = last.ci, no = last.co;
+  p->Wf.assign((size_t)n_rows * dR, 0.0);
+  p->bf.assign(n_rows, 0.0);
+  for (int r = 0; r < n_rows; ++r) {
+    for (int o = 0; o < no; ++o) {
+      const double cv = C[(size_t)r * no + o];
+      if (cv == 0.0) continue;
+      for (int k = 0; k < dR; ++k) p->Wf[(size_t)r * dR + k] += cv * last.W[(size_t)o * dR + k];
+      p->bf[r] += cv * last.b[o];
+    }
+    if (d) p->bf[r] += d[r];
+  }
+  std::vector<float> Wf(p->Wf.begin(), p->Wf.end()), bf(p->bf.begin(), p->bf.end());
+  PropDev& pd = p->pd;
+  float* dlo = dalloc_t<float>(c, n->d0);
+  float* dhi = dalloc_t<float>(c, n->d0);
+  float* dWf = dalloc_t<float>(c, Wf.size());
+  float* dbf = dalloc_t<float>(c, bf.size());
+  h2d(c, dlo, x_lo, n->d0);
+  h2d(c, dhi, x_hi, n->d0);
+  h2d(c, dWf, Wf.data(), Wf.size());
+  h2d(c, dbf, bf.data(), bf.size());
+  pd.lo = dlo; pd.hi = dhi; pd.Wf = dWf; pd.bf = dbf; pd.n_rows = n_rows; pd.E = 0;
+  c->props.push_back(p);
+  upload_props(c);
+  p->row_open.assign(n_rows, 0);
+  p->row_leaf.assign(n_rows, 0);
+  p->row_fals.assign(n_rows, 0);
+  p->row_lb.assign(n_rows, INFINITY);
+  // root bounds: a slot with l = -inf, u = +inf, re-bounded from layer 1
+  const int rs = alloc_slot(n);
+  p->root_slot = rs;
+  n->slot_prop[rs] = p->index;
+  n->slot_row[rs] = 0;
+  n->slot_split[rs] = 0;
+  launch_fill(n->pool.L + (size_t)rs * n->SD, n->SD, -INFINITY, c->st);
+  launch_fill(n->pool.U + (size_t)rs * n->SD, n->SD, INFINITY, c->st);
+  ck(cudaMemsetAsync(n->pool.S + (size_t)rs * n->SD, 0, n->SD, c->st), "memset");
+  int pi = p->index;
+  h2d(c, n->pool.prop + rs, &pi, 1);
+  std::vector<int> one{rs};
+  rebound(n, one);
+  // root nodes, one per row, FIFO
+  std::vector<int> slots(n_rows);
+  for (int r = 0; r < n_rows; ++r) {
+    slots[r] = alloc_slot(n);
+    n->slot_prop[slots[r]] = p->index;
+    n->slot_row[slots[r]] = r;
+    n->slot_split[slots[r]] = n->R;
+  }
+  std::vector<int> rows(n_rows);
+  for (int r = 0; r < n_rows; ++r) rows[r] = r;
+  if (n_rows > 2 * n->B) fail(MNBAB_E_INVALID_ARG, "too many property rows");
+  int* tmp = n->kid_slots;  // scratch for the slot list
+  h2d(c, tmp, slots.data(), n_rows);
+  launch_root_init(n_rows, tmp, rs, n->pool, c->st);
+  for (int r = 0; r < n_rows; ++r) h2d(c, n->pool.row + slots[r], &rows[r], 1);
+  sync(c);
+  for (int r = 0; r < n_rows; ++r) {
+    p->queue.push_back(QNode{slots[r], p->next_seq++, r, 0, n->R});
+    p->row_open[r]++;
+  }
+  *out = p;
+  API_END(c)
+}
+
+mnbab_status mnbab_get_root_bounds(const mnbab_ctx* cc, const mnbab_prop* p, int32_t layer,
+                                   float* l_out, float* u_out) {
+  mnbab_ctx* c = const_cast<mnbab_ctx*>(cc);
+  API_BEGIN(c)
+  if (!p || !l_out || !u_out) fail(MNBAB_E_INVALID_ARG, "null argument");
+  mnbab_net* n = p->net;
+  if (layer < 1 || layer > n->R) fail(MNBAB_E_INVALID_ARG, "bad layer");
+  const size_t base = (size_t)p->root_slot * n->SD + n->nd.off[layer];
+  d2h(c, l_out, n->pool.L + base, n->nd.d[layer]);
+  d2h(c, u_out, n->pool.U + base, n->nd.d[layer]);
+  sync(c);
+  API_END(c)
+}
+
+mnbab_status mnbab_set_mnc(mnbab_ctx* c, mnbab_prop* p, int32_t layer, int32_t n_rows, int32_t k,
+                           const int32_t* idx, const float* P, const float* Phat, const float* pv) {
+  API_BEGIN(c)
+  if (!p || layer < 1 || layer > p->net->R || n_rows < 0 || k <= 0 || (n_rows && (!idx || !P ||
+      !Phat || !pv)))
+    fail(MNBAB_E_INVALID_ARG, "bad constraint arguments");
+  if (p->mnc_set[layer]) fail(MNBAB_E_INVALID_ARG, "constraints of this layer already set");
+  mnbab_net* n = p->net;
+  const int d = n->nd.d[layer];
+  if (p->pd.E + n_rows > c->EC)
+    fail(MNBAB_E_BUDGET, "more constraint rows than mnbab_options.max_mnc_rows");
+  for (int64_t q = 0; q < (int64_t)n_rows * k; ++q)
+    if (idx[q] < 0 || idx[q] >= d) fail(MNBAB_E_INVALID_ARG, "constraint neuron index out of range");
+  MncDev& m = p->pd.mnc[layer];
+  m.e = n_rows;
+  m.k = k;
+  m.goff = p->pd.E;
+  if (n_rows > 0) {
+    const size_t nk = (size_t)n_rows * k;
+    // CSR by neuron
+    std::vector<int> cnt(d + 1, 0);
+    for (size_t q = 0; q < nk; ++q) cnt[idx[q] + 1]++;
+    for (int j = 0; j < d; ++j) cnt[j + 1] += cnt[j];
+    std::vector<int> ce(nk), pos(cnt.begin(), cnt.end() - 1);
+    std::vector<float> cP(nk), cPh(nk);
+    for (int e = 0; e < n_rows; ++e)
+      for (int kk = 0; kk < k; ++kk) {
+        const size_t q = (size_t)e * k + kk;
+        const int at = pos[idx[q]]++;
+        ce[at] = e;
+        cP[at] = P[q];
+        cPh[at] = Phat[q];
+      }
+    int* didx = dalloc_t<int>(c, nk);
+    float* dP = dalloc_t<float>(c, nk);
+    float* dPh = dalloc_t<float>(c, nk);
+    float* dp = dalloc_t<float>(c, n_rows);
+    int* dcptr = dalloc_t<int>(c, d + 1);
+    int* dce = dalloc_t<int>(c, nk);
+    float* dcP = dalloc_t<float>(c, nk);
+    float* dcPh = dalloc_t<float>(c, nk);
+    h2d(c, didx, idx, nk);
+    h2d(c, dP, P, nk);
+    h2d(c, dPh, Phat, nk);
+    h2d(c, dp, pv, n_rows);
+    h2d(c, dcptr, cnt.data(), d + 1);
+    h2d(c, dce, ce.data(), nk);
+    h2d(c, dcP, cP.data(), nk);
+    h2d(c, dcPh, cPh.data(), nk);
+    m.idx = didx; m.P = dP; m.Ph = dPh; m.p = dp;
+    m.cptr = dcptr; m.ce = dce; m.cP = dcP; m.cPh = dcPh;
+  }
+  p->pd.E += n_rows;
+  p->mnc_set[layer] = 1;
+  upload_props(c);
+  sync(c);
+  API_END(c)
+}
+
+mnbab_status mnbab_node_root(mnbab_ctx* c, mnbab_prop* p, int32_t row, mnbab_node_id* out) {
+  API_BEGIN(c)
+  if (!p || !out || row < 0 || row >= p->n_rows) fail(MNBAB_E_INVALID_ARG, "bad row");
+  mnbab_net* n = p->net;
+  const int s = alloc_slot(n);
+  n->slot_prop[s] = p->index;
+  n->slot_row[s] = row;
+  n->slot_split[s] = n->R;
+  h2d(c, n->kid_slots, &s, 1);
+  launch_root_init(1, n->kid_slots, p->root_slot, n->pool, c->st);
+  h2d(c, n->pool.row + s, &row, 1);
+  sync(c);
+  *out = ((int64_t)n->id << 32) | (int64_t)s;
+  API_END(c)
+}
+
+mnbab_status mnbab_node_free(mnbab_ctx* c, mnbab_node_id node) {
+  API_BEGIN(c)
+  int s;
+  mnbab_net* n = net_of(c, node, &s);
+  free_slot(n, s);
+  API_END(c)
+}
+
+mnbab_status mnbab_export_params(const mnbab_ctx* cc, mnbab_node_id node, void* buf,
+                                 size_t* bytes) {
+  mnbab_ctx* c = const_cast<mnbab_ctx*>(cc);
+  API_BEGIN(c)
+  if (!bytes) fail(MNBAB_E_INVALID_ARG, "null size");
+  int s;
+  mnbab_net* n = net_of(c, node, &s);
+  const int E = c->props[n->slot_prop[s]]->pd.E;
+  const size_t SD = n->SD;
+  const size_t need = 16 + SD * (4 + 4 + 1 + 4 + 4) + (size_t)E * 4;
+  if (!buf) {
+    *bytes = need;
+    return MNBAB_OK;
+  }
+  if (*bytes < need) fail(MNBAB_E_INVALID_ARG, "buffer too small");
+  char* b = static_cast<char*>(buf);
+  int32_t hdr[4] = {n->slot_split[s], n->R, n->SD, E};
+  std::memcpy(b, hdr, 16);
+  char* q = b + 16;
+  d2h(c, (float*)q, n->pool.L + s * SD, SD); q += SD * 4;
+  d2h(c, (float*)q, n->pool.U + s * SD, SD); q += SD * 4;
+  d2h(c, (int8_t*)q, n->pool.S + s * SD, SD); q += SD;
+  d2h(c, (float*)q, n->pool.ALPHA + s * SD, SD); q += SD * 4;
+  d2h(c, (float*)q, n->pool.BETA + s * SD, SD); q += SD * 4;
+  d2h(c, (float*)q, n->pool.GAM + (size_t)s * c->EC, E);
+  sync(c);
+  *bytes = need;
+  API_END(c)
+}
+
+mnbab_status mnbab_import_params(mnbab_ctx* c, mnbab_node_id node, const void* buf, size_t bytes) {
+  API_BEGIN(c)
+  if (!buf) fail(MNBAB_E_INVALID_ARG, "null buffer");
+  int s;
+  mnbab_net* n = net_of(c, node, &s);
+  const int E = c->props[n->slot_prop[s]]->pd.E;
+  const size_t SD = n->SD;
+  const size_t need = 16 + SD * (4 + 4 + 1 + 4 + 4) + (size_t)E * 4;
+  if (bytes < need) fail(MNBAB_E_INVALID_ARG, "parameter block too small");
+  const char* b = static_cast<const char*>(buf);
+  int32_t hdr[4];
+  std::memcpy(hdr, b, 16);
+  if (hdr[1] != n->R || hdr[2] != n->SD || hdr[3] != E)
+    fail(MNBAB_E_INVALID_ARG, "parameter block does not match the node's network / property");
+  if (hdr[0] < 0 || hdr[0] > n->R) fail(MNBAB_E_INVALID_ARG, "bad split layer");
+  const char* q = b + 16;
+  h2d(c, n->pool.L + s * SD, (const float*)q, SD); q += SD * 4;
+  h2d(c, n->pool.U + s * SD, (const float*)q, SD); q += SD * 4;
+  h2d(c, n->pool.S + s * SD, (const int8_t*)q, SD); q += SD;
+  h2d(c, n->pool.ALPHA + s * SD, (const float*)q, SD); q += SD * 4;
+  h2d(c, n->pool.BETA + s * SD, (const float*)q, SD); q += SD * 4;
+  h2d(c, n->pool.GAM + (size_t)s * c->EC, (const float*)q, E);
+  sync(c);
+  n->slot_split[s] = hdr[0];
+  API_END(c)
+}
+
+mnbab_status mnbab_bound_batch(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t nn,
+                               float* lb_out, float* ub_out) {
+  API_BEGIN(c)
+  std::vector<int> slots;
+  mnbab_net* n = slots_of(c, nodes, nn, slots);
+  if (!lb_out) fail(MNBAB_E_INVALID_ARG, "null output");
+  rebound(n, slots);
+  upload_batch(n, slots);
+  const bool g = batch_has_gamma(n, slots);
+  if (g) launch_gamma_proj(nn, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+  SweepOpts o;
+  o.final_mode = true;
+  o.has_gamma = g;
+  o.store = true;
+  sweep(n, n->R + 1, obj_rows(n, nn), o);
+  d2h(c, lb_out, n->lb, nn);
+  if (ub_out) {
+    forward_rows(n, nn, n->X);
+    d2h(c, ub_out, n->fout, nn);
+  }
+  sync(c);
+  API_END(c)
+}
+
+mnbab_status mnbab_deeppoly_batch(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t nn,
+                                  float* lb_out) {
+  API_BEGIN(c)
+  std::vector<int> slots;
+  mnbab_net* n = slots_of(c, nodes, nn, slots);
+  if (!lb_out) fail(MNBAB_E_INVALID_ARG, "null output");
+  upload_batch(n, slots);
+  SweepOpts o;
+  sweep(n, n->R + 1, obj_rows(n, nn), o);
+  d2h(c, lb_out, n->lb, nn);
+  sync(c);
+  API_END(c)
+}
+
+mnbab_status mnbab_bound_grad(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t nn,
+                              float* lb_out, float* grad_out) {
+  API_BEGIN(c)
+  std::vector<int> slots;
+  mnbab_net* n = slots_of(c, nodes, nn, slots);
+  if (!lb_out || !grad_out) fail(MNBAB_E_INVALID_ARG, "null output");
+  upload_batch(n, slots);
+  const bool g = batch_has_gamma(n, slots);
+  if (g) launch_gamma_proj(nn, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+  SweepOpts o;
+  o.final_mode = true;
+  o.has_gamma = g;
+  o.store = true;
+  sweep(n, n->R + 1, obj_rows(n, nn), o);
+  adjoint(n, nn, g);
+  d2h(c, lb_out, n->lb, nn);
+  sync(c);
+  size_t at = 0;
+  for (int i = 0; i < nn; ++i) {
+    const int E = c->props[n->slot_prop[slots[i]]]->pd.E;
+    d2h(c, grad_out + at, n->GA + (size_t)i * n->SD, n->SD);
+    at += n->SD;
+    d2h(c, grad_out + at, n->GB + (size_t)i * n->SD, n->SD);
+    at += n->SD;
+    if (E) d2h(c, grad_out + at, n->GG + (size_t)i * c->EC, E);
+    at += E;
+  }
+  sync(c);
+  API_END(c)
+}
+
+mnbab_status mnbab_optimize(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t nn,
+                            const mnbab_adam* cfg, float* best_lb_out) {
+  API_BEGIN(c)
+  std::vector<int> slots;
+  mnbab_net* n = slots_of(c, nodes, nn, slots);
+  if (!best_lb_out) fail(MNBAB_E_INVALID_ARG, "null output");
+  const mnbab_adam a = cfg ? *cfg : default_adam();
+  if (a.steps < 0) fail(MNBAB_E_INVALID_ARG, "negative step count");
+  upload_batch(n, slots);
+  launch_set_best(nn, n->bslots, n->pool, -INFINITY, c->st);
+  run_optimize(n, nn, batch_has_gamma(n, slots), a);
+  gather_best(n, nn, best_lb_out);
+  sync(c);
+  API_END(c)
+}
+
+mnbab_status mnbab_score_branches(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t nn,
+                                  int32_t* layer_out, int32_t* neuron_out, float* score_out) {
+  API_BEGIN(c)
+  std::vector<int> slots;
+  mnbab_net* n = slots_of(c, nodes, nn, slots);
+  if (!layer_out || !neuron_out) fail(MNBAB_E_INVALID_ARG, "null output");
+  upload_batch(n, slots);
+  const bool g = batch_has_gamma(n, slots);
+  if (g) launch_gamma_proj(nn, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+  SweepOpts o;
+  o.final_mode = true;
+  o.has_gamma = g;
+  o.store = true;
+  sweep(n, n->R + 1, obj_rows(n, nn), o);
+  launch_acs(nn, n->bslots, n->pool, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0, n->acs_layer,
+             n->acs_neuron, n->score, n->acs_fb, c->st);
+  d2h(c, layer_out, n->acs_layer, nn);
+  d2h(c, neuron_out, n->acs_neuron, nn);
+  if (score_out) d2h(c, score_out, n->score, nn);
+  sync(c);
+  API_END(c)
+}
+
+mnbab_status mnbab_bab_step(mnbab_ctx* c, mnbab_prop* const* props, int32_t n_props,
+                            int32_t max_nodes, const mnbab_adam* cfg, mnbab_step_stats* out) {
+  API_BEGIN(c)
+  if (!props || !out) fail(MNBAB_E_INVALID_ARG, "null argument");
+  const mnbab_adam a = cfg ? *cfg : default_adam();
+  bab_step_impl(c, props, n_props, max_nodes, a, out);
+  API_END(c)
+}
+
+mnbab_status mnbab_set_budget(mnbab_ctx* c, mnbab_prop* p, int32_t max_nodes) {
+  API_BEGIN(c)
+  if (!p || max_nodes <= 0) fail(MNBAB_E_INVALID_ARG, "bad budget");
+  p->budget = max_nodes;
+  API_END(c)
+}
+
+mnbab_status mnbab_get_verdict(const mnbab_ctx* cc, const mnbab_prop* p, int32_t row,
+                               int32_t* verdict, float* lb, float* x_cex) {
+  mnbab_ctx* c = const_cast<mnbab_ctx*>(cc);
+  API_BEGIN(c)
+  if (!p || !verdict) fail(MNBAB_E_INVALID_ARG, "null argument");
+  if (row >= p->n_rows) fail(MNBAB_E_INVALID_ARG, "bad row");
+  if (row < 0) {
+    *verdict = p->done ? p->verdict : MNBAB_UNKNOWN;
+    if (lb) {
+      float m = INFINITY;
+      for (float v : p->row_lb) m = std::min(m, v);
+      *lb = m;
+    }
+    if (x_cex && p->verdict == MNBAB_FALSIFIED)
+      std::memcpy(x_cex, p->cex.data(), p->cex.size() * sizeof(float));
+  } else {
+    int v = MNBAB_UNKNOWN;
+    if (p->row_fals[row]) v = MNBAB_FALSIFIED;
+    else if (p->row_open[row] == 0 && !p->row_leaf[row] &&
+             !(p->done && p->verdict != MNBAB_VERIFIED && p->row_lb[row] <= 0.f))
+      v = MNBAB_VERIFIED;
+    *verdict = v;
+    if (lb) *lb = p->row_lb[row];
+    if (x_cex && p->cex_row == row)
+      std::memcpy(x_cex, p->cex.data(), p->cex.size() * sizeof(float));
+  }
+  API_END(c)
+}
+
+mnbab_status mnbab_get_trace(const mnbab_ctx* cc, const mnbab_prop* p, mnbab_trace_rec* recs,
+                             int32_t max_recs, int32_t* n_out) {
+  mnbab_ctx* c = const_cast<mnbab_ctx*>(cc);
+  API_BEGIN(c)
+  if (!p || !n_out) fail(MNBAB_E_INVALID_ARG, "null argument");
+  const int nt = (int)p->trace.size();
+  const int k = recs ? std::min(nt, std::max(0, (int)max_recs)) : 0;
+  for (int i = 0; i < k; ++i) recs[i] = p->trace[i];
+  *n_out = recs ? k : nt;
+  API_END(c)
+}
+
+mnbab_status mnbab_queue_size(const mnbab_ctx* cc, const mnbab_prop* p, int32_t* n_out) {
+  mnbab_ctx* c = const_cast<mnbab_ctx*>(cc);
+  API_BEGIN(c)
+  if (!p || !n_out) fail(MNBAB_E_INVALID_ARG, "null argument");
+  *n_out = (int)p->queue.size();
+  API_END(c)
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+"""Shared set-up for the GPU-vs-oracle parity tests."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import synth
+from oracle import bab, core, mnc
+from oracle.core import DT
+
+TOL = 1e-4  # bound tolerance: |gpu - oracle| <= TOL * (1 + |oracle|)
+
+
+def close(g, o, tol=TOL):
+    g = np.asarray(g, np.float64)
+    o = np.asarray(o, np.float64)
+    both_inf = np.isinf(g) & np.isinf(o) & (np.sign(g) == np.sign(o))
+    ok = both_inf | (np.abs(g - o) <= tol * (1.0 + np.abs(o)))
+    return ok
+
+
+def f32(t):
+    return torch.as_tensor(np.asarray(t, np.float32).astype(np.float64), dtype=DT)
+
+
+def fc_case(seed, dims, eps, with_mnc=False, x_seed=None):
+    layers = synth.tiny_fc_net(seed, list(dims))
+    rng = np.random.default_rng(seed + 100 if x_seed is None else x_seed)
+    x0 = rng.uniform(0.2, 0.8, dims[0]).astype(np.float32)
+    y = synth.net_forward(layers, x0)
+    C, d = synth.property_rows(int(np.argmax(y)), dims[-1])
+    lo, hi = synth.input_box(x0, eps)
+    prep = bab.prepare(layers, C, d, lo, hi, mnc.mnc_fn() if with_mnc else None)
+    return layers, C, d, lo, hi, prep
+
+
+def conv_spec(seed):
+    """Small conv chain with ragged sizes (stride 2, padding, odd widths)."""
+    return dict(seed=seed, in_shape=(2, 11, 11),
+                layers=[("conv", 5, 3, 2, 1), ("relu",), ("conv", 7, 4, 2, 1), ("relu",),
+                        ("fc", 13), ("relu",), ("fc", 4)])
+
+
+def conv_case(seed, eps):
+    spec = conv_spec(seed)
+    layers = synth.make_network(spec)
+    x0 = synth.make_image(seed + 7, spec["in_shape"]).reshape(-1)
+    y = synth.net_forward(layers, x0)
+    C, d = synth.property_rows(int(np.argmax(y)), 4)
+    lo, hi = synth.input_box(x0, eps)
+    prep = bab.prepare(layers, C, d, lo, hi)
+    return layers, C, d, lo, hi, prep
+
+
+def gpu_property(ctx, layers, lo, hi, C, d, mncs=None):
+    net = ctx.load_network(layers)
+    prop = ctx.set_property(net, lo, hi, C, d)
+    if mncs:
+        for i in sorted(mncs):
+            m = mncs[i]
+            ctx.set_mnc(prop, i, m.idx, m.P, m.Ph, m.p)
+    return net, prop
+
+
+def random_node(prep, rng, n_splits, row=0, gamma_scale=0.2):
+    """Oracle node with random splits (clamped, not yet re-bounded) and random
+    parameters, all rounded to float32 so both sides start from the same values."""
+    net, lo, hi, l, u, S, m, dense = prep
+    node = bab.root_node(net, row, l, u, S, m)
+    cands = [(i, j) for i in l for j in range(l[i].numel()) if l[i][j] < 0 < u[i][j]]
+    k = min(n_splits, len(cands))
+    picks = [cands[t] for t in rng.choice(len(cands), size=k, replace=False)] if k else []
+    for (i, j) in picks:
+        sgn = int(rng.choice([1, -1]))
+        node.S[i][j] = sgn
+        if sgn == 1:
+            node.u[i][j] = min(float(node.u[i][j]), 0.0)
+        else:
+            node.l[i][j] = max(float(node.l[i][j]), 0.0)
+    node.split_layer = max([p[0] for p in picks], default=net.R) if picks else net.R
+    if picks and rng.random() < 0.5:
+        node.split_layer = min(p[0] for p in picks)
+    for i in l:
+        node.l[i] = f32(node.l[i].numpy())
+        node.u[i] = f32(node.u[i].numpy())
+        node.alpha[i] = f32(rng.uniform(0, 1, l[i].numel()))
+        node.beta[i] = f32(rng.uniform(0, 1, l[i].numel()) * (node.S[i].numpy() != 0))
+        node.gamma[i] = f32(rng.uniform(0, gamma_scale, node.gamma[i].numel()))
+    return node
+
+
+def to_params(node, R):
+    from paper_2205_00263_gb300 import NodeParams
+    ks = range(1, R + 1)
+    cat = lambda D, dt: np.concatenate([np.asarray(D[i].numpy(), dt) for i in ks])
+    gam = [node.gamma[i].numpy() for i in ks if node.gamma[i].numel()]
+    return NodeParams(node.split_layer, R, cat(node.l, np.float32), cat(node.u, np.float32),
+                      cat(node.S, np.int8), cat(node.alpha, np.float32), cat(node.beta, np.float32),
+                      np.concatenate(gam).astype(np.float32) if gam else np.zeros(0, np.float32))
+
+
+def concat(D, R):
+    return np.concatenate([D[i].numpy() for i in range(1, R + 1)])

@@ -1,0 +1,355 @@
+"""GPU library (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerance (bounds and gradients): |gpu - oracle| <= 1e-4 (1 + |oracle|).
+Verdicts must match except where the oracle's margin lies inside that band
+(flagged); branching choices must match except at ACS ties within 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import TOL, close, concat, conv_case, fc_case, f32, gpu_property, random_node, to_params
+from oracle import bab, core, mnc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Context():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_00263_gb300 import Context
+    return Context
+
+
+def _assert_close(g, o, what, tol=TOL):
+    ok = close(g, o, tol)
+    if not ok.all():
+        i = int(np.argmin(ok))
+        raise AssertionError(f"{what}: {int((~ok).sum())} mismatches, first at {i}: "
+                             f"gpu {np.asarray(g).reshape(-1)[i]} oracle {np.asarray(o).reshape(-1)[i]}")
+
+
+# --------------------------------------------------------------------------
+# root bounds (DeepPoly back-substitution of every neuron, both sides)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["ragged_fc", "conv", "cfg0"])
+def test_root_bounds(Context, case):
+    if case == "ragged_fc":
+        layers, C, d, lo, hi, prep = fc_case(1, (37, 53, 29, 7), 0.1)
+    elif case == "conv":
+        layers, C, d, lo, hi, prep = conv_case(2, 0.05)
+    else:
+        layers = synth.make_network(0)
+        pr = synth.make_properties(0, layers, n=1, eps=synth.load_eps(0))[0]
+        layers, C, d, lo, hi = layers, pr.C, pr.d, pr.lo, pr.hi
+        prep = bab.prepare(layers, C, d, lo, hi)
+    net, lo_t, hi_t, l, u, S, _, _ = prep
+    with Context(node_capacity=64) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
+        for i in range(1, net.R + 1):
+            gl, gu = ctx.root_bounds(prop, i)
+            _assert_close(gl, l[i].numpy(), f"l{i}")
+            _assert_close(gu, u[i].numpy(), f"u{i}")
+
+
+# --------------------------------------------------------------------------
+# fixed parameters: re-bounding after splits and the objective bound
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["fc_mnc", "conv"])
+def test_rebound_and_bound_at_fixed_parameters(Context, case):
+    if case == "fc_mnc":
+        layers, C, d, lo, hi, prep = fc_case(3, (37, 53, 29, 7), 0.12, with_mnc=True)
+    else:
+        layers, C, d, lo, hi, prep = conv_case(4, 0.08)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    E = sum(v.idx.shape[0] for v in m.values()) if m else 0
+    rng = np.random.default_rng(11)
+    with Context(node_capacity=256, max_mnc_rows=max(E, 1)) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d, m)
+        onodes, gids = [], []
+        for k in range(40):
+            on = random_node(prep, rng, n_splits=k % 5, row=k % C.shape[0])
+            gid = ctx.node_root(prop, on.row)
+            ctx.import_params(gid, to_params(on, net.R))
+            onodes.append(on)
+            gids.append(gid)
+        lb, ub = ctx.bound_batch(gids)
+        for k, (on, gid) in enumerate(zip(onodes, gids)):
+            core.rebound_node(net, on, lo_t, hi_t)
+            p = ctx.export_params(gid)
+            _assert_close(p.l, concat(on.l, net.R), f"node {k} l")
+            _assert_close(p.u, concat(on.u, net.R), f"node {k} u")
+            ref, xs, _ = core.final_bound(net, on, on.alpha, on.beta, on.gamma, dense, lo_t, hi_t)
+            _assert_close(lb[k], float(ref), f"node {k} lb")
+            f_ref = float(net.forward(xs.reshape(1, -1))[0, on.row])
+            assert ub[k] >= lb[k] - 1e-5 * (1 + abs(lb[k]))   # f(x*) is an upper bound
+            # x* may differ only on coordinates whose coefficient is ~0
+            assert abs(ub[k] - f_ref) <= 5e-2 * (1 + abs(f_ref))
+
+
+def test_deeppoly_pass(Context):
+    layers, C, d, lo, hi, prep = fc_case(5, (37, 53, 29, 7), 0.1, with_mnc=True)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    E = sum(v.idx.shape[0] for v in m.values())
+    rng = np.random.default_rng(5)
+    with Context(node_capacity=128, max_mnc_rows=E) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d, m)
+        onodes, gids = [], []
+        for k in range(12):
+            on = random_node(prep, rng, n_splits=k % 4, row=k % C.shape[0])
+            on.split_layer = net.R
+            gid = ctx.node_root(prop, on.row)
+            ctx.import_params(gid, to_params(on, net.R))
+            onodes.append(on)
+            gids.append(gid)
+        lb = ctx.deeppoly_batch(gids)
+        for k, on in enumerate(onodes):
+            ref, _ = core.deeppoly_final(net, on, lo_t, hi_t)
+            _assert_close(lb[k], float(ref), f"node {k}")
+
+
+# --------------------------------------------------------------------------
+# adjoint: gradient of the bound w.r.t. alpha, beta, gamma
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["fc_mnc", "conv"])
+def test_gradient_matches_oracle(Context, case):
+    if case == "fc_mnc":
+        layers, C, d, lo, hi, prep = fc_case(6, (37, 53, 29, 7), 0.12, with_mnc=True)
+    else:
+        layers, C, d, lo, hi, prep = conv_case(7, 0.08)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    E = sum(v.idx.shape[0] for v in m.values()) if m else 0
+    SD = sum(l[i].numel() for i in l)
+    rng = np.random.default_rng(3)
+    with Context(node_capacity=128, max_mnc_rows=max(E, 1)) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d, m)
+        onodes, gids = [], []
+        for k in range(10):
+            on = random_node(prep, rng, n_splits=k % 4, row=k % C.shape[0])
+            on.split_layer = net.R
+            gid = ctx.node_root(prop, on.row)
+            ctx.import_params(gid, to_params(on, net.R))
+            onodes.append(on)
+            gids.append(gid)
+        lb, ga, gb, gg = ctx.bound_grad(gids, SD, E)
+        for k, on in enumerate(onodes):
+            ref, _, oa, ob, og = core.bound_and_grad(net, on, on.alpha, on.beta, on.gamma,
+                                                     dense, lo_t, hi_t)
+            _assert_close(lb[k], float(ref), f"node {k} lb")
+            for name, g, o in (("alpha", ga[k], concat(oa, net.R)), ("beta", gb[k], concat(ob, net.R))):
+                scale = 1e-4 * (1 + np.abs(o).max())
+                assert np.abs(g - o).max() <= scale, (name, k, np.abs(g - o).max())
+            if E:
+                o = np.concatenate([og[i].numpy() for i in sorted(og) if og[i].numel()])
+                scale = 1e-4 * (1 + np.abs(o).max())
+                assert np.abs(gg[k] - o).max() <= scale, ("gamma", k, np.abs(gg[k] - o).max())
+
+
+# --------------------------------------------------------------------------
+# projected Adam (20 steps) and ACS
+# --------------------------------------------------------------------------
+def test_optimized_bound_matches_oracle(Context):
+    layers, C, d, lo, hi, prep = fc_case(8, (37, 53, 29, 7), 0.12, with_mnc=True)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    E = sum(v.idx.shape[0] for v in m.values())
+    rng = np.random.default_rng(8)
+    with Context(node_capacity=128, max_mnc_rows=E) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d, m)
+        onodes, gids = [], []
+        for k in range(8):
+            on = random_node(prep, rng, n_splits=k % 3, row=k % C.shape[0], gamma_scale=0.0)
+            on.split_layer = net.R
+            gid = ctx.node_root(prop, on.row)
+            ctx.import_params(gid, to_params(on, net.R))
+            onodes.append(on)
+            gids.append(gid)
+        best = ctx.optimize(gids, steps=20)
+        n_ok = 0
+        for k, on in enumerate(onodes):
+            ref, *_ = core.optimize(net, on, dense, lo_t, hi_t, core.AdamHP())
+            ok = abs(best[k] - ref) <= TOL * (1 + abs(ref))
+            n_ok += ok
+            # never worse than the fixed-parameter start by more than the tolerance
+            assert abs(best[k] - ref) <= 5e-3 * (1 + abs(ref)), (k, best[k], ref)
+        assert n_ok >= len(onodes) - 1, n_ok
+
+
+def test_acs_choice_matches_oracle(Context):
+    layers, C, d, lo, hi, prep = fc_case(9, (37, 53, 29, 7), 0.12, with_mnc=True)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    E = sum(v.idx.shape[0] for v in m.values())
+    rng = np.random.default_rng(9)
+    with Context(node_capacity=128, max_mnc_rows=E) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d, m)
+        for k in range(12):
+            # half the nodes without active constraints: intercept fallback
+            on = random_node(prep, rng, n_splits=k % 3, row=k % C.shape[0],
+                             gamma_scale=0.0 if k % 2 else 0.3)
+            on.split_layer = net.R
+            gid = ctx.node_root(prop, on.row)
+            ctx.import_params(gid, to_params(on, net.R))
+            lay, neu, sc = ctx.score_branches([gid])
+            _, _, aps = core.final_bound(net, on, on.alpha, on.beta, on.gamma, dense, lo_t, hi_t,
+                                         keep_ap=True)
+            scores, fb = core.acs_scores(on, on.gamma, dense, aps)
+            pick = core.pick_split(scores)
+            assert pick is not None and lay[0] > 0
+            _assert_close(sc[0], pick[2], f"node {k} max score")
+            if (lay[0], neu[0]) != pick[:2]:
+                s_gpu = float(scores[int(lay[0])][int(neu[0])])
+                assert s_gpu >= pick[2] - 1e-4 * abs(pick[2]), "choice outside the tie band"
+
+
+# --------------------------------------------------------------------------
+# branch and bound: node-by-node trace against the oracle
+# --------------------------------------------------------------------------
+def _run_gpu_bab(ctx, props, max_nodes, steps=20):
+    for _ in range(10000):
+        st = ctx.bab_step(props, max_nodes=max_nodes, steps=steps)
+        if st["nodes_bounded"] == 0:
+            break
+
+
+def _compare_trace(gtr, ores, max_cmp=None):
+    """Node-by-node agreement up to the first flagged divergence."""
+    flagged = 0
+    n = min(len(gtr), len(ores.nodes)) if max_cmp is None else min(max_cmp, len(gtr), len(ores.nodes))
+    for k in range(n):
+        g, o = gtr[k], ores.nodes[k]
+        assert g["seq"] == o.node_id and g["row"] == o.row, (k, g, o)
+        band = TOL * (1 + abs(o.lb))
+        assert abs(g["lb"] - o.lb) <= max(band, 5e-3 * (1 + abs(o.lb))), (k, g["lb"], o.lb)
+        if abs(o.lb) <= 5e-3 * (1 + abs(o.lb)):
+            flagged += 1
+            return k, flagged
+        assert g["verdict"] == o.verdict, (k, g, o)
+        gs = (g["split_layer"], g["split_neuron"]) if g["split_layer"] > 0 else None
+        if gs != o.split:
+            return k, flagged + 1   # tie-band divergence: trees differ from here on
+    return n, flagged
+
+
+def test_bab_trace_matches_oracle_fc_with_mnc(Context):
+    layers = synth.make_network(0)
+    eps = synth.load_eps(0)
+    prs = synth.make_properties(0, layers, n=3, eps=eps)
+    budget = 20
+    with Context(node_capacity=4096, max_mnc_rows=65536) as ctx:
+        matched = 0
+        for pr in prs:
+            prep = bab.prepare(layers, pr.C, pr.d, pr.lo, pr.hi, mnc.mnc_fn())
+            ores = bab.verify(layers, pr.C, pr.d, pr.lo, pr.hi, max_nodes=budget, prepared=prep)
+            gnet, prop = gpu_property(ctx, layers, pr.lo, pr.hi, pr.C, pr.d, prep[6])
+            ctx.set_budget(prop, budget)
+            _run_gpu_bab(ctx, [prop], max_nodes=1)
+            gtr = ctx.trace(prop)
+            k, flagged = _compare_trace(gtr, ores)
+            matched += k
+            if flagged == 0 and k == len(ores.nodes):
+                v, _, _ = ctx.verdict(prop)
+                assert v == ores.verdict
+        assert matched >= 20
+
+
+def test_batched_equals_one_node_per_launch(Context):
+    """The batched form and the one-subproblem-per-launch form give identical
+    trees and bounds (FIFO order does not depend on the batch size)."""
+    layers = synth.make_network(1)
+    eps = synth.load_eps(1)
+    prs = synth.make_properties(1, layers, n=3, eps=eps)
+    traces = []
+    for max_nodes in (1, 512):
+        with Context(node_capacity=4096) as ctx:
+            net = ctx.load_network(layers)
+            props = []
+            for pr in prs:
+                p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+                ctx.set_budget(p, 24)
+                props.append(p)
+            _run_gpu_bab(ctx, props, max_nodes=max_nodes, steps=5)
+            traces.append([ctx.trace(p) for p in props])
+    for ta, tb in zip(*traces):
+        n = min(len(ta), len(tb))
+        assert n > 0
+        for a, b in zip(ta[:n], tb[:n]):
+            for key in ("seq", "row", "verdict", "split_layer", "split_neuron"):
+                assert a[key] == b[key], (key, a, b)
+            assert a["lb"] == b["lb"] or abs(a["lb"] - b["lb"]) <= 1e-6 * (1 + abs(a["lb"]))
+
+
+def test_conv_full_size_sampled(Context):
+    """28x28 conv net, 100 properties, 512 subproblems per step (the timed
+    configuration): sampled nodes agree with the oracle computed one by one, and
+    every bound is sound at sampled inputs."""
+    layers = synth.make_network(1)
+    eps = synth.load_eps(1)
+    prs = synth.make_properties(1, layers, eps=eps)
+    with Context(node_capacity=16384) as ctx:
+        net = ctx.load_network(layers)
+        props = [ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d) for pr in prs]
+        for _ in range(3):
+            ctx.bab_step(props, max_nodes=512, steps=20)
+        # property 0 against the oracle, node by node (roots and first children)
+        ores = bab.verify(layers, prs[0].C, prs[0].d, prs[0].lo, prs[0].hi, max_nodes=12)
+        gtr = ctx.trace(props[0])
+        k, flagged = _compare_trace(gtr, ores, max_cmp=12)
+        assert k + flagged >= min(9, len(ores.nodes))
+        # soundness of root bounds at sampled inputs, counterexamples confirmed in FP64
+        rng = np.random.default_rng(0)
+        for pr, p in zip(prs[:20], props[:20]):
+            X = rng.uniform(pr.lo, pr.hi, size=(256, pr.lo.size))
+            F = np.stack([pr.C @ synth.net_forward(layers, x) + pr.d for x in X])
+            for rec in ctx.trace(p):
+                if rec["depth"] == 0:
+                    assert rec["lb"] <= F[:, rec["row"]].min() + 1e-4
+            v, _, xc = ctx.verdict(p)
+            if v == -1:
+                assert np.all(xc >= pr.lo) and np.all(xc <= pr.hi)
+                assert (pr.C @ synth.net_forward(layers, xc) + pr.d).min() < 0
+
+
+# --------------------------------------------------------------------------
+# edge cases
+# --------------------------------------------------------------------------
+def test_zero_radius_box_is_exact(Context):
+    layers, C, d, lo, hi, prep = fc_case(12, (37, 53, 29, 7), 0.0)
+    x0 = lo
+    with Context(node_capacity=64) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
+        nodes = [ctx.node_root(prop, r) for r in range(C.shape[0])]
+        lb = ctx.deeppoly_batch(nodes)
+        ref = C @ synth.net_forward(layers, x0) + d
+        assert np.all(np.abs(lb - ref) <= 1e-5 * (1 + np.abs(ref)))
+        ctx.bab_step([prop], max_nodes=64, steps=2)
+        v, _, _ = ctx.verdict(prop)
+        assert v == 1
+
+
+def test_batch_capacity_and_errors(Context):
+    from paper_2205_00263_gb300 import MnbabError
+    layers, C, d, lo, hi, prep = fc_case(13, (37, 53, 29, 7), 0.1)
+    with Context(node_capacity=2048) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
+        nodes = [ctx.node_root(prop, r % C.shape[0]) for r in range(1024)]
+        lb = ctx.deeppoly_batch(nodes)
+        assert np.all(np.isfinite(lb))
+        # identical nodes give identical bounds, wherever they sit in the batch
+        for r in range(C.shape[0]):
+            assert np.all(lb[r::C.shape[0]] == lb[r])
+        extra = ctx.node_root(prop, 0)
+        with pytest.raises(MnbabError):
+            ctx.deeppoly_batch(nodes + [extra])
+        with pytest.raises(MnbabError):
+            ctx.deeppoly_batch([])
+        p = ctx.export_params(nodes[0])
+        p.l = p.l[:-1]
+        with pytest.raises(MnbabError):
+            ctx.import_params(nodes[0], p)
+        with pytest.raises(MnbabError):
+            ctx.set_property(gnet, hi + 1, lo, C, d)   # empty box
