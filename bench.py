@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Throughput of batched MN-BaB bounding on one GB300: BaB nodes bounded / s.
+
+Workload: the 28x28 conv net 1x28x28 -> conv16 4x4 s2 -> ReLU -> conv32 4x4 s2
+-> ReLU -> FC100 -> ReLU -> FC10 (He-normal, seed 1), properties built from
+seeded blurred-uniform images with the calibrated L-inf radius, margins
+y_t - y_j as rows, 256-node budget per property, up to 512 subproblems per
+BaB step, 20 projected-Adam steps per node with the adjoint kernels.  A
+rolling window of 100 active properties keeps the queue full: a finished
+property is replaced by the next seeded one (its root bounding runs inside the
+step that admits it).
+
+One step = one mnbab_bab_step (re-bounding after splits, DeepPoly pass,
+optimisation, counterexample check, ACS, queue step) over one batch.  Steps
+are timed with CUDA events on the library's stream; L2 is flushed (256 MiB
+write) between timed steps, outside the timed spans.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload instead (the only place besides the cpu_baseline leg where this file
+runs the oracle).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+CFG = 1
+WINDOW = 100
+BATCH = 512
+BUDGET = 256
+ADAM_STEPS = 20
+METRIC = "BaB nodes bounded/s & verdicts@timeout, batched/serving vs plain, 1 GB300"
+WORKLOAD = ("conv_small_28: 1x28x28 -> conv16 4x4 s2 -> ReLU -> conv32 4x4 s2 -> ReLU -> FC100 -> "
+            "ReLU -> FC10, 100 active properties (rolling window), 9 margin rows each, "
+            "<=512 subproblems per step, 20 Adam steps per node, budget 256 nodes/property")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-nodes", type=int, default=48)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def roofline(stats, peaks, src, kernels_hash):
+    """Dominant kernel class (largest summed launch time) against its roofline."""
+    name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    per_launch_ms = st["ms"] / max(1, st["launches"])
+    simt = name in ("backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm", "forward_conv")
+    if simt:
+        # SIMT FP32 FMA: 152 SMs x 128 lanes x 2 flop per cycle at the maximum SM clock
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = st["flops"] / (st["ms"] * 1e-3) / 1e12
+        r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        peak = peaks["hbm_gbs"]
+        ach = st["bytes"] / (st["ms"] * 1e-3) / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+    r["frac"] = r["achieved"] / r["peak"]
+    r["kernel"] = name
+    r["launches"] = st["launches"]
+    r["avg_launch_us"] = per_launch_ms * 1e3
+    r["traffic"] = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        if t.get("kernels_sha") == kernels_hash and name in t.get("bytes_per_launch", {}):
+            r["traffic"] = t["bytes_per_launch"][name]
+    except (OSError, ValueError):
+        pass
+    return r
+
+
+def kernels_sha():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2205_00263_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------
+class Window:
+    """Rolling window of active properties (admission inside the steps)."""
+
+    def __init__(self, ctx, net, layers, eps, start, n_active, pool_size=None):
+        self.ctx, self.net, self.layers, self.eps = ctx, net, layers, eps
+        self.next = 0
+        # host-side inputs are drawn before any timing starts
+        self.pool = synth.make_properties(CFG, layers, n=pool_size or 4 * n_active, eps=eps,
+                                          start=start)
+        self.active = []
+        self.verdicts = {1: 0, -1: 0, 0: 0}
+        self.h2d = 0
+        self.d2h = 0
+        for _ in range(n_active):
+            self.admit()
+
+    def admit(self):
+        if self.next >= len(self.pool):
+            raise RuntimeError("property pool exhausted; raise pool_size")
+        pr = self.pool[self.next]
+        self.next += 1
+        p = self.ctx.set_property(self.net, pr.lo, pr.hi, pr.C, pr.d)
+        self.ctx.set_budget(p, BUDGET)
+        self.h2d += pr.lo.nbytes + pr.hi.nbytes + pr.C.nbytes + pr.d.nbytes
+        self.active.append(p)
+
+    def step(self):
+        st = self.ctx.bab_step(self.active, max_nodes=BATCH, steps=ADAM_STEPS)
+        keep = []
+        for p in self.active:
+            if self.ctx.queue_size(p) == 0:
+                v, _, _ = self.ctx.verdict(p)
+                self.d2h += 4
+                self.verdicts[v] += 1
+            else:
+                keep.append(p)
+        n_done = len(self.active) - len(keep)
+        self.active = keep
+        for _ in range(n_done):
+            self.admit()
+        self.h2d += st["h2d_bytes"]
+        self.d2h += st["d2h_bytes"]
+        return st
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2205_00263_gb300 import Context
+
+    stream = torch.cuda.current_stream()
+    layers = synth.make_network(CFG)
+    eps = synth.load_eps(CFG)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ctx = Context(device=local, stream=stream.cuda_stream, node_capacity=65536)
+    net = ctx.load_network(layers)
+    start = rank * 1_000_000
+    win = Window(ctx, net, layers, eps, start, WINDOW, pool_size=WINDOW + 60 * (args.steps + args.warmup) + 50)
+
+    for _ in range(args.warmup):
+        win.step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ctx.profile(True)
+    _, launches0 = ctx.profile_read()
+    clocks = Clocks(local)
+    clocks.start()
+    nodes = 0
+    ms = 0.0
+    verdicts0 = dict(win.verdicts)
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = win.step()
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        nodes += st["nodes_bounded"]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    stats, launches1 = ctx.profile_read()
+    ctx.profile(False)
+    tot_ms = ms
+    tot_nodes = nodes
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        n = torch.tensor([nodes], device="cuda", dtype=torch.float64)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        tot_nodes = int(n.item())
+    value = tot_nodes / (tot_ms * 1e-3)
+
+    # plain: one subproblem per launch on fresh properties (same kernels, no batching)
+    plain = None
+    if args.plain_nodes > 0:
+        win2 = Window(ctx, net, layers, eps, start + 500_000, 8, pool_size=8 + args.plain_nodes)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        pn = 0
+        e0.record(stream)
+        while pn < args.plain_nodes:
+            st = win2.ctx.bab_step(win2.active, max_nodes=1, steps=ADAM_STEPS)
+            pn += st["nodes_bounded"]
+            if st["nodes_bounded"] == 0:
+                win2.admit()
+        e1.record(stream)
+        e1.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {"value": pn / (pms * 1e-3), "unit": "nodes/s", "nodes": pn,
+                 "form": "one subproblem per launch (max_nodes=1), same kernels, no graph"}
+
+    # e2e: public API from host arrays to verdicts, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        en, et, eh, ed = 0, 0.0, 0, 0
+        pools = [synth.make_properties(CFG, layers, n=16, eps=eps, start=start + 700_000 + 1000 * k)
+                 for k in range(args.e2e_steps)]
+        for k in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            w3 = Window.__new__(Window)
+            w3.ctx, w3.net, w3.layers, w3.eps = ctx, net, layers, eps
+            w3.pool, w3.next, w3.active, w3.h2d, w3.d2h = pools[k], 0, [], 0, 0
+            w3.verdicts = {1: 0, -1: 0, 0: 0}
+            for _ in range(16):
+                w3.admit()
+            for p in w3.active:
+                ctx.set_budget(p, 32)
+            props = list(w3.active)
+            while True:
+                st = ctx.bab_step(props, max_nodes=BATCH, steps=ADAM_STEPS)
+                en += st["nodes_bounded"]
+                eh += st["h2d_bytes"]
+                ed += st["d2h_bytes"]
+                if st["nodes_bounded"] == 0:
+                    break
+            for p in props:
+                ctx.verdict(p)
+                ed += 4 + 4 * p.net.d0
+            torch.cuda.synchronize()
+            et += time.perf_counter() - t0
+            eh += w3.h2d
+        e2e = {"value": en / et, "unit": "nodes/s",
+               "h2d_bytes_per_step": eh // args.e2e_steps, "d2h_bytes_per_step": ed // args.e2e_steps,
+               "step": "16 fresh properties from host arrays (32-node budget each) to verdicts"}
+
+    peaks, src = load_peaks()
+    roof = roofline(stats, peaks, src, kernels_sha())
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+        cpu = {k: v for k, v in cpu.items() if not k.startswith("_")}
+    if rank == 0:
+        vd = {k: win.verdicts[k] - verdicts0.get(k, 0) for k in win.verdicts}
+        out = {
+            "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded He-normal net, blurred-uniform images; no dataset)",
+            "config": {"workload": WORKLOAD, "l2": "flushed (256 MiB write) between timed steps",
+                       "parallelism": f"replicas x{world} (independent properties per rank)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches1 - launches0), "clocks": clk,
+            "plain": plain,
+            "batched_over_plain": (value / world / plain["value"]) if plain else None,
+            "verdicts_in_timed_steps": {"verified": vd[1], "falsified": vd[-1], "unknown": vd[0]},
+            "kernel_breakdown_ms": {k: round(v["ms"], 3) for k, v in stats.items()},
+            "nodes_timed": tot_nodes,
+        }
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+def cpu_baseline(seconds: float, start: int = 0):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
+    BaB on seeded properties of the same net until ~`seconds` of CPU work."""
+    import torch
+    from oracle import bab, core
+    layers = synth.make_network(CFG)
+    eps = synth.load_eps(CFG)
+    nodes, t = 0, 0.0
+    k = start
+    while t < seconds:
+        pr = synth.make_properties(CFG, layers, n=1, eps=eps, start=k)[0]
+        k += 1
+        t0 = time.perf_counter()
+        r = bab.verify(layers, pr.C, pr.d, pr.lo, pr.hi, max_nodes=12,
+                       hp=core.AdamHP(steps=ADAM_STEPS))
+        t += time.perf_counter() - t0
+        nodes += r.n_bounded
+    return {"value": nodes / t, "unit": "nodes/s", "cores": torch.get_num_threads(),
+            "kind": "oracle", "_nodes": nodes, "_seconds": t,
+            "sample": f"{k - start} properties of the same net and radius, first <=12 FIFO nodes "
+                      f"each (root bounding, DeepPoly pass, 20 Adam steps, ACS), {nodes} nodes "
+                      f"in {t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    per = []
+    total_nodes, total_t = 0, 0.0
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(max(1.0, args.cpu_seconds / max(1, args.steps)), start=100 * s)
+        if s >= args.warmup:
+            total_nodes += cb["_nodes"]
+            total_t += cb["_seconds"]
+            per.append(cb["_seconds"])
+    value = total_nodes / total_t
+    import torch
+    out = {"metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * total_t / max(1, args.steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD}, "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": "nodes/s", "kind": "oracle",
+                            "cores": torch.get_num_threads(),
+                            "sample": "per step: seeded properties, first <=12 FIFO nodes each"},
+           "e2e": {"value": value, "unit": "nodes/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

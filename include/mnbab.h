@@ -99,7 +99,19 @@ typedef struct {
   int32_t nodes_leaf;      /* open but nothing left to split */
   int32_t props_done;      /* properties with a final verdict after this step */
   int64_t rows_rebounded;  /* intermediate-bound rows back-substituted */
+  int64_t h2d_bytes;       /* host-to-device bytes copied by the step */
+  int64_t d2h_bytes;       /* device-to-host bytes copied by the step */
 } mnbab_step_stats;
+
+/* Per-kernel-class timing (CUDA events on the context's stream around every
+ * launch of the class) and the algorithmic work those launches did. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double ms;     /* summed launch durations */
+  double flops;  /* algorithmic floating-point operations (1 FMA = 2) */
+  double bytes;  /* algorithmic HBM bytes (each operand read or written once) */
+} mnbab_kernel_stat;
 
 /* One record per bounded node, in bounding order (for traces and tests). */
 typedef struct {
@@ -230,6 +242,15 @@ mnbab_status mnbab_get_verdict(const mnbab_ctx* ctx, const mnbab_prop* prop, int
 /* Copies up to max_recs trace records of the property's bounded nodes. */
 mnbab_status mnbab_get_trace(const mnbab_ctx* ctx, const mnbab_prop* prop, mnbab_trace_rec* recs,
                              int32_t max_recs, int32_t* n_out);
+
+/* enable = 1 clears the per-kernel statistics and starts timing every launch
+ * with CUDA events (adds a little launch overhead); enable = 0 stops. */
+mnbab_status mnbab_profile(mnbab_ctx* ctx, int32_t enable);
+
+/* Reads up to max_stats kernel-class statistics (synchronises the stream) and
+ * the number of kernels the context has launched since it was created. */
+mnbab_status mnbab_profile_read(mnbab_ctx* ctx, mnbab_kernel_stat* stats, int32_t max_stats,
+                                int32_t* n_out, int64_t* total_launches);
 
 /* Number of open nodes queued for the property. */
 mnbab_status mnbab_queue_size(const mnbab_ctx* ctx, const mnbab_prop* prop, int32_t* n_out);

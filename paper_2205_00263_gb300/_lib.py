@@ -44,7 +44,13 @@ class StepStats(C.Structure):
     _fields_ = [("nodes_bounded", C.c_int32), ("nodes_verified", C.c_int32),
                 ("nodes_falsified", C.c_int32), ("nodes_branched", C.c_int32),
                 ("nodes_leaf", C.c_int32), ("props_done", C.c_int32),
-                ("rows_rebounded", C.c_int64)]
+                ("rows_rebounded", C.c_int64), ("h2d_bytes", C.c_int64),
+                ("d2h_bytes", C.c_int64)]
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("ms", C.c_double),
+                ("flops", C.c_double), ("bytes", C.c_double)]
 
 
 class TraceRec(C.Structure):
@@ -82,6 +88,9 @@ SIGNATURES = {
     "mnbab_get_verdict": (status, [VP, VP, C.c_int32, IP, FP, FP]),
     "mnbab_get_trace": (status, [VP, VP, C.POINTER(TraceRec), C.c_int32, IP]),
     "mnbab_queue_size": (status, [VP, VP, IP]),
+    "mnbab_profile": (status, [VP, C.c_int32]),
+    "mnbab_profile_read": (status, [VP, C.POINTER(KernelStat), C.c_int32, IP,
+                                    C.POINTER(C.c_int64)]),
 }
 
 _lib = None

@@ -270,3 +270,19 @@ class Context:
         n = C.c_int32()
         self._ck(self.lib.mnbab_queue_size(self.h, prop.h, C.byref(n)))
         return n.value
+
+    # ---- profiling --------------------------------------------------------
+    def profile(self, enable: bool):
+        self._ck(self.lib.mnbab_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """({kernel class: {launches, ms, flops, bytes}}, total launches)."""
+        arr = (L.KernelStat * 16)()
+        n = C.c_int32()
+        tot = C.c_int64()
+        self._ck(self.lib.mnbab_profile_read(self.h, arr, 16, C.byref(n), C.byref(tot)))
+        out = {}
+        for i in range(n.value):
+            k = arr[i]
+            out[k.name.decode()] = dict(launches=k.launches, ms=k.ms, flops=k.flops, bytes=k.bytes)
+        return out, tot.value

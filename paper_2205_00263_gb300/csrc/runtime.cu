@@ -119,6 +119,14 @@ struct mnbab_ctx {
   PropDev* d_props = nullptr;
   int props_cap = 0;
   std::vector<std::pair<void*, size_t>> allocs;
+  // profiling: kernel-class timing with CUDA events, launch and copy counters
+  bool prof = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> ev_free;
+  int64_t launches = 0;
+  int64_t acc_n[16] = {0};
+  double acc_ms[16] = {0}, acc_flops[16] = {0}, acc_bytes[16] = {0};
+  int64_t h2d_bytes = 0, d2h_bytes = 0;
 };
 
 namespace {
@@ -143,17 +151,84 @@ T* dalloc_t(mnbab_ctx* c, size_t n) {
 
 template <typename T>
 void h2d(mnbab_ctx* c, T* dst, const T* src, size_t n) {
+  c->h2d_bytes += (int64_t)(n * sizeof(T));
   if (n) ck(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, c->st), "H2D");
 }
 
 template <typename T>
 void d2h(mnbab_ctx* c, T* dst, const T* src, size_t n) {
+  c->d2h_bytes += (int64_t)(n * sizeof(T));
   if (n) ck(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToHost, c->st), "D2H");
+}
+
+enum Cat {
+  C_BACKSUB_FC, C_BACKSUB_CONV, C_FWD_FC, C_FWD_CONV, C_INIT, C_REDUCE, C_GAMMA, C_ADAM, C_ACS,
+  C_BOOK, NCAT
+};
+const char* CAT_NAMES[NCAT] = {"backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm",
+                               "forward_conv",    "init_rows",              "reduce_lb",
+                               "gamma_terms",     "adam",                   "acs",
+                               "bookkeeping"};
+
+void resolve_prof(mnbab_ctx* c) {
+  for (auto& r : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.second.first, r.second.second) == cudaSuccess)
+      c->acc_ms[r.first] += ms;
+    c->ev_free.push_back(r.second.first);
+    c->ev_free.push_back(r.second.second);
+  }
+  c->pending.clear();
 }
 
 void sync(mnbab_ctx* c) {
   ck(cudaStreamSynchronize(c->st), "stream synchronize");
   ck(cudaGetLastError(), "kernel launch");
+  if (!c->pending.empty()) resolve_prof(c);
+}
+
+cudaEvent_t get_event(mnbab_ctx* c) {
+  if (c->ev_free.empty()) {
+    cudaEvent_t e;
+    ck(cudaEventCreate(&e), "cudaEventCreate");
+    return e;
+  }
+  cudaEvent_t e = c->ev_free.back();
+  c->ev_free.pop_back();
+  return e;
+}
+
+// Counts the launches of one kernel class and their algorithmic work; with
+// profiling on, brackets them with CUDA events on the context's stream.
+struct Scope {
+  mnbab_ctx* c;
+  int cat;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Scope(mnbab_ctx* c_, int cat_, double flops, double bytes, int nl = 1) : c(c_), cat(cat_) {
+    c->launches += nl;
+    c->acc_n[cat] += nl;
+    c->acc_flops[cat] += flops;
+    c->acc_bytes[cat] += bytes;
+    if (c->prof) {
+      if (c->pending.size() > 8192) sync(c);
+      a = get_event(c);
+      b = get_event(c);
+      cudaEventRecord(a, c->st);
+    }
+  }
+  ~Scope() {
+    if (a) {
+      cudaEventRecord(b, c->st);
+      c->pending.push_back({cat, {a, b}});
+    }
+  }
+};
+
+double layer_macs(const LayerDev& L) {
+  return L.kind == 1 ? (double)L.d_in * L.d_out : (double)L.co * L.ho * L.wo * L.ci * L.k * L.k;
+}
+double layer_wbytes(const LayerDev& L) {
+  return 4.0 * (L.kind == 1 ? (double)L.d_in * L.d_out : (double)L.co * L.ci * L.k * L.k);
 }
 
 // ---------------------------------------------------------------------------
@@ -242,16 +317,23 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
   e0.slot_base = 0;
   float* cur = n->LamA;
   float* nxt = n->LamB;
-  launch_init_rows(n->nd, t, rows, t - 1 >= 1 ? cur : nullptr, n->maxd, e0, c->st);
+  {
+    Scope sc(c, C_INIT, 0.0, 4.0 * rows.M * n->nd.d[t - 1]);
+    launch_init_rows(n->nd, t, rows, t - 1 >= 1 ? cur : nullptr, n->maxd, e0, c->st);
+  }
   int used = 1;
   for (int i = t - 1; i >= 1; --i) {
     Epi e = base_epi(n, rows.node);
     setup(e, i - 1);
     e.slot_base = used;
-    used += launch_backsub(n->nd.aff[i], rows.M, cur, n->maxd, i - 1 >= 1 ? nxt : nullptr,
-                           n->maxd, e, c->st);
+    const LayerDev& L = n->nd.aff[i];
+    Scope sc(c, L.kind == 1 ? C_BACKSUB_FC : C_BACKSUB_CONV, 2.0 * rows.M * layer_macs(L),
+             4.0 * rows.M * (L.d_out + (i > 1 ? L.d_in : 0)) + layer_wbytes(L));
+    used += launch_backsub(L, rows.M, cur, n->maxd, i - 1 >= 1 ? nxt : nullptr, n->maxd, e,
+                           c->st);
     std::swap(cur, nxt);
   }
+  Scope sc(c, C_REDUCE, 0.0, 4.0 * rows.M * used);
   launch_reduce_lb(rows.M, n->part, n->nslot, used,
                    (o.final_mode && o.has_gamma) ? n->gp0 : nullptr, n->lb, o.track, rows.node,
                    n->pool, n->X, n->d0, c->st);
@@ -275,8 +357,11 @@ int64_t rebound(mnbab_net* n, const std::vector<int>& slots) {
       const int nb = std::min((int)sel.size() - done, std::min(per, n->B));
       h2d(c, n->bslots, sel.data() + done, nb);
       ck(cudaMemsetAsync(n->counter, 0, sizeof(int), c->st), "memset");
-      launch_collect_rows(nb, n->bslots, n->pool, n->nd.off[t], n->nd.d[t], n->counter,
-                          n->row_node, n->row_j, n->row_sign, c->st);
+      {
+        Scope sc(c, C_BOOK, 0.0, 9.0 * nb * n->nd.d[t]);
+        launch_collect_rows(nb, n->bslots, n->pool, n->nd.off[t], n->nd.d[t], n->counter,
+                            n->row_node, n->row_j, n->row_sign, c->st);
+      }
       int M = 0;
       d2h(c, &M, n->counter, 1);
       sync(c);
@@ -286,6 +371,7 @@ int64_t rebound(mnbab_net* n, const std::vector<int>& slots) {
         RowsDev r{Mc, n->row_node + s0, n->row_j + s0, n->row_sign + s0};
         SweepOpts o;
         sweep(n, t, r, o);
+        Scope sc(c, C_BOOK, 0.0, 24.0 * Mc);
         launch_update_bounds(Mc / 2, r.node, r.j, n->lb, n->pool, n->nd.off[t], c->st);
       }
       done += nb;
@@ -331,17 +417,25 @@ void adjoint(mnbab_net* n, int M, bool has_gamma) {
     }
     e.part = nullptr;
     float* out = bufs[i & 1];
-    launch_forward(n->nd.aff[i], M, in, ld_in, out, n->maxd, e, c->st);
+    const LayerDev& L = n->nd.aff[i];
+    Scope sc(c, L.kind == 1 ? C_FWD_FC : C_FWD_CONV, 2.0 * M * layer_macs(L),
+             4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
+    launch_forward(L, M, in, ld_in, out, n->maxd, e, c->st);
     in = out;
     ld_in = n->maxd;
   }
-  if (has_gamma)
+  if (has_gamma) {
+    Scope sc(c, C_GAMMA, 0.0, 4.0 * M * c->EC);
     launch_gamma_grad(M, n->bslots, n->pool, c->d_props, n->nd, n->Gz, n->Hz, n->GG, c->st);
+  }
 }
 
 void run_optimize(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
   mnbab_ctx* c = n->ctx;
-  launch_zero_adam(M, n->bslots, n->pool, c->st);
+  {
+    Scope sc(c, C_BOOK, 0.0, 16.0 * M * (n->SD + c->EC));
+    launch_zero_adam(M, n->bslots, n->pool, c->st);
+  }
   SweepOpts o;
   o.final_mode = true;
   o.has_gamma = has_gamma;
@@ -349,13 +443,16 @@ void run_optimize(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
   o.track = true;
   double b1t = 1.0, b2t = 1.0;
   for (int step = 0; step <= a.steps; ++step) {
-    if (has_gamma)
+    if (has_gamma) {
+      Scope sc(c, C_GAMMA, 0.0, 4.0 * M * (c->EC + 2.0 * n->SD), 2);
       launch_gamma_proj(M, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+    }
     sweep(n, n->R + 1, obj_rows(n, M), o);
     if (step == a.steps) break;
     adjoint(n, M, has_gamma);
     b1t *= a.beta1;
     b2t *= a.beta2;
+    Scope sc(c, C_ADAM, 0.0, 4.0 * M * (2.0 * n->SD + c->EC) * 7.0);
     launch_adam(M, n->bslots, n->pool, c->d_props, n->SD, n->GA, n->GB, n->GG, a.lr_alpha,
                 a.lr_beta, a.lr_gamma, a.beta1, a.beta2, a.eps, (float)(1.0 - b1t),
                 (float)(1.0 - b2t), c->st);
@@ -373,10 +470,14 @@ void forward_rows(mnbab_net* n, int M, const float* x) {
     e.kind = EPI_FWD_RELU;
     e.part = nullptr;
     float* out = bufs[i & 1];
-    launch_forward(n->nd.aff[i], M, in, ld, out, n->maxd, e, c->st);
+    const LayerDev& L = n->nd.aff[i];
+    Scope sc(c, L.kind == 1 ? C_FWD_FC : C_FWD_CONV, 2.0 * M * layer_macs(L),
+             4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
+    launch_forward(L, M, in, ld, out, n->maxd, e, c->st);
     in = out;
     ld = n->maxd;
   }
+  Scope sc(c, C_BOOK, 2.0 * M * n->nd.d[n->R], 8.0 * M * n->nd.d[n->R]);
   launch_final_dot(M, n->bslots, n->pool, c->d_props, in, ld, n->nd.d[n->R], n->fout, c->st);
 }
 
@@ -472,7 +573,10 @@ mnbab_net* slots_of(mnbab_ctx* c, const mnbab_node_id* nodes, int nn, std::vecto
 }
 
 void gather_best(mnbab_net* n, int M, float* host_out) {
-  k_gather1<<<(M + 255) / 256, 256, 0, n->ctx->st>>>(M, n->bslots, n->pool.BEST, n->bestb);
+  {
+    Scope sc(n->ctx, C_BOOK, 0.0, 12.0 * M);
+    k_gather1<<<(M + 255) / 256, 256, 0, n->ctx->st>>>(M, n->bslots, n->pool.BEST, n->bestb);
+  }
   d2h(n->ctx, host_out, n->bestb, M);
 }
 
@@ -553,7 +657,11 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   n->kid_slots = dalloc_t<int>(c, 2 * B);
   n->kid_layer = dalloc_t<int>(c, B);
   n->kid_neuron = dalloc_t<int>(c, B);
-  ck(cudaMemsetAsync(P.GAM, 0, cap * EC * sizeof(float) + 16, c->st), "memset");
+  if (EC) {
+    ck(cudaMemsetAsync(P.GAM, 0, cap * EC * sizeof(float), c->st), "memset");
+    ck(cudaMemsetAsync(P.MG, 0, cap * EC * sizeof(float), c->st), "memset");
+    ck(cudaMemsetAsync(P.VG, 0, cap * EC * sizeof(float), c->st), "memset");
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -568,6 +676,11 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
                    const mnbab_adam& adam, mnbab_step_stats* st) {
   std::memset(st, 0, sizeof(*st));
   if (n_props <= 0) return;
+  const int64_t h2d0 = c->h2d_bytes, d2h0 = c->d2h_bytes;
+  struct Fin {
+    mnbab_ctx* c; mnbab_step_stats* st; int64_t a, b;
+    ~Fin() { st->h2d_bytes = c->h2d_bytes - a; st->d2h_bytes = c->d2h_bytes - b; }
+  } fin{c, st, h2d0, d2h0};
   mnbab_net* n = props[0]->net;
   for (int i = 0; i < n_props; ++i)
     if (props[i]->net != n) fail(MNBAB_E_INVALID_ARG, "properties of different networks");
@@ -593,7 +706,10 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
     st->rows_rebounded = rebound(n, slots);
     // 2. DeepPoly pass of the objective
     upload_batch(n, slots);
-    launch_set_best(M, n->bslots, n->pool, -INFINITY, c->st);
+    {
+      Scope sc(c, C_BOOK, 0.0, 8.0 * M);
+      launch_set_best(M, n->bslots, n->pool, -INFINITY, c->st);
+    }
     SweepOpts dp;
     dp.track = true;
     sweep(n, n->R + 1, obj_rows(n, M), dp);
@@ -615,11 +731,17 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
       const bool g = batch_has_gamma(n, oslots);
       run_optimize(n, Mo, g, adam);
       // 5. ACS at the final parameters (a' and gamma^T P of the last sweep)
-      launch_acs(Mo, n->bslots, n->pool, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0, n->acs_layer,
-                 n->acs_neuron, n->score, n->acs_fb, c->st);
+      {
+        Scope sc(c, C_ACS, 0.0, 4.0 * Mo * n->SD * (g ? 5.0 : 4.0));
+        launch_acs(Mo, n->bslots, n->pool, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0, n->acs_layer,
+                   n->acs_neuron, n->score, n->acs_fb, c->st);
+      }
       // 4. counterexample check at the best minimiser
-      k_gather_rows<<<Mo, 128, 0, c->st>>>(Mo, n->bslots, n->pool.BESTX, n->d0, n->Xb, n->d0,
-                                           n->d0);
+      {
+        Scope sc(c, C_BOOK, 0.0, 8.0 * Mo * n->d0);
+        k_gather_rows<<<Mo, 128, 0, c->st>>>(Mo, n->bslots, n->pool.BESTX, n->d0, n->Xb, n->d0,
+                                             n->d0);
+      }
       forward_rows(n, Mo, n->Xb);
       d2h(c, f32.data(), n->fout, Mo);
       d2h(c, acs_l.data(), n->acs_layer, Mo);
@@ -713,8 +835,11 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
       h2d(c, n->kid_slots, kidslots.data(), 2 * nb);
       h2d(c, n->kid_layer, lay.data(), nb);
       h2d(c, n->kid_neuron, neu.data(), nb);
-      launch_children(nb, n->kid_parent, n->kid_slots, n->kid_layer, n->kid_neuron, n->pool,
-                      n->nd, c->st);
+      {
+        Scope sc(c, C_BOOK, 0.0, 3.0 * nb * (17.0 * n->SD + 4.0 * c->EC));
+        launch_children(nb, n->kid_parent, n->kid_slots, n->kid_layer, n->kid_neuron, n->pool,
+                        n->nd, c->st);
+      }
       for (int b = 0; b < nb; ++b) {
         const Picked& pk = picked[branch_of[b].first];
         for (int k = 0; k < 2; ++k) {
@@ -809,6 +934,11 @@ void mnbab_destroy(mnbab_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->st);
+  for (auto& r : c->pending) {
+    cudaEventDestroy(r.second.first);
+    cudaEventDestroy(r.second.second);
+  }
+  for (auto e : c->ev_free) cudaEventDestroy(e);
   for (auto& a : c->allocs) cudaFree(a.first);
   for (auto* n : c->nets) delete n;
   for (auto* p : c->props) delete p;
@@ -965,8 +1095,11 @@ mnbab_status mnbab_set_property(mnbab_ctx* c, const mnbab_net* cnet, const float
   n->slot_prop[rs] = p->index;
   n->slot_row[rs] = 0;
   n->slot_split[rs] = 0;
-  launch_fill(n->pool.L + (size_t)rs * n->SD, n->SD, -INFINITY, c->st);
-  launch_fill(n->pool.U + (size_t)rs * n->SD, n->SD, INFINITY, c->st);
+  {
+    Scope sc(c, C_BOOK, 0.0, 8.0 * n->SD, 2);
+    launch_fill(n->pool.L + (size_t)rs * n->SD, n->SD, -INFINITY, c->st);
+    launch_fill(n->pool.U + (size_t)rs * n->SD, n->SD, INFINITY, c->st);
+  }
   ck(cudaMemsetAsync(n->pool.S + (size_t)rs * n->SD, 0, n->SD, c->st), "memset");
   int pi = p->index;
   h2d(c, n->pool.prop + rs, &pi, 1);
@@ -985,7 +1118,10 @@ mnbab_status mnbab_set_property(mnbab_ctx* c, const mnbab_net* cnet, const float
   if (n_rows > 2 * n->B) fail(MNBAB_E_INVALID_ARG, "too many property rows");
   int* tmp = n->kid_slots;  // scratch for the slot list
   h2d(c, tmp, slots.data(), n_rows);
-  launch_root_init(n_rows, tmp, rs, n->pool, c->st);
+  {
+    Scope sc(c, C_BOOK, 0.0, 25.0 * n_rows * n->SD);
+    launch_root_init(n_rows, tmp, rs, n->pool, c->st);
+  }
   for (int r = 0; r < n_rows; ++r) h2d(c, n->pool.row + slots[r], &rows[r], 1);
   sync(c);
   for (int r = 0; r < n_rows; ++r) {
@@ -1078,7 +1214,10 @@ mnbab_status mnbab_node_root(mnbab_ctx* c, mnbab_prop* p, int32_t row, mnbab_nod
   n->slot_row[s] = row;
   n->slot_split[s] = n->R;
   h2d(c, n->kid_slots, &s, 1);
-  launch_root_init(1, n->kid_slots, p->root_slot, n->pool, c->st);
+  {
+    Scope sc(c, C_BOOK, 0.0, 25.0 * n->SD);
+    launch_root_init(1, n->kid_slots, p->root_slot, n->pool, c->st);
+  }
   h2d(c, n->pool.row + s, &row, 1);
   sync(c);
   *out = ((int64_t)n->id << 32) | (int64_t)s;
@@ -1159,7 +1298,10 @@ mnbab_status mnbab_bound_batch(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t
   rebound(n, slots);
   upload_batch(n, slots);
   const bool g = batch_has_gamma(n, slots);
-  if (g) launch_gamma_proj(nn, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+  if (g) {
+    Scope sc(c, C_GAMMA, 0.0, 4.0 * nn * (c->EC + 2.0 * n->SD), 2);
+    launch_gamma_proj(nn, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+  }
   SweepOpts o;
   o.final_mode = true;
   o.has_gamma = g;
@@ -1196,7 +1338,10 @@ mnbab_status mnbab_bound_grad(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t 
   if (!lb_out || !grad_out) fail(MNBAB_E_INVALID_ARG, "null output");
   upload_batch(n, slots);
   const bool g = batch_has_gamma(n, slots);
-  if (g) launch_gamma_proj(nn, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+  if (g) {
+    Scope sc(c, C_GAMMA, 0.0, 4.0 * nn * (c->EC + 2.0 * n->SD), 2);
+    launch_gamma_proj(nn, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+  }
   SweepOpts o;
   o.final_mode = true;
   o.has_gamma = g;
@@ -1228,7 +1373,10 @@ mnbab_status mnbab_optimize(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t nn
   const mnbab_adam a = cfg ? *cfg : default_adam();
   if (a.steps < 0) fail(MNBAB_E_INVALID_ARG, "negative step count");
   upload_batch(n, slots);
-  launch_set_best(nn, n->bslots, n->pool, -INFINITY, c->st);
+  {
+    Scope sc(c, C_BOOK, 0.0, 8.0 * nn);
+    launch_set_best(nn, n->bslots, n->pool, -INFINITY, c->st);
+  }
   run_optimize(n, nn, batch_has_gamma(n, slots), a);
   gather_best(n, nn, best_lb_out);
   sync(c);
@@ -1243,14 +1391,20 @@ mnbab_status mnbab_score_branches(mnbab_ctx* c, const mnbab_node_id* nodes, int3
   if (!layer_out || !neuron_out) fail(MNBAB_E_INVALID_ARG, "null output");
   upload_batch(n, slots);
   const bool g = batch_has_gamma(n, slots);
-  if (g) launch_gamma_proj(nn, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+  if (g) {
+    Scope sc(c, C_GAMMA, 0.0, 4.0 * nn * (c->EC + 2.0 * n->SD), 2);
+    launch_gamma_proj(nn, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+  }
   SweepOpts o;
   o.final_mode = true;
   o.has_gamma = g;
   o.store = true;
   sweep(n, n->R + 1, obj_rows(n, nn), o);
-  launch_acs(nn, n->bslots, n->pool, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0, n->acs_layer,
-             n->acs_neuron, n->score, n->acs_fb, c->st);
+  {
+    Scope sc(c, C_ACS, 0.0, 4.0 * nn * n->SD * 5.0);
+    launch_acs(nn, n->bslots, n->pool, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0, n->acs_layer,
+               n->acs_neuron, n->score, n->acs_fb, c->st);
+  }
   d2h(c, layer_out, n->acs_layer, nn);
   d2h(c, neuron_out, n->acs_neuron, nn);
   if (score_out) d2h(c, score_out, n->score, nn);
@@ -1312,6 +1466,37 @@ mnbab_status mnbab_get_trace(const mnbab_ctx* cc, const mnbab_prop* p, mnbab_tra
   const int k = recs ? std::min(nt, std::max(0, (int)max_recs)) : 0;
   for (int i = 0; i < k; ++i) recs[i] = p->trace[i];
   *n_out = recs ? k : nt;
+  API_END(c)
+}
+
+mnbab_status mnbab_profile(mnbab_ctx* c, int32_t enable) {
+  API_BEGIN(c)
+  sync(c);
+  if (enable) {
+    for (int i = 0; i < 16; ++i) {
+      c->acc_n[i] = 0;
+      c->acc_ms[i] = c->acc_flops[i] = c->acc_bytes[i] = 0.0;
+    }
+  }
+  c->prof = enable != 0;
+  API_END(c)
+}
+
+mnbab_status mnbab_profile_read(mnbab_ctx* c, mnbab_kernel_stat* stats, int32_t max_stats,
+                                int32_t* n_out, int64_t* total_launches) {
+  API_BEGIN(c)
+  sync(c);
+  const int k = stats ? std::min((int)NCAT, std::max(0, (int)max_stats)) : 0;
+  for (int i = 0; i < k; ++i) {
+    std::memset(stats[i].name, 0, sizeof(stats[i].name));
+    std::strncpy(stats[i].name, CAT_NAMES[i], sizeof(stats[i].name) - 1);
+    stats[i].launches = c->acc_n[i];
+    stats[i].ms = c->acc_ms[i];
+    stats[i].flops = c->acc_flops[i];
+    stats[i].bytes = c->acc_bytes[i];
+  }
+  if (n_out) *n_out = stats ? k : (int)NCAT;
+  if (total_launches) *total_launches = c->launches;
   API_END(c)
 }
 

@@ -182,12 +182,12 @@ class Property:
 
 
 def make_properties(cfg: int, layers: list[dict] | None = None, n: int | None = None,
-                    eps: float | None = None) -> list[Property]:
+                    eps: float | None = None, start: int = 0) -> list[Property]:
     spec = CONFIGS[cfg]
     layers = layers if layers is not None else make_network(cfg)
     n = spec["n_props"] if n is None else n
     props = []
-    for p in range(n):
+    for p in range(start, start + n):
         x0 = make_image(spec["seed"] + 1000 + p, spec["in_shape"]).reshape(-1)
         y = net_forward(layers, x0)
         t = int(np.argmax(y))
