@@ -403,6 +403,11 @@ class AdamHP:
     b1: float = 0.9
     b2: float = 0.999
     eps: float = 1e-8
+    # gradient components below grad_floor * (largest |component| of the node)
+    # count as zero: constraints that are tight at the relaxed point have
+    # gradients at rounding level, and Adam's per-component normalisation would
+    # turn that noise into full steps of random sign
+    grad_floor: float = 1e-5
 
 
 def bound_and_grad(net, node, alpha, beta, gamma, dense_mnc, lo, hi):
@@ -443,6 +448,11 @@ def optimize(net, node: Node, dense_mnc, lo, hi, hp: AdamHP):
         if step == hp.steps:
             break
         t = step + 1
+        gmax = max([float(G[i].abs().max()) for G in (ga, gb, gg) for i in G if G[i].numel()] + [0.0])
+        floor = hp.grad_floor * gmax
+        for G in (ga, gb, gg):
+            for i in G:
+                G[i] = torch.where(G[i].abs() <= floor, torch.zeros_like(G[i]), G[i])
         for grp, P, G in (("a", alpha, ga), ("b", beta, gb), ("g", gamma, gg)):
             for i in P:
                 m, v = state[(grp, i)]
