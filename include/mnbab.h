@@ -89,6 +89,11 @@ typedef struct {
   int32_t steps;   /* gradient steps; the bound is evaluated steps + 1 times */
   float lr_alpha, lr_beta, lr_gamma;
   float beta1, beta2, eps;
+  /* gradient components with |g| <= grad_floor * max_j |g_j| (over all of a
+   * node's parameters) count as zero; default 1e-5.  Constraints tight at the
+   * relaxed point have gradients at rounding level, which Adam's
+   * per-component normalisation would otherwise turn into full steps. */
+  float grad_floor;
 } mnbab_adam;
 
 typedef struct {

@@ -635,23 +635,47 @@ __device__ __forceinline__ void adam1(float& th, float& mo, float& ve, float g, 
   th = th + lr * mh / (sqrtf(vh) + eps);
 }
 
+// largest |gradient component| of each row over alpha, beta and gamma
+__global__ void k_grad_max(int SD, int EC, const int* row_node, const PoolDev pool,
+                           const PropDev* props, const float* GA, const float* GB,
+                           const float* GG, float* gmax) {
+  const int m = blockIdx.x;
+  const int E = props[pool.prop[row_node[m]]].E;
+  float mx = 0.f;
+  for (int i = threadIdx.x; i < SD; i += blockDim.x)
+    mx = fmaxf(mx, fmaxf(fabsf(GA[(size_t)m * SD + i]), fabsf(GB[(size_t)m * SD + i])));
+  for (int e = threadIdx.x; e < E; e += blockDim.x) mx = fmaxf(mx, fabsf(GG[(size_t)m * EC + e]));
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ float sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = fmaxf(r, sh[i]);
+    gmax[m] = r;
+  }
+}
+
 __global__ void k_adam(int M, const int* row_node, PoolDev pool, const PropDev* props, int SD,
-                       const float* GA, const float* GB, const float* GG, float lr_a, float lr_b,
-                       float lr_g, float b1, float b2, float eps, float bc1, float bc2) {
+                       const float* GA, const float* GB, const float* GG, const float* gmax,
+                       float floor, float lr_a, float lr_b, float lr_g, float b1, float b2,
+                       float eps, float bc1, float bc2) {
   const int m = blockIdx.y;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = row_node[m];
+  const float thr = floor * gmax[m];
+  auto dz = [thr](float g) { return fabsf(g) <= thr ? 0.f : g; };
   if (idx < SD) {
     const size_t q = (size_t)n * SD + idx;
     float th = pool.ALPHA[q], mo = pool.MA[q], ve = pool.VA[q];
-    adam1(th, mo, ve, GA[(size_t)m * SD + idx], lr_a, b1, b2, eps, bc1, bc2);
+    adam1(th, mo, ve, dz(GA[(size_t)m * SD + idx]), lr_a, b1, b2, eps, bc1, bc2);
     pool.ALPHA[q] = fminf(fmaxf(th, 0.f), 1.f);
     pool.MA[q] = mo; pool.VA[q] = ve;
   } else if (idx < 2 * SD) {
     const int f = idx - SD;
     const size_t q = (size_t)n * SD + f;
     float th = pool.BETA[q], mo = pool.MB[q], ve = pool.VB[q];
-    adam1(th, mo, ve, GB[(size_t)m * SD + f], lr_b, b1, b2, eps, bc1, bc2);
+    adam1(th, mo, ve, dz(GB[(size_t)m * SD + f]), lr_b, b1, b2, eps, bc1, bc2);
     pool.BETA[q] = fmaxf(th, 0.f);
     pool.MB[q] = mo; pool.VB[q] = ve;
   } else {
@@ -659,21 +683,22 @@ __global__ void k_adam(int M, const int* row_node, PoolDev pool, const PropDev* 
     if (e >= props[pool.prop[n]].E) return;
     const size_t q = (size_t)n * pool.EC + e;
     float th = pool.GAM[q], mo = pool.MG[q], ve = pool.VG[q];
-    adam1(th, mo, ve, GG[(size_t)m * pool.EC + e], lr_g, b1, b2, eps, bc1, bc2);
+    adam1(th, mo, ve, dz(GG[(size_t)m * pool.EC + e]), lr_g, b1, b2, eps, bc1, bc2);
     pool.GAM[q] = fmaxf(th, 0.f);
     pool.MG[q] = mo; pool.VG[q] = ve;
   }
 }
 
 void launch_adam(int M, const int* row_node, PoolDev pool, const PropDev* props, int SD,
-                 const float* GA, const float* GB, const float* GG, float lr_a, float lr_b,
-                 float lr_g, float b1, float b2, float eps, float bc1, float bc2,
-                 cudaStream_t st) {
+                 const float* GA, const float* GB, const float* GG, float* gmax, float floor,
+                 float lr_a, float lr_b, float lr_g, float b1, float b2, float eps, float bc1,
+                 float bc2, cudaStream_t st) {
   if (M <= 0) return;
+  k_grad_max<<<M, 256, 0, st>>>(SD, pool.EC, row_node, pool, props, GA, GB, GG, gmax);
   const int tot = 2 * SD + pool.EC;
   dim3 grid((tot + 255) / 256, M);
-  k_adam<<<grid, 256, 0, st>>>(M, row_node, pool, props, SD, GA, GB, GG, lr_a, lr_b, lr_g, b1, b2,
-                               eps, bc1, bc2);
+  k_adam<<<grid, 256, 0, st>>>(M, row_node, pool, props, SD, GA, GB, GG, gmax, floor, lr_a, lr_b,
+                               lr_g, b1, b2, eps, bc1, bc2);
 }
 
 __global__ void k_zero_adam(const int* row_node, PoolDev pool) {

@@ -78,7 +78,7 @@ struct mnbab_net {
   size_t rows_cap = 0;
   float *AP = nullptr, *GA = nullptr, *GB = nullptr, *GP = nullptr, *GPh = nullptr;
   float *Gz = nullptr, *Hz = nullptr, *X = nullptr, *Xb = nullptr, *GG = nullptr, *gp0 = nullptr;
-  float *fout = nullptr, *score = nullptr, *bestb = nullptr;
+  float *fout = nullptr, *score = nullptr, *bestb = nullptr, *gmax = nullptr;
   int *bslots = nullptr, *brows = nullptr, *acs_layer = nullptr, *acs_neuron = nullptr,
       *acs_fb = nullptr, *kid_parent = nullptr, *kid_slots = nullptr, *kid_layer = nullptr,
       *kid_neuron = nullptr;
@@ -452,8 +452,9 @@ void run_optimize(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
     adjoint(n, M, has_gamma);
     b1t *= a.beta1;
     b2t *= a.beta2;
-    Scope sc(c, C_ADAM, 0.0, 4.0 * M * (2.0 * n->SD + c->EC) * 7.0);
-    launch_adam(M, n->bslots, n->pool, c->d_props, n->SD, n->GA, n->GB, n->GG, a.lr_alpha,
+    Scope sc(c, C_ADAM, 0.0, 4.0 * M * (2.0 * n->SD + c->EC) * 8.0, 2);
+    launch_adam(M, n->bslots, n->pool, c->d_props, n->SD, n->GA, n->GB, n->GG, n->gmax,
+                a.grad_floor, a.lr_alpha,
                 a.lr_beta, a.lr_gamma, a.beta1, a.beta2, a.eps, (float)(1.0 - b1t),
                 (float)(1.0 - b2t), c->st);
   }
@@ -544,6 +545,7 @@ mnbab_adam default_adam() {
   a.beta1 = 0.9f;
   a.beta2 = 0.999f;
   a.eps = 1e-8f;
+  a.grad_floor = 1e-5f;
   return a;
 }
 
@@ -648,6 +650,7 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   n->fout = dalloc_t<float>(c, B);
   n->score = dalloc_t<float>(c, B);
   n->bestb = dalloc_t<float>(c, B);
+  n->gmax = dalloc_t<float>(c, B);
   n->bslots = dalloc_t<int>(c, B);
   n->brows = dalloc_t<int>(c, B);
   n->acs_layer = dalloc_t<int>(c, B);

@@ -170,14 +170,9 @@ def test_optimized_bound_matches_oracle(Context):
             onodes.append(on)
             gids.append(gid)
         best = ctx.optimize(gids, steps=20)
-        n_ok = 0
         for k, on in enumerate(onodes):
             ref, *_ = core.optimize(net, on, dense, lo_t, hi_t, core.AdamHP())
-            ok = abs(best[k] - ref) <= TOL * (1 + abs(ref))
-            n_ok += ok
-            # never worse than the fixed-parameter start by more than the tolerance
-            assert abs(best[k] - ref) <= 5e-3 * (1 + abs(ref)), (k, best[k], ref)
-        assert n_ok >= len(onodes) - 1, n_ok
+            _assert_close(best[k], ref, f"node {k} optimised bound")
 
 
 def test_acs_choice_matches_oracle(Context):
@@ -224,9 +219,9 @@ def _compare_trace(gtr, ores, max_cmp=None):
         g, o = gtr[k], ores.nodes[k]
         assert g["seq"] == o.node_id and g["row"] == o.row, (k, g, o)
         band = TOL * (1 + abs(o.lb))
-        assert abs(g["lb"] - o.lb) <= max(band, 5e-3 * (1 + abs(o.lb))), (k, g["lb"], o.lb)
-        if abs(o.lb) <= 5e-3 * (1 + abs(o.lb)):
-            flagged += 1
+        assert abs(g["lb"] - o.lb) <= band, (k, g["lb"], o.lb)
+        if abs(o.lb) <= band:
+            flagged += 1   # margin inside the tolerance band: verdict may differ
             return k, flagged
         assert g["verdict"] == o.verdict, (k, g, o)
         gs = (g["split_layer"], g["split_neuron"]) if g["split_layer"] > 0 else None
