@@ -358,6 +358,7 @@ def run_ours(args):
             "verdicts_in_timed_steps": {"verified": vd[1], "falsified": vd[-1], "unknown": vd[0]},
             "kernel_breakdown_ms": {k: round(v["ms"], 3) for k, v in stats.items()},
             "nodes_timed": tot_nodes,
+            "launches_before_timed": int(launches0),
         }
         print(json.dumps(out), flush=True)
     ctx.close()
