@@ -260,6 +260,52 @@ mnbab_status mnbab_profile_read(mnbab_ctx* ctx, mnbab_kernel_stat* stats, int32_
 /* Number of open nodes queued for the property. */
 mnbab_status mnbab_queue_size(const mnbab_ctx* ctx, const mnbab_prop* prop, int32_t* n_out);
 
+/* ---- allocation-free variant ----------------------------------------------- */
+/* Size of the device scratch array that mnbab_deeppoly_fc_noalloc uses. */
+#define MNBAB_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* DeepPoly lower bounds of query rows of a fully connected ReLU network, for
+ * callers that cannot allocate device memory (code running inside another
+ * framework's memory pool or allocator hooks, code that must not allocate
+ * while a stream capture is active, hosts whose device memory is partitioned
+ * up front).  The paper has no counterpart: this is a deployment variant of
+ * the back-substitution sweep of mnbab_deeppoly_batch, with every scratch
+ * buffer taken from a static device array of MNBAB_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) that each GPU loading the library holds until the process exits.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Arguments (all arrays are DEVICE pointers owned by the caller, FP32,
+ * row-major, except dims, W and b, which are host arrays):
+ *   n_affine    affine layers in the chain affine, ReLU, ..., affine (>= 1);
+ *   dims        host [n_affine]: dims[0] input width, dims[i] width of the
+ *               ReLU layer after hidden affine layer i (i = 1..n_affine-1);
+ *   W, b        host arrays of n_affine - 1 device pointers: hidden layer i
+ *               has W[i-1] [dims[i]][dims[i-1]] and b[i-1] [dims[i]];
+ *   x_lo, x_hi  input box [dims[0]];
+ *   l, u        pre-activation bounds of the ReLU layers, concatenated
+ *               [dims[1] + ... + dims[n_affine-1]];
+ *   Wf, bf      the query rows on the last ReLU layer's output (a property
+ *               folded into the last affine layer): Wf [n_rows][dims[n_affine-1]]
+ *               (dims[0] when n_affine == 1), bf [n_rows];
+ *   lb_out      [n_rows] lower bounds, written on `stream`;
+ *   stream      cudaStream_t (NULL = the legacy default stream);
+ *   err, err_len  optional buffer for a message.
+ * Returns MNBAB_E_BUDGET (with a message) when n_rows rows need more scratch
+ * than the static array holds (about 4 * n_rows * (2 * max_width + 20)
+ * bytes); split the rows over several calls then.  The first call on a device
+ * looks up the array's device address with that device current (done once per
+ * device); make that first call before any stream capture.  Each device has
+ * its own copy of the array; every call on a device uses that copy, which keeps
+ * the last call's contents.  Two calls whose GPU work overlaps on one device
+ * (for example on two streams) race on it: issue them one after another on one
+ * stream. */
+mnbab_status mnbab_deeppoly_fc_noalloc(int32_t n_affine, const int32_t* dims,
+                                       const float* const* W, const float* const* b,
+                                       const float* x_lo, const float* x_hi, const float* l,
+                                       const float* u, const float* Wf, const float* bf,
+                                       int32_t n_rows, float* lb_out, void* stream, char* err,
+                                       size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,9 @@ SIGNATURES = {
     "mnbab_get_trace": (status, [VP, VP, C.POINTER(TraceRec), C.c_int32, IP]),
     "mnbab_queue_size": (status, [VP, VP, IP]),
     "mnbab_profile": (status, [VP, C.c_int32]),
+    "mnbab_deeppoly_fc_noalloc": (status, [C.c_int32, IP, C.POINTER(VP), C.POINTER(VP), VP, VP,
+                                           VP, VP, VP, VP, C.c_int32, VP, VP, C.c_char_p,
+                                           C.c_size_t]),
     "mnbab_profile_read": (status, [VP, C.POINTER(KernelStat), C.c_int32, IP,
                                     C.POINTER(C.c_int64)]),
 }
