@@ -127,6 +127,7 @@ __global__ void k_init_rows(NetDev net, int t, RowsDev rows, float* out, int ld,
   const int j = rows.j[m];
   const float sg = rows.sign ? rows.sign[m] : 1.f;
   const int width = net.d[t - 1];
+  const bool zero_passes = e.kind == EPI_RELU && !e.final_mode && !e.GP && !e.GPh && !e.AP;
   float c0 = 0.f;
   float part = 0.f;
   if (t == net.R + 1) {
@@ -156,11 +157,18 @@ __global__ void k_init_rows(NetDev net, int t, RowsDev rows, float* out, int ld,
       for (int col = threadIdx.x; col < width; col += blockDim.x) {
         const int ci = col / ihw, ih = (col % ihw) / L.wi, iw = col % L.wi;
         const int kh = ih - h0, kw = iw - w0;
-        float a = 0.f;
-        if (kh >= 0 && kh < L.k && kw >= 0 && kw < L.k)
-          a = sg * L.W[(((size_t)co * L.ci + ci) * L.k + kh) * L.k + kw];
-        const float o = epi_apply(e, m, col, a, part);
-        if (out) out[(size_t)m * ld + col] = o;
+        if (kh >= 0 && kh < L.k && kw >= 0 && kw < L.k) {
+          const float a = sg * L.W[(((size_t)co * L.ci + ci) * L.k + kh) * L.k + kw];
+          const float o = epi_apply(e, m, col, a, part);
+          if (out) out[(size_t)m * ld + col] = o;
+        } else if (zero_passes) {
+          // outside the receptive field a = 0 and, without beta or gamma terms,
+          // the ReLU step maps it to 0 with no offset contribution
+          if (out) out[(size_t)m * ld + col] = 0.f;
+        } else {
+          const float o = epi_apply(e, m, col, 0.f, part);
+          if (out) out[(size_t)m * ld + col] = o;
+        }
       }
     }
   }
@@ -177,57 +185,60 @@ void launch_init_rows(const NetDev& net, int t, const RowsDev& rows, float* out,
 // ---------------------------------------------------------------------------
 // dense GEMM C = A B (+ bias) with a fused epilogue; SIMT FP32, 64x64x16 tiles
 // ---------------------------------------------------------------------------
-constexpr int GBM = 64, GBN = 64, GBK = 16;
+constexpr int GBK = 16;
 
+// BM x BN tile, 256 threads as 16 x 16, each thread (BM/16) x (BN/16) outputs.
+template <int BM, int BN>
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* __restrict__ A,
                                               int lda, const float* __restrict__ B, int ldb,
                                               const float* __restrict__ bias, int bias_div,
                                               float* C, int ldc, Epi e) {
-  __shared__ float As[GBK][GBM + 4];
-  __shared__ float Bs[GBK][GBN + 4];
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ float As[GBK][BM + 4];
+  __shared__ float Bs[GBK][BN + 4];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-  float acc[4][4];
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  float acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
   for (int k0 = 0; k0 < K; k0 += GBK) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = (tid >> 4) + 16 * i, c = tid & 15;
-      const int gm = m0 + r, gk = k0 + c;
-      As[c][r] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.f;
+    for (int q = tid; q < BM * GBK; q += 256) {
+      const int r = q >> 4, cc = q & 15;
+      const int gm = m0 + r, gk = k0 + cc;
+      As[cc][r] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.f;
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = (tid >> 6) + 4 * i, c = tid & 63;
-      const int gk = k0 + r, gn = n0 + c;
-      Bs[r][c] = (gk < K && gn < N) ? B[(size_t)gk * ldb + gn] : 0.f;
+    for (int q = tid; q < BN * GBK; q += 256) {
+      const int r = q / BN, cc = q % BN;
+      const int gk = k0 + r, gn = n0 + cc;
+      Bs[r][cc] = (gk < K && gn < N) ? B[(size_t)gk * ldb + gn] : 0.f;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GBK; ++kk) {
-      float a[4], b[4];
+      float a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
-  float part[4] = {0.f, 0.f, 0.f, 0.f};
+  float part[TM];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TM; ++i) part[i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
     const int m = m0 + ty + 16 * i;
     if (m >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= N) continue;
       float v = acc[i][j];
@@ -238,13 +249,28 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* 
   }
   if (epi_has_part(e)) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TM; ++i) {
       float p = part[i];
       for (int o = 8; o; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o, 16);
       const int m = m0 + ty + 16 * i;
       if (tx == 0 && m < M) e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = p;
     }
   }
+}
+
+// 64 x 64 tiles unless that grid would leave most of the 152 SMs idle.
+static int gemm_launch(int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                       const float* bias, int bias_div, float* C, int ldc, const Epi& e,
+                       cudaStream_t st) {
+  const long big = (long)((N + 63) / 64) * ((M + 63) / 64);
+  if (big >= 2 * 152) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    k_gemm<64, 64><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e);
+    return grid.x;
+  }
+  dim3 grid((N + 31) / 32, (M + 31) / 32);
+  k_gemm<32, 32><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e);
+  return grid.x;
 }
 
 // ---------------------------------------------------------------------------
@@ -336,11 +362,13 @@ __global__ void __launch_bounds__(128) k_conv_fwd(int M, const float* __restrict
   const int nW = L.co * L.ci * L.k * L.k;
   for (int i = threadIdx.x; i < nW; i += blockDim.x) Ws[i] = L.W[i];
   __syncthreads();
-  const int m = blockIdx.y;
+  // rows_per: rows sharing one CTA (output planes smaller than the CTA)
   const int Pout = L.ho * L.wo;
-  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rows_per = Pout >= (int)blockDim.x ? 1 : (int)blockDim.x / Pout;
+  const int m = rows_per == 1 ? (int)blockIdx.y : (int)blockIdx.y * rows_per + (int)threadIdx.x / Pout;
+  const int pos = rows_per == 1 ? (int)(blockIdx.x * blockDim.x + threadIdx.x) : (int)threadIdx.x % Pout;
   float part = 0.f;
-  if (pos < Pout) {
+  if (pos < Pout && m < M && (rows_per == 1 || (int)threadIdx.x < rows_per * Pout)) {
     const int oh = pos / L.wo, ow = pos % L.wo;
     const float* x = in + (size_t)m * ld_in;
     const int kk = L.k * L.k;
@@ -374,7 +402,9 @@ __global__ void __launch_bounds__(128) k_conv_fwd(int M, const float* __restrict
       }
     }
   }
-  if (epi_has_part(e)) {
+  // forward epilogues (adjoint, ReLU) produce no offset partials; the partial
+  // slot layout below assumes one row per CTA
+  if (epi_has_part(e) && rows_per == 1) {
     const float tot = block_sum(part);
     if (threadIdx.x == 0) e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = tot;
   }
@@ -386,7 +416,7 @@ static void set_smem(F f, int bytes) {
 }
 
 int backsub_slots(const LayerDev& L) {
-  if (L.kind == 1) return (L.d_in + GBN - 1) / GBN;
+  if (L.kind == 1) return (L.d_in + 31) / 32;  // upper bound over the tile shapes
   return (L.hi * L.wi + 127) / 128;
 }
 
@@ -395,10 +425,7 @@ int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* 
   if (M <= 0) return backsub_slots(L);
   if (L.kind == 1) {
     // Lambda [M][d_out] x W [d_out][d_in]
-    dim3 grid((L.d_in + GBN - 1) / GBN, (M + GBM - 1) / GBM);
-    k_gemm<<<grid, 256, 0, st>>>(M, L.d_in, L.d_out, in, ld_in, L.W, L.d_in, nullptr, 1, out,
-                                 ld_out, e);
-    return grid.x;
+    return gemm_launch(M, L.d_in, L.d_out, in, ld_in, L.W, L.d_in, nullptr, 1, out, ld_out, e, st);
   }
   const int smem = L.co * L.ci * L.k * L.k * 4;
   dim3 grid((L.hi * L.wi + 127) / 128, M);
@@ -422,13 +449,13 @@ void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float*
                     const Epi& e, cudaStream_t st) {
   if (M <= 0) return;
   if (L.kind == 1) {
-    dim3 grid((L.d_out + GBN - 1) / GBN, (M + GBM - 1) / GBM);
-    k_gemm<<<grid, 256, 0, st>>>(M, L.d_out, L.d_in, in, ld_in, L.Wt, L.d_out, L.b, 1, out,
-                                 ld_out, e);
+    gemm_launch(M, L.d_out, L.d_in, in, ld_in, L.Wt, L.d_out, L.b, 1, out, ld_out, e, st);
     return;
   }
   const int smem = L.co * L.ci * L.k * L.k * 4;
-  dim3 grid((L.ho * L.wo + 127) / 128, M);
+  const int Pout = L.ho * L.wo;
+  const int rows_per = Pout >= 128 ? 1 : 128 / Pout;
+  dim3 grid(rows_per == 1 ? (Pout + 127) / 128 : 1, (M + rows_per - 1) / rows_per);
   if (L.co <= 16) {
     set_smem(k_conv_fwd<16>, smem);
     k_conv_fwd<16><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
@@ -859,10 +886,11 @@ void launch_children(int nb, const int* parents, const int* kids, const int* lay
   k_children<<<grid, 256, 0, st>>>(parents, kids, layer, neuron, pool, net);
 }
 
-// Root nodes from a property's root-bound slot: DeepPoly slopes
+// Root nodes from their property's root-bound slot: DeepPoly slopes
 // (alpha = 1 if u >= -l else 0), beta = gamma = 0, no splits.
-__global__ void k_root_init(const int* slots, int src, PoolDev pool) {
+__global__ void k_root_init(const int* slots, const int* srcs, const int* rows, PoolDev pool) {
   const int dst = slots[blockIdx.y];
+  const int src = srcs[blockIdx.y];
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < pool.SD) {
     const size_t qs = (size_t)src * pool.SD + idx, qd = (size_t)dst * pool.SD + idx;
@@ -873,13 +901,17 @@ __global__ void k_root_init(const int* slots, int src, PoolDev pool) {
   } else if (idx < pool.SD + pool.EC) {
     pool.GAM[(size_t)dst * pool.EC + idx - pool.SD] = 0.f;
   }
-  if (idx == 0) pool.prop[dst] = pool.prop[src];
+  if (idx == 0) {
+    pool.prop[dst] = pool.prop[src];
+    pool.row[dst] = rows[blockIdx.y];
+  }
 }
 
-void launch_root_init(int nb, const int* slots, int src_slot, PoolDev pool, cudaStream_t st) {
+void launch_root_init(int nb, const int* slots, const int* srcs, const int* rows, PoolDev pool,
+                      cudaStream_t st) {
   if (nb <= 0) return;
   dim3 grid((pool.SD + pool.EC + 255) / 256, nb);
-  k_root_init<<<grid, 256, 0, st>>>(slots, src_slot, pool);
+  k_root_init<<<grid, 256, 0, st>>>(slots, srcs, rows, pool);
 }
 
 // f_r(z_R) through the property's folded last layer, one warp per row.

@@ -137,7 +137,9 @@ void launch_acs(int M, const int* row_node, PoolDev pool, const NetDev& net, con
                 float* out_score, int* out_fallback, cudaStream_t st);
 void launch_children(int nb, const int* parents, const int* kids, const int* layer,
                      const int* neuron, PoolDev pool, const NetDev& net, cudaStream_t st);
-void launch_root_init(int nb, const int* slots, int src_slot, PoolDev pool, cudaStream_t st);
+// Root nodes: slots[i] initialised from root-bound slot srcs[i] for row rows[i].
+void launch_root_init(int nb, const int* slots, const int* srcs, const int* rows, PoolDev pool,
+                      cudaStream_t st);
 void launch_final_dot(int M, const int* row_node, PoolDev pool, const PropDev* props,
                       const float* z, int ld, int dR, float* f, cudaStream_t st);
 void launch_fill(float* p, size_t n, float v, cudaStream_t st);

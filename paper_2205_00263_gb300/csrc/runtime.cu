@@ -76,6 +76,7 @@ struct mnbab_net {
   int *row_node = nullptr, *row_j = nullptr, *counter = nullptr;
   float* row_sign = nullptr;
   size_t rows_cap = 0;
+  int *rb_nodes = nullptr, *ri_dst = nullptr, *ri_src = nullptr, *ri_row = nullptr;
   float *AP = nullptr, *GA = nullptr, *GB = nullptr, *GP = nullptr, *GPh = nullptr;
   float *Gz = nullptr, *Hz = nullptr, *X = nullptr, *Xb = nullptr, *GG = nullptr, *gp0 = nullptr;
   float *fout = nullptr, *score = nullptr, *bestb = nullptr, *gmax = nullptr;
@@ -105,6 +106,8 @@ struct mnbab_prop {
   int cex_row = -1;
   std::vector<mnbab_trace_rec> trace;
   int mnc_set[MNBAB_MAXR + 1] = {0};
+  bool root_pending = false;         // root bounds not computed yet
+  std::vector<int> root_row_slots;   // its row root nodes, initialised with the bounds
 };
 
 struct mnbab_ctx {
@@ -340,44 +343,56 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
 }
 
 // Re-bounds ReLU layers t > split layer of each node (Sec. 3.2, enforcing
-// splits); rows are the node's unstable unsplit neurons, both sides.
+// splits); rows are the node's unstable unsplit neurons, both sides.  The rows
+// of every layer are collected up front (a layer's row set depends only on its
+// own current bounds), so a pass costs one host synchronisation.
 int64_t rebound(mnbab_net* n, const std::vector<int>& slots) {
   mnbab_ctx* c = n->ctx;
+  const int R = n->R;
   int64_t total = 0;
   std::vector<int> sel;
-  for (int t = 1; t <= n->R; ++t) {
-    sel.clear();
-    for (int s : slots)
-      if (n->slot_split[s] < t) sel.push_back(s);
-    if (sel.empty()) continue;
-    int done = 0;
-    while (done < (int)sel.size()) {
-      // nodes per collection pass bounded by the rows capacity
-      const int per = std::max(1, (int)(n->rows_cap / (2 * (size_t)n->nd.d[t])));
-      const int nb = std::min((int)sel.size() - done, std::min(per, n->B));
-      h2d(c, n->bslots, sel.data() + done, nb);
-      ck(cudaMemsetAsync(n->counter, 0, sizeof(int), c->st), "memset");
-      {
-        Scope sc(c, C_BOOK, 0.0, 9.0 * nb * n->nd.d[t]);
-        launch_collect_rows(nb, n->bslots, n->pool, n->nd.off[t], n->nd.d[t], n->counter,
-                            n->row_node, n->row_j, n->row_sign, c->st);
-      }
-      int M = 0;
-      d2h(c, &M, n->counter, 1);
-      sync(c);
-      total += M;
-      for (int s0 = 0; s0 < M; s0 += n->chunk) {
-        const int Mc = std::min(n->chunk, M - s0);
-        RowsDev r{Mc, n->row_node + s0, n->row_j + s0, n->row_sign + s0};
-        SweepOpts o;
-        sweep(n, t, r, o);
+  for (int s : slots)
+    if (n->slot_split[s] < R) sel.push_back(s);
+  const int per = std::max(1, std::min(n->B, (int)(n->rows_cap / (2 * (size_t)n->SD))));
+  std::vector<int> lay;
+  for (size_t done = 0; done < sel.size(); done += per) {
+    const int nb = (int)std::min(sel.size() - done, (size_t)per);
+    int cnt[MNBAB_MAXR + 2] = {0};
+    size_t region[MNBAB_MAXR + 2] = {0};
+    size_t at = 0;
+    ck(cudaMemsetAsync(n->counter, 0, (MNBAB_MAXR + 2) * sizeof(int), c->st), "memset");
+    for (int t = 1; t <= R; ++t) {
+      lay.clear();
+      for (int k = 0; k < nb; ++k)
+        if (n->slot_split[sel[done + k]] < t) lay.push_back(sel[done + k]);
+      region[t] = at;
+      cnt[t] = (int)lay.size();
+      if (lay.empty()) continue;
+      h2d(c, n->rb_nodes + (size_t)t * n->B, lay.data(), lay.size());
+      Scope sc(c, C_BOOK, 0.0, 9.0 * lay.size() * n->nd.d[t]);
+      launch_collect_rows((int)lay.size(), n->rb_nodes + (size_t)t * n->B, n->pool, n->nd.off[t],
+                          n->nd.d[t], n->counter + t, n->row_node + at, n->row_j + at,
+                          n->row_sign + at, c->st);
+      at += 2 * lay.size() * (size_t)n->nd.d[t];
+    }
+    int M[MNBAB_MAXR + 2] = {0};
+    d2h(c, M, n->counter, R + 1);
+    sync(c);
+    for (int t = 1; t <= R; ++t) {
+      if (!cnt[t] || !M[t]) continue;
+      total += M[t];
+      for (int s0 = 0; s0 < M[t]; s0 += n->chunk) {
+        const int Mc = std::min(n->chunk, M[t] - s0);
+        const size_t o = region[t] + s0;
+        RowsDev r{Mc, n->row_node + o, n->row_j + o, n->row_sign + o};
+        SweepOpts so;
+        sweep(n, t, r, so);
         Scope sc(c, C_BOOK, 0.0, 24.0 * Mc);
         launch_update_bounds(Mc / 2, r.node, r.j, n->lb, n->pool, n->nd.off[t], c->st);
       }
-      done += nb;
     }
   }
-  for (int s : slots) n->slot_split[s] = n->R;
+  for (int s : slots) n->slot_split[s] = R;
   return total;
 }
 
@@ -631,11 +646,16 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   n->LamB = dalloc_t<float>(c, mrows * n->maxd);
   n->part = dalloc_t<float>(c, mrows * n->nslot);
   n->lb = dalloc_t<float>(c, mrows);
-  n->rows_cap = std::max(chunk, (size_t)2 * n->maxd_relu);
+  n->rows_cap = std::max(chunk, std::min((size_t)2 * SD * B, (size_t)1 << 26));
+  n->rows_cap = std::max(n->rows_cap, (size_t)2 * SD);
   n->row_node = dalloc_t<int>(c, n->rows_cap);
   n->row_j = dalloc_t<int>(c, n->rows_cap);
   n->row_sign = dalloc_t<float>(c, n->rows_cap);
-  n->counter = dalloc_t<int>(c, 4);
+  n->counter = dalloc_t<int>(c, MNBAB_MAXR + 2);
+  n->rb_nodes = dalloc_t<int>(c, (size_t)(MNBAB_MAXR + 2) * B);
+  n->ri_dst = dalloc_t<int>(c, 2 * B);
+  n->ri_src = dalloc_t<int>(c, 2 * B);
+  n->ri_row = dalloc_t<int>(c, 2 * B);
   n->AP = dalloc_t<float>(c, B * SD);
   n->GA = dalloc_t<float>(c, B * SD);
   n->GB = dalloc_t<float>(c, B * SD);
@@ -667,6 +687,41 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   }
 }
 
+// Root bounds of every property of the network admitted since the last call,
+// computed together in one re-bounding pass, then their row root nodes.
+void ensure_roots(mnbab_net* n) {
+  mnbab_ctx* c = n->ctx;
+  std::vector<mnbab_prop*> pend;
+  for (auto* p : c->props)
+    if (p->net == n && p->root_pending) pend.push_back(p);
+  if (pend.empty()) return;
+  std::vector<int> roots;
+  for (auto* p : pend) roots.push_back(p->root_slot);
+  rebound(n, roots);
+  std::vector<int> dst, src, row;
+  auto flush = [&]() {
+    if (dst.empty()) return;
+    h2d(c, n->ri_dst, dst.data(), dst.size());
+    h2d(c, n->ri_src, src.data(), src.size());
+    h2d(c, n->ri_row, row.data(), row.size());
+    Scope sc(c, C_BOOK, 0.0, 25.0 * dst.size() * n->SD);
+    launch_root_init((int)dst.size(), n->ri_dst, n->ri_src, n->ri_row, n->pool, c->st);
+    sync(c);
+    dst.clear(); src.clear(); row.clear();
+  };
+  for (auto* p : pend) {
+    for (size_t r = 0; r < p->root_row_slots.size(); ++r) {
+      if ((int)dst.size() == 2 * n->B) flush();
+      dst.push_back(p->root_row_slots[r]);
+      src.push_back(p->root_slot);
+      row.push_back((int)r);
+    }
+    p->root_pending = false;
+    p->root_row_slots.clear();
+  }
+  flush();
+}
+
 // ---------------------------------------------------------------------------
 // BaB step (Sec. 2.2; Sec. 3.2)
 // ---------------------------------------------------------------------------
@@ -688,6 +743,7 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
   for (int i = 0; i < n_props; ++i)
     if (props[i]->net != n) fail(MNBAB_E_INVALID_ARG, "properties of different networks");
   max_nodes = std::max(1, std::min(max_nodes, n->B));
+  ensure_roots(n);
   // pop FIFO
   std::vector<Picked> picked;
   for (int i = 0; i < n_props && (int)picked.size() < max_nodes; ++i) {
@@ -1092,7 +1148,8 @@ mnbab_status mnbab_set_property(mnbab_ctx* c, const mnbab_net* cnet, const float
   p->row_leaf.assign(n_rows, 0);
   p->row_fals.assign(n_rows, 0);
   p->row_lb.assign(n_rows, INFINITY);
-  // root bounds: a slot with l = -inf, u = +inf, re-bounded from layer 1
+  // root bounds: a slot with l = -inf, u = +inf, re-bounded from layer 1 by the
+  // next call that needs them (admissions are bounded together)
   const int rs = alloc_slot(n);
   p->root_slot = rs;
   n->slot_prop[rs] = p->index;
@@ -1106,31 +1163,17 @@ mnbab_status mnbab_set_property(mnbab_ctx* c, const mnbab_net* cnet, const float
   ck(cudaMemsetAsync(n->pool.S + (size_t)rs * n->SD, 0, n->SD, c->st), "memset");
   int pi = p->index;
   h2d(c, n->pool.prop + rs, &pi, 1);
-  std::vector<int> one{rs};
-  rebound(n, one);
   // root nodes, one per row, FIFO
-  std::vector<int> slots(n_rows);
   for (int r = 0; r < n_rows; ++r) {
-    slots[r] = alloc_slot(n);
-    n->slot_prop[slots[r]] = p->index;
-    n->slot_row[slots[r]] = r;
-    n->slot_split[slots[r]] = n->R;
-  }
-  std::vector<int> rows(n_rows);
-  for (int r = 0; r < n_rows; ++r) rows[r] = r;
-  if (n_rows > 2 * n->B) fail(MNBAB_E_INVALID_ARG, "too many property rows");
-  int* tmp = n->kid_slots;  // scratch for the slot list
-  h2d(c, tmp, slots.data(), n_rows);
-  {
-    Scope sc(c, C_BOOK, 0.0, 25.0 * n_rows * n->SD);
-    launch_root_init(n_rows, tmp, rs, n->pool, c->st);
-  }
-  for (int r = 0; r < n_rows; ++r) h2d(c, n->pool.row + slots[r], &rows[r], 1);
-  sync(c);
-  for (int r = 0; r < n_rows; ++r) {
-    p->queue.push_back(QNode{slots[r], p->next_seq++, r, 0, n->R});
+    const int sl = alloc_slot(n);
+    n->slot_prop[sl] = p->index;
+    n->slot_row[sl] = r;
+    n->slot_split[sl] = n->R;
+    p->root_row_slots.push_back(sl);
+    p->queue.push_back(QNode{sl, p->next_seq++, r, 0, n->R});
     p->row_open[r]++;
   }
+  p->root_pending = true;
   *out = p;
   API_END(c)
 }
@@ -1142,6 +1185,7 @@ mnbab_status mnbab_get_root_bounds(const mnbab_ctx* cc, const mnbab_prop* p, int
   if (!p || !l_out || !u_out) fail(MNBAB_E_INVALID_ARG, "null argument");
   mnbab_net* n = p->net;
   if (layer < 1 || layer > n->R) fail(MNBAB_E_INVALID_ARG, "bad layer");
+  ensure_roots(n);
   const size_t base = (size_t)p->root_slot * n->SD + n->nd.off[layer];
   d2h(c, l_out, n->pool.L + base, n->nd.d[layer]);
   d2h(c, u_out, n->pool.U + base, n->nd.d[layer]);
@@ -1212,16 +1256,19 @@ mnbab_status mnbab_node_root(mnbab_ctx* c, mnbab_prop* p, int32_t row, mnbab_nod
   API_BEGIN(c)
   if (!p || !out || row < 0 || row >= p->n_rows) fail(MNBAB_E_INVALID_ARG, "bad row");
   mnbab_net* n = p->net;
+  ensure_roots(n);
   const int s = alloc_slot(n);
   n->slot_prop[s] = p->index;
   n->slot_row[s] = row;
   n->slot_split[s] = n->R;
-  h2d(c, n->kid_slots, &s, 1);
+  const int src = p->root_slot;
+  h2d(c, n->ri_dst, &s, 1);
+  h2d(c, n->ri_src, &src, 1);
+  h2d(c, n->ri_row, &row, 1);
   {
     Scope sc(c, C_BOOK, 0.0, 25.0 * n->SD);
-    launch_root_init(1, n->kid_slots, p->root_slot, n->pool, c->st);
+    launch_root_init(1, n->ri_dst, n->ri_src, n->ri_row, n->pool, c->st);
   }
-  h2d(c, n->pool.row + s, &row, 1);
   sync(c);
   *out = ((int64_t)n->id << 32) | (int64_t)s;
   API_END(c)
@@ -1298,6 +1345,7 @@ mnbab_status mnbab_bound_batch(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t
   std::vector<int> slots;
   mnbab_net* n = slots_of(c, nodes, nn, slots);
   if (!lb_out) fail(MNBAB_E_INVALID_ARG, "null output");
+  ensure_roots(n);
   rebound(n, slots);
   upload_batch(n, slots);
   const bool g = batch_has_gamma(n, slots);
