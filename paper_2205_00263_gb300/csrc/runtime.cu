@@ -121,6 +121,8 @@ struct mnbab_ctx {
   std::vector<mnbab_prop*> props;
   PropDev* d_props = nullptr;
   int props_cap = 0;
+  float* arena = nullptr;
+  size_t arena_cap = 0, arena_used = 0;
   std::vector<std::pair<void*, size_t>> allocs;
   // profiling: kernel-class timing with CUDA events, launch and copy counters
   bool prof = false;
@@ -251,17 +253,36 @@ void free_slot(mnbab_net* n, int s) {
   n->free_slots.push_back(s);
 }
 
-void upload_props(mnbab_ctx* c) {
+// Device property table: grows by doubling (the previous table stays
+// allocated until destroy: kernels already queued may still read it); a new or
+// changed property uploads only its own entry.
+void upload_prop(mnbab_ctx* c, int index) {
   const int np = (int)c->props.size();
   if (np > c->props_cap) {
     const int nc = std::max(64, np * 2);
     PropDev* nd = dalloc_t<PropDev>(c, nc);
-    c->d_props = nd;  // old table stays allocated until destroy (small)
+    if (c->d_props && c->props_cap)
+      ck(cudaMemcpyAsync(nd, c->d_props, (size_t)c->props_cap * sizeof(PropDev),
+                         cudaMemcpyDeviceToDevice, c->st), "table copy");
+    c->d_props = nd;
     c->props_cap = nc;
   }
-  std::vector<PropDev> h(np);
-  for (int i = 0; i < np; ++i) h[i] = c->props[i]->pd;
-  h2d(c, c->d_props, h.data(), np);
+  h2d(c, c->d_props + index, &c->props[index]->pd, 1);
+}
+
+// Bump allocator for per-property arrays (input box, folded last layer), so
+// admitting a property issues no cudaMalloc in the common case.
+float* prop_arena(mnbab_ctx* c, size_t nfloats) {
+  nfloats = (nfloats + 63) & ~size_t(63);
+  if (c->arena_used + nfloats > c->arena_cap) {
+    const size_t cap = std::max(nfloats, (size_t)16 << 20);  // 64 MiB blocks
+    c->arena = dalloc_t<float>(c, cap);
+    c->arena_cap = cap;
+    c->arena_used = 0;
+  }
+  float* p = c->arena + c->arena_used;
+  c->arena_used += nfloats;
+  return p;
 }
 
 Epi base_epi(mnbab_net* n, const int* row_node) {
@@ -1133,17 +1154,17 @@ mnbab_status mnbab_set_property(mnbab_ctx* c, const mnbab_net* cnet, const float
   }
   std::vector<float> Wf(p->Wf.begin(), p->Wf.end()), bf(p->bf.begin(), p->bf.end());
   PropDev& pd = p->pd;
-  float* dlo = dalloc_t<float>(c, n->d0);
-  float* dhi = dalloc_t<float>(c, n->d0);
-  float* dWf = dalloc_t<float>(c, Wf.size());
-  float* dbf = dalloc_t<float>(c, bf.size());
+  float* dlo = prop_arena(c, n->d0);
+  float* dhi = prop_arena(c, n->d0);
+  float* dWf = prop_arena(c, Wf.size());
+  float* dbf = prop_arena(c, bf.size());
   h2d(c, dlo, x_lo, n->d0);
   h2d(c, dhi, x_hi, n->d0);
   h2d(c, dWf, Wf.data(), Wf.size());
   h2d(c, dbf, bf.data(), bf.size());
   pd.lo = dlo; pd.hi = dhi; pd.Wf = dWf; pd.bf = dbf; pd.n_rows = n_rows; pd.E = 0;
   c->props.push_back(p);
-  upload_props(c);
+  upload_prop(c, p->index);
   p->row_open.assign(n_rows, 0);
   p->row_leaf.assign(n_rows, 0);
   p->row_fals.assign(n_rows, 0);
@@ -1247,7 +1268,7 @@ mnbab_status mnbab_set_mnc(mnbab_ctx* c, mnbab_prop* p, int32_t layer, int32_t n
   }
   p->pd.E += n_rows;
   p->mnc_set[layer] = 1;
-  upload_props(c);
+  upload_prop(c, p->index);
   sync(c);
   API_END(c)
 }
