@@ -96,9 +96,11 @@ class Context:
     """One libmnbab context on one CUDA device."""
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, stream=None,
-                 node_capacity: int = 0, max_mnc_rows: int = 0, row_chunk: int = 0):
+                 node_capacity: int = 0, max_mnc_rows: int = 0, row_chunk: int = 0,
+                 gemm_path: int = 0):
         self.lib = L.load()
-        o = L.Options(device, hbm_budget_bytes, stream, node_capacity, max_mnc_rows, row_chunk)
+        o = L.Options(device, hbm_budget_bytes, stream, node_capacity, max_mnc_rows, row_chunk,
+                      gemm_path)
         h = C.c_void_p()
         st = self.lib.mnbab_create(C.byref(o), C.byref(h))
         if st != 0:

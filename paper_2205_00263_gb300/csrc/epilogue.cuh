@@ -1,0 +1,101 @@
+// Fused back-substitution epilogues shared by the SIMT and tensor-core kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mnbab_internal.h"
+
+namespace mnbab {
+
+// ---------------------------------------------------------------------------
+// epilogues
+// ---------------------------------------------------------------------------
+// ReLU back-substitution of one coefficient a on z_j (Sec. 3.1, combined ReLU
+// step): a' = a + (gamma^T P)_j, D / blow from the single-neuron table with
+// split precedence, ahat = a' D + beta S + (gamma^T Phat)_j.  The offset
+// contribution a' blow + ahat b_j (bias of the consuming affine layer) goes to
+// the row partial sum.
+__device__ __forceinline__ float epi_relu(const Epi& e, int m, int j, float a, float& part) {
+  const int n = e.row_node[m];
+  const size_t q = (size_t)n * e.SD + e.off + j;
+  const size_t qm = (size_t)m * e.SD + e.off + j;
+  const float l = e.pool.L[q], u = e.pool.U[q];
+  const int s = e.pool.S[q];
+  float ap = a;
+  if (e.GP) ap += e.GP[qm];
+  float D, bl = 0.f;
+  if (s == -1) D = 1.f;
+  else if (s == 1) D = 0.f;
+  else if (l >= 0.f) D = 1.f;
+  else if (u <= 0.f) D = 0.f;
+  else if (ap >= 0.f) D = e.final_mode ? e.pool.ALPHA[q] : (u >= -l ? 1.f : 0.f);
+  else {
+    const float den = u - l;
+    D = u / den;
+    bl = (-u * l) / den;
+  }
+  float ah = ap * D;
+  if (e.final_mode) ah += e.pool.BETA[q] * (float)s;
+  if (e.GPh) ah += e.GPh[qm];
+  if (e.AP) e.AP[qm] = ap;
+  part += ap * bl + ah * e.bias[j / e.bias_div];
+  return ah;
+}
+
+// Concretisation of a coefficient on input x_j over [lo, hi] (Eq. minimum):
+// x*_j = lo_j if a >= 0 else hi_j, contribution a x*_j.
+__device__ __forceinline__ float epi_conc(const Epi& e, int m, int j, float a, float& part) {
+  const int n = e.row_node[m];
+  const PropDev& P = e.props[e.pool.prop[n]];
+  const float x = a >= 0.f ? P.lo[j] : P.hi[j];
+  part += a * x;
+  if (e.X) e.X[(size_t)m * e.d0 + j] = x;
+  return a;
+}
+
+// Adjoint of the ReLU step at pre-activation adjoint h = d lb / d ahat_j:
+// d lb / d alpha_j = h a'_j on the alpha branch, d lb / d beta_j = h S_j,
+// and d lb / d a'_j = h D_j + blow_j flows to the next layer.
+__device__ __forceinline__ float epi_adj(const Epi& e, int m, int j, float h) {
+  const int n = e.row_node[m];
+  const size_t q = (size_t)n * e.SD + e.off + j;
+  const size_t qm = (size_t)m * e.SD + e.off + j;
+  const float l = e.pool.L[q], u = e.pool.U[q];
+  const int s = e.pool.S[q];
+  const float ap = e.AP[qm];
+  float D, bl = 0.f;
+  bool abr = false;
+  if (s == -1) D = 1.f;
+  else if (s == 1) D = 0.f;
+  else if (l >= 0.f) D = 1.f;
+  else if (u <= 0.f) D = 0.f;
+  else if (ap >= 0.f) { D = e.pool.ALPHA[q]; abr = true; }
+  else {
+    const float den = u - l;
+    D = u / den;
+    bl = (-u * l) / den;
+  }
+  e.GA[qm] = abr ? h * ap : 0.f;
+  e.GB[qm] = h * (float)s;
+  const float g = h * D + bl;
+  if (e.Hz) {
+    e.Hz[qm] = h;
+    e.Gz[qm] = g;
+  }
+  return g;
+}
+
+__device__ __forceinline__ float epi_apply(const Epi& e, int m, int j, float v, float& part) {
+  switch (e.kind) {
+    case EPI_RELU: return epi_relu(e, m, j, v, part);
+    case EPI_CONC: return epi_conc(e, m, j, v, part);
+    case EPI_ADJ: return epi_adj(e, m, j, v);
+    case EPI_FWD_RELU: return fmaxf(v, 0.f);
+    default: return v;
+  }
+}
+
+__device__ __forceinline__ bool epi_has_part(const Epi& e) {
+  return e.part != nullptr && (e.kind == EPI_RELU || e.kind == EPI_CONC);
+}
+
+}  // namespace mnbab

@@ -95,9 +95,16 @@ struct Epi {
   float* part;       // [M][nslot] row partial sums of the offset c
   int nslot;
   int slot_base;
+  int gemm_path;     // 0 auto, 1 SIMT, 2 tensor cores (dense FC steps)
+  int* err;          // device error flag (bounded waits of the tensor-core kernel)
 };
 
-// ---- launchers (kernels.cu) --------------------------------------------
+// ---- launchers (kernels.cu, tc_gemm.cu) ----------------------------------
+// Tensor-core 3xTF32 GEMM C = A . Bnk^T (+ bias) with the fused epilogue;
+// returns the number of column tiles (partial-sum slots written).
+int launch_gemm_tc(int M, int N, int K, const float* A, int lda, const float* Bnk, int ldb,
+                   const float* bias, int bias_div, float* C, int ldc, const Epi& e, int* err,
+                   cudaStream_t st);
 // Starting rows: a = sign * W_t[j, :] (t <= R) or Wf[row, :] (t = R + 1) on
 // z^(t-1), with c = sign * b_t[j] into slot 0, through epilogue `e`.
 void launch_init_rows(const NetDev& net, int t, const RowsDev& rows, float* out, int ld,

@@ -179,6 +179,7 @@ extern "C" mnbab_status mnbab_deeppoly_fc_noalloc(int32_t n_affine, const int32_
     ep.part = d_part;
     ep.nslot = nslot;
     ep.bias_div = 1;
+    ep.gemm_path = 1;  // SIMT kernels: no error flag to report through
     if (layer >= 1) {
       ep.kind = EPI_RELU;
       ep.layer = layer;

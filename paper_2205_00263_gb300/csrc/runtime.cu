@@ -115,7 +115,8 @@ struct mnbab_ctx {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   uint64_t budget = 0, used = 0;
-  int node_cap = 65536, EC = 0, row_chunk = 32768;
+  int node_cap = 65536, EC = 0, row_chunk = 32768, gemm_path = 0;
+  int* d_err = nullptr;  // device error flag of bounded device waits
   std::string err;
   std::vector<mnbab_net*> nets;
   std::vector<mnbab_prop*> props;
@@ -190,6 +191,14 @@ void sync(mnbab_ctx* c) {
   ck(cudaStreamSynchronize(c->st), "stream synchronize");
   ck(cudaGetLastError(), "kernel launch");
   if (!c->pending.empty()) resolve_prof(c);
+  if (c->d_err && c->gemm_path != 1) {
+    int e = 0;
+    ck(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+    if (e) {
+      cudaMemset(c->d_err, 0, sizeof(int));
+      fail(MNBAB_E_TIMEOUT, "a tensor-core kernel timed out waiting for its MMAs");
+    }
+  }
 }
 
 cudaEvent_t get_event(mnbab_ctx* c) {
@@ -295,6 +304,8 @@ Epi base_epi(mnbab_net* n, const int* row_node) {
   e.part = n->part;
   e.nslot = n->nslot;
   e.bias_div = 1;
+  e.gemm_path = n->ctx->gemm_path;
+  e.err = n->ctx->d_err;
   return e;
 }
 
@@ -988,6 +999,7 @@ mnbab_status mnbab_create(const mnbab_options* opt, mnbab_ctx** out) {
   c->node_cap = o.node_capacity > 0 ? o.node_capacity : 65536;
   c->EC = std::max(0, o.max_mnc_rows);
   c->row_chunk = std::min(o.row_chunk > 0 ? o.row_chunk : 32768, 65534);
+  c->gemm_path = (o.gemm_path >= 0 && o.gemm_path <= 2) ? o.gemm_path : 0;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
     delete c;
@@ -1005,6 +1017,13 @@ mnbab_status mnbab_create(const mnbab_options* opt, mnbab_ctx** out) {
       return MNBAB_E_DEVICE;
     }
     c->own_stream = true;
+  }
+  try {
+    c->d_err = dalloc_t<int>(c, 1);
+    ck(cudaMemset(c->d_err, 0, sizeof(int)), "memset");
+  } catch (const Err& e) {
+    mnbab_destroy(c);
+    return e.code;
   }
   *out = c;
   return MNBAB_OK;

@@ -1,0 +1,272 @@
+// Tensor-core (tcgen05, sm_103a) GEMM with 3xTF32 split products and the
+// fused back-substitution epilogues: the dense affine steps Lambda . W (Sec. 3.1,
+// affine back-substitution) and G . W^T + b (adjoint / forward sweeps).
+//
+// C[M][N] = A[M][K] . B^T with A row-major (K contiguous) and B given as
+// [N][K] (K contiguous); both operands are "K-major" for the MMA.  Every FP32
+// value x is split into hi = tf32(x) and lo = tf32(x - hi); the product uses
+// hi.hi + hi.lo + lo.hi accumulated in FP32 in tensor memory, which keeps FP32
+// accuracy (the dropped lo.lo term is below 2^-22 relative).
+//
+// One CTA = 4 warps computes a 128 x BN tile.  Per K block of 32, the threads
+// load A and B, split them and store the four tiles in the no-swizzle
+// canonical K-major layout (8-row x 16-byte core matrices; adjacent core
+// matrices along K are LBO = 128 B apart, along M/N SBO = 1024 B apart); one
+// thread issues 4 k-steps x 3 tcgen05.mma (K = 8 each) and commits them to an
+// mbarrier.  The epilogue reads the accumulator with tcgen05.ld (warp w owns
+// TMEM lanes 32w..32w+31 = tile rows) and applies the same epilogue functions
+// as the SIMT kernels; each thread owns one row, so the row partial sums of
+// the offset need no cross-thread reduction.
+//
+// Every wait on the mbarrier is bounded: on timeout the kernel records an
+// error, waits once more (bounded) for its own MMAs, frees its tensor memory
+// and returns.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "epilogue.cuh"
+#include "mnbab_internal.h"
+
+namespace mnbab {
+
+namespace {
+
+constexpr int TBM = 128;  // tile rows (TMEM lanes)
+constexpr int TBK = 32;   // K per staged block (4 MMAs of K = 8)
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// canonical no-swizzle K-major offset (bytes) of element (r, k) in a tile with
+// TBK = 32 K-columns: 8 core matrices of 128 B along K per 8-row group
+__device__ __forceinline__ uint32_t tile_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  const uint64_t lbo = 128, sbo = 1024;
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  // base offset 0, LBO mode 0, layout type 0 = no swizzle
+  return d;
+}
+
+// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (unsigned i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if (i > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace
+
+template <int BN>
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const float* __restrict__ A,
+                                                 int lda, const float* __restrict__ B, int ldb,
+                                                 const float* __restrict__ bias, int bias_div,
+                                                 float* C, int ldc, Epi e, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-aligned tiles: A_hi, A_lo (128 x 32), B_hi, B_lo (BN x 32)
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* a_hi = base;
+  unsigned char* a_lo = a_hi + TBM * TBK * 4;
+  unsigned char* b_hi = a_lo + TBM * TBK * 4;
+  unsigned char* b_lo = b_hi + BN * TBK * 4;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(b_lo + BN * TBK * 4);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * BN;
+  const uint32_t bar_a = smem_u32(bar);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"((uint32_t)BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_a), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_holder;
+  constexpr uint32_t idesc = idesc_tf32(BN);
+
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int k0 = 0; k0 < K; k0 += TBK) {
+    // stage A (128 x 32) and B (BN x 32), split into hi / lo TF32
+    for (int q = tid; q < TBM * TBK; q += 128) {
+      const int r = q >> 5, k = q & 31;
+      const int gm = m0 + r, gk = k0 + k;
+      const float x = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.f;
+      const uint32_t h = to_tf32(x);
+      const uint32_t l = to_tf32(x - __uint_as_float(h));
+      const uint32_t o = tile_off(r, k);
+      *reinterpret_cast<uint32_t*>(a_hi + o) = h;
+      *reinterpret_cast<uint32_t*>(a_lo + o) = l;
+    }
+    for (int q = tid; q < BN * TBK; q += 128) {
+      const int r = q >> 5, k = q & 31;
+      const int gn = n0 + r, gk = k0 + k;
+      const float x = (gn < N && gk < K) ? B[(size_t)gn * ldb + gk] : 0.f;
+      const uint32_t h = to_tf32(x);
+      const uint32_t l = to_tf32(x - __uint_as_float(h));
+      const uint32_t o = tile_off(r, k);
+      *reinterpret_cast<uint32_t*>(b_hi + o) = h;
+      *reinterpret_cast<uint32_t*>(b_lo + o) = l;
+    }
+    // make the generic-proxy smem writes visible to the tensor core
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
+      const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+      for (int ks = 0; ks < TBK / 8; ++ks) {
+        const uint32_t off = ks * 256;  // two core matrices of K per MMA
+        const uint32_t first = (k0 == 0 && ks == 0) ? 0u : 1u;
+        mma_tf32(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, first);
+        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
+        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, 1u);
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              bar_a)
+          : "memory");
+    }
+    // all threads wait for the MMAs before reusing the tiles
+    const bool mine = mbar_wait(bar_a, phase);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(mine) != 0;  // uniform across the CTA
+    if (!ok) break;
+    phase ^= 1u;
+  }
+  if (!ok) {
+    // record the timeout, then give the MMAs in flight one more bounded wait
+    // before the tensor memory they write is released
+    if (tid == 0) {
+      atomicExch(err, 1);
+      mbar_wait(bar_a, phase);
+    }
+    __syncthreads();
+  }
+  if (ok) {
+    // epilogue: warp w owns rows 32w..32w+31 of the tile, one row per thread
+    const int m = m0 + warp * 32 + lane;
+    float part = 0.f;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16<16>(trow + (uint32_t)c0, v);
+      if (m < M) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int n = n0 + c0 + i;
+          if (n < N) {
+            float x = v[i];
+            if (bias) x += bias[n / bias_div];
+            const float o = epi_apply(e, m, n, x, part);
+            if (C) C[(size_t)m * ldc + n] = o;
+          }
+        }
+      }
+    }
+    if (epi_has_part(e) && m < M) e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = part;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)BN));
+  }
+}
+
+template <int BN>
+static constexpr int tc_smem_bytes() {
+  return 1024 + 2 * TBM * TBK * 4 + 2 * BN * TBK * 4 + 64;
+}
+
+template <int BN>
+static int launch_bn(int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                     const float* bias, int bias_div, float* C, int ldc, const Epi& e, int* err,
+                     cudaStream_t st) {
+  constexpr int smem = tc_smem_bytes<BN>();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  dim3 grid((N + BN - 1) / BN, (M + TBM - 1) / TBM);
+  k_gemm_tc<BN><<<grid, 128, smem, st>>>(M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e, err);
+  return grid.x;
+}
+
+// Tile width: the smallest of 64 / 128 / 256 that covers N in one tile, else 256.
+int launch_gemm_tc(int M, int N, int K, const float* A, int lda, const float* Bnk, int ldb,
+                   const float* bias, int bias_div, float* C, int ldc, const Epi& e, int* err,
+                   cudaStream_t st) {
+  if (N <= 64) return launch_bn<64>(M, N, K, A, lda, Bnk, ldb, bias, bias_div, C, ldc, e, err, st);
+  if (N <= 128)
+    return launch_bn<128>(M, N, K, A, lda, Bnk, ldb, bias, bias_div, C, ldc, e, err, st);
+  return launch_bn<256>(M, N, K, A, lda, Bnk, ldb, bias, bias_div, C, ldc, e, err, st);
+}
+
+}  // namespace mnbab

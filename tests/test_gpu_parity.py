@@ -38,8 +38,9 @@ def _assert_close(g, o, what, tol=TOL):
 # --------------------------------------------------------------------------
 # root bounds (DeepPoly back-substitution of every neuron, both sides)
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("case", ["ragged_fc", "conv", "cfg0"])
-def test_root_bounds(Context, case):
+def test_root_bounds(Context, case, path):
     if case == "ragged_fc":
         layers, C, d, lo, hi, prep = fc_case(1, (37, 53, 29, 7), 0.1)
     elif case == "conv":
@@ -50,7 +51,7 @@ def test_root_bounds(Context, case):
         layers, C, d, lo, hi = layers, pr.C, pr.d, pr.lo, pr.hi
         prep = bab.prepare(layers, C, d, lo, hi)
     net, lo_t, hi_t, l, u, S, _, _ = prep
-    with Context(node_capacity=64) as ctx:
+    with Context(node_capacity=64, gemm_path=path) as ctx:
         gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
         for i in range(1, net.R + 1):
             gl, gu = ctx.root_bounds(prop, i)
@@ -61,8 +62,9 @@ def test_root_bounds(Context, case):
 # --------------------------------------------------------------------------
 # fixed parameters: re-bounding after splits and the objective bound
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("case", ["fc_mnc", "conv"])
-def test_rebound_and_bound_at_fixed_parameters(Context, case):
+def test_rebound_and_bound_at_fixed_parameters(Context, case, path):
     if case == "fc_mnc":
         layers, C, d, lo, hi, prep = fc_case(3, (37, 53, 29, 7), 0.12, with_mnc=True)
     else:
@@ -70,7 +72,7 @@ def test_rebound_and_bound_at_fixed_parameters(Context, case):
     net, lo_t, hi_t, l, u, S, m, dense = prep
     E = sum(v.idx.shape[0] for v in m.values()) if m else 0
     rng = np.random.default_rng(11)
-    with Context(node_capacity=256, max_mnc_rows=max(E, 1)) as ctx:
+    with Context(node_capacity=256, max_mnc_rows=max(E, 1), gemm_path=path) as ctx:
         gnet, prop = gpu_property(ctx, layers, lo, hi, C, d, m)
         onodes, gids = [], []
         for k in range(40):
@@ -117,8 +119,9 @@ def test_deeppoly_pass(Context):
 # --------------------------------------------------------------------------
 # adjoint: gradient of the bound w.r.t. alpha, beta, gamma
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("case", ["fc_mnc", "conv"])
-def test_gradient_matches_oracle(Context, case):
+def test_gradient_matches_oracle(Context, case, path):
     if case == "fc_mnc":
         layers, C, d, lo, hi, prep = fc_case(6, (37, 53, 29, 7), 0.12, with_mnc=True)
     else:
@@ -127,7 +130,7 @@ def test_gradient_matches_oracle(Context, case):
     E = sum(v.idx.shape[0] for v in m.values()) if m else 0
     SD = sum(l[i].numel() for i in l)
     rng = np.random.default_rng(3)
-    with Context(node_capacity=128, max_mnc_rows=max(E, 1)) as ctx:
+    with Context(node_capacity=128, max_mnc_rows=max(E, 1), gemm_path=path) as ctx:
         gnet, prop = gpu_property(ctx, layers, lo, hi, C, d, m)
         onodes, gids = [], []
         for k in range(10):
@@ -154,12 +157,13 @@ def test_gradient_matches_oracle(Context, case):
 # --------------------------------------------------------------------------
 # projected Adam (20 steps) and ACS
 # --------------------------------------------------------------------------
-def test_optimized_bound_matches_oracle(Context):
+@pytest.mark.parametrize("path", [1, 2])
+def test_optimized_bound_matches_oracle(Context, path):
     layers, C, d, lo, hi, prep = fc_case(8, (37, 53, 29, 7), 0.12, with_mnc=True)
     net, lo_t, hi_t, l, u, S, m, dense = prep
     E = sum(v.idx.shape[0] for v in m.values())
     rng = np.random.default_rng(8)
-    with Context(node_capacity=128, max_mnc_rows=E) as ctx:
+    with Context(node_capacity=128, max_mnc_rows=E, gemm_path=path) as ctx:
         gnet, prop = gpu_property(ctx, layers, lo, hi, C, d, m)
         onodes, gids = [], []
         for k in range(8):
@@ -335,10 +339,11 @@ def test_zero_radius_box_is_exact(Context):
         assert v == 1
 
 
-def test_batch_capacity_and_errors(Context):
+@pytest.mark.parametrize("path", [1, 2])
+def test_batch_capacity_and_errors(Context, path):
     from paper_2205_00263_gb300 import MnbabError
     layers, C, d, lo, hi, prep = fc_case(13, (37, 53, 29, 7), 0.1)
-    with Context(node_capacity=2048) as ctx:
+    with Context(node_capacity=2048, gemm_path=path) as ctx:
         gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
         nodes = [ctx.node_root(prop, r % C.shape[0]) for r in range(1024)]
         lb = ctx.deeppoly_batch(nodes)
