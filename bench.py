@@ -134,7 +134,8 @@ def load_peaks():
 
 def roofline(stats, peaks, src, kernels_hash):
     """Dominant kernel class (largest summed launch time) against its roofline."""
-    name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    kern = {k: v for k, v in stats.items() if not k.startswith("step_")}
+    name, st = max(kern.items(), key=lambda kv: kv[1]["ms"])
     per_launch_ms = st["ms"] / max(1, st["launches"])
     simt = name in ("backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm", "forward_conv")
     if simt:

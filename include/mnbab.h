@@ -19,7 +19,7 @@
  *    stream the library creates); calls are synchronous with respect to the
  *    host unless stated otherwise.  One context per host thread.
  *  - Floating point is IEEE FP32 on the device; the library re-checks every
- *    counterexample with an FP64 forward pass on the host.
+ *    counterexample with an FP64 forward pass (device kernel) before reporting it.
  *  - Errors: MNBAB_E_INVALID_ARG for bad handles, sizes or shapes;
  *    MNBAB_E_BUDGET when the HBM budget or a pool capacity would be exceeded;
  *    MNBAB_E_DEVICE for CUDA errors; MNBAB_E_UNSUPPORTED for layer kinds or

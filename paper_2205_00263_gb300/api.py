@@ -279,10 +279,10 @@ class Context:
 
     def profile_read(self):
         """({kernel class: {launches, ms, flops, bytes}}, total launches)."""
-        arr = (L.KernelStat * 16)()
+        arr = (L.KernelStat * 32)()
         n = C.c_int32()
         tot = C.c_int64()
-        self._ck(self.lib.mnbab_profile_read(self.h, arr, 16, C.byref(n), C.byref(tot)))
+        self._ck(self.lib.mnbab_profile_read(self.h, arr, 32, C.byref(n), C.byref(tot)))
         out = {}
         for i in range(n.value):
             k = arr[i]

@@ -854,6 +854,70 @@ void launch_final_dot(int M, const int* row_node, PoolDev pool, const PropDev* p
   k_final_dot<<<(M + 7) / 8, 256, 0, st>>>(M, row_node, pool, props, z, ld, dR, f);
 }
 
+// Concrete forward pass f_r(x) in FP64 (one CTA per row), used to confirm
+// counterexamples: the sign of f_r at x* decides FALSIFIED (Sec. 2.2), so it is
+// evaluated in double precision from the FP32 weights.
+__global__ void k_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                              NetDev net, const float* X, int ldx, double* b1, double* b2,
+                              int ldb, double* fout) {
+  const int m = blockIdx.x;
+  double* h = b1 + (size_t)m * ldb;
+  double* g = b2 + (size_t)m * ldb;
+  for (int k = threadIdx.x; k < net.d[0]; k += blockDim.x) h[k] = (double)X[(size_t)m * ldx + k];
+  __syncthreads();
+  for (int i = 1; i <= net.R; ++i) {
+    const LayerDev& L = net.aff[i];
+    for (int o = threadIdx.x; o < L.d_out; o += blockDim.x) {
+      double acc;
+      if (L.kind == 1) {
+        acc = (double)L.b[o];
+        const float* w = L.W + (size_t)o * L.d_in;
+        for (int k = 0; k < L.d_in; ++k) acc = fma((double)w[k], h[k], acc);
+      } else {
+        const int hw = L.ho * L.wo;
+        const int co = o / hw, oh = (o % hw) / L.wo, ow = o % L.wo;
+        acc = (double)L.b[co];
+        for (int ci = 0; ci < L.ci; ++ci)
+          for (int kh = 0; kh < L.k; ++kh) {
+            const int ih = oh * L.s - L.p + kh;
+            if (ih < 0 || ih >= L.hi) continue;
+            for (int kw = 0; kw < L.k; ++kw) {
+              const int iw = ow * L.s - L.p + kw;
+              if (iw < 0 || iw >= L.wi) continue;
+              acc = fma((double)L.W[(((size_t)co * L.ci + ci) * L.k + kh) * L.k + kw],
+                        h[((size_t)ci * L.hi + ih) * L.wi + iw], acc);
+            }
+          }
+      }
+      g[o] = acc > 0.0 ? acc : 0.0;
+    }
+    __syncthreads();
+    double* t = h; h = g; g = t;
+  }
+  const int n = row_node[m];
+  const PropDev& P = props[pool.prop[n]];
+  const int r = pool.row[n];
+  const int dR = net.d[net.R];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < dR; k += blockDim.x) acc = fma((double)P.Wf[(size_t)r * dR + k], h[k], acc);
+  __shared__ double sh[32];
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = (double)P.bf[r];
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+    fout[m] = t;
+  }
+}
+
+void launch_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                        const NetDev& net, const float* X, int ldx, double* b1, double* b2,
+                        int ldb, double* fout, cudaStream_t st) {
+  if (M <= 0) return;
+  k_forward_f64<<<M, 256, 0, st>>>(M, row_node, pool, props, net, X, ldx, b1, b2, ldb, fout);
+}
+
 __global__ void k_fill(float* p, size_t n, float v) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;

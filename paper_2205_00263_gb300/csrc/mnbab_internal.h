@@ -150,5 +150,9 @@ void launch_root_init(int nb, const int* slots, const int* srcs, const int* rows
 void launch_final_dot(int M, const int* row_node, PoolDev pool, const PropDev* props,
                       const float* z, int ld, int dR, float* f, cudaStream_t st);
 void launch_fill(float* p, size_t n, float v, cudaStream_t st);
+// FP64 forward pass f_r(x) of rows of X (counterexample confirmation).
+void launch_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                        const NetDev& net, const float* X, int ldx, double* b1, double* b2,
+                        int ldb, double* fout, cudaStream_t st);
 
 }  // namespace mnbab

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -80,6 +81,8 @@ struct mnbab_net {
   float *AP = nullptr, *GA = nullptr, *GB = nullptr, *GP = nullptr, *GPh = nullptr;
   float *Gz = nullptr, *Hz = nullptr, *X = nullptr, *Xb = nullptr, *GG = nullptr, *gp0 = nullptr;
   float *fout = nullptr, *score = nullptr, *bestb = nullptr, *gmax = nullptr;
+  double *f64a = nullptr, *f64b = nullptr, *f64out = nullptr;
+  int* cslots = nullptr;
   int *bslots = nullptr, *brows = nullptr, *acs_layer = nullptr, *acs_neuron = nullptr,
       *acs_fb = nullptr, *kid_parent = nullptr, *kid_slots = nullptr, *kid_layer = nullptr,
       *kid_neuron = nullptr;
@@ -130,8 +133,8 @@ struct mnbab_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<cudaEvent_t> ev_free;
   int64_t launches = 0;
-  int64_t acc_n[16] = {0};
-  double acc_ms[16] = {0}, acc_flops[16] = {0}, acc_bytes[16] = {0};
+  int64_t acc_n[32] = {0};
+  double acc_ms[32] = {0}, acc_flops[32] = {0}, acc_bytes[32] = {0};
   int64_t h2d_bytes = 0, d2h_bytes = 0;
 };
 
@@ -169,12 +172,23 @@ void d2h(mnbab_ctx* c, T* dst, const T* src, size_t n) {
 
 enum Cat {
   C_BACKSUB_FC, C_BACKSUB_CONV, C_FWD_FC, C_FWD_CONV, C_INIT, C_REDUCE, C_GAMMA, C_ADAM, C_ACS,
-  C_BOOK, NCAT
+  C_BOOK, NKCAT,
+  // host wall time of the BaB step phases (stream work included up to their syncs)
+  H_ROOTS = NKCAT, H_REBOUND, H_DEEPPOLY, H_OPTIMIZE, H_CONFIRM, H_FINISH, NCAT
 };
 const char* CAT_NAMES[NCAT] = {"backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm",
                                "forward_conv",    "init_rows",              "reduce_lb",
                                "gamma_terms",     "adam",                   "acs",
-                               "bookkeeping"};
+                               "bookkeeping",     "step_roots_wall",        "step_rebound_wall",
+                               "step_deeppoly_wall", "step_optimize_wall",  "step_confirm_wall",
+                               "step_finish_wall"};
+
+struct HostTimer {
+  mnbab_ctx* c;
+  std::chrono::steady_clock::time_point t;
+  explicit HostTimer(mnbab_ctx* c_) : c(c_), t(std::chrono::steady_clock::now()) {}
+  void lap(int cat);
+};
 
 void resolve_prof(mnbab_ctx* c) {
   for (auto& r : c->pending) {
@@ -237,6 +251,15 @@ struct Scope {
     }
   }
 };
+
+void HostTimer::lap(int cat) {
+  const auto now = std::chrono::steady_clock::now();
+  if (c->prof) {
+    c->acc_ms[cat] += std::chrono::duration<double, std::milli>(now - t).count();
+    c->acc_n[cat] += 1;
+  }
+  t = now;
+}
 
 double layer_macs(const LayerDev& L) {
   return L.kind == 1 ? (double)L.d_in * L.d_out : (double)L.co * L.ho * L.wo * L.ci * L.k * L.k;
@@ -541,48 +564,6 @@ __global__ void k_gather1(int M, const int* idx, const float* src, float* dst) {
   if (m < M) dst[m] = src[idx[m]];
 }
 
-// FP64 forward pass on the host (counterexample confirmation)
-double host_forward(mnbab_net* n, mnbab_prop* p, int row, const float* x) {
-  std::vector<double> h(x, x + n->d0), g;
-  for (int i = 1; i <= n->R; ++i) {
-    const HostLayer& L = n->host[i];
-    if (L.kind == MNBAB_FC) {
-      const int din = L.ci, dout = L.co;
-      g.assign(dout, 0.0);
-      for (int o = 0; o < dout; ++o) {
-        double acc = L.b[o];
-        for (int k = 0; k < din; ++k) acc += L.W[(size_t)o * din + k] * h[k];
-        g[o] = acc;
-      }
-    } else {
-      g.assign((size_t)L.co * L.ho * L.wo, 0.0);
-      for (int co = 0; co < L.co; ++co)
-        for (int oh = 0; oh < L.ho; ++oh)
-          for (int ow = 0; ow < L.wo; ++ow) {
-            double acc = L.b[co];
-            for (int ci = 0; ci < L.ci; ++ci)
-              for (int kh = 0; kh < L.k; ++kh) {
-                const int ih = oh * L.s - L.p + kh;
-                if (ih < 0 || ih >= L.hi) continue;
-                for (int kw = 0; kw < L.k; ++kw) {
-                  const int iw = ow * L.s - L.p + kw;
-                  if (iw < 0 || iw >= L.wi) continue;
-                  acc += L.W[(((size_t)co * L.ci + ci) * L.k + kh) * L.k + kw] *
-                         h[((size_t)ci * L.hi + ih) * L.wi + iw];
-                }
-              }
-            g[((size_t)co * L.ho + oh) * L.wo + ow] = acc;
-          }
-    }
-    for (auto& v : g) v = v > 0.0 ? v : 0.0;
-    h.swap(g);
-  }
-  const int dR = (int)h.size();
-  double f = p->bf[row];
-  for (int k = 0; k < dR; ++k) f += p->Wf[(size_t)row * dR + k] * h[k];
-  return f;
-}
-
 mnbab_adam default_adam() {
   mnbab_adam a;
   a.steps = 20;
@@ -703,6 +684,10 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   n->score = dalloc_t<float>(c, B);
   n->bestb = dalloc_t<float>(c, B);
   n->gmax = dalloc_t<float>(c, B);
+  n->f64a = dalloc_t<double>(c, B * n->maxd);
+  n->f64b = dalloc_t<double>(c, B * n->maxd);
+  n->f64out = dalloc_t<double>(c, B);
+  n->cslots = dalloc_t<int>(c, B);
   n->bslots = dalloc_t<int>(c, B);
   n->brows = dalloc_t<int>(c, B);
   n->acs_layer = dalloc_t<int>(c, B);
@@ -775,7 +760,9 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
   for (int i = 0; i < n_props; ++i)
     if (props[i]->net != n) fail(MNBAB_E_INVALID_ARG, "properties of different networks");
   max_nodes = std::max(1, std::min(max_nodes, n->B));
+  HostTimer ht(c);
   ensure_roots(n);
+  ht.lap(H_ROOTS);
   // pop FIFO
   std::vector<Picked> picked;
   for (int i = 0; i < n_props && (int)picked.size() < max_nodes; ++i) {
@@ -795,6 +782,7 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
     for (int i = 0; i < M; ++i) slots[i] = picked[i].q.slot;
     // 1. re-bound layers after the split layer
     st->rows_rebounded = rebound(n, slots);
+    ht.lap(H_REBOUND);
     // 2. DeepPoly pass of the objective
     upload_batch(n, slots);
     {
@@ -807,6 +795,7 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
     std::vector<float> lb_dp(M);
     d2h(c, lb_dp.data(), n->lb, M);
     sync(c);
+    ht.lap(H_DEEPPOLY);
     // 3. projected Adam on the nodes DeepPoly does not verify
     std::vector<int> opt_idx;
     for (int i = 0; i < M; ++i)
@@ -843,12 +832,40 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
     upload_batch(n, slots);
     gather_best(n, M, best.data());
     sync(c);
+    ht.lap(H_OPTIMIZE);
+    // FP64 confirmation of every FP32 counterexample candidate, in one batch
+    std::vector<int> cand_o;
+    for (int o = 0; o < Mo; ++o)
+      if (f32[o] < 0.f && !(best[opt_idx[o]] > 0.f)) cand_o.push_back(o);
+    const int Mc = (int)cand_o.size();
+    std::vector<double> f64(Mc);
+    std::vector<float> xc((size_t)Mc * n->d0);
+    if (Mc > 0) {
+      std::vector<int> cs(Mc);
+      for (int k = 0; k < Mc; ++k) cs[k] = oslots[cand_o[k]];
+      h2d(c, n->cslots, cs.data(), Mc);
+      {
+        Scope sc(c, C_BOOK, 0.0, 8.0 * Mc * n->d0);
+        k_gather_rows<<<Mc, 128, 0, c->st>>>(Mc, n->cslots, n->pool.BESTX, n->d0, n->Xb, n->d0,
+                                             n->d0);
+      }
+      {
+        Scope sc(c, C_BOOK, 0.0, 8.0 * Mc * n->maxd);
+        launch_forward_f64(Mc, n->cslots, n->pool, c->d_props, n->nd, n->Xb, n->d0, n->f64a,
+                           n->f64b, n->maxd, n->f64out, c->st);
+      }
+      d2h(c, f64.data(), n->f64out, Mc);
+      d2h(c, xc.data(), n->Xb, (size_t)Mc * n->d0);
+      sync(c);
+    }
+    std::vector<int> cand_of(Mo, -1);
+    for (int k = 0; k < Mc; ++k) cand_of[cand_o[k]] = k;
+    ht.lap(H_CONFIRM);
     // host: verdicts, counterexample confirmation, children
     std::vector<int> par, lay, neu;
     std::vector<int> kidslots;
     std::vector<std::pair<int, int>> branch_of;  // (picked index, opt index)
     int oi = 0;
-    std::vector<float> xs(n->d0);
     for (int i = 0; i < M; ++i) {
       mnbab_prop* p = picked[i].p;
       const QNode& q = picked[i].q;
@@ -870,15 +887,13 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
         bool fals = false;
         if (optimised) {
           rec.f_xstar = f32[o];
-          if (f32[o] < 0.f) {
-            d2h(c, xs.data(), n->pool.BESTX + (size_t)q.slot * n->d0, n->d0);
-            sync(c);
-            const double f64 = host_forward(n, p, q.row, xs.data());
-            rec.f_xstar = (float)f64;
-            if (f64 < 0.0) {
+          const int k = cand_of[o];
+          if (k >= 0) {
+            rec.f_xstar = (float)f64[k];
+            if (f64[k] < 0.0) {
               fals = true;
               if (!p->done) {
-                p->cex = xs;
+                p->cex.assign(xc.begin() + (size_t)k * n->d0, xc.begin() + (size_t)(k + 1) * n->d0);
                 p->cex_row = q.row;
               }
             }
@@ -946,6 +961,7 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
       for (int b = 0; b < nb; ++b) free_slot(n, par[b]);
     }
   }
+  ht.lap(H_FINISH);
   // property completion
   for (int i = 0; i < n_props; ++i) {
     mnbab_prop* p = props[i];
@@ -1564,7 +1580,7 @@ mnbab_status mnbab_profile(mnbab_ctx* c, int32_t enable) {
   API_BEGIN(c)
   sync(c);
   if (enable) {
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < 32; ++i) {
       c->acc_n[i] = 0;
       c->acc_ms[i] = c->acc_flops[i] = c->acc_bytes[i] = 0.0;
     }
