@@ -319,13 +319,178 @@ __global__ void __launch_bounds__(128) k_conv_fwd(int M, const float* __restrict
   }
 }
 
+// Row-resident convolution kernels: one CTA per (row, chunk of output
+// positions).  The CTA stages its row's input in shared memory together with
+// the weights rearranged so that the channel block a thread accumulates is
+// contiguous (float4 loads), and each thread computes CB channels of one
+// output position.
+
+// smem floats of the row-resident transposed conv (input row + weights)
+static int convT_row_smem(const LayerDev& L) {
+  return L.co * L.ho * L.wo + L.co * L.k * L.k * L.ci;
+}
+
+template <int CB>
+__global__ void __launch_bounds__(256) k_convT_row(int M, const float* __restrict__ in, int ld_in,
+                                                   float* out, int ld_out, LayerDev L, Epi e,
+                                                   int pos_per_cta) {
+  extern __shared__ __align__(16) float sm[];
+  const int kk = L.k * L.k;
+  const int nIn = L.co * L.ho * L.wo;
+  float* Ws = sm;              // [co][kh][kw][ci]
+  float* Ls = sm + L.co * kk * L.ci;  // input row
+  const int m = blockIdx.y;
+  for (int i = threadIdx.x; i < L.co * kk * L.ci; i += blockDim.x) {
+    const int ci = i % L.ci, t = i / L.ci;  // t = (co * k + kh) * k + kw
+    const int co = t / kk, r = t % kk;
+    Ws[i] = L.W[((size_t)co * L.ci + ci) * kk + r];
+  }
+  const float* lam = in + (size_t)m * ld_in;
+  for (int i = threadIdx.x; i < nIn; i += blockDim.x) Ls[i] = lam[i];
+  __syncthreads();
+  const int Pin = L.hi * L.wi;
+  const int p0 = blockIdx.x * pos_per_cta;
+  const int np = min(pos_per_cta, Pin - p0);
+  const int nblk = (L.ci + CB - 1) / CB;
+  const int hwo = L.ho * L.wo;
+  float part = 0.f;
+  for (int item = threadIdx.x; item < np * nblk; item += blockDim.x) {
+    const int cb = item / np, pidx = p0 + item % np;
+    int ih, iw;
+    decode_phase(pidx, L.hi, L.wi, L.s, ih, iw);
+    float acc[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) acc[c] = 0.f;
+    const int kh0 = (ih + L.p) % L.s, kw0 = (iw + L.p) % L.s;
+    for (int kh = kh0; kh < L.k; kh += L.s) {
+      const int th = ih + L.p - kh;
+      if (th < 0) break;
+      const int oh = th / L.s;
+      if (oh >= L.ho) continue;
+      for (int kw = kw0; kw < L.k; kw += L.s) {
+        const int tw = iw + L.p - kw;
+        if (tw < 0) break;
+        const int ow = tw / L.s;
+        if (ow >= L.wo) continue;
+        const float* lp = Ls + oh * L.wo + ow;
+        const float* wp = Ws + (size_t)(kh * L.k + kw) * L.ci + cb * CB;
+        for (int co = 0; co < L.co; ++co) {
+          const float v = lp[co * hwo];
+          const float* w = wp + (size_t)co * kk * L.ci;
+          if (CB % 4 == 0 && (L.ci % 4) == 0) {
+#pragma unroll
+            for (int c = 0; c < CB; c += 4) {
+              const float4 w4 = *reinterpret_cast<const float4*>(w + c);
+              acc[c] = fmaf(v, w4.x, acc[c]);
+              acc[c + 1] = fmaf(v, w4.y, acc[c + 1]);
+              acc[c + 2] = fmaf(v, w4.z, acc[c + 2]);
+              acc[c + 3] = fmaf(v, w4.w, acc[c + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < CB; ++c)
+              if (cb * CB + c < L.ci) acc[c] = fmaf(v, w[c], acc[c]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+      const int ci = cb * CB + c;
+      if (ci >= L.ci) break;
+      const int j = ci * Pin + ih * L.wi + iw;
+      const float o = epi_apply(e, m, j, acc[c], part);
+      if (out) out[(size_t)m * ld_out + j] = o;
+    }
+  }
+  if (epi_has_part(e)) {
+    const float tot = block_sum(part);
+    if (threadIdx.x == 0) e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = tot;
+  }
+}
+
+static int conv_fwd_row_smem(const LayerDev& L) {
+  return L.ci * L.hi * L.wi + L.ci * L.k * L.k * L.co;
+}
+
+template <int CB>
+__global__ void __launch_bounds__(256) k_conv_fwd_row(int M, const float* __restrict__ in,
+                                                      int ld_in, float* out, int ld_out,
+                                                      LayerDev L, Epi e) {
+  extern __shared__ __align__(16) float sm[];
+  const int kk = L.k * L.k;
+  const int nIn = L.ci * L.hi * L.wi;
+  float* Ws = sm;                       // [ci][kh][kw][co]
+  float* Xs = sm + L.ci * kk * L.co;    // input row
+  const int m = blockIdx.x;
+  for (int i = threadIdx.x; i < L.ci * kk * L.co; i += blockDim.x) {
+    const int co = i % L.co, t = i / L.co;  // t = (ci * k + kh) * k + kw
+    const int ci = t / kk, r = t % kk;
+    Ws[i] = L.W[((size_t)co * L.ci + ci) * kk + r];
+  }
+  const float* x = in + (size_t)m * ld_in;
+  for (int i = threadIdx.x; i < nIn; i += blockDim.x) Xs[i] = x[i];
+  __syncthreads();
+  const int P = L.ho * L.wo;
+  const int nblk = (L.co + CB - 1) / CB;
+  const int hwi = L.hi * L.wi;
+  float part = 0.f;
+  for (int item = threadIdx.x; item < P * nblk; item += blockDim.x) {
+    const int cb = item / P, pos = item % P;
+    const int oh = pos / L.wo, ow = pos % L.wo;
+    float acc[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) acc[c] = 0.f;
+    for (int ci = 0; ci < L.ci; ++ci) {
+      for (int kh = 0; kh < L.k; ++kh) {
+        const int ih = oh * L.s - L.p + kh;
+        if (ih < 0 || ih >= L.hi) continue;
+        for (int kw = 0; kw < L.k; ++kw) {
+          const int iw = ow * L.s - L.p + kw;
+          if (iw < 0 || iw >= L.wi) continue;
+          const float v = Xs[ci * hwi + ih * L.wi + iw];
+          const float* w = Ws + (size_t)((ci * L.k + kh) * L.k + kw) * L.co + cb * CB;
+          if (CB % 4 == 0 && (L.co % 4) == 0) {
+#pragma unroll
+            for (int c = 0; c < CB; c += 4) {
+              const float4 w4 = *reinterpret_cast<const float4*>(w + c);
+              acc[c] = fmaf(v, w4.x, acc[c]);
+              acc[c + 1] = fmaf(v, w4.y, acc[c + 1]);
+              acc[c + 2] = fmaf(v, w4.z, acc[c + 2]);
+              acc[c + 3] = fmaf(v, w4.w, acc[c + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < CB; ++c)
+              if (cb * CB + c < L.co) acc[c] = fmaf(v, w[c], acc[c]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+      const int co = cb * CB + c;
+      if (co >= L.co) break;
+      const int j = co * P + pos;
+      const float o = epi_apply(e, m, j, acc[c] + L.b[co], part);
+      if (out) out[(size_t)m * ld_out + j] = o;
+    }
+  }
+  (void)part;  // forward epilogues (adjoint, ReLU) produce no offset partials
+}
+
 template <typename F>
 static void set_smem(F f, int bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+// positions per CTA of the row-resident transposed conv (one CTA per row unless
+// the output plane is large)
+static int convT_pos_per_cta(const LayerDev& L) { return L.hi * L.wi <= 4096 ? L.hi * L.wi : 1024; }
+
 int backsub_slots(const LayerDev& L) {
   if (L.kind == 1) return (L.d_in + 31) / 32;  // upper bound over the tile shapes
+  // upper bound over the row-resident (positions per CTA) and fallback (128) tilings
   return (L.hi * L.wi + 127) / 128;
 }
 
@@ -338,6 +503,22 @@ int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* 
       return launch_gemm_tc(M, L.d_in, L.d_out, in, ld_in, L.Wt, L.d_out, nullptr, 1, out, ld_out,
                             e, e.err, st);
     return gemm_launch(M, L.d_in, L.d_out, in, ld_in, L.W, L.d_in, nullptr, 1, out, ld_out, e, st);
+  }
+  const int rsm = convT_row_smem(L) * 4;
+  if (rsm <= 160 * 1024) {
+    const int ppc = convT_pos_per_cta(L);
+    dim3 grid((L.hi * L.wi + ppc - 1) / ppc, M);
+    if (L.ci <= 1) {
+      set_smem(k_convT_row<1>, rsm);
+      k_convT_row<1><<<grid, 256, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, ppc);
+    } else if (L.ci <= 4) {
+      set_smem(k_convT_row<4>, rsm);
+      k_convT_row<4><<<grid, 256, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, ppc);
+    } else {
+      set_smem(k_convT_row<16>, rsm);
+      k_convT_row<16><<<grid, 256, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, ppc);
+    }
+    return grid.x;
   }
   const int smem = L.co * L.ci * L.k * L.k * 4;
   dim3 grid((L.hi * L.wi + 127) / 128, M);
@@ -367,6 +548,17 @@ void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float*
       return;
     }
     gemm_launch(M, L.d_out, L.d_in, in, ld_in, L.Wt, L.d_out, L.b, 1, out, ld_out, e, st);
+    return;
+  }
+  const int rsm = conv_fwd_row_smem(L) * 4;
+  if (rsm <= 160 * 1024) {
+    if (L.co % 8 == 0 && L.ho * L.wo < 64) {
+      set_smem(k_conv_fwd_row<8>, rsm);
+      k_conv_fwd_row<8><<<M, 256, rsm, st>>>(M, in, ld_in, out, ld_out, L, e);
+    } else {
+      set_smem(k_conv_fwd_row<16>, rsm);
+      k_conv_fwd_row<16><<<M, 256, rsm, st>>>(M, in, ld_in, out, ld_out, L, e);
+    }
     return;
   }
   const int smem = L.co * L.ci * L.k * L.k * 4;
