@@ -63,8 +63,9 @@ typedef struct {
   int32_t node_capacity;       /* node slots per network pool; 0 = 65536 */
   int32_t max_mnc_rows;        /* gamma entries per node (sum over layers); 0 = none */
   int32_t row_chunk;           /* max back-substitution rows per launch; 0 = 32768, at most 65534 */
-  int32_t gemm_path;           /* dense FC steps: 0 = auto (tcgen05 3xTF32 from 128 rows up),
-                                  1 = SIMT FP32 only, 2 = tcgen05 3xTF32 always */
+  int32_t gemm_path;           /* dense FC steps: 0 = auto (tcgen05 3xTF32 when a launch fills
+                                  two waves of 128-row tiles, else SIMT FP32), 1 = SIMT FP32
+                                  only, 2 = tcgen05 3xTF32 always */
 } mnbab_options;
 
 /* Layer kinds.  A network is a chain affine, RELU, affine, ..., affine. */

@@ -5,6 +5,8 @@
 // splits).  All arithmetic is IEEE FP32 with FMA accumulation.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "epilogue.cuh"
@@ -36,7 +38,10 @@ __global__ void k_init_rows(NetDev net, int t, RowsDev rows, float* out, int ld,
   const int j = rows.j[m];
   const float sg = rows.sign ? rows.sign[m] : 1.f;
   const int width = net.d[t - 1];
-  const bool zero_passes = e.kind == EPI_RELU && !e.final_mode && !e.GP && !e.GPh && !e.AP;
+  // a = 0 contributes nothing and maps to 0 through an intermediate ReLU step
+  // (no beta / gamma terms) and through concretisation (x* not kept)
+  const bool zero_passes = (e.kind == EPI_RELU && !e.final_mode && !e.GP && !e.GPh && !e.AP) ||
+                           (e.kind == EPI_CONC && !e.X);
   float c0 = 0.f;
   float part = 0.f;
   if (t == net.R + 1) {
@@ -167,11 +172,95 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* 
   }
 }
 
-// 64 x 64 tiles unless that grid would leave most of the 152 SMs idle.
+// Split-K partial products: CTA z computes K range [z*kc, (z+1)*kc) of a
+// 32 x 32 tile into ws[z][m][n] (no epilogue).
+__global__ void __launch_bounds__(256) k_gemm_splitk(int M, int N, int K, int kc,
+                                                     const float* __restrict__ A, int lda,
+                                                     const float* __restrict__ B, int ldb,
+                                                     float* __restrict__ ws) {
+  __shared__ float As[GBK][32 + 4];
+  __shared__ float Bs[GBK][32 + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  for (int k0 = kb; k0 < ke; k0 += GBK) {
+    for (int q = tid; q < 32 * GBK; q += 256) {
+      const int r = q >> 4, cc = q & 15;
+      const int gm = m0 + r, gk = k0 + cc;
+      As[cc][r] = (gm < M && gk < ke) ? A[(size_t)gm * lda + gk] : 0.f;
+    }
+    for (int q = tid; q < 32 * GBK; q += 256) {
+      const int r = q >> 5, cc = q & 31;
+      const int gk = k0 + r, gn = n0 + cc;
+      Bs[r][cc] = (gk < ke && gn < N) ? B[(size_t)gk * ldb + gn] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      const float a0 = As[kk][ty], a1 = As[kk][ty + 16];
+      const float b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      acc[0][0] = fmaf(a0, b0, acc[0][0]);
+      acc[0][1] = fmaf(a0, b1, acc[0][1]);
+      acc[1][0] = fmaf(a1, b0, acc[1][0]);
+      acc[1][1] = fmaf(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  float* w = ws + (size_t)blockIdx.z * M * N;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+      if (m < M && n < N) w[(size_t)m * N + n] = acc[i][j];
+    }
+}
+
+// Sum of the split-K partials (fixed order) + bias, then the epilogue; a CTA
+// covers 8 rows x 32 columns, one warp per row, and writes one offset partial
+// per (row, 32-column tile).
+__global__ void __launch_bounds__(256) k_splitk_epi(int M, int N, int S, const float* __restrict__ ws,
+                                                    const float* __restrict__ bias, int bias_div,
+                                                    float* C, int ldc, Epi e) {
+  const int m = blockIdx.y * 8 + (threadIdx.x >> 5);
+  const int n = blockIdx.x * 32 + (threadIdx.x & 31);
+  float part = 0.f;
+  if (m < M && n < N) {
+    float v = 0.f;
+    for (int z = 0; z < S; ++z) v += ws[((size_t)z * M + m) * N + n];
+    if (bias) v += bias[n / bias_div];
+    const float o = epi_apply(e, m, n, v, part);
+    if (C) C[(size_t)m * ldc + n] = o;
+  }
+  if (epi_has_part(e)) {
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0 && m < M)
+      e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = part;
+  }
+}
+
+// 64 x 64 tiles unless that grid would leave most of the 152 SMs idle; then
+// 32 x 32 tiles, split along K when the K loop is long and the workspace fits.
 static int gemm_launch(int M, int N, int K, const float* A, int lda, const float* B, int ldb,
                        const float* bias, int bias_div, float* C, int ldc, const Epi& e,
                        cudaStream_t st) {
   const long big = (long)((N + 63) / 64) * ((M + 63) / 64);
+  const long small = (long)((N + 31) / 32) * ((M + 31) / 32);
+  if (big < 2 * 152 && small < 2 * 152 && K >= 256 && e.ws) {
+    int S = (int)std::min<long>(16, std::max<long>(2, (2 * 152 + small - 1) / small));
+    S = std::min(S, K / 64);
+    while (S > 1 && (size_t)S * M * N > e.ws_floats) --S;
+    if (S > 1) {
+      const int kc = ((K + S - 1) / S + GBK - 1) / GBK * GBK;
+      S = (K + kc - 1) / kc;
+      dim3 g1((N + 31) / 32, (M + 31) / 32, S);
+      k_gemm_splitk<<<g1, 256, 0, st>>>(M, N, K, kc, A, lda, B, ldb, e.ws);
+      dim3 g2((N + 31) / 32, (M + 7) / 8);
+      k_splitk_epi<<<g2, 256, 0, st>>>(M, N, S, e.ws, bias, bias_div, C, ldc, e);
+      return g2.x;
+    }
+  }
   if (big >= 2 * 152) {
     dim3 grid((N + 63) / 64, (M + 63) / 64);
     k_gemm<64, 64><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e);
@@ -488,6 +577,15 @@ static void set_smem(F f, int bytes) {
 // the output plane is large)
 static int convT_pos_per_cta(const LayerDev& L) { return L.hi * L.wi <= 4096 ? L.hi * L.wi : 1024; }
 
+// Tensor-core path: always when forced, and automatically when the problem
+// fills at least two waves of 128 x BN tiles on the 152 SMs.
+static bool use_tc(const Epi& e, int M, int N) {
+  if (e.gemm_path == 2) return true;
+  if (e.gemm_path != 0 || !e.err) return false;
+  const int bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+  return (long)((M + 127) / 128) * ((N + bn - 1) / bn) >= 2 * 152;
+}
+
 int backsub_slots(const LayerDev& L) {
   if (L.kind == 1) return (L.d_in + 31) / 32;  // upper bound over the tile shapes
   // upper bound over the row-resident (positions per CTA) and fallback (128) tilings
@@ -499,7 +597,7 @@ int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* 
   if (M <= 0) return backsub_slots(L);
   if (L.kind == 1) {
     // Lambda [M][d_out] x W [d_out][d_in]; the tensor-core kernel takes W as [d_in][d_out] = W^T
-    if (e.gemm_path == 2 || (e.gemm_path == 0 && M >= 128))
+    if (use_tc(e, M, L.d_in))
       return launch_gemm_tc(M, L.d_in, L.d_out, in, ld_in, L.Wt, L.d_out, nullptr, 1, out, ld_out,
                             e, e.err, st);
     return gemm_launch(M, L.d_in, L.d_out, in, ld_in, L.W, L.d_in, nullptr, 1, out, ld_out, e, st);
@@ -543,7 +641,7 @@ void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float*
   if (M <= 0) return;
   if (L.kind == 1) {
     // G [M][d_in] x W^T + b; the tensor-core kernel takes W [d_out][d_in] as is
-    if (e.gemm_path == 2 || (e.gemm_path == 0 && M >= 128)) {
+    if (use_tc(e, M, L.d_out)) {
       launch_gemm_tc(M, L.d_out, L.d_in, in, ld_in, L.W, L.d_in, L.b, 1, out, ld_out, e, e.err, st);
       return;
     }

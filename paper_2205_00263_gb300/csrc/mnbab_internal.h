@@ -97,6 +97,8 @@ struct Epi {
   int slot_base;
   int gemm_path;     // 0 auto, 1 SIMT, 2 tensor cores (dense FC steps)
   int* err;          // device error flag (bounded waits of the tensor-core kernel)
+  float* ws;         // split-K workspace (may be null: no split)
+  size_t ws_floats;
 };
 
 // ---- launchers (kernels.cu, tc_gemm.cu) ----------------------------------

@@ -82,6 +82,8 @@ struct mnbab_net {
   float *Gz = nullptr, *Hz = nullptr, *X = nullptr, *Xb = nullptr, *GG = nullptr, *gp0 = nullptr;
   float *fout = nullptr, *score = nullptr, *bestb = nullptr, *gmax = nullptr;
   double *f64a = nullptr, *f64b = nullptr, *f64out = nullptr;
+  float* splitk = nullptr;
+  size_t splitk_floats = 0;
   int* cslots = nullptr;
   int *bslots = nullptr, *brows = nullptr, *acs_layer = nullptr, *acs_neuron = nullptr,
       *acs_fb = nullptr, *kid_parent = nullptr, *kid_slots = nullptr, *kid_layer = nullptr,
@@ -329,6 +331,8 @@ Epi base_epi(mnbab_net* n, const int* row_node) {
   e.bias_div = 1;
   e.gemm_path = n->ctx->gemm_path;
   e.err = n->ctx->d_err;
+  e.ws = n->splitk;
+  e.ws_floats = n->splitk_floats;
   return e;
 }
 
@@ -688,6 +692,17 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   n->f64b = dalloc_t<double>(c, B * n->maxd);
   n->f64out = dalloc_t<double>(c, B);
   n->cslots = dalloc_t<int>(c, B);
+  // split-K workspace: 16 splits of a B x (widest FC layer) product
+  {
+    size_t wmax = 0;
+    for (int i = 1; i <= n->R; ++i)
+      if (n->nd.aff[i].kind == 1)
+        wmax = std::max(wmax, (size_t)std::max(n->nd.aff[i].d_in, n->nd.aff[i].d_out));
+    if (wmax) {
+      n->splitk_floats = 16 * B * wmax;
+      n->splitk = dalloc_t<float>(c, n->splitk_floats);
+    }
+  }
   n->bslots = dalloc_t<int>(c, B);
   n->brows = dalloc_t<int>(c, B);
   n->acs_layer = dalloc_t<int>(c, B);
