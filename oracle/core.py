@@ -403,11 +403,14 @@ class AdamHP:
     b1: float = 0.9
     b2: float = 0.999
     eps: float = 1e-8
-    # gradient components below grad_floor * (largest |component| of the node)
-    # count as zero: constraints that are tight at the relaxed point have
-    # gradients at rounding level, and Adam's per-component normalisation would
-    # turn that noise into full steps of random sign
-    grad_floor: float = 1e-5
+    # Adam's denominator uses eps_eff = max(eps, eps_rel * G) with G the node's
+    # largest |gradient component|.  Constraints that are tight at the relaxed
+    # point have gradients at rounding level; with a fixed tiny eps, Adam's
+    # per-component normalisation turns that noise into full steps of random
+    # sign.  Scaling eps with G keeps the update continuous in the gradient.
+    eps_rel: float = 1e-3
+    # optional hard dead-zone: components with |g| <= grad_floor * G count as 0
+    grad_floor: float = 0.0
 
 
 def bound_and_grad(net, node, alpha, beta, gamma, dense_mnc, lo, hi):
@@ -450,6 +453,7 @@ def optimize(net, node: Node, dense_mnc, lo, hi, hp: AdamHP):
         t = step + 1
         gmax = max([float(G[i].abs().max()) for G in (ga, gb, gg) for i in G if G[i].numel()] + [0.0])
         floor = hp.grad_floor * gmax
+        eps = max(hp.eps, hp.eps_rel * gmax)
         for G in (ga, gb, gg):
             for i in G:
                 G[i] = torch.where(G[i].abs() <= floor, torch.zeros_like(G[i]), G[i])
@@ -461,7 +465,7 @@ def optimize(net, node: Node, dense_mnc, lo, hi, hp: AdamHP):
                 state[(grp, i)] = (m, v)
                 mh = m / (1 - hp.b1 ** t)
                 vh = v / (1 - hp.b2 ** t)
-                P[i] = P[i] + lr[grp] * mh / (torch.sqrt(vh) + hp.eps)
+                P[i] = P[i] + lr[grp] * mh / (torch.sqrt(vh) + eps)
                 if grp == "a":
                     P[i] = torch.clamp(P[i], 0.0, 1.0)
                 else:
