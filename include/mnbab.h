@@ -92,11 +92,14 @@ typedef struct {
   int32_t steps;   /* gradient steps; the bound is evaluated steps + 1 times */
   float lr_alpha, lr_beta, lr_gamma;
   float beta1, beta2, eps;
-  /* gradient components with |g| <= grad_floor * max_j |g_j| (over all of a
-   * node's parameters) count as zero; default 1e-5.  Constraints tight at the
-   * relaxed point have gradients at rounding level, which Adam's
-   * per-component normalisation would otherwise turn into full steps. */
+  /* optional dead-zone: components with |g| <= grad_floor * G count as zero,
+   * G = max_j |g_j| over all of a node's parameters; default 0 (off) */
   float grad_floor;
+  /* Adam's denominator uses max(eps, eps_rel * G); default 1e-3.  Constraints
+   * tight at the relaxed point have gradients at rounding level, and with a
+   * fixed tiny eps the per-component normalisation turns that noise into full
+   * steps of random sign; scaling eps with G keeps the update continuous. */
+  float eps_rel;
 } mnbab_adam;
 
 typedef struct {

@@ -37,7 +37,7 @@ class LayerDesc(C.Structure):
 class Adam(C.Structure):
     _fields_ = [("steps", C.c_int32), ("lr_alpha", C.c_float), ("lr_beta", C.c_float),
                 ("lr_gamma", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("eps", C.c_float), ("grad_floor", C.c_float)]
+                ("eps", C.c_float), ("grad_floor", C.c_float), ("eps_rel", C.c_float)]
 
 
 class StepStats(C.Structure):

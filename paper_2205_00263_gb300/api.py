@@ -230,9 +230,9 @@ class Context:
         return lb, g[:, :SD], g[:, SD:2 * SD], g[:, 2 * SD:]
 
     def optimize(self, nodes, steps=20, lr_alpha=0.1, lr_beta=0.05, lr_gamma=0.05, beta1=0.9,
-                 beta2=0.999, eps=1e-8, grad_floor=1e-5):
+                 beta2=0.999, eps=1e-8, grad_floor=0.0, eps_rel=1e-3):
         ids, n = self._ids(nodes)
-        a = L.Adam(steps, lr_alpha, lr_beta, lr_gamma, beta1, beta2, eps, grad_floor)
+        a = L.Adam(steps, lr_alpha, lr_beta, lr_gamma, beta1, beta2, eps, grad_floor, eps_rel)
         best = np.empty(n, np.float32)
         self._ck(self.lib.mnbab_optimize(self.h, ids, n, C.byref(a), _fp(best)))
         return best
@@ -248,7 +248,8 @@ class Context:
     # ---- branch and bound ----------------------------------------------------
     def bab_step(self, props, max_nodes: int, steps: int = 20, adam: dict | None = None):
         arr = (C.c_void_p * len(props))(*[p.h.value for p in props])
-        a = L.Adam(steps, *(adam or {}).get("rates", (0.1, 0.05, 0.05, 0.9, 0.999, 1e-8, 1e-5)))
+        a = L.Adam(steps, *(adam or {}).get("rates", (0.1, 0.05, 0.05, 0.9, 0.999, 1e-8, 0.0,
+                                                       1e-3)))
         st = L.StepStats()
         self._ck(self.lib.mnbab_bab_step(self.h, arr, len(props), max_nodes, C.byref(a),
                                          C.byref(st)))

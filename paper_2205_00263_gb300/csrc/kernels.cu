@@ -893,11 +893,12 @@ __global__ void k_grad_max(int SD, int EC, const int* row_node, const PoolDev po
 __global__ void k_adam(int M, const int* row_node, PoolDev pool, const PropDev* props, int SD,
                        const float* GA, const float* GB, const float* GG, const float* gmax,
                        float floor, float lr_a, float lr_b, float lr_g, float b1, float b2,
-                       float eps, float bc1, float bc2) {
+                       float eps_abs, float eps_rel, float bc1, float bc2) {
   const int m = blockIdx.y;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = row_node[m];
   const float thr = floor * gmax[m];
+  const float eps = fmaxf(eps_abs, eps_rel * gmax[m]);
   auto dz = [thr](float g) { return fabsf(g) <= thr ? 0.f : g; };
   if (idx < SD) {
     const size_t q = (size_t)n * SD + idx;
@@ -925,14 +926,14 @@ __global__ void k_adam(int M, const int* row_node, PoolDev pool, const PropDev* 
 
 void launch_adam(int M, const int* row_node, PoolDev pool, const PropDev* props, int SD,
                  const float* GA, const float* GB, const float* GG, float* gmax, float floor,
-                 float lr_a, float lr_b, float lr_g, float b1, float b2, float eps, float bc1,
-                 float bc2, cudaStream_t st) {
+                 float lr_a, float lr_b, float lr_g, float b1, float b2, float eps, float eps_rel,
+                 float bc1, float bc2, cudaStream_t st) {
   if (M <= 0) return;
   k_grad_max<<<M, 256, 0, st>>>(SD, pool.EC, row_node, pool, props, GA, GB, GG, gmax);
   const int tot = 2 * SD + pool.EC;
   dim3 grid((tot + 255) / 256, M);
   k_adam<<<grid, 256, 0, st>>>(M, row_node, pool, props, SD, GA, GB, GG, gmax, floor, lr_a, lr_b,
-                               lr_g, b1, b2, eps, bc1, bc2);
+                               lr_g, b1, b2, eps, eps_rel, bc1, bc2);
 }
 
 __global__ void k_zero_adam(const int* row_node, PoolDev pool) {

@@ -134,11 +134,12 @@ void launch_gamma_proj(int M, const int* row_node, PoolDev pool, const PropDev* 
 void launch_gamma_grad(int M, const int* row_node, PoolDev pool, const PropDev* props,
                        const NetDev& net, const float* Gz, const float* Hz, float* GG,
                        cudaStream_t st);
-// Adam step with the gradient dead-zone |g| <= floor * max|g| of the row.
+// Adam step; with G = max|g| of the row: dead-zone |g| <= floor * G and
+// denominator eps max(eps, eps_rel * G).
 void launch_adam(int M, const int* row_node, PoolDev pool, const PropDev* props, int SD,
                  const float* GA, const float* GB, const float* GG, float* gmax, float floor,
-                 float lr_a, float lr_b, float lr_g, float b1, float b2, float eps, float bc1,
-                 float bc2, cudaStream_t st);
+                 float lr_a, float lr_b, float lr_g, float b1, float b2, float eps, float eps_rel,
+                 float bc1, float bc2, cudaStream_t st);
 void launch_zero_adam(int M, const int* row_node, PoolDev pool, cudaStream_t st);
 void launch_set_best(int M, const int* row_node, PoolDev pool, float v, cudaStream_t st);
 void launch_acs(int M, const int* row_node, PoolDev pool, const NetDev& net, const float* GP,

@@ -528,9 +528,8 @@ void run_optimize(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
     b2t *= a.beta2;
     Scope sc(c, C_ADAM, 0.0, 4.0 * M * (2.0 * n->SD + c->EC) * 8.0, 2);
     launch_adam(M, n->bslots, n->pool, c->d_props, n->SD, n->GA, n->GB, n->GG, n->gmax,
-                a.grad_floor, a.lr_alpha,
-                a.lr_beta, a.lr_gamma, a.beta1, a.beta2, a.eps, (float)(1.0 - b1t),
-                (float)(1.0 - b2t), c->st);
+                a.grad_floor, a.lr_alpha, a.lr_beta, a.lr_gamma, a.beta1, a.beta2, a.eps,
+                a.eps_rel, (float)(1.0 - b1t), (float)(1.0 - b2t), c->st);
   }
 }
 
@@ -577,7 +576,8 @@ mnbab_adam default_adam() {
   a.beta1 = 0.9f;
   a.beta2 = 0.999f;
   a.eps = 1e-8f;
-  a.grad_floor = 1e-5f;
+  a.grad_floor = 0.0f;
+  a.eps_rel = 1e-3f;
   return a;
 }
 
