@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--node-capacity", type=int, default=65536,
+                    help="node slots of the context (device memory ~ 122 KB per slot)")
+    ap.add_argument("--window", type=int, default=WINDOW, help="active properties")
     return ap.parse_args()
 
 
@@ -238,10 +241,11 @@ def run_ours(args):
     layers = synth.make_network(CFG)
     eps = synth.load_eps(CFG)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ctx = Context(device=local, stream=stream.cuda_stream, node_capacity=65536)
+    ctx = Context(device=local, stream=stream.cuda_stream, node_capacity=args.node_capacity)
     net = ctx.load_network(layers)
     start = rank * 1_000_000
-    win = Window(ctx, net, layers, eps, start, WINDOW, pool_size=WINDOW + 60 * (args.steps + args.warmup) + 50)
+    win = Window(ctx, net, layers, eps, start, args.window,
+                 pool_size=args.window + 60 * (args.steps + args.warmup) + 50)
 
     for _ in range(args.warmup):
         win.step()

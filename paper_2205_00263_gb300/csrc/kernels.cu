@@ -435,8 +435,29 @@ __global__ void __launch_bounds__(256) k_convT_row(int M, const float* __restric
     Ws[i] = L.W[((size_t)co * L.ci + ci) * kk + r];
   }
   const float* lam = in + (size_t)m * ld_in;
-  for (int i = threadIdx.x; i < nIn; i += blockDim.x) Ls[i] = lam[i];
+  // bounding box (over all channels) of the row's nonzero coefficients: rows
+  // that start at a convolution neuron are nonzero only in its receptive field
+  __shared__ int box[4];
+  if (threadIdx.x == 0) { box[0] = L.ho; box[1] = -1; box[2] = L.wo; box[3] = -1; }
   __syncthreads();
+  int bh0 = L.ho, bh1 = -1, bw0 = L.wo, bw1 = -1;
+  for (int i = threadIdx.x; i < nIn; i += blockDim.x) {
+    const float v = lam[i];
+    Ls[i] = v;
+    if (v != 0.f) {
+      const int r = i % (L.ho * L.wo), oh = r / L.wo, ow = r % L.wo;
+      bh0 = min(bh0, oh); bh1 = max(bh1, oh); bw0 = min(bw0, ow); bw1 = max(bw1, ow);
+    }
+  }
+  atomicMin(&box[0], bh0); atomicMax(&box[1], bh1); atomicMin(&box[2], bw0); atomicMax(&box[3], bw1);
+  __syncthreads();
+  // output positions that can be nonzero: ih in [oh0*s - p, oh1*s - p + k - 1]
+  const int ih_lo = box[0] * L.s - L.p, ih_hi = box[1] * L.s - L.p + L.k - 1;
+  const int iw_lo = box[2] * L.s - L.p, iw_hi = box[3] * L.s - L.p + L.k - 1;
+  // a zero coefficient maps to 0 with no offset contribution through these
+  // epilogues, so positions outside the window are written as 0 directly
+  const bool zero_passes = (e.kind == EPI_RELU && !e.final_mode && !e.GP && !e.GPh && !e.AP) ||
+                           (e.kind == EPI_CONC && !e.X);
   const int Pin = L.hi * L.wi;
   const int p0 = blockIdx.x * pos_per_cta;
   const int np = min(pos_per_cta, Pin - p0);
@@ -447,6 +468,12 @@ __global__ void __launch_bounds__(256) k_convT_row(int M, const float* __restric
     const int cb = item / np, pidx = p0 + item % np;
     int ih, iw;
     decode_phase(pidx, L.hi, L.wi, L.s, ih, iw);
+    if (zero_passes && (ih < ih_lo || ih > ih_hi || iw < iw_lo || iw > iw_hi)) {
+      if (out)
+        for (int c = 0; c < CB && cb * CB + c < L.ci; ++c)
+          out[(size_t)m * ld_out + (cb * CB + c) * Pin + ih * L.wi + iw] = 0.f;
+      continue;
+    }
     float acc[CB];
 #pragma unroll
     for (int c = 0; c < CB; ++c) acc[c] = 0.f;
