@@ -61,6 +61,21 @@ __global__ void k_init_rows(NetDev net, int t, RowsDev rows, float* out, int ld,
         const float o = epi_apply(e, m, col, sg * w[col], part);
         if (out) out[(size_t)m * ld + col] = o;
       }
+    } else if (!out && zero_passes) {
+      // only the kernel window of neuron j = (co, oh, ow) is nonzero and
+      // nothing is stored: walk the window
+      const int hw = L.ho * L.wo;
+      const int co = j / hw, oh = (j % hw) / L.wo, ow = j % L.wo;
+      c0 = sg * L.b[co];
+      const int h0 = oh * L.s - L.p, w0 = ow * L.s - L.p;
+      const int kk = L.k * L.k;
+      for (int q = threadIdx.x; q < L.ci * kk; q += blockDim.x) {
+        const int ci = q / kk, kh = (q % kk) / L.k, kw = q % L.k;
+        const int ih = h0 + kh, iw = w0 + kw;
+        if (ih < 0 || ih >= L.hi || iw < 0 || iw >= L.wi) continue;
+        const float a = sg * L.W[(((size_t)co * L.ci + ci) * L.k + kh) * L.k + kw];
+        epi_apply(e, m, (ci * L.hi + ih) * L.wi + iw, a, part);
+      }
     } else {
       // row j = (co, oh, ow) of the convolution's Toeplitz matrix
       const int hw = L.ho * L.wo;
@@ -408,31 +423,54 @@ __global__ void __launch_bounds__(128) k_conv_fwd(int M, const float* __restrict
   }
 }
 
-// Row-resident convolution kernels: one CTA per (row, chunk of output
-// positions).  The CTA stages its row's input in shared memory together with
-// the weights rearranged so that the channel block a thread accumulates is
-// contiguous (float4 loads), and each thread computes CB channels of one
-// output position.
+// Row-resident convolution kernels.  A CTA takes one row, one chunk of output
+// positions and one group of channel blocks.  It stages the row's input and
+// its slice of the weights (pre-arranged in global memory so that a channel
+// block is contiguous, float4 loads) in shared memory; each thread computes
+// CB channels of one output position.  Few rows are spread over more CTAs
+// (position chunks x channel groups) so that a launch fills the GPU.
+struct ConvSplit {
+  int ppc;   // positions per chunk
+  int npc;   // position chunks
+  int bpg;   // channel blocks per group
+  int ngrp;  // channel groups
+};
 
-// smem floats of the row-resident transposed conv (input row + weights)
-static int convT_row_smem(const LayerDev& L) {
-  return L.co * L.ho * L.wo + L.co * L.k * L.k * L.ci;
+static ConvSplit conv_split(int M, int P, int nblk) {
+  const int per_row = std::max(1, std::min(32, (4 * 152 + M - 1) / M));
+  ConvSplit cs;
+  cs.ngrp = std::min(nblk, per_row);
+  cs.bpg = (nblk + cs.ngrp - 1) / cs.ngrp;
+  cs.ngrp = (nblk + cs.bpg - 1) / cs.bpg;
+  cs.npc = std::max(1, std::min((per_row + cs.ngrp - 1) / cs.ngrp, (P + 31) / 32));
+  cs.npc = std::max(cs.npc, (P + 1023) / 1024);
+  cs.ppc = (P + cs.npc - 1) / cs.npc;
+  cs.npc = (P + cs.ppc - 1) / cs.ppc;
+  return cs;
+}
+
+static int convT_row_smem(const LayerDev& L, int cwidth) {
+  return L.co * L.ho * L.wo + L.co * L.k * L.k * cwidth;
 }
 
 template <int CB>
-__global__ void __launch_bounds__(256) k_convT_row(int M, const float* __restrict__ in, int ld_in,
+__global__ void __launch_bounds__(128) k_convT_row(int M, const float* __restrict__ in, int ld_in,
                                                    float* out, int ld_out, LayerDev L, Epi e,
-                                                   int pos_per_cta) {
+                                                   ConvSplit cs) {
   extern __shared__ __align__(16) float sm[];
   const int kk = L.k * L.k;
   const int nIn = L.co * L.ho * L.wo;
-  float* Ws = sm;              // [co][kh][kw][ci]
-  float* Ls = sm + L.co * kk * L.ci;  // input row
+  const int chunk = blockIdx.x % cs.npc, grp = blockIdx.x / cs.npc;
+  const int nblk = (L.ci + CB - 1) / CB;
+  const int b0 = grp * cs.bpg, b1 = min(nblk, b0 + cs.bpg);
+  const int c0 = b0 * CB, c1 = min(L.ci, b1 * CB);
+  const int cw = cs.bpg * CB;       // stride of the staged channel slice
+  float* Ws = sm;                   // [co][kh][kw][cw]
+  float* Ls = sm + L.co * kk * cw;  // input row
   const int m = blockIdx.y;
-  for (int i = threadIdx.x; i < L.co * kk * L.ci; i += blockDim.x) {
-    const int ci = i % L.ci, t = i / L.ci;  // t = (co * k + kh) * k + kw
-    const int co = t / kk, r = t % kk;
-    Ws[i] = L.W[((size_t)co * L.ci + ci) * kk + r];
+  for (int i = threadIdx.x; i < L.co * kk * cw; i += blockDim.x) {
+    const int c = i % cw, t = i / cw;
+    Ws[i] = (c0 + c < c1) ? L.Wb[(size_t)t * L.ci + c0 + c] : 0.f;
   }
   const float* lam = in + (size_t)m * ld_in;
   // bounding box (over all channels) of the row's nonzero coefficients: rows
@@ -459,13 +497,12 @@ __global__ void __launch_bounds__(256) k_convT_row(int M, const float* __restric
   const bool zero_passes = (e.kind == EPI_RELU && !e.final_mode && !e.GP && !e.GPh && !e.AP) ||
                            (e.kind == EPI_CONC && !e.X);
   const int Pin = L.hi * L.wi;
-  const int p0 = blockIdx.x * pos_per_cta;
-  const int np = min(pos_per_cta, Pin - p0);
-  const int nblk = (L.ci + CB - 1) / CB;
+  const int p0 = chunk * cs.ppc;
+  const int np = min(cs.ppc, Pin - p0);
   const int hwo = L.ho * L.wo;
   float part = 0.f;
-  for (int item = threadIdx.x; item < np * nblk; item += blockDim.x) {
-    const int cb = item / np, pidx = p0 + item % np;
+  for (int item = threadIdx.x; item < np * (b1 - b0); item += blockDim.x) {
+    const int cb = b0 + item / np, pidx = p0 + item % np;
     int ih, iw;
     decode_phase(pidx, L.hi, L.wi, L.s, ih, iw);
     if (zero_passes && (ih < ih_lo || ih > ih_hi || iw < iw_lo || iw > iw_hi)) {
@@ -478,6 +515,7 @@ __global__ void __launch_bounds__(256) k_convT_row(int M, const float* __restric
 #pragma unroll
     for (int c = 0; c < CB; ++c) acc[c] = 0.f;
     const int kh0 = (ih + L.p) % L.s, kw0 = (iw + L.p) % L.s;
+    const int coff = (cb - b0) * CB;
     for (int kh = kh0; kh < L.k; kh += L.s) {
       const int th = ih + L.p - kh;
       if (th < 0) break;
@@ -489,11 +527,11 @@ __global__ void __launch_bounds__(256) k_convT_row(int M, const float* __restric
         const int ow = tw / L.s;
         if (ow >= L.wo) continue;
         const float* lp = Ls + oh * L.wo + ow;
-        const float* wp = Ws + (size_t)(kh * L.k + kw) * L.ci + cb * CB;
+        const float* wp = Ws + (size_t)(kh * L.k + kw) * cw + coff;
         for (int co = 0; co < L.co; ++co) {
           const float v = lp[co * hwo];
-          const float* w = wp + (size_t)co * kk * L.ci;
-          if (CB % 4 == 0 && (L.ci % 4) == 0) {
+          const float* w = wp + (size_t)co * kk * cw;
+          if (CB % 4 == 0) {
 #pragma unroll
             for (int c = 0; c < CB; c += 4) {
               const float4 w4 = *reinterpret_cast<const float4*>(w + c);
@@ -504,8 +542,7 @@ __global__ void __launch_bounds__(256) k_convT_row(int M, const float* __restric
             }
           } else {
 #pragma unroll
-            for (int c = 0; c < CB; ++c)
-              if (cb * CB + c < L.ci) acc[c] = fmaf(v, w[c], acc[c]);
+            for (int c = 0; c < CB; ++c) acc[c] = fmaf(v, w[c], acc[c]);
           }
         }
       }
@@ -525,35 +562,41 @@ __global__ void __launch_bounds__(256) k_convT_row(int M, const float* __restric
   }
 }
 
-static int conv_fwd_row_smem(const LayerDev& L) {
-  return L.ci * L.hi * L.wi + L.ci * L.k * L.k * L.co;
+static int conv_fwd_row_smem(const LayerDev& L, int cwidth) {
+  return L.ci * L.hi * L.wi + L.ci * L.k * L.k * cwidth;
 }
 
 template <int CB>
-__global__ void __launch_bounds__(256) k_conv_fwd_row(int M, const float* __restrict__ in,
+__global__ void __launch_bounds__(128) k_conv_fwd_row(int M, const float* __restrict__ in,
                                                       int ld_in, float* out, int ld_out,
-                                                      LayerDev L, Epi e) {
+                                                      LayerDev L, Epi e, ConvSplit cs) {
   extern __shared__ __align__(16) float sm[];
   const int kk = L.k * L.k;
   const int nIn = L.ci * L.hi * L.wi;
-  float* Ws = sm;                       // [ci][kh][kw][co]
-  float* Xs = sm + L.ci * kk * L.co;    // input row
-  const int m = blockIdx.x;
-  for (int i = threadIdx.x; i < L.ci * kk * L.co; i += blockDim.x) {
-    const int co = i % L.co, t = i / L.co;  // t = (ci * k + kh) * k + kw
-    const int ci = t / kk, r = t % kk;
-    Ws[i] = L.W[((size_t)co * L.ci + ci) * kk + r];
+  const int chunk = blockIdx.x % cs.npc, grp = blockIdx.x / cs.npc;
+  const int nblk = (L.co + CB - 1) / CB;
+  const int b0 = grp * cs.bpg, b1 = min(nblk, b0 + cs.bpg);
+  const int c0 = b0 * CB, c1 = min(L.co, b1 * CB);
+  const int cw = cs.bpg * CB;
+  float* Ws = sm;                   // [ci][kh][kw][cw]
+  float* Xs = sm + L.ci * kk * cw;  // input row
+  const int m = blockIdx.y;
+  for (int i = threadIdx.x; i < L.ci * kk * cw; i += blockDim.x) {
+    const int c = i % cw, t = i / cw;
+    Ws[i] = (c0 + c < c1) ? L.Wf[(size_t)t * L.co + c0 + c] : 0.f;
   }
   const float* x = in + (size_t)m * ld_in;
   for (int i = threadIdx.x; i < nIn; i += blockDim.x) Xs[i] = x[i];
   __syncthreads();
   const int P = L.ho * L.wo;
-  const int nblk = (L.co + CB - 1) / CB;
+  const int p0 = chunk * cs.ppc;
+  const int np = min(cs.ppc, P - p0);
   const int hwi = L.hi * L.wi;
   float part = 0.f;
-  for (int item = threadIdx.x; item < P * nblk; item += blockDim.x) {
-    const int cb = item / P, pos = item % P;
+  for (int item = threadIdx.x; item < np * (b1 - b0); item += blockDim.x) {
+    const int cb = b0 + item / np, pos = p0 + item % np;
     const int oh = pos / L.wo, ow = pos % L.wo;
+    const int coff = (cb - b0) * CB;
     float acc[CB];
 #pragma unroll
     for (int c = 0; c < CB; ++c) acc[c] = 0.f;
@@ -565,8 +608,8 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row(int M, const float* __rest
           const int iw = ow * L.s - L.p + kw;
           if (iw < 0 || iw >= L.wi) continue;
           const float v = Xs[ci * hwi + ih * L.wi + iw];
-          const float* w = Ws + (size_t)((ci * L.k + kh) * L.k + kw) * L.co + cb * CB;
-          if (CB % 4 == 0 && (L.co % 4) == 0) {
+          const float* w = Ws + (size_t)((ci * L.k + kh) * L.k + kw) * cw + coff;
+          if (CB % 4 == 0) {
 #pragma unroll
             for (int c = 0; c < CB; c += 4) {
               const float4 w4 = *reinterpret_cast<const float4*>(w + c);
@@ -577,8 +620,7 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row(int M, const float* __rest
             }
           } else {
 #pragma unroll
-            for (int c = 0; c < CB; ++c)
-              if (cb * CB + c < L.co) acc[c] = fmaf(v, w[c], acc[c]);
+            for (int c = 0; c < CB; ++c) acc[c] = fmaf(v, w[c], acc[c]);
           }
         }
       }
@@ -600,9 +642,6 @@ static void set_smem(F f, int bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// positions per CTA of the row-resident transposed conv (one CTA per row unless
-// the output plane is large)
-static int convT_pos_per_cta(const LayerDev& L) { return L.hi * L.wi <= 4096 ? L.hi * L.wi : 1024; }
 
 // Tensor-core path: always when forced, and automatically when the problem
 // fills at least two waves of 128 x BN tiles on the 152 SMs.
@@ -615,8 +654,10 @@ static bool use_tc(const Epi& e, int M, int N) {
 
 int backsub_slots(const LayerDev& L) {
   if (L.kind == 1) return (L.d_in + 31) / 32;  // upper bound over the tile shapes
-  // upper bound over the row-resident (positions per CTA) and fallback (128) tilings
-  return (L.hi * L.wi + 127) / 128;
+  // upper bound over the row-resident splits (<= 32 CTAs per row, more for large
+  // planes) and the fallback tiling (128 positions per CTA)
+  const int P = L.hi * L.wi;
+  return std::max(32 * ((P + 1023) / 1024), (P + 127) / 128);
 }
 
 int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
@@ -629,21 +670,24 @@ int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* 
                             e, e.err, st);
     return gemm_launch(M, L.d_in, L.d_out, in, ld_in, L.W, L.d_in, nullptr, 1, out, ld_out, e, st);
   }
-  const int rsm = convT_row_smem(L) * 4;
-  if (rsm <= 160 * 1024) {
-    const int ppc = convT_pos_per_cta(L);
-    dim3 grid((L.hi * L.wi + ppc - 1) / ppc, M);
-    if (L.ci <= 1) {
-      set_smem(k_convT_row<1>, rsm);
-      k_convT_row<1><<<grid, 256, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, ppc);
-    } else if (L.ci <= 4) {
-      set_smem(k_convT_row<4>, rsm);
-      k_convT_row<4><<<grid, 256, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, ppc);
-    } else {
-      set_smem(k_convT_row<16>, rsm);
-      k_convT_row<16><<<grid, 256, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, ppc);
+  {
+    const int CBv = L.ci <= 1 ? 1 : (L.ci <= 4 ? 4 : 8);
+    const ConvSplit cs = conv_split(M, L.hi * L.wi, (L.ci + CBv - 1) / CBv);
+    const int rsm = convT_row_smem(L, cs.bpg * CBv) * 4;
+    if (rsm <= 160 * 1024 && L.Wb && cs.npc * cs.ngrp <= backsub_slots(L)) {
+      dim3 grid(cs.npc * cs.ngrp, M);
+      if (CBv == 1) {
+        set_smem(k_convT_row<1>, rsm);
+        k_convT_row<1><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
+      } else if (CBv == 4) {
+        set_smem(k_convT_row<4>, rsm);
+        k_convT_row<4><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
+      } else {
+        set_smem(k_convT_row<8>, rsm);
+        k_convT_row<8><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
+      }
+      return grid.x;
     }
-    return grid.x;
   }
   const int smem = L.co * L.ci * L.k * L.k * 4;
   dim3 grid((L.hi * L.wi + 127) / 128, M);
@@ -675,16 +719,21 @@ void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float*
     gemm_launch(M, L.d_out, L.d_in, in, ld_in, L.Wt, L.d_out, L.b, 1, out, ld_out, e, st);
     return;
   }
-  const int rsm = conv_fwd_row_smem(L) * 4;
-  if (rsm <= 160 * 1024) {
-    if (L.co % 8 == 0 && L.ho * L.wo < 64) {
-      set_smem(k_conv_fwd_row<8>, rsm);
-      k_conv_fwd_row<8><<<M, 256, rsm, st>>>(M, in, ld_in, out, ld_out, L, e);
-    } else {
-      set_smem(k_conv_fwd_row<16>, rsm);
-      k_conv_fwd_row<16><<<M, 256, rsm, st>>>(M, in, ld_in, out, ld_out, L, e);
+  {
+    const int CBv = (L.co % 8 == 0 && L.ho * L.wo >= 64) ? 8 : 4;
+    const ConvSplit cs = conv_split(M, L.ho * L.wo, (L.co + CBv - 1) / CBv);
+    const int rsm = conv_fwd_row_smem(L, cs.bpg * CBv) * 4;
+    if (rsm <= 160 * 1024 && L.Wf) {
+      dim3 grid(cs.npc * cs.ngrp, M);
+      if (CBv == 8) {
+        set_smem(k_conv_fwd_row<8>, rsm);
+        k_conv_fwd_row<8><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
+      } else {
+        set_smem(k_conv_fwd_row<4>, rsm);
+        k_conv_fwd_row<4><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
+      }
+      return;
     }
-    return;
   }
   const int smem = L.co * L.ci * L.k * L.k * 4;
   const int Pout = L.ho * L.wo;

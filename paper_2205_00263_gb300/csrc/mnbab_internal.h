@@ -20,6 +20,8 @@ struct LayerDev {
   const float* W;   // fc [d_out][d_in]; conv [co][ci][k][k]
   const float* Wt;  // fc only: [d_in][d_out]
   const float* b;   // [d_out] (fc) or [co] (conv)
+  const float* Wb;  // conv only: [co][kh][kw][ci] (back-substitution layout)
+  const float* Wf;  // conv only: [ci][kh][kw][co] (forward layout)
 };
 
 struct NetDev {

@@ -1154,6 +1154,22 @@ mnbab_status mnbab_load_network(mnbab_ctx* c, const mnbab_layer_desc* layers, in
     } else {
       if ((size_t)L.co * L.ci * L.k * L.k * 4 > 227 * 1024)
         fail(MNBAB_E_UNSUPPORTED, "convolution weights exceed shared memory");
+      // weights pre-arranged for the row-resident kernels: channel blocks contiguous
+      const int kk = L.k * L.k;
+      std::vector<float> Wb((size_t)L.co * kk * L.ci), Wfw((size_t)L.ci * kk * L.co);
+      for (int co = 0; co < L.co; ++co)
+        for (int ci = 0; ci < L.ci; ++ci)
+          for (int r = 0; r < kk; ++r) {
+            const float w = W[((size_t)co * L.ci + ci) * kk + r];
+            Wb[((size_t)co * kk + r) * L.ci + ci] = w;
+            Wfw[((size_t)ci * kk + r) * L.co + co] = w;
+          }
+      float* dWb = dalloc_t<float>(c, Wb.size());
+      float* dWf = dalloc_t<float>(c, Wfw.size());
+      h2d(c, dWb, Wb.data(), Wb.size());
+      h2d(c, dWf, Wfw.data(), Wfw.size());
+      L.Wb = dWb;
+      L.Wf = dWf;
     }
     if (i <= n->R) {
       nd.d[i] = L.d_out;
