@@ -62,10 +62,35 @@ def parse():
     ap.add_argument("--node-capacity", type=int, default=65536,
                     help="node slots of the context (device memory ~ 122 KB per slot)")
     ap.add_argument("--window", type=int, default=WINDOW, help="active properties")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch the optimisation loop kernel by kernel")
     return ap.parse_args()
 
 
 # ----------------------------------------------------------------------------
+# Replicas: ranks bound disjoint seeded property streams (no data-path
+# collective); the only exchange is the timing / node-count reduction.
+RANK_STRIDE = 1_000_000
+
+
+def rank_start(rank: int) -> int:
+    """First property index of a rank's stream (disjoint across ranks)."""
+    return rank * RANK_STRIDE
+
+
+def reduce_timing(ms: float, nodes: int, device="cpu"):
+    """(max of ms over ranks, sum of nodes over ranks); identity without a group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, nodes
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(nodes)], dtype=torch.float64, device=device)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -237,13 +262,17 @@ def run_ours(args):
         torch.distributed.barrier()
     from paper_2205_00263_gb300 import Context
 
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library launches on it (CUDA graphs cannot be
+    # captured on the legacy default stream) and the step events are recorded on it
+    stream = torch.cuda.Stream()
     layers = synth.make_network(CFG)
     eps = synth.load_eps(CFG)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ctx = Context(device=local, stream=stream.cuda_stream, node_capacity=args.node_capacity)
+    ap_graphs = not args.no_graphs
+    ctx = Context(device=local, stream=stream.cuda_stream, node_capacity=args.node_capacity,
+                  graphs=ap_graphs)
     net = ctx.load_network(layers)
-    start = rank * 1_000_000
+    start = rank_start(rank)
     win = Window(ctx, net, layers, eps, start, args.window,
                  pool_size=args.window + 60 * (args.steps + args.warmup) + 50)
 
@@ -260,7 +289,8 @@ def run_ours(args):
     ms = 0.0
     verdicts0 = dict(win.verdicts)
     for _ in range(args.steps):
-        flush.zero_()
+        with torch.cuda.stream(stream):
+            flush.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -274,16 +304,7 @@ def run_ours(args):
     clk = clocks.stop()
     stats, launches1 = ctx.profile_read()
     ctx.profile(False)
-    tot_ms = ms
-    tot_nodes = nodes
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-        n = torch.tensor([nodes], device="cuda", dtype=torch.float64)
-        dist.all_reduce(n, op=dist.ReduceOp.SUM)
-        tot_nodes = int(n.item())
+    tot_ms, tot_nodes = reduce_timing(ms, nodes, device="cuda")
     value = tot_nodes / (tot_ms * 1e-3)
 
     # plain: one subproblem per launch on fresh properties (same kernels, no batching)

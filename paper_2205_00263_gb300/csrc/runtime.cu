@@ -72,6 +72,7 @@ struct mnbab_net {
   std::vector<char> slot_used;
   // scratch
   int B = 0;          // batch capacity (objective rows)
+  int pad_slot = -1;  // scratch node for padded graph rows
   int chunk = 0;      // rows per back-substitution launch
   float *LamA = nullptr, *LamB = nullptr, *part = nullptr, *lb = nullptr;
   int *row_node = nullptr, *row_j = nullptr, *counter = nullptr;
@@ -138,6 +139,23 @@ struct mnbab_ctx {
   int64_t acc_n[32] = {0};
   double acc_ms[32] = {0}, acc_flops[32] = {0}, acc_bytes[32] = {0};
   int64_t h2d_bytes = 0, d2h_bytes = 0;
+  // CUDA graphs of the optimisation loop
+  bool graphs = true;
+  struct GraphEntry* cap = nullptr;  // entry being captured (Scope records into it)
+  std::vector<struct GraphEntry*> graph_cache;
+  std::vector<cudaEvent_t> graph_events;  // events owned by captured graphs
+};
+
+// A captured optimisation loop: its executable graph, the kernel-class work it
+// does per replay, and (when captured with profiling) its event pairs.
+struct GraphEntry {
+  int net_id, M, steps, gamma, prof;
+  float hp[8];
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+  int64_t n[32] = {0};
+  double flops[32] = {0}, bytes[32] = {0};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pairs;
 };
 
 namespace {
@@ -194,11 +212,15 @@ struct HostTimer {
 
 void resolve_prof(mnbab_ctx* c) {
   for (auto& r : c->pending) {
+    const bool owned = r.first >= 1000;  // event pair owned by a captured graph
+    const int cat = owned ? r.first - 1000 : r.first;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.second.first, r.second.second) == cudaSuccess)
-      c->acc_ms[r.first] += ms;
-    c->ev_free.push_back(r.second.first);
-    c->ev_free.push_back(r.second.second);
+      c->acc_ms[cat] += ms;
+    if (!owned) {
+      c->ev_free.push_back(r.second.first);
+      c->ev_free.push_back(r.second.second);
+    }
   }
   c->pending.clear();
 }
@@ -235,6 +257,23 @@ struct Scope {
   int cat;
   cudaEvent_t a = nullptr, b = nullptr;
   Scope(mnbab_ctx* c_, int cat_, double flops, double bytes, int nl = 1) : c(c_), cat(cat_) {
+    if (c->cap) {
+      // inside a graph capture: the work is counted per replay; with profiling the
+      // events become event-record nodes of the graph
+      GraphEntry* g = c->cap;
+      g->launches += nl;
+      g->n[cat] += nl;
+      g->flops[cat] += flops;
+      g->bytes[cat] += bytes;
+      if (g->prof) {
+        ck(cudaEventCreate(&a), "cudaEventCreate");
+        ck(cudaEventCreate(&b), "cudaEventCreate");
+        c->graph_events.push_back(a);
+        c->graph_events.push_back(b);
+        ck(cudaEventRecordWithFlags(a, c->st, cudaEventRecordExternal), "event record");
+      }
+      return;
+    }
     c->launches += nl;
     c->acc_n[cat] += nl;
     c->acc_flops[cat] += flops;
@@ -247,10 +286,14 @@ struct Scope {
     }
   }
   ~Scope() {
-    if (a) {
-      cudaEventRecord(b, c->st);
-      c->pending.push_back({cat, {a, b}});
+    if (!a) return;
+    if (c->cap) {
+      cudaEventRecordWithFlags(b, c->st, cudaEventRecordExternal);
+      c->cap->pairs.push_back({cat, {a, b}});
+      return;
     }
+    cudaEventRecord(b, c->st);
+    c->pending.push_back({cat, {a, b}});
   }
 };
 
@@ -504,7 +547,71 @@ void adjoint(mnbab_net* n, int M, bool has_gamma) {
   }
 }
 
+void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a);
+
+// The optimisation loop, replayed from a CUDA graph: the row count is padded up
+// to a multiple of 64 with rows that point at the network's pad slot (its state
+// is scratch: nothing reads it), so a handful of graphs cover every batch size.
 void run_optimize(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
+  mnbab_ctx* c = n->ctx;
+  if (!c->graphs || n->pad_slot < 0) {
+    run_optimize_body(n, M, has_gamma, a);
+    return;
+  }
+  const int Mb = std::min(n->B, (M + 63) / 64 * 64);
+  if (Mb > M) {
+    std::vector<int> pad(Mb - M, n->pad_slot), zr(Mb - M, 0);
+    h2d(c, n->bslots + M, pad.data(), pad.size());
+    h2d(c, n->brows + M, zr.data(), zr.size());
+  }
+  const float hp[8] = {a.lr_alpha, a.lr_beta, a.lr_gamma, a.beta1, a.beta2, a.eps, a.grad_floor,
+                       a.eps_rel};
+  GraphEntry* g = nullptr;
+  for (auto* e : c->graph_cache)
+    if (e->net_id == n->id && e->M == Mb && e->steps == a.steps && e->gamma == (int)has_gamma &&
+        e->prof == (int)c->prof && std::memcmp(e->hp, hp, sizeof(hp)) == 0)
+      g = e;
+  if (!g) {
+    g = new GraphEntry();
+    g->net_id = n->id;
+    g->M = Mb;
+    g->steps = a.steps;
+    g->gamma = has_gamma;
+    g->prof = c->prof;
+    std::memcpy(g->hp, hp, sizeof(hp));
+    cudaGraph_t graph = nullptr;
+    ck(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    c->cap = g;
+    try {
+      run_optimize_body(n, Mb, has_gamma, a);
+    } catch (...) {
+      c->cap = nullptr;
+      cudaStreamEndCapture(c->st, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      delete g;
+      throw;
+    }
+    c->cap = nullptr;
+    ck(cudaStreamEndCapture(c->st, &graph), "end capture");
+    const cudaError_t ie = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      delete g;
+      fail(MNBAB_E_DEVICE, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    }
+    c->graph_cache.push_back(g);
+  }
+  ck(cudaGraphLaunch(g->exec, c->st), "graph launch");
+  c->launches += g->launches;
+  for (int i = 0; i < 32; ++i) {
+    c->acc_n[i] += g->n[i];
+    c->acc_flops[i] += g->flops[i];
+    c->acc_bytes[i] += g->bytes[i];
+  }
+  for (auto& pr : g->pairs) c->pending.push_back({1000 + pr.first, pr.second});
+}
+
+void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
   mnbab_ctx* c = n->ctx;
   {
     Scope sc(c, C_BOOK, 0.0, 16.0 * M * (n->SD + c->EC));
@@ -654,6 +761,18 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   n->slot_row.assign(cap, 0);
   n->slot_prop.assign(cap, 0);
   n->slot_used.assign(cap, 0);
+  // pad slot: finite scratch state (l = u = 0, no splits, zero parameters)
+  n->pad_slot = alloc_slot(n);
+  {
+    const size_t o = (size_t)n->pad_slot * SD;
+    ck(cudaMemsetAsync(P.L + o, 0, SD * sizeof(float), c->st), "memset");
+    ck(cudaMemsetAsync(P.U + o, 0, SD * sizeof(float), c->st), "memset");
+    ck(cudaMemsetAsync(P.S + o, 0, SD, c->st), "memset");
+    ck(cudaMemsetAsync(P.ALPHA + o, 0, SD * sizeof(float), c->st), "memset");
+    ck(cudaMemsetAsync(P.BETA + o, 0, SD * sizeof(float), c->st), "memset");
+    ck(cudaMemsetAsync(P.prop + n->pad_slot, 0, sizeof(int), c->st), "memset");
+    ck(cudaMemsetAsync(P.row + n->pad_slot, 0, sizeof(int), c->st), "memset");
+  }
   // scratch
   n->B = std::min(1024, std::max(1, (int)cap / 2));
   n->chunk = std::max(2, c->row_chunk & ~1);
@@ -1031,6 +1150,8 @@ mnbab_status mnbab_create(const mnbab_options* opt, mnbab_ctx** out) {
   c->EC = std::max(0, o.max_mnc_rows);
   c->row_chunk = std::min(o.row_chunk > 0 ? o.row_chunk : 32768, 65534);
   c->gemm_path = (o.gemm_path >= 0 && o.gemm_path <= 2) ? o.gemm_path : 0;
+  // graphs cannot be captured on the legacy default stream
+  c->graphs = o.no_graphs == 0;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
     delete c;
@@ -1040,7 +1161,8 @@ mnbab_status mnbab_create(const mnbab_options* opt, mnbab_ctx** out) {
     delete c;
     return MNBAB_E_DEVICE;
   }
-  if (o.stream) {
+  if (o.stream && (cudaStream_t)o.stream != cudaStreamLegacy &&
+      (cudaStream_t)o.stream != cudaStreamPerThread) {
     c->st = (cudaStream_t)o.stream;
   } else {
     if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1069,6 +1191,11 @@ void mnbab_destroy(mnbab_ctx* c) {
     cudaEventDestroy(r.second.second);
   }
   for (auto e : c->ev_free) cudaEventDestroy(e);
+  for (auto* g : c->graph_cache) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    delete g;
+  }
+  for (auto e : c->graph_events) cudaEventDestroy(e);
   for (auto& a : c->allocs) cudaFree(a.first);
   for (auto* n : c->nets) delete n;
   for (auto* p : c->props) delete p;

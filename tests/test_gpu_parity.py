@@ -362,3 +362,29 @@ def test_batch_capacity_and_errors(Context, path):
             ctx.import_params(nodes[0], p)
         with pytest.raises(MnbabError):
             ctx.set_property(gnet, hi + 1, lo, C, d)   # empty box
+
+
+def test_graph_replay_matches_direct_launches(Context):
+    """The optimisation loop replayed from a captured CUDA graph (rows padded to
+    a multiple of 64) gives the same bounds and parameters as direct launches."""
+    layers, C, d, lo, hi, prep = fc_case(14, (37, 53, 29, 7), 0.12, with_mnc=True)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    E = sum(v.idx.shape[0] for v in m.values())
+    out = []
+    for graphs in (False, True, True):   # second graph run replays the cached graph
+        rng = np.random.default_rng(14)
+        with Context(node_capacity=128, max_mnc_rows=E, graphs=graphs) as ctx:
+            gnet, prop = gpu_property(ctx, layers, lo, hi, C, d, m)
+            gids = []
+            for k in range(11):
+                on = random_node(prep, rng, n_splits=k % 3, row=k % C.shape[0])
+                on.split_layer = net.R
+                gid = ctx.node_root(prop, on.row)
+                ctx.import_params(gid, to_params(on, net.R))
+                gids.append(gid)
+            best = ctx.optimize(gids, steps=20)
+            best2 = ctx.optimize(gids, steps=20)
+            out.append((best, best2, ctx.export_params(gids[3]).alpha))
+    for o in out[1:]:
+        assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
+        assert np.array_equal(o[2], out[0][2])
