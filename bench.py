@@ -62,8 +62,8 @@ def parse():
     ap.add_argument("--node-capacity", type=int, default=65536,
                     help="node slots of the context (device memory ~ 122 KB per slot)")
     ap.add_argument("--window", type=int, default=WINDOW, help="active properties")
-    ap.add_argument("--no-graphs", action="store_true",
-                    help="launch the optimisation loop kernel by kernel")
+    ap.add_argument("--graphs", action="store_true",
+                    help="replay the optimisation loop from captured CUDA graphs")
     return ap.parse_args()
 
 
@@ -268,7 +268,7 @@ def run_ours(args):
     layers = synth.make_network(CFG)
     eps = synth.load_eps(CFG)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ap_graphs = not args.no_graphs
+    ap_graphs = args.graphs
     ctx = Context(device=local, stream=stream.cuda_stream, node_capacity=args.node_capacity,
                   graphs=ap_graphs)
     net = ctx.load_network(layers)

@@ -66,8 +66,9 @@ typedef struct {
   int32_t gemm_path;           /* dense FC steps: 0 = auto (tcgen05 3xTF32 when a launch fills
                                   two waves of 128-row tiles, else SIMT FP32), 1 = SIMT FP32
                                   only, 2 = tcgen05 3xTF32 always */
-  int32_t no_graphs;           /* 1 = launch the optimisation loop kernel by kernel instead of
-                                  replaying captured CUDA graphs (needs a non-legacy stream) */
+  int32_t use_graphs;          /* 1 = replay the optimisation loop from captured CUDA graphs
+                                  (rows padded to multiples of 64, one graph per padded size);
+                                  0 = launch it kernel by kernel (default) */
 } mnbab_options;
 
 /* Layer kinds.  A network is a chain affine, RELU, affine, ..., affine. */

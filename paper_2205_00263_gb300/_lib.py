@@ -24,7 +24,7 @@ class Options(C.Structure):
     _fields_ = [("device", C.c_int32), ("hbm_budget_bytes", C.c_uint64), ("stream", C.c_void_p),
                 ("node_capacity", C.c_int32), ("max_mnc_rows", C.c_int32),
                 ("row_chunk", C.c_int32), ("gemm_path", C.c_int32),
-                ("no_graphs", C.c_int32)]
+                ("use_graphs", C.c_int32)]
 
 
 class LayerDesc(C.Structure):

@@ -97,10 +97,10 @@ class Context:
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, stream=None,
                  node_capacity: int = 0, max_mnc_rows: int = 0, row_chunk: int = 0,
-                 gemm_path: int = 0, graphs: bool = True):
+                 gemm_path: int = 0, graphs: bool = False):
         self.lib = L.load()
         o = L.Options(device, hbm_budget_bytes, stream, node_capacity, max_mnc_rows, row_chunk,
-                      gemm_path, 0 if graphs else 1)
+                      gemm_path, 1 if graphs else 0)
         h = C.c_void_p()
         st = self.lib.mnbab_create(C.byref(o), C.byref(h))
         if st != 0:

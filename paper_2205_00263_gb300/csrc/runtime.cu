@@ -140,7 +140,7 @@ struct mnbab_ctx {
   double acc_ms[32] = {0}, acc_flops[32] = {0}, acc_bytes[32] = {0};
   int64_t h2d_bytes = 0, d2h_bytes = 0;
   // CUDA graphs of the optimisation loop
-  bool graphs = true;
+  bool graphs = false;
   struct GraphEntry* cap = nullptr;  // entry being captured (Scope records into it)
   std::vector<struct GraphEntry*> graph_cache;
   std::vector<cudaEvent_t> graph_events;  // events owned by captured graphs
@@ -1150,8 +1150,7 @@ mnbab_status mnbab_create(const mnbab_options* opt, mnbab_ctx** out) {
   c->EC = std::max(0, o.max_mnc_rows);
   c->row_chunk = std::min(o.row_chunk > 0 ? o.row_chunk : 32768, 65534);
   c->gemm_path = (o.gemm_path >= 0 && o.gemm_path <= 2) ? o.gemm_path : 0;
-  // graphs cannot be captured on the legacy default stream
-  c->graphs = o.no_graphs == 0;
+  c->graphs = o.use_graphs != 0;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
     delete c;
