@@ -247,6 +247,15 @@ mnbab_status mnbab_bab_step(mnbab_ctx* ctx, mnbab_prop* const* props, int32_t n_
 /* Per-property node budget (bounded nodes including roots); default 256. */
 mnbab_status mnbab_set_budget(mnbab_ctx* ctx, mnbab_prop* prop, int32_t max_nodes);
 
+/* Branching score of a property (Sec. 3.2): mode 0 = ACS; mode 1 = ACS + CAB,
+ * the score divided by the cost of the split (App. B): with per-layer costs
+ * (affine: weight entries, or d_out k^2 for a convolution; ReLU: d + number
+ * of multi-neuron constraints) and C_t the cost of back-substituting from
+ * zhat_t, a split in ReLU layer k costs sum_{t>k} 2 d_t C_t plus one
+ * objective back-substitution (this library's addition, so that the last
+ * layer's cost is positive). */
+mnbab_status mnbab_set_branching(mnbab_ctx* ctx, mnbab_prop* prop, int32_t mode);
+
 /* Verdict of a property (row < 0) or of one row.  lb (nullable) = the lowest
  * open or leaf lower bound seen (+inf if verified).  x_cex (nullable, d0
  * floats) receives the counterexample when FALSIFIED. */

@@ -105,10 +105,14 @@ def bound_node(net, node: Node, dense, lo, hi, hp: AdamHP):
     return res, params
 
 
-def branch(net, node: Node, params, dense, lo, hi):
+def branch(net, node: Node, params, dense, lo, hi, cab=None):
+    """ACS split choice; with ``cab`` (layer costs from core.cab_costs) the
+    cost-adjusted score (Sec. 3.2) is used instead."""
     a, b, g = params
     _, _, aps = core.final_bound(net, node, a, b, g, dense, lo, hi, keep_ap=True)
     scores, fb = core.acs_scores(node, g, dense, aps)
+    if cab is not None:
+        scores = core.cab_scores(scores, cab)
     return core.pick_split(scores), fb
 
 
@@ -135,10 +139,13 @@ def children(node: Node, params, split, next_id: int):
 
 
 def verify(layers, C, d, lo, hi, max_nodes=256, hp: AdamHP | None = None, mnc_fn=None,
-           rows=None, prepared=None) -> PropResult:
-    """BaB on every row of one property; verdict VERIFIED / FALSIFIED / UNKNOWN."""
+           rows=None, prepared=None, cab=False) -> PropResult:
+    """BaB on every row of one property; verdict VERIFIED / FALSIFIED / UNKNOWN.
+    With ``cab`` the split is chosen by the cost-adjusted ACS score."""
     hp = hp or AdamHP()
     net, lo_t, hi_t, l, u, S, mnc, dense = prepared or prepare(layers, C, d, lo, hi, mnc_fn)
+    costs = core.cab_costs(net, {i: m.idx.shape[0] for i, m in mnc.items()} if mnc else None) \
+        if cab else None
     rows = list(range(net.aff[-1].d_out)) if rows is None else rows
     q = deque()
     nid = 0
@@ -152,7 +159,7 @@ def verify(layers, C, d, lo, hi, max_nodes=256, hp: AdamHP | None = None, mnc_fn
         nr, params = bound_node(net, node, dense, lo_t, hi_t, hp)
         res.n_bounded += 1
         if nr.verdict == UNKNOWN:
-            split, fb = branch(net, node, params, dense, lo_t, hi_t)
+            split, fb = branch(net, node, params, dense, lo_t, hi_t, costs)
             nr.fallback = fb
             if split is None:
                 unknown_leaf = True

@@ -512,6 +512,43 @@ def acs_scores(node: Node, gamma, dense_mnc, aps: dict):
     return fb, True
 
 
+def cab_costs(net: Net, n_mnc: dict | None = None) -> dict:
+    """Cost of splitting a neuron of ReLU layer k (App. B, cost-adjusted branching).
+
+    Per-layer costs: affine layer = number of weight entries (FC) or d_out k^2
+    (conv); ReLU layer = d + (number of multi-neuron constraints).  C_t = sum of
+    the costs of every layer below zhat_t; a split at layer k recomputes both
+    bounds of every neuron of the later ReLU layers: sum_{t>k} 2 d_t C_t.
+    Reading (the paper is silent): the cost of one objective back-substitution
+    C_obj (a single row, d_R weight entries in the last layer) is added so that
+    splits in the last ReLU layer have a positive cost.
+    """
+    n_mnc = n_mnc or {}
+    R = net.R
+
+    def aff_cost(A: Affine) -> float:
+        if A.kind == "fc":
+            return float(A.W.numel())
+        return float(A.d_out * A.W.shape[2] * A.W.shape[3])
+
+    C = {}
+    acc = 0.0
+    for t in range(1, R + 1):
+        acc += aff_cost(net.aff[t])
+        C[t] = acc                              # below zhat_t: aff_t, relu_{t-1}, ..., aff_1
+        acc += net.aff[t].d_out + n_mnc.get(t, 0)  # relu_t
+    c_obj = acc + net.aff[R].d_out if R >= 1 else acc   # one objective row through the last layer
+    costs = {}
+    for k in range(1, R + 1):
+        costs[k] = c_obj + sum(2.0 * net.aff[t].d_out * C[t] for t in range(k + 1, R + 1))
+    return costs
+
+
+def cab_scores(scores: dict, costs: dict) -> dict:
+    """ACS (or fallback) score divided by the cost of the split (Sec. 3.2, CAB)."""
+    return {i: scores[i] / costs[i] for i in scores}
+
+
 def pick_split(scores: dict):
     """Argmax with ties |s - max| <= 1e-5 * max broken by lowest (layer, index)."""
     mx = -math.inf

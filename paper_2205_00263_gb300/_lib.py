@@ -86,6 +86,7 @@ SIGNATURES = {
     "mnbab_bab_step": (status, [VP, C.POINTER(VP), C.c_int32, C.c_int32, C.POINTER(Adam),
                                 C.POINTER(StepStats)]),
     "mnbab_set_budget": (status, [VP, VP, C.c_int32]),
+    "mnbab_set_branching": (status, [VP, VP, C.c_int32]),
     "mnbab_get_verdict": (status, [VP, VP, C.c_int32, IP, FP, FP]),
     "mnbab_get_trace": (status, [VP, VP, C.POINTER(TraceRec), C.c_int32, IP]),
     "mnbab_queue_size": (status, [VP, VP, IP]),

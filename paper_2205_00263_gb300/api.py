@@ -183,6 +183,10 @@ class Context:
     def set_budget(self, prop: Prop, n: int):
         self._ck(self.lib.mnbab_set_budget(self.h, prop.h, n))
 
+    def set_branching(self, prop: Prop, cab: bool):
+        """ACS (cab=False) or cost-adjusted ACS (cab=True) for this property."""
+        self._ck(self.lib.mnbab_set_branching(self.h, prop.h, 1 if cab else 0))
+
     # ---- nodes ------------------------------------------------------------
     def node_root(self, prop: Prop, row: int) -> int:
         out = L.node_id()

@@ -1040,27 +1040,20 @@ void launch_set_best(int M, const int* row_node, PoolDev pool, float v, cudaStre
   k_set_best<<<(M + 255) / 256, 256, 0, st>>>(M, row_node, pool, v);
 }
 
-// ACS (Sec. 3.2) with the intercept fallback; ties within 1e-5 of the maximum
-// go to the lowest (layer, neuron).
-__global__ void k_acs(int M, const int* row_node, PoolDev pool, NetDev net, const float* GP,
-                      const float* GPh, const float* AP, int has_gamma, int* out_layer,
-                      int* out_neuron, float* out_score, int* out_fallback) {
+// ACS (Sec. 3.2) with the intercept fallback; with CAB the score is divided by
+// the cost of a split in the neuron's layer (the fallback decision is taken on
+// the raw scores).  Ties within 1e-5 of the maximum go to the lowest
+// (layer, neuron).
+__global__ void k_acs(int M, const int* row_node, PoolDev pool, const PropDev* props, NetDev net,
+                      const float* GP, const float* GPh, const float* AP, int has_gamma,
+                      int* out_layer, int* out_neuron, float* out_score, int* out_fallback) {
   const int m = blockIdx.x;
   const int n = row_node[m];
+  const PropDev& P = props[pool.prop[n]];
   const size_t nb = (size_t)n * pool.SD, mb = (size_t)m * net.SD;
   __shared__ float smax[32];
   __shared__ int sany[32];
   __shared__ int smin[32];
-  float mx = -INFINITY;
-  int any = 0;
-  for (int f = threadIdx.x; f < net.SD; f += blockDim.x) {
-    const float l = pool.L[nb + f], u = pool.U[nb + f];
-    if (l < 0.f && u > 0.f && pool.S[nb + f] == 0) {
-      any = 1;
-      const float s = has_gamma ? fabsf(GP[mb + f]) + fabsf(GPh[mb + f]) : 0.f;
-      mx = fmaxf(mx, s);
-    }
-  }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   auto bmax = [&](float v) {
     for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -1071,7 +1064,18 @@ __global__ void k_acs(int M, const int* row_node, PoolDev pool, NetDev net, cons
     for (int i = 0; i < nw; ++i) r = fmaxf(r, smax[i]);
     return r;
   };
-  mx = bmax(mx);
+  // candidates and whether any active-constraint score is positive
+  float raw = -INFINITY;
+  int any = 0;
+  for (int f = threadIdx.x; f < net.SD; f += blockDim.x) {
+    const float l = pool.L[nb + f], u = pool.U[nb + f];
+    if (l < 0.f && u > 0.f && pool.S[nb + f] == 0) {
+      any = 1;
+      const float sc = has_gamma ? fabsf(GP[mb + f]) + fabsf(GPh[mb + f]) : 0.f;
+      raw = fmaxf(raw, sc);
+    }
+  }
+  raw = bmax(raw);
   for (int o = 16; o; o >>= 1) any |= __shfl_xor_sync(0xffffffffu, any, o);
   if (lane == 0) sany[w] = any;
   __syncthreads();
@@ -1083,27 +1087,24 @@ __global__ void k_acs(int M, const int* row_node, PoolDev pool, NetDev net, cons
     }
     return;
   }
-  const int fallback = !(mx > 0.f);
-  if (fallback) {
-    mx = -INFINITY;
-    for (int f = threadIdx.x; f < net.SD; f += blockDim.x) {
-      const float l = pool.L[nb + f], u = pool.U[nb + f];
-      if (l < 0.f && u > 0.f && pool.S[nb + f] == 0) {
-        const float s = fabsf(AP[mb + f]) * ((-l * u) / (u - l));
-        mx = fmaxf(mx, s);
-      }
-    }
-    mx = bmax(mx);
+  const int fallback = !(raw > 0.f);
+  auto score = [&](int f, float l, float u) {
+    float sc = fallback ? fabsf(AP[mb + f]) * ((-l * u) / (u - l))
+                        : fabsf(GP[mb + f]) + fabsf(GPh[mb + f]);
+    if (P.cab) sc *= P.cab_inv[layer_of(net, f)];
+    return sc;
+  };
+  float mx = -INFINITY;
+  for (int f = threadIdx.x; f < net.SD; f += blockDim.x) {
+    const float l = pool.L[nb + f], u = pool.U[nb + f];
+    if (l < 0.f && u > 0.f && pool.S[nb + f] == 0) mx = fmaxf(mx, score(f, l, u));
   }
+  mx = bmax(mx);
   const float thr = mx - 1e-5f * fabsf(mx);
   int best = 0x7fffffff;
   for (int f = threadIdx.x; f < net.SD; f += blockDim.x) {
     const float l = pool.L[nb + f], u = pool.U[nb + f];
-    if (l < 0.f && u > 0.f && pool.S[nb + f] == 0) {
-      const float s = fallback ? fabsf(AP[mb + f]) * ((-l * u) / (u - l))
-                               : fabsf(GP[mb + f]) + fabsf(GPh[mb + f]);
-      if (s >= thr && f < best) best = f;
-    }
+    if (l < 0.f && u > 0.f && pool.S[nb + f] == 0 && score(f, l, u) >= thr && f < best) best = f;
   }
   for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
   __syncthreads();
@@ -1120,12 +1121,12 @@ __global__ void k_acs(int M, const int* row_node, PoolDev pool, NetDev net, cons
   }
 }
 
-void launch_acs(int M, const int* row_node, PoolDev pool, const NetDev& net, const float* GP,
-                const float* GPh, const float* AP, int has_gamma, int* out_layer, int* out_neuron,
-                float* out_score, int* out_fallback, cudaStream_t st) {
+void launch_acs(int M, const int* row_node, PoolDev pool, const PropDev* props, const NetDev& net,
+                const float* GP, const float* GPh, const float* AP, int has_gamma, int* out_layer,
+                int* out_neuron, float* out_score, int* out_fallback, cudaStream_t st) {
   if (M <= 0) return;
-  k_acs<<<M, 256, 0, st>>>(M, row_node, pool, net, GP, GPh, AP, has_gamma, out_layer, out_neuron,
-                            out_score, out_fallback);
+  k_acs<<<M, 256, 0, st>>>(M, row_node, pool, props, net, GP, GPh, AP, has_gamma, out_layer,
+                            out_neuron, out_score, out_fallback);
 }
 
 // Children of a split (Sec. 3.2, enforcing splits): copies of the parent with

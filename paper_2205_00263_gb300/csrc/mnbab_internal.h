@@ -50,6 +50,8 @@ struct PropDev {
   const float* bf;   // [n_rows]
   int n_rows;
   int E;             // gamma entries per node
+  int cab;           // 1: branching scores are divided by the split cost (CAB)
+  float cab_inv[MNBAB_MAXR + 1];  // 1 / cost of a split in ReLU layer i
   MncDev mnc[MNBAB_MAXR + 1];  // 1..R
 };
 
@@ -144,9 +146,9 @@ void launch_adam(int M, const int* row_node, PoolDev pool, const PropDev* props,
                  float bc1, float bc2, cudaStream_t st);
 void launch_zero_adam(int M, const int* row_node, PoolDev pool, cudaStream_t st);
 void launch_set_best(int M, const int* row_node, PoolDev pool, float v, cudaStream_t st);
-void launch_acs(int M, const int* row_node, PoolDev pool, const NetDev& net, const float* GP,
-                const float* GPh, const float* AP, int has_gamma, int* out_layer, int* out_neuron,
-                float* out_score, int* out_fallback, cudaStream_t st);
+void launch_acs(int M, const int* row_node, PoolDev pool, const PropDev* props, const NetDev& net,
+                const float* GP, const float* GPh, const float* AP, int has_gamma, int* out_layer,
+                int* out_neuron, float* out_score, int* out_fallback, cudaStream_t st);
 void launch_children(int nb, const int* parents, const int* kids, const int* layer,
                      const int* neuron, PoolDev pool, const NetDev& net, cudaStream_t st);
 // Root nodes: slots[i] initialised from root-bound slot srcs[i] for row rows[i].

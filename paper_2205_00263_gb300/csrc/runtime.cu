@@ -838,6 +838,28 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   }
 }
 
+// Cost of a split in each ReLU layer for cost-adjusted branching (App. B):
+// affine layers cost their weight entries (FC) or d_out k^2 (conv), a ReLU layer
+// d + #constraints; C_t sums the layers below zhat_t; a split at layer k costs
+// the re-bounding of every later layer (2 d_t C_t each) plus one objective row.
+void update_cab(mnbab_net* n, mnbab_prop* p) {
+  const int R = n->R;
+  double C[MNBAB_MAXR + 2] = {0};
+  double acc = 0.0;
+  for (int t = 1; t <= R; ++t) {
+    const HostLayer& L = n->host[t];
+    acc += L.kind == MNBAB_FC ? (double)L.ci * L.co : (double)L.co * L.ho * L.wo * L.k * L.k;
+    C[t] = acc;
+    acc += (double)n->nd.d[t] + (double)p->pd.mnc[t].e;
+  }
+  const double c_obj = acc + (R >= 1 ? (double)n->nd.d[R] : 0.0);
+  for (int k = 1; k <= R; ++k) {
+    double cost = c_obj;
+    for (int t = k + 1; t <= R; ++t) cost += 2.0 * n->nd.d[t] * C[t];
+    p->pd.cab_inv[k] = (float)(1.0 / cost);
+  }
+}
+
 // Root bounds of every property of the network admitted since the last call,
 // computed together in one re-bounding pass, then their row root nodes.
 void ensure_roots(mnbab_net* n) {
@@ -947,7 +969,8 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
       // 5. ACS at the final parameters (a' and gamma^T P of the last sweep)
       {
         Scope sc(c, C_ACS, 0.0, 4.0 * Mo * n->SD * (g ? 5.0 : 4.0));
-        launch_acs(Mo, n->bslots, n->pool, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0, n->acs_layer,
+        launch_acs(Mo, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0,
+                   n->acs_layer,
                    n->acs_neuron, n->score, n->acs_fb, c->st);
       }
       // 4. counterexample check at the best minimiser
@@ -1355,6 +1378,8 @@ mnbab_status mnbab_set_property(mnbab_ctx* c, const mnbab_net* cnet, const float
   h2d(c, dWf, Wf.data(), Wf.size());
   h2d(c, dbf, bf.data(), bf.size());
   pd.lo = dlo; pd.hi = dhi; pd.Wf = dWf; pd.bf = dbf; pd.n_rows = n_rows; pd.E = 0;
+  pd.cab = 0;
+  update_cab(n, p);
   c->props.push_back(p);
   upload_prop(c, p->index);
   p->row_open.assign(n_rows, 0);
@@ -1460,6 +1485,7 @@ mnbab_status mnbab_set_mnc(mnbab_ctx* c, mnbab_prop* p, int32_t layer, int32_t n
   }
   p->pd.E += n_rows;
   p->mnc_set[layer] = 1;
+  update_cab(n, p);
   upload_prop(c, p->index);
   sync(c);
   API_END(c)
@@ -1666,7 +1692,8 @@ mnbab_status mnbab_score_branches(mnbab_ctx* c, const mnbab_node_id* nodes, int3
   sweep(n, n->R + 1, obj_rows(n, nn), o);
   {
     Scope sc(c, C_ACS, 0.0, 4.0 * nn * n->SD * 5.0);
-    launch_acs(nn, n->bslots, n->pool, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0, n->acs_layer,
+    launch_acs(nn, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0,
+               n->acs_layer,
                n->acs_neuron, n->score, n->acs_fb, c->st);
   }
   d2h(c, layer_out, n->acs_layer, nn);
@@ -1689,6 +1716,15 @@ mnbab_status mnbab_set_budget(mnbab_ctx* c, mnbab_prop* p, int32_t max_nodes) {
   API_BEGIN(c)
   if (!p || max_nodes <= 0) fail(MNBAB_E_INVALID_ARG, "bad budget");
   p->budget = max_nodes;
+  API_END(c)
+}
+
+mnbab_status mnbab_set_branching(mnbab_ctx* c, mnbab_prop* p, int32_t mode) {
+  API_BEGIN(c)
+  if (!p || mode < 0 || mode > 1) fail(MNBAB_E_INVALID_ARG, "bad branching mode");
+  p->pd.cab = mode;
+  upload_prop(c, p->index);
+  sync(c);
   API_END(c)
 }
 

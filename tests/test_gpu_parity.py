@@ -179,13 +179,18 @@ def test_optimized_bound_matches_oracle(Context, path):
             _assert_close(best[k], ref, f"node {k} optimised bound")
 
 
-def test_acs_choice_matches_oracle(Context):
+@pytest.mark.parametrize("cab", [False, True])
+def test_acs_choice_matches_oracle(Context, cab):
+    """ACS (and, with cab, the cost-adjusted score of App. B) picks the same
+    split as the oracle, up to ties within the 1e-5 band."""
     layers, C, d, lo, hi, prep = fc_case(9, (37, 53, 29, 7), 0.12, with_mnc=True)
     net, lo_t, hi_t, l, u, S, m, dense = prep
     E = sum(v.idx.shape[0] for v in m.values())
+    costs = core.cab_costs(net, {i: v.idx.shape[0] for i, v in m.items()})
     rng = np.random.default_rng(9)
     with Context(node_capacity=128, max_mnc_rows=E) as ctx:
         gnet, prop = gpu_property(ctx, layers, lo, hi, C, d, m)
+        ctx.set_branching(prop, cab)
         for k in range(12):
             # half the nodes without active constraints: intercept fallback
             on = random_node(prep, rng, n_splits=k % 3, row=k % C.shape[0],
@@ -197,6 +202,8 @@ def test_acs_choice_matches_oracle(Context):
             _, _, aps = core.final_bound(net, on, on.alpha, on.beta, on.gamma, dense, lo_t, hi_t,
                                          keep_ap=True)
             scores, fb = core.acs_scores(on, on.gamma, dense, aps)
+            if cab:
+                scores = core.cab_scores(scores, costs)
             pick = core.pick_split(scores)
             assert pick is not None and lay[0] > 0
             _assert_close(sc[0], pick[2], f"node {k} max score")

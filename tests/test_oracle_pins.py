@@ -408,3 +408,25 @@ def test_children_keep_earlier_bounds():
         assert bool((ch.l[2] >= l[2] - 1e-12).all()) and bool((ch.u[2] <= u[2] + 1e-12).all())
     assert float(kids[0].u[1][j]) == 0.0 and int(kids[0].S[1][j]) == 1
     assert float(kids[1].l[1][j]) == 0.0 and int(kids[1].S[1][j]) == -1
+
+
+def test_cab_costs_by_hand():
+    """CAB costs (App. B): 2 -> 3 -> 4 -> 2 net with 5 and 7 constraint rows.
+    Layer costs: aff1 = 6, relu1 = 3 + 5, aff2 = 12, relu2 = 4 + 7; C_1 = 6,
+    C_2 = 6 + 8 + 12 = 26; objective row: 26 + 11 + 4 = 41.  Split at layer 1
+    recomputes layer 2: 41 + 2 * 4 * 26 = 249; split at layer 2: 41."""
+    L = [_fc(np.ones((3, 2)), np.zeros(3)), RELU, _fc(np.ones((4, 3)), np.zeros(4)), RELU,
+         _fc(np.ones((2, 4)), np.zeros(2))]
+    net = core.load_net(L)
+    costs = core.cab_costs(net, {1: 5, 2: 7})
+    assert costs == {1: 249.0, 2: 41.0}
+    # conv layers count d_out k^2
+    Lc = [dict(kind="conv", W=np.ones((2, 1, 3, 3), np.float32), b=np.zeros(2, np.float32),
+               stride=1, pad=0, in_shape=(1, 5, 5), out_shape=(2, 3, 3)), RELU,
+          _fc(np.ones((4, 18)), np.zeros(4)), RELU, _fc(np.ones((2, 4)), np.zeros(2))]
+    c2 = core.cab_costs(core.load_net(Lc))
+    # aff1 = 18 * 9 = 162, relu1 = 18, aff2 = 72 -> C_2 = 252; objective 252 + 4 + 4 = 260
+    assert c2 == {1: 260.0 + 2 * 4 * 252, 2: 260.0}
+    sc = {1: torch.tensor([1.0, 2.0]), 2: torch.tensor([0.5, 0.1])}
+    cab = core.cab_scores(sc, {1: 10.0, 2: 1.0})
+    assert core.pick_split(cab)[:2] == (2, 0)
