@@ -61,7 +61,13 @@ def calibrate(cfg: int, n_props: int | None = None, iters: int = 20, frac: float
 
 
 def main(argv):
-    cfgs = [int(a) for a in argv] or [0, 1]
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cfgs", nargs="*", type=int, default=[0, 1])
+    ap.add_argument("--n", type=int, default=None, help="properties (default: the config's)")
+    ap.add_argument("--iters", type=int, default=20)
+    a = ap.parse_args(argv)
+    cfgs = a.cfgs
     try:
         with open(synth.EPS_FILE) as f:
             data = json.load(f)
@@ -69,10 +75,12 @@ def main(argv):
         data = {}
     for c in cfgs:
         t = time.time()
-        r = calibrate(c)
+        r = calibrate(c, n_props=a.n, iters=a.iters)
         r["seconds"] = round(time.time() - t, 1)
         data[str(c)] = r
         print(c, r["eps"], r["seconds"], flush=True)
+        with open(synth.EPS_FILE) as f:   # other calibrations may have finished meanwhile
+            data.update({k: v for k, v in json.load(f).items() if k != str(c)})
         with open(synth.EPS_FILE, "w") as f:
             json.dump(data, f, indent=1)
 
