@@ -436,10 +436,15 @@ struct ConvSplit {
   int ngrp;  // channel groups
 };
 
-static ConvSplit conv_split(int M, int P, int nblk) {
+// smem_of(channel width) gives the staged floats for a slice of that width;
+// groups are added until the slice fits in `limit` floats.
+template <typename F>
+static ConvSplit conv_split(int M, int P, int nblk, int CB, F smem_of, int limit) {
   const int per_row = std::max(1, std::min(32, (4 * 152 + M - 1) / M));
   ConvSplit cs;
-  cs.ngrp = std::min(nblk, per_row);
+  int min_grp = 1;
+  while (min_grp < nblk && smem_of(((nblk + min_grp - 1) / min_grp) * CB) > limit) ++min_grp;
+  cs.ngrp = std::max(min_grp, std::min(nblk, per_row));
   cs.bpg = (nblk + cs.ngrp - 1) / cs.ngrp;
   cs.ngrp = (nblk + cs.bpg - 1) / cs.bpg;
   cs.npc = std::max(1, std::min((per_row + cs.ngrp - 1) / cs.ngrp, (P + 31) / 32));
@@ -652,6 +657,13 @@ static bool use_tc(const Epi& e, int M, int N) {
   return (long)((M + 127) / 128) * ((N + bn - 1) / bn) >= 2 * 152;
 }
 
+// Whether the row-resident conv kernels can stage this layer (input row plus the
+// narrowest weight slice within 40 K floats = 160 KB of shared memory).
+bool conv_supported(const LayerDev& L) {
+  const int cbT = L.ci <= 1 ? 1 : (L.ci <= 4 ? 4 : 8);
+  return convT_row_smem(L, cbT) <= 40 * 1024 && conv_fwd_row_smem(L, 4) <= 40 * 1024;
+}
+
 int backsub_slots(const LayerDev& L) {
   if (L.kind == 1) return (L.d_in + 31) / 32;  // upper bound over the tile shapes
   // upper bound over the row-resident splits (<= 32 CTAs per row, more for large
@@ -672,7 +684,8 @@ int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* 
   }
   {
     const int CBv = L.ci <= 1 ? 1 : (L.ci <= 4 ? 4 : 8);
-    const ConvSplit cs = conv_split(M, L.hi * L.wi, (L.ci + CBv - 1) / CBv);
+    const ConvSplit cs = conv_split(M, L.hi * L.wi, (L.ci + CBv - 1) / CBv, CBv,
+                                    [&](int cw) { return convT_row_smem(L, cw); }, 40 * 1024);
     const int rsm = convT_row_smem(L, cs.bpg * CBv) * 4;
     if (rsm <= 160 * 1024 && L.Wb && cs.npc * cs.ngrp <= backsub_slots(L)) {
       dim3 grid(cs.npc * cs.ngrp, M);
@@ -721,7 +734,8 @@ void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float*
   }
   {
     const int CBv = (L.co % 8 == 0 && L.ho * L.wo >= 64) ? 8 : 4;
-    const ConvSplit cs = conv_split(M, L.ho * L.wo, (L.co + CBv - 1) / CBv);
+    const ConvSplit cs = conv_split(M, L.ho * L.wo, (L.co + CBv - 1) / CBv, CBv,
+                                    [&](int cw) { return conv_fwd_row_smem(L, cw); }, 40 * 1024);
     const int rsm = conv_fwd_row_smem(L, cs.bpg * CBv) * 4;
     if (rsm <= 160 * 1024 && L.Wf) {
       dim3 grid(cs.npc * cs.ngrp, M);

@@ -120,6 +120,8 @@ void launch_init_rows(const NetDev& net, int t, const RowsDev& rows, float* out,
 int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
                    const Epi& e, cudaStream_t st);
 int backsub_slots(const LayerDev& L);
+// Whether the conv kernels can stage the layer in shared memory.
+bool conv_supported(const LayerDev& L);
 // Forward through affine layer i (+ bias): in [M][d_{i-1}] -> out [M][d_i].
 void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
                     const Epi& e, cudaStream_t st);

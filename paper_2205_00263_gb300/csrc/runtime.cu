@@ -1301,8 +1301,8 @@ mnbab_status mnbab_load_network(mnbab_ctx* c, const mnbab_layer_desc* layers, in
       h2d(c, dWt, Wt.data(), Wt.size());
       L.Wt = dWt;
     } else {
-      if ((size_t)L.co * L.ci * L.k * L.k * 4 > 227 * 1024)
-        fail(MNBAB_E_UNSUPPORTED, "convolution weights exceed shared memory");
+      if (!conv_supported(L))
+        fail(MNBAB_E_UNSUPPORTED, "convolution row does not fit in shared memory");
       // weights pre-arranged for the row-resident kernels: channel blocks contiguous
       const int kk = L.k * L.k;
       std::vector<float> Wb((size_t)L.co * kk * L.ci), Wfw((size_t)L.ci * kk * L.co);

@@ -41,12 +41,22 @@ def conv_spec(seed):
                         ("fc", 13), ("relu",), ("fc", 4)])
 
 
-def conv_case(seed, eps):
-    spec = conv_spec(seed)
+def convbig_spec(seed):
+    """The conv-big layer pattern (3x3 s1 p1, 4x4 s2 p1; 32 and 64 channels) on
+    a 3x12x12 input: the 64 -> 64 4x4 layer's weights (256 KB) exceed shared
+    memory, so the kernels must stage them in channel slices."""
+    return dict(seed=seed, in_shape=(3, 12, 12),
+                layers=[("conv", 32, 3, 1, 1), ("relu",), ("conv", 32, 4, 2, 1), ("relu",),
+                        ("conv", 64, 3, 1, 1), ("relu",), ("conv", 64, 4, 2, 1), ("relu",),
+                        ("fc", 50), ("relu",), ("fc", 10)])
+
+
+def conv_case(seed, eps, spec_fn=None):
+    spec = (spec_fn or conv_spec)(seed)
     layers = synth.make_network(spec)
     x0 = synth.make_image(seed + 7, spec["in_shape"]).reshape(-1)
     y = synth.net_forward(layers, x0)
-    C, d = synth.property_rows(int(np.argmax(y)), 4)
+    C, d = synth.property_rows(int(np.argmax(y)), y.shape[0])
     lo, hi = synth.input_box(x0, eps)
     prep = bab.prepare(layers, C, d, lo, hi)
     return layers, C, d, lo, hi, prep

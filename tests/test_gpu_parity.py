@@ -11,7 +11,8 @@ import pytest
 import torch
 
 import synth
-from helpers import TOL, close, concat, conv_case, fc_case, f32, gpu_property, random_node, to_params
+from helpers import (TOL, close, concat, conv_case, convbig_spec, fc_case, f32, gpu_property,
+                     random_node, to_params)
 from oracle import bab, core, mnc
 
 pytestmark = pytest.mark.gpu
@@ -39,12 +40,14 @@ def _assert_close(g, o, what, tol=TOL):
 # root bounds (DeepPoly back-substitution of every neuron, both sides)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("path", [1, 2])
-@pytest.mark.parametrize("case", ["ragged_fc", "conv", "cfg0"])
+@pytest.mark.parametrize("case", ["ragged_fc", "conv", "convbig", "cfg0"])
 def test_root_bounds(Context, case, path):
     if case == "ragged_fc":
         layers, C, d, lo, hi, prep = fc_case(1, (37, 53, 29, 7), 0.1)
     elif case == "conv":
         layers, C, d, lo, hi, prep = conv_case(2, 0.05)
+    elif case == "convbig":
+        layers, C, d, lo, hi, prep = conv_case(3, 0.01, convbig_spec)
     else:
         layers = synth.make_network(0)
         pr = synth.make_properties(0, layers, n=1, eps=synth.load_eps(0))[0]
@@ -63,12 +66,14 @@ def test_root_bounds(Context, case, path):
 # fixed parameters: re-bounding after splits and the objective bound
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("path", [1, 2])
-@pytest.mark.parametrize("case", ["fc_mnc", "conv"])
+@pytest.mark.parametrize("case", ["fc_mnc", "conv", "convbig"])
 def test_rebound_and_bound_at_fixed_parameters(Context, case, path):
     if case == "fc_mnc":
         layers, C, d, lo, hi, prep = fc_case(3, (37, 53, 29, 7), 0.12, with_mnc=True)
-    else:
+    elif case == "conv":
         layers, C, d, lo, hi, prep = conv_case(4, 0.08)
+    else:
+        layers, C, d, lo, hi, prep = conv_case(5, 0.01, convbig_spec)
     net, lo_t, hi_t, l, u, S, m, dense = prep
     E = sum(v.idx.shape[0] for v in m.values()) if m else 0
     rng = np.random.default_rng(11)
@@ -120,12 +125,14 @@ def test_deeppoly_pass(Context):
 # adjoint: gradient of the bound w.r.t. alpha, beta, gamma
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("path", [1, 2])
-@pytest.mark.parametrize("case", ["fc_mnc", "conv"])
+@pytest.mark.parametrize("case", ["fc_mnc", "conv", "convbig"])
 def test_gradient_matches_oracle(Context, case, path):
     if case == "fc_mnc":
         layers, C, d, lo, hi, prep = fc_case(6, (37, 53, 29, 7), 0.12, with_mnc=True)
-    else:
+    elif case == "conv":
         layers, C, d, lo, hi, prep = conv_case(7, 0.08)
+    else:
+        layers, C, d, lo, hi, prep = conv_case(8, 0.01, convbig_spec)
     net, lo_t, hi_t, l, u, S, m, dense = prep
     E = sum(v.idx.shape[0] for v in m.values()) if m else 0
     SD = sum(l[i].numel() for i in l)
