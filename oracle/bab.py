@@ -146,7 +146,7 @@ def verify(layers, C, d, lo, hi, max_nodes=256, hp: AdamHP | None = None, mnc_fn
     net, lo_t, hi_t, l, u, S, mnc, dense = prepared or prepare(layers, C, d, lo, hi, mnc_fn)
     costs = core.cab_costs(net, {i: m.idx.shape[0] for i, m in mnc.items()} if mnc else None) \
         if cab else None
-    rows = list(range(net.aff[-1].d_out)) if rows is None else rows
+    rows = list(range(net.width(net.R + 1))) if rows is None else rows
     q = deque()
     nid = 0
     for r in rows:

@@ -28,7 +28,7 @@ def deeppoly_verifies(net, lo, hi) -> bool:
     l, u, S = core.root_bounds(net, lo_t, hi_t)
     relax = {i: core.deeppoly_relax(l[i], u[i], S[i]) for i in l}
     R = net.R
-    E = torch.eye(net.aff[R + 1].d_out, dtype=DT)
+    E = torch.eye(net.width(R + 1), dtype=DT)
     lb, _, _ = core.backsub_rows(net, R + 1, E, relax, lo_t, hi_t)
     return bool((lb > 0).all())
 

@@ -106,55 +106,92 @@ class Affine:
 
 @dataclass
 class Net:
-    aff: list            # aff[0] unused; aff[1..R+1]
+    """ReLU network as a DAG of affine edges: zhat^(t) = sum over the edges
+    (s, A) into t of A(z^(s)), with z^(0) = x; ReLU layers t = 1..R, the output
+    is node R + 1.  A chain has one edge (t - 1, aff[t]) per node; residual
+    networks (ResAdd) have two edges into the sum after a block."""
+    edges: list          # edges[t] = [(s, Affine), ...], t = 1..R+1 (edges[0] unused)
+
     @property
     def R(self) -> int:
-        return len(self.aff) - 2
+        return len(self.edges) - 2
+
+    @property
+    def aff(self) -> list:
+        """First edge of every node (the whole network for a chain)."""
+        return [None] + [self.edges[t][0][1] for t in range(1, len(self.edges))]
+
+    def width(self, t: int) -> int:
+        return self.edges[t][0][1].d_out
 
     def dims(self) -> list[int]:
         """d_i of each ReLU layer i = 1..R (index 0 is the input)."""
-        return [self.aff[1].d_in] + [self.aff[i].d_out for i in range(1, self.R + 1)]
+        d0 = [A.d_in for (s, A) in self.edges[1] if s == 0][0]
+        return [d0] + [self.width(i) for i in range(1, self.R + 1)]
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
         """Exact network output f(x) for rows of x (Eq. 1 constraints)."""
-        h = x
-        for i in range(1, self.R + 2):
-            h = self.aff[i].forward(h)
-            if i <= self.R:
-                h = torch.clamp(h, min=0.0)
-        return h
+        z = {0: x}
+        for t in range(1, self.R + 2):
+            h = sum(A.forward(z[s]) for s, A in self.edges[t])
+            z[t] = torch.clamp(h, min=0.0) if t <= self.R else h
+        return z[self.R + 1]
+
+
+def _affine(L) -> Affine:
+    W = torch.as_tensor(np.asarray(L["W"]), dtype=DT)
+    b = torch.as_tensor(np.asarray(L["b"]), dtype=DT)
+    if L["kind"] == "fc":
+        return Affine("fc", W, b)
+    return Affine("conv", W, b, L["stride"], L["pad"], tuple(L["in_shape"]), tuple(L["out_shape"]))
 
 
 def load_net(layers: list[dict]) -> Net:
-    """Chain spec from ``synth`` -> oracle Net in float64."""
-    aff = [None]
-    expect_affine = True
-    for L in layers:
-        if L["kind"] == "relu":
-            assert not expect_affine, "ReLU must follow an affine layer"
-            expect_affine = True
-            continue
-        assert expect_affine, "two affine layers in a row are not a chain of this form"
-        W = torch.as_tensor(np.asarray(L["W"]), dtype=DT)
-        b = torch.as_tensor(np.asarray(L["b"]), dtype=DT)
-        if L["kind"] == "fc":
-            aff.append(Affine("fc", W, b))
+    """Layer list from ``synth`` -> oracle Net in float64.
+
+    Every op reads the previous op unless it names ``src`` (an op index);
+    ``add`` sums the affine ops (or adds) listed in ``src``.  A ReLU's input is
+    an affine op or a sum of them; affine ops read a ReLU output or the input.
+    """
+    relu_of = {}        # op index of a ReLU -> ReLU layer number
+    feed = {}           # op index of an affine / add -> [(source ReLU layer, Affine)]
+    edges = [[]]
+    for i, L in enumerate(layers):
+        k = L["kind"]
+        if k == "relu":
+            src = L.get("src", i - 1)
+            assert src in feed, "a ReLU must read an affine layer or a sum"
+            edges.append(list(feed[src]))
+            relu_of[i] = len(edges) - 1
+        elif k == "add":
+            parts = []
+            for a in L["src"]:
+                assert a in feed, "add sums affine layers"
+                parts += feed[a]
+            feed[i] = parts
         else:
-            aff.append(Affine("conv", W, b, L["stride"], L["pad"], tuple(L["in_shape"]),
-                              tuple(L["out_shape"])))
-        expect_affine = False
-    assert not expect_affine, "the chain must end with an affine layer"
-    return Net(aff)
+            src = L.get("src", i - 1)
+            if src < 0:   # the network input
+                s = 0
+            else:
+                assert src in relu_of, "an affine layer must read a ReLU output or the input"
+                s = relu_of[src]
+            feed[i] = [(s, _affine(L))]
+    last = len(layers) - 1
+    assert last in feed, "the network must end with an affine layer"
+    edges.append(list(feed[last]))
+    return Net(edges)
 
 
 def fold_property(net: Net, C: np.ndarray, d: np.ndarray) -> Net:
     """Fold the linear property C f(x) + d > 0 into the last affine layer (Sec. 2.1)."""
-    last = net.aff[-1]
+    assert len(net.edges[-1]) == 1
+    s, last = net.edges[-1][0]
     assert last.kind == "fc"
     Ct = torch.as_tensor(np.asarray(C), dtype=DT)
     dt = torch.as_tensor(np.asarray(d), dtype=DT)
     new = Affine("fc", Ct @ last.W, Ct @ last.b + dt)
-    return Net(net.aff[:-1] + [new])
+    return Net(net.edges[:-1] + [[(s, new)]])
 
 
 # ----------------------------------------------------------------------------
@@ -226,22 +263,34 @@ class Relax:
 def backsub_rows(net: Net, t: int, E: torch.Tensor, relax: dict, lo, hi, keep_ap=False):
     """Lower bounds of the rows E (coefficients on zhat^(t)) over the box.
 
-    Pushes E through aff[t], then ReLU t-1, aff[t-1], ..., aff[1] and
-    concretises.  ``relax[i]`` gives the relaxation of ReLU layer i.
+    Pushes E through the affine edges into t, then through ReLU t-1, its edges,
+    ..., down to the input (coefficients reaching one z^(s) from several edges
+    add up) and concretises.  ``relax[i]`` gives the relaxation of ReLU layer i.
     Returns (lb, x*, {i: a'_i} if keep_ap).
     """
-    A = net.aff[t].backsub(E)
-    c = net.aff[t].bias_dot(E)
+    lam = {}
+    c = torch.zeros(E.shape[0], dtype=DT)
+
+    def push(u, Ahat):
+        nonlocal c
+        for s, A in net.edges[u]:
+            lam[s] = lam[s] + A.backsub(Ahat) if s in lam else A.backsub(Ahat)
+            c = c + A.bias_dot(Ahat)
+
+    push(t, E)
     aps = {}
     for i in range(t - 1, 0, -1):
+        if i not in lam:
+            continue
         r = relax[i]
-        A, dc, ap = relu_backsub(A, r.l, r.u, r.S, r.alpha, r.beta, r.GP, r.GPh, r.gp0)
+        A, dc, ap = relu_backsub(lam.pop(i), r.l, r.u, r.S, r.alpha, r.beta, r.GP, r.GPh, r.gp0)
         if keep_ap:
             aps[i] = ap
         c = c + dc
-        c = c + net.aff[i].bias_dot(A)
-        A = net.aff[i].backsub(A)
-    lb, xstar = concretize(A, c, lo, hi)
+        push(i, A)
+    d0 = net.dims()[0]
+    A0 = lam.get(0, torch.zeros(E.shape[0], d0, dtype=DT))
+    lb, xstar = concretize(A0, c, lo, hi)
     return lb, xstar, aps
 
 
@@ -375,7 +424,7 @@ def final_relax(node: Node, alpha, beta, gamma, dense_mnc: dict | None):
 def final_bound(net: Net, node: Node, alpha, beta, gamma, dense_mnc, lo, hi, keep_ap=False):
     """Lower bound of property row ``node.row`` at parameters (alpha, beta, gamma)."""
     R = net.R
-    E = torch.zeros(1, net.aff[R + 1].d_out, dtype=DT)
+    E = torch.zeros(1, net.width(R + 1), dtype=DT)
     E[0, node.row] = 1.0
     relax = final_relax(node, alpha, beta, gamma, dense_mnc)
     lb, xstar, aps = backsub_rows(net, R + 1, E, relax, lo, hi, keep_ap)
@@ -534,13 +583,13 @@ def cab_costs(net: Net, n_mnc: dict | None = None) -> dict:
     C = {}
     acc = 0.0
     for t in range(1, R + 1):
-        acc += aff_cost(net.aff[t])
-        C[t] = acc                              # below zhat_t: aff_t, relu_{t-1}, ..., aff_1
-        acc += net.aff[t].d_out + n_mnc.get(t, 0)  # relu_t
-    c_obj = acc + net.aff[R].d_out if R >= 1 else acc   # one objective row through the last layer
+        acc += sum(aff_cost(A) for _, A in net.edges[t])
+        C[t] = acc                                   # all layers below zhat_t
+        acc += net.width(t) + n_mnc.get(t, 0)        # relu_t
+    c_obj = acc + net.width(R) if R >= 1 else acc    # one objective row through the last layer
     costs = {}
     for k in range(1, R + 1):
-        costs[k] = c_obj + sum(2.0 * net.aff[t].d_out * C[t] for t in range(k + 1, R + 1))
+        costs[k] = c_obj + sum(2.0 * net.width(t) * C[t] for t in range(k + 1, R + 1))
     return costs
 
 

@@ -46,8 +46,11 @@ def _conv_out(n: int, k: int, s: int, p: int) -> int:
     return (n + 2 * p - k) // s + 1
 
 
-# Layer specs: ("fc", out) | ("conv", Co, k, stride, pad) | ("relu",)
-# Each network is a plain chain: affine, relu, affine, ..., affine.
+# Layer specs: ("fc", out[, src]) | ("conv", Co, k, stride, pad[, src[, scale]]) | ("relu",)
+#              | ("add", a, b).
+# Every op reads the previous op unless it names ``src`` (an op index, -1 for
+# the network input); ``add`` sums two affine ops (residual sum).  ``scale``
+# multiplies the drawn He-normal weights (residual branches).
 CONFIGS = {
     0: dict(name="fc_784_100_100_10", seed=0, in_shape=(1, 28, 28), n_props=16,
             layers=[("fc", 100), ("relu",), ("fc", 100), ("relu",), ("fc", 10)],
@@ -61,6 +64,16 @@ CONFIGS = {
                     ("conv", 64, 3, 1, 1), ("relu",), ("conv", 64, 4, 2, 1), ("relu",),
                     ("fc", 512), ("relu",), ("fc", 512), ("relu",), ("fc", 10)],
             mnc_k=3, adam_steps=20, max_nodes=256, batch=256, timeout_s=60.0),
+    # ResNet6-like: stem, two basic blocks (3x3 s2 + 3x3 s1 main branch whose
+    # second conv is scaled by 0.5, 1x1 s2 shortcut), FC100, FC10
+    3: dict(name="resnet_32", seed=3, in_shape=(3, 32, 32), n_props=50,
+            layers=[("conv", 16, 3, 1, 1), ("relu",),
+                    ("conv", 32, 3, 2, 1, 1), ("relu",), ("conv", 32, 3, 1, 1, 3, 0.5),
+                    ("conv", 32, 1, 2, 0, 1), ("add", 4, 5), ("relu",),
+                    ("conv", 64, 3, 2, 1, 7), ("relu",), ("conv", 64, 3, 1, 1, 9, 0.5),
+                    ("conv", 64, 1, 2, 0, 7), ("add", 10, 11), ("relu",),
+                    ("fc", 100), ("relu",), ("fc", 10)],
+            mnc_k=3, adam_steps=20, max_nodes=256, batch=128, timeout_s=120.0),
 }
 
 
@@ -68,29 +81,45 @@ def make_network(cfg: int | dict) -> list[dict]:
     """Seeded He-normal network of a config (float32 arrays)."""
     spec = CONFIGS[cfg] if isinstance(cfg, int) else cfg
     rng = np.random.default_rng(spec["seed"])
-    shape = tuple(spec["in_shape"])
+    shapes = {-1: tuple(spec["in_shape"])}
     layers: list[dict] = []
-    for L in spec["layers"]:
+    for i, L in enumerate(spec["layers"]):
+        prev = i - 1
         if L[0] == "relu":
             layers.append(dict(kind="relu"))
+            shapes[i] = shapes[prev]
+            continue
+        if L[0] == "add":
+            layers.append(dict(kind="add", src=(L[1], L[2])))
+            shapes[i] = shapes[L[1]]
             continue
         if L[0] == "fc":
+            src = L[2] if len(L) > 2 else prev
+            shape = shapes[src]
             fan_in = int(np.prod(shape))
             out = L[1]
             W = rng.standard_normal((out, fan_in)) * np.sqrt(2.0 / fan_in)
             b = rng.standard_normal(out) * 0.01
-            layers.append(dict(kind="fc", W=W.astype(np.float32), b=b.astype(np.float32)))
-            shape = (out,)
+            d = dict(kind="fc", W=W.astype(np.float32), b=b.astype(np.float32))
+            if len(L) > 2:
+                d["src"] = src
+            layers.append(d)
+            shapes[i] = (out,)
         else:
-            _, co, k, s, p = L
-            ci, hi, wi = shape
+            co, k, s, p = L[1:5]
+            src = L[5] if len(L) > 5 else prev
+            scale = L[6] if len(L) > 6 else 1.0
+            ci, hi, wi = shapes[src]
             fan_in = ci * k * k
-            W = rng.standard_normal((co, ci, k, k)) * np.sqrt(2.0 / fan_in)
+            W = rng.standard_normal((co, ci, k, k)) * np.sqrt(2.0 / fan_in) * scale
             b = rng.standard_normal(co) * 0.01
             ho, wo = _conv_out(hi, k, s, p), _conv_out(wi, k, s, p)
-            layers.append(dict(kind="conv", W=W.astype(np.float32), b=b.astype(np.float32),
-                               stride=s, pad=p, in_shape=(ci, hi, wi), out_shape=(co, ho, wo)))
-            shape = (co, ho, wo)
+            d = dict(kind="conv", W=W.astype(np.float32), b=b.astype(np.float32),
+                     stride=s, pad=p, in_shape=(ci, hi, wi), out_shape=(co, ho, wo))
+            if len(L) > 5:
+                d["src"] = src
+            layers.append(d)
+            shapes[i] = (co, ho, wo)
     return layers
 
 
@@ -129,27 +158,32 @@ def make_image(seed: int, in_shape) -> np.ndarray:
 
 def net_forward(layers: list[dict], x: np.ndarray) -> np.ndarray:
     """Plain float64 network evaluation, used only to label the images."""
-    h = np.asarray(x, dtype=np.float64).reshape(-1)
-    for L in layers:
-        if L["kind"] == "relu":
-            h = np.maximum(h, 0.0)
-        elif L["kind"] == "fc":
-            h = L["W"].astype(np.float64) @ h + L["b"].astype(np.float64)
+    out = {-1: np.asarray(x, dtype=np.float64).reshape(-1)}
+    for i, L in enumerate(layers):
+        k = L["kind"]
+        if k == "add":
+            out[i] = out[L["src"][0]] + out[L["src"][1]]
+            continue
+        h = out[L.get("src", i - 1)]
+        if k == "relu":
+            out[i] = np.maximum(h, 0.0)
+        elif k == "fc":
+            out[i] = L["W"].astype(np.float64) @ h + L["b"].astype(np.float64)
         else:
             ci, hi, wi = L["in_shape"]
             co, ho, wo = L["out_shape"]
             s, p = L["stride"], L["pad"]
             W = L["W"].astype(np.float64)
-            k = W.shape[2]
+            kk = W.shape[2]
             xi = np.zeros((ci, hi + 2 * p, wi + 2 * p))
             xi[:, p:p + hi, p:p + wi] = h.reshape(ci, hi, wi)
-            out = np.zeros((co, ho, wo))
-            for kh in range(k):
-                for kw in range(k):
+            o = np.zeros((co, ho, wo))
+            for kh in range(kk):
+                for kw in range(kk):
                     patch = xi[:, kh:kh + s * (ho - 1) + 1:s, kw:kw + s * (wo - 1) + 1:s]
-                    out += np.einsum("oc,chw->ohw", W[:, :, kh, kw], patch)
-            h = (out + L["b"].astype(np.float64)[:, None, None]).reshape(-1)
-    return h
+                    o += np.einsum("oc,chw->ohw", W[:, :, kh, kw], patch)
+            out[i] = (o + L["b"].astype(np.float64)[:, None, None]).reshape(-1)
+    return out[len(layers) - 1]
 
 
 def property_rows(label: int, n_classes: int) -> tuple[np.ndarray, np.ndarray]:

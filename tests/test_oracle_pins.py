@@ -430,3 +430,72 @@ def test_cab_costs_by_hand():
     sc = {1: torch.tensor([1.0, 2.0]), 2: torch.tensor([0.5, 0.1])}
     cab = core.cab_scores(sc, {1: 10.0, 2: 1.0})
     assert core.pick_split(cab)[:2] == (2, 0)
+
+
+# --------------------------------------------------------------------------
+# residual (ResAdd) networks
+# --------------------------------------------------------------------------
+def _tiny_resnet(seed, bias=0.1):
+    """x(6) -> fc8 -> relu -> fc8 -> relu -> fc8 (+ fc8 shortcut from the first
+    relu) -> relu -> fc3."""
+    rng = np.random.default_rng(seed)
+    def fc(o, i, src=None):
+        d = _fc(rng.standard_normal((o, i)) * 0.6, rng.standard_normal(o) * 0.1 + bias)
+        if src is not None:
+            d["src"] = src
+        return d
+    return [fc(8, 6), RELU, fc(8, 8), RELU, fc(8, 8, 3), fc(8, 8, 1),
+            dict(kind="add", src=(4, 5)), RELU, fc(3, 8)]
+
+
+def test_resnet_forward_matches_definition():
+    L = _tiny_resnet(0)
+    net = core.load_net(L)
+    assert net.R == 3 and len(net.edges[3]) == 2
+    x = np.random.default_rng(1).uniform(0, 1, 6)
+    assert np.allclose(net.forward(_t(x)[None])[0].numpy(), synth.net_forward(L, x), atol=1e-12)
+
+
+def test_resnet_bound_is_exact_when_linear():
+    """With every ReLU stable (large biases, small box) the network is affine
+    on the box and the back-substituted bound through both edges of the
+    residual sum equals the exact minimum of that affine map."""
+    L = _tiny_resnet(5, bias=20.0)
+    x0 = np.full(6, 0.5)
+    lo, hi = synth.input_box(x0, 0.002)
+    C, d = np.array([[1.0, -1.0, 0.0]], np.float32), np.zeros(1, np.float32)
+    net, lo_t, hi_t, l, u, S, _, _ = bab.prepare(L, C, d, lo, hi)
+    assert all(bool(((l[i] >= 0) | (u[i] <= 0)).all()) for i in l)
+    assert any(bool((l[i] >= 0).any()) for i in l)
+    node = bab.root_node(net, 0, l, u, S, None)
+    lb, _ = core.deeppoly_final(net, node, lo_t, hi_t)
+    # affine map by evaluating the net at the box centre and along the axes
+    f = lambda x: float((C @ synth.net_forward(L, x) + d)[0])
+    c0 = f(np.zeros(6))
+    g = np.array([f(np.eye(6)[k]) - c0 for k in range(6)])
+    exact = c0 + np.minimum(g * lo, g * hi).sum()
+    assert float(lb) == pytest.approx(exact, rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_resnet_soundness_random_parameters(seed):
+    L = _tiny_resnet(seed, bias=0.0)
+    rng = np.random.default_rng(seed)
+    x0 = rng.uniform(0.2, 0.8, 6)
+    y = synth.net_forward(L, x0)
+    C, d = synth.property_rows(int(np.argmax(y)), 3)
+    lo, hi = synth.input_box(x0, 0.3)
+    net, lo_t, hi_t, l, u, S, _, _ = bab.prepare(L, C, d, lo, hi)
+    X = rng.uniform(lo, hi, size=(20000, 6))
+    F = np.stack([C @ synth.net_forward(L, x) + d for x in X[:4000]])
+    # root bounds contain every sampled pre-activation (the residual sum included)
+    z = {0: _t(X)}
+    for t in range(1, net.R + 1):
+        h = sum(A.forward(z[s]) for s, A in net.edges[t])
+        assert bool((h >= l[t] - 1e-9).all()) and bool((h <= u[t] + 1e-9).all())
+        z[t] = torch.clamp(h, min=0)
+    for trial in range(3):
+        node = bab.root_node(net, trial % C.shape[0], l, u, S, None)
+        node.alpha = {i: _t(rng.uniform(0, 1, l[i].numel())) for i in l}
+        lb, _, _ = core.final_bound(net, node, node.alpha, node.beta, node.gamma, None, lo_t, hi_t)
+        assert float(lb) <= F[:, node.row].min() + 1e-9
