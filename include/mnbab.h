@@ -71,11 +71,17 @@ typedef struct {
                                   0 = launch it kernel by kernel (default) */
 } mnbab_options;
 
-/* Layer kinds.  A network is a chain affine, RELU, affine, ..., affine. */
+/* Layer kinds.  A network is a list of ops; an FC or CONV2D op reads the
+ * previous op unless src_a names another (1-based op index, or -1 for the
+ * network input); a RELU reads the previous op, which must be an FC / CONV2D
+ * op or an ADD; an ADD sums the outputs of the FC / CONV2D / ADD ops src_a and
+ * src_b (1-based), as in residual blocks (ResAdd).  Every affine op must read
+ * a RELU output or the input, at most two affine ops may sum into one RELU,
+ * and the last op must be an FC layer. */
 #define MNBAB_FC 1
 #define MNBAB_CONV2D 2
 #define MNBAB_RELU 3
-#define MNBAB_ADD 4 /* residual sum; not supported by this build */
+#define MNBAB_ADD 4
 
 typedef struct {
   int32_t kind;
@@ -87,7 +93,7 @@ typedef struct {
   int32_t k, stride, pad;
   const float* W; /* FC [out_c][in_c]; CONV2D [out_c][in_c][k][k]; row-major */
   const float* b; /* [out_c] */
-  int32_t src_a, src_b; /* ADD only */
+  int32_t src_a, src_b; /* see the layer kinds above; 0 = the previous op */
 } mnbab_layer_desc;
 
 /* Projected Adam ascent on (alpha, beta, gamma) (Sec. 3.1). */

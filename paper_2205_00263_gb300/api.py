@@ -74,15 +74,21 @@ class NodeParams:
 class Net:
     def __init__(self, ctx: "Context", handle, layers):
         self.ctx, self.h = ctx, handle
-        self.dims = []
+        out_dim = {}
         self.d0 = None
-        for Ly in layers:
-            if Ly["kind"] == "relu":
-                continue
-            if self.d0 is None:
-                self.d0 = int(np.prod(Ly["W"].shape[1:])) if Ly["kind"] == "fc" else int(np.prod(Ly["in_shape"]))
-            self.dims.append(Ly["W"].shape[0] if Ly["kind"] == "fc" else int(np.prod(Ly["out_shape"])))
-        self.relu_dims = self.dims[:-1]
+        self.relu_dims = []
+        for i, Ly in enumerate(layers):
+            k = Ly["kind"]
+            if k == "relu":
+                out_dim[i] = out_dim[i - 1]
+                self.relu_dims.append(out_dim[i])
+            elif k == "add":
+                out_dim[i] = out_dim[Ly["src"][0]]
+            else:
+                if self.d0 is None and Ly.get("src", i - 1) < 0:   # reads the network input
+                    self.d0 = (int(np.prod(Ly["W"].shape[1:])) if k == "fc"
+                               else int(np.prod(Ly["in_shape"])))
+                out_dim[i] = Ly["W"].shape[0] if k == "fc" else int(np.prod(Ly["out_shape"]))
         self.R = len(self.relu_dims)
         self.SD = int(sum(self.relu_dims))
 
@@ -139,6 +145,12 @@ class Context:
             if Ly["kind"] == "relu":
                 d.kind = L.RELU
                 continue
+            if Ly["kind"] == "add":
+                d.kind = L.ADD
+                d.src_a, d.src_b = Ly["src"][0] + 1, Ly["src"][1] + 1
+                continue
+            if "src" in Ly:   # op index it reads; -1 = the network input
+                d.src_a = Ly["src"] + 1 if Ly["src"] >= 0 else -1
             W = _f32(Ly["W"])
             b = _f32(Ly["b"])
             keep += [W, b]

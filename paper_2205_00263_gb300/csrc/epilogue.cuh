@@ -85,6 +85,9 @@ __device__ __forceinline__ float epi_adj(const Epi& e, int m, int j, float h) {
 }
 
 __device__ __forceinline__ float epi_apply(const Epi& e, int m, int j, float v, float& part) {
+  // a node that sums two affine edges: the first edge's contribution is added
+  // before the epilogue of the second
+  if (e.acc_in) v += e.acc_in[(size_t)m * e.acc_ld + j];
   switch (e.kind) {
     case EPI_RELU: return epi_relu(e, m, j, v, part);
     case EPI_CONC: return epi_conc(e, m, j, v, part);

@@ -31,17 +31,23 @@ __device__ float block_sum(float v) {
 // ---------------------------------------------------------------------------
 // starting rows
 // ---------------------------------------------------------------------------
-__global__ void k_init_rows(NetDev net, int t, RowsDev rows, float* out, int ld, Epi e) {
+// Starting rows through one affine edge into node t: a = sign * A[j, :] on the
+// edge's source (the folded objective rows Wf for t = R + 1), c0 = sign * (sum
+// of the edge biases at j) on the first edge; the partial goes to slot_base.
+__global__ void k_init_rows(NetDev net, int t, int edge, RowsDev rows, float* out, int ld, Epi e) {
   const int m = blockIdx.x;
   if (m >= rows.M) return;
   const int n = rows.node[m];
   const int j = rows.j[m];
   const float sg = rows.sign ? rows.sign[m] : 1.f;
-  const int width = net.d[t - 1];
+  const int src = edge == 0 ? net.src1[t] : net.src2[t];
+  const int width = net.d[src];
   // a = 0 contributes nothing and maps to 0 through an intermediate ReLU step
-  // (no beta / gamma terms) and through concretisation (x* not kept)
-  const bool zero_passes = (e.kind == EPI_RELU && !e.final_mode && !e.GP && !e.GPh && !e.AP) ||
-                           (e.kind == EPI_CONC && !e.X);
+  // (no beta / gamma terms), through concretisation (x* not kept) and as a raw
+  // contribution, unless an earlier edge's contribution must be added
+  const bool zero_passes = !e.acc_in &&
+                           ((e.kind == EPI_RELU && !e.final_mode && !e.GP && !e.GPh && !e.AP) ||
+                            (e.kind == EPI_CONC && !e.X) || e.kind == EPI_STORE);
   float c0 = 0.f;
   float part = 0.f;
   if (t == net.R + 1) {
@@ -53,9 +59,13 @@ __global__ void k_init_rows(NetDev net, int t, RowsDev rows, float* out, int ld,
       if (out) out[(size_t)m * ld + col] = o;
     }
   } else {
-    const LayerDev& L = net.aff[t];
+    const LayerDev& L = edge == 0 ? net.aff[t] : net.aff2[t];
+    if (edge == 0) {
+      const float bj = net.bfull[t] ? net.bfull[t][j]
+                                    : (L.kind == 1 ? L.b[j] : L.b[j / (L.ho * L.wo)]);
+      c0 = sg * bj;
+    }
     if (L.kind == 1) {
-      c0 = sg * L.b[j];
       const float* w = L.W + (size_t)j * width;
       for (int col = threadIdx.x; col < width; col += blockDim.x) {
         const float o = epi_apply(e, m, col, sg * w[col], part);
@@ -66,7 +76,6 @@ __global__ void k_init_rows(NetDev net, int t, RowsDev rows, float* out, int ld,
       // nothing is stored: walk the window
       const int hw = L.ho * L.wo;
       const int co = j / hw, oh = (j % hw) / L.wo, ow = j % L.wo;
-      c0 = sg * L.b[co];
       const int h0 = oh * L.s - L.p, w0 = ow * L.s - L.p;
       const int kk = L.k * L.k;
       for (int q = threadIdx.x; q < L.ci * kk; q += blockDim.x) {
@@ -80,7 +89,6 @@ __global__ void k_init_rows(NetDev net, int t, RowsDev rows, float* out, int ld,
       // row j = (co, oh, ow) of the convolution's Toeplitz matrix
       const int hw = L.ho * L.wo;
       const int co = j / hw, oh = (j % hw) / L.wo, ow = j % L.wo;
-      c0 = sg * L.b[co];
       const int h0 = oh * L.s - L.p, w0 = ow * L.s - L.p;
       const int ihw = L.hi * L.wi;
       for (int col = threadIdx.x; col < width; col += blockDim.x) {
@@ -102,13 +110,13 @@ __global__ void k_init_rows(NetDev net, int t, RowsDev rows, float* out, int ld,
     }
   }
   const float tot = block_sum(part);
-  if (threadIdx.x == 0 && e.part) e.part[(size_t)m * e.nslot + 0] = tot + c0;
+  if (threadIdx.x == 0 && e.part) e.part[(size_t)m * e.nslot + e.slot_base] = tot + c0;
 }
 
-void launch_init_rows(const NetDev& net, int t, const RowsDev& rows, float* out, int ld,
+void launch_init_rows(const NetDev& net, int t, int edge, const RowsDev& rows, float* out, int ld,
                       const Epi& e, cudaStream_t st) {
   if (rows.M <= 0) return;
-  k_init_rows<<<rows.M, 128, 0, st>>>(net, t, rows, out, ld, e);
+  k_init_rows<<<rows.M, 128, 0, st>>>(net, t, edge, rows, out, ld, e);
 }
 
 // ---------------------------------------------------------------------------
@@ -499,8 +507,9 @@ __global__ void __launch_bounds__(128) k_convT_row(int M, const float* __restric
   const int iw_lo = box[2] * L.s - L.p, iw_hi = box[3] * L.s - L.p + L.k - 1;
   // a zero coefficient maps to 0 with no offset contribution through these
   // epilogues, so positions outside the window are written as 0 directly
-  const bool zero_passes = (e.kind == EPI_RELU && !e.final_mode && !e.GP && !e.GPh && !e.AP) ||
-                           (e.kind == EPI_CONC && !e.X);
+  const bool zero_passes = !e.acc_in &&
+                           ((e.kind == EPI_RELU && !e.final_mode && !e.GP && !e.GPh && !e.AP) ||
+                            (e.kind == EPI_CONC && !e.X) || e.kind == EPI_STORE);
   const int Pin = L.hi * L.wi;
   const int p0 = chunk * cs.ppc;
   const int np = min(cs.ppc, Pin - p0);
@@ -1238,48 +1247,57 @@ void launch_final_dot(int M, const int* row_node, PoolDev pool, const PropDev* p
 
 // Concrete forward pass f_r(x) in FP64 (one CTA per row), used to confirm
 // counterexamples: the sign of f_r at x* decides FALSIFIED (Sec. 2.2), so it is
-// evaluated in double precision from the FP32 weights.
-__global__ void k_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev* props,
-                              NetDev net, const float* X, int ldx, double* b1, double* b2,
-                              int ldb, double* fout) {
-  const int m = blockIdx.x;
-  double* h = b1 + (size_t)m * ldb;
-  double* g = b2 + (size_t)m * ldb;
-  for (int k = threadIdx.x; k < net.d[0]; k += blockDim.x) h[k] = (double)X[(size_t)m * ldx + k];
-  __syncthreads();
-  for (int i = 1; i <= net.R; ++i) {
-    const LayerDev& L = net.aff[i];
-    for (int o = threadIdx.x; o < L.d_out; o += blockDim.x) {
-      double acc;
-      if (L.kind == 1) {
-        acc = (double)L.b[o];
-        const float* w = L.W + (size_t)o * L.d_in;
-        for (int k = 0; k < L.d_in; ++k) acc = fma((double)w[k], h[k], acc);
-      } else {
-        const int hw = L.ho * L.wo;
-        const int co = o / hw, oh = (o % hw) / L.wo, ow = o % L.wo;
-        acc = (double)L.b[co];
-        for (int ci = 0; ci < L.ci; ++ci)
-          for (int kh = 0; kh < L.k; ++kh) {
-            const int ih = oh * L.s - L.p + kh;
-            if (ih < 0 || ih >= L.hi) continue;
-            for (int kw = 0; kw < L.k; ++kw) {
-              const int iw = ow * L.s - L.p + kw;
-              if (iw < 0 || iw >= L.wi) continue;
-              acc = fma((double)L.W[(((size_t)co * L.ci + ci) * L.k + kh) * L.k + kw],
-                        h[((size_t)ci * L.hi + ih) * L.wi + iw], acc);
-            }
-          }
+// evaluated in double precision from the FP32 weights.  The row buffer holds
+// x and every ReLU output (layer t at offset d0 + off[t]), so residual edges
+// can read any earlier layer.
+__device__ double f64_edge(const LayerDev& L, const double* z, int o) {
+  if (L.kind == 1) {
+    double acc = (double)L.b[o];
+    const float* w = L.W + (size_t)o * L.d_in;
+    for (int k = 0; k < L.d_in; ++k) acc = fma((double)w[k], z[k], acc);
+    return acc;
+  }
+  const int hw = L.ho * L.wo;
+  const int co = o / hw, oh = (o % hw) / L.wo, ow = o % L.wo;
+  double acc = (double)L.b[co];
+  for (int ci = 0; ci < L.ci; ++ci)
+    for (int kh = 0; kh < L.k; ++kh) {
+      const int ih = oh * L.s - L.p + kh;
+      if (ih < 0 || ih >= L.hi) continue;
+      for (int kw = 0; kw < L.k; ++kw) {
+        const int iw = ow * L.s - L.p + kw;
+        if (iw < 0 || iw >= L.wi) continue;
+        acc = fma((double)L.W[(((size_t)co * L.ci + ci) * L.k + kh) * L.k + kw],
+                  z[((size_t)ci * L.hi + ih) * L.wi + iw], acc);
       }
-      g[o] = acc > 0.0 ? acc : 0.0;
+    }
+  return acc;
+}
+
+__global__ void k_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                              NetDev net, const float* X, int ldx, double* buf, int ldb,
+                              double* fout) {
+  const int m = blockIdx.x;
+  double* z = buf + (size_t)m * ldb;
+  const int d0 = net.d[0];
+  auto seg = [&](int s) { return s == 0 ? z : z + d0 + net.off[s]; };
+  for (int k = threadIdx.x; k < d0; k += blockDim.x) z[k] = (double)X[(size_t)m * ldx + k];
+  __syncthreads();
+  for (int t = 1; t <= net.R; ++t) {
+    double* out = seg(t);
+    for (int o = threadIdx.x; o < net.d[t]; o += blockDim.x) {
+      double v = f64_edge(net.aff[t], seg(net.src1[t]), o);
+      if (net.n_edge[t] > 1) v += f64_edge(net.aff2[t], seg(net.src2[t]), o);
+      out[o] = v > 0.0 ? v : 0.0;
     }
     __syncthreads();
-    double* t = h; h = g; g = t;
   }
   const int n = row_node[m];
   const PropDev& P = props[pool.prop[n]];
   const int r = pool.row[n];
-  const int dR = net.d[net.R];
+  const int sR = net.src1[net.R + 1];
+  const int dR = net.d[sR];
+  const double* h = seg(sR);
   double acc = 0.0;
   for (int k = threadIdx.x; k < dR; k += blockDim.x) acc = fma((double)P.Wf[(size_t)r * dR + k], h[k], acc);
   __shared__ double sh[32];
@@ -1287,17 +1305,17 @@ __global__ void k_forward_f64(int M, const int* row_node, PoolDev pool, const Pr
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = (double)P.bf[r];
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
-    fout[m] = t;
+    double tt = (double)P.bf[r];
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tt += sh[i];
+    fout[m] = tt;
   }
 }
 
 void launch_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev* props,
-                        const NetDev& net, const float* X, int ldx, double* b1, double* b2,
-                        int ldb, double* fout, cudaStream_t st) {
+                        const NetDev& net, const float* X, int ldx, double* buf, int ldb,
+                        double* fout, cudaStream_t st) {
   if (M <= 0) return;
-  k_forward_f64<<<M, 256, 0, st>>>(M, row_node, pool, props, net, X, ldx, b1, b2, ldb, fout);
+  k_forward_f64<<<M, 256, 0, st>>>(M, row_node, pool, props, net, X, ldx, buf, ldb, fout);
 }
 
 __global__ void k_fill(float* p, size_t n, float v) {

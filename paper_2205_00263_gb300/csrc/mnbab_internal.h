@@ -24,13 +24,21 @@ struct LayerDev {
   const float* Wf;  // conv only: [ci][kh][kw][co] (forward layout)
 };
 
+// The network as a DAG: node t = 1..R (ReLU layers) and R + 1 (output) sums
+// one or two affine edges, zhat_t = A1(z_src1) + A2(z_src2) (+ biases), with
+// z_0 = x.  A chain has one edge (t - 1, aff[t]) per node.
 struct NetDev {
-  int R;                         // ReLU layers
-  int d[MNBAB_MAXR + 2];         // d[0] input, d[i] ReLU layer i
-  int off[MNBAB_MAXR + 2];       // offset of ReLU layer i in a node row
-  int SD;                        // sum of d[1..R]
-  int n_out;                     // logits
-  LayerDev aff[MNBAB_MAXR + 2];  // 1..R+1
+  int R;                          // ReLU layers
+  int d[MNBAB_MAXR + 2];          // d[0] input, d[i] ReLU layer i
+  int off[MNBAB_MAXR + 2];        // offset of ReLU layer i in a node row
+  int SD;                         // sum of d[1..R]
+  int n_out;                      // logits
+  LayerDev aff[MNBAB_MAXR + 2];   // first edge into node t = 1..R+1
+  LayerDev aff2[MNBAB_MAXR + 2];  // second edge (residual sum), if n_edge[t] == 2
+  int src1[MNBAB_MAXR + 2];       // source node of the first edge
+  int src2[MNBAB_MAXR + 2];       // source node of the second edge
+  int n_edge[MNBAB_MAXR + 2];
+  const float* bfull[MNBAB_MAXR + 2];  // per-neuron sum of the edge biases into t (may be null)
 };
 
 // Multi-neuron constraints of one property and ReLU layer.  Row form
@@ -103,6 +111,8 @@ struct Epi {
   int* err;          // device error flag (bounded waits of the tensor-core kernel)
   float* ws;         // split-K workspace (may be null: no split)
   size_t ws_floats;
+  const float* acc_in;  // earlier edge's contribution added before the epilogue (may alias out)
+  int acc_ld;
 };
 
 // ---- launchers (kernels.cu, tc_gemm.cu) ----------------------------------
@@ -113,7 +123,7 @@ int launch_gemm_tc(int M, int N, int K, const float* A, int lda, const float* Bn
                    cudaStream_t st);
 // Starting rows: a = sign * W_t[j, :] (t <= R) or Wf[row, :] (t = R + 1) on
 // z^(t-1), with c = sign * b_t[j] into slot 0, through epilogue `e`.
-void launch_init_rows(const NetDev& net, int t, const RowsDev& rows, float* out, int ld,
+void launch_init_rows(const NetDev& net, int t, int edge, const RowsDev& rows, float* out, int ld,
                       const Epi& e, cudaStream_t st);
 // Back-substitution through affine layer i: in [M][d_i] -> out [M][d_{i-1}].
 // Returns the number of partial-sum slots used.
@@ -158,10 +168,12 @@ void launch_root_init(int nb, const int* slots, const int* srcs, const int* rows
                       cudaStream_t st);
 void launch_final_dot(int M, const int* row_node, PoolDev pool, const PropDev* props,
                       const float* z, int ld, int dR, float* f, cudaStream_t st);
+// Counterexample confirmation in FP64 needs a per-row buffer of d0 + SD doubles.
+
 void launch_fill(float* p, size_t n, float v, cudaStream_t st);
 // FP64 forward pass f_r(x) of rows of X (counterexample confirmation).
 void launch_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev* props,
-                        const NetDev& net, const float* X, int ldx, double* b1, double* b2,
-                        int ldb, double* fout, cudaStream_t st);
+                        const NetDev& net, const float* X, int ldx, double* buf, int ldb,
+                        double* fout, cudaStream_t st);
 
 }  // namespace mnbab

@@ -86,12 +86,16 @@ extern "C" mnbab_status mnbab_deeppoly_fc_noalloc(int32_t n_affine, const int32_
       return MNBAB_E_INVALID_ARG;
     }
     nd.d[i] = dims[i];
+    nd.n_edge[i] = 1;
+    nd.src1[i] = i - 1;
     nd.off[i] = off;
     off += dims[i];
     maxd = std::max(maxd, dims[i]);
   }
   nd.SD = off;
   nd.off[R + 1] = off;
+  nd.n_edge[R + 1] = 1;
+  nd.src1[R + 1] = R;
   int nslot = 1;
   for (int i = 1; i <= R; ++i) nslot += backsub_slots(nd.aff[i]);
   // scratch layout
@@ -196,7 +200,7 @@ extern "C" mnbab_status mnbab_deeppoly_fc_noalloc(int32_t n_affine, const int32_
   e0.slot_base = 0;
   float* cur = d_A;
   float* nxt = d_B;
-  launch_init_rows(nd, R + 1, rows, R >= 1 ? cur : nullptr, maxd, e0, st);
+  launch_init_rows(nd, R + 1, 0, rows, R >= 1 ? cur : nullptr, maxd, e0, st);
   int used = 1;
   for (int i = R; i >= 1; --i) {
     Epi ei = epi_for(i - 1);

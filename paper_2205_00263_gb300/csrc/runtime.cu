@@ -59,7 +59,10 @@ struct mnbab_net {
   int id = 0;
   mnbab_ctx* ctx = nullptr;
   NetDev nd{};
-  std::vector<HostLayer> host;  // 1..R+1 (index 0 unused)
+  std::vector<HostLayer> hops;   // affine ops
+  int eop[MNBAB_MAXR + 2][2] = {{0}};  // affine op of the edges into node t
+  float* lam = nullptr;          // per-layer coefficient buffers: layer s at lam_off[s], ld d[s]
+  size_t lam_off[MNBAB_MAXR + 2] = {0};
   int R = 0, d0 = 0, SD = 0, n_out = 0, maxd = 0, maxd_relu = 0;
   int nslot = 0;
   // node pool
@@ -74,7 +77,7 @@ struct mnbab_net {
   int B = 0;          // batch capacity (objective rows)
   int pad_slot = -1;  // scratch node for padded graph rows
   int chunk = 0;      // rows per back-substitution launch
-  float *LamA = nullptr, *LamB = nullptr, *part = nullptr, *lb = nullptr;
+  float *part = nullptr, *lb = nullptr;
   int *row_node = nullptr, *row_j = nullptr, *counter = nullptr;
   float* row_sign = nullptr;
   size_t rows_cap = 0;
@@ -82,7 +85,7 @@ struct mnbab_net {
   float *AP = nullptr, *GA = nullptr, *GB = nullptr, *GP = nullptr, *GPh = nullptr;
   float *Gz = nullptr, *Hz = nullptr, *X = nullptr, *Xb = nullptr, *GG = nullptr, *gp0 = nullptr;
   float *fout = nullptr, *score = nullptr, *bestb = nullptr, *gmax = nullptr;
-  double *f64a = nullptr, *f64b = nullptr, *f64out = nullptr;
+  double *f64a = nullptr, *f64out = nullptr;
   float* splitk = nullptr;
   size_t splitk_floats = 0;
   int* cslots = nullptr;
@@ -383,10 +386,16 @@ void relu_epi(mnbab_net* n, Epi& e, int layer) {
   e.kind = EPI_RELU;
   e.layer = layer;
   e.off = n->nd.off[layer];
-  const LayerDev& L = n->nd.aff[layer];
-  e.bias = L.b;
-  e.bias_div = L.kind == 2 ? L.ho * L.wo : 1;
+  e.bias = n->nd.bfull[layer];  // sum of the edge biases into zhat_layer, per neuron
+  e.bias_div = 1;
 }
+
+float* lam_buf(mnbab_net* n, int s) { return n->lam + n->lam_off[s]; }
+
+const LayerDev& edge_of(const mnbab_net* n, int t, int k) {
+  return k == 0 ? n->nd.aff[t] : n->nd.aff2[t];
+}
+int src_of(const mnbab_net* n, int t, int k) { return k == 0 ? n->nd.src1[t] : n->nd.src2[t]; }
 
 struct SweepOpts {
   bool final_mode = false;  // objective rows with the node's alpha, beta (gamma if has_gamma)
@@ -395,11 +404,15 @@ struct SweepOpts {
   bool track = false;       // keep best bound / minimiser per node
 };
 
-// Back-substitutes rows that all start at zhat^(t) down to the input.
+// Back-substitutes rows that all start at zhat^(t) down to the input, node by
+// node in descending order.  Every node's coefficients live in its own buffer;
+// an edge into source s writes its contribution raw unless it is s's last
+// consumer in this sweep, which adds the earlier contribution and applies s's
+// ReLU (or concretisation) epilogue.
 void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
   mnbab_ctx* c = n->ctx;
   if (rows.M <= 0) return;
-  Epi e0 = base_epi(n, rows.node);
+  const NetDev& nd = n->nd;
   auto setup = [&](Epi& e, int layer) {
     if (layer >= 1) {
       relu_epi(n, e, layer);
@@ -414,29 +427,54 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
       if (o.store || o.track) e.X = n->X;
     }
   };
+  // nodes reached from t, and the last (smallest) consumer of every source
+  bool reached[MNBAB_MAXR + 2] = {false};
+  int lastc[MNBAB_MAXR + 2];
+  for (int s0 = 0; s0 <= MNBAB_MAXR + 1; ++s0) lastc[s0] = -1;
+  reached[t] = true;
+  for (int v = t; v >= 1; --v) {
+    if (!reached[v]) continue;
+    for (int k = 0; k < nd.n_edge[v]; ++k) {
+      const int sidx = src_of(n, v, k);
+      reached[sidx] = true;
+      lastc[sidx] = v;  // descending scan: ends at the smallest consumer
+    }
+  }
   int need = 1;
-  for (int i = t - 1; i >= 1; --i) need += backsub_slots(n->nd.aff[i]);
+  for (int v = t; v >= 1; --v)
+    if (reached[v])
+      for (int k = 0; k < nd.n_edge[v]; ++k)
+        need += v == t ? 1 : backsub_slots(edge_of(n, v, k));
   if (need > n->nslot) fail(MNBAB_E_DEVICE, "partial-sum slots overflow");
   if (rows.M > n->chunk && rows.M > n->B) fail(MNBAB_E_DEVICE, "row block larger than scratch");
-  setup(e0, t - 1);
-  e0.slot_base = 0;
-  float* cur = n->LamA;
-  float* nxt = n->LamB;
-  {
-    Scope sc(c, C_INIT, 0.0, 4.0 * rows.M * n->nd.d[t - 1]);
-    launch_init_rows(n->nd, t, rows, t - 1 >= 1 ? cur : nullptr, n->maxd, e0, c->st);
-  }
-  int used = 1;
-  for (int i = t - 1; i >= 1; --i) {
-    Epi e = base_epi(n, rows.node);
-    setup(e, i - 1);
-    e.slot_base = used;
-    const LayerDev& L = n->nd.aff[i];
-    Scope sc(c, L.kind == 1 ? C_BACKSUB_FC : C_BACKSUB_CONV, 2.0 * rows.M * layer_macs(L),
-             4.0 * rows.M * (L.d_out + (i > 1 ? L.d_in : 0)) + layer_wbytes(L));
-    used += launch_backsub(L, rows.M, cur, n->maxd, i - 1 >= 1 ? nxt : nullptr, n->maxd, e,
-                           c->st);
-    std::swap(cur, nxt);
+  bool written[MNBAB_MAXR + 2] = {false};
+  int used = 0;
+  for (int v = t; v >= 1; --v) {
+    if (!reached[v]) continue;
+    for (int k = 0; k < nd.n_edge[v]; ++k) {
+      const int sidx = src_of(n, v, k);
+      const bool last = lastc[sidx] == v;
+      Epi e = base_epi(n, rows.node);
+      if (last) setup(e, sidx);
+      else e.kind = EPI_STORE;
+      if (written[sidx]) {
+        e.acc_in = lam_buf(n, sidx);
+        e.acc_ld = nd.d[sidx];
+      }
+      e.slot_base = used;
+      float* out = (sidx >= 1 || !last) ? lam_buf(n, sidx) : nullptr;
+      if (v == t) {
+        Scope sc(c, C_INIT, 0.0, 4.0 * rows.M * nd.d[sidx]);
+        launch_init_rows(nd, t, k, rows, out, nd.d[sidx], e, c->st);
+        used += 1;
+      } else {
+        const LayerDev& L = edge_of(n, v, k);
+        Scope sc(c, L.kind == 1 ? C_BACKSUB_FC : C_BACKSUB_CONV, 2.0 * rows.M * layer_macs(L),
+                 4.0 * rows.M * (L.d_out + (out ? L.d_in : 0)) + layer_wbytes(L));
+        used += launch_backsub(L, rows.M, lam_buf(n, v), nd.d[v], out, nd.d[sidx], e, c->st);
+      }
+      written[sidx] = true;
+    }
   }
   Scope sc(c, C_REDUCE, 0.0, 4.0 * rows.M * used);
   launch_reduce_lb(rows.M, n->part, n->nslot, used,
@@ -513,33 +551,42 @@ void upload_batch(mnbab_net* n, const std::vector<int>& slots) {
 
 RowsDev obj_rows(mnbab_net* n, int M) { return RowsDev{M, n->bslots, n->brows, nullptr}; }
 
-// adjoint sweep from x* up through the ReLU layers (d lb / d ahat_i is the
-// forward pass of the relaxed network at x*)
+// adjoint sweep from x* up through the ReLU layers (d lb / d ahat_t is the
+// forward pass of the relaxed network at x*); a node with two edges stores the
+// first edge's product and finishes with the second.
 void adjoint(mnbab_net* n, int M, bool has_gamma) {
   mnbab_ctx* c = n->ctx;
-  const float* in = n->X;
-  int ld_in = n->d0;
-  float* bufs[2] = {n->LamA, n->LamB};
-  for (int i = 1; i <= n->R; ++i) {
-    Epi e = base_epi(n, n->bslots);
-    e.kind = EPI_ADJ;
-    e.layer = i;
-    e.off = n->nd.off[i];
-    e.AP = n->AP;
-    e.GA = n->GA;
-    e.GB = n->GB;
-    if (has_gamma) {
-      e.Gz = n->Gz;
-      e.Hz = n->Hz;
+  const NetDev& nd = n->nd;
+  for (int t = 1; t <= n->R; ++t) {
+    for (int k = 0; k < nd.n_edge[t]; ++k) {
+      const int sidx = src_of(n, t, k);
+      Epi e = base_epi(n, n->bslots);
+      e.part = nullptr;
+      if (k == nd.n_edge[t] - 1) {
+        e.kind = EPI_ADJ;
+        e.layer = t;
+        e.off = nd.off[t];
+        e.AP = n->AP;
+        e.GA = n->GA;
+        e.GB = n->GB;
+        if (has_gamma) {
+          e.Gz = n->Gz;
+          e.Hz = n->Hz;
+        }
+      } else {
+        e.kind = EPI_STORE;
+      }
+      if (k > 0) {
+        e.acc_in = lam_buf(n, t);
+        e.acc_ld = nd.d[t];
+      }
+      const float* in = sidx == 0 ? n->X : lam_buf(n, sidx);
+      const int ld_in = sidx == 0 ? n->d0 : nd.d[sidx];
+      const LayerDev& L = edge_of(n, t, k);
+      Scope sc(c, L.kind == 1 ? C_FWD_FC : C_FWD_CONV, 2.0 * M * layer_macs(L),
+               4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
+      launch_forward(L, M, in, ld_in, lam_buf(n, t), nd.d[t], e, c->st);
     }
-    e.part = nullptr;
-    float* out = bufs[i & 1];
-    const LayerDev& L = n->nd.aff[i];
-    Scope sc(c, L.kind == 1 ? C_FWD_FC : C_FWD_CONV, 2.0 * M * layer_macs(L),
-             4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
-    launch_forward(L, M, in, ld_in, out, n->maxd, e, c->st);
-    in = out;
-    ld_in = n->maxd;
   }
   if (has_gamma) {
     Scope sc(c, C_GAMMA, 0.0, 4.0 * M * c->EC);
@@ -643,23 +690,30 @@ void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a)
 // FP32 forward pass of rows of `x` ([M][d0]) -> f_r in n->fout
 void forward_rows(mnbab_net* n, int M, const float* x) {
   mnbab_ctx* c = n->ctx;
-  const float* in = x;
-  int ld = n->d0;
-  float* bufs[2] = {n->LamA, n->LamB};
-  for (int i = 1; i <= n->R; ++i) {
-    Epi e = base_epi(n, n->bslots);
-    e.kind = EPI_FWD_RELU;
-    e.part = nullptr;
-    float* out = bufs[i & 1];
-    const LayerDev& L = n->nd.aff[i];
-    Scope sc(c, L.kind == 1 ? C_FWD_FC : C_FWD_CONV, 2.0 * M * layer_macs(L),
-             4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
-    launch_forward(L, M, in, ld, out, n->maxd, e, c->st);
-    in = out;
-    ld = n->maxd;
+  const NetDev& nd = n->nd;
+  for (int t = 1; t <= n->R; ++t) {
+    for (int k = 0; k < nd.n_edge[t]; ++k) {
+      const int sidx = src_of(n, t, k);
+      Epi e = base_epi(n, n->bslots);
+      e.part = nullptr;
+      e.kind = k == nd.n_edge[t] - 1 ? EPI_FWD_RELU : EPI_STORE;
+      if (k > 0) {
+        e.acc_in = lam_buf(n, t);
+        e.acc_ld = nd.d[t];
+      }
+      const float* in = sidx == 0 ? x : lam_buf(n, sidx);
+      const int ld_in = sidx == 0 ? n->d0 : nd.d[sidx];
+      const LayerDev& L = edge_of(n, t, k);
+      Scope sc(c, L.kind == 1 ? C_FWD_FC : C_FWD_CONV, 2.0 * M * layer_macs(L),
+               4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
+      launch_forward(L, M, in, ld_in, lam_buf(n, t), nd.d[t], e, c->st);
+    }
   }
-  Scope sc(c, C_BOOK, 2.0 * M * n->nd.d[n->R], 8.0 * M * n->nd.d[n->R]);
-  launch_final_dot(M, n->bslots, n->pool, c->d_props, in, ld, n->nd.d[n->R], n->fout, c->st);
+  const int sR = nd.src1[n->R + 1];
+  const int dR = nd.d[sR];
+  const float* z = sR == 0 ? x : lam_buf(n, sR);
+  Scope sc(c, C_BOOK, 2.0 * M * dR, 8.0 * M * dR);
+  launch_final_dot(M, n->bslots, n->pool, c->d_props, z, sR == 0 ? n->d0 : dR, dR, n->fout, c->st);
 }
 
 __global__ void k_gather_rows(int M, const int* idx, const float* src, int ld_src, float* dst,
@@ -729,9 +783,10 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
     n->maxd = std::max(n->maxd, n->nd.d[i]);
     n->maxd_relu = std::max(n->maxd_relu, n->nd.d[i]);
   }
-  n->nslot = 1;
-  for (int i = 1; i <= n->R; ++i) n->nslot += backsub_slots(n->nd.aff[i]);
-  n->nslot = std::max(n->nslot, 8);
+  n->nslot = 4;
+  for (int i = 1; i <= n->R + 1; ++i)
+    for (int k = 0; k < n->nd.n_edge[i]; ++k)
+      n->nslot += backsub_slots(k == 0 ? n->nd.aff[i] : n->nd.aff2[i]);
   // pool
   n->cap = c->node_cap;
   const size_t SD = n->SD, EC = c->EC, cap = n->cap;
@@ -778,8 +833,15 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   n->chunk = std::max(2, c->row_chunk & ~1);
   const size_t chunk = n->chunk, B = n->B;
   const size_t mrows = std::max(chunk, B);
-  n->LamA = dalloc_t<float>(c, mrows * n->maxd);
-  n->LamB = dalloc_t<float>(c, mrows * n->maxd);
+  // per-layer coefficient buffers (input layer included)
+  {
+    size_t at = 0;
+    for (int sidx = 0; sidx <= n->R; ++sidx) {
+      n->lam_off[sidx] = at;
+      at += mrows * (size_t)n->nd.d[sidx];
+    }
+    n->lam = dalloc_t<float>(c, at);
+  }
   n->part = dalloc_t<float>(c, mrows * n->nslot);
   n->lb = dalloc_t<float>(c, mrows);
   n->rows_cap = std::max(chunk, std::min((size_t)2 * SD * B, (size_t)1 << 26));
@@ -807,16 +869,17 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   n->score = dalloc_t<float>(c, B);
   n->bestb = dalloc_t<float>(c, B);
   n->gmax = dalloc_t<float>(c, B);
-  n->f64a = dalloc_t<double>(c, B * n->maxd);
-  n->f64b = dalloc_t<double>(c, B * n->maxd);
+  n->f64a = dalloc_t<double>(c, B * (size_t)(n->d0 + n->SD));
   n->f64out = dalloc_t<double>(c, B);
   n->cslots = dalloc_t<int>(c, B);
   // split-K workspace: 16 splits of a B x (widest FC layer) product
   {
     size_t wmax = 0;
-    for (int i = 1; i <= n->R; ++i)
-      if (n->nd.aff[i].kind == 1)
-        wmax = std::max(wmax, (size_t)std::max(n->nd.aff[i].d_in, n->nd.aff[i].d_out));
+    for (int i = 1; i <= n->R + 1; ++i)
+      for (int k = 0; k < n->nd.n_edge[i]; ++k) {
+        const LayerDev& L = k == 0 ? n->nd.aff[i] : n->nd.aff2[i];
+        if (L.kind == 1) wmax = std::max(wmax, (size_t)std::max(L.d_in, L.d_out));
+      }
     if (wmax) {
       n->splitk_floats = 16 * B * wmax;
       n->splitk = dalloc_t<float>(c, n->splitk_floats);
@@ -847,8 +910,10 @@ void update_cab(mnbab_net* n, mnbab_prop* p) {
   double C[MNBAB_MAXR + 2] = {0};
   double acc = 0.0;
   for (int t = 1; t <= R; ++t) {
-    const HostLayer& L = n->host[t];
-    acc += L.kind == MNBAB_FC ? (double)L.ci * L.co : (double)L.co * L.ho * L.wo * L.k * L.k;
+    for (int k = 0; k < n->nd.n_edge[t]; ++k) {
+      const HostLayer& L = n->hops[n->eop[t][k]];
+      acc += L.kind == MNBAB_FC ? (double)L.ci * L.co : (double)L.co * L.ho * L.wo * L.k * L.k;
+    }
     C[t] = acc;
     acc += (double)n->nd.d[t] + (double)p->pd.mnc[t].e;
   }
@@ -1009,7 +1074,7 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
       {
         Scope sc(c, C_BOOK, 0.0, 8.0 * Mc * n->maxd);
         launch_forward_f64(Mc, n->cslots, n->pool, c->d_props, n->nd, n->Xb, n->d0, n->f64a,
-                           n->f64b, n->maxd, n->f64out, c->st);
+                           n->d0 + n->SD, n->f64out, c->st);
       }
       d2h(c, f64.data(), n->f64out, Mc);
       d2h(c, xc.data(), n->Xb, (size_t)Mc * n->d0);
@@ -1227,6 +1292,51 @@ void mnbab_destroy(mnbab_ctx* c) {
 
 const char* mnbab_last_error(const mnbab_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+// Device copy of one affine op (weights in the layouts the kernels read).
+LayerDev upload_affine(mnbab_ctx* c, const HostLayer& h) {
+  LayerDev L{};
+  L.kind = h.kind;
+  L.ci = h.ci; L.hi = h.hi; L.wi = h.wi; L.co = h.co; L.ho = h.ho; L.wo = h.wo;
+  L.k = h.k; L.s = h.s; L.p = h.p;
+  L.d_in = h.ci * h.hi * h.wi;
+  L.d_out = h.co * h.ho * h.wo;
+  std::vector<float> W(h.W.begin(), h.W.end()), b(h.b.begin(), h.b.end());
+  float* dW = dalloc_t<float>(c, W.size());
+  float* db = dalloc_t<float>(c, b.size());
+  h2d(c, dW, W.data(), W.size());
+  h2d(c, db, b.data(), b.size());
+  L.W = dW;
+  L.b = db;
+  if (h.kind == MNBAB_FC) {
+    std::vector<float> Wt((size_t)L.d_in * L.d_out);
+    for (int o = 0; o < L.d_out; ++o)
+      for (int k = 0; k < L.d_in; ++k) Wt[(size_t)k * L.d_out + o] = W[(size_t)o * L.d_in + k];
+    float* dWt = dalloc_t<float>(c, Wt.size());
+    h2d(c, dWt, Wt.data(), Wt.size());
+    L.Wt = dWt;
+  } else {
+    if (!conv_supported(L))
+      fail(MNBAB_E_UNSUPPORTED, "convolution row does not fit in shared memory");
+    // weights pre-arranged for the row-resident kernels: channel blocks contiguous
+    const int kk = L.k * L.k;
+    std::vector<float> Wb((size_t)L.co * kk * L.ci), Wfw((size_t)L.ci * kk * L.co);
+    for (int co = 0; co < L.co; ++co)
+      for (int ci = 0; ci < L.ci; ++ci)
+        for (int r = 0; r < kk; ++r) {
+          const float w = W[((size_t)co * L.ci + ci) * kk + r];
+          Wb[((size_t)co * kk + r) * L.ci + ci] = w;
+          Wfw[((size_t)ci * kk + r) * L.co + co] = w;
+        }
+    float* dWb = dalloc_t<float>(c, Wb.size());
+    float* dWf = dalloc_t<float>(c, Wfw.size());
+    h2d(c, dWb, Wb.data(), Wb.size());
+    h2d(c, dWf, Wfw.data(), Wfw.size());
+    L.Wb = dWb;
+    L.Wf = dWf;
+  }
+  return L;
+}
+
 mnbab_status mnbab_load_network(mnbab_ctx* c, const mnbab_layer_desc* layers, int32_t n_layers,
                                 mnbab_net** out) {
   API_BEGIN(c)
@@ -1234,19 +1344,41 @@ mnbab_status mnbab_load_network(mnbab_ctx* c, const mnbab_layer_desc* layers, in
   mnbab_net* n = new mnbab_net();
   n->ctx = c;
   n->id = (int)c->nets.size();
-  n->host.resize(1);
-  bool expect_aff = true;
-  int prev = -1;
+  // parse: ReLU layers get numbers 1..R; an affine op feeds the sum of its
+  // consumer; an ADD concatenates the feeds of its two operands
+  std::vector<int> relu_of(n_layers, -1);
+  std::vector<std::vector<std::pair<int, int>>> feed(n_layers);  // (source node, affine op)
+  std::vector<char> is_feed(n_layers, 0);
+  std::vector<int> out_dim(n_layers, 0);
+  std::vector<std::vector<std::pair<int, int>>> edges(1);
+  int d0 = -1;
+  auto op_index = [&](int i, int32_t src) {  // 0 = previous op, k >= 1 = op k - 1, -1 = input
+    if (src == 0) return i - 1;
+    if (src < 0) return -1;
+    return (int)src - 1;
+  };
   for (int i = 0; i < n_layers; ++i) {
     const mnbab_layer_desc& d = layers[i];
     if (d.kind == MNBAB_RELU) {
-      if (expect_aff) fail(MNBAB_E_INVALID_ARG, "ReLU must follow an affine layer");
-      expect_aff = true;
+      if (i == 0 || !is_feed[i - 1]) fail(MNBAB_E_INVALID_ARG, "ReLU must follow an affine layer or ADD");
+      if (feed[i - 1].size() > 2) fail(MNBAB_E_UNSUPPORTED, "more than two edges into a ReLU layer");
+      edges.push_back(feed[i - 1]);
+      relu_of[i] = (int)edges.size() - 1;
+      out_dim[i] = out_dim[i - 1];
       continue;
     }
-    if (d.kind == MNBAB_ADD) fail(MNBAB_E_UNSUPPORTED, "residual ADD layers are not supported");
+    if (d.kind == MNBAB_ADD) {
+      const int a = op_index(i, d.src_a), b = op_index(i, d.src_b);
+      if (d.src_a <= 0 || d.src_b <= 0 || a >= i || b >= i || !is_feed[a] || !is_feed[b])
+        fail(MNBAB_E_INVALID_ARG, "ADD must sum two earlier affine layers");
+      if (out_dim[a] != out_dim[b]) fail(MNBAB_E_INVALID_ARG, "ADD of different widths");
+      feed[i] = feed[a];
+      feed[i].insert(feed[i].end(), feed[b].begin(), feed[b].end());
+      is_feed[i] = 1;
+      out_dim[i] = out_dim[a];
+      continue;
+    }
     if (d.kind != MNBAB_FC && d.kind != MNBAB_CONV2D) fail(MNBAB_E_INVALID_ARG, "bad layer kind");
-    if (!expect_aff) fail(MNBAB_E_INVALID_ARG, "two affine layers without a ReLU between");
     if (!d.W || !d.b) fail(MNBAB_E_INVALID_ARG, "missing weights");
     HostLayer h{};
     h.kind = d.kind;
@@ -1261,69 +1393,66 @@ mnbab_status mnbab_load_network(mnbab_ctx* c, const mnbab_layer_desc* layers, in
     }
     const int din = h.ci * h.hi * h.wi, dout = h.co * h.ho * h.wo;
     if (din <= 0 || dout <= 0) fail(MNBAB_E_INVALID_ARG, "empty layer");
-    if (prev >= 0 && din != prev) fail(MNBAB_E_INVALID_ARG, "layer sizes do not chain");
-    prev = dout;
+    const int src_op = op_index(i, d.src_a);
+    int snode = 0;
+    if (src_op >= 0) {
+      if (src_op >= i || relu_of[src_op] < 0)
+        fail(MNBAB_E_INVALID_ARG, "an affine layer must read a ReLU output or the input");
+      snode = relu_of[src_op];
+      if (out_dim[src_op] != din) fail(MNBAB_E_INVALID_ARG, "layer sizes do not chain");
+    } else {
+      if (d0 >= 0 && d0 != din) fail(MNBAB_E_INVALID_ARG, "inconsistent input width");
+      d0 = din;
+    }
     const size_t nW = d.kind == MNBAB_FC ? (size_t)dout * din : (size_t)h.co * h.ci * h.k * h.k;
     h.W.assign(d.W, d.W + nW);
     h.b.assign(d.b, d.b + h.co);
-    n->host.push_back(std::move(h));
-    expect_aff = false;
+    n->hops.push_back(std::move(h));
+    feed[i] = {{snode, (int)n->hops.size() - 1}};
+    is_feed[i] = 1;
+    out_dim[i] = dout;
   }
-  if (expect_aff) fail(MNBAB_E_INVALID_ARG, "network must end with an affine layer");
-  n->R = (int)n->host.size() - 2;
+  if (!is_feed[n_layers - 1]) fail(MNBAB_E_INVALID_ARG, "network must end with an affine layer");
+  if (d0 < 0) fail(MNBAB_E_INVALID_ARG, "no layer reads the input");
+  edges.push_back(feed[n_layers - 1]);
+  n->R = (int)edges.size() - 2;
   if (n->R < 0 || n->R > MNBAB_MAXR) fail(MNBAB_E_UNSUPPORTED, "too many ReLU layers");
-  if (n->host.back().kind != MNBAB_FC) fail(MNBAB_E_UNSUPPORTED, "last layer must be FC");
+  if (edges.back().size() != 1 || n->hops[edges.back()[0].second].kind != MNBAB_FC)
+    fail(MNBAB_E_UNSUPPORTED, "the last layer must be a single FC layer");
   NetDev& nd = n->nd;
   nd.R = n->R;
-  n->d0 = n->host[1].ci * n->host[1].hi * n->host[1].wi;
-  nd.d[0] = n->d0;
+  n->d0 = d0;
+  nd.d[0] = d0;
+  std::vector<LayerDev> ops;
+  for (const auto& h : n->hops) ops.push_back(upload_affine(c, h));
   int off = 0;
-  for (int i = 1; i <= n->R + 1; ++i) {
-    const HostLayer& h = n->host[i];
-    LayerDev& L = nd.aff[i];
-    L.kind = h.kind;
-    L.ci = h.ci; L.hi = h.hi; L.wi = h.wi; L.co = h.co; L.ho = h.ho; L.wo = h.wo;
-    L.k = h.k; L.s = h.s; L.p = h.p;
-    L.d_in = h.ci * h.hi * h.wi;
-    L.d_out = h.co * h.ho * h.wo;
-    std::vector<float> W(h.W.begin(), h.W.end()), b(h.b.begin(), h.b.end());
-    float* dW = dalloc_t<float>(c, W.size());
-    float* db = dalloc_t<float>(c, b.size());
-    h2d(c, dW, W.data(), W.size());
-    h2d(c, db, b.data(), b.size());
-    L.W = dW;
-    L.b = db;
-    if (h.kind == MNBAB_FC) {
-      std::vector<float> Wt((size_t)L.d_in * L.d_out);
-      for (int o = 0; o < L.d_out; ++o)
-        for (int k = 0; k < L.d_in; ++k) Wt[(size_t)k * L.d_out + o] = W[(size_t)o * L.d_in + k];
-      float* dWt = dalloc_t<float>(c, Wt.size());
-      h2d(c, dWt, Wt.data(), Wt.size());
-      L.Wt = dWt;
-    } else {
-      if (!conv_supported(L))
-        fail(MNBAB_E_UNSUPPORTED, "convolution row does not fit in shared memory");
-      // weights pre-arranged for the row-resident kernels: channel blocks contiguous
-      const int kk = L.k * L.k;
-      std::vector<float> Wb((size_t)L.co * kk * L.ci), Wfw((size_t)L.ci * kk * L.co);
-      for (int co = 0; co < L.co; ++co)
-        for (int ci = 0; ci < L.ci; ++ci)
-          for (int r = 0; r < kk; ++r) {
-            const float w = W[((size_t)co * L.ci + ci) * kk + r];
-            Wb[((size_t)co * kk + r) * L.ci + ci] = w;
-            Wfw[((size_t)ci * kk + r) * L.co + co] = w;
-          }
-      float* dWb = dalloc_t<float>(c, Wb.size());
-      float* dWf = dalloc_t<float>(c, Wfw.size());
-      h2d(c, dWb, Wb.data(), Wb.size());
-      h2d(c, dWf, Wfw.data(), Wfw.size());
-      L.Wb = dWb;
-      L.Wf = dWf;
+  for (int t = 1; t <= n->R + 1; ++t) {
+    nd.n_edge[t] = (int)edges[t].size();
+    nd.src1[t] = edges[t][0].first;
+    nd.aff[t] = ops[edges[t][0].second];
+    n->eop[t][0] = edges[t][0].second;
+    if (nd.n_edge[t] > 1) {
+      nd.src2[t] = edges[t][1].first;
+      nd.aff2[t] = ops[edges[t][1].second];
+      n->eop[t][1] = edges[t][1].second;
+      if (nd.aff2[t].d_out != nd.aff[t].d_out) fail(MNBAB_E_INVALID_ARG, "ADD of different widths");
     }
-    if (i <= n->R) {
-      nd.d[i] = L.d_out;
-      nd.off[i] = off;
-      off += L.d_out;
+    for (int k = 0; k < nd.n_edge[t]; ++k)
+      if (edges[t][k].first >= t) fail(MNBAB_E_INVALID_ARG, "edges must point forward");
+    if (t <= n->R) {
+      nd.d[t] = nd.aff[t].d_out;
+      nd.off[t] = off;
+      off += nd.d[t];
+      // per-neuron sum of the edge biases into zhat_t
+      std::vector<float> bf(nd.d[t], 0.f);
+      for (int k = 0; k < nd.n_edge[t]; ++k) {
+        const HostLayer& h = n->hops[n->eop[t][k]];
+        const int per = h.ho * h.wo;
+        for (int j = 0; j < nd.d[t]; ++j) bf[j] += (float)h.b[j / per];
+      }
+      float* dbf = dalloc_t<float>(c, bf.size());
+      h2d(c, dbf, bf.data(), bf.size());
+      nd.bfull[t] = dbf;
     }
   }
   nd.off[n->R + 1] = off;
@@ -1354,7 +1483,7 @@ mnbab_status mnbab_set_property(mnbab_ctx* c, const mnbab_net* cnet, const float
   p->lo.assign(x_lo, x_lo + n->d0);
   p->hi.assign(x_hi, x_hi + n->d0);
   // fold the property into the last layer (Sec. 2.1)
-  const HostLayer& last = n->host[n->R + 1];
+  const HostLayer& last = n->hops[n->eop[n->R + 1][0]];
   const int dR = last.ci, no = last.co;
   p->Wf.assign((size_t)n_rows * dR, 0.0);
   p->bf.assign(n_rows, 0.0);

@@ -51,6 +51,18 @@ def convbig_spec(seed):
                         ("fc", 50), ("relu",), ("fc", 10)])
 
 
+def resnet_spec(seed):
+    """Two residual blocks (ResAdd of a 3x3 main branch and a 1x1 shortcut, the
+    second with stride 2) on a 3x10x10 input."""
+    return dict(seed=seed, in_shape=(3, 10, 10),
+                layers=[("conv", 8, 3, 1, 1), ("relu",),
+                        ("conv", 8, 3, 1, 1, 1), ("relu",), ("conv", 8, 3, 1, 1, 3, 0.5),
+                        ("conv", 8, 1, 1, 0, 1), ("add", 4, 5), ("relu",),
+                        ("conv", 16, 3, 2, 1, 7), ("relu",), ("conv", 16, 3, 1, 1, 9, 0.5),
+                        ("conv", 16, 1, 2, 0, 7), ("add", 10, 11), ("relu",),
+                        ("fc", 20), ("relu",), ("fc", 5)])
+
+
 def conv_case(seed, eps, spec_fn=None):
     spec = (spec_fn or conv_spec)(seed)
     layers = synth.make_network(spec)

@@ -12,7 +12,7 @@ import torch
 
 import synth
 from helpers import (TOL, close, concat, conv_case, convbig_spec, fc_case, f32, gpu_property,
-                     random_node, to_params)
+                     random_node, resnet_spec, to_params)
 from oracle import bab, core, mnc
 
 pytestmark = pytest.mark.gpu
@@ -40,7 +40,7 @@ def _assert_close(g, o, what, tol=TOL):
 # root bounds (DeepPoly back-substitution of every neuron, both sides)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("path", [1, 2])
-@pytest.mark.parametrize("case", ["ragged_fc", "conv", "convbig", "cfg0"])
+@pytest.mark.parametrize("case", ["ragged_fc", "conv", "convbig", "resnet", "cfg0"])
 def test_root_bounds(Context, case, path):
     if case == "ragged_fc":
         layers, C, d, lo, hi, prep = fc_case(1, (37, 53, 29, 7), 0.1)
@@ -48,6 +48,8 @@ def test_root_bounds(Context, case, path):
         layers, C, d, lo, hi, prep = conv_case(2, 0.05)
     elif case == "convbig":
         layers, C, d, lo, hi, prep = conv_case(3, 0.01, convbig_spec)
+    elif case == "resnet":
+        layers, C, d, lo, hi, prep = conv_case(4, 0.02, resnet_spec)
     else:
         layers = synth.make_network(0)
         pr = synth.make_properties(0, layers, n=1, eps=synth.load_eps(0))[0]
@@ -66,14 +68,16 @@ def test_root_bounds(Context, case, path):
 # fixed parameters: re-bounding after splits and the objective bound
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("path", [1, 2])
-@pytest.mark.parametrize("case", ["fc_mnc", "conv", "convbig"])
+@pytest.mark.parametrize("case", ["fc_mnc", "conv", "convbig", "resnet"])
 def test_rebound_and_bound_at_fixed_parameters(Context, case, path):
     if case == "fc_mnc":
         layers, C, d, lo, hi, prep = fc_case(3, (37, 53, 29, 7), 0.12, with_mnc=True)
     elif case == "conv":
         layers, C, d, lo, hi, prep = conv_case(4, 0.08)
-    else:
+    elif case == "convbig":
         layers, C, d, lo, hi, prep = conv_case(5, 0.01, convbig_spec)
+    else:
+        layers, C, d, lo, hi, prep = conv_case(6, 0.02, resnet_spec)
     net, lo_t, hi_t, l, u, S, m, dense = prep
     E = sum(v.idx.shape[0] for v in m.values()) if m else 0
     rng = np.random.default_rng(11)
@@ -125,14 +129,16 @@ def test_deeppoly_pass(Context):
 # adjoint: gradient of the bound w.r.t. alpha, beta, gamma
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("path", [1, 2])
-@pytest.mark.parametrize("case", ["fc_mnc", "conv", "convbig"])
+@pytest.mark.parametrize("case", ["fc_mnc", "conv", "convbig", "resnet"])
 def test_gradient_matches_oracle(Context, case, path):
     if case == "fc_mnc":
         layers, C, d, lo, hi, prep = fc_case(6, (37, 53, 29, 7), 0.12, with_mnc=True)
     elif case == "conv":
         layers, C, d, lo, hi, prep = conv_case(7, 0.08)
-    else:
+    elif case == "convbig":
         layers, C, d, lo, hi, prep = conv_case(8, 0.01, convbig_spec)
+    else:
+        layers, C, d, lo, hi, prep = conv_case(9, 0.02, resnet_spec)
     net, lo_t, hi_t, l, u, S, m, dense = prep
     E = sum(v.idx.shape[0] for v in m.values()) if m else 0
     SD = sum(l[i].numel() for i in l)
@@ -402,3 +408,15 @@ def test_graph_replay_matches_direct_launches(Context):
     for o in out[1:]:
         assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
         assert np.array_equal(o[2], out[0][2])
+
+
+def test_bab_trace_matches_oracle_resnet(Context):
+    """Residual network: the GPU BaB tree matches the oracle node by node."""
+    layers, C, d, lo, hi, prep = conv_case(10, 0.03, resnet_spec)
+    ores = bab.verify(layers, C, d, lo, hi, max_nodes=14, prepared=prep)
+    with Context(node_capacity=1024) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
+        ctx.set_budget(prop, 14)
+        _run_gpu_bab(ctx, [prop], max_nodes=1)
+        k, flagged = _compare_trace(ctx.trace(prop), ores)
+        assert k + flagged >= min(8, len(ores.nodes))
