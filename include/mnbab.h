@@ -281,6 +281,39 @@ mnbab_status mnbab_profile(mnbab_ctx* ctx, int32_t enable);
 mnbab_status mnbab_profile_read(mnbab_ctx* ctx, mnbab_kernel_stat* stats, int32_t max_stats,
                                 int32_t* n_out, int64_t* total_launches);
 
+/* ---- serving: continuous batching of verification requests ------------ */
+typedef struct {
+  int32_t admitted;        /* requests admitted in this pass */
+  int32_t finished;        /* requests that got their final verdict in this pass */
+  int32_t active;          /* admitted, not finished */
+  int32_t queued;          /* waiting for admission */
+  mnbab_step_stats step;   /* summed over the networks' BaB steps */
+} mnbab_serve_stats;
+
+/* Queues a property (created by mnbab_set_property and not yet used) as a
+ * request of the context's request loop; timeout_s > 0 limits its time from
+ * this call to its verdict (UNKNOWN when exceeded). */
+mnbab_status mnbab_submit(mnbab_ctx* ctx, mnbab_prop* prop, double timeout_s, uint64_t* ticket);
+
+/* One pass of the request loop: admits queued requests in FIFO order while
+ * their network's node pool (allocated within the HBM budget) can hold their
+ * reservation (n_rows + 1 + 2 * node budget slots), runs one BaB step per
+ * network over all of its active requests (nodes of different requests share
+ * the launches, so requests that arrive while others run join the next
+ * batch), and retires requests that reached a verdict, their node budget or
+ * their timeout.  Results of a request do not depend on the others it ran
+ * with. */
+mnbab_status mnbab_serve_step(mnbab_ctx* ctx, int32_t max_nodes, const mnbab_adam* cfg,
+                              mnbab_serve_stats* out);
+
+/* done = 1 once the request has its final verdict. */
+mnbab_status mnbab_poll(mnbab_ctx* ctx, uint64_t ticket, int32_t* done);
+
+/* Verdict, queueing time, time to verdict (from submission, seconds) and
+ * bounded nodes of a finished request. */
+mnbab_status mnbab_request_result(mnbab_ctx* ctx, uint64_t ticket, int32_t* verdict, double* wait_s,
+                                  double* total_s, int32_t* nodes);
+
 /* Number of open nodes queued for the property. */
 mnbab_status mnbab_queue_size(const mnbab_ctx* ctx, const mnbab_prop* prop, int32_t* n_out);
 

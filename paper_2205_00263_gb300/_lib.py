@@ -49,6 +49,11 @@ class StepStats(C.Structure):
                 ("d2h_bytes", C.c_int64)]
 
 
+class ServeStats(C.Structure):
+    _fields_ = [("admitted", C.c_int32), ("finished", C.c_int32), ("active", C.c_int32),
+                ("queued", C.c_int32), ("step", StepStats)]
+
+
 class KernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("ms", C.c_double),
                 ("flops", C.c_double), ("bytes", C.c_double)]
@@ -91,6 +96,11 @@ SIGNATURES = {
     "mnbab_get_trace": (status, [VP, VP, C.POINTER(TraceRec), C.c_int32, IP]),
     "mnbab_queue_size": (status, [VP, VP, IP]),
     "mnbab_profile": (status, [VP, C.c_int32]),
+    "mnbab_submit": (status, [VP, VP, C.c_double, C.POINTER(C.c_uint64)]),
+    "mnbab_serve_step": (status, [VP, C.c_int32, C.POINTER(Adam), C.POINTER(ServeStats)]),
+    "mnbab_poll": (status, [VP, C.c_uint64, IP]),
+    "mnbab_request_result": (status, [VP, C.c_uint64, IP, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), IP]),
     "mnbab_deeppoly_fc_noalloc": (status, [C.c_int32, IP, C.POINTER(VP), C.POINTER(VP), VP, VP,
                                            VP, VP, VP, VP, C.c_int32, VP, VP, C.c_char_p,
                                            C.c_size_t]),

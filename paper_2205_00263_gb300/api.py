@@ -305,3 +305,29 @@ class Context:
             k = arr[i]
             out[k.name.decode()] = dict(launches=k.launches, ms=k.ms, flops=k.flops, bytes=k.bytes)
         return out, tot.value
+
+    # ---- serving ------------------------------------------------------------
+    def submit(self, prop: Prop, timeout_s: float = 0.0) -> int:
+        t = C.c_uint64()
+        self._ck(self.lib.mnbab_submit(self.h, prop.h, timeout_s, C.byref(t)))
+        return t.value
+
+    def serve_step(self, max_nodes: int, steps: int = 20):
+        a = L.Adam(steps, 0.1, 0.05, 0.05, 0.9, 0.999, 1e-8, 0.0, 1e-3)
+        st = L.ServeStats()
+        self._ck(self.lib.mnbab_serve_step(self.h, max_nodes, C.byref(a), C.byref(st)))
+        out = {k: getattr(st, k) for k, _ in L.ServeStats._fields_ if k != "step"}
+        out["step"] = {k: getattr(st.step, k) for k, _ in L.StepStats._fields_}
+        return out
+
+    def poll(self, ticket: int) -> bool:
+        d = C.c_int32()
+        self._ck(self.lib.mnbab_poll(self.h, ticket, C.byref(d)))
+        return bool(d.value)
+
+    def request_result(self, ticket: int):
+        v, n = C.c_int32(), C.c_int32()
+        w, t = C.c_double(), C.c_double()
+        self._ck(self.lib.mnbab_request_result(self.h, ticket, C.byref(v), C.byref(w), C.byref(t),
+                                               C.byref(n)))
+        return dict(verdict=v.value, wait_s=w.value, total_s=t.value, nodes=n.value)

@@ -117,6 +117,18 @@ struct mnbab_prop {
   int mnc_set[MNBAB_MAXR + 1] = {0};
   bool root_pending = false;         // root bounds not computed yet
   std::vector<int> root_row_slots;   // its row root nodes, initialised with the bounds
+  bool admitted = true;              // false while queued in the request loop
+  bool materialized = false;         // node slots allocated
+};
+
+// A request of the serving loop.
+struct Request {
+  uint64_t ticket = 0;
+  mnbab_prop* p = nullptr;
+  double t_submit = 0, t_admit = 0, t_done = 0, deadline = 0;
+  int state = 0;    // 0 queued, 1 active, 2 done
+  int reserve = 0;  // node slots reserved in its network's pool
+  int timed_out = 0;
 };
 
 struct mnbab_ctx {
@@ -142,6 +154,10 @@ struct mnbab_ctx {
   int64_t acc_n[32] = {0};
   double acc_ms[32] = {0}, acc_flops[32] = {0}, acc_bytes[32] = {0};
   int64_t h2d_bytes = 0, d2h_bytes = 0;
+  // request loop
+  std::vector<Request*> requests;        // by ticket - 1
+  std::deque<Request*> req_queue;        // queued, FIFO
+  std::vector<int> reserved;             // reserved node slots per network
   // CUDA graphs of the optimisation loop
   bool graphs = false;
   struct GraphEntry* cap = nullptr;  // entry being captured (Scope records into it)
@@ -927,8 +943,41 @@ void update_cab(mnbab_net* n, mnbab_prop* p) {
 
 // Root bounds of every property of the network admitted since the last call,
 // computed together in one re-bounding pass, then their row root nodes.
+// Node slots of a property: the root-bound slot (l = -inf, u = +inf, re-bounded
+// from layer 1 with the next batch of admissions) and one root node per row.
+void materialize(mnbab_net* n, mnbab_prop* p) {
+  mnbab_ctx* c = n->ctx;
+  if ((int)n->free_slots.size() < p->n_rows + 1) fail(MNBAB_E_BUDGET, "node pool exhausted");
+  const int rs = alloc_slot(n);
+  p->root_slot = rs;
+  n->slot_prop[rs] = p->index;
+  n->slot_row[rs] = 0;
+  n->slot_split[rs] = 0;
+  {
+    Scope sc(c, C_BOOK, 0.0, 8.0 * n->SD, 2);
+    launch_fill(n->pool.L + (size_t)rs * n->SD, n->SD, -INFINITY, c->st);
+    launch_fill(n->pool.U + (size_t)rs * n->SD, n->SD, INFINITY, c->st);
+  }
+  ck(cudaMemsetAsync(n->pool.S + (size_t)rs * n->SD, 0, n->SD, c->st), "memset");
+  int pi = p->index;
+  h2d(c, n->pool.prop + rs, &pi, 1);
+  for (int r = 0; r < p->n_rows; ++r) {
+    const int sl = alloc_slot(n);
+    n->slot_prop[sl] = p->index;
+    n->slot_row[sl] = r;
+    n->slot_split[sl] = n->R;
+    p->root_row_slots.push_back(sl);
+    p->queue.push_back(QNode{sl, p->next_seq++, r, 0, n->R});
+    p->row_open[r]++;
+  }
+  p->root_pending = true;
+  p->materialized = true;
+}
+
 void ensure_roots(mnbab_net* n) {
   mnbab_ctx* c = n->ctx;
+  for (auto* p : c->props)
+    if (p->net == n && p->admitted && !p->materialized) materialize(n, p);
   std::vector<mnbab_prop*> pend;
   for (auto* p : c->props)
     if (p->net == n && p->root_pending) pend.push_back(p);
@@ -988,6 +1037,7 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
   std::vector<Picked> picked;
   for (int i = 0; i < n_props && (int)picked.size() < max_nodes; ++i) {
     mnbab_prop* p = props[i];
+    if (!p->materialized) continue;
     while (!p->done && !p->queue.empty() && p->bounded < p->budget &&
            (int)picked.size() < max_nodes) {
       picked.push_back({p, p->queue.front()});
@@ -1187,6 +1237,7 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
   // property completion
   for (int i = 0; i < n_props; ++i) {
     mnbab_prop* p = props[i];
+    if (!p->materialized) continue;
     if (p->done) {
       for (auto& q : p->queue) free_slot(n, q.slot);
       p->queue.clear();
@@ -1284,6 +1335,7 @@ void mnbab_destroy(mnbab_ctx* c) {
   }
   for (auto e : c->graph_events) cudaEventDestroy(e);
   for (auto& a : c->allocs) cudaFree(a.first);
+  for (auto* r : c->requests) delete r;
   for (auto* n : c->nets) delete n;
   for (auto* p : c->props) delete p;
   if (c->own_stream) cudaStreamDestroy(c->st);
@@ -1515,32 +1567,8 @@ mnbab_status mnbab_set_property(mnbab_ctx* c, const mnbab_net* cnet, const float
   p->row_leaf.assign(n_rows, 0);
   p->row_fals.assign(n_rows, 0);
   p->row_lb.assign(n_rows, INFINITY);
-  // root bounds: a slot with l = -inf, u = +inf, re-bounded from layer 1 by the
-  // next call that needs them (admissions are bounded together)
-  const int rs = alloc_slot(n);
-  p->root_slot = rs;
-  n->slot_prop[rs] = p->index;
-  n->slot_row[rs] = 0;
-  n->slot_split[rs] = 0;
-  {
-    Scope sc(c, C_BOOK, 0.0, 8.0 * n->SD, 2);
-    launch_fill(n->pool.L + (size_t)rs * n->SD, n->SD, -INFINITY, c->st);
-    launch_fill(n->pool.U + (size_t)rs * n->SD, n->SD, INFINITY, c->st);
-  }
-  ck(cudaMemsetAsync(n->pool.S + (size_t)rs * n->SD, 0, n->SD, c->st), "memset");
-  int pi = p->index;
-  h2d(c, n->pool.prop + rs, &pi, 1);
-  // root nodes, one per row, FIFO
-  for (int r = 0; r < n_rows; ++r) {
-    const int sl = alloc_slot(n);
-    n->slot_prop[sl] = p->index;
-    n->slot_row[sl] = r;
-    n->slot_split[sl] = n->R;
-    p->root_row_slots.push_back(sl);
-    p->queue.push_back(QNode{sl, p->next_seq++, r, 0, n->R});
-    p->row_open[r]++;
-  }
-  p->root_pending = true;
+  // node slots are allocated when the property starts (materialize): right
+  // away for direct use, on admission in the request loop
   *out = p;
   API_END(c)
 }
@@ -1553,6 +1581,7 @@ mnbab_status mnbab_get_root_bounds(const mnbab_ctx* cc, const mnbab_prop* p, int
   mnbab_net* n = p->net;
   if (layer < 1 || layer > n->R) fail(MNBAB_E_INVALID_ARG, "bad layer");
   ensure_roots(n);
+  if (!p->materialized) fail(MNBAB_E_INVALID_ARG, "property is still queued in the request loop");
   const size_t base = (size_t)p->root_slot * n->SD + n->nd.off[layer];
   d2h(c, l_out, n->pool.L + base, n->nd.d[layer]);
   d2h(c, u_out, n->pool.U + base, n->nd.d[layer]);
@@ -1625,6 +1654,7 @@ mnbab_status mnbab_node_root(mnbab_ctx* c, mnbab_prop* p, int32_t row, mnbab_nod
   if (!p || !out || row < 0 || row >= p->n_rows) fail(MNBAB_E_INVALID_ARG, "bad row");
   mnbab_net* n = p->net;
   ensure_roots(n);
+  if (!p->materialized) fail(MNBAB_E_INVALID_ARG, "property is still queued in the request loop");
   const int s = alloc_slot(n);
   n->slot_prop[s] = p->index;
   n->slot_row[s] = row;
@@ -1895,6 +1925,115 @@ mnbab_status mnbab_get_trace(const mnbab_ctx* cc, const mnbab_prop* p, mnbab_tra
   const int k = recs ? std::min(nt, std::max(0, (int)max_recs)) : 0;
   for (int i = 0; i < k; ++i) recs[i] = p->trace[i];
   *n_out = recs ? k : nt;
+  API_END(c)
+}
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+mnbab_status mnbab_submit(mnbab_ctx* c, mnbab_prop* p, double timeout_s, uint64_t* ticket) {
+  API_BEGIN(c)
+  if (!p || !ticket) fail(MNBAB_E_INVALID_ARG, "null argument");
+  if (p->materialized || !p->admitted) fail(MNBAB_E_INVALID_ARG, "property already started or queued");
+  mnbab_net* n = p->net;
+  Request* r = new Request();
+  r->ticket = c->requests.size() + 1;
+  r->p = p;
+  r->t_submit = now_s();
+  r->deadline = timeout_s > 0 ? r->t_submit + timeout_s : 0.0;
+  // live nodes never exceed the rows' roots plus two children per bounded node
+  r->reserve = std::min(n->cap, p->n_rows + 1 + 2 * p->budget);
+  p->admitted = false;
+  c->requests.push_back(r);
+  c->req_queue.push_back(r);
+  *ticket = r->ticket;
+  API_END(c)
+}
+
+mnbab_status mnbab_serve_step(mnbab_ctx* c, int32_t max_nodes, const mnbab_adam* cfg,
+                              mnbab_serve_stats* out) {
+  API_BEGIN(c)
+  if (!out) fail(MNBAB_E_INVALID_ARG, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  const mnbab_adam a = cfg ? *cfg : default_adam();
+  if (c->reserved.size() < c->nets.size()) c->reserved.resize(c->nets.size(), 0);
+  // admission, FIFO: a request starts once its network's pool can hold its
+  // reservation (the pools are allocated within the context's HBM budget)
+  while (!c->req_queue.empty()) {
+    Request* r = c->req_queue.front();
+    mnbab_net* n = r->p->net;
+    const int avail = n->cap - 2 * n->B - 8;  // keep room for the pad slot and children
+    if (c->reserved[n->id] + r->reserve > avail) break;
+    c->reserved[n->id] += r->reserve;
+    r->p->admitted = true;
+    r->state = 1;
+    r->t_admit = now_s();
+    c->req_queue.pop_front();
+    out->admitted++;
+  }
+  // one BaB step per network over all its active requests: nodes of different
+  // requests share the launches
+  for (auto* n : c->nets) {
+    std::vector<mnbab_prop*> props;
+    for (auto* r : c->requests)
+      if (r->state == 1 && r->p->net == n) props.push_back(r->p);
+    if (props.empty()) continue;
+    mnbab_step_stats st;
+    bab_step_impl(c, props.data(), (int)props.size(), max_nodes, a, &st);
+    out->step.nodes_bounded += st.nodes_bounded;
+    out->step.nodes_verified += st.nodes_verified;
+    out->step.nodes_falsified += st.nodes_falsified;
+    out->step.nodes_branched += st.nodes_branched;
+    out->step.nodes_leaf += st.nodes_leaf;
+    out->step.rows_rebounded += st.rows_rebounded;
+    out->step.h2d_bytes += st.h2d_bytes;
+    out->step.d2h_bytes += st.d2h_bytes;
+  }
+  // retire: verdict, node budget, or timeout
+  const double t = now_s();
+  for (auto* r : c->requests) {
+    if (r->state != 1) continue;
+    mnbab_prop* p = r->p;
+    mnbab_net* n = p->net;
+    if (!p->done && r->deadline > 0 && t > r->deadline) {
+      p->verdict = MNBAB_UNKNOWN;
+      p->done = true;
+      for (auto& q : p->queue) free_slot(n, q.slot);
+      p->queue.clear();
+      r->timed_out = 1;
+    }
+    if (p->done) {
+      r->state = 2;
+      r->t_done = t;
+      c->reserved[n->id] -= r->reserve;
+      out->finished++;
+    }
+  }
+  for (auto* r : c->requests) {
+    if (r->state == 0) out->queued++;
+    if (r->state == 1) out->active++;
+  }
+  API_END(c)
+}
+
+mnbab_status mnbab_poll(mnbab_ctx* c, uint64_t ticket, int32_t* done) {
+  API_BEGIN(c)
+  if (!done || ticket == 0 || ticket > c->requests.size()) fail(MNBAB_E_INVALID_ARG, "bad ticket");
+  *done = c->requests[ticket - 1]->state == 2 ? 1 : 0;
+  API_END(c)
+}
+
+mnbab_status mnbab_request_result(mnbab_ctx* c, uint64_t ticket, int32_t* verdict, double* wait_s,
+                                  double* total_s, int32_t* nodes) {
+  API_BEGIN(c)
+  if (ticket == 0 || ticket > c->requests.size()) fail(MNBAB_E_INVALID_ARG, "bad ticket");
+  const Request* r = c->requests[ticket - 1];
+  if (r->state != 2) fail(MNBAB_E_INVALID_ARG, "request not finished");
+  if (verdict) *verdict = r->p->verdict;
+  if (wait_s) *wait_s = r->t_admit - r->t_submit;
+  if (total_s) *total_s = r->t_done - r->t_submit;
+  if (nodes) *nodes = r->p->bounded;
   API_END(c)
 }
 

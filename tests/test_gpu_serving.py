@@ -1,0 +1,104 @@
+"""Request loop (continuous batching): a request's verdict and BaB trace are the
+same whether it runs alone or mixed with requests of other properties and
+networks that arrive while it runs; admission waits for node-pool room;
+timeouts end a request with UNKNOWN."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import conv_case, resnet_spec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Context():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_00263_gb300 import Context
+    return Context
+
+
+def _drain(ctx, tickets, max_nodes=512, steps=5, limit=500):
+    for _ in range(limit):
+        if all(ctx.poll(t) for t in tickets):
+            return
+        ctx.serve_step(max_nodes, steps=steps)
+    raise AssertionError("requests did not finish")
+
+
+def _key(tr):
+    return [(r["seq"], r["row"], r["verdict"], r["split_layer"], r["split_neuron"], r["lb"])
+            for r in tr]
+
+
+def test_results_alone_equal_results_in_the_mix(Context):
+    layers = synth.make_network(1)
+    eps = synth.load_eps(1)
+    prs = synth.make_properties(1, layers, n=5, eps=eps)
+    rl, rC, rd, rlo, rhi, _ = conv_case(11, 0.03, resnet_spec)
+    rspec = synth.make_network(resnet_spec(11))
+    alone = []
+    for pr in prs:
+        with Context(node_capacity=2048) as ctx:
+            net = ctx.load_network(layers)
+            p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+            ctx.set_budget(p, 24)
+            t = ctx.submit(p)
+            _drain(ctx, [t])
+            alone.append((ctx.request_result(t)["verdict"], _key(ctx.trace(p))))
+    with Context(node_capacity=2048) as ctx:
+        res_alone = ctx.load_network(rl)
+        rp = ctx.set_property(res_alone, rlo, rhi, rC, rd)
+        ctx.set_budget(rp, 12)
+        rt = ctx.submit(rp)
+        _drain(ctx, [rt])
+        r_alone = (ctx.request_result(rt)["verdict"], _key(ctx.trace(rp)))
+    with Context(node_capacity=2048) as ctx:
+        net = ctx.load_network(layers)
+        rnet = ctx.load_network(rl)
+        tickets, props = [], []
+        for k, pr in enumerate(prs):
+            p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+            ctx.set_budget(p, 24)
+            tickets.append(ctx.submit(p))
+            props.append(p)
+            if k == 2:   # a request of another network arrives mid-way
+                rp = ctx.set_property(rnet, rlo, rhi, rC, rd)
+                ctx.set_budget(rp, 12)
+                rt = ctx.submit(rp)
+            ctx.serve_step(512, steps=5)   # arrivals while earlier requests run
+        _drain(ctx, tickets + [rt])
+        for t, p, (v, key) in zip(tickets, props, alone):
+            assert ctx.request_result(t)["verdict"] == v
+            assert _key(ctx.trace(p)) == key
+        assert (ctx.request_result(rt)["verdict"], _key(ctx.trace(rp))) == r_alone
+
+
+def test_admission_waits_for_pool_room_and_timeouts(Context):
+    layers = synth.make_network(1)
+    eps = synth.load_eps(1)
+    prs = synth.make_properties(1, layers, n=4, eps=eps, start=50)
+    # room for one request of budget 40 at a time (reservation 9 + 1 + 80 slots)
+    with Context(node_capacity=2 * 1024 + 8 + 100) as ctx:
+        net = ctx.load_network(layers)
+        tickets = []
+        for pr in prs:
+            p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+            ctx.set_budget(p, 40)
+            tickets.append(ctx.submit(p))
+        st = ctx.serve_step(512, steps=5)
+        assert st["admitted"] == 1 and st["queued"] == 3
+        _drain(ctx, tickets, limit=2000)
+        waits = [ctx.request_result(t)["wait_s"] for t in tickets]
+        assert waits[-1] > waits[0]
+        # a request that times out ends UNKNOWN
+        pr = synth.make_properties(1, layers, n=1, eps=eps * 3, start=90)[0]
+        p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+        t = ctx.submit(p, timeout_s=1e-9)
+        _drain(ctx, [t])
+        r = ctx.request_result(t)
+        assert r["verdict"] in (0, -1)
