@@ -487,7 +487,8 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
         const LayerDev& L = edge_of(n, v, k);
         Scope sc(c, L.kind == 1 ? C_BACKSUB_FC : C_BACKSUB_CONV, 2.0 * rows.M * layer_macs(L),
                  4.0 * rows.M * (L.d_out + (out ? L.d_in : 0)) + layer_wbytes(L));
-        used += launch_backsub(L, rows.M, lam_buf(n, v), nd.d[v], out, nd.d[sidx], e, c->st);
+        const int sl = launch_backsub(L, rows.M, lam_buf(n, v), nd.d[v], out, nd.d[sidx], e, c->st);
+        if (last) used += sl;  // raw contributions write no offset partials
       }
       written[sidx] = true;
     }
@@ -1963,7 +1964,7 @@ mnbab_status mnbab_serve_step(mnbab_ctx* c, int32_t max_nodes, const mnbab_adam*
   while (!c->req_queue.empty()) {
     Request* r = c->req_queue.front();
     mnbab_net* n = r->p->net;
-    const int avail = n->cap - 2 * n->B - 8;  // keep room for the pad slot and children
+    const int avail = n->cap - 8;  // the pad slot and a small margin
     if (c->reserved[n->id] + r->reserve > avail) break;
     c->reserved[n->id] += r->reserve;
     r->p->admitted = true;

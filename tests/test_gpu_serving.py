@@ -83,7 +83,7 @@ def test_admission_waits_for_pool_room_and_timeouts(Context):
     eps = synth.load_eps(1)
     prs = synth.make_properties(1, layers, n=4, eps=eps, start=50)
     # room for one request of budget 40 at a time (reservation 9 + 1 + 80 slots)
-    with Context(node_capacity=2 * 1024 + 8 + 100) as ctx:
+    with Context(node_capacity=150) as ctx:
         net = ctx.load_network(layers)
         tickets = []
         for pr in prs:
