@@ -297,7 +297,8 @@ mnbab_status mnbab_submit(mnbab_ctx* ctx, mnbab_prop* prop, double timeout_s, ui
 
 /* One pass of the request loop: admits queued requests in FIFO order while
  * their network's node pool (allocated within the HBM budget) can hold their
- * reservation (n_rows + 1 + 2 * node budget slots), runs one BaB step per
+ * reservation (n_rows + 1 + 2 * node budget slots; a request larger than the
+ * pool runs once its network is idle), runs one BaB step per
  * network over all of its active requests (nodes of different requests share
  * the launches, so requests that arrive while others run join the next
  * batch), and retires requests that reached a verdict, their node budget or

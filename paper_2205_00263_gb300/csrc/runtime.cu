@@ -1965,7 +1965,8 @@ mnbab_status mnbab_serve_step(mnbab_ctx* c, int32_t max_nodes, const mnbab_adam*
     Request* r = c->req_queue.front();
     mnbab_net* n = r->p->net;
     const int avail = n->cap - 8;  // the pad slot and a small margin
-    if (c->reserved[n->id] + r->reserve > avail) break;
+    // a request larger than the room still runs once its network is idle
+    if (c->reserved[n->id] > 0 && c->reserved[n->id] + r->reserve > avail) break;
     c->reserved[n->id] += r->reserve;
     r->p->admitted = true;
     r->state = 1;

@@ -98,6 +98,7 @@ def test_admission_waits_for_pool_room_and_timeouts(Context):
         # a request that times out ends UNKNOWN
         pr = synth.make_properties(1, layers, n=1, eps=eps * 3, start=90)[0]
         p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+        ctx.set_budget(p, 40)
         t = ctx.submit(p, timeout_s=1e-9)
         _drain(ctx, [t])
         r = ctx.request_result(t)
