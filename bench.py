@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--window", type=int, default=WINDOW, help="active properties")
     ap.add_argument("--graphs", action="store_true",
                     help="replay the optimisation loop from captured CUDA graphs")
+    ap.add_argument("--serving", action="store_true",
+                    help="only the serving run (Poisson request stream), full size")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-rate", type=float, default=8.0)
     return ap.parse_args()
 
 
@@ -362,6 +366,15 @@ def run_ours(args):
                "h2d_bytes_per_step": eh // args.e2e_steps, "d2h_bytes_per_step": ed // args.e2e_steps,
                "step": "16 fresh properties from host arrays (32-node budget each) to verdicts"}
 
+    serving = None
+    if world == 1 and args.serve_requests > 0:
+        sctx = Context(device=local, stream=stream.cuda_stream, node_capacity=args.node_capacity)
+        try:
+            serving = serving_run(sctx, serving_nets(sctx), args.serve_requests, args.serve_rate,
+                                  seed=4, timeout_s=60.0, budget=BUDGET, plain_sample=4,
+                                  stream=stream)
+        finally:
+            sctx.close()
     peaks, src = load_peaks()
     roof = roofline(stats, peaks, src, kernels_sha())
     cpu = None
@@ -384,12 +397,92 @@ def run_ours(args):
             "verdicts_in_timed_steps": {"verified": vd[1], "falsified": vd[-1], "unknown": vd[0]},
             "kernel_breakdown_ms": {k: round(v["ms"], 3) for k, v in stats.items()},
             "nodes_timed": tot_nodes,
+            "serving": serving,
             "launches_before_timed": int(launches0),
         }
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# Serving: a Poisson stream of verification requests over the networks whose
+# radius has been calibrated, admitted into the running request loop as they
+# arrive (continuous batching), against the plain per-request loop.
+def serving_run(ctx, nets, n_req, rate, seed, timeout_s, budget, plain_sample, stream):
+    import torch
+    reqs = synth.poisson_stream(rate=rate, n=n_req, seed=seed, nets=tuple(sorted(nets)))
+    host = []
+    for k, r in enumerate(reqs):
+        cfg = r["cfg"]
+        layers, net, eps = nets[cfg]
+        spec = synth.CONFIGS[cfg]
+        x0 = synth.make_image(r["input_seed"], spec["in_shape"]).reshape(-1)
+        y = synth.net_forward(layers, x0)
+        C, d = synth.property_rows(int(np.argmax(y)), y.shape[0])
+        lo, hi = synth.input_box(x0, eps)
+        host.append((r["arrival_s"], cfg, lo, hi, C, d))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pending = list(range(len(host)))
+    tickets = {}
+    nodes = 0
+    while pending or any(not ctx.poll(t) for t in tickets.values()):
+        now = time.perf_counter() - t0
+        while pending and host[pending[0]][0] <= now:
+            k = pending.pop(0)
+            _, cfg, lo, hi, C, d = host[k]
+            p = ctx.set_property(nets[cfg][1], lo, hi, C, d)
+            ctx.set_budget(p, budget)
+            tickets[k] = ctx.submit(p, timeout_s)
+        if not tickets or all(ctx.poll(t) for t in tickets.values()):
+            if pending:
+                time.sleep(max(0.0, host[pending[0]][0] - (time.perf_counter() - t0)))
+            continue
+        st = ctx.serve_step(BATCH, steps=ADAM_STEPS)
+        nodes += st["step"]["nodes_bounded"]
+    wall = time.perf_counter() - t0
+    res = [ctx.request_result(t) for t in tickets.values()]
+    ttv = np.array([r["total_s"] for r in res])
+    verd = {1: 0, -1: 0, 0: 0}
+    for r in res:
+        verd[r["verdict"]] += 1
+    out = {"requests": len(res), "rate_per_s": rate, "networks": sorted(nets),
+           "nodes_per_s": nodes / wall, "nodes": nodes, "wall_s": wall,
+           "time_to_verdict_p50_s": float(np.percentile(ttv, 50)),
+           "time_to_verdict_p99_s": float(np.percentile(ttv, 99)),
+           "verdicts": {"verified": verd[1], "falsified": verd[-1], "unknown": verd[0]},
+           "timeout_s": timeout_s, "node_budget": budget}
+    # plain per-request loop on a sample: one request at a time, one subproblem per launch
+    if plain_sample > 0:
+        pn, t1 = 0, time.perf_counter()
+        for k in range(min(plain_sample, len(host))):
+            _, cfg, lo, hi, C, d = host[k]
+            p = ctx.set_property(nets[cfg][1], lo, hi, C, d)
+            ctx.set_budget(p, budget)
+            for _ in range(100000):
+                st = ctx.bab_step([p], max_nodes=1, steps=ADAM_STEPS)
+                pn += st["nodes_bounded"]
+                if st["nodes_bounded"] == 0 or time.perf_counter() - t1 > 60:
+                    break
+        pw = time.perf_counter() - t1
+        out["plain"] = {"nodes_per_s": pn / pw, "requests": min(plain_sample, len(host)),
+                        "form": "requests one at a time, one subproblem per launch"}
+        out["batched_over_plain"] = out["nodes_per_s"] / out["plain"]["nodes_per_s"]
+    return out
+
+
+def serving_nets(ctx):
+    nets = {}
+    for cfg in (1, 2, 3):
+        try:
+            eps = synth.load_eps(cfg)
+        except (KeyError, OSError, ValueError):
+            continue
+        layers = synth.make_network(cfg)
+        nets[cfg] = (layers, ctx.load_network(layers), eps)
+    return nets
 
 
 # ----------------------------------------------------------------------------
@@ -444,9 +537,30 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serving(args):
+    """Config 4: Poisson stream (rate 4/s, 400 requests, seed 4) over the
+    calibrated networks of configs 1-3, 60 s timeout, continuous batching."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_00263_gb300 import Context
+    stream = torch.cuda.Stream()
+    ctx = Context(device=0, stream=stream.cuda_stream, node_capacity=args.node_capacity,
+                  hbm_budget_bytes=64 << 30)
+    out = serving_run(ctx, serving_nets(ctx), args.serve_requests, args.serve_rate, seed=4,
+                      timeout_s=60.0, budget=BUDGET, plain_sample=8, stream=stream)
+    out["metric"] = METRIC
+    out["workload"] = ("serving: Poisson stream of verification requests over the calibrated "
+                       "networks of configs 1-3, 60 s timeout, 64 GB HBM budget")
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.serving:
+        run_serving(a)
     else:
         run_ours(a)
