@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include "epilogue.cuh"
+#include "mnbab.h"
 #include "mnbab_internal.h"
 
 namespace mnbab {
@@ -26,6 +27,11 @@ __device__ float block_sum(float v) {
   float r = 0.f;
   for (int i = 0; i < nw; ++i) r += sh[i];
   return r;
+}
+
+template <typename F>
+static void set_smem(F f, int bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 // ---------------------------------------------------------------------------
@@ -117,6 +123,136 @@ void launch_init_rows(const NetDev& net, int t, int edge, const RowsDev& rows, f
                       const Epi& e, cudaStream_t st) {
   if (rows.M <= 0) return;
   k_init_rows<<<rows.M, 128, 0, st>>>(net, t, edge, rows, out, ld, e);
+}
+
+// ---------------------------------------------------------------------------
+// windowed rows (intermediate bounds of convolution neurons)
+// ---------------------------------------------------------------------------
+// A row at neuron (co, oh, ow) of zhat_t starts, after its first step, as the
+// k x k kernel patch of output channel co with origin (oh s - p, ow s - p) at
+// layer t-1.  A convolution (stride s, kernel k, padding p) maps coefficients
+// on an h x w window with origin (y0, x0) to a ((h-1)s + k) x ((w-1)s + k)
+// window with origin (y0 s - p, x0 s - p); relative output position yy takes
+// input position Y = (yy - kh) / s wherever that is an integer in [0, h).
+// Positions outside the layer (padding) carry no coefficient.
+constexpr int WIN_MAX_FLOATS = 12288;  // per buffer: two buffers = 96 KB
+
+bool win_plan(const NetDev& net, int t, WinPlan& wp) {
+  if (t < 2 || t > net.R) return false;  // rows at layer 1 are direct in k_init_rows
+  for (int i = 1; i <= t; ++i)
+    if (net.n_edge[i] != 1 || net.src1[i] != i - 1 || net.aff[i].kind != MNBAB_CONV2D)
+      return false;
+  wp.t = t;
+  int h = net.aff[t].k, w = net.aff[t].k;
+  wp.h[t - 1] = h;
+  wp.w[t - 1] = w;
+  int mx = net.aff[t].ci * h * w;
+  for (int i = t - 1; i >= 1; --i) {
+    const LayerDev& L = net.aff[i];
+    h = (h - 1) * L.s + L.k;
+    w = (w - 1) * L.s + L.k;
+    wp.h[i - 1] = h;
+    wp.w[i - 1] = w;
+    mx = std::max(mx, L.ci * h * w);
+  }
+  wp.maxw = mx;
+  return mx <= WIN_MAX_FLOATS;
+}
+
+__global__ void k_win_rows(NetDev net, WinPlan wp, RowsDev rows, Epi e) {
+  extern __shared__ __align__(16) float wsm[];
+  float* A = wsm;
+  float* B = wsm + wp.maxw;
+  const int m = blockIdx.x;
+  const int t = wp.t;
+  const int j = rows.j[m];
+  const float sg = rows.sign ? rows.sign[m] : 1.f;
+  const LayerDev& Lt = net.aff[t];
+  const int hwt = Lt.ho * Lt.wo;
+  const int co = j / hwt, oh = (j % hwt) / Lt.wo, ow = j % Lt.wo;
+  int y0 = oh * Lt.s - Lt.p, x0 = ow * Lt.s - Lt.p;
+  {
+    const int n0 = Lt.ci * Lt.k * Lt.k;
+    for (int q = threadIdx.x; q < n0; q += blockDim.x) A[q] = sg * __ldg(Lt.W + (size_t)co * n0 + q);
+  }
+  const float c0 = sg * (net.bfull[t] ? net.bfull[t][j] : Lt.b[co]);
+  float part = 0.f;
+  int h = Lt.k, w = Lt.k;
+  for (int i = t - 1; i >= 0; --i) {
+    const LayerDev& Ln = net.aff[i + 1];  // layer i is this edge's input
+    const int C = Ln.ci, H = Ln.hi, W = Ln.wi, hw = h * w;
+    __syncthreads();
+    if (i == 0) {
+      // concretisation over the input box
+      const PropDev& P = e.props[e.pool.prop[rows.node[m]]];
+      for (int q = threadIdx.x; q < C * hw; q += blockDim.x) {
+        const int c = q / hw, r = q % hw, y = y0 + r / w, x = x0 + r % w;
+        if (y < 0 || y >= H || x < 0 || x >= W) continue;
+        const int jx = (c * H + y) * W + x;
+        const float a = A[q];
+        part += a * (a >= 0.f ? P.lo[jx] : P.hi[jx]);
+      }
+      break;
+    }
+    // ReLU step of layer i (DeepPoly slopes, splits enforced)
+    Epi el = e;
+    el.kind = EPI_RELU;
+    el.off = net.off[i];
+    el.bias = net.bfull[i];
+    el.bias_div = 1;
+    for (int q = threadIdx.x; q < C * hw; q += blockDim.x) {
+      const int c = q / hw, r = q % hw, y = y0 + r / w, x = x0 + r % w;
+      if (y < 0 || y >= H || x < 0 || x >= W) {
+        A[q] = 0.f;
+        continue;
+      }
+      A[q] = epi_relu(el, m, (c * H + y) * W + x, A[q], part);
+    }
+    __syncthreads();
+    // transposed convolution through layer i's edge
+    const LayerDev& Li = net.aff[i];
+    const int s = Li.s, k = Li.k, kk = k * k;
+    const int h2 = (h - 1) * s + k, w2 = (w - 1) * s + k, hw2 = h2 * w2;
+    const int y2 = y0 * s - Li.p, x2 = x0 * s - Li.p;
+    const size_t wco = (size_t)Li.ci * kk;  // stride of W over output channels
+    for (int q = threadIdx.x; q < Li.ci * hw2; q += blockDim.x) {
+      const int c = q / hw2, r = q % hw2, yy = r / w2, xx = r % w2;
+      const int ya = y2 + yy, xa = x2 + xx;
+      float acc = 0.f;
+      if (ya >= 0 && ya < Li.hi && xa >= 0 && xa < Li.wi) {
+        for (int kh = yy % s; kh < k && kh <= yy; kh += s) {
+          const int Y = (yy - kh) / s;
+          if (Y >= h) continue;
+          for (int kw = xx % s; kw < k && kw <= xx; kw += s) {
+            const int X = (xx - kw) / s;
+            if (X >= w) continue;
+            const float* ap = A + Y * w + X;
+            const float* wp2 = Li.W + (size_t)c * kk + kh * k + kw;
+            for (int o = 0; o < Li.co; ++o) acc = fmaf(ap[o * hw], __ldg(wp2 + o * wco), acc);
+          }
+        }
+      }
+      B[q] = acc;
+    }
+    float* tmp = A;
+    A = B;
+    B = tmp;
+    h = h2;
+    w = w2;
+    y0 = y2;
+    x0 = x2;
+  }
+  const float tot = block_sum(part);
+  if (threadIdx.x == 0) e.part[(size_t)m * e.nslot + e.slot_base] = tot + c0;
+}
+
+void launch_win_rows(const NetDev& net, const WinPlan& wp, const RowsDev& rows, const Epi& e,
+                     cudaStream_t st) {
+  if (rows.M <= 0) return;
+  const int threads = wp.maxw >= 1024 ? 256 : 128;
+  const int smem = 2 * wp.maxw * (int)sizeof(float);
+  set_smem(k_win_rows, smem);
+  k_win_rows<<<rows.M, threads, smem, st>>>(net, wp, rows, e);
 }
 
 // ---------------------------------------------------------------------------
@@ -651,10 +787,6 @@ __global__ void __launch_bounds__(128) k_conv_fwd_row(int M, const float* __rest
   (void)part;  // forward epilogues (adjoint, ReLU) produce no offset partials
 }
 
-template <typename F>
-static void set_smem(F f, int bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
 
 
 // Tensor-core path: always when forced, and automatically when the problem

@@ -125,6 +125,23 @@ int launch_gemm_tc(int M, int N, int K, const float* A, int lda, const float* Bn
 // z^(t-1), with c = sign * b_t[j] into slot 0, through epilogue `e`.
 void launch_init_rows(const NetDev& net, int t, int edge, const RowsDev& rows, float* out, int ld,
                       const Epi& e, cudaStream_t st);
+// Windowed back-substitution of intermediate-bound rows that start at a
+// convolution neuron of zhat_t and meet only convolutions below it: after each
+// step the row is nonzero only within its receptive-field window, so one CTA
+// carries it to the input in shared memory.  h[i] x w[i] is the window at
+// layer i (all of the layer's channels); maxw the largest window in floats.
+struct WinPlan {
+  int t;
+  int h[MNBAB_MAXR + 2], w[MNBAB_MAXR + 2];
+  int maxw;
+};
+// Plan for rows at zhat_t with the DeepPoly epilogue, or false where the layers
+// below t are not a single chain of convolutions or the windows do not fit.
+bool win_plan(const NetDev& net, int t, WinPlan& wp);
+// Bounds of rows.M rows through plan wp: the whole lower bound of row m (offset
+// terms, concretisation and sign * b_t[j]) goes to partial slot e.slot_base.
+void launch_win_rows(const NetDev& net, const WinPlan& wp, const RowsDev& rows, const Epi& e,
+                     cudaStream_t st);
 // Back-substitution through affine layer i: in [M][d_i] -> out [M][d_{i-1}].
 // Returns the number of partial-sum slots used.
 int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,

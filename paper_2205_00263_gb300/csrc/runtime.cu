@@ -148,7 +148,9 @@ struct mnbab_ctx {
   std::vector<std::pair<void*, size_t>> allocs;
   // profiling: kernel-class timing with CUDA events, launch and copy counters
   bool prof = false;
+  // (class | (phase + 1) << 8 | graph-owned << 16, event pair)
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  int phase = -1;  // BaB step phase whose launches are being issued (-1: none)
   std::vector<cudaEvent_t> ev_free;
   int64_t launches = 0;
   int64_t acc_n[32] = {0};
@@ -211,31 +213,39 @@ void d2h(mnbab_ctx* c, T* dst, const T* src, size_t n) {
 
 enum Cat {
   C_BACKSUB_FC, C_BACKSUB_CONV, C_FWD_FC, C_FWD_CONV, C_INIT, C_REDUCE, C_GAMMA, C_ADAM, C_ACS,
-  C_BOOK, NKCAT,
+  C_BOOK, C_WIN, NKCAT,
   // host wall time of the BaB step phases (stream work included up to their syncs)
-  H_ROOTS = NKCAT, H_REBOUND, H_DEEPPOLY, H_OPTIMIZE, H_CONFIRM, H_FINISH, NCAT
+  H_ROOTS = NKCAT, H_REBOUND, H_DEEPPOLY, H_OPTIMIZE, H_CONFIRM, H_FINISH,
+  // device time of all kernel classes launched within each phase
+  G_ROOTS, G_REBOUND, G_DEEPPOLY, G_OPTIMIZE, G_CONFIRM, G_FINISH, NCAT
 };
+constexpr int NPHASE = 6;
 const char* CAT_NAMES[NCAT] = {"backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm",
                                "forward_conv",    "init_rows",              "reduce_lb",
                                "gamma_terms",     "adam",                   "acs",
-                               "bookkeeping",     "step_roots_wall",        "step_rebound_wall",
+                               "bookkeeping",     "backsub_conv_window",    "step_roots_wall",        "step_rebound_wall",
                                "step_deeppoly_wall", "step_optimize_wall",  "step_confirm_wall",
-                               "step_finish_wall"};
+                               "step_finish_wall", "phase_roots_gpu",        "phase_rebound_gpu",
+                               "phase_deeppoly_gpu", "phase_optimize_gpu",   "phase_confirm_gpu",
+                               "phase_finish_gpu"};
 
 struct HostTimer {
   mnbab_ctx* c;
   std::chrono::steady_clock::time_point t;
-  explicit HostTimer(mnbab_ctx* c_) : c(c_), t(std::chrono::steady_clock::now()) {}
+  explicit HostTimer(mnbab_ctx* c_) : c(c_), t(std::chrono::steady_clock::now()) { c->phase = 0; }
+  ~HostTimer() { c->phase = -1; }
   void lap(int cat);
 };
 
 void resolve_prof(mnbab_ctx* c) {
   for (auto& r : c->pending) {
-    const bool owned = r.first >= 1000;  // event pair owned by a captured graph
-    const int cat = owned ? r.first - 1000 : r.first;
+    const bool owned = (r.first >> 16) & 1;  // event pair owned by a captured graph
+    const int cat = r.first & 0xff, phase = ((r.first >> 8) & 0xff) - 1;
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, r.second.first, r.second.second) == cudaSuccess)
+    if (cudaEventElapsedTime(&ms, r.second.first, r.second.second) == cudaSuccess) {
       c->acc_ms[cat] += ms;
+      if (phase >= 0 && phase < NPHASE) c->acc_ms[G_ROOTS + phase] += ms;
+    }
     if (!owned) {
       c->ev_free.push_back(r.second.first);
       c->ev_free.push_back(r.second.second);
@@ -308,11 +318,11 @@ struct Scope {
     if (!a) return;
     if (c->cap) {
       cudaEventRecordWithFlags(b, c->st, cudaEventRecordExternal);
-      c->cap->pairs.push_back({cat, {a, b}});
+      c->cap->pairs.push_back({cat | ((c->phase + 1) << 8), {a, b}});
       return;
     }
     cudaEventRecord(b, c->st);
-    c->pending.push_back({cat, {a, b}});
+    c->pending.push_back({cat | ((c->phase + 1) << 8), {a, b}});
   }
 };
 
@@ -322,6 +332,7 @@ void HostTimer::lap(int cat) {
     c->acc_ms[cat] += std::chrono::duration<double, std::milli>(now - t).count();
     c->acc_n[cat] += 1;
   }
+  c->phase = cat + 1 - H_ROOTS < NPHASE ? cat + 1 - H_ROOTS : -1;  // the phase that follows
   t = now;
 }
 
@@ -429,6 +440,27 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
   mnbab_ctx* c = n->ctx;
   if (rows.M <= 0) return;
   const NetDev& nd = n->nd;
+  WinPlan wp;
+  if (!o.final_mode && !o.store && !o.track && win_plan(nd, t, wp)) {
+    // intermediate-bound rows of a convolution neuron: receptive-field windows
+    double macs = 0.0, elems = (double)nd.aff[t].ci * wp.h[t - 1] * wp.w[t - 1];
+    for (int i = t - 1; i >= 1; --i) {
+      const LayerDev& L = nd.aff[i];
+      const double taps = std::ceil((double)L.k / L.s);
+      macs += (double)L.ci * wp.h[i - 1] * wp.w[i - 1] * L.co * taps * taps;
+      elems += (double)L.ci * wp.h[i - 1] * wp.w[i - 1];
+    }
+    Epi e = base_epi(n, rows.node);
+    e.slot_base = 0;
+    {
+      Scope sc(c, C_WIN, 2.0 * rows.M * macs, 9.0 * rows.M * elems);
+      launch_win_rows(nd, wp, rows, e, c->st);
+    }
+    Scope sc(c, C_REDUCE, 0.0, 4.0 * rows.M);
+    launch_reduce_lb(rows.M, n->part, n->nslot, 1, nullptr, n->lb, false, rows.node, n->pool,
+                     n->X, n->d0, c->st);
+    return;
+  }
   auto setup = [&](Epi& e, int layer) {
     if (layer >= 1) {
       relu_epi(n, e, layer);
@@ -672,7 +704,7 @@ void run_optimize(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
     c->acc_flops[i] += g->flops[i];
     c->acc_bytes[i] += g->bytes[i];
   }
-  for (auto& pr : g->pairs) c->pending.push_back({1000 + pr.first, pr.second});
+  for (auto& pr : g->pairs) c->pending.push_back({(1 << 16) | pr.first, pr.second});
 }
 
 void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
@@ -1326,6 +1358,7 @@ void mnbab_destroy(mnbab_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->st);
   for (auto& r : c->pending) {
+    if ((r.first >> 16) & 1) continue;  // owned by a graph: destroyed with graph_events
     cudaEventDestroy(r.second.first);
     cudaEventDestroy(r.second.second);
   }

@@ -57,11 +57,19 @@ def test_root_bounds(Context, case, path):
         prep = bab.prepare(layers, C, d, lo, hi)
     net, lo_t, hi_t, l, u, S, _, _ = prep
     with Context(node_capacity=64, gemm_path=path) as ctx:
+        ctx.profile(True)
         gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
         for i in range(1, net.R + 1):
             gl, gu = ctx.root_bounds(prop, i)
             _assert_close(gl, l[i].numpy(), f"l{i}")
             _assert_close(gu, u[i].numpy(), f"u{i}")
+        stats, _ = ctx.profile_read()
+        # rows of convolution neurons above a convolution chain take the
+        # receptive-field window kernel; the others the full-width sweep
+        if case in ("conv", "convbig", "resnet"):
+            assert stats["backsub_conv_window"]["launches"] > 0
+        else:
+            assert stats["backsub_conv_window"]["launches"] == 0
 
 
 # --------------------------------------------------------------------------
