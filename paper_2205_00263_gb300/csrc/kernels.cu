@@ -789,6 +789,308 @@ __global__ void __launch_bounds__(128) k_conv_fwd_row(int M, const float* __rest
 
 
 
+// ---------------------------------------------------------------------------
+// implicit-GEMM convolutions for dense rows
+// ---------------------------------------------------------------------------
+// Forward: out[m, n, oy, ox] = sum over (ci, kh, kw) of
+//   in[m, ci, oy s - p + kh, ox s - p + kw] W[n, ci, kh, kw]  (+ b[n]);
+// GEMM rows (m, oy, ox), columns n = co, reduction (ci, kh, kw), weights Wf.
+// Transposed (back-substitution): out[m, n, y, x] = sum over (o, kh, kw) with
+//   (y + p - kh) and (x + p - kw) divisible by s of
+//   in[m, o, (y + p - kh) / s, (x + p - kw) / s] W[o, n, kh, kw].
+// Output positions with (y + p) mod s = ry, (x + p) mod s = rx (a parity
+// class) take exactly the taps kh = ry + s a, kw = rx + s b, so each class is
+// a dense GEMM with reduction (o, a, b) and weights Wb; no masked taps.
+// A CTA computes RB rows x one chunk of pc positions of one class x tn
+// channels; each row has its own group of tpr threads, so a row's outputs and
+// its partial sum do not depend on which rows share the CTA.
+struct IgCfg {
+  int dir;     // 0 forward, 1 transposed
+  int N;       // output channels (co forward, ci transposed)
+  int RB, tpr, pc, nchunk, ncls, tn, ngrp, KC;
+};
+
+struct IgClass {
+  int P, K;             // positions and reduction length of the class
+  int y0, x0, ny, nx;   // first output row / column of the class and their counts
+  int ry, rx, na, nb;   // residues and tap counts (transposed)
+};
+
+__device__ __forceinline__ IgClass ig_class(const LayerDev& L, int dir, int cls) {
+  IgClass c;
+  if (dir == 0) {
+    c.P = L.ho * L.wo;
+    c.K = L.ci * L.k * L.k;
+    c.y0 = c.x0 = 0;
+    c.ny = L.ho;
+    c.nx = L.wo;
+    c.ry = c.rx = 0;
+    c.na = c.nb = L.k;
+    return c;
+  }
+  const int s = L.s;
+  c.ry = cls / s;
+  c.rx = cls % s;
+  c.y0 = ((c.ry - L.p) % s + s) % s;
+  c.x0 = ((c.rx - L.p) % s + s) % s;
+  c.ny = c.y0 < L.hi ? (L.hi - c.y0 + s - 1) / s : 0;
+  c.nx = c.x0 < L.wi ? (L.wi - c.x0 + s - 1) / s : 0;
+  c.na = c.ry < L.k ? (L.k - c.ry + s - 1) / s : 0;
+  c.nb = c.rx < L.k ? (L.k - c.rx + s - 1) / s : 0;
+  c.P = c.ny * c.nx;
+  c.K = L.co * c.na * c.nb;
+  return c;
+}
+
+template <int TN>
+__global__ void __launch_bounds__(256) k_conv_igemm(int M, const float* __restrict__ in, int ld_in,
+                                                    float* out, int ld_out, LayerDev L, Epi e,
+                                                    IgCfg g) {
+  extern __shared__ __align__(16) float ism[];
+  constexpr int TM = 4;
+  constexpr int PPT = 4;  // (row, position) pairs a thread gathers: RB pc <= 4 RB tpr
+  __shared__ int t_off[32], t_dy[32], t_dx[32], t_row[32];
+  const int nthr = blockDim.x;
+  float* As = ism;                              // [KC][RB][pc]
+  float* Bs = ism + (size_t)g.KC * g.RB * g.pc;  // [KC][tn]
+  const int bx = blockIdx.x;
+  const int grp = bx % g.ngrp;
+  const int chunk = (bx / g.ngrp) % g.nchunk;
+  const int cls = bx / (g.ngrp * g.nchunk);
+  const IgClass c = ig_class(L, g.dir, cls);
+  const int m0 = blockIdx.y * g.RB;
+  const int p0 = chunk * g.pc;
+  const int np = max(0, min(g.pc, c.P - p0));
+  const int n0 = grp * g.tn;
+  const int nn = min(g.tn, g.N - n0);
+  const int q = threadIdx.x / g.tpr, tl = threadIdx.x % g.tpr;
+  const int npg = g.pc / TM, nng = g.tn / TN;
+  const int pg = tl % npg, ng = tl / npg;
+  const bool act = q < g.RB && ng < nng;
+  const int rpc = g.RB * g.pc;
+  const float* Wsrc = g.dir == 0 ? L.Wf : L.Wb;
+  // source plane of the gather (input of the forward conv, coefficients of the
+  // transposed one) and this thread's gather pairs, decoded once
+  const int Hs = g.dir == 0 ? L.hi : L.ho, Ws_ = g.dir == 0 ? L.wi : L.wo;
+  int pr_base[PPT], pr_y[PPT], pr_x[PPT];
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int pr = threadIdx.x + i * nthr;
+    const int qq = pr / g.pc, pos = pr % g.pc;
+    pr_base[i] = -1;
+    pr_y[i] = pr_x[i] = 0;
+    if (pr < rpc && m0 + qq < M && pos < np) {
+      const int pi = p0 + pos;
+      const int iy = pi / c.nx, ix = pi % c.nx;
+      int y, x;
+      if (g.dir == 0) {
+        y = iy * L.s - L.p;
+        x = ix * L.s - L.p;
+      } else {
+        y = (c.y0 + L.s * iy + L.p - c.ry) / L.s;
+        x = (c.x0 + L.s * ix + L.p - c.rx) / L.s;
+      }
+      pr_y[i] = y;
+      pr_x[i] = x;
+      pr_base[i] = 0;  // valid pair; the row offset is added at the load
+    }
+  }
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int jn = 0; jn < TN; ++jn) acc[i][jn] = 0.f;
+  const int Kc = np > 0 ? c.K : 0;
+  const int KC = min(g.KC, 32);
+  for (int k0 = 0; k0 < Kc; k0 += KC) {
+    const int kcn = min(KC, Kc - k0);
+    __syncthreads();
+    // reduction-index table of this chunk: channel-plane offset, tap shifts, weight row
+    if (threadIdx.x < kcn) {
+      const int kidx = k0 + threadIdx.x;
+      if (g.dir == 0) {
+        const int kk2 = L.k * L.k;
+        const int ci = kidx / kk2, kh = (kidx / L.k) % L.k, kw = kidx % L.k;
+        t_dy[threadIdx.x] = kh;
+        t_dx[threadIdx.x] = kw;
+        t_off[threadIdx.x] = ci * L.hi * L.wi;
+        t_row[threadIdx.x] = kidx;  // Wf [ci][kh][kw][co]
+      } else {
+        const int nab = c.na * c.nb;
+        const int o = kidx / nab, a = (kidx / c.nb) % c.na, b = kidx % c.nb;
+        t_dy[threadIdx.x] = -a;
+        t_dx[threadIdx.x] = -b;
+        t_off[threadIdx.x] = o * L.ho * L.wo;
+        t_row[threadIdx.x] = (o * L.k + c.ry + L.s * a) * L.k + c.rx + L.s * b;  // Wb [co][kh][kw][ci]
+      }
+    }
+    __syncthreads();
+    // gather the A chunk: consecutive threads take consecutive positions
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      const int pr = threadIdx.x + i * nthr;
+      if (pr >= rpc) break;
+      const float* src = in + (size_t)(m0 + pr / g.pc) * ld_in;
+      for (int kk = 0; kk < kcn; ++kk) {
+        float v = 0.f;
+        if (pr_base[i] == 0) {
+          const int yy = pr_y[i] + t_dy[kk], xx = pr_x[i] + t_dx[kk];
+          if (yy >= 0 && yy < Hs && xx >= 0 && xx < Ws_) v = __ldg(src + t_off[kk] + yy * Ws_ + xx);
+        }
+        As[kk * rpc + pr] = v;
+      }
+    }
+    // the B chunk: weight rows of the reduction indices, channels n0 .. n0 + tn
+    for (int el = threadIdx.x; el < kcn * g.tn; el += nthr) {
+      const int kk = el / g.tn, n = el % g.tn;
+      Bs[kk * g.tn + n] = n < nn ? __ldg(Wsrc + (size_t)t_row[kk] * g.N + n0 + n) : 0.f;
+    }
+    __syncthreads();
+    if (act) {
+      const float* ap = As + q * g.pc + pg * TM;
+      const float* bp = Bs + ng * TN;
+#pragma unroll 4
+      for (int kk = 0; kk < kcn; ++kk) {
+        const float4 a4 = *reinterpret_cast<const float4*>(ap + (size_t)kk * rpc);
+        float bv[TN];
+        if constexpr (TN == 4) {
+          const float4 b4 = *reinterpret_cast<const float4*>(bp + kk * g.tn);
+          bv[0] = b4.x;
+          bv[1] = b4.y;
+          bv[2] = b4.z;
+          bv[3] = b4.w;
+        } else {
+#pragma unroll
+          for (int jn = 0; jn < TN; ++jn) bv[jn] = bp[kk * g.tn + jn];
+        }
+        const float av[TM] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int jn = 0; jn < TN; ++jn) acc[i][jn] = fmaf(av[i], bv[jn], acc[i][jn]);
+      }
+    }
+  }
+  // epilogue
+  float part = 0.f;
+  const int m = m0 + q;
+  if (act && m < M) {
+    const int plane = g.dir == 0 ? L.ho * L.wo : L.hi * L.wi;
+    const int W2 = g.dir == 0 ? L.wo : L.wi;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int pos = pg * TM + i;
+      if (pos >= np) break;
+      const int pi = p0 + pos;
+      const int iy = pi / c.nx, ix = pi % c.nx;
+      const int y = g.dir == 0 ? iy : c.y0 + L.s * iy;
+      const int x = g.dir == 0 ? ix : c.x0 + L.s * ix;
+#pragma unroll
+      for (int jn = 0; jn < TN; ++jn) {
+        const int n = ng * TN + jn;
+        if (n >= nn) break;
+        const int j = (n0 + n) * plane + y * W2 + x;
+        float v = acc[i][jn];
+        if (g.dir == 0) v += L.b[n0 + n];
+        const float o = epi_apply(e, m, j, v, part);
+        if (out) out[(size_t)m * ld_out + j] = o;
+      }
+    }
+  }
+  if (g.dir == 1 && epi_has_part(e)) {
+    // per-row sum in a fixed order: warps of the row group, then their sums
+    __shared__ float wsum[32];
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = part;
+    __syncthreads();
+    const int wpr = g.tpr >> 5;
+    if (tl == 0 && q < g.RB && m < M) {
+      float tot = 0.f;
+      for (int w = 0; w < wpr; ++w) tot += wsum[q * wpr + w];
+      e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = tot;
+    }
+  }
+}
+
+static IgCfg ig_plan(const LayerDev& L, int dir, int M) {
+  IgCfg g;
+  g.dir = dir;
+  g.N = dir == 0 ? L.co : L.ci;
+  const int TN = g.N % 4 == 0 ? 4 : 1;
+  g.tn = TN == 4 ? std::min(g.N, 64) : std::min(g.N, 8);
+  g.ncls = dir == 0 ? 1 : L.s * L.s;
+  int pmax = 0;
+  if (dir == 0) {
+    pmax = L.ho * L.wo;
+  } else {
+    for (int r = 0; r < L.s; ++r) {
+      const int y0 = ((r - L.p) % L.s + L.s) % L.s;
+      const int ny = y0 < L.hi ? (L.hi - y0 + L.s - 1) / L.s : 0;
+      for (int r2 = 0; r2 < L.s; ++r2) {
+        const int x0 = ((r2 - L.p) % L.s + L.s) % L.s;
+        const int nx = x0 < L.wi ? (L.wi - x0 + L.s - 1) / L.s : 0;
+        pmax = std::max(pmax, ny * nx);
+      }
+    }
+  }
+  const int cap = TN == 4 ? 64 : 128;
+  g.pc = std::max(4, std::min((pmax + 3) / 4 * 4, cap));
+  // few rows: fewer rows per CTA, then narrower channel groups and shorter
+  // position chunks, so that the grid covers the SMs (at most the ig_slots blocks)
+  g.RB = 8;
+  for (;;) {
+    g.ngrp = (g.N + g.tn - 1) / g.tn;
+    g.nchunk = std::max(1, (pmax + g.pc - 1) / g.pc);
+    g.tpr = ((g.pc / 4) * (g.tn / TN) + 31) / 32 * 32;
+    g.RB = std::max(1, std::min(g.RB, 256 / g.tpr));
+    const long blocks = (long)((M + g.RB - 1) / g.RB) * g.ncls * g.nchunk * g.ngrp;
+    if (blocks >= 2 * 152) break;
+    if (g.RB > 1) g.RB >>= 1;
+    else if (TN == 4 && g.tn > 16) g.tn = (g.tn / 2 + 3) / 4 * 4;
+    else if (g.pc > 16) g.pc = std::max(16, (g.pc / 2 + 3) / 4 * 4);
+    else break;
+  }
+  g.KC = g.RB * g.pc <= 512 ? 32 : 16;  // at most 32 (reduction-index table)
+  return g;
+}
+
+static int ig_smem(const IgCfg& g) { return g.KC * (g.RB * g.pc + g.tn) * (int)sizeof(float); }
+
+static bool ig_supported(const LayerDev& L, int dir) {
+  const IgCfg g = ig_plan(L, dir, 1 << 20);
+  return g.tpr <= 256 && ig_smem(g) <= 96 * 1024 && (dir == 0 ? L.Wf : L.Wb) != nullptr;
+}
+
+static int ig_slots(const LayerDev& L) {
+  // the finest split of ig_plan (one row: position chunks of 16, channel groups of 16)
+  const IgCfg g = ig_plan(L, 1, 1);
+  return g.ncls * g.nchunk * g.ngrp;
+}
+
+// Per-row work above which the implicit GEMM beats the row-resident kernels
+// (whose per-row CTAs then serialise too much work)
+static bool ig_preferred(const LayerDev& L) {
+  return (double)L.co * L.ho * L.wo * L.ci * L.k * L.k >= 512.0 * 1024.0;
+}
+
+// launches the implicit-GEMM kernel; returns the partial-sum slots (transposed)
+static int launch_ig(const LayerDev& L, int dir, int M, const float* in, int ld_in, float* out,
+                     int ld_out, const Epi& e, cudaStream_t st) {
+  const IgCfg g = ig_plan(L, dir, M);
+  const int smem = ig_smem(g);
+  dim3 grid(g.ncls * g.nchunk * g.ngrp, (M + g.RB - 1) / g.RB);
+  const int thr = g.RB * g.tpr;
+  if (g.N % 4 == 0) {
+    set_smem(k_conv_igemm<4>, smem);
+    k_conv_igemm<4><<<grid, thr, smem, st>>>(M, in, ld_in, out, ld_out, L, e, g);
+  } else {
+    set_smem(k_conv_igemm<1>, smem);
+    k_conv_igemm<1><<<grid, thr, smem, st>>>(M, in, ld_in, out, ld_out, L, e, g);
+  }
+  return grid.x;
+}
+
 // Tensor-core path: always when forced, and automatically when the problem
 // fills at least two waves of 128 x BN tiles on the 152 SMs.
 static bool use_tc(const Epi& e, int M, int N) {
@@ -807,10 +1109,11 @@ bool conv_supported(const LayerDev& L) {
 
 int backsub_slots(const LayerDev& L) {
   if (L.kind == 1) return (L.d_in + 31) / 32;  // upper bound over the tile shapes
-  // upper bound over the row-resident splits (<= 32 CTAs per row, more for large
-  // planes) and the fallback tiling (128 positions per CTA)
+  // upper bound over the implicit-GEMM blocks, the row-resident splits (<= 32
+  // CTAs per row, more for large planes) and the fallback tiling (128 positions
+  // per CTA)
   const int P = L.hi * L.wi;
-  return std::max(32 * ((P + 1023) / 1024), (P + 127) / 128);
+  return std::max(std::max(32 * ((P + 1023) / 1024), (P + 127) / 128), ig_slots(L));
 }
 
 int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
@@ -823,6 +1126,10 @@ int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* 
                             e, e.err, st);
     return gemm_launch(M, L.d_in, L.d_out, in, ld_in, L.W, L.d_in, nullptr, 1, out, ld_out, e, st);
   }
+  // dense rows: implicit GEMM per parity class; rows that start at a neuron
+  // (nonzero only near it) skip the zero region in the row-resident kernel
+  if (!e.sparse_rows && ig_supported(L, 1) && (ig_preferred(L) || !conv_supported(L)))
+    return launch_ig(L, 1, M, in, ld_in, out, ld_out, e, st);
   {
     const int CBv = L.ci <= 1 ? 1 : (L.ci <= 4 ? 4 : 8);
     const ConvSplit cs = conv_split(M, L.hi * L.wi, (L.ci + CBv - 1) / CBv, CBv,
@@ -871,6 +1178,10 @@ void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float*
       return;
     }
     gemm_launch(M, L.d_out, L.d_in, in, ld_in, L.Wt, L.d_out, L.b, 1, out, ld_out, e, st);
+    return;
+  }
+  if (ig_supported(L, 0) && (ig_preferred(L) || !conv_supported(L))) {
+    launch_ig(L, 0, M, in, ld_in, out, ld_out, e, st);
     return;
   }
   {

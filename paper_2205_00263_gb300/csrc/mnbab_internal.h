@@ -113,6 +113,8 @@ struct Epi {
   size_t ws_floats;
   const float* acc_in;  // earlier edge's contribution added before the epilogue (may alias out)
   int acc_ld;
+  int sparse_rows;   // rows started at one neuron and met only convolutions since:
+                     // nonzero near it, so conv steps skip the zero region
 };
 
 // ---- launchers (kernels.cu, tc_gemm.cu) ----------------------------------

@@ -497,6 +497,7 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
   if (rows.M > n->chunk && rows.M > n->B) fail(MNBAB_E_DEVICE, "row block larger than scratch");
   bool written[MNBAB_MAXR + 2] = {false};
   int used = 0;
+  bool conv_only = t <= nd.R;  // every edge met so far is a convolution
   for (int v = t; v >= 1; --v) {
     if (!reached[v]) continue;
     for (int k = 0; k < nd.n_edge[v]; ++k) {
@@ -510,6 +511,7 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
         e.acc_ld = nd.d[sidx];
       }
       e.slot_base = used;
+      e.sparse_rows = conv_only ? 1 : 0;
       float* out = (sidx >= 1 || !last) ? lam_buf(n, sidx) : nullptr;
       if (v == t) {
         Scope sc(c, C_INIT, 0.0, 4.0 * rows.M * nd.d[sidx]);
@@ -524,6 +526,8 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
       }
       written[sidx] = true;
     }
+    for (int k = 0; k < nd.n_edge[v]; ++k)
+      if (edge_of(n, v, k).kind != MNBAB_CONV2D) conv_only = false;
   }
   Scope sc(c, C_REDUCE, 0.0, 4.0 * rows.M * used);
   launch_reduce_lb(rows.M, n->part, n->nslot, used,
