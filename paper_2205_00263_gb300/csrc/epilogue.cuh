@@ -97,6 +97,111 @@ __device__ __forceinline__ float epi_apply(const Epi& e, int m, int j, float v, 
   }
 }
 
+// Two-phase form of epi_apply for kernels that finish several outputs per
+// thread: epi_load issues every global load an output's epilogue needs (so the
+// loads of all of a thread's outputs are in flight together), epi_finish does
+// the same arithmetic as epi_apply on the loaded values.
+struct EpiIn {
+  float acc, l, u, al, be, gp, gph;
+  int s;
+};
+
+__device__ __forceinline__ const PropDev* epi_prop(const Epi& e, int n) {
+  return e.kind == EPI_CONC ? &e.props[e.pool.prop[n]] : nullptr;
+}
+
+__device__ __forceinline__ void epi_load(const Epi& e, int n, const PropDev* P, int m, int j,
+                                         EpiIn& in) {
+  in.acc = e.acc_in ? e.acc_in[(size_t)m * e.acc_ld + j] : 0.f;
+  in.al = in.be = in.gp = in.gph = 0.f;
+  in.s = 0;
+  if (e.kind == EPI_RELU || e.kind == EPI_ADJ) {
+    const size_t q = (size_t)n * e.SD + e.off + j;
+    const size_t qm = (size_t)m * e.SD + e.off + j;
+    in.l = e.pool.L[q];
+    in.u = e.pool.U[q];
+    in.s = e.pool.S[q];
+    if (e.kind == EPI_RELU) {
+      if (e.final_mode) {
+        in.al = e.pool.ALPHA[q];
+        in.be = e.pool.BETA[q];
+      }
+      if (e.GP) in.gp = e.GP[qm];
+      if (e.GPh) in.gph = e.GPh[qm];
+    } else {
+      in.al = e.pool.ALPHA[q];
+      in.gp = e.AP[qm];
+    }
+  } else if (e.kind == EPI_CONC) {
+    in.l = P->lo[j];
+    in.u = P->hi[j];
+  }
+}
+
+__device__ __forceinline__ float epi_finish(const Epi& e, int m, int j, float v, const EpiIn& in,
+                                            float& part) {
+  if (e.acc_in) v += in.acc;
+  switch (e.kind) {
+    case EPI_RELU: {
+      const size_t qm = (size_t)m * e.SD + e.off + j;
+      const float l = in.l, u = in.u;
+      const int s = in.s;
+      float ap = v;
+      if (e.GP) ap += in.gp;
+      float D, bl = 0.f;
+      if (s == -1) D = 1.f;
+      else if (s == 1) D = 0.f;
+      else if (l >= 0.f) D = 1.f;
+      else if (u <= 0.f) D = 0.f;
+      else if (ap >= 0.f) D = e.final_mode ? in.al : (u >= -l ? 1.f : 0.f);
+      else {
+        const float den = u - l;
+        D = u / den;
+        bl = (-u * l) / den;
+      }
+      float ah = ap * D;
+      if (e.final_mode) ah += in.be * (float)s;
+      if (e.GPh) ah += in.gph;
+      if (e.AP) e.AP[qm] = ap;
+      part += ap * bl + ah * e.bias[j / e.bias_div];
+      return ah;
+    }
+    case EPI_CONC: {
+      const float x = v >= 0.f ? in.l : in.u;
+      part += v * x;
+      if (e.X) e.X[(size_t)m * e.d0 + j] = x;
+      return v;
+    }
+    case EPI_ADJ: {
+      const size_t qm = (size_t)m * e.SD + e.off + j;
+      const float l = in.l, u = in.u, ap = in.gp, h = v;
+      const int s = in.s;
+      float D, bl = 0.f;
+      bool abr = false;
+      if (s == -1) D = 1.f;
+      else if (s == 1) D = 0.f;
+      else if (l >= 0.f) D = 1.f;
+      else if (u <= 0.f) D = 0.f;
+      else if (ap >= 0.f) { D = in.al; abr = true; }
+      else {
+        const float den = u - l;
+        D = u / den;
+        bl = (-u * l) / den;
+      }
+      e.GA[qm] = abr ? h * ap : 0.f;
+      e.GB[qm] = h * (float)s;
+      const float g = h * D + bl;
+      if (e.Hz) {
+        e.Hz[qm] = h;
+        e.Gz[qm] = g;
+      }
+      return g;
+    }
+    case EPI_FWD_RELU: return fmaxf(v, 0.f);
+    default: return v;
+  }
+}
+
 __device__ __forceinline__ bool epi_has_part(const Epi& e) {
   return e.part != nullptr && (e.kind == EPI_RELU || e.kind == EPI_CONC);
 }

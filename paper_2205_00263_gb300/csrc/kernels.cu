@@ -567,6 +567,56 @@ __global__ void __launch_bounds__(128) k_conv_fwd(int M, const float* __restrict
   }
 }
 
+// Staging into shared memory with all of a thread's loads in flight: rows of
+// `width` floats taken at src + r * stride (r < nrows), written densely.  float4
+// loads when every row start is 16-byte aligned, 4 per thread per round.
+__device__ __forceinline__ void stage_rows(float* __restrict__ dst, const float* __restrict__ src,
+                                           int nrows, int width, size_t stride, int valid) {
+  const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) |
+                     (stride * 4)) & 15) == 0 &&
+                   (width & 3) == 0 && (valid & 3) == 0;
+  if (vec) {
+    const int w4 = width >> 2, n4 = nrows * w4;
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    int i = threadIdx.x;
+    const int bd = blockDim.x;
+    for (; i + 3 * bd < n4; i += 4 * bd) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int ii = i + u * bd, r = ii / w4, c = (ii % w4) * 4;
+        v[u] = c < valid ? __ldg(reinterpret_cast<const float4*>(src + r * stride + c))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) d4[i + u * bd] = v[u];
+    }
+    for (; i < n4; i += bd) {
+      const int r = i / w4, c = (i % w4) * 4;
+      d4[i] = c < valid ? __ldg(reinterpret_cast<const float4*>(src + r * stride + c))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    return;
+  }
+  const int n = nrows * width;
+  int i = threadIdx.x;
+  const int bd = blockDim.x;
+  for (; i + 3 * bd < n; i += 4 * bd) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int ii = i + u * bd, r = ii / width, c = ii % width;
+      v[u] = c < valid ? __ldg(src + r * stride + c) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) dst[i + u * bd] = v[u];
+  }
+  for (; i < n; i += bd) {
+    const int r = i / width, c = i % width;
+    dst[i] = c < valid ? __ldg(src + r * stride + c) : 0.f;
+  }
+}
+
 // Row-resident convolution kernels.  A CTA takes one row, one chunk of output
 // positions and one group of channel blocks.  It stages the row's input and
 // its slice of the weights (pre-arranged in global memory so that a channel
@@ -617,10 +667,8 @@ __global__ void __launch_bounds__(128) k_convT_row(int M, const float* __restric
   float* Ws = sm;                   // [co][kh][kw][cw]
   float* Ls = sm + L.co * kk * cw;  // input row
   const int m = blockIdx.y;
-  for (int i = threadIdx.x; i < L.co * kk * cw; i += blockDim.x) {
-    const int c = i % cw, t = i / cw;
-    Ws[i] = (c0 + c < c1) ? L.Wb[(size_t)t * L.ci + c0 + c] : 0.f;
-  }
+  // weight slice: rows (co, kh, kw) of Wb [co][kh][kw][ci], channels c0 .. c0 + cw
+  stage_rows(Ws, L.Wb + c0, L.co * kk, cw, (size_t)L.ci, c1 - c0);
   const float* lam = in + (size_t)m * ld_in;
   // bounding box (over all channels) of the row's nonzero coefficients: rows
   // that start at a convolution neuron are nonzero only in its receptive field
@@ -628,10 +676,16 @@ __global__ void __launch_bounds__(128) k_convT_row(int M, const float* __restric
   if (threadIdx.x == 0) { box[0] = L.ho; box[1] = -1; box[2] = L.wo; box[3] = -1; }
   __syncthreads();
   int bh0 = L.ho, bh1 = -1, bw0 = L.wo, bw1 = -1;
-  for (int i = threadIdx.x; i < nIn; i += blockDim.x) {
-    const float v = lam[i];
-    Ls[i] = v;
-    if (v != 0.f) {
+  stage_rows(Ls, lam, 1, nIn, 0, nIn);
+  __syncthreads();
+  // (dense rows: the whole plane)
+  if (!e.sparse_rows) {
+    bh0 = bw0 = 0;
+    bh1 = L.ho - 1;
+    bw1 = L.wo - 1;
+  }
+  for (int i = threadIdx.x; e.sparse_rows && i < nIn; i += blockDim.x) {
+    if (Ls[i] != 0.f) {
       const int r = i % (L.ho * L.wo), oh = r / L.wo, ow = r % L.wo;
       bh0 = min(bh0, oh); bh1 = max(bh1, oh); bw0 = min(bw0, ow); bw1 = max(bw1, ow);
     }
@@ -650,6 +704,8 @@ __global__ void __launch_bounds__(128) k_convT_row(int M, const float* __restric
   const int p0 = chunk * cs.ppc;
   const int np = min(cs.ppc, Pin - p0);
   const int hwo = L.ho * L.wo;
+  const int rn = e.row_node[m];
+  const PropDev* rp = epi_prop(e, rn);
   float part = 0.f;
   for (int item = threadIdx.x; item < np * (b1 - b0); item += blockDim.x) {
     const int cb = b0 + item / np, pidx = p0 + item % np;
@@ -697,12 +753,16 @@ __global__ void __launch_bounds__(128) k_convT_row(int M, const float* __restric
         }
       }
     }
+    EpiIn pin[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c)
+      if (cb * CB + c < L.ci) epi_load(e, rn, rp, m, (cb * CB + c) * Pin + ih * L.wi + iw, pin[c]);
 #pragma unroll
     for (int c = 0; c < CB; ++c) {
       const int ci = cb * CB + c;
       if (ci >= L.ci) break;
       const int j = ci * Pin + ih * L.wi + iw;
-      const float o = epi_apply(e, m, j, acc[c], part);
+      const float o = epi_finish(e, m, j, acc[c], pin[c], part);
       if (out) out[(size_t)m * ld_out + j] = o;
     }
   }
@@ -731,17 +791,15 @@ __global__ void __launch_bounds__(128) k_conv_fwd_row(int M, const float* __rest
   float* Ws = sm;                   // [ci][kh][kw][cw]
   float* Xs = sm + L.ci * kk * cw;  // input row
   const int m = blockIdx.y;
-  for (int i = threadIdx.x; i < L.ci * kk * cw; i += blockDim.x) {
-    const int c = i % cw, t = i / cw;
-    Ws[i] = (c0 + c < c1) ? L.Wf[(size_t)t * L.co + c0 + c] : 0.f;
-  }
-  const float* x = in + (size_t)m * ld_in;
-  for (int i = threadIdx.x; i < nIn; i += blockDim.x) Xs[i] = x[i];
+  // weight slice: rows (ci, kh, kw) of Wf [ci][kh][kw][co], channels c0 .. c0 + cw
+  stage_rows(Ws, L.Wf + c0, L.ci * kk, cw, (size_t)L.co, c1 - c0);
+  stage_rows(Xs, in + (size_t)m * ld_in, 1, nIn, 0, nIn);
   __syncthreads();
   const int P = L.ho * L.wo;
   const int p0 = chunk * cs.ppc;
   const int np = min(cs.ppc, P - p0);
   const int hwi = L.hi * L.wi;
+  const int rn = (e.kind == EPI_RELU || e.kind == EPI_ADJ) ? e.row_node[m] : 0;
   float part = 0.f;
   for (int item = threadIdx.x; item < np * (b1 - b0); item += blockDim.x) {
     const int cb = b0 + item / np, pos = p0 + item % np;
@@ -775,12 +833,16 @@ __global__ void __launch_bounds__(128) k_conv_fwd_row(int M, const float* __rest
         }
       }
     }
+    EpiIn pin[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c)
+      if (cb * CB + c < L.co) epi_load(e, rn, nullptr, m, (cb * CB + c) * P + pos, pin[c]);
 #pragma unroll
     for (int c = 0; c < CB; ++c) {
       const int co = cb * CB + c;
       if (co >= L.co) break;
       const int j = co * P + pos;
-      const float o = epi_apply(e, m, j, acc[c] + L.b[co], part);
+      const float o = epi_finish(e, m, j, acc[c] + L.b[co], pin[c], part);
       if (out) out[(size_t)m * ld_out + j] = o;
     }
   }
