@@ -5,7 +5,10 @@ For every property the largest radius eps_p at which a single DeepPoly pass
 branching, no slope optimisation) verifies it is found by bisection on
 [0, 0.5]; the workload radius is the largest eps at which at least 30% of the
 properties verify, i.e. the ceil(0.3 n)-th largest eps_p, times 1.5.  Only the
-FP64 oracle is used.  Run: ``python -m oracle.calibrate_eps 0 1``.
+FP64 oracle is used.  Run: ``python -m oracle.calibrate_eps 0 1``; the large
+convolutional networks use a sample of properties and a narrower bracket
+(``python -m oracle.calibrate_eps 3 2 --n 6 --iters 7 --hi 0.02``: DeepPoly
+fails for every sampled property at 0.02).
 """
 from __future__ import annotations
 
@@ -46,18 +49,19 @@ def critical_eps(net, x0, iters=20, hi_eps=0.5) -> float:
 
 
 def calibrate(cfg: int, n_props: int | None = None, iters: int = 20, frac: float = 0.3,
-              factor: float = 1.5) -> dict:
+              factor: float = 1.5, hi_eps: float = 0.5) -> dict:
     layers = synth.make_network(cfg)
     props = synth.make_properties(cfg, layers, n=n_props)
     crit = []
     for pr in props:
         net = core.fold_property(core.load_net(layers), pr.C, pr.d)
-        crit.append(critical_eps(net, pr.x0, iters))
+        crit.append(critical_eps(net, pr.x0, iters, hi_eps))
+        print(cfg, "property", pr.index, "critical eps", crit[-1], flush=True)
     s = sorted(crit, reverse=True)
     k = max(1, math.ceil(frac * len(s)))
     eps0 = s[k - 1]
     return dict(eps=eps0 * factor, eps_deeppoly_30pct=eps0, n_props=len(props),
-                bisection_iters=iters, critical=crit)
+                bisection_iters=iters, bracket=[0.0, hi_eps], critical=crit)
 
 
 def main(argv):
@@ -66,6 +70,7 @@ def main(argv):
     ap.add_argument("cfgs", nargs="*", type=int, default=[0, 1])
     ap.add_argument("--n", type=int, default=None, help="properties (default: the config's)")
     ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--hi", type=float, default=0.5, help="upper end of the bisection bracket")
     a = ap.parse_args(argv)
     cfgs = a.cfgs
     try:
@@ -75,7 +80,7 @@ def main(argv):
         data = {}
     for c in cfgs:
         t = time.time()
-        r = calibrate(c, n_props=a.n, iters=a.iters)
+        r = calibrate(c, n_props=a.n, iters=a.iters, hi_eps=a.hi)
         r["seconds"] = round(time.time() - t, 1)
         data[str(c)] = r
         print(c, r["eps"], r["seconds"], flush=True)
