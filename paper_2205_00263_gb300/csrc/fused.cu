@@ -1,0 +1,504 @@
+// Fused optimisation loop (Sec. 3.1) for chain networks without multi-neuron
+// constraints: one CTA carries one objective row through all Adam iterations.
+//
+// Per iteration the CTA runs, on its row alone:
+//   1. the back-substitution sweep at the node's current (alpha, beta): the
+//      objective row a = (C W_L)_r, then for t = R .. 1 the ReLU step of layer t
+//      (a' = a; D, blow by the sign of a'; ahat = a' D + beta S; offset
+//      a' blow + ahat b_t) followed by the affine step through layer t, and the
+//      concretisation over the input box (x*_k = lo_k if a0_k >= 0 else hi_k);
+//   2. best-bound tracking: the node keeps the best bound and its minimiser;
+//   3. the adjoint: the relaxed network evaluated forward at x* (h_t = W_t g +
+//      b_t, g_t = h_t D_t + blow_t) gives d lb / d alpha_j = h_j a'_j on the
+//      alpha branch and d lb / d beta_j = h_j S_j;
+//   4. projected Adam on (alpha, beta) with the gradient-scaled eps.
+// The coefficient rows, the a' checkpoints, the gradients and x* stay in shared
+// memory; only the node's state (bounds, splits, parameters, moments) and the
+// weights are read from global memory.  The arithmetic of each element is that
+// of the unfused kernels; sums are accumulated in a different order.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "epilogue.cuh"
+#include "mnbab.h"
+#include "mnbab_internal.h"
+
+namespace mnbab {
+
+namespace {
+
+constexpr int FT = 1024;  // threads per CTA
+
+__device__ __forceinline__ float f_block_sum(float v, float* red) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = 0.f;
+  for (int i = 0; i < FT / 32; ++i) r += red[i];
+  return r;
+}
+
+__device__ __forceinline__ float f_block_max(float v, float* red) {
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = 0.f;
+  for (int i = 0; i < FT / 32; ++i) r = fmaxf(r, red[i]);
+  return r;
+}
+
+__device__ __forceinline__ void f_adam(float& th, float& mo, float& ve, float g, float lr,
+                                       float b1, float b2, float eps, float bc1, float bc2) {
+  mo = b1 * mo + (1.f - b1) * g;
+  ve = b2 * ve + (1.f - b2) * g * g;
+  const float mh = mo / bc1;
+  const float vh = ve / bc2;
+  th = th + lr * mh / (sqrtf(vh) + eps);
+}
+
+// Threads that share one output (a split of its reduction over adjacent
+// lanes): the largest power of two <= 8 with items * KS <= FT.
+__device__ __forceinline__ int f_split(int items) {
+  int ks = 1;
+  while (ks < 8 && items * ks * 2 <= FT) ks <<= 1;
+  return ks;
+}
+
+__device__ __forceinline__ float f_group_sum(float v, int ks) {
+  for (int o = ks >> 1; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Back-substitution through FC layer L: cur (d_out) -> nxt (d_in) = cur W.
+__device__ void f_fc_back(const LayerDev& L, const float* cur, float* nxt) {
+  const int din = L.d_in, dout = L.d_out;
+  const bool vec = (din & 3) == 0 && (reinterpret_cast<uintptr_t>(L.W) & 15) == 0;
+  const int CB = vec ? 4 : 1;
+  const int items = din / CB;
+  const int ks = f_split(items);
+  const int rounds = (items * ks + FT - 1) / FT;
+  for (int rr = 0; rr < rounds; ++rr) {
+    const int b = rr * FT + threadIdx.x;
+    const int it = b / ks, k0 = b % ks;
+    const bool act = it < items;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (act) {
+      if (vec) {
+        const float4* w4 = reinterpret_cast<const float4*>(L.W) + it;
+        const int n4 = din >> 2;
+        int j = k0;
+        for (; j + 3 * ks < dout; j += 4 * ks) {
+          float4 w[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) w[u] = __ldg(w4 + (size_t)(j + u * ks) * n4);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float a = cur[j + u * ks];
+            a0 = fmaf(a, w[u].x, a0);
+            a1 = fmaf(a, w[u].y, a1);
+            a2 = fmaf(a, w[u].z, a2);
+            a3 = fmaf(a, w[u].w, a3);
+          }
+        }
+        for (; j < dout; j += ks) {
+          const float4 w = __ldg(w4 + (size_t)j * n4);
+          const float a = cur[j];
+          a0 = fmaf(a, w.x, a0);
+          a1 = fmaf(a, w.y, a1);
+          a2 = fmaf(a, w.z, a2);
+          a3 = fmaf(a, w.w, a3);
+        }
+      } else {
+        for (int j = k0; j < dout; j += ks) a0 = fmaf(cur[j], __ldg(L.W + (size_t)j * din + it), a0);
+      }
+    }
+    a0 = f_group_sum(a0, ks);
+    if (vec) {
+      a1 = f_group_sum(a1, ks);
+      a2 = f_group_sum(a2, ks);
+      a3 = f_group_sum(a3, ks);
+    }
+    if (act && k0 == 0) {
+      if (vec) reinterpret_cast<float4*>(nxt)[it] = make_float4(a0, a1, a2, a3);
+      else nxt[it] = a0;
+    }
+  }
+}
+
+// Forward through FC layer L: g (d_in) -> h (d_out) = W g + b; one warp per output.
+__device__ void f_fc_fwd(const LayerDev& L, const float* g, float* h) {
+  const int din = L.d_in, dout = L.d_out;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool vec = (din & 3) == 0 && (reinterpret_cast<uintptr_t>(L.W) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(g) & 15) == 0;
+  for (int i = warp; i < dout; i += FT / 32) {
+    float acc = 0.f;
+    if (vec) {
+      const float4* w4 = reinterpret_cast<const float4*>(L.W + (size_t)i * din);
+      const float4* g4 = reinterpret_cast<const float4*>(g);
+      const int n4 = din >> 2;
+      for (int c0 = lane; c0 < n4; c0 += 32 * 4) {
+        float4 w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = c0 + 32 * u;
+          w[u] = c < n4 ? __ldg(w4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = c0 + 32 * u;
+          if (c < n4) {
+            const float4 x = g4[c];
+            acc = fmaf(w[u].x, x.x, acc);
+            acc = fmaf(w[u].y, x.y, acc);
+            acc = fmaf(w[u].z, x.z, acc);
+            acc = fmaf(w[u].w, x.w, acc);
+          }
+        }
+      }
+    } else {
+      for (int j = lane; j < din; j += 32) acc = fmaf(__ldg(L.W + (size_t)i * din + j), g[j], acc);
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) h[i] = acc + L.b[i];
+  }
+}
+
+// Transposed convolution (back-substitution) through conv layer L with its
+// weights in shared memory as Wb [co][kh][kw][ci]: cur [co][ho][wo] -> nxt
+// [ci][hi][wi].  A thread group takes one input position and CB channels; the
+// valid taps of a position are those with kh = (ih + p) mod s (+ s, ...).
+__device__ void f_conv_back(const LayerDev& L, const float* cur, float* nxt, const float* Wb) {
+  const int CB = (L.ci & 3) == 0 ? 4 : 1;
+  const int ngr = L.ci / CB, P = L.hi * L.wi, hwo = L.ho * L.wo;
+  const int items = P * ngr;
+  const int ks = f_split(items);
+  const int rounds = (items * ks + FT - 1) / FT;
+  const size_t wco = (size_t)L.k * L.k * L.ci;
+  for (int rr = 0; rr < rounds; ++rr) {
+    const int b = rr * FT + threadIdx.x;
+    const int it = b / ks, k0 = b % ks;
+    const bool act = it < items;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int grp = 0, ih = 0, iw = 0;
+    if (act) {
+      grp = it / P;
+      const int pos = it % P;
+      ih = pos / L.wi;
+      iw = pos % L.wi;
+      const int kh0 = (ih + L.p) % L.s, kw0 = (iw + L.p) % L.s;
+      const int oh0 = (ih + L.p - kh0) / L.s, ow0 = (iw + L.p - kw0) / L.s;
+      for (int kh = kh0, oh = oh0; kh < L.k && oh >= 0; kh += L.s, --oh) {
+        if (oh >= L.ho) continue;
+        for (int kw = kw0, ow = ow0; kw < L.k && ow >= 0; kw += L.s, --ow) {
+          if (ow >= L.wo) continue;
+          const float* ap = cur + oh * L.wo + ow;
+          const float* wp = Wb + (size_t)(kh * L.k + kw) * L.ci + grp * CB;
+          if (CB == 4) {
+            for (int co = k0; co < L.co; co += ks) {
+              const float v = ap[co * hwo];
+              const float4 w = *reinterpret_cast<const float4*>(wp + co * wco);
+              a0 = fmaf(v, w.x, a0);
+              a1 = fmaf(v, w.y, a1);
+              a2 = fmaf(v, w.z, a2);
+              a3 = fmaf(v, w.w, a3);
+            }
+          } else {
+            for (int co = k0; co < L.co; co += ks) a0 = fmaf(ap[co * hwo], wp[co * wco], a0);
+          }
+        }
+      }
+    }
+    a0 = f_group_sum(a0, ks);
+    if (CB == 4) {
+      a1 = f_group_sum(a1, ks);
+      a2 = f_group_sum(a2, ks);
+      a3 = f_group_sum(a3, ks);
+    }
+    if (act && k0 == 0) {
+      const int o = grp * CB * P + ih * L.wi + iw;
+      nxt[o] = a0;
+      if (CB == 4) {
+        nxt[o + P] = a1;
+        nxt[o + 2 * P] = a2;
+        nxt[o + 3 * P] = a3;
+      }
+    }
+  }
+}
+
+// Forward convolution through L (+ bias) with its weights in shared memory as
+// Wf [ci][kh][kw][co]: g [ci][hi][wi] -> h [co][ho][wo].
+__device__ void f_conv_fwd(const LayerDev& L, const float* g, float* h, const float* Wf) {
+  const int CB = (L.co & 3) == 0 ? 4 : 1;
+  const int ngr = L.co / CB, P = L.ho * L.wo, hwi = L.hi * L.wi;
+  const int items = P * ngr;
+  const int ks = f_split(items);
+  const int rounds = (items * ks + FT - 1) / FT;
+  for (int rr = 0; rr < rounds; ++rr) {
+    const int b = rr * FT + threadIdx.x;
+    const int it = b / ks, k0 = b % ks;
+    const bool act = it < items;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int grp = 0, pos = 0;
+    if (act) {
+      grp = it / P;
+      pos = it % P;
+      const int oh = pos / L.wo, ow = pos % L.wo;
+      const int ih0 = oh * L.s - L.p, iw0 = ow * L.s - L.p;
+      const int kh_lo = max(0, -ih0), kh_hi = min(L.k, L.hi - ih0);
+      const int kw_lo = max(0, -iw0), kw_hi = min(L.k, L.wi - iw0);
+      for (int ci = k0; ci < L.ci; ci += ks) {
+        const float* gp = g + ci * hwi;
+        const float* wc = Wf + (size_t)ci * L.k * L.k * L.co + grp * CB;
+        for (int kh = kh_lo; kh < kh_hi; ++kh)
+          for (int kw = kw_lo; kw < kw_hi; ++kw) {
+            const float v = gp[(ih0 + kh) * L.wi + iw0 + kw];
+            const float* wp = wc + (size_t)(kh * L.k + kw) * L.co;
+            if (CB == 4) {
+              const float4 w = *reinterpret_cast<const float4*>(wp);
+              a0 = fmaf(v, w.x, a0);
+              a1 = fmaf(v, w.y, a1);
+              a2 = fmaf(v, w.z, a2);
+              a3 = fmaf(v, w.w, a3);
+            } else {
+              a0 = fmaf(v, wp[0], a0);
+            }
+          }
+      }
+    }
+    a0 = f_group_sum(a0, ks);
+    if (CB == 4) {
+      a1 = f_group_sum(a1, ks);
+      a2 = f_group_sum(a2, ks);
+      a3 = f_group_sum(a3, ks);
+    }
+    if (act && k0 == 0) {
+      const int c = grp * CB;
+      h[c * P + pos] = a0 + L.b[c];
+      if (CB == 4) {
+        h[(c + 1) * P + pos] = a1 + L.b[c + 1];
+        h[(c + 2) * P + pos] = a2 + L.b[c + 2];
+        h[(c + 3) * P + pos] = a3 + L.b[c + 3];
+      }
+    }
+  }
+}
+
+// shared-memory floats of the conv weights of layers 1..R (both layouts)
+__host__ __device__ inline int f_conv_wfloats(const LayerDev& L) {
+  return L.kind == MNBAB_CONV2D ? 2 * ((L.co * L.ci * L.k * L.k + 3) / 4 * 4) : 0;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, const PropDev* props,
+                                                  const int* row_node, const int* row_j,
+                                                  FusedHP hp, float* AP_out, int maxw) {
+  extern __shared__ __align__(16) float fsm[];
+  __shared__ float red[32];
+  __shared__ int improved;
+  const int SD = pool.SD, d0 = pool.d0, R = net.R;
+  // conv weights of every layer, staged once: Wb then Wf per conv layer
+  int wtot = 0;
+  for (int t = 1; t <= R; ++t) {
+    const LayerDev& L = net.aff[t];
+    if (L.kind != MNBAB_CONV2D) continue;
+    const int nw = L.co * L.ci * L.k * L.k, nwp = (nw + 3) / 4 * 4;
+    for (int i = threadIdx.x; i < nw; i += FT) {
+      fsm[wtot + i] = L.Wb[i];
+      fsm[wtot + nwp + i] = L.Wf[i];
+    }
+    wtot += 2 * nwp;
+  }
+  const int SDp = (SD + 3) & ~3;  // 16-byte aligned sub-buffers
+  float* B0 = fsm + wtot;
+  float* B1 = B0 + maxw;
+  float* APs = B1 + maxw;  // a' checkpoints, then d lb / d alpha
+  float* GBs = APs + SDp;  // d lb / d beta
+  float* Xs = GBs + SDp;   // minimiser x*
+  auto wsm = [&](int t) {  // staged weights of conv layer t
+    int o = 0;
+    for (int u = 1; u < t; ++u) o += f_conv_wfloats(net.aff[u]);
+    return fsm + o;
+  };
+  const int m = blockIdx.x;
+  const int n = row_node[m], r = row_j[m];
+  const PropDev& P = props[pool.prop[n]];
+  const size_t nb = (size_t)n * SD;
+  // Adam moments restart per node
+  for (int i = threadIdx.x; i < SD; i += FT) {
+    pool.MA[nb + i] = 0.f;
+    pool.VA[nb + i] = 0.f;
+    pool.MB[nb + i] = 0.f;
+    pool.VB[nb + i] = 0.f;
+  }
+  const int dR = net.d[R];
+  for (int step = 0; step <= hp.steps; ++step) {
+    // ---- 1. back-substitution sweep at the current parameters
+    __syncthreads();
+    float part = 0.f;
+    float* cur = B0;
+    float* nxt = B1;
+    for (int j = threadIdx.x; j < dR; j += FT) cur[j] = P.Wf[(size_t)r * dR + j];
+    __syncthreads();
+    for (int t = R; t >= 1; --t) {
+      const int dt = net.d[t], off = net.off[t];
+      const float* bias = net.bfull[t];
+      for (int j = threadIdx.x; j < dt; j += FT) {
+        const size_t q = nb + off + j;
+        const float l = pool.L[q], u = pool.U[q];
+        const int s = pool.S[q];
+        const float ap = cur[j];
+        float D, bl = 0.f;
+        if (s == -1) D = 1.f;
+        else if (s == 1) D = 0.f;
+        else if (l >= 0.f) D = 1.f;
+        else if (u <= 0.f) D = 0.f;
+        else if (ap >= 0.f) D = pool.ALPHA[q];
+        else {
+          const float den = u - l;
+          D = u / den;
+          bl = (-u * l) / den;
+        }
+        const float ah = ap * D + pool.BETA[q] * (float)s;
+        APs[off + j] = ap;
+        part += ap * bl + ah * bias[j];
+        cur[j] = ah;
+      }
+      __syncthreads();
+      const LayerDev& L = net.aff[t];
+      if (L.kind == MNBAB_FC) f_fc_back(L, cur, nxt);
+      else f_conv_back(L, cur, nxt, wsm(t));
+      __syncthreads();
+      float* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
+    for (int j = threadIdx.x; j < d0; j += FT) {
+      const float a = cur[j];
+      const float x = a >= 0.f ? P.lo[j] : P.hi[j];
+      part += a * x;
+      Xs[j] = x;
+    }
+    const float lb = f_block_sum(part, red) + P.bf[r];
+    // ---- 2. best bound and its minimiser
+    if (threadIdx.x == 0) {
+      improved = lb > pool.BEST[n];
+      if (improved) pool.BEST[n] = lb;
+    }
+    __syncthreads();
+    if (improved)
+      for (int j = threadIdx.x; j < d0; j += FT) pool.BESTX[(size_t)n * d0 + j] = Xs[j];
+    if (step == hp.steps) {
+      // a' at the final parameters, for the branching scores
+      for (int i = threadIdx.x; i < SD; i += FT) AP_out[(size_t)m * SD + i] = APs[i];
+      break;
+    }
+    // ---- 3. adjoint: the relaxed network forward at x*
+    const float* g = Xs;
+    float gm = 0.f;
+    for (int t = 1; t <= R; ++t) {
+      float* h = (t & 1) ? B0 : B1;
+      __syncthreads();
+      const LayerDev& L = net.aff[t];
+      if (L.kind == MNBAB_FC) f_fc_fwd(L, g, h);
+      else f_conv_fwd(L, g, h, wsm(t) + f_conv_wfloats(L) / 2);
+      __syncthreads();
+      const int dt = net.d[t], off = net.off[t];
+      for (int j = threadIdx.x; j < dt; j += FT) {
+        const size_t q = nb + off + j;
+        const float l = pool.L[q], u = pool.U[q];
+        const int s = pool.S[q];
+        const float ap = APs[off + j];
+        const float hv = h[j];
+        float D, bl = 0.f;
+        bool abr = false;
+        if (s == -1) D = 1.f;
+        else if (s == 1) D = 0.f;
+        else if (l >= 0.f) D = 1.f;
+        else if (u <= 0.f) D = 0.f;
+        else if (ap >= 0.f) {
+          D = pool.ALPHA[q];
+          abr = true;
+        } else {
+          const float den = u - l;
+          D = u / den;
+          bl = (-u * l) / den;
+        }
+        const float ga = abr ? hv * ap : 0.f;
+        const float gb = hv * (float)s;
+        APs[off + j] = ga;
+        GBs[off + j] = gb;
+        gm = fmaxf(gm, fmaxf(fabsf(ga), fabsf(gb)));
+        h[j] = hv * D + bl;
+      }
+      g = h;
+    }
+    // ---- 4. projected Adam
+    const float gmax = f_block_max(gm, red);
+    const float thr = hp.floor * gmax;
+    const float eps = fmaxf(hp.eps_abs, hp.eps_rel * gmax);
+    const float bc1 = hp.bc1[step], bc2 = hp.bc2[step];
+    for (int i = threadIdx.x; i < SD; i += FT) {
+      const size_t q = nb + i;
+      float ga = APs[i], gb = GBs[i];
+      if (fabsf(ga) <= thr) ga = 0.f;
+      if (fabsf(gb) <= thr) gb = 0.f;
+      float th = pool.ALPHA[q], mo = pool.MA[q], ve = pool.VA[q];
+      f_adam(th, mo, ve, ga, hp.lr_a, hp.b1, hp.b2, eps, bc1, bc2);
+      pool.ALPHA[q] = fminf(fmaxf(th, 0.f), 1.f);
+      pool.MA[q] = mo;
+      pool.VA[q] = ve;
+      th = pool.BETA[q];
+      mo = pool.MB[q];
+      ve = pool.VB[q];
+      f_adam(th, mo, ve, gb, hp.lr_b, hp.b1, hp.b2, eps, bc1, bc2);
+      pool.BETA[q] = fmaxf(th, 0.f);
+      pool.MB[q] = mo;
+      pool.VB[q] = ve;
+    }
+  }
+}
+
+static int fused_maxw(const NetDev& net, int d0) {
+  int maxw = d0;
+  for (int t = 1; t <= net.R; ++t) maxw = std::max(maxw, net.d[t]);
+  return (maxw + 3) / 4 * 4;
+}
+
+static int fused_smem_floats(const NetDev& net, int SD, int d0) {
+  int w = 0;
+  for (int t = 1; t <= net.R; ++t) w += f_conv_wfloats(net.aff[t]);
+  return w + 2 * fused_maxw(net, d0) + 2 * ((SD + 3) / 4 * 4) + d0;
+}
+
+bool fused_supported(const NetDev& net, int SD, int d0, int steps) {
+  if (steps < 0 || steps > FUSED_MAX_STEPS || net.R < 1) return false;
+  for (int t = 1; t <= net.R + 1; ++t)
+    if (net.n_edge[t] != 1 || net.src1[t] != t - 1) return false;
+  for (int t = 1; t <= net.R; ++t) {
+    const LayerDev& L = net.aff[t];
+    if (!net.bfull[t] || (L.kind != MNBAB_FC && L.kind != MNBAB_CONV2D)) return false;
+    if (L.kind == MNBAB_CONV2D && (!L.Wb || !L.Wf)) return false;
+  }
+  return fused_smem_floats(net, SD, d0) * (int)sizeof(float) <= 200 * 1024;
+}
+
+void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropDev* props,
+                      const int* row_node, const int* row_j, const FusedHP& hp, float* AP_out,
+                      cudaStream_t st) {
+  if (M <= 0) return;
+  const int smem = fused_smem_floats(net, pool.SD, pool.d0) * (int)sizeof(float);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_opt_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_opt_chain<<<M, FT, smem, st>>>(net, pool, props, row_node, row_j, hp, AP_out,
+                                  fused_maxw(net, pool.d0));
+}
+
+}  // namespace mnbab

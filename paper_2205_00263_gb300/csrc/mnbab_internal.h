@@ -144,6 +144,21 @@ bool win_plan(const NetDev& net, int t, WinPlan& wp);
 // terms, concretisation and sign * b_t[j]) goes to partial slot e.slot_base.
 void launch_win_rows(const NetDev& net, const WinPlan& wp, const RowsDev& rows, const Epi& e,
                      cudaStream_t st);
+// Fused optimisation loop for chain networks without multi-neuron constraints
+// (csrc/fused.cu): one CTA per objective row runs all sweeps, adjoints and Adam
+// steps.  bc1[s] / bc2[s] are Adam's bias corrections 1 - beta^(s+1).
+constexpr int FUSED_MAX_STEPS = 64;
+struct FusedHP {
+  int steps;
+  float lr_a, lr_b, b1, b2, eps_abs, eps_rel, floor;
+  float bc1[FUSED_MAX_STEPS], bc2[FUSED_MAX_STEPS];
+};
+bool fused_supported(const NetDev& net, int SD, int d0, int steps);
+// rows m < M: node row_node[m], objective row row_j[m]; a' of the final sweep
+// goes to AP_out [M][SD]; BEST / BESTX of the node track the best iterate.
+void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropDev* props,
+                      const int* row_node, const int* row_j, const FusedHP& hp, float* AP_out,
+                      cudaStream_t st);
 // Back-substitution through affine layer i: in [M][d_i] -> out [M][d_{i-1}].
 // Returns the number of partial-sum slots used.
 int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,

@@ -213,7 +213,7 @@ void d2h(mnbab_ctx* c, T* dst, const T* src, size_t n) {
 
 enum Cat {
   C_BACKSUB_FC, C_BACKSUB_CONV, C_FWD_FC, C_FWD_CONV, C_INIT, C_REDUCE, C_GAMMA, C_ADAM, C_ACS,
-  C_BOOK, C_WIN, NKCAT,
+  C_BOOK, C_WIN, C_FUSED, NKCAT,
   // host wall time of the BaB step phases (stream work included up to their syncs)
   H_ROOTS = NKCAT, H_REBOUND, H_DEEPPOLY, H_OPTIMIZE, H_CONFIRM, H_FINISH,
   // device time of all kernel classes launched within each phase
@@ -223,7 +223,8 @@ constexpr int NPHASE = 6;
 const char* CAT_NAMES[NCAT] = {"backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm",
                                "forward_conv",    "init_rows",              "reduce_lb",
                                "gamma_terms",     "adam",                   "acs",
-                               "bookkeeping",     "backsub_conv_window",    "step_roots_wall",        "step_rebound_wall",
+                               "bookkeeping",     "backsub_conv_window",    "opt_fused_chain",
+                               "step_roots_wall",        "step_rebound_wall",
                                "step_deeppoly_wall", "step_optimize_wall",  "step_confirm_wall",
                                "step_finish_wall", "phase_roots_gpu",        "phase_rebound_gpu",
                                "phase_deeppoly_gpu", "phase_optimize_gpu",   "phase_confirm_gpu",
@@ -713,6 +714,32 @@ void run_optimize(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
 
 void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
   mnbab_ctx* c = n->ctx;
+  if (!has_gamma && c->gemm_path != 2 && fused_supported(n->nd, n->SD, n->d0, a.steps)) {
+    // the whole loop in one launch, one CTA per row
+    FusedHP hp{};
+    hp.steps = a.steps;
+    hp.lr_a = a.lr_alpha;
+    hp.lr_b = a.lr_beta;
+    hp.b1 = a.beta1;
+    hp.b2 = a.beta2;
+    hp.eps_abs = a.eps;
+    hp.eps_rel = a.eps_rel;
+    hp.floor = a.grad_floor;
+    double b1t = 1.0, b2t = 1.0;
+    for (int s = 0; s < a.steps; ++s) {
+      b1t *= a.beta1;
+      b2t *= a.beta2;
+      hp.bc1[s] = (float)(1.0 - b1t);
+      hp.bc2[s] = (float)(1.0 - b2t);
+    }
+    double macs = 0.0;
+    for (int t = 1; t <= n->R; ++t) macs += layer_macs(n->nd.aff[t]);
+    Scope sc(c, C_FUSED,
+             2.0 * M * ((a.steps + 1.0) * (macs + n->nd.d[n->R]) + a.steps * macs),
+             (double)M * (a.steps + 1.0) * n->SD * 66.0);
+    launch_opt_chain(M, n->nd, n->pool, c->d_props, n->bslots, n->brows, hp, n->AP, c->st);
+    return;
+  }
   {
     Scope sc(c, C_BOOK, 0.0, 16.0 * M * (n->SD + c->EC));
     launch_zero_adam(M, n->bslots, n->pool, c->st);

@@ -200,6 +200,37 @@ def test_optimized_bound_matches_oracle(Context, path):
             _assert_close(best[k], ref, f"node {k} optimised bound")
 
 
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("case", ["fc", "conv"])
+def test_optimized_bound_without_constraints(Context, case, path):
+    """Without multi-neuron constraints the optimisation loop of a chain network
+    runs in one fused launch (path 1) or as separate sweeps, adjoints and Adam
+    steps (path 2, tensor-core GEMMs); both match the oracle's 20-step Adam."""
+    if case == "fc":
+        layers, C, d, lo, hi, prep = fc_case(9, (37, 53, 29, 7), 0.12)
+    else:
+        layers, C, d, lo, hi, prep = conv_case(5, 0.05)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    rng = np.random.default_rng(9)
+    with Context(node_capacity=128, gemm_path=path) as ctx:
+        ctx.profile(True)
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
+        onodes, gids = [], []
+        for k in range(8):
+            on = random_node(prep, rng, n_splits=k % 3, row=k % C.shape[0], gamma_scale=0.0)
+            on.split_layer = net.R
+            gid = ctx.node_root(prop, on.row)
+            ctx.import_params(gid, to_params(on, net.R))
+            onodes.append(on)
+            gids.append(gid)
+        best = ctx.optimize(gids, steps=20)
+        stats, _ = ctx.profile_read()
+        assert (stats["opt_fused_chain"]["launches"] > 0) == (path == 1)
+        for k, on in enumerate(onodes):
+            ref, *_ = core.optimize(net, on, dense, lo_t, hi_t, core.AdamHP())
+            _assert_close(best[k], ref, f"node {k} optimised bound")
+
+
 @pytest.mark.parametrize("cab", [False, True])
 def test_acs_choice_matches_oracle(Context, cab):
     """ACS (and, with cab, the cost-adjusted score of App. B) picks the same
