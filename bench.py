@@ -165,12 +165,17 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def dominant(stats):
+    kern = {k: v for k, v in stats.items() if not k.startswith(("step_", "phase_"))}
+    return max(kern.items(), key=lambda kv: kv[1]["ms"])
+
+
 def roofline(stats, peaks, src, kernels_hash):
     """Dominant kernel class (largest summed launch time) against its roofline."""
-    kern = {k: v for k, v in stats.items() if not k.startswith(("step_", "phase_"))}
-    name, st = max(kern.items(), key=lambda kv: kv[1]["ms"])
+    name, st = dominant(stats)
     per_launch_ms = st["ms"] / max(1, st["launches"])
-    simt = name in ("backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm", "forward_conv")
+    simt = name in ("backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm", "forward_conv",
+                    "opt_fused_chain", "backsub_conv_window", "backsub_rows_fused")
     if simt:
         # SIMT FP32 FMA: 152 SMs x 128 lanes x 2 flop per cycle at the maximum SM clock
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -279,14 +284,23 @@ def run_ours(args):
     net = ctx.load_network(layers)
     start = rank_start(rank)
     win = Window(ctx, net, layers, eps, start, args.window,
-                 pool_size=args.window + 60 * (args.steps + args.warmup) + 50)
+                 pool_size=args.window + 60 * (args.steps + args.warmup + 1) + 50)
 
     for _ in range(args.warmup):
         win.step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    # one untimed step with every kernel class timed: the per-class breakdown and
+    # the dominant class; the timed steps then time that class alone (per-launch
+    # events on every class would add their own overhead to the measured steps)
     ctx.profile(True)
+    win.step()
+    torch.cuda.synchronize()
+    breakdown, _ = ctx.profile_read()
+    dom_name = dominant(breakdown)[0]
+    ctx.profile(True)
+    ctx.profile_mask([dom_name])
     _, launches0 = ctx.profile_read()
     clocks = Clocks(local)
     clocks.start()
@@ -309,6 +323,8 @@ def run_ours(args):
     clk = clocks.stop()
     stats, launches1 = ctx.profile_read()
     ctx.profile(False)
+    ctx.profile_mask(None)
+    stats = {dom_name: stats[dom_name]}
     tot_ms, tot_nodes = reduce_timing(ms, nodes, device="cuda")
     value = tot_nodes / (tot_ms * 1e-3)
 
@@ -396,7 +412,8 @@ def run_ours(args):
             "plain": plain,
             "batched_over_plain": (value / world / plain["value"]) if plain else None,
             "verdicts_in_timed_steps": {"verified": vd[1], "falsified": vd[-1], "unknown": vd[0]},
-            "kernel_breakdown_ms": {k: round(v["ms"], 3) for k, v in stats.items()},
+            "kernel_breakdown_ms": {k: round(v["ms"], 3) for k, v in breakdown.items() if v["ms"]},
+            "kernel_breakdown_note": "one untimed step before the timed region, every class timed",
             "nodes_timed": tot_nodes,
             "serving": serving,
             "launches_before_timed": int(launches0),

@@ -276,6 +276,12 @@ mnbab_status mnbab_get_trace(const mnbab_ctx* ctx, const mnbab_prop* prop, mnbab
  * with CUDA events (adds a little launch overhead); enable = 0 stops. */
 mnbab_status mnbab_profile(mnbab_ctx* ctx, int32_t enable);
 
+/* Restricts CUDA-event timing to the kernel classes whose bit is set (bit i =
+ * the i-th statistic of mnbab_profile_read); launches and algorithmic work are
+ * still counted for every class.  All classes are timed by default.  Timing
+ * few classes keeps the per-launch event overhead out of a measured region. */
+mnbab_status mnbab_profile_mask(mnbab_ctx* ctx, uint64_t class_mask);
+
 /* Reads up to max_stats kernel-class statistics (synchronises the stream) and
  * the number of kernels the context has launched since it was created. */
 mnbab_status mnbab_profile_read(mnbab_ctx* ctx, mnbab_kernel_stat* stats, int32_t max_stats,

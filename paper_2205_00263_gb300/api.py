@@ -294,6 +294,18 @@ class Context:
     def profile(self, enable: bool):
         self._ck(self.lib.mnbab_profile(self.h, 1 if enable else 0))
 
+    def profile_mask(self, classes=None):
+        """Time only the named kernel classes with CUDA events (None: all)."""
+        if classes is None:
+            mask = (1 << 64) - 1
+        else:
+            stats, _ = self.profile_read()
+            names = list(stats)
+            mask = 0
+            for c in classes:
+                mask |= 1 << names.index(c)
+        self._ck(self.lib.mnbab_profile_mask(self.h, mask))
+
     def profile_read(self):
         """({kernel class: {launches, ms, flops, bytes}}, total launches)."""
         arr = (L.KernelStat * 32)()

@@ -466,6 +466,97 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
   }
 }
 
+// Intermediate-bound rows (Sec. 3.2 re-bounding, DeepPoly slopes, beta = gamma =
+// 0) that start at a fully connected neuron of zhat_t, above a chain: each CTA
+// stages the transposed-conv weights once and carries rows to the input in
+// shared memory, one row at a time; row m's lower bound goes to lb[m].
+__global__ void __launch_bounds__(FT) k_sweep_chain(NetDev net, PoolDev pool,
+                                                    const PropDev* props, RowsDev rows, int t0,
+                                                    float* lb, int maxw) {
+  extern __shared__ __align__(16) float fsm[];
+  __shared__ float red[32];
+  int wtot = 0;
+  for (int t = 1; t < t0; ++t) {
+    const LayerDev& L = net.aff[t];
+    if (L.kind != MNBAB_CONV2D) continue;
+    const int nw = L.co * L.ci * L.k * L.k;
+    for (int i = threadIdx.x; i < nw; i += FT) fsm[wtot + i] = L.Wb[i];
+    wtot += (nw + 3) / 4 * 4;
+  }
+  float* B0 = fsm + wtot;
+  float* B1 = B0 + maxw;
+  const int SD = pool.SD;
+  const LayerDev& Lt = net.aff[t0];
+  for (int m = blockIdx.x; m < rows.M; m += gridDim.x) {
+    const int n = rows.node[m], j = rows.j[m];
+    const float sg = rows.sign ? rows.sign[m] : 1.f;
+    const size_t nb = (size_t)n * SD;
+    const int dprev = Lt.d_in;
+    __syncthreads();
+    float* cur = B0;
+    float* nxt = B1;
+    for (int k = threadIdx.x; k < dprev; k += FT) cur[k] = sg * __ldg(Lt.W + (size_t)j * dprev + k);
+    __syncthreads();
+    float part = 0.f;
+    int wo = wtot;
+    for (int t = t0 - 1; t >= 1; --t) {
+      const int dt = net.d[t], off = net.off[t];
+      const float* bias = net.bfull[t];
+      for (int k = threadIdx.x; k < dt; k += FT) {
+        const size_t q = nb + off + k;
+        const float l = pool.L[q], u = pool.U[q];
+        const int s = pool.S[q];
+        const float ap = cur[k];
+        float D, bl = 0.f;
+        if (s == -1) D = 1.f;
+        else if (s == 1) D = 0.f;
+        else if (l >= 0.f) D = 1.f;
+        else if (u <= 0.f) D = 0.f;
+        else if (ap >= 0.f) D = u >= -l ? 1.f : 0.f;
+        else {
+          const float den = u - l;
+          D = u / den;
+          bl = (-u * l) / den;
+        }
+        const float ah = ap * D;
+        part += ap * bl + ah * bias[k];
+        cur[k] = ah;
+      }
+      __syncthreads();
+      const LayerDev& L = net.aff[t];
+      if (L.kind == MNBAB_FC) {
+        f_fc_back(L, cur, nxt);
+      } else {
+        wo -= (L.co * L.ci * L.k * L.k + 3) / 4 * 4;
+        f_conv_back(L, cur, nxt, fsm + wo);
+      }
+      __syncthreads();
+      float* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
+    const PropDev& P = props[pool.prop[n]];
+    for (int k = threadIdx.x; k < pool.d0; k += FT) {
+      const float a = cur[k];
+      part += a * (a >= 0.f ? P.lo[k] : P.hi[k]);
+    }
+    const float tot = f_block_sum(part, red);
+    if (threadIdx.x == 0) {
+      const float bj = net.bfull[t0] ? net.bfull[t0][j] : Lt.b[j];
+      lb[m] = tot + sg * bj;
+    }
+  }
+}
+
+static int sweep_wfloats(const NetDev& net, int t0) {
+  int w = 0;
+  for (int t = 1; t < t0; ++t) {
+    const LayerDev& L = net.aff[t];
+    if (L.kind == MNBAB_CONV2D) w += (L.co * L.ci * L.k * L.k + 3) / 4 * 4;
+  }
+  return w;
+}
+
 static int fused_maxw(const NetDev& net, int d0) {
   int maxw = d0;
   for (int t = 1; t <= net.R; ++t) maxw = std::max(maxw, net.d[t]);
@@ -499,6 +590,40 @@ void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropD
     cudaFuncSetAttribute(k_opt_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_opt_chain<<<M, FT, smem, st>>>(net, pool, props, row_node, row_j, hp, AP_out,
                                   fused_maxw(net, pool.d0));
+}
+
+bool sweep_chain_supported(const NetDev& net, int t0) {
+  if (t0 < 2 || t0 > net.R || net.aff[t0].kind != MNBAB_FC) return false;
+  for (int t = 1; t <= t0; ++t) {
+    if (net.n_edge[t] != 1 || net.src1[t] != t - 1 || !net.bfull[t]) return false;
+    const LayerDev& L = net.aff[t];
+    if (L.kind != MNBAB_FC && L.kind != MNBAB_CONV2D) return false;
+    if (L.kind == MNBAB_CONV2D && !L.Wb) return false;
+  }
+  int maxw = net.d[0];
+  for (int t = 1; t < t0; ++t) maxw = std::max(maxw, net.d[t]);
+  maxw = (maxw + 3) / 4 * 4;
+  return (sweep_wfloats(net, t0) + 2 * maxw) * (int)sizeof(float) <= 100 * 1024;
+}
+
+void launch_sweep_chain(const NetDev& net, const PoolDev& pool, const PropDev* props,
+                        const RowsDev& rows, int t0, float* lb, cudaStream_t st) {
+  if (rows.M <= 0) return;
+  int maxw = net.d[0];
+  for (int t = 1; t < t0; ++t) maxw = std::max(maxw, net.d[t]);
+  maxw = (maxw + 3) / 4 * 4;
+  const int smem = (sweep_wfloats(net, t0) + 2 * maxw) * (int)sizeof(float);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_sweep_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  static int sms = 0;
+  if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
+    sms = 152;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_chain, FT, smem) !=
+          cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int grid = std::min(rows.M, sms * per_sm);
+  k_sweep_chain<<<grid, FT, smem, st>>>(net, pool, props, rows, t0, lb, maxw);
 }
 
 }  // namespace mnbab

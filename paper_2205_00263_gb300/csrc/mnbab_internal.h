@@ -159,6 +159,12 @@ bool fused_supported(const NetDev& net, int SD, int d0, int steps);
 void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropDev* props,
                       const int* row_node, const int* row_j, const FusedHP& hp, float* AP_out,
                       cudaStream_t st);
+// Intermediate-bound rows that start at a fully connected neuron of zhat_t0
+// above a chain of FC / conv layers: one persistent CTA loop, each row carried
+// to the input in shared memory with DeepPoly epilogues; lower bounds to lb[m].
+bool sweep_chain_supported(const NetDev& net, int t0);
+void launch_sweep_chain(const NetDev& net, const PoolDev& pool, const PropDev* props,
+                        const RowsDev& rows, int t0, float* lb, cudaStream_t st);
 // Back-substitution through affine layer i: in [M][d_i] -> out [M][d_{i-1}].
 // Returns the number of partial-sum slots used.
 int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,

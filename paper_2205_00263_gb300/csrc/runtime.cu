@@ -145,9 +145,15 @@ struct mnbab_ctx {
   int props_cap = 0;
   float* arena = nullptr;
   size_t arena_cap = 0, arena_used = 0;
+  // pinned staging ring for small host-to-device copies: a copy's source is
+  // copied here and the transfer runs asynchronously; the ring restarts after
+  // every full stream synchronisation (all earlier transfers are done)
+  unsigned char* pin = nullptr;
+  size_t pin_cap = 0, pin_used = 0;
   std::vector<std::pair<void*, size_t>> allocs;
   // profiling: kernel-class timing with CUDA events, launch and copy counters
   bool prof = false;
+  uint64_t prof_mask = ~uint64_t(0);  // kernel classes timed with CUDA events
   // (class | (phase + 1) << 8 | graph-owned << 16, event pair)
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   int phase = -1;  // BaB step phase whose launches are being issued (-1: none)
@@ -199,10 +205,25 @@ T* dalloc_t(mnbab_ctx* c, size_t n) {
   return static_cast<T*>(dalloc(c, n * sizeof(T)));
 }
 
+void sync(mnbab_ctx* c);
+
+void h2d_bytes(mnbab_ctx* c, void* dst, const void* src, size_t bytes) {
+  c->h2d_bytes += (int64_t)bytes;
+  if (!bytes) return;
+  if (c->pin && bytes <= c->pin_cap / 4) {
+    if (c->pin_used + bytes > c->pin_cap) sync(c);  // every staged transfer has completed
+    unsigned char* stage = c->pin + c->pin_used;
+    std::memcpy(stage, src, bytes);
+    c->pin_used += (bytes + 15) & ~size_t(15);
+    ck(cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyHostToDevice, c->st), "H2D");
+    return;
+  }
+  ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->st), "H2D");
+}
+
 template <typename T>
 void h2d(mnbab_ctx* c, T* dst, const T* src, size_t n) {
-  c->h2d_bytes += (int64_t)(n * sizeof(T));
-  if (n) ck(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, c->st), "H2D");
+  h2d_bytes(c, dst, src, n * sizeof(T));
 }
 
 template <typename T>
@@ -213,7 +234,7 @@ void d2h(mnbab_ctx* c, T* dst, const T* src, size_t n) {
 
 enum Cat {
   C_BACKSUB_FC, C_BACKSUB_CONV, C_FWD_FC, C_FWD_CONV, C_INIT, C_REDUCE, C_GAMMA, C_ADAM, C_ACS,
-  C_BOOK, C_WIN, C_FUSED, NKCAT,
+  C_BOOK, C_WIN, C_FUSED, C_SWEEP, NKCAT,
   // host wall time of the BaB step phases (stream work included up to their syncs)
   H_ROOTS = NKCAT, H_REBOUND, H_DEEPPOLY, H_OPTIMIZE, H_CONFIRM, H_FINISH,
   // device time of all kernel classes launched within each phase
@@ -224,6 +245,7 @@ const char* CAT_NAMES[NCAT] = {"backsub_fc_gemm", "backsub_conv_transpose", "for
                                "forward_conv",    "init_rows",              "reduce_lb",
                                "gamma_terms",     "adam",                   "acs",
                                "bookkeeping",     "backsub_conv_window",    "opt_fused_chain",
+                               "backsub_rows_fused",
                                "step_roots_wall",        "step_rebound_wall",
                                "step_deeppoly_wall", "step_optimize_wall",  "step_confirm_wall",
                                "step_finish_wall", "phase_roots_gpu",        "phase_rebound_gpu",
@@ -257,6 +279,7 @@ void resolve_prof(mnbab_ctx* c) {
 
 void sync(mnbab_ctx* c) {
   ck(cudaStreamSynchronize(c->st), "stream synchronize");
+  c->pin_used = 0;
   ck(cudaGetLastError(), "kernel launch");
   if (!c->pending.empty()) resolve_prof(c);
   if (c->d_err && c->gemm_path != 1) {
@@ -295,7 +318,7 @@ struct Scope {
       g->n[cat] += nl;
       g->flops[cat] += flops;
       g->bytes[cat] += bytes;
-      if (g->prof) {
+      if (g->prof && ((c->prof_mask >> cat) & 1)) {
         ck(cudaEventCreate(&a), "cudaEventCreate");
         ck(cudaEventCreate(&b), "cudaEventCreate");
         c->graph_events.push_back(a);
@@ -308,7 +331,7 @@ struct Scope {
     c->acc_n[cat] += nl;
     c->acc_flops[cat] += flops;
     c->acc_bytes[cat] += bytes;
-    if (c->prof) {
+    if (c->prof && ((c->prof_mask >> cat) & 1)) {
       if (c->pending.size() > 8192) sync(c);
       a = get_event(c);
       b = get_event(c);
@@ -441,6 +464,14 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
   mnbab_ctx* c = n->ctx;
   if (rows.M <= 0) return;
   const NetDev& nd = n->nd;
+  if (!o.final_mode && !o.store && !o.track && sweep_chain_supported(nd, t)) {
+    // dense intermediate-bound rows above a chain: persistent fused sweep
+    double macs = nd.d[t - 1];
+    for (int i = 1; i < t; ++i) macs += layer_macs(nd.aff[i]);
+    Scope sc(c, C_SWEEP, 2.0 * rows.M * macs, 4.0 * rows.M * (nd.d[t - 1] + 4.0 * n->SD));
+    launch_sweep_chain(nd, n->pool, c->d_props, rows, t, n->lb, c->st);
+    return;
+  }
   WinPlan wp;
   if (!o.final_mode && !o.store && !o.track && win_plan(nd, t, wp)) {
     // intermediate-bound rows of a convolution neuron: receptive-field windows
@@ -1375,6 +1406,13 @@ mnbab_status mnbab_create(const mnbab_options* opt, mnbab_ctx** out) {
   }
   try {
     c->d_err = dalloc_t<int>(c, 1);
+    void* pin = nullptr;
+    if (cudaHostAlloc(&pin, (size_t)16 << 20, cudaHostAllocDefault) == cudaSuccess) {
+      c->pin = static_cast<unsigned char*>(pin);
+      c->pin_cap = (size_t)16 << 20;
+    } else {
+      cudaGetLastError();  // unpinned copies instead
+    }
     ck(cudaMemset(c->d_err, 0, sizeof(int)), "memset");
   } catch (const Err& e) {
     mnbab_destroy(c);
@@ -1400,6 +1438,7 @@ void mnbab_destroy(mnbab_ctx* c) {
   }
   for (auto e : c->graph_events) cudaEventDestroy(e);
   for (auto& a : c->allocs) cudaFree(a.first);
+  if (c->pin) cudaFreeHost(c->pin);
   for (auto* r : c->requests) delete r;
   for (auto* n : c->nets) delete n;
   for (auto* p : c->props) delete p;
@@ -1613,16 +1652,22 @@ mnbab_status mnbab_set_property(mnbab_ctx* c, const mnbab_net* cnet, const float
     }
     if (d) p->bf[r] += d[r];
   }
-  std::vector<float> Wf(p->Wf.begin(), p->Wf.end()), bf(p->bf.begin(), p->bf.end());
+  // input box, folded last layer and offsets in one arena block, one copy
   PropDev& pd = p->pd;
-  float* dlo = prop_arena(c, n->d0);
-  float* dhi = prop_arena(c, n->d0);
-  float* dWf = prop_arena(c, Wf.size());
-  float* dbf = prop_arena(c, bf.size());
-  h2d(c, dlo, x_lo, n->d0);
-  h2d(c, dhi, x_hi, n->d0);
-  h2d(c, dWf, Wf.data(), Wf.size());
-  h2d(c, dbf, bf.data(), bf.size());
+  auto up16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+  const size_t o_hi = up16(n->d0), o_wf = o_hi + up16(n->d0);
+  const size_t o_bf = o_wf + up16(p->Wf.size()), tot = o_bf + up16(p->bf.size());
+  std::vector<float> pack(tot, 0.f);
+  std::copy(x_lo, x_lo + n->d0, pack.begin());
+  std::copy(x_hi, x_hi + n->d0, pack.begin() + o_hi);
+  for (size_t k = 0; k < p->Wf.size(); ++k) pack[o_wf + k] = (float)p->Wf[k];
+  for (size_t k = 0; k < p->bf.size(); ++k) pack[o_bf + k] = (float)p->bf[k];
+  float* blk = prop_arena(c, tot);
+  h2d(c, blk, pack.data(), tot);
+  float* dlo = blk;
+  float* dhi = blk + o_hi;
+  float* dWf = blk + o_wf;
+  float* dbf = blk + o_bf;
   pd.lo = dlo; pd.hi = dhi; pd.Wf = dWf; pd.bf = dbf; pd.n_rows = n_rows; pd.E = 0;
   pd.cab = 0;
   update_cab(n, p);
@@ -2113,6 +2158,12 @@ mnbab_status mnbab_profile(mnbab_ctx* c, int32_t enable) {
     }
   }
   c->prof = enable != 0;
+  API_END(c)
+}
+
+mnbab_status mnbab_profile_mask(mnbab_ctx* c, uint64_t class_mask) {
+  API_BEGIN(c)
+  c->prof_mask = class_mask;
   API_END(c)
 }
 
