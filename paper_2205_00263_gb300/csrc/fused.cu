@@ -169,6 +169,36 @@ __device__ void f_fc_fwd(const LayerDev& L, const float* g, float* h) {
   }
 }
 
+// Staged conv weights: one row per channel of the reduction-split dimension
+// (Wb: a row per output channel co, Wf: a row per input channel ci).  Row
+// strides are padded so that the lanes that split a reduction over channels
+// (adjacent lanes, channels k0, k0 + ks, ...) fall in different shared-memory
+// banks: stride = 4 mod 32 floats for float4 rows, 1 mod 32 for scalar rows.
+__host__ __device__ inline int f_padw(int w, bool vec) {
+  return vec ? w + ((36 - (w & 31)) & 31) : w + ((33 - (w & 31)) & 31);
+}
+__host__ __device__ inline int f_wb_stride(const LayerDev& L) {
+  return f_padw(L.k * L.k * L.ci, (L.ci & 3) == 0);
+}
+__host__ __device__ inline int f_wf_stride(const LayerDev& L) {
+  return f_padw(L.k * L.k * L.co, (L.co & 3) == 0);
+}
+__host__ __device__ inline int f_wb_floats(const LayerDev& L) {
+  return (L.co * f_wb_stride(L) + 3) / 4 * 4;
+}
+__host__ __device__ inline int f_wf_floats(const LayerDev& L) {
+  return (L.ci * f_wf_stride(L) + 3) / 4 * 4;
+}
+// shared-memory floats of a layer's staged weights (both layouts)
+__host__ __device__ inline int f_conv_wfloats(const LayerDev& L) {
+  return L.kind == MNBAB_CONV2D ? f_wb_floats(L) + f_wf_floats(L) : 0;
+}
+// copies rows of `w` floats from src (dense) to dst (stride `stride`)
+__device__ inline void f_stage(float* dst, const float* src, int rows, int w, int stride,
+                               int nthr) {
+  for (int i = threadIdx.x; i < rows * w; i += nthr) dst[(i / w) * stride + i % w] = __ldg(src + i);
+}
+
 // Transposed convolution (back-substitution) through conv layer L with its
 // weights in shared memory as Wb [co][kh][kw][ci]: cur [co][ho][wo] -> nxt
 // [ci][hi][wi].  A thread group takes one input position and CB channels; the
@@ -179,7 +209,7 @@ __device__ void f_conv_back(const LayerDev& L, const float* cur, float* nxt, con
   const int items = P * ngr;
   const int ks = f_split(items);
   const int rounds = (items * ks + FT - 1) / FT;
-  const size_t wco = (size_t)L.k * L.k * L.ci;
+  const size_t wco = (size_t)f_wb_stride(L);
   for (int rr = 0; rr < rounds; ++rr) {
     const int b = rr * FT + threadIdx.x;
     const int it = b / ks, k0 = b % ks;
@@ -255,7 +285,7 @@ __device__ void f_conv_fwd(const LayerDev& L, const float* g, float* h, const fl
       const int kw_lo = max(0, -iw0), kw_hi = min(L.k, L.wi - iw0);
       for (int ci = k0; ci < L.ci; ci += ks) {
         const float* gp = g + ci * hwi;
-        const float* wc = Wf + (size_t)ci * L.k * L.k * L.co + grp * CB;
+        const float* wc = Wf + (size_t)ci * f_wf_stride(L) + grp * CB;
         for (int kh = kh_lo; kh < kh_hi; ++kh)
           for (int kw = kw_lo; kw < kw_hi; ++kw) {
             const float v = gp[(ih0 + kh) * L.wi + iw0 + kw];
@@ -290,10 +320,6 @@ __device__ void f_conv_fwd(const LayerDev& L, const float* g, float* h, const fl
   }
 }
 
-// shared-memory floats of the conv weights of layers 1..R (both layouts)
-__host__ __device__ inline int f_conv_wfloats(const LayerDev& L) {
-  return L.kind == MNBAB_CONV2D ? 2 * ((L.co * L.ci * L.k * L.k + 3) / 4 * 4) : 0;
-}
 
 }  // namespace
 
@@ -309,12 +335,9 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
   for (int t = 1; t <= R; ++t) {
     const LayerDev& L = net.aff[t];
     if (L.kind != MNBAB_CONV2D) continue;
-    const int nw = L.co * L.ci * L.k * L.k, nwp = (nw + 3) / 4 * 4;
-    for (int i = threadIdx.x; i < nw; i += FT) {
-      fsm[wtot + i] = L.Wb[i];
-      fsm[wtot + nwp + i] = L.Wf[i];
-    }
-    wtot += 2 * nwp;
+    f_stage(fsm + wtot, L.Wb, L.co, L.k * L.k * L.ci, f_wb_stride(L), FT);
+    f_stage(fsm + wtot + f_wb_floats(L), L.Wf, L.ci, L.k * L.k * L.co, f_wf_stride(L), FT);
+    wtot += f_conv_wfloats(L);
   }
   const int SDp = (SD + 3) & ~3;  // 16-byte aligned sub-buffers
   float* B0 = fsm + wtot;
@@ -408,7 +431,7 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
       __syncthreads();
       const LayerDev& L = net.aff[t];
       if (L.kind == MNBAB_FC) f_fc_fwd(L, g, h);
-      else f_conv_fwd(L, g, h, wsm(t) + f_conv_wfloats(L) / 2);
+      else f_conv_fwd(L, g, h, wsm(t) + f_wb_floats(L));
       __syncthreads();
       const int dt = net.d[t], off = net.off[t];
       for (int j = threadIdx.x; j < dt; j += FT) {
@@ -479,9 +502,8 @@ __global__ void __launch_bounds__(FT) k_sweep_chain(NetDev net, PoolDev pool,
   for (int t = 1; t < t0; ++t) {
     const LayerDev& L = net.aff[t];
     if (L.kind != MNBAB_CONV2D) continue;
-    const int nw = L.co * L.ci * L.k * L.k;
-    for (int i = threadIdx.x; i < nw; i += FT) fsm[wtot + i] = L.Wb[i];
-    wtot += (nw + 3) / 4 * 4;
+    f_stage(fsm + wtot, L.Wb, L.co, L.k * L.k * L.ci, f_wb_stride(L), FT);
+    wtot += f_wb_floats(L);
   }
   float* B0 = fsm + wtot;
   float* B1 = B0 + maxw;
@@ -527,7 +549,7 @@ __global__ void __launch_bounds__(FT) k_sweep_chain(NetDev net, PoolDev pool,
       if (L.kind == MNBAB_FC) {
         f_fc_back(L, cur, nxt);
       } else {
-        wo -= (L.co * L.ci * L.k * L.k + 3) / 4 * 4;
+        wo -= f_wb_floats(L);
         f_conv_back(L, cur, nxt, fsm + wo);
       }
       __syncthreads();
@@ -550,10 +572,8 @@ __global__ void __launch_bounds__(FT) k_sweep_chain(NetDev net, PoolDev pool,
 
 static int sweep_wfloats(const NetDev& net, int t0) {
   int w = 0;
-  for (int t = 1; t < t0; ++t) {
-    const LayerDev& L = net.aff[t];
-    if (L.kind == MNBAB_CONV2D) w += (L.co * L.ci * L.k * L.k + 3) / 4 * 4;
-  }
+  for (int t = 1; t < t0; ++t)
+    if (net.aff[t].kind == MNBAB_CONV2D) w += f_wb_floats(net.aff[t]);
   return w;
 }
 
