@@ -1779,30 +1779,37 @@ __device__ double f64_edge(const LayerDev& L, const double* z, int o) {
   return acc;
 }
 
-__global__ void k_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev* props,
-                              NetDev net, const float* X, int ldx, double* buf, int ldb,
-                              double* fout) {
-  const int m = blockIdx.x;
+// FP64 forward pass of counterexample candidates (Sec. 3.1, upper bounding):
+// one launch per layer, one thread per (candidate, neuron), then the objective
+// row per candidate.
+__global__ void k_f64_input(int M, const float* X, int ldx, double* buf, int ldb, int d0) {
+  const int m = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < M && k < d0) buf[(size_t)m * ldb + k] = (double)X[(size_t)m * ldx + k];
+}
+
+__global__ void k_f64_layer(int M, NetDev net, int t, double* buf, int ldb) {
+  const int m = blockIdx.y;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M || o >= net.d[t]) return;
   double* z = buf + (size_t)m * ldb;
   const int d0 = net.d[0];
   auto seg = [&](int s) { return s == 0 ? z : z + d0 + net.off[s]; };
-  for (int k = threadIdx.x; k < d0; k += blockDim.x) z[k] = (double)X[(size_t)m * ldx + k];
-  __syncthreads();
-  for (int t = 1; t <= net.R; ++t) {
-    double* out = seg(t);
-    for (int o = threadIdx.x; o < net.d[t]; o += blockDim.x) {
-      double v = f64_edge(net.aff[t], seg(net.src1[t]), o);
-      if (net.n_edge[t] > 1) v += f64_edge(net.aff2[t], seg(net.src2[t]), o);
-      out[o] = v > 0.0 ? v : 0.0;
-    }
-    __syncthreads();
-  }
+  double v = f64_edge(net.aff[t], seg(net.src1[t]), o);
+  if (net.n_edge[t] > 1) v += f64_edge(net.aff2[t], seg(net.src2[t]), o);
+  seg(t)[o] = v > 0.0 ? v : 0.0;
+}
+
+__global__ void k_f64_objective(int M, const int* row_node, PoolDev pool, const PropDev* props,
+                                NetDev net, const double* buf, int ldb, double* fout) {
+  const int m = blockIdx.x;
+  const double* z = buf + (size_t)m * ldb;
   const int n = row_node[m];
   const PropDev& P = props[pool.prop[n]];
   const int r = pool.row[n];
   const int sR = net.src1[net.R + 1];
   const int dR = net.d[sR];
-  const double* h = seg(sR);
+  const double* h = sR == 0 ? z : z + net.d[0] + net.off[sR];
   double acc = 0.0;
   for (int k = threadIdx.x; k < dR; k += blockDim.x) acc = fma((double)P.Wf[(size_t)r * dR + k], h[k], acc);
   __shared__ double sh[32];
@@ -1820,12 +1827,34 @@ void launch_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev*
                         const NetDev& net, const float* X, int ldx, double* buf, int ldb,
                         double* fout, cudaStream_t st) {
   if (M <= 0) return;
-  k_forward_f64<<<M, 256, 0, st>>>(M, row_node, pool, props, net, X, ldx, buf, ldb, fout);
+  k_f64_input<<<dim3((net.d[0] + 255) / 256, M), 256, 0, st>>>(M, X, ldx, buf, ldb, net.d[0]);
+  for (int t = 1; t <= net.R; ++t)
+    k_f64_layer<<<dim3((net.d[t] + 127) / 128, M), 128, 0, st>>>(M, net, t, buf, ldb);
+  k_f64_objective<<<M, 256, 0, st>>>(M, row_node, pool, props, net, buf, ldb, fout);
 }
 
 __global__ void k_fill(float* p, size_t n, float v) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
+}
+
+// Root-bound slots of newly started properties: l = -inf, u = +inf, no splits,
+// and the slot's property index.
+__global__ void k_root_slot_init(int nb, const int* slots, const int* prop, PoolDev pool) {
+  const int b = blockIdx.x;
+  if (b >= nb) return;
+  const size_t o = (size_t)slots[b] * pool.SD;
+  for (int j = threadIdx.x; j < pool.SD; j += blockDim.x) {
+    pool.L[o + j] = -INFINITY;
+    pool.U[o + j] = INFINITY;
+    pool.S[o + j] = 0;
+  }
+  if (threadIdx.x == 0) pool.prop[slots[b]] = prop[b];
+}
+
+void launch_root_slot_init(int nb, const int* slots, const int* prop, PoolDev pool,
+                           cudaStream_t st) {
+  if (nb > 0) k_root_slot_init<<<nb, 256, 0, st>>>(nb, slots, prop, pool);
 }
 
 void launch_fill(float* p, size_t n, float v, cudaStream_t st) {

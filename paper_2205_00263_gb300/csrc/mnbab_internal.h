@@ -211,6 +211,9 @@ void launch_final_dot(int M, const int* row_node, PoolDev pool, const PropDev* p
 // Counterexample confirmation in FP64 needs a per-row buffer of d0 + SD doubles.
 
 void launch_fill(float* p, size_t n, float v, cudaStream_t st);
+// slots[b]: l = -inf, u = +inf, S = 0, prop = prop[b] (b < nb)
+void launch_root_slot_init(int nb, const int* slots, const int* prop, PoolDev pool,
+                           cudaStream_t st);
 // FP64 forward pass f_r(x) of rows of X (counterexample confirmation).
 void launch_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev* props,
                         const NetDev& net, const float* X, int ldx, double* buf, int ldb,

@@ -76,6 +76,7 @@ struct mnbab_net {
   // scratch
   int B = 0;          // batch capacity (objective rows)
   int pad_slot = -1;  // scratch node for padded graph rows
+  std::vector<int> new_roots, new_root_props;  // root-bound slots awaiting initialisation
   int chunk = 0;      // rows per back-substitution launch
   float *part = nullptr, *lb = nullptr;
   int *row_node = nullptr, *row_j = nullptr, *counter = nullptr;
@@ -1048,14 +1049,10 @@ void materialize(mnbab_net* n, mnbab_prop* p) {
   n->slot_prop[rs] = p->index;
   n->slot_row[rs] = 0;
   n->slot_split[rs] = 0;
-  {
-    Scope sc(c, C_BOOK, 0.0, 8.0 * n->SD, 2);
-    launch_fill(n->pool.L + (size_t)rs * n->SD, n->SD, -INFINITY, c->st);
-    launch_fill(n->pool.U + (size_t)rs * n->SD, n->SD, INFINITY, c->st);
-  }
-  ck(cudaMemsetAsync(n->pool.S + (size_t)rs * n->SD, 0, n->SD, c->st), "memset");
-  int pi = p->index;
-  h2d(c, n->pool.prop + rs, &pi, 1);
+  // slot state (l = -inf, u = +inf, no splits, property index) is set for all
+  // properties started together, in one launch (ensure_roots)
+  n->new_roots.push_back(rs);
+  n->new_root_props.push_back(p->index);
   for (int r = 0; r < p->n_rows; ++r) {
     const int sl = alloc_slot(n);
     n->slot_prop[sl] = p->index;
@@ -1073,6 +1070,15 @@ void ensure_roots(mnbab_net* n) {
   mnbab_ctx* c = n->ctx;
   for (auto* p : c->props)
     if (p->net == n && p->admitted && !p->materialized) materialize(n, p);
+  for (size_t b0 = 0; b0 < n->new_roots.size(); b0 += 2 * (size_t)n->B) {
+    const int nb = (int)std::min(n->new_roots.size() - b0, 2 * (size_t)n->B);
+    h2d(c, n->ri_dst, n->new_roots.data() + b0, nb);
+    h2d(c, n->ri_src, n->new_root_props.data() + b0, nb);
+    Scope sc(c, C_BOOK, 0.0, 9.0 * nb * n->SD);
+    launch_root_slot_init(nb, n->ri_dst, n->ri_src, n->pool, c->st);
+  }
+  n->new_roots.clear();
+  n->new_root_props.clear();
   std::vector<mnbab_prop*> pend;
   for (auto* p : c->props)
     if (p->net == n && p->root_pending) pend.push_back(p);
@@ -1217,7 +1223,7 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
                                              n->d0);
       }
       {
-        Scope sc(c, C_BOOK, 0.0, 8.0 * Mc * n->maxd);
+        Scope sc(c, C_BOOK, 0.0, 8.0 * Mc * n->maxd, n->R + 2);
         launch_forward_f64(Mc, n->cslots, n->pool, c->d_props, n->nd, n->Xb, n->d0, n->f64a,
                            n->d0 + n->SD, n->f64out, c->st);
       }
