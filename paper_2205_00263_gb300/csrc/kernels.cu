@@ -126,6 +126,68 @@ void launch_init_rows(const NetDev& net, int t, int edge, const RowsDev& rows, f
 }
 
 // ---------------------------------------------------------------------------
+// rows of layer 1: one affine step from the input box, then concretisation
+// ---------------------------------------------------------------------------
+// lb = sign * b_j + sum_k min(a_k lo_k, a_k hi_k), a = sign * W_1[j, :]; a conv
+// neuron touches only its k x k x ci patch (one thread per row), an FC neuron
+// its whole weight row (one warp per row).
+__global__ void k_first_rows_conv(NetDev net, PoolDev pool, const PropDev* props, RowsDev rows,
+                                  float* lb) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= rows.M) return;
+  const LayerDev& L = net.aff[1];
+  const int j = rows.j[m];
+  const float sg = rows.sign ? rows.sign[m] : 1.f;
+  const PropDev& P = props[pool.prop[rows.node[m]]];
+  const int hw = L.ho * L.wo;
+  const int co = j / hw, oh = (j % hw) / L.wo, ow = j % L.wo;
+  const int h0 = oh * L.s - L.p, w0 = ow * L.s - L.p;
+  const float* w = L.W + (size_t)co * L.ci * L.k * L.k;
+  float acc = 0.f;
+  for (int ci = 0; ci < L.ci; ++ci)
+    for (int kh = 0; kh < L.k; ++kh) {
+      const int ih = h0 + kh;
+      if (ih < 0 || ih >= L.hi) continue;
+      for (int kw = 0; kw < L.k; ++kw) {
+        const int iw = w0 + kw;
+        if (iw < 0 || iw >= L.wi) continue;
+        const float a = sg * __ldg(w + (ci * L.k + kh) * L.k + kw);
+        const int x = (ci * L.hi + ih) * L.wi + iw;
+        acc += a * (a >= 0.f ? P.lo[x] : P.hi[x]);
+      }
+    }
+  lb[m] = acc + sg * (net.bfull[1] ? net.bfull[1][j] : L.b[co]);
+}
+
+__global__ void k_first_rows_fc(NetDev net, PoolDev pool, const PropDev* props, RowsDev rows,
+                                float* lb) {
+  const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (m >= rows.M) return;
+  const LayerDev& L = net.aff[1];
+  const int j = rows.j[m];
+  const float sg = rows.sign ? rows.sign[m] : 1.f;
+  const PropDev& P = props[pool.prop[rows.node[m]]];
+  const float* w = L.W + (size_t)j * L.d_in;
+  float acc = 0.f;
+  for (int k = lane; k < L.d_in; k += 32) {
+    const float a = sg * __ldg(w + k);
+    acc += a * (a >= 0.f ? P.lo[k] : P.hi[k]);
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) lb[m] = acc + sg * (net.bfull[1] ? net.bfull[1][j] : L.b[j]);
+}
+
+void launch_first_rows(const NetDev& net, const PoolDev& pool, const PropDev* props,
+                       const RowsDev& rows, float* lb, cudaStream_t st) {
+  if (rows.M <= 0) return;
+  if (net.aff[1].kind == MNBAB_CONV2D)
+    k_first_rows_conv<<<(rows.M + 127) / 128, 128, 0, st>>>(net, pool, props, rows, lb);
+  else
+    k_first_rows_fc<<<(rows.M + 7) / 8, 256, 0, st>>>(net, pool, props, rows, lb);
+}
+
+// ---------------------------------------------------------------------------
 // windowed rows (intermediate bounds of convolution neurons)
 // ---------------------------------------------------------------------------
 // A row at neuron (co, oh, ow) of zhat_t starts, after its first step, as the

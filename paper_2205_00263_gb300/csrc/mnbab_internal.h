@@ -127,6 +127,10 @@ int launch_gemm_tc(int M, int N, int K, const float* A, int lda, const float* Bn
 // z^(t-1), with c = sign * b_t[j] into slot 0, through epilogue `e`.
 void launch_init_rows(const NetDev& net, int t, int edge, const RowsDev& rows, float* out, int ld,
                       const Epi& e, cudaStream_t st);
+// Intermediate-bound rows of ReLU layer 1 (one affine step from the input box):
+// lower bounds straight to lb[m].
+void launch_first_rows(const NetDev& net, const PoolDev& pool, const PropDev* props,
+                       const RowsDev& rows, float* lb, cudaStream_t st);
 // Windowed back-substitution of intermediate-bound rows that start at a
 // convolution neuron of zhat_t and meet only convolutions below it: after each
 // step the row is nonzero only within its receptive-field window, so one CTA

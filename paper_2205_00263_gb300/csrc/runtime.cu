@@ -465,6 +465,12 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
   mnbab_ctx* c = n->ctx;
   if (rows.M <= 0) return;
   const NetDev& nd = n->nd;
+  if (!o.final_mode && !o.store && !o.track && t == 1 && nd.n_edge[1] == 1 && nd.src1[1] == 0) {
+    // rows of layer 1: a dot product with the input box per row
+    Scope sc(c, C_INIT, 2.0 * rows.M * nd.d[0], 12.0 * rows.M);
+    launch_first_rows(nd, n->pool, c->d_props, rows, n->lb, c->st);
+    return;
+  }
   if (!o.final_mode && !o.store && !o.track && sweep_chain_supported(nd, t)) {
     // dense intermediate-bound rows above a chain: persistent fused sweep
     double macs = nd.d[t - 1];
