@@ -195,8 +195,12 @@ def roofline(stats, peaks, src, kernels_hash):
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        if t.get("kernels_sha") == kernels_hash and name in t.get("bytes_per_launch", {}):
-            r["traffic"] = t["bytes_per_launch"][name]
+        # DRAM bytes per row from one capture, scaled by the rows of an average
+        # launch (its algorithmic flops over the flops of one row)
+        if (t.get("kernels_sha") == kernels_hash and name in t.get("dram_bytes_per_row", {})
+                and name in t.get("flops_per_row", {})):
+            rows = st["flops"] / max(1, st["launches"]) / t["flops_per_row"][name]
+            r["traffic"] = t["dram_bytes_per_row"][name] * rows
     except (OSError, ValueError):
         pass
     return r
