@@ -30,7 +30,7 @@ namespace mnbab {
 
 namespace {
 
-constexpr int FT = 1024;  // threads per CTA
+constexpr int FT = 512;  // threads per CTA (two CTAs per SM)
 
 __device__ __forceinline__ float f_block_sum(float v, float* red) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -325,7 +325,8 @@ __device__ void f_conv_fwd(const LayerDev& L, const float* g, float* h, const fl
 
 __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, const PropDev* props,
                                                   const int* row_node, const int* row_j,
-                                                  FusedHP hp, float* AP_out, int maxw) {
+                                                  FusedHP hp, float* AP_out, float* GB_out,
+                                                  int maxw) {
   extern __shared__ __align__(16) float fsm[];
   __shared__ float red[32];
   __shared__ int improved;
@@ -343,8 +344,7 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
   float* B0 = fsm + wtot;
   float* B1 = B0 + maxw;
   float* APs = B1 + maxw;  // a' checkpoints, then d lb / d alpha
-  float* GBs = APs + SDp;  // d lb / d beta
-  float* Xs = GBs + SDp;   // minimiser x*
+  float* Xs = APs + SDp;   // minimiser x*
   auto wsm = [&](int t) {  // staged weights of conv layer t
     int o = 0;
     for (int u = 1; u < t; ++u) o += f_conv_wfloats(net.aff[u]);
@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
   const int n = row_node[m], r = row_j[m];
   const PropDev& P = props[pool.prop[n]];
   const size_t nb = (size_t)n * SD;
+  float* GBs = GB_out + (size_t)m * SD;  // d lb / d beta
   // Adam moments restart per node
   for (int i = threadIdx.x; i < SD; i += FT) {
     pool.MA[nb + i] = 0.f;
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
         const float ga = abr ? hv * ap : 0.f;
         const float gb = hv * (float)s;
         APs[off + j] = ga;
-        GBs[off + j] = gb;
+        GBs[off + j] = gb;  // row scratch in global memory (L2-resident)
         gm = fmaxf(gm, fmaxf(fabsf(ga), fabsf(gb)));
         h[j] = hv * D + bl;
       }
@@ -586,7 +587,7 @@ static int fused_maxw(const NetDev& net, int d0) {
 static int fused_smem_floats(const NetDev& net, int SD, int d0) {
   int w = 0;
   for (int t = 1; t <= net.R; ++t) w += f_conv_wfloats(net.aff[t]);
-  return w + 2 * fused_maxw(net, d0) + 2 * ((SD + 3) / 4 * 4) + d0;
+  return w + 2 * fused_maxw(net, d0) + (SD + 3) / 4 * 4 + d0;
 }
 
 bool fused_supported(const NetDev& net, int SD, int d0, int steps) {
@@ -603,12 +604,13 @@ bool fused_supported(const NetDev& net, int SD, int d0, int steps) {
 
 void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropDev* props,
                       const int* row_node, const int* row_j, const FusedHP& hp, float* AP_out,
+                      float* GB_out,
                       cudaStream_t st) {
   if (M <= 0) return;
   const int smem = fused_smem_floats(net, pool.SD, pool.d0) * (int)sizeof(float);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_opt_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_opt_chain<<<M, FT, smem, st>>>(net, pool, props, row_node, row_j, hp, AP_out,
+  k_opt_chain<<<M, FT, smem, st>>>(net, pool, props, row_node, row_j, hp, AP_out, GB_out,
                                   fused_maxw(net, pool.d0));
 }
 

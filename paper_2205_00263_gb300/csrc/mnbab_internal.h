@@ -159,9 +159,11 @@ struct FusedHP {
 };
 bool fused_supported(const NetDev& net, int SD, int d0, int steps);
 // rows m < M: node row_node[m], objective row row_j[m]; a' of the final sweep
-// goes to AP_out [M][SD]; BEST / BESTX of the node track the best iterate.
+// goes to AP_out [M][SD]; GB_out [M][SD] is row scratch for d lb / d beta;
+// BEST / BESTX of the node track the best iterate.
 void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropDev* props,
                       const int* row_node, const int* row_j, const FusedHP& hp, float* AP_out,
+                      float* GB_out,
                       cudaStream_t st);
 // Intermediate-bound rows that start at a fully connected neuron of zhat_t0
 // above a chain of FC / conv layers: one persistent CTA loop, each row carried

@@ -775,7 +775,8 @@ void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a)
     Scope sc(c, C_FUSED,
              2.0 * M * ((a.steps + 1.0) * (macs + n->nd.d[n->R]) + a.steps * macs),
              (double)M * (a.steps + 1.0) * n->SD * 66.0);
-    launch_opt_chain(M, n->nd, n->pool, c->d_props, n->bslots, n->brows, hp, n->AP, c->st);
+    launch_opt_chain(M, n->nd, n->pool, c->d_props, n->bslots, n->brows, hp, n->AP, n->GB,
+                     c->st);
     return;
   }
   {
