@@ -44,6 +44,8 @@ BATCH = 512
 BUDGET = 256
 ADAM_STEPS = 20
 METRIC = "BaB nodes bounded/s & verdicts@timeout, batched/serving vs plain, 1 GB300"
+SERVE_CAPACITY = 4096     # node slots per network in the serving context
+SERVE_HBM = 64 << 30      # serving context's HBM budget (config 4: 64 GB)
 WORKLOAD = ("conv_small_28: 1x28x28 -> conv16 4x4 s2 -> ReLU -> conv32 4x4 s2 -> ReLU -> FC100 -> "
             "ReLU -> FC10, 100 active properties (rolling window), 9 margin rows each, "
             "<=512 subproblems per step, 20 Adam steps per node, budget 256 nodes/property")
@@ -389,7 +391,8 @@ def run_ours(args):
 
     serving = None
     if world == 1 and (args.serve_requests is None or args.serve_requests > 0):
-        sctx = Context(device=local, stream=stream.cuda_stream, node_capacity=args.node_capacity)
+        sctx = Context(device=local, stream=stream.cuda_stream, node_capacity=SERVE_CAPACITY,
+                       hbm_budget_bytes=SERVE_HBM)
         try:
             serving = serving_run(sctx, serving_nets(sctx), args.serve_requests or 24, args.serve_rate,
                                   seed=4, timeout_s=60.0, budget=BUDGET, plain_cap_s=15.0,
@@ -611,10 +614,10 @@ def run_serving(args):
     __graft_entry__.build()
     from paper_2205_00263_gb300 import Context
     stream = torch.cuda.Stream()
-    ctx = Context(device=0, stream=stream.cuda_stream, node_capacity=args.node_capacity,
-                  hbm_budget_bytes=64 << 30)
+    ctx = Context(device=0, stream=stream.cuda_stream, node_capacity=SERVE_CAPACITY,
+                  hbm_budget_bytes=SERVE_HBM)
     out = serving_run(ctx, serving_nets(ctx), args.serve_requests or 400, args.serve_rate, seed=4,
-                      timeout_s=60.0, budget=BUDGET, plain_cap_s=300.0, stream=stream)
+                      timeout_s=60.0, budget=BUDGET, plain_cap_s=120.0, stream=stream)
     out["metric"] = METRIC
     out["workload"] = ("serving: Poisson stream of verification requests over the calibrated "
                        "networks of configs 1-3, 60 s timeout, 64 GB HBM budget")
