@@ -345,6 +345,10 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
   float* B1 = B0 + maxw;
   float* APs = B1 + maxw;  // a' checkpoints, then d lb / d alpha
   float* Xs = APs + SDp;   // minimiser x*
+  // case of each neuron, fixed during the optimisation (bounds and splits do not
+  // change): 0 inactive, 1 active, 2 unstable and unsplit, 3 split with S = -1
+  // (zhat >= 0), 4 split with S = +1 (zhat <= 0)
+  unsigned char* code = reinterpret_cast<unsigned char*>(Xs + ((d0 + 3) & ~3));
   auto wsm = [&](int t) {  // staged weights of conv layer t
     int o = 0;
     for (int u = 1; u < t; ++u) o += f_conv_wfloats(net.aff[u]);
@@ -361,6 +365,8 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
     pool.VA[nb + i] = 0.f;
     pool.MB[nb + i] = 0.f;
     pool.VB[nb + i] = 0.f;
+    const int sv = pool.S[nb + i];
+    code[i] = sv == -1 ? 3 : sv == 1 ? 4 : pool.L[nb + i] >= 0.f ? 1 : pool.U[nb + i] <= 0.f ? 0 : 2;
   }
   const int dR = net.d[R];
   for (int step = 0; step <= hp.steps; ++step) {
@@ -375,22 +381,24 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
       const int dt = net.d[t], off = net.off[t];
       const float* bias = net.bfull[t];
       for (int j = threadIdx.x; j < dt; j += FT) {
-        const size_t q = nb + off + j;
-        const float l = pool.L[q], u = pool.U[q];
-        const int s = pool.S[q];
+        const int cd = code[off + j];
         const float ap = cur[j];
-        float D, bl = 0.f;
-        if (s == -1) D = 1.f;
-        else if (s == 1) D = 0.f;
-        else if (l >= 0.f) D = 1.f;
-        else if (u <= 0.f) D = 0.f;
-        else if (ap >= 0.f) D = pool.ALPHA[q];
-        else {
-          const float den = u - l;
-          D = u / den;
-          bl = (-u * l) / den;
+        float D, bl = 0.f, bt = 0.f;
+        if (cd == 2) {
+          const size_t q = nb + off + j;
+          if (ap >= 0.f) {
+            D = pool.ALPHA[q];
+          } else {
+            const float l = pool.L[q], u = pool.U[q];
+            const float den = u - l;
+            D = u / den;
+            bl = (-u * l) / den;
+          }
+        } else {
+          D = (cd == 1 || cd == 3) ? 1.f : 0.f;
+          if (cd >= 3) bt = pool.BETA[nb + off + j] * (cd == 3 ? -1.f : 1.f);
         }
-        const float ah = ap * D + pool.BETA[q] * (float)s;
+        const float ah = ap * D + bt;
         APs[off + j] = ap;
         part += ap * bl + ah * bias[j];
         cur[j] = ah;
@@ -436,29 +444,29 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
       __syncthreads();
       const int dt = net.d[t], off = net.off[t];
       for (int j = threadIdx.x; j < dt; j += FT) {
-        const size_t q = nb + off + j;
-        const float l = pool.L[q], u = pool.U[q];
-        const int s = pool.S[q];
+        const int cd = code[off + j];
         const float ap = APs[off + j];
         const float hv = h[j];
-        float D, bl = 0.f;
-        bool abr = false;
-        if (s == -1) D = 1.f;
-        else if (s == 1) D = 0.f;
-        else if (l >= 0.f) D = 1.f;
-        else if (u <= 0.f) D = 0.f;
-        else if (ap >= 0.f) {
-          D = pool.ALPHA[q];
-          abr = true;
+        float D, bl = 0.f, ga = 0.f, gb = 0.f;
+        if (cd == 2) {
+          const size_t q = nb + off + j;
+          if (ap >= 0.f) {
+            D = pool.ALPHA[q];
+            ga = hv * ap;
+          } else {
+            const float l = pool.L[q], u = pool.U[q];
+            const float den = u - l;
+            D = u / den;
+            bl = (-u * l) / den;
+          }
         } else {
-          const float den = u - l;
-          D = u / den;
-          bl = (-u * l) / den;
+          D = (cd == 1 || cd == 3) ? 1.f : 0.f;
+          if (cd >= 3) {
+            gb = hv * (cd == 3 ? -1.f : 1.f);
+            GBs[off + j] = gb;  // row scratch in global memory (L2-resident)
+          }
         }
-        const float ga = abr ? hv * ap : 0.f;
-        const float gb = hv * (float)s;
         APs[off + j] = ga;
-        GBs[off + j] = gb;  // row scratch in global memory (L2-resident)
         gm = fmaxf(gm, fmaxf(fabsf(ga), fabsf(gb)));
         h[j] = hv * D + bl;
       }
@@ -469,23 +477,28 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
     const float thr = hp.floor * gmax;
     const float eps = fmaxf(hp.eps_abs, hp.eps_rel * gmax);
     const float bc1 = hp.bc1[step], bc2 = hp.bc2[step];
+    // the alpha of a stable or split neuron and the beta of an unsplit one have a
+    // zero gradient at every step, so their (zero-moment) updates are identities
     for (int i = threadIdx.x; i < SD; i += FT) {
+      const int cd = code[i];
       const size_t q = nb + i;
-      float ga = APs[i], gb = GBs[i];
-      if (fabsf(ga) <= thr) ga = 0.f;
-      if (fabsf(gb) <= thr) gb = 0.f;
-      float th = pool.ALPHA[q], mo = pool.MA[q], ve = pool.VA[q];
-      f_adam(th, mo, ve, ga, hp.lr_a, hp.b1, hp.b2, eps, bc1, bc2);
-      pool.ALPHA[q] = fminf(fmaxf(th, 0.f), 1.f);
-      pool.MA[q] = mo;
-      pool.VA[q] = ve;
-      th = pool.BETA[q];
-      mo = pool.MB[q];
-      ve = pool.VB[q];
-      f_adam(th, mo, ve, gb, hp.lr_b, hp.b1, hp.b2, eps, bc1, bc2);
-      pool.BETA[q] = fmaxf(th, 0.f);
-      pool.MB[q] = mo;
-      pool.VB[q] = ve;
+      if (cd == 2) {
+        float ga = APs[i];
+        if (fabsf(ga) <= thr) ga = 0.f;
+        float th = pool.ALPHA[q], mo = pool.MA[q], ve = pool.VA[q];
+        f_adam(th, mo, ve, ga, hp.lr_a, hp.b1, hp.b2, eps, bc1, bc2);
+        pool.ALPHA[q] = fminf(fmaxf(th, 0.f), 1.f);
+        pool.MA[q] = mo;
+        pool.VA[q] = ve;
+      } else if (cd >= 3) {
+        float gb = GBs[i];
+        if (fabsf(gb) <= thr) gb = 0.f;
+        float th = pool.BETA[q], mo = pool.MB[q], ve = pool.VB[q];
+        f_adam(th, mo, ve, gb, hp.lr_b, hp.b1, hp.b2, eps, bc1, bc2);
+        pool.BETA[q] = fmaxf(th, 0.f);
+        pool.MB[q] = mo;
+        pool.VB[q] = ve;
+      }
     }
   }
 }
@@ -587,7 +600,7 @@ static int fused_maxw(const NetDev& net, int d0) {
 static int fused_smem_floats(const NetDev& net, int SD, int d0) {
   int w = 0;
   for (int t = 1; t <= net.R; ++t) w += f_conv_wfloats(net.aff[t]);
-  return w + 2 * fused_maxw(net, d0) + (SD + 3) / 4 * 4 + d0;
+  return w + 2 * fused_maxw(net, d0) + (SD + 3) / 4 * 4 + (d0 + 3) / 4 * 4 + (SD + 3) / 4;
 }
 
 bool fused_supported(const NetDev& net, int SD, int d0, int steps) {
