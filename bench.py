@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--window", type=int, default=WINDOW, help="active properties")
     ap.add_argument("--graphs", action="store_true",
                     help="replay the optimisation loop from captured CUDA graphs")
+    ap.add_argument("--gemm-tc", action="store_true",
+                    help="tensor-core GEMM check: conv_big_32 root bounding on the tcgen05 path")
     ap.add_argument("--serving", action="store_true",
                     help="only the serving run (Poisson request stream), full size")
     ap.add_argument("--serve-requests", type=int, default=None,
@@ -606,6 +608,47 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_gemm_tc(args):
+    """Root bounding of conv_big_32 properties with the FC back-substitution and
+    forward products forced onto the tcgen05 kernel (3xTF32: operands split into
+    TF32 hi and lo parts, three MMAs per K step, FP32 accumulation in TMEM).  The
+    FC512 rows give products of 2,048 rows x 4,096 x 512.  Reports the summed
+    CUDA-event time and algorithmic flops of those GEMM launches."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_00263_gb300 import Context
+    stream = torch.cuda.Stream()
+    layers = synth.make_network(2)
+    eps = synth.load_eps(2)
+    props = synth.make_properties(2, layers, n=4, eps=eps)
+    out = {}
+    for path, label in ((2, "tcgen05_3xtf32"), (1, "simt_fp32")):
+        ctx = Context(device=0, stream=stream.cuda_stream, node_capacity=256, gemm_path=path)
+        net = ctx.load_network(layers)
+        ps = [ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d) for pr in props]
+        ctx.root_bounds(ps[0], 1)  # warm-up: first property's root bounds
+        ps = [ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d) for pr in props]
+        ctx.profile(True)
+        for p in ps:
+            ctx.root_bounds(p, 1)
+        stats, _ = ctx.profile_read()
+        ctx.profile(False)
+        g = stats["backsub_fc_gemm"]
+        out[label] = {"launches": g["launches"], "ms": g["ms"], "gflop": g["flops"] / 1e9,
+                      "tflops": g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] else None}
+        ctx.close()
+    peaks, src = load_peaks()
+    tf32 = peaks["bf16_tflops"] / 2.0
+    out["peak_3xtf32_tflops"] = tf32 / 3.0
+    out["peak_source"] = f"{src} bf16_tflops x 1/2 (nominal TF32/BF16 ratio) / 3 (three MMAs)"
+    t = out["tcgen05_3xtf32"]["tflops"]
+    out["frac_of_3xtf32"] = t / out["peak_3xtf32_tflops"] if t else None
+    out["workload"] = ("conv_big_32 root bounding, 4 properties: FC back-substitution GEMMs "
+                       "(rows of FC512 and FC512 neurons, both sides)")
+    print(json.dumps(out), flush=True)
+
+
 def run_serving(args):
     """Config 4: Poisson stream (rate 4/s, 400 requests, seed 4) over the
     calibrated networks of configs 1-3, 60 s timeout, continuous batching."""
@@ -629,6 +672,8 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.gemm_tc:
+        run_gemm_tc(a)
     elif a.serving:
         run_serving(a)
     else:

@@ -8,12 +8,13 @@
 // hi.hi + hi.lo + lo.hi accumulated in FP32 in tensor memory, which keeps FP32
 // accuracy (the dropped lo.lo term is below 2^-22 relative).
 //
-// One CTA = 4 warps computes a 128 x BN tile.  Per K block of 32, the threads
+// One CTA = 16 warps computes a 128 x BN tile.  Per K block of 32, the threads
 // load A and B, split them and store the four tiles in the no-swizzle
 // canonical K-major layout (8-row x 16-byte core matrices; adjacent core
 // matrices along K are LBO = 128 B apart, along M/N SBO = 1024 B apart); one
-// thread issues 4 k-steps x 3 tcgen05.mma (K = 8 each) and commits them to an
-// mbarrier.  The epilogue reads the accumulator with tcgen05.ld (warp w owns
+// thread issues 4 k-steps x 3 tcgen05.mma (K = 8 each) and commits them to the
+// stage's mbarrier.  Two stages: the threads load and split block k + 1 while
+// the tensor core works on block k.  The epilogue reads the accumulator with tcgen05.ld (warp w owns
 // TMEM lanes 32w..32w+31 = tile rows) and applies the same epilogue functions
 // as the SIMT kernels; each thread owns one row, so the row partial sums of
 // the offset need no cross-thread reduction.
@@ -111,25 +112,74 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 }  // namespace
 
+// Loads the 128-or-BN-row x 32 K block of a K-major operand starting at
+// (row0, k0), splits it into TF32 hi / lo and stores both in the canonical
+// layout.  Vector path: a lane loads 4 consecutive K values (16 B) and stores 16 B
+// per part; lanes 0-7 of each quarter-warp take 8 consecutive rows at the same
+// K quad (conflict-free 16-byte shared stores), the quarter-warps 4 K quads
+// (64 contiguous bytes per row in global memory).
+constexpr int TC_THREADS = 512;  // 16 warps: loads in flight while staging
+
+template <int ROWS>
+__device__ __forceinline__ void tc_stage(const float* __restrict__ X, int ld, int nrows, int K,
+                                         int row0, int k0, bool vec, unsigned char* hi,
+                                         unsigned char* lo) {
+  const int tid = threadIdx.x;
+  if (vec) {
+    constexpr int NQ = ROWS * TBK / 4;  // float4 per block
+#pragma unroll 4
+    for (int q = tid; q < NQ; q += TC_THREADS) {
+      const int lane = q & 31, w = q >> 5;
+      const int r = (w >> 1) * 8 + (lane & 7);
+      const int k4 = (w & 1) * 4 + (lane >> 3);
+      const int gr = row0 + r, gk = k0 + 4 * k4;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gr < nrows && gk < K) x = __ldg(reinterpret_cast<const float4*>(X + (size_t)gr * ld + gk));
+      uint4 h, l;
+      h.x = to_tf32(x.x);
+      l.x = to_tf32(x.x - __uint_as_float(h.x));
+      h.y = to_tf32(x.y);
+      l.y = to_tf32(x.y - __uint_as_float(h.y));
+      h.z = to_tf32(x.z);
+      l.z = to_tf32(x.z - __uint_as_float(h.z));
+      h.w = to_tf32(x.w);
+      l.w = to_tf32(x.w - __uint_as_float(h.w));
+      const uint32_t o = tile_off(r, 4 * k4);
+      *reinterpret_cast<uint4*>(hi + o) = h;
+      *reinterpret_cast<uint4*>(lo + o) = l;
+    }
+    return;
+  }
+  for (int q = tid; q < ROWS * TBK; q += TC_THREADS) {
+    const int r = q >> 5, k = q & 31;
+    const int gr = row0 + r, gk = k0 + k;
+    const float x = (gr < nrows && gk < K) ? X[(size_t)gr * ld + gk] : 0.f;
+    const uint32_t h = to_tf32(x);
+    const uint32_t l = to_tf32(x - __uint_as_float(h));
+    const uint32_t o = tile_off(r, k);
+    *reinterpret_cast<uint32_t*>(hi + o) = h;
+    *reinterpret_cast<uint32_t*>(lo + o) = l;
+  }
+}
+
 template <int BN>
-__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const float* __restrict__ A,
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, const float* __restrict__ A,
                                                  int lda, const float* __restrict__ B, int ldb,
                                                  const float* __restrict__ bias, int bias_div,
                                                  float* C, int ldc, Epi e, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-aligned tiles: A_hi, A_lo (128 x 32), B_hi, B_lo (BN x 32)
+  // two stages of 1024-aligned tiles: A_hi, A_lo (128 x 32), B_hi, B_lo (BN x 32)
+  constexpr int STAGE = 2 * TBM * TBK * 4 + 2 * BN * TBK * 4;
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* a_hi = base;
-  unsigned char* a_lo = a_hi + TBM * TBK * 4;
-  unsigned char* b_hi = a_lo + TBM * TBK * 4;
-  unsigned char* b_lo = b_hi + BN * TBK * 4;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(b_lo + BN * TBK * 4);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * STAGE);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * BN;
-  const uint32_t bar_a = smem_u32(bar);
+  const uint32_t bar0 = smem_u32(bar), bar1 = smem_u32(bar + 1);
+  const bool vecA = (lda & 3) == 0 && (K & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  const bool vecB = (ldb & 3) == 0 && (K & 3) == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -138,7 +188,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const floa
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_a), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -147,30 +198,28 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const floa
   const uint32_t tmem = *tmem_holder;
   constexpr uint32_t idesc = idesc_tf32(BN);
 
-  uint32_t phase = 0;
+  // block kb uses stage kb & 1 and commits to that stage's barrier; before a
+  // stage is refilled, the MMAs of the block that last used it (kb - 2) must be
+  // done: that barrier's ((kb >> 1) - 1)-th completion
+  const int nk = (K + TBK - 1) / TBK;
   bool ok = true;
-  for (int k0 = 0; k0 < K; k0 += TBK) {
-    // stage A (128 x 32) and B (BN x 32), split into hi / lo TF32
-    for (int q = tid; q < TBM * TBK; q += 128) {
-      const int r = q >> 5, k = q & 31;
-      const int gm = m0 + r, gk = k0 + k;
-      const float x = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.f;
-      const uint32_t h = to_tf32(x);
-      const uint32_t l = to_tf32(x - __uint_as_float(h));
-      const uint32_t o = tile_off(r, k);
-      *reinterpret_cast<uint32_t*>(a_hi + o) = h;
-      *reinterpret_cast<uint32_t*>(a_lo + o) = l;
+  int last = -1;  // last committed block
+  for (int kb = 0; kb < nk; ++kb) {
+    const int st = kb & 1;
+    const uint32_t bst = st ? bar1 : bar0;
+    if (kb >= 2) {
+      const bool mine = mbar_wait(bst, (uint32_t)(((kb >> 1) - 1) & 1));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      ok = __syncthreads_and(mine) != 0;  // uniform across the CTA
+      if (!ok) break;
     }
-    for (int q = tid; q < BN * TBK; q += 128) {
-      const int r = q >> 5, k = q & 31;
-      const int gn = n0 + r, gk = k0 + k;
-      const float x = (gn < N && gk < K) ? B[(size_t)gn * ldb + gk] : 0.f;
-      const uint32_t h = to_tf32(x);
-      const uint32_t l = to_tf32(x - __uint_as_float(h));
-      const uint32_t o = tile_off(r, k);
-      *reinterpret_cast<uint32_t*>(b_hi + o) = h;
-      *reinterpret_cast<uint32_t*>(b_lo + o) = l;
-    }
+    unsigned char* a_hi = base + st * STAGE;
+    unsigned char* a_lo = a_hi + TBM * TBK * 4;
+    unsigned char* b_hi = a_lo + TBM * TBK * 4;
+    unsigned char* b_lo = b_hi + BN * TBK * 4;
+    const int k0 = kb * TBK;
+    tc_stage<TBM>(A, lda, M, K, m0, k0, vecA, a_hi, a_lo);
+    tc_stage<BN>(B, ldb, N, K, n0, k0, vecB, b_hi, b_lo);
     // make the generic-proxy smem writes visible to the tensor core
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -181,38 +230,42 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const floa
 #pragma unroll
       for (int ks = 0; ks < TBK / 8; ++ks) {
         const uint32_t off = ks * 256;  // two core matrices of K per MMA
-        const uint32_t first = (k0 == 0 && ks == 0) ? 0u : 1u;
+        const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
         mma_tf32(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, first);
         mma_tf32(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
         mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, 1u);
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              bar_a)
+              bst)
           : "memory");
     }
-    // all threads wait for the MMAs before reusing the tiles
-    const bool mine = mbar_wait(bar_a, phase);
+    last = kb;
+  }
+  if (ok && last >= 0) {
+    // the last commit covers every MMA issued before it
+    const bool mine = mbar_wait(last & 1 ? bar1 : bar0, (uint32_t)((last >> 1) & 1));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    ok = __syncthreads_and(mine) != 0;  // uniform across the CTA
-    if (!ok) break;
-    phase ^= 1u;
+    ok = __syncthreads_and(mine) != 0;
   }
   if (!ok) {
     // record the timeout, then give the MMAs in flight one more bounded wait
     // before the tensor memory they write is released
     if (tid == 0) {
       atomicExch(err, 1);
-      mbar_wait(bar_a, phase);
+      if (last >= 0) mbar_wait(last & 1 ? bar1 : bar0, (uint32_t)((last >> 1) & 1));
     }
     __syncthreads();
   }
+  __shared__ float cpart[4][TBM];  // row partials of the four column groups
   if (ok) {
-    // epilogue: warp w owns rows 32w..32w+31 of the tile, one row per thread
-    const int m = m0 + warp * 32 + lane;
+    // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (tile rows, one
+    // per thread) and column group w / 4 (BN / 4 columns)
+    const int quarter = warp & 3, cg = warp >> 2;
+    const int m = m0 + quarter * 32 + lane;
     float part = 0.f;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < BN; c0 += 16) {
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+    for (int c0 = cg * (BN / 4); c0 < (cg + 1) * (BN / 4); c0 += 16) {
       float v[16];
       tmem_ld16<16>(trow + (uint32_t)c0, v);
       if (m < M) {
@@ -228,7 +281,14 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const floa
         }
       }
     }
-    if (epi_has_part(e) && m < M) e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = part;
+    cpart[cg][quarter * 32 + lane] = part;
+  }
+  __syncthreads();
+  if (ok && warp < 4 && epi_has_part(e)) {
+    const int r = warp * 32 + lane, m = m0 + r;
+    if (m < M)
+      e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] =
+          ((cpart[0][r] + cpart[1][r]) + cpart[2][r]) + cpart[3][r];
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -241,7 +301,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const floa
 
 template <int BN>
 static constexpr int tc_smem_bytes() {
-  return 1024 + 2 * TBM * TBK * 4 + 2 * BN * TBK * 4 + 64;
+  return 1024 + 2 * (2 * TBM * TBK * 4 + 2 * BN * TBK * 4) + 64;
 }
 
 template <int BN>
@@ -255,7 +315,7 @@ static int launch_bn(int M, int N, int K, const float* A, int lda, const float* 
     attr = true;
   }
   dim3 grid((N + BN - 1) / BN, (M + TBM - 1) / TBM);
-  k_gemm_tc<BN><<<grid, 128, smem, st>>>(M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e, err);
+  k_gemm_tc<BN><<<grid, TC_THREADS, smem, st>>>(M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e, err);
   return grid.x;
 }
 
