@@ -258,6 +258,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, con
     __syncthreads();
   }
   __shared__ float cpart[4][TBM];  // row partials of the four column groups
+  constexpr int CTS = BN + 1;       // output tile row stride (floats)
+  float* ctile = reinterpret_cast<float*>(base);
   if (ok) {
     // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (tile rows, one
     // per thread) and column group w / 4 (BN / 4 columns)
@@ -265,6 +267,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, con
     const int m = m0 + quarter * 32 + lane;
     float part = 0.f;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+    // the finished tile goes through shared memory (the operand stages, idle now
+    // that every MMA has completed) so that its global stores are coalesced
     for (int c0 = cg * (BN / 4); c0 < (cg + 1) * (BN / 4); c0 += 16) {
       float v[16];
       tmem_ld16<16>(trow + (uint32_t)c0, v);
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, con
             float x = v[i];
             if (bias) x += bias[n / bias_div];
             const float o = epi_apply(e, m, n, x, part);
-            if (C) C[(size_t)m * ldc + n] = o;
+            if (C) ctile[(quarter * 32 + lane) * CTS + c0 + i] = o;
           }
         }
       }
@@ -284,6 +288,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, con
     cpart[cg][quarter * 32 + lane] = part;
   }
   __syncthreads();
+  if (ok && C) {
+    for (int q = tid; q < TBM * BN; q += TC_THREADS) {
+      const int r = q / BN, c = q % BN;
+      const int m = m0 + r, n = n0 + c;
+      if (m < M && n < N) C[(size_t)m * ldc + n] = ctile[r * CTS + c];
+    }
+  }
   if (ok && warp < 4 && epi_has_part(e)) {
     const int r = warp * 32 + lane, m = m0 + r;
     if (m < M)
