@@ -156,8 +156,9 @@ def make_image(seed: int, in_shape) -> np.ndarray:
     return _blur3(img).astype(np.float32)
 
 
-def net_forward(layers: list[dict], x: np.ndarray) -> np.ndarray:
-    """Plain float64 network evaluation, used only to label the images."""
+def net_forward(layers: list[dict], x: np.ndarray, collect: list | None = None) -> np.ndarray:
+    """Plain float64 network evaluation (labels the images; with `collect`, the
+    input of every ReLU is appended to it in layer order)."""
     out = {-1: np.asarray(x, dtype=np.float64).reshape(-1)}
     for i, L in enumerate(layers):
         k = L["kind"]
@@ -166,6 +167,8 @@ def net_forward(layers: list[dict], x: np.ndarray) -> np.ndarray:
             continue
         h = out[L.get("src", i - 1)]
         if k == "relu":
+            if collect is not None:
+                collect.append(h)
             out[i] = np.maximum(h, 0.0)
         elif k == "fc":
             out[i] = L["W"].astype(np.float64) @ h + L["b"].astype(np.float64)

@@ -384,6 +384,39 @@ def test_conv_full_size_sampled(Context):
 # --------------------------------------------------------------------------
 # edge cases
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_big_networks_full_size_sound_and_paths_agree(Context, cfg):
+    """Conv-big and the ResNet at their full 3x32x32 input (the oracle needs about a
+    minute per DeepPoly pass there): root bounds contain the pre-activations of
+    sampled inputs and box corners, and the tensor-core (3xTF32) and SIMT paths
+    give the same bounds within the tolerance."""
+    layers = synth.make_network(cfg)
+    pr = synth.make_properties(cfg, layers, n=1, eps=synth.load_eps(cfg))[0]
+    res = {}
+    for path in (1, 2):
+        with Context(node_capacity=64, gemm_path=path) as ctx:
+            net = ctx.load_network(layers)
+            p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+            res[path] = [ctx.root_bounds(p, i) for i in range(1, net.R + 1)]
+    for i, ((l1, u1), (l2, u2)) in enumerate(zip(res[1], res[2])):
+        _assert_close(l2, l1, f"l{i + 1} tensor-core vs SIMT")
+        _assert_close(u2, u1, f"u{i + 1} tensor-core vs SIMT")
+    rng = np.random.default_rng(cfg)
+    lo, hi = pr.lo.astype(np.float64), pr.hi.astype(np.float64)
+    for k in range(24):
+        if k < 4:
+            x = np.where(rng.uniform(size=lo.size) < 0.5, lo, hi)  # box corners
+        else:
+            x = lo + (hi - lo) * rng.uniform(size=lo.size)
+        pre = []
+        synth.net_forward(layers, x, collect=pre)
+        assert len(pre) == len(res[1])
+        for i, ((l, u), z) in enumerate(zip(res[1], pre)):
+            slack = TOL * (1.0 + np.abs(z))
+            assert (z >= l - slack).all(), f"layer {i + 1}: lower bound above an activation"
+            assert (z <= u + slack).all(), f"layer {i + 1}: upper bound below an activation"
+
+
 def test_zero_radius_box_is_exact(Context):
     layers, C, d, lo, hi, prep = fc_case(12, (37, 53, 29, 7), 0.0)
     x0 = lo
