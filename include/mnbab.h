@@ -321,6 +321,20 @@ mnbab_status mnbab_poll(mnbab_ctx* ctx, uint64_t ticket, int32_t* done);
 mnbab_status mnbab_request_result(mnbab_ctx* ctx, uint64_t ticket, int32_t* verdict, double* wait_s,
                                   double* total_s, int32_t* nodes);
 
+/* Adversarial pre-attack (Sec. 4, experimental setup: counterexamples are
+ * searched before branch-and-bound).  For every row r of the property,
+ * projected gradient descent with sign steps on the margin (C f(x) + d)_r:
+ *   x_{k+1} = clip(x_k - alpha sign(grad), lo, hi), alpha = 2.5 (hi - lo) / (2 steps),
+ * k = 0 .. steps - 1, from each of n_starts starting points (host, [n_starts][d0],
+ * clipped to the box; the caller draws them).  best_out[r] (host, n_rows) is the
+ * smallest FP32 margin over all iterates of all starts; x_out (host,
+ * [n_rows][d0], nullable) its first minimiser (starts in order).  A negative
+ * margin is a counterexample candidate: confirm it in higher precision before
+ * using it.  Chain networks of FC / convolution layers whose weights fit in
+ * shared memory; MNBAB_E_UNSUPPORTED otherwise. */
+mnbab_status mnbab_attack(mnbab_ctx* ctx, const mnbab_prop* prop, int32_t n_starts, int32_t steps,
+                          const float* starts, float* best_out, float* x_out);
+
 /* Number of open nodes queued for the property. */
 mnbab_status mnbab_queue_size(const mnbab_ctx* ctx, const mnbab_prop* prop, int32_t* n_out);
 

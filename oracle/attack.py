@@ -13,7 +13,8 @@ projected gradient descent with sign steps on the margin of one property row,
 from caller-given starting points x_0 (one per restart; random numbers are
 inputs, not drawn here), and the result of a row is the smallest margin over all
 iterates of all restarts with its first minimiser (restarts in order, iterates in
-order).  ReLU'(0) = 0 and sign(0) = 0.  A negative margin is a counterexample.
+order).  ReLU'(0) = 1 (the derivative autograd gives the forward pass's clamp)
+and sign(0) = 0.  A negative margin is a counterexample.
 
 Gradients are exact reverse-mode derivatives of the FP64 forward pass (torch
 autograd as a library step); they are pinned by central finite differences.

@@ -290,6 +290,16 @@ class Context:
         self._ck(self.lib.mnbab_queue_size(self.h, prop.h, C.byref(n)))
         return n.value
 
+    def attack(self, prop: Prop, starts, steps: int):
+        """Adversarial pre-attack (sign-step PGD per property row from the given
+        starting points [n_starts][d0]); returns (best margin per row, minimisers)."""
+        st = _f32(np.asarray(starts).reshape(-1, prop.net.d0))
+        best = np.empty(prop.n_rows, np.float32)
+        x = np.empty((prop.n_rows, prop.net.d0), np.float32)
+        self._ck(self.lib.mnbab_attack(self.h, prop.h, st.shape[0], int(steps), _fp(st),
+                                       _fp(best), _fp(x)))
+        return best, x
+
     # ---- profiling --------------------------------------------------------
     def profile(self, enable: bool):
         self._ck(self.lib.mnbab_profile(self.h, 1 if enable else 0))

@@ -591,6 +591,108 @@ static int sweep_wfloats(const NetDev& net, int t0) {
   return w;
 }
 
+// Adversarial pre-attack (Sec. 4): sign-step projected gradient descent on the
+// margin f_r(x) = (C f(x) + d)_r of one property row from one starting point;
+// one CTA per (row, start).  Per iterate: the forward pass (pre-activations kept
+// for the ReLU derivatives, ReLU'(0) = 1), the margin, best tracking (first
+// minimiser), the gradient by the backward pass, and x <- clip(x - alpha sign(g)).
+__global__ void __launch_bounds__(FT) k_attack_chain(NetDev net, const PropDev* props, int prop,
+                                                     const float* starts, int n_starts,
+                                                     int steps, float* best_out,
+                                                     float* bx_out, int maxw) {
+  extern __shared__ __align__(16) float fsm[];
+  __shared__ float red[32];
+  __shared__ int improved;
+  const int R = net.R, d0 = net.d[0];
+  int wtot = 0;
+  for (int t = 1; t <= R; ++t) {
+    const LayerDev& L = net.aff[t];
+    if (L.kind != MNBAB_CONV2D) continue;
+    f_stage(fsm + wtot, L.Wb, L.co, L.k * L.k * L.ci, f_wb_stride(L), FT);
+    f_stage(fsm + wtot + f_wb_floats(L), L.Wf, L.ci, L.k * L.k * L.co, f_wf_stride(L), FT);
+    wtot += f_conv_wfloats(L);
+  }
+  int SD = 0;
+  for (int t = 1; t <= R; ++t) SD += net.d[t];
+  const int d0p = (d0 + 3) & ~3;
+  float* B0 = fsm + wtot;
+  float* B1 = B0 + maxw;
+  float* Z = B1 + maxw;                  // pre-activations of every ReLU layer
+  float* X = Z + ((SD + 3) & ~3);        // current iterate
+  auto wsm = [&](int t) {
+    int o = 0;
+    for (int u = 1; u < t; ++u) o += f_conv_wfloats(net.aff[u]);
+    return fsm + o;
+  };
+  const int r = blockIdx.x / n_starts, sidx = blockIdx.x % n_starts;
+  const PropDev& P = props[prop];
+  const int dR = net.d[R];
+  const float* wf = P.Wf + (size_t)r * dR;
+  float* bx = bx_out + (size_t)blockIdx.x * d0;
+  for (int j = threadIdx.x; j < d0; j += FT)
+    X[j] = fminf(fmaxf(starts[(size_t)sidx * d0 + j], P.lo[j]), P.hi[j]);
+  float best = INFINITY;
+  for (int k = 0; k <= steps; ++k) {
+    // forward pass
+    __syncthreads();
+    const float* g = X;
+    for (int t = 1; t <= R; ++t) {
+      float* h = (t & 1) ? B0 : B1;
+      const LayerDev& L = net.aff[t];
+      if (L.kind == MNBAB_FC) f_fc_fwd(L, g, h);
+      else f_conv_fwd(L, g, h, wsm(t) + f_wb_floats(L));
+      __syncthreads();
+      const int off = net.off[t];
+      for (int j = threadIdx.x; j < net.d[t]; j += FT) {
+        const float z = h[j];
+        Z[off + j] = z;
+        h[j] = fmaxf(z, 0.f);
+      }
+      __syncthreads();
+      g = h;
+    }
+    float part = 0.f;
+    for (int j = threadIdx.x; j < dR; j += FT) part = fmaf(wf[j], g[j], part);
+    const float f = f_block_sum(part, red) + P.bf[r];
+    if (threadIdx.x == 0) improved = f < best;
+    __syncthreads();
+    if (improved) {
+      best = f;
+      for (int j = threadIdx.x; j < d0; j += FT) bx[j] = X[j];
+    }
+    if (k == steps) break;
+    // backward pass: d f / d x through the ReLU derivatives at the pre-activations
+    float* cur = (R & 1) ? B1 : B0;  // not the buffer holding g_R
+    __syncthreads();
+    for (int j = threadIdx.x; j < dR; j += FT) cur[j] = Z[net.off[R] + j] >= 0.f ? wf[j] : 0.f;
+    __syncthreads();
+    float* nxt = (cur == B0) ? B1 : B0;
+    for (int t = R; t >= 1; --t) {
+      const LayerDev& L = net.aff[t];
+      if (L.kind == MNBAB_FC) f_fc_back(L, cur, nxt);
+      else f_conv_back(L, cur, nxt, wsm(t));
+      __syncthreads();
+      if (t > 1) {
+        const int off = net.off[t - 1];
+        for (int j = threadIdx.x; j < net.d[t - 1]; j += FT)
+          nxt[j] = Z[off + j] >= 0.f ? nxt[j] : 0.f;
+        __syncthreads();
+      }
+      float* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
+    // sign step and projection onto the box
+    for (int j = threadIdx.x; j < d0; j += FT) {
+      const float gj = cur[j];
+      const float sg = gj > 0.f ? 1.f : (gj < 0.f ? -1.f : 0.f);
+      const float alpha = 2.5f * (P.hi[j] - P.lo[j]) / (2.0f * (float)steps);
+      X[j] = fminf(fmaxf(X[j] - alpha * sg, P.lo[j]), P.hi[j]);
+    }
+  }
+  if (threadIdx.x == 0) best_out[blockIdx.x] = best;
+}
+
 static int fused_maxw(const NetDev& net, int d0) {
   int maxw = d0;
   for (int t = 1; t <= net.R; ++t) maxw = std::max(maxw, net.d[t]);
@@ -659,6 +761,39 @@ void launch_sweep_chain(const NetDev& net, const PoolDev& pool, const PropDev* p
     per_sm = 1;
   const int grid = std::min(rows.M, sms * per_sm);
   k_sweep_chain<<<grid, FT, smem, st>>>(net, pool, props, rows, t0, lb, maxw);
+}
+
+int attack_smem_bytes(const NetDev& net) {
+  int w = 0, SD = 0;
+  for (int t = 1; t <= net.R; ++t) {
+    w += f_conv_wfloats(net.aff[t]);
+    SD += net.d[t];
+  }
+  return (w + 2 * fused_maxw(net, net.d[0]) + (SD + 3) / 4 * 4 + (net.d[0] + 3) / 4 * 4) *
+         (int)sizeof(float);
+}
+
+bool attack_supported(const NetDev& net) {
+  if (net.R < 1) return false;
+  for (int t = 1; t <= net.R + 1; ++t)
+    if (net.n_edge[t] != 1 || net.src1[t] != t - 1) return false;
+  for (int t = 1; t <= net.R; ++t) {
+    const LayerDev& L = net.aff[t];
+    if (L.kind != MNBAB_FC && L.kind != MNBAB_CONV2D) return false;
+    if (L.kind == MNBAB_CONV2D && (!L.Wb || !L.Wf)) return false;
+  }
+  return attack_smem_bytes(net) <= 200 * 1024;
+}
+
+void launch_attack_chain(const NetDev& net, const PropDev* props, int prop, int n_rows,
+                         const float* starts, int n_starts, int steps, float* best_out,
+                         float* bx_out, cudaStream_t st) {
+  if (n_rows <= 0 || n_starts <= 0) return;
+  const int smem = attack_smem_bytes(net);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_attack_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_attack_chain<<<n_rows * n_starts, FT, smem, st>>>(net, props, prop, starts, n_starts, steps,
+                                                      best_out, bx_out, fused_maxw(net, net.d[0]));
 }
 
 }  // namespace mnbab

@@ -171,6 +171,13 @@ void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropD
 bool sweep_chain_supported(const NetDev& net, int t0);
 void launch_sweep_chain(const NetDev& net, const PoolDev& pool, const PropDev* props,
                         const RowsDev& rows, int t0, float* lb, cudaStream_t st);
+// Adversarial pre-attack of property `prop` (chain networks): CTA b = r *
+// n_starts + s runs sign-step PGD on row r from start s; best_out[b] is its
+// smallest margin, bx_out [b][d0] the first minimiser.
+bool attack_supported(const NetDev& net);
+void launch_attack_chain(const NetDev& net, const PropDev* props, int prop, int n_rows,
+                         const float* starts, int n_starts, int steps, float* best_out,
+                         float* bx_out, cudaStream_t st);
 // Back-substitution through affine layer i: in [M][d_i] -> out [M][d_{i-1}].
 // Returns the number of partial-sum slots used.
 int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,

@@ -77,6 +77,8 @@ struct mnbab_net {
   int B = 0;          // batch capacity (objective rows)
   int pad_slot = -1;  // scratch node for padded graph rows
   std::vector<int> new_roots, new_root_props;  // root-bound slots awaiting initialisation
+  float* atk = nullptr;  // adversarial pre-attack scratch (grown on demand)
+  size_t atk_cap = 0;
   int chunk = 0;      // rows per back-substitution launch
   float *part = nullptr, *lb = nullptr;
   int *row_node = nullptr, *row_j = nullptr, *counter = nullptr;
@@ -2195,6 +2197,47 @@ mnbab_status mnbab_profile_read(mnbab_ctx* c, mnbab_kernel_stat* stats, int32_t 
   }
   if (n_out) *n_out = stats ? k : (int)NCAT;
   if (total_launches) *total_launches = c->launches;
+  API_END(c)
+}
+
+mnbab_status mnbab_attack(mnbab_ctx* c, const mnbab_prop* p, int32_t n_starts, int32_t steps,
+                          const float* starts, float* best_out, float* x_out) {
+  API_BEGIN(c)
+  if (!p || n_starts <= 0 || steps < 1 || !starts || !best_out)
+    fail(MNBAB_E_INVALID_ARG, "bad attack arguments");
+  mnbab_net* n = p->net;
+  if (!attack_supported(n->nd))
+    fail(MNBAB_E_UNSUPPORTED, "the attack runs on chain networks whose weights fit in shared memory");
+  const int nr = p->n_rows, d0 = n->d0, nb = nr * n_starts;
+  const size_t need = (size_t)n_starts * d0 + nb + (size_t)nb * d0;
+  if (n->atk_cap < need) {
+    n->atk = dalloc_t<float>(c, need);
+    n->atk_cap = need;
+  }
+  float* dst = n->atk;
+  float* dbest = dst + (size_t)n_starts * d0;
+  float* dbx = dbest + nb;
+  h2d(c, dst, starts, (size_t)n_starts * d0);
+  {
+    Scope sc(c, C_BOOK, 0.0, 4.0 * nb * d0);
+    launch_attack_chain(n->nd, c->d_props, p->index, nr, dst, n_starts, steps, dbest, dbx, c->st);
+  }
+  std::vector<float> hb(nb), hx;
+  d2h(c, hb.data(), dbest, nb);
+  if (x_out) {
+    hx.resize((size_t)nb * d0);
+    d2h(c, hx.data(), dbx, hx.size());
+  }
+  sync(c);
+  for (int r = 0; r < nr; ++r) {
+    int bs = 0;
+    for (int s = 1; s < n_starts; ++s)
+      if (hb[(size_t)r * n_starts + s] < hb[(size_t)r * n_starts + bs]) bs = s;  // first on ties
+    best_out[r] = hb[(size_t)r * n_starts + bs];
+    if (x_out)
+      std::memcpy(x_out + (size_t)r * d0, hx.data() + ((size_t)r * n_starts + bs) * d0,
+                  (size_t)d0 * sizeof(float));
+  }
   API_END(c)
 }
 

@@ -1,0 +1,106 @@
+"""GPU adversarial pre-attack (mnbab_attack) against the oracle (oracle/attack.py)."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import TOL, conv_case, resnet_spec
+from oracle import attack, core
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Context():
+    from paper_2205_00263_gb300 import Context as C
+    return C
+
+
+def _margin64(layers, C, d, r, x):
+    return float(C[r] @ synth.net_forward(layers, np.asarray(x, np.float64)) + d[r])
+
+
+def test_affine_region_reaches_the_closed_form_minimum(Context):
+    """Every ReLU active on the box: the margin is affine and the sign steps end at
+    the minimising corner, so the attack must return the exact minimum."""
+    layers = synth.tiny_fc_net(5, [5, 8, 6, 3])
+    layers[0]["b"] = (layers[0]["b"] + 50.0).astype(np.float32)
+    layers[2]["W"] = np.abs(layers[2]["W"]).astype(np.float32)
+    layers[2]["b"] = (layers[2]["b"] + 50.0).astype(np.float32)
+    C, d = synth.property_rows(0, 3)
+    lo, hi = np.full(5, -0.3, np.float32), np.full(5, 0.4, np.float32)
+    starts = (lo + (hi - lo) * np.random.default_rng(1).uniform(size=(2, 5))).astype(np.float32)
+    ref = attack.attack(layers, C, d, lo, hi, starts.astype(np.float64), steps=6)
+    with Context(node_capacity=64) as ctx:
+        net = ctx.load_network(layers)
+        p = ctx.set_property(net, lo, hi, C, d)
+        best, x = ctx.attack(p, starts, steps=6)
+    for r, (rb, _) in enumerate(ref):
+        assert abs(best[r] - rb) <= TOL * (1 + abs(rb)), (r, best[r], rb)
+        assert abs(_margin64(layers, C, d, r, x[r]) - rb) <= TOL * (1 + abs(rb))
+
+
+@pytest.mark.parametrize("case", ["fc", "conv"])
+def test_one_step_matches_oracle(Context, case):
+    """From identical starting points, one sign step gives the oracle's iterate and
+    margin wherever no gradient component is near zero (there FP32 and FP64 may
+    take different signs, so such samples are skipped)."""
+    if case == "fc":
+        layers = synth.tiny_fc_net(11, [12, 16, 9, 4])
+        x0 = np.random.default_rng(12).uniform(0.2, 0.8, 12).astype(np.float32)
+        y = synth.net_forward(layers, x0)
+        C, d = synth.property_rows(int(np.argmax(y)), 4)
+        lo, hi = synth.input_box(x0, 0.1)
+    else:
+        layers, C, d, lo, hi, _ = conv_case(6, 0.05)
+    net64 = core.fold_property(core.load_net(layers), C, d)
+    rng = np.random.default_rng(13)
+    checked = 0
+    with Context(node_capacity=64) as ctx:
+        net = ctx.load_network(layers)
+        p = ctx.set_property(net, lo, hi, C, d)
+        for _ in range(6):
+            s = (lo + (hi - lo) * rng.uniform(size=lo.size)).astype(np.float32)
+            best, x = ctx.attack(p, s[None, :], steps=1)
+            for r in range(C.shape[0]):
+                f0, g = attack.margin_and_grad(net64, s.astype(np.float64), r)
+                if np.abs(g).min() <= 1e-3 * np.abs(g).max():
+                    continue
+                rb, rx, _ = attack.pgd_row(net64, lo, hi, r, s[None, :].astype(np.float64), 1)
+                f1 = _margin64(layers, C, d, r, np.clip(s - attack.step_size(lo, hi, 1) * np.sign(g),
+                                                        lo, hi))
+                if abs(f1 - f0) <= 1e-3 * (1 + abs(f0)):
+                    continue  # argmin of two nearly equal margins
+                assert abs(best[r] - rb) <= TOL * (1 + abs(rb)), (r, best[r], rb)
+                assert np.allclose(x[r], rx, rtol=0, atol=1e-5)
+                checked += 1
+    assert checked >= 5
+
+
+def test_full_attack_on_the_conv_net_is_sound(Context):
+    """The 28x28 conv net, 5 starts x 50 steps: every minimiser lies in the box, its
+    FP64 margin is the reported one, and it is no worse than the starts; negative
+    margins are counterexamples."""
+    layers = synth.make_network(1)
+    pr = synth.make_properties(1, layers, n=1, eps=synth.load_eps(1))[0]
+    rng = np.random.default_rng(14)
+    starts = (pr.lo + (pr.hi - pr.lo) * rng.uniform(size=(5, pr.lo.size))).astype(np.float32)
+    with Context(node_capacity=64) as ctx:
+        net = ctx.load_network(layers)
+        p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+        best, x = ctx.attack(p, starts, steps=50)
+    for r in range(pr.C.shape[0]):
+        assert (x[r] >= pr.lo).all() and (x[r] <= pr.hi).all()
+        m = _margin64(layers, pr.C, pr.d, r, x[r])
+        assert abs(m - best[r]) <= TOL * (1 + abs(m))
+        f_starts = min(_margin64(layers, pr.C, pr.d, r, s) for s in starts)
+        assert best[r] <= f_starts + TOL * (1 + abs(f_starts))
+
+
+def test_residual_networks_are_refused(Context):
+    from paper_2205_00263_gb300 import MnbabError
+    layers, C, d, lo, hi, _ = conv_case(4, 0.02, resnet_spec)
+    with Context(node_capacity=64) as ctx:
+        net = ctx.load_network(layers)
+        p = ctx.set_property(net, lo, hi, C, d)
+        with pytest.raises(MnbabError):
+            ctx.attack(p, lo[None, :], steps=2)
