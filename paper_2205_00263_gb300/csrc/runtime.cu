@@ -214,7 +214,7 @@ void h2d_bytes(mnbab_ctx* c, void* dst, const void* src, size_t bytes) {
   c->h2d_bytes += (int64_t)bytes;
   if (!bytes) return;
   if (c->pin && bytes <= c->pin_cap / 4) {
-    if (c->pin_used + bytes > c->pin_cap) sync(c);  // every staged transfer has completed
+    if (c->pin_used + bytes > c->pin_cap - 64) sync(c);  // every staged transfer has completed
     unsigned char* stage = c->pin + c->pin_used;
     std::memcpy(stage, src, bytes);
     c->pin_used += (bytes + 15) & ~size_t(15);
@@ -281,13 +281,19 @@ void resolve_prof(mnbab_ctx* c) {
 }
 
 void sync(mnbab_ctx* c) {
+  // the tensor-core error flag rides on the same synchronisation (pinned copy)
+  int* flag = c->pin ? reinterpret_cast<int*>(c->pin + c->pin_cap - 64) : nullptr;
+  const bool check = c->d_err && c->gemm_path != 1;
+  if (check && flag)
+    ck(cudaMemcpyAsync(flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st), "error flag");
   ck(cudaStreamSynchronize(c->st), "stream synchronize");
   c->pin_used = 0;
   ck(cudaGetLastError(), "kernel launch");
   if (!c->pending.empty()) resolve_prof(c);
-  if (c->d_err && c->gemm_path != 1) {
+  if (check) {
     int e = 0;
-    ck(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+    if (flag) e = *flag;
+    else ck(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
     if (e) {
       cudaMemset(c->d_err, 0, sizeof(int));
       fail(MNBAB_E_TIMEOUT, "a tensor-core kernel timed out waiting for its MMAs");
