@@ -503,10 +503,119 @@ __global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, cons
   }
 }
 
+// Multi-row forms of the back-substitution helpers: RB rows in lockstep, row q's
+// coefficients at cur + q * ps; each staged weight and each index computation
+// serves all RB rows.
+template <int RB>
+__device__ void f_fc_back_rows(const LayerDev& L, const float* cur, float* nxt, int ps) {
+  const int din = L.d_in, dout = L.d_out;
+  const int items = din;
+  const int ks = f_split(items);
+  const int rounds = (items * ks + FT - 1) / FT;
+  for (int rr = 0; rr < rounds; ++rr) {
+    const int b = rr * FT + threadIdx.x;
+    const int it = b / ks, k0 = b % ks;
+    const bool act = it < items;
+    float acc[RB];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) acc[q] = 0.f;
+    if (act)
+      for (int j = k0; j < dout; j += ks) {
+        const float w = __ldg(L.W + (size_t)j * din + it);
+#pragma unroll
+        for (int q = 0; q < RB; ++q) acc[q] = fmaf(cur[q * ps + j], w, acc[q]);
+      }
+#pragma unroll
+    for (int q = 0; q < RB; ++q) acc[q] = f_group_sum(acc[q], ks);
+    if (act && k0 == 0)
+#pragma unroll
+      for (int q = 0; q < RB; ++q) nxt[q * ps + it] = acc[q];
+  }
+}
+
+template <int RB>
+__device__ void f_conv_back_rows(const LayerDev& L, const float* cur, float* nxt, int ps,
+                                 const float* Wb) {
+  const int CB = (L.ci & 3) == 0 ? 4 : 1;
+  const int ngr = L.ci / CB, P = L.hi * L.wi, hwo = L.ho * L.wo;
+  const int items = P * ngr;
+  const int ks = f_split(items);
+  const int rounds = (items * ks + FT - 1) / FT;
+  const size_t wco = (size_t)f_wb_stride(L);
+  for (int rr = 0; rr < rounds; ++rr) {
+    const int b = rr * FT + threadIdx.x;
+    const int it = b / ks, k0 = b % ks;
+    const bool act = it < items;
+    float acc[RB][4];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+    int grp = 0, ih = 0, iw = 0;
+    if (act) {
+      grp = it / P;
+      const int pos = it % P;
+      ih = pos / L.wi;
+      iw = pos % L.wi;
+      const int kh0 = (ih + L.p) % L.s, kw0 = (iw + L.p) % L.s;
+      const int oh0 = (ih + L.p - kh0) / L.s, ow0 = (iw + L.p - kw0) / L.s;
+      for (int kh = kh0, oh = oh0; kh < L.k && oh >= 0; kh += L.s, --oh) {
+        if (oh >= L.ho) continue;
+        for (int kw = kw0, ow = ow0; kw < L.k && ow >= 0; kw += L.s, --ow) {
+          if (ow >= L.wo) continue;
+          const float* ap = cur + oh * L.wo + ow;
+          const float* wp = Wb + (size_t)(kh * L.k + kw) * L.ci + grp * CB;
+          if (CB == 4) {
+            for (int co = k0; co < L.co; co += ks) {
+              const float4 w = *reinterpret_cast<const float4*>(wp + co * wco);
+#pragma unroll
+              for (int q = 0; q < RB; ++q) {
+                const float v = ap[q * ps + co * hwo];
+                acc[q][0] = fmaf(v, w.x, acc[q][0]);
+                acc[q][1] = fmaf(v, w.y, acc[q][1]);
+                acc[q][2] = fmaf(v, w.z, acc[q][2]);
+                acc[q][3] = fmaf(v, w.w, acc[q][3]);
+              }
+            }
+          } else {
+            for (int co = k0; co < L.co; co += ks) {
+              const float w = wp[co * wco];
+#pragma unroll
+              for (int q = 0; q < RB; ++q) acc[q][0] = fmaf(ap[q * ps + co * hwo], w, acc[q][0]);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      acc[q][0] = f_group_sum(acc[q][0], ks);
+      if (CB == 4) {
+        acc[q][1] = f_group_sum(acc[q][1], ks);
+        acc[q][2] = f_group_sum(acc[q][2], ks);
+        acc[q][3] = f_group_sum(acc[q][3], ks);
+      }
+    }
+    if (act && k0 == 0) {
+      const int o = grp * CB * P + ih * L.wi + iw;
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        nxt[q * ps + o] = acc[q][0];
+        if (CB == 4) {
+          nxt[q * ps + o + P] = acc[q][1];
+          nxt[q * ps + o + 2 * P] = acc[q][2];
+          nxt[q * ps + o + 3 * P] = acc[q][3];
+        }
+      }
+    }
+  }
+}
+
+constexpr int SWEEP_RB = 4;  // rows per CTA pass
+
 // Intermediate-bound rows (Sec. 3.2 re-bounding, DeepPoly slopes, beta = gamma =
 // 0) that start at a fully connected neuron of zhat_t, above a chain: each CTA
-// stages the transposed-conv weights once and carries rows to the input in
-// shared memory, one row at a time; row m's lower bound goes to lb[m].
+// stages the transposed-conv weights once and carries groups of RB rows to the
+// input in shared memory, in lockstep; row m's lower bound goes to lb[m].
+template <int RB>
 __global__ void __launch_bounds__(FT) k_sweep_chain(NetDev net, PoolDev pool,
                                                     const PropDev* props, RowsDev rows, int t0,
                                                     float* lb, int maxw) {
@@ -519,67 +628,91 @@ __global__ void __launch_bounds__(FT) k_sweep_chain(NetDev net, PoolDev pool,
     f_stage(fsm + wtot, L.Wb, L.co, L.k * L.k * L.ci, f_wb_stride(L), FT);
     wtot += f_wb_floats(L);
   }
+  const int ps = maxw;  // plane stride of a row's coefficients
   float* B0 = fsm + wtot;
-  float* B1 = B0 + maxw;
+  float* B1 = B0 + RB * ps;
   const int SD = pool.SD;
   const LayerDev& Lt = net.aff[t0];
-  for (int m = blockIdx.x; m < rows.M; m += gridDim.x) {
-    const int n = rows.node[m], j = rows.j[m];
-    const float sg = rows.sign ? rows.sign[m] : 1.f;
-    const size_t nb = (size_t)n * SD;
+  const int ngroups = (rows.M + RB - 1) / RB;
+  for (int gI = blockIdx.x; gI < ngroups; gI += gridDim.x) {
+    const int m0 = gI * RB;
+    int nq[RB], jq[RB];
+    float sq[RB];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const bool in = m0 + q < rows.M;
+      nq[q] = in ? rows.node[m0 + q] : rows.node[m0];
+      jq[q] = in ? rows.j[m0 + q] : 0;
+      sq[q] = in ? (rows.sign ? rows.sign[m0 + q] : 1.f) : 0.f;  // absent rows are zero
+    }
     const int dprev = Lt.d_in;
     __syncthreads();
     float* cur = B0;
     float* nxt = B1;
-    for (int k = threadIdx.x; k < dprev; k += FT) cur[k] = sg * __ldg(Lt.W + (size_t)j * dprev + k);
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+      for (int k = threadIdx.x; k < dprev; k += FT)
+        cur[q * ps + k] = sq[q] * __ldg(Lt.W + (size_t)jq[q] * dprev + k);
     __syncthreads();
-    float part = 0.f;
+    float part[RB];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) part[q] = 0.f;
     int wo = wtot;
     for (int t = t0 - 1; t >= 1; --t) {
       const int dt = net.d[t], off = net.off[t];
       const float* bias = net.bfull[t];
-      for (int k = threadIdx.x; k < dt; k += FT) {
-        const size_t q = nb + off + k;
-        const float l = pool.L[q], u = pool.U[q];
-        const int s = pool.S[q];
-        const float ap = cur[k];
-        float D, bl = 0.f;
-        if (s == -1) D = 1.f;
-        else if (s == 1) D = 0.f;
-        else if (l >= 0.f) D = 1.f;
-        else if (u <= 0.f) D = 0.f;
-        else if (ap >= 0.f) D = u >= -l ? 1.f : 0.f;
-        else {
-          const float den = u - l;
-          D = u / den;
-          bl = (-u * l) / den;
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const size_t nb = (size_t)nq[q] * SD;
+        for (int k = threadIdx.x; k < dt; k += FT) {
+          const size_t qq = nb + off + k;
+          const float l = pool.L[qq], u = pool.U[qq];
+          const int s = pool.S[qq];
+          const float ap = cur[q * ps + k];
+          float D, bl = 0.f;
+          if (s == -1) D = 1.f;
+          else if (s == 1) D = 0.f;
+          else if (l >= 0.f) D = 1.f;
+          else if (u <= 0.f) D = 0.f;
+          else if (ap >= 0.f) D = u >= -l ? 1.f : 0.f;
+          else {
+            const float den = u - l;
+            D = u / den;
+            bl = (-u * l) / den;
+          }
+          const float ah = ap * D;
+          part[q] += ap * bl + ah * bias[k];
+          cur[q * ps + k] = ah;
         }
-        const float ah = ap * D;
-        part += ap * bl + ah * bias[k];
-        cur[k] = ah;
       }
       __syncthreads();
       const LayerDev& L = net.aff[t];
       if (L.kind == MNBAB_FC) {
-        f_fc_back(L, cur, nxt);
+        f_fc_back_rows<RB>(L, cur, nxt, ps);
       } else {
         wo -= f_wb_floats(L);
-        f_conv_back(L, cur, nxt, fsm + wo);
+        f_conv_back_rows<RB>(L, cur, nxt, ps, fsm + wo);
       }
       __syncthreads();
       float* tmp = cur;
       cur = nxt;
       nxt = tmp;
     }
-    const PropDev& P = props[pool.prop[n]];
-    for (int k = threadIdx.x; k < pool.d0; k += FT) {
-      const float a = cur[k];
-      part += a * (a >= 0.f ? P.lo[k] : P.hi[k]);
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const PropDev& P = props[pool.prop[nq[q]]];
+      for (int k = threadIdx.x; k < pool.d0; k += FT) {
+        const float a = cur[q * ps + k];
+        part[q] += a * (a >= 0.f ? P.lo[k] : P.hi[k]);
+      }
     }
-    const float tot = f_block_sum(part, red);
-    if (threadIdx.x == 0) {
-      const float bj = net.bfull[t0] ? net.bfull[t0][j] : Lt.b[j];
-      lb[m] = tot + sg * bj;
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const float tot = f_block_sum(part[q], red);
+      if (threadIdx.x == 0 && m0 + q < rows.M) {
+        const float bj = net.bfull[t0] ? net.bfull[t0][jq[q]] : Lt.b[jq[q]];
+        lb[m0 + q] = tot + sq[q] * bj;
+      }
     }
   }
 }
@@ -740,7 +873,7 @@ bool sweep_chain_supported(const NetDev& net, int t0) {
   int maxw = net.d[0];
   for (int t = 1; t < t0; ++t) maxw = std::max(maxw, net.d[t]);
   maxw = (maxw + 3) / 4 * 4;
-  return (sweep_wfloats(net, t0) + 2 * maxw) * (int)sizeof(float) <= 100 * 1024;
+  return (sweep_wfloats(net, t0) + 2 * SWEEP_RB * maxw) * (int)sizeof(float) <= 200 * 1024;
 }
 
 void launch_sweep_chain(const NetDev& net, const PoolDev& pool, const PropDev* props,
@@ -749,18 +882,19 @@ void launch_sweep_chain(const NetDev& net, const PoolDev& pool, const PropDev* p
   int maxw = net.d[0];
   for (int t = 1; t < t0; ++t) maxw = std::max(maxw, net.d[t]);
   maxw = (maxw + 3) / 4 * 4;
-  const int smem = (sweep_wfloats(net, t0) + 2 * maxw) * (int)sizeof(float);
+  const int smem = (sweep_wfloats(net, t0) + 2 * SWEEP_RB * maxw) * (int)sizeof(float);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_sweep_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_sweep_chain<SWEEP_RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
   static int sms = 0;
   if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
     sms = 152;
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_chain, FT, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_chain<SWEEP_RB>, FT, smem) !=
           cudaSuccess || per_sm < 1)
     per_sm = 1;
-  const int grid = std::min(rows.M, sms * per_sm);
-  k_sweep_chain<<<grid, FT, smem, st>>>(net, pool, props, rows, t0, lb, maxw);
+  const int grid = std::min((rows.M + SWEEP_RB - 1) / SWEEP_RB, sms * per_sm);
+  k_sweep_chain<SWEEP_RB><<<grid, FT, smem, st>>>(net, pool, props, rows, t0, lb, maxw);
 }
 
 int attack_smem_bytes(const NetDev& net) {
