@@ -308,9 +308,130 @@ __global__ void k_win_rows(NetDev net, WinPlan wp, RowsDev rows, Epi e) {
   if (threadIdx.x == 0) e.part[(size_t)m * e.nslot + e.slot_base] = tot + c0;
 }
 
+// The same windowed rows, RB rows per CTA in lockstep (small windows): every
+// phase covers the RB rows' windows, so each barrier and index computation
+// serves RB rows; row q keeps its own window origin, node and partial sum.
+template <int RB>
+__global__ void k_win_rows_rb(NetDev net, WinPlan wp, RowsDev rows, Epi e) {
+  extern __shared__ __align__(16) float wsm[];
+  const int t = wp.t;
+  const LayerDev& Lt = net.aff[t];
+  const int m0 = blockIdx.x * RB;
+  float* A = wsm;                   // RB planes of wp.maxw
+  float* B = wsm + RB * wp.maxw;
+  int y0[RB], x0[RB], mq[RB];
+  float part[RB], c0[RB];
+  const int hwt = Lt.ho * Lt.wo;
+  const int n0 = Lt.ci * Lt.k * Lt.k;
+#pragma unroll
+  for (int q = 0; q < RB; ++q) {
+    const bool in = m0 + q < rows.M;
+    mq[q] = in ? m0 + q : m0;  // absent rows repeat the first (results dropped)
+    const int j = rows.j[mq[q]];
+    const float sg = rows.sign ? rows.sign[mq[q]] : 1.f;
+    const int co = j / hwt, oh = (j % hwt) / Lt.wo, ow = j % Lt.wo;
+    y0[q] = oh * Lt.s - Lt.p;
+    x0[q] = ow * Lt.s - Lt.p;
+    c0[q] = sg * (net.bfull[t] ? net.bfull[t][j] : Lt.b[co]);
+    part[q] = 0.f;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x)
+      A[q * wp.maxw + i] = sg * __ldg(Lt.W + (size_t)co * n0 + i);
+  }
+  int h = Lt.k, w = Lt.k;
+  for (int i = t - 1; i >= 0; --i) {
+    const LayerDev& Ln = net.aff[i + 1];
+    const int C = Ln.ci, H = Ln.hi, W = Ln.wi, hw = h * w;
+    __syncthreads();
+    if (i == 0) {
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const PropDev& P = e.props[e.pool.prop[rows.node[mq[q]]]];
+        for (int r0 = threadIdx.x; r0 < C * hw; r0 += blockDim.x) {
+          const int c = r0 / hw, r = r0 % hw, y = y0[q] + r / w, x = x0[q] + r % w;
+          if (y < 0 || y >= H || x < 0 || x >= W) continue;
+          const int jx = (c * H + y) * W + x;
+          const float a = A[q * wp.maxw + r0];
+          part[q] += a * (a >= 0.f ? P.lo[jx] : P.hi[jx]);
+        }
+      }
+      break;
+    }
+    Epi el = e;
+    el.kind = EPI_RELU;
+    el.off = net.off[i];
+    el.bias = net.bfull[i];
+    el.bias_div = 1;
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+      for (int r0 = threadIdx.x; r0 < C * hw; r0 += blockDim.x) {
+        const int c = r0 / hw, r = r0 % hw, y = y0[q] + r / w, x = x0[q] + r % w;
+        float* a = A + q * wp.maxw + r0;
+        if (y < 0 || y >= H || x < 0 || x >= W) {
+          *a = 0.f;
+          continue;
+        }
+        *a = epi_relu(el, mq[q], (c * H + y) * W + x, *a, part[q]);
+      }
+    __syncthreads();
+    const LayerDev& Li = net.aff[i];
+    const int s = Li.s, k = Li.k, kk = k * k;
+    const int h2 = (h - 1) * s + k, w2 = (w - 1) * s + k, hw2 = h2 * w2;
+    const size_t wco = (size_t)Li.ci * kk;
+    for (int r0 = threadIdx.x; r0 < Li.ci * hw2; r0 += blockDim.x) {
+      const int c = r0 / hw2, r = r0 % hw2, yy = r / w2, xx = r % w2;
+      float acc[RB];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) acc[q] = 0.f;
+      for (int kh = yy % s; kh < k && kh <= yy; kh += s) {
+        const int Y = (yy - kh) / s;
+        if (Y >= h) continue;
+        for (int kw = xx % s; kw < k && kw <= xx; kw += s) {
+          const int X = (xx - kw) / s;
+          if (X >= w) continue;
+          const float* ap = A + Y * w + X;
+          const float* wp2 = Li.W + (size_t)c * kk + kh * k + kw;
+          for (int o = 0; o < Li.co; ++o) {
+            const float wv = __ldg(wp2 + o * wco);
+#pragma unroll
+            for (int q = 0; q < RB; ++q) acc[q] = fmaf(ap[q * wp.maxw + o * hw], wv, acc[q]);
+          }
+        }
+      }
+      // positions outside the layer (padding) carry no coefficient
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const int ya = y0[q] * s - Li.p + yy, xa = x0[q] * s - Li.p + xx;
+        B[q * wp.maxw + r0] = (ya >= 0 && ya < Li.hi && xa >= 0 && xa < Li.wi) ? acc[q] : 0.f;
+      }
+    }
+    float* tmp = A;
+    A = B;
+    B = tmp;
+    h = h2;
+    w = w2;
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      y0[q] = y0[q] * s - Li.p;
+      x0[q] = x0[q] * s - Li.p;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RB; ++q) {
+    const float tot = block_sum(part[q]);
+    if (threadIdx.x == 0 && m0 + q < rows.M)
+      e.part[(size_t)(m0 + q) * e.nslot + e.slot_base] = tot + c0[q];
+  }
+}
+
 void launch_win_rows(const NetDev& net, const WinPlan& wp, const RowsDev& rows, const Epi& e,
                      cudaStream_t st) {
   if (rows.M <= 0) return;
+  if (wp.maxw <= 1024) {
+    constexpr int RB = 4;
+    const int smem = 2 * RB * wp.maxw * (int)sizeof(float);
+    k_win_rows_rb<RB><<<(rows.M + RB - 1) / RB, 128, smem, st>>>(net, wp, rows, e);
+    return;
+  }
   const int threads = wp.maxw >= 1024 ? 256 : 128;
   const int smem = 2 * wp.maxw * (int)sizeof(float);
   set_smem(k_win_rows, smem);
