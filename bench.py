@@ -7,8 +7,9 @@ seeded blurred-uniform images with the calibrated L-inf radius, margins
 y_t - y_j as rows, 256-node budget per property, up to 512 subproblems per
 BaB step, 20 projected-Adam steps per node with the adjoint kernels.  A
 rolling window of 100 active properties keeps the queue full: a finished
-property is replaced by the next seeded one (its root bounding runs inside the
-step that admits it).
+property is replaced by the next seeded one.  All properties are uploaded to
+HBM before timing; a new property's root bounding runs inside the step that
+admits it.
 
 One step = one mnbab_bab_step (re-bounding after splits, DeepPoly pass,
 optimisation, counterexample check, ACS, queue step) over one batch.  Steps
@@ -222,30 +223,36 @@ def kernels_sha():
 
 # ----------------------------------------------------------------------------
 class Window:
-    """Rolling window of active properties (admission inside the steps)."""
+    """Rolling window of active properties.
+
+    Every property of the pool is drawn and uploaded to HBM before any timing
+    starts; admission inside the steps only hands the next uploaded property to
+    bab_step, which starts it (root nodes, root bounds) in its own launches.
+    """
 
     def __init__(self, ctx, net, layers, eps, start, n_active, pool_size=None):
         self.ctx, self.net, self.layers, self.eps = ctx, net, layers, eps
         self.next = 0
-        # host-side inputs are drawn before any timing starts
-        self.pool = synth.make_properties(CFG, layers, n=pool_size or 4 * n_active, eps=eps,
-                                          start=start)
-        self.active = []
-        self.verdicts = {1: 0, -1: 0, 0: 0}
+        pool = synth.make_properties(CFG, layers, n=pool_size or 4 * n_active, eps=eps,
+                                     start=start)
         self.h2d = 0
         self.d2h = 0
+        self.pool = []
+        for pr in pool:
+            p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+            ctx.set_budget(p, BUDGET)
+            self.h2d += pr.lo.nbytes + pr.hi.nbytes + pr.C.nbytes + pr.d.nbytes
+            self.pool.append(p)
+        self.active = []
+        self.verdicts = {1: 0, -1: 0, 0: 0}
         for _ in range(n_active):
             self.admit()
 
     def admit(self):
         if self.next >= len(self.pool):
             raise RuntimeError("property pool exhausted; raise pool_size")
-        pr = self.pool[self.next]
+        self.active.append(self.pool[self.next])
         self.next += 1
-        p = self.ctx.set_property(self.net, pr.lo, pr.hi, pr.C, pr.d)
-        self.ctx.set_budget(p, BUDGET)
-        self.h2d += pr.lo.nbytes + pr.hi.nbytes + pr.C.nbytes + pr.d.nbytes
-        self.active.append(p)
 
     def step(self):
         st = self.ctx.bab_step(self.active, max_nodes=BATCH, steps=ADAM_STEPS)
@@ -365,15 +372,12 @@ def run_ours(args):
         for k in range(args.e2e_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            w3 = Window.__new__(Window)
-            w3.ctx, w3.net, w3.layers, w3.eps = ctx, net, layers, eps
-            w3.pool, w3.next, w3.active, w3.h2d, w3.d2h = pools[k], 0, [], 0, 0
-            w3.verdicts = {1: 0, -1: 0, 0: 0}
-            for _ in range(16):
-                w3.admit()
-            for p in w3.active:
+            props = []
+            for pr in pools[k]:
+                p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
                 ctx.set_budget(p, 32)
-            props = list(w3.active)
+                eh += pr.lo.nbytes + pr.hi.nbytes + pr.C.nbytes + pr.d.nbytes
+                props.append(p)
             while True:
                 st = ctx.bab_step(props, max_nodes=BATCH, steps=ADAM_STEPS)
                 en += st["nodes_bounded"]
@@ -386,7 +390,6 @@ def run_ours(args):
                 ed += 4 + 4 * p.net.d0
             torch.cuda.synchronize()
             et += time.perf_counter() - t0
-            eh += w3.h2d
         e2e = {"value": en / et, "unit": "nodes/s",
                "h2d_bytes_per_step": eh // args.e2e_steps, "d2h_bytes_per_step": ed // args.e2e_steps,
                "step": "16 fresh properties from host arrays (32-node budget each) to verdicts"}
@@ -415,6 +418,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded He-normal net, blurred-uniform images; no dataset)",
             "config": {"workload": WORKLOAD, "l2": "flushed (256 MiB write) between timed steps",
+                       "inputs": "every property uploaded to HBM before the timed region",
                        "parallelism": f"replicas x{world} (independent properties per rank)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches1 - launches0), "clocks": clk,

@@ -244,8 +244,12 @@ mnbab_status mnbab_score_branches(mnbab_ctx* ctx, const mnbab_node_id* nodes, in
  * max_nodes open nodes in FIFO order from their queues (within each
  * property's node budget), re-bounds, runs the DeepPoly pass, optimises the
  * nodes it does not verify, checks the minimiser for a counterexample,
- * branches the rest by ACS and queues their two children.  cfg may be NULL
- * (20 steps, default rates).  max_nodes is clamped to the context's batch
+ * branches the rest by ACS and queues their two children.  This call starts
+ * (creates and bounds the root nodes of) only the properties passed to it;
+ * calls that read roots (get_root_bounds, node_root, bound_batch ...) start
+ * every property set on the network.  A caller can so upload many properties
+ * ahead of time and step a window of them.  cfg may be
+ * NULL (20 steps, default rates).  max_nodes is clamped to the context's batch
  * capacity. */
 mnbab_status mnbab_bab_step(mnbab_ctx* ctx, mnbab_prop* const* props, int32_t n_props,
                             int32_t max_nodes, const mnbab_adam* cfg, mnbab_step_stats* out);

@@ -1081,10 +1081,17 @@ void materialize(mnbab_net* n, mnbab_prop* p) {
   p->materialized = true;
 }
 
-void ensure_roots(mnbab_net* n) {
+// Starts the given properties (all admitted properties of the network when
+// `only` is null) and bounds every root still pending, in shared launches.
+void ensure_roots(mnbab_net* n, mnbab_prop* const* only = nullptr, int n_only = 0) {
   mnbab_ctx* c = n->ctx;
-  for (auto* p : c->props)
-    if (p->net == n && p->admitted && !p->materialized) materialize(n, p);
+  if (only) {
+    for (int i = 0; i < n_only; ++i)
+      if (only[i]->admitted && !only[i]->materialized) materialize(n, only[i]);
+  } else {
+    for (auto* p : c->props)
+      if (p->net == n && p->admitted && !p->materialized) materialize(n, p);
+  }
   for (size_t b0 = 0; b0 < n->new_roots.size(); b0 += 2 * (size_t)n->B) {
     const int nb = (int)std::min(n->new_roots.size() - b0, 2 * (size_t)n->B);
     h2d(c, n->ri_dst, n->new_roots.data() + b0, nb);
@@ -1147,7 +1154,7 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
     if (props[i]->net != n) fail(MNBAB_E_INVALID_ARG, "properties of different networks");
   max_nodes = std::max(1, std::min(max_nodes, n->B));
   HostTimer ht(c);
-  ensure_roots(n);
+  ensure_roots(n, props, n_props);
   ht.lap(H_ROOTS);
   // pop FIFO
   std::vector<Picked> picked;
