@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-nodes", type=int, default=48)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=2,
+                    help="cold solves of the e2e arm (0 skips the e2e arm)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--node-capacity", type=int, default=65536,
@@ -225,33 +226,39 @@ def kernels_sha():
 class Window:
     """Rolling window of active properties.
 
-    Every property of the pool is drawn and uploaded to HBM before any timing
-    starts; admission inside the steps only hands the next uploaded property to
-    bab_step, which starts it (root nodes, root bounds) in its own launches.
+    With preload (the device-timed arm) every property of the pool is drawn and
+    uploaded to HBM before any timing starts; admission inside the steps only
+    hands the next uploaded property to bab_step, which starts it (root nodes,
+    root bounds) in its own launches.  Without preload (the end-to-end arm)
+    admission uploads the property from its host arrays inside the step, and a
+    finished property's verdict and counterexample are read back.
     """
 
-    def __init__(self, ctx, net, layers, eps, start, n_active, pool_size=None):
+    def __init__(self, ctx, net, layers, eps, start, n_active, pool_size=None, preload=True):
         self.ctx, self.net, self.layers, self.eps = ctx, net, layers, eps
         self.next = 0
+        self.preload = preload
         pool = synth.make_properties(CFG, layers, n=pool_size or 4 * n_active, eps=eps,
                                      start=start)
         self.h2d = 0
         self.d2h = 0
-        self.pool = []
-        for pr in pool:
-            p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
-            ctx.set_budget(p, BUDGET)
-            self.h2d += pr.lo.nbytes + pr.hi.nbytes + pr.C.nbytes + pr.d.nbytes
-            self.pool.append(p)
+        self.pool = [self._upload(pr) for pr in pool] if preload else pool
         self.active = []
         self.verdicts = {1: 0, -1: 0, 0: 0}
         for _ in range(n_active):
             self.admit()
 
+    def _upload(self, pr):
+        p = self.ctx.set_property(self.net, pr.lo, pr.hi, pr.C, pr.d)
+        self.ctx.set_budget(p, BUDGET)
+        self.h2d += pr.lo.nbytes + pr.hi.nbytes + pr.C.nbytes + pr.d.nbytes
+        return p
+
     def admit(self):
         if self.next >= len(self.pool):
             raise RuntimeError("property pool exhausted; raise pool_size")
-        self.active.append(self.pool[self.next])
+        pr = self.pool[self.next]
+        self.active.append(pr if self.preload else self._upload(pr))
         self.next += 1
 
     def step(self):
@@ -260,7 +267,7 @@ class Window:
         for p in self.active:
             if self.ctx.queue_size(p) == 0:
                 v, _, _ = self.ctx.verdict(p)
-                self.d2h += 4
+                self.d2h += 8 + 4 * self.net.d0  # verdict, bound, minimiser
                 self.verdicts[v] += 1
             else:
                 keep.append(p)
@@ -363,37 +370,61 @@ def run_ours(args):
         plain = {"value": pn / (pms * 1e-3), "unit": "nodes/s", "nodes": pn,
                  "form": "one subproblem per launch (max_nodes=1), same kernels, no graph"}
 
-    # e2e: public API from host arrays to verdicts, copies inside the timed region
+    # e2e: the same rolling-window workload through the public API, every step
+    # uploading its newly admitted properties from host arrays and reading the
+    # finished properties' verdicts back, timed on the host clock
     e2e = None
     if args.e2e_steps > 0:
-        en, et, eh, ed = 0, 0.0, 0, 0
-        pools = [synth.make_properties(CFG, layers, n=16, eps=eps, start=start + 700_000 + 1000 * k)
+        # a context of its own: the device-timed window still holds its nodes
+        ectx = Context(device=local, stream=stream.cuda_stream, node_capacity=args.node_capacity)
+        enet = ectx.load_network(layers)
+        win3 = Window(ectx, enet, layers, eps, start + 700_000, args.window,
+                      pool_size=args.window + 60 * (args.steps + args.warmup + 1) + 50,
+                      preload=False)
+        for _ in range(args.warmup):
+            win3.step()
+        torch.cuda.synchronize()
+        h0, d0_ = win3.h2d, win3.d2h
+        en, et = 0, 0.0
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = win3.step()
+            torch.cuda.synchronize()
+            et += time.perf_counter() - t0
+            en += st["nodes_bounded"]
+        et_ms, en = reduce_timing(et * 1e3, en, device="cuda")
+        e2e = {"value": en / (et_ms * 1e-3), "unit": "nodes/s",
+               "h2d_bytes_per_step": (win3.h2d - h0) // args.steps,
+               "d2h_bytes_per_step": (win3.d2h - d0_) // args.steps,
+               "step": "one mnbab_bab_step over the 100-property rolling window; newly admitted "
+                       "properties uploaded from host arrays and finished verdicts read back "
+                       "inside the timed step (host clock)"}
+        # cold solves: fresh properties from host arrays to verdicts
+        cn, ct = 0, 0.0
+        pools = [synth.make_properties(CFG, layers, n=16, eps=eps, start=start + 800_000 + 1000 * k)
                  for k in range(args.e2e_steps)]
         for k in range(args.e2e_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             props = []
             for pr in pools[k]:
-                p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
-                ctx.set_budget(p, 32)
-                eh += pr.lo.nbytes + pr.hi.nbytes + pr.C.nbytes + pr.d.nbytes
+                p = ectx.set_property(enet, pr.lo, pr.hi, pr.C, pr.d)
+                ectx.set_budget(p, 32)
                 props.append(p)
             while True:
-                st = ctx.bab_step(props, max_nodes=BATCH, steps=ADAM_STEPS)
-                en += st["nodes_bounded"]
-                eh += st["h2d_bytes"]
-                ed += st["d2h_bytes"]
-                if st["nodes_bounded"] == 0:
+                nb = ectx.bab_step(props, max_nodes=BATCH, steps=ADAM_STEPS)["nodes_bounded"]
+                cn += nb
+                if nb == 0:
                     break
             for p in props:
-                ctx.verdict(p)
-                ed += 4 + 4 * p.net.d0
+                ectx.verdict(p)
             torch.cuda.synchronize()
-            et += time.perf_counter() - t0
-        e2e = {"value": en / et, "unit": "nodes/s",
-               "h2d_bytes_per_step": eh // args.e2e_steps, "d2h_bytes_per_step": ed // args.e2e_steps,
-               "step": "16 fresh properties from host arrays (32-node budget each) to verdicts"}
-
+            ct += time.perf_counter() - t0
+        e2e["cold_solve"] = {"value": cn / ct, "unit": "nodes/s", "solves": args.e2e_steps,
+                             "solve": "16 fresh properties from host arrays (32-node budget "
+                                      "each) to verdicts"}
+        ectx.close()
     serving = None
     if world == 1 and (args.serve_requests is None or args.serve_requests > 0):
         sctx = Context(device=local, stream=stream.cuda_stream, node_capacity=SERVE_CAPACITY,

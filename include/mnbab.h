@@ -163,10 +163,12 @@ mnbab_status mnbab_load_network(mnbab_ctx* ctx, const mnbab_layer_desc* layers, 
 
 /* Sets a property: input box x_lo <= x <= x_hi (d0 floats each, the clipped
  * L-inf ball of Sec. 2.1) and rows C f(x) + d > 0 (C [n_rows][n_out]
- * row-major, d [n_rows]).  Folds C into the last layer, computes the DeepPoly
- * intermediate bounds of every ReLU layer on the device (Sec. 3.1, one
- * back-substitution per neuron and side), and queues one root node per row.
- * *out stays valid until mnbab_destroy. */
+ * row-major, d [n_rows]).  Folds C into the last layer and uploads the box
+ * and the folded layer.  When the property starts (its first mnbab_bab_step,
+ * or the first call that reads roots), the DeepPoly intermediate bounds of
+ * every ReLU layer are computed on the device (Sec. 3.1, one
+ * back-substitution per neuron and side) and one root node per row is
+ * queued.  *out stays valid until mnbab_destroy. */
 mnbab_status mnbab_set_property(mnbab_ctx* ctx, const mnbab_net* net, const float* x_lo,
                                 const float* x_hi, const float* C, const float* d,
                                 int32_t n_rows, mnbab_prop** out);
