@@ -130,42 +130,62 @@ __device__ void f_fc_back(const LayerDev& L, const float* cur, float* nxt) {
   }
 }
 
-// Forward through FC layer L: g (d_in) -> h (d_out) = W g + b; one warp per output.
+// Forward through FC layer L: g (d_in) -> h (d_out) = W g + b; one warp per
+// pair of outputs (each load of g serves both rows).
 __device__ void f_fc_fwd(const LayerDev& L, const float* g, float* h) {
   const int din = L.d_in, dout = L.d_out;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool vec = (din & 3) == 0 && (reinterpret_cast<uintptr_t>(L.W) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(g) & 15) == 0;
-  for (int i = warp; i < dout; i += FT / 32) {
-    float acc = 0.f;
+  for (int i = 2 * warp; i < dout; i += FT / 16) {
+    const bool two = i + 1 < dout;
+    const int i1 = two ? i + 1 : i;
+    float acc0 = 0.f, acc1 = 0.f;
     if (vec) {
-      const float4* w4 = reinterpret_cast<const float4*>(L.W + (size_t)i * din);
+      const float4* w0 = reinterpret_cast<const float4*>(L.W + (size_t)i * din);
+      const float4* w1 = reinterpret_cast<const float4*>(L.W + (size_t)i1 * din);
       const float4* g4 = reinterpret_cast<const float4*>(g);
       const int n4 = din >> 2;
-      for (int c0 = lane; c0 < n4; c0 += 32 * 4) {
-        float4 w[4];
+      for (int c0 = lane; c0 < n4; c0 += 32 * 2) {
+        float4 a[2], b[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
           const int c = c0 + 32 * u;
-          w[u] = c < n4 ? __ldg(w4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          const bool in = c < n4;
+          a[u] = in ? __ldg(w0 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          b[u] = in ? __ldg(w1 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
           const int c = c0 + 32 * u;
           if (c < n4) {
             const float4 x = g4[c];
-            acc = fmaf(w[u].x, x.x, acc);
-            acc = fmaf(w[u].y, x.y, acc);
-            acc = fmaf(w[u].z, x.z, acc);
-            acc = fmaf(w[u].w, x.w, acc);
+            acc0 = fmaf(a[u].x, x.x, acc0);
+            acc0 = fmaf(a[u].y, x.y, acc0);
+            acc0 = fmaf(a[u].z, x.z, acc0);
+            acc0 = fmaf(a[u].w, x.w, acc0);
+            acc1 = fmaf(b[u].x, x.x, acc1);
+            acc1 = fmaf(b[u].y, x.y, acc1);
+            acc1 = fmaf(b[u].z, x.z, acc1);
+            acc1 = fmaf(b[u].w, x.w, acc1);
           }
         }
       }
     } else {
-      for (int j = lane; j < din; j += 32) acc = fmaf(__ldg(L.W + (size_t)i * din + j), g[j], acc);
+      for (int j = lane; j < din; j += 32) {
+        const float x = g[j];
+        acc0 = fmaf(__ldg(L.W + (size_t)i * din + j), x, acc0);
+        acc1 = fmaf(__ldg(L.W + (size_t)i1 * din + j), x, acc1);
+      }
     }
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) h[i] = acc + L.b[i];
+    for (int o = 16; o; o >>= 1) {
+      acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+      acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+    }
+    if (lane == 0) {
+      h[i] = acc0 + L.b[i];
+      if (two) h[i + 1] = acc1 + L.b[i + 1];
+    }
   }
 }
 
@@ -201,54 +221,83 @@ __device__ inline void f_stage(float* dst, const float* src, int rows, int w, in
 
 // Transposed convolution (back-substitution) through conv layer L with its
 // weights in shared memory as Wb [co][kh][kw][ci]: cur [co][ho][wo] -> nxt
-// [ci][hi][wi].  A thread group takes one input position and CB channels; the
-// valid taps of a position are those with kh = (ih + p) mod s (+ s, ...).
+// [ci][hi][wi].  A thread group takes CB channels at two input positions of
+// one row, s columns apart: both have the taps kh = (ih + p) mod s (+ s, ...),
+// kw = (iw + p) mod s (+ s, ...), the second at ow + 1, so every staged
+// weight load serves both positions.
 __device__ void f_conv_back(const LayerDev& L, const float* cur, float* nxt, const float* Wb) {
   const int CB = (L.ci & 3) == 0 ? 4 : 1;
-  const int ngr = L.ci / CB, P = L.hi * L.wi, hwo = L.ho * L.wo;
-  const int items = P * ngr;
+  const int S = L.s;
+  const int W2 = (L.wi + 2 * S - 1) / (2 * S) * S;  // first positions per row (a few past the edge)
+  const int ngr = L.ci / CB, P = L.hi * L.wi, hwo = L.ho * L.wo, PP = L.hi * W2;
+  const int items = PP * ngr;
   const int ks = f_split(items);
   const int rounds = (items * ks + FT - 1) / FT;
   const size_t wco = (size_t)f_wb_stride(L);
   for (int rr = 0; rr < rounds; ++rr) {
     const int b = rr * FT + threadIdx.x;
     const int it = b / ks, k0 = b % ks;
-    const bool act = it < items;
+    bool act = it < items;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
     int grp = 0, ih = 0, iw = 0;
+    bool two = false;
     if (act) {
-      grp = it / P;
-      const int pos = it % P;
-      ih = pos / L.wi;
-      iw = pos % L.wi;
-      const int kh0 = (ih + L.p) % L.s, kw0 = (iw + L.p) % L.s;
-      const int oh0 = (ih + L.p - kh0) / L.s, ow0 = (iw + L.p - kw0) / L.s;
-      for (int kh = kh0, oh = oh0; kh < L.k && oh >= 0; kh += L.s, --oh) {
+      grp = it / PP;
+      const int q = it % PP;
+      ih = q / W2;
+      const int qw = q % W2;
+      iw = (qw / S) * 2 * S + qw % S;
+      act = iw < L.wi;
+      two = iw + S < L.wi;
+    }
+    if (act) {
+      const int kh0 = (ih + L.p) % S, kw0 = (iw + L.p) % S;
+      const int oh0 = (ih + L.p - kh0) / S, ow0 = (iw + L.p - kw0) / S;
+      for (int kh = kh0, oh = oh0; kh < L.k && oh >= 0; kh += S, --oh) {
         if (oh >= L.ho) continue;
-        for (int kw = kw0, ow = ow0; kw < L.k && ow >= 0; kw += L.s, --ow) {
-          if (ow >= L.wo) continue;
+        // the second position's ow is ow + 1, valid down to ow = -1
+        for (int kw = kw0, ow = ow0; kw < L.k && ow >= -1; kw += S, --ow) {
+          const bool ok0 = ow >= 0 && ow < L.wo;
+          const bool ok1 = two && ow + 1 < L.wo;
+          if (!ok0 && !ok1) continue;
           const float* ap = cur + oh * L.wo + ow;
           const float* wp = Wb + (size_t)(kh * L.k + kw) * L.ci + grp * CB;
           if (CB == 4) {
+#pragma unroll 2
             for (int co = k0; co < L.co; co += ks) {
-              const float v = ap[co * hwo];
+              const float v0 = ok0 ? ap[co * hwo] : 0.f;
+              const float v1 = ok1 ? ap[co * hwo + 1] : 0.f;
               const float4 w = *reinterpret_cast<const float4*>(wp + co * wco);
-              a0 = fmaf(v, w.x, a0);
-              a1 = fmaf(v, w.y, a1);
-              a2 = fmaf(v, w.z, a2);
-              a3 = fmaf(v, w.w, a3);
+              a0 = fmaf(v0, w.x, a0);
+              a1 = fmaf(v0, w.y, a1);
+              a2 = fmaf(v0, w.z, a2);
+              a3 = fmaf(v0, w.w, a3);
+              c0 = fmaf(v1, w.x, c0);
+              c1 = fmaf(v1, w.y, c1);
+              c2 = fmaf(v1, w.z, c2);
+              c3 = fmaf(v1, w.w, c3);
             }
           } else {
-            for (int co = k0; co < L.co; co += ks) a0 = fmaf(ap[co * hwo], wp[co * wco], a0);
+#pragma unroll 2
+            for (int co = k0; co < L.co; co += ks) {
+              const float w = wp[co * wco];
+              a0 = fmaf(ok0 ? ap[co * hwo] : 0.f, w, a0);
+              c0 = fmaf(ok1 ? ap[co * hwo + 1] : 0.f, w, c0);
+            }
           }
         }
       }
     }
     a0 = f_group_sum(a0, ks);
+    c0 = f_group_sum(c0, ks);
     if (CB == 4) {
       a1 = f_group_sum(a1, ks);
       a2 = f_group_sum(a2, ks);
       a3 = f_group_sum(a3, ks);
+      c1 = f_group_sum(c1, ks);
+      c2 = f_group_sum(c2, ks);
+      c3 = f_group_sum(c3, ks);
     }
     if (act && k0 == 0) {
       const int o = grp * CB * P + ih * L.wi + iw;
@@ -257,6 +306,14 @@ __device__ void f_conv_back(const LayerDev& L, const float* cur, float* nxt, con
         nxt[o + P] = a1;
         nxt[o + 2 * P] = a2;
         nxt[o + 3 * P] = a3;
+      }
+      if (two) {
+        nxt[o + S] = c0;
+        if (CB == 4) {
+          nxt[o + S + P] = c1;
+          nxt[o + S + 2 * P] = c2;
+          nxt[o + S + 3 * P] = c3;
+        }
       }
     }
   }
@@ -287,6 +344,7 @@ __device__ void f_conv_fwd(const LayerDev& L, const float* g, float* h, const fl
         const float* gp = g + ci * hwi;
         const float* wc = Wf + (size_t)ci * f_wf_stride(L) + grp * CB;
         for (int kh = kh_lo; kh < kh_hi; ++kh)
+#pragma unroll 4
           for (int kw = kw_lo; kw < kw_hi; ++kw) {
             const float v = gp[(ih0 + kh) * L.wi + iw0 + kw];
             const float* wp = wc + (size_t)(kh * L.k + kw) * L.co;
@@ -323,7 +381,8 @@ __device__ void f_conv_fwd(const LayerDev& L, const float* g, float* h, const fl
 
 }  // namespace
 
-__global__ void __launch_bounds__(FT) k_opt_chain(NetDev net, PoolDev pool, const PropDev* props,
+// two CTAs per SM: at most 64 registers a thread
+__global__ void __launch_bounds__(FT, 2) k_opt_chain(NetDev net, PoolDev pool, const PropDev* props,
                                                   const int* row_node, const int* row_j,
                                                   FusedHP hp, float* AP_out, float* GB_out,
                                                   int maxw) {
@@ -564,6 +623,7 @@ __device__ void f_conv_back_rows(const LayerDev& L, const float* cur, float* nxt
           const float* ap = cur + oh * L.wo + ow;
           const float* wp = Wb + (size_t)(kh * L.k + kw) * L.ci + grp * CB;
           if (CB == 4) {
+#pragma unroll 4
             for (int co = k0; co < L.co; co += ks) {
               const float4 w = *reinterpret_cast<const float4*>(wp + co * wco);
 #pragma unroll
@@ -576,6 +636,7 @@ __device__ void f_conv_back_rows(const LayerDev& L, const float* cur, float* nxt
               }
             }
           } else {
+#pragma unroll 4
             for (int co = k0; co < L.co; co += ks) {
               const float w = wp[co * wco];
 #pragma unroll
