@@ -523,6 +523,101 @@ def optimize(net, node: Node, dense_mnc, lo, hi, hp: AdamHP):
 
 
 # ----------------------------------------------------------------------------
+# Optimised intermediate bounds (Sec. 3.1, parameter sharing)
+# ----------------------------------------------------------------------------
+def intermediate_objective(net: Net, node: Node, t: int, idx, side: int, alpha, beta, lo, hi):
+    """Lower bounds of the rows side * e_j (j in idx) of zhat^(t) with one
+    parameter set (alpha_i, beta_i for i < t) shared by every row.
+
+    side = +1 gives lower bounds of zhat_j, side = -1 lower bounds of -zhat_j
+    (the upper bounds, negated).  Returns the per-row bounds; their sum is the
+    objective that the set ascends.
+    """
+    E = torch.zeros(idx.numel(), node.l[t].numel(), dtype=DT)
+    E[torch.arange(idx.numel()), idx] = float(side)
+    relax = {i: Relax(node.l[i], node.u[i], node.S[i], alpha[i], beta[i]) for i in range(1, t)}
+    lb, _, _ = backsub_rows(net, t, E, relax, lo, hi)
+    return lb
+
+
+def intermediate_objective_grad(net: Net, node: Node, t: int, idx, side: int, alpha, beta, lo, hi):
+    """Per-row bounds and the gradient of their sum w.r.t. the shared set."""
+    a = {i: alpha[i].detach().clone().requires_grad_(True) for i in alpha}
+    b = {i: beta[i].detach().clone().requires_grad_(True) for i in beta}
+    lb = intermediate_objective(net, node, t, idx, side, a, b, lo, hi)
+    keys = list(a.keys())
+    grads = torch.autograd.grad(lb.sum(), [a[k] for k in keys] + [b[k] for k in keys],
+                                allow_unused=True)
+    n = len(keys)
+    ga = {k: (g if g is not None else torch.zeros_like(a[k])) for k, g in zip(keys, grads[:n])}
+    gb = {k: (g if g is not None else torch.zeros_like(b[k])) for k, g in zip(keys, grads[n:])}
+    return lb.detach(), ga, gb
+
+
+def optimize_intermediate(net: Net, node: Node, lo, hi, hp: AdamHP, first_layer: int = 2):
+    """Optimised intermediate bounds of a node (Sec. 3.1: intermediate bounds
+    come from the same bounding procedure; each layer's neurons share one
+    parameter set, with separate sets for lower and upper bounds).
+
+    For t = max(2, first_layer) .. R in order (layer 1 bounds over the box are
+    exact already): the rows are the unstable, unsplit neurons j of layer t,
+    once with side +1 (lower bounds) and once with side -1 (upper bounds).  Each
+    side has one set (alpha_i, beta_i for the ReLU layers i < t) shared by all
+    its rows, started at DeepPoly slopes and beta = 0, and takes hp.steps
+    projected Adam steps (as in ``optimize``) ascending sum_j lb_j.  Every
+    iterate gives valid bounds, so each row keeps the best bound it reached
+    (the first iterate is the DeepPoly bound); the node's bounds of layer t are
+    intersected with them before layer t + 1 is bounded.  Returns the number of
+    rows bounded.
+    """
+    R = net.R
+    total = 0
+    lr = {"a": hp.lr_alpha, "b": hp.lr_beta}
+    for t in range(max(2, first_layer), R + 1):
+        l, u, S = node.l[t], node.u[t], node.S[t]
+        idx = torch.nonzero((l < 0) & (u > 0) & (S == 0)).reshape(-1)
+        if idx.numel() == 0:
+            continue
+        best = {}
+        for side in (1, -1):
+            alpha = {i: deeppoly_alpha(node.l[i], node.u[i]) for i in range(1, t)}
+            beta = {i: torch.zeros_like(node.l[i]) for i in range(1, t)}
+            state = {(g, i): (torch.zeros_like(node.l[i]), torch.zeros_like(node.l[i]))
+                     for g in ("a", "b") for i in range(1, t)}
+            bs = torch.full((idx.numel(),), -math.inf, dtype=DT)
+            for step in range(hp.steps + 1):
+                lb, ga, gb = intermediate_objective_grad(net, node, t, idx, side, alpha, beta,
+                                                         lo, hi)
+                bs = torch.maximum(bs, lb)
+                if step == hp.steps:
+                    break
+                k = step + 1
+                gmax = max([float(G[i].abs().max()) for G in (ga, gb) for i in G
+                            if G[i].numel()] + [0.0])
+                floor = hp.grad_floor * gmax
+                eps = max(hp.eps, hp.eps_rel * gmax)
+                for grp, P, G in (("a", alpha, ga), ("b", beta, gb)):
+                    for i in P:
+                        g = torch.where(G[i].abs() <= floor, torch.zeros_like(G[i]), G[i])
+                        m, v = state[(grp, i)]
+                        m = hp.b1 * m + (1 - hp.b1) * g
+                        v = hp.b2 * v + (1 - hp.b2) * g * g
+                        state[(grp, i)] = (m, v)
+                        mh = m / (1 - hp.b1 ** k)
+                        vh = v / (1 - hp.b2 ** k)
+                        P[i] = P[i] + lr[grp] * mh / (torch.sqrt(vh) + eps)
+                        P[i] = torch.clamp(P[i], 0.0, 1.0) if grp == "a" else torch.clamp(P[i], min=0.0)
+            best[side] = bs
+        l = l.clone()
+        u = u.clone()
+        l[idx] = torch.maximum(l[idx], best[1])
+        u[idx] = torch.minimum(u[idx], -best[-1])
+        node.l[t], node.u[t] = l, u
+        total += 2 * idx.numel()
+    return total
+
+
+# ----------------------------------------------------------------------------
 # Branching (Sec. 3.2)
 # ----------------------------------------------------------------------------
 ACS_TIE = 1e-5
