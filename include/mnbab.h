@@ -232,6 +232,26 @@ mnbab_status mnbab_bound_grad(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_
 mnbab_status mnbab_optimize(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
                             const mnbab_adam* cfg, float* best_lb_out);
 
+/* Optimised intermediate bounds (Sec. 3.1, parameter sharing).  For ReLU
+ * layers t = max(2, first_layer) .. R in order: the rows are the unstable,
+ * unsplit neurons j of layer t of each node, once as lower bounds (+e_j) and
+ * once as upper bounds (-e_j).  Each (node, side) has one parameter set
+ * (alpha and beta over the ReLU layers below t) shared by its rows, started at
+ * DeepPoly slopes (alpha = 1 if u >= -l else 0) and beta = 0; cfg->steps
+ * projected Adam steps ascend the sum of the rows' bounds (cfg NULL: 20 steps,
+ * default rates).  Each row keeps the best bound of the steps + 1 iterates,
+ * and the node's bounds of layer t are intersected with them before layer
+ * t + 1.  Works on each node's current bounds (re-bound split nodes first,
+ * e.g. with mnbab_bound_batch); the nodes' own parameters are unchanged.
+ * At most half the context's batch capacity of nodes per call; properties
+ * with multi-neuron constraints return MNBAB_E_UNSUPPORTED.  *rows_out
+ * (nullable) receives the number of rows bounded.  Scratch node slots are
+ * taken from the pool for the duration of the call (MNBAB_E_BUDGET if it is
+ * full). */
+mnbab_status mnbab_optimize_intermediate(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
+                                         int32_t first_layer, const mnbab_adam* cfg,
+                                         int64_t* rows_out);
+
 /* ACS branching score (Sec. 3.2) at each node's current parameters:
  * s_j = |(gamma^T P)_j| + |(gamma^T Phat)_j| over unstable unsplit neurons,
  * or, when every candidate scores 0, the intercept score

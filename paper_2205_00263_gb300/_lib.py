@@ -87,6 +87,8 @@ SIGNATURES = {
     "mnbab_deeppoly_batch": (status, [VP, C.POINTER(node_id), C.c_int32, FP]),
     "mnbab_bound_grad": (status, [VP, C.POINTER(node_id), C.c_int32, FP, FP]),
     "mnbab_optimize": (status, [VP, C.POINTER(node_id), C.c_int32, C.POINTER(Adam), FP]),
+    "mnbab_optimize_intermediate": (status, [VP, C.POINTER(node_id), C.c_int32, C.c_int32,
+                                             C.POINTER(Adam), C.POINTER(C.c_int64)]),
     "mnbab_score_branches": (status, [VP, C.POINTER(node_id), C.c_int32, IP, IP, FP]),
     "mnbab_bab_step": (status, [VP, C.POINTER(VP), C.c_int32, C.c_int32, C.POINTER(Adam),
                                 C.POINTER(StepStats)]),

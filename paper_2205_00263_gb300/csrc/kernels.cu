@@ -1882,6 +1882,95 @@ void launch_children(int nb, const int* parents, const int* kids, const int* lay
   k_children<<<grid, 256, 0, st>>>(parents, kids, layer, neuron, pool, net);
 }
 
+// ---------------------------------------------------------------------------
+// Optimised intermediate bounds (Sec. 3.1, parameter sharing): the parameter
+// set of one (node, target layer, side) lives in a scratch pool slot.
+// ---------------------------------------------------------------------------
+// Set slot dst[b] from node src[b]: bounds and splits, DeepPoly slopes
+// (alpha = 1 if u >= -l else 0), beta = 0, zero Adam moments.
+__global__ void k_set_init(const int* src, const int* dst, PoolDev pool) {
+  const int b = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = src[b], d = dst[b];
+  if (i < pool.SD) {
+    const size_t qs = (size_t)s * pool.SD + i, qd = (size_t)d * pool.SD + i;
+    const float l = pool.L[qs], u = pool.U[qs];
+    pool.L[qd] = l;
+    pool.U[qd] = u;
+    pool.S[qd] = pool.S[qs];
+    pool.ALPHA[qd] = u >= -l ? 1.f : 0.f;
+    pool.BETA[qd] = 0.f;
+    pool.MA[qd] = 0.f;
+    pool.VA[qd] = 0.f;
+    pool.MB[qd] = 0.f;
+    pool.VB[qd] = 0.f;
+  }
+  if (i == 0) {
+    pool.prop[d] = pool.prop[s];
+    pool.row[d] = pool.row[s];
+  }
+}
+
+void launch_set_init(int nsets, const int* src, const int* dst, PoolDev pool, cudaStream_t st) {
+  if (nsets <= 0) return;
+  dim3 grid((pool.SD + 255) / 256, nsets);
+  k_set_init<<<grid, 256, 0, st>>>(src, dst, pool);
+}
+
+// best[m] = lb[m] on the first iterate, max(best[m], lb[m]) after.
+__global__ void k_rows_best(int M, const float* lb, float* best, int first) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < M) best[m] = first ? lb[m] : fmaxf(best[m], lb[m]);
+}
+
+void launch_rows_best(int M, const float* lb, float* best, int first, cudaStream_t st) {
+  if (M <= 0) return;
+  k_rows_best<<<(M + 255) / 256, 256, 0, st>>>(M, lb, best, first);
+}
+
+// Adds the per-row gradients GA, GB ([row][SD], rows of one chunk) of each
+// set's rows to the set's gradients IGA, IGB ([set][SD]), entries k < lim.
+// seg holds (set, first row, end row) per block row, rows relative to the
+// chunk; the rows of a set are summed in order.
+__global__ void k_set_grad(const int* seg, int SD, int lim, const float* GA, const float* GB,
+                           float* IGA, float* IGB) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= lim) return;
+  const int s = seg[3 * blockIdx.y], r0 = seg[3 * blockIdx.y + 1], r1 = seg[3 * blockIdx.y + 2];
+  float ga = 0.f, gb = 0.f;
+  for (int m = r0; m < r1; ++m) {
+    ga += GA[(size_t)m * SD + k];
+    gb += GB[(size_t)m * SD + k];
+  }
+  IGA[(size_t)s * SD + k] += ga;
+  IGB[(size_t)s * SD + k] += gb;
+}
+
+void launch_set_grad(int nseg, const int* seg, int SD, int lim, const float* GA, const float* GB,
+                     float* IGA, float* IGB, cudaStream_t st) {
+  if (nseg <= 0 || lim <= 0) return;
+  dim3 grid((lim + 255) / 256, nseg);
+  k_set_grad<<<grid, 256, 0, st>>>(seg, SD, lim, GA, GB, IGA, IGB);
+}
+
+// Intersects the bounds of neuron j[m] of the layer at offset off of node
+// orig[m] with row m's best bound: sign +1 bounds zhat_j from below, -1 is
+// the lower bound of -zhat_j, so -best bounds it from above.
+__global__ void k_set_update(int M, const int* orig, const int* j, const float* sign,
+                             const float* best, PoolDev pool, int off) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const size_t q = (size_t)orig[m] * pool.SD + off + j[m];
+  if (sign[m] > 0.f) pool.L[q] = fmaxf(pool.L[q], best[m]);
+  else pool.U[q] = fminf(pool.U[q], -best[m]);
+}
+
+void launch_set_update(int M, const int* orig, const int* j, const float* sign, const float* best,
+                       PoolDev pool, int off, cudaStream_t st) {
+  if (M <= 0) return;
+  k_set_update<<<(M + 255) / 256, 256, 0, st>>>(M, orig, j, sign, best, pool, off);
+}
+
 // Root nodes from their property's root-bound slot: DeepPoly slopes
 // (alpha = 1 if u >= -l else 0), beta = gamma = 0, no splits.
 __global__ void k_root_init(const int* slots, const int* srcs, const int* rows, PoolDev pool) {

@@ -216,6 +216,16 @@ void launch_acs(int M, const int* row_node, PoolDev pool, const PropDev* props, 
                 int* out_neuron, float* out_score, int* out_fallback, cudaStream_t st);
 void launch_children(int nb, const int* parents, const int* kids, const int* layer,
                      const int* neuron, PoolDev pool, const NetDev& net, cudaStream_t st);
+// Optimised intermediate bounds (Sec. 3.1, parameter sharing): set slots
+// dst[b] start from node src[b] with DeepPoly slopes, beta = 0, zero moments;
+// per-row best bounds; per-set gradient sums over segments (set, first row,
+// end row) of a chunk's rows; the nodes' bounds intersected with the best.
+void launch_set_init(int nsets, const int* src, const int* dst, PoolDev pool, cudaStream_t st);
+void launch_rows_best(int M, const float* lb, float* best, int first, cudaStream_t st);
+void launch_set_grad(int nseg, const int* seg, int SD, int lim, const float* GA, const float* GB,
+                     float* IGA, float* IGB, cudaStream_t st);
+void launch_set_update(int M, const int* orig, const int* j, const float* sign, const float* best,
+                       PoolDev pool, int off, cudaStream_t st);
 // Root nodes: slots[i] initialised from root-bound slot srcs[i] for row rows[i].
 void launch_root_init(int nb, const int* slots, const int* srcs, const int* rows, PoolDev pool,
                       cudaStream_t st);

@@ -1,0 +1,109 @@
+"""GPU parity of the optimised intermediate bounds (Sec. 3.1, parameter
+sharing: one set per layer and side, shared by the layer's neurons) against
+the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from helpers import TOL, close, concat, conv_case, fc_case, gpu_property, random_node, to_params
+from oracle import core
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Context():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_00263_gb300 import Context as Ctx
+    return Ctx
+
+
+def _case(kind):
+    if kind == "fc":
+        return fc_case(21, (37, 53, 41, 29, 7), 0.1)
+    return conv_case(5, 0.05)
+
+
+@pytest.mark.parametrize("kind", ["fc", "conv"])
+def test_optimized_intermediate_bounds_match_oracle(Context, kind):
+    """Root and split nodes (float32 start values shared by both sides): after
+    20 Adam steps per set, every neuron's bounds match the oracle's within
+    1e-4 (1 + |b|), the row counts agree exactly, and the nodes' own
+    parameters are left as they were."""
+    layers, C, d, lo, hi, prep = _case(kind)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    R = net.R
+    assert R >= 3
+    rng = np.random.default_rng(21)
+    with Context(node_capacity=64) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
+        onodes, gids = [], []
+        for k in range(4):
+            on = random_node(prep, rng, n_splits=k, row=k % C.shape[0], gamma_scale=0.0)
+            on.split_layer = R
+            gid = ctx.node_root(prop, on.row)
+            ctx.import_params(gid, to_params(on, R))
+            onodes.append(on)
+            gids.append(gid)
+        before = [ctx.export_params(g) for g in gids]
+        rows = ctx.optimize_intermediate(gids, first_layer=2, steps=20)
+        ref_rows = 0
+        for k, on in enumerate(onodes):
+            ref_rows += core.optimize_intermediate(net, on, lo_t, hi_t, core.AdamHP())
+            got = ctx.export_params(gids[k])
+            for name, g_, o_ in (("l", got.l, concat(on.l, R)), ("u", got.u, concat(on.u, R))):
+                ok = close(g_, o_)
+                assert ok.all(), (f"node {k} {name}: {int((~ok).sum())} of {ok.size} off, worst "
+                                  f"{np.max(np.abs(g_ - o_) / (1 + np.abs(o_)))}")
+            assert np.array_equal(got.alpha, before[k].alpha)
+            assert np.array_equal(got.beta, before[k].beta)
+            assert np.all(got.l >= before[k].l) and np.all(got.u <= before[k].u)
+        assert rows == ref_rows
+
+
+def test_optimized_intermediate_bounds_sound_on_samples(Context):
+    """Root node of the conv case: the GPU's optimised bounds contain every
+    pre-activation of 10^4 sampled inputs, and tighten some neuron."""
+    layers, C, d, lo, hi, prep = _case("conv")
+    net = prep[0]
+    with Context(node_capacity=64) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
+        gid = ctx.node_root(prop, 0)
+        before = ctx.export_params(gid)
+        ctx.optimize_intermediate([gid], steps=20)
+        got = ctx.export_params(gid)
+    gain = float(np.sum(got.l - before.l) + np.sum(before.u - got.u))
+    assert gain > 1e-4
+    import torch
+    X = np.random.default_rng(3).uniform(lo, hi, size=(10000, lo.size))
+    h = torch.as_tensor(X, dtype=torch.float64)
+    off = 0
+    for i in range(1, net.R + 1):
+        zh = net.aff[i].forward(h).numpy()
+        di = zh.shape[1]
+        li, ui = got.l[off:off + di], got.u[off:off + di]
+        slack = TOL * (1.0 + np.abs(zh))
+        assert np.all(zh >= li - slack), f"layer {i}: lower bound above a sample"
+        assert np.all(zh <= ui + slack), f"layer {i}: upper bound below a sample"
+        h = torch.clamp(torch.as_tensor(zh), min=0)
+        off += di
+
+
+def test_optimized_intermediate_refuses_constraints(Context):
+    """Properties with multi-neuron constraints are refused (alpha and beta
+    sets only), without changing the node."""
+    from paper_2205_00263_gb300 import MnbabError
+    layers, C, d, lo, hi, prep = fc_case(8, (37, 53, 29, 7), 0.12, with_mnc=True)
+    m = prep[6]
+    E = sum(v.idx.shape[0] for v in m.values())
+    with Context(node_capacity=64, max_mnc_rows=E) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d, m)
+        gid = ctx.node_root(prop, 0)
+        before = ctx.export_params(gid)
+        with pytest.raises(MnbabError):
+            ctx.optimize_intermediate([gid])
+        after = ctx.export_params(gid)
+        assert np.array_equal(before.l, after.l) and np.array_equal(before.u, after.u)
