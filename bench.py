@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=None,
                     help="requests of the serving stream (default 24 in the main line, 400 with --serving)")
     ap.add_argument("--serve-rate", type=float, default=4.0)
+    ap.add_argument("--inter-nodes", type=int, default=128,
+                    help="root nodes of the optimised-intermediate-bounds arm (0 skips it)")
     return ap.parse_args()
 
 
@@ -425,6 +427,10 @@ def run_ours(args):
                              "solve": "16 fresh properties from host arrays (32-node budget "
                                       "each) to verdicts"}
         ectx.close()
+    inter = None
+    if args.inter_nodes > 0:
+        inter = intermediate_run(local, stream, layers, eps, start + 600_000, args.inter_nodes,
+                                 0 if (args.no_cpu_baseline or rank != 0) else 4)
     serving = None
     if world == 1 and (args.serve_requests is None or args.serve_requests > 0):
         sctx = Context(device=local, stream=stream.cuda_stream, node_capacity=SERVE_CAPACITY,
@@ -460,6 +466,7 @@ def run_ours(args):
             "kernel_breakdown_note": "one untimed step before the timed region, every class timed",
             "nodes_timed": tot_nodes,
             "serving": serving,
+            "intermediate": inter,
             "launches_before_timed": int(launches0),
         }
         print(json.dumps(out), flush=True)
@@ -589,6 +596,61 @@ def serving_nets(ctx):
         layers = synth.make_network(cfg)
         nets[cfg] = (layers, ctx.load_network(layers), eps)
     return nets
+
+
+# ----------------------------------------------------------------------------
+# Optimised intermediate bounds (Sec. 3.1, parameter sharing) of root nodes of
+# the same workload: one mnbab_optimize_intermediate call over n_nodes roots.
+def intermediate_run(local, stream, layers, eps, start, n_nodes, oracle_nodes):
+    import torch
+    from paper_2205_00263_gb300 import Context
+    props = synth.make_properties(CFG, layers, n=n_nodes + 4, eps=eps, start=start)
+    # each property also holds its root-bound slot and one root node per row
+    ctx = Context(device=local, stream=stream.cuda_stream, node_capacity=4096)
+    try:
+        net = ctx.load_network(layers)
+        ps = [ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d) for pr in props]
+        nodes = [ctx.node_root(p, 0) for p in ps]  # starts every property (root bounds)
+        # warm-up on 4 other roots (scratch allocation), every kernel class timed
+        ctx.profile(True)
+        ctx.optimize_intermediate(nodes[:4], steps=ADAM_STEPS)
+        stats, _ = ctx.profile_read()
+        ctx.profile(False)
+        timed = nodes[4:]
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        rows = ctx.optimize_intermediate(timed, steps=ADAM_STEPS)
+        e1.record(stream)
+        e1.synchronize()
+        wall = time.perf_counter() - t0
+        ms = e0.elapsed_time(e1)
+    finally:
+        ctx.close()
+    top = sorted(((k, v["ms"]) for k, v in stats.items()
+                  if v["ms"] and not k.startswith(("phase_", "step_"))), key=lambda kv: -kv[1])
+    out = {"nodes": len(timed), "rows": rows, "ms": ms, "wall_ms": 1e3 * wall,
+           "nodes_per_s": len(timed) / (ms * 1e-3), "rows_per_s": rows / (ms * 1e-3),
+           "steps": ADAM_STEPS,
+           "form": "one call over root nodes (row 0) of fresh properties; layers 2..R, lower and "
+                   "upper sets per node",
+           "breakdown_warmup_ms": {k: round(v, 3) for k, v in top[:5]}}
+    if oracle_nodes > 0:
+        from oracle import bab, core
+        t_or, rows_or = 0.0, 0
+        for pr in props[4:4 + oracle_nodes]:
+            net_o, lo_t, hi_t, l, u, S, m, dense = bab.prepare(layers, pr.C, pr.d, pr.lo, pr.hi)
+            node = bab.root_node(net_o, 0, l, u, S, None)
+            t1 = time.perf_counter()
+            rows_or += core.optimize_intermediate(net_o, node, lo_t, hi_t,
+                                                  core.AdamHP(steps=ADAM_STEPS))
+            t_or += time.perf_counter() - t1
+        out["cpu_oracle"] = {"nodes_per_s": oracle_nodes / t_or, "rows": rows_or,
+                             "nodes": oracle_nodes, "cores": torch.get_num_threads(),
+                             "kind": "oracle"}
+    return out
 
 
 # ----------------------------------------------------------------------------
