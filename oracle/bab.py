@@ -26,7 +26,7 @@ from __future__ import annotations
 
 import math
 from collections import deque
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 import torch
@@ -139,11 +139,18 @@ def children(node: Node, params, split, next_id: int):
 
 
 def verify(layers, C, d, lo, hi, max_nodes=256, hp: AdamHP | None = None, mnc_fn=None,
-           rows=None, prepared=None, cab=False) -> PropResult:
+           rows=None, prepared=None, cab=False, inter_steps=0) -> PropResult:
     """BaB on every row of one property; verdict VERIFIED / FALSIFIED / UNKNOWN.
-    With ``cab`` the split is chosen by the cost-adjusted ACS score."""
+    With ``cab`` the split is chosen by the cost-adjusted ACS score.  With
+    ``inter_steps`` > 0 the root's intermediate bounds are first optimised
+    (``core.optimize_intermediate``, Sec. 3.1 parameter sharing, that many Adam
+    steps at hp's rates) and shared by every row's root node."""
     hp = hp or AdamHP()
     net, lo_t, hi_t, l, u, S, mnc, dense = prepared or prepare(layers, C, d, lo, hi, mnc_fn)
+    if inter_steps > 0:
+        root = root_node(net, 0, l, u, S, mnc)
+        core.optimize_intermediate(net, root, lo_t, hi_t, replace(hp, steps=inter_steps))
+        l, u = root.l, root.u
     costs = core.cab_costs(net, {i: m.idx.shape[0] for i, m in mnc.items()} if mnc else None) \
         if cab else None
     rows = list(range(net.width(net.R + 1))) if rows is None else rows
