@@ -252,6 +252,15 @@ mnbab_status mnbab_optimize_intermediate(mnbab_ctx* ctx, const mnbab_node_id* no
                                          int32_t first_layer, const mnbab_adam* cfg,
                                          int64_t* rows_out);
 
+/* Optimised intermediate bounds at the root of a property, as
+ * mnbab_optimize_intermediate with `steps` Adam steps at the default rates:
+ * run when the property starts, after its DeepPoly root bounds and before its
+ * root nodes take them; 0 (the default) keeps the DeepPoly root bounds.  Call
+ * before the property starts (MNBAB_E_INVALID_ARG after); properties with
+ * multi-neuron constraints return MNBAB_E_UNSUPPORTED (and mnbab_set_mnc
+ * refuses a property with steps > 0). */
+mnbab_status mnbab_set_intermediate_steps(mnbab_ctx* ctx, mnbab_prop* prop, int32_t steps);
+
 /* ACS branching score (Sec. 3.2) at each node's current parameters:
  * s_j = |(gamma^T P)_j| + |(gamma^T Phat)_j| over unstable unsplit neurons,
  * or, when every candidate scores 0, the intercept score

@@ -94,6 +94,7 @@ SIGNATURES = {
                                 C.POINTER(StepStats)]),
     "mnbab_set_budget": (status, [VP, VP, C.c_int32]),
     "mnbab_set_branching": (status, [VP, VP, C.c_int32]),
+    "mnbab_set_intermediate_steps": (status, [VP, VP, C.c_int32]),
     "mnbab_get_verdict": (status, [VP, VP, C.c_int32, IP, FP, FP]),
     "mnbab_get_trace": (status, [VP, VP, C.POINTER(TraceRec), C.c_int32, IP]),
     "mnbab_queue_size": (status, [VP, VP, IP]),

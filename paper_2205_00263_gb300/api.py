@@ -253,6 +253,10 @@ class Context:
         self._ck(self.lib.mnbab_optimize(self.h, ids, n, C.byref(a), _fp(best)))
         return best
 
+    def set_intermediate_steps(self, prop: Prop, steps: int):
+        """Optimised intermediate bounds at the property's root when it starts."""
+        self._ck(self.lib.mnbab_set_intermediate_steps(self.h, prop.h, steps))
+
     def optimize_intermediate(self, nodes, first_layer=2, steps=20, lr_alpha=0.1, lr_beta=0.05,
                               beta1=0.9, beta2=0.999, eps=1e-8, grad_floor=0.0, eps_rel=1e-3):
         """Optimised intermediate bounds of the nodes (shared per-layer sets);

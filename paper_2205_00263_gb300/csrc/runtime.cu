@@ -127,6 +127,7 @@ struct mnbab_prop {
   std::vector<int> root_row_slots;   // its row root nodes, initialised with the bounds
   bool admitted = true;              // false while queued in the request loop
   bool materialized = false;         // node slots allocated
+  int inter_steps = 0;               // Adam steps of optimised root intermediate bounds
 };
 
 // A request of the serving loop.
@@ -1089,6 +1090,161 @@ void materialize(mnbab_net* n, mnbab_prop* p) {
   p->materialized = true;
 }
 
+// Optimised intermediate bounds (Sec. 3.1, parameter sharing).  For ReLU
+// layers t = max(2, first_layer) .. R in order, the unstable unsplit neurons
+// of t of every node give rows +e_j (lower bounds) and -e_j (upper bounds).
+// Each (node, side) has one (alpha, beta) set over the layers below t, held in
+// a scratch slot and shared by its rows.  A step bounds the rows (one sweep
+// per chunk of rows), sums the rows' gradients per set and takes one projected
+// Adam step per set; every row keeps its best bound, and the nodes' bounds of
+// layer t are intersected with them before layer t + 1 is bounded.
+int64_t optimize_intermediate_impl(mnbab_net* n, const std::vector<int>& slots, int first_layer,
+                                   const mnbab_adam& a) {
+  mnbab_ctx* c = n->ctx;
+  const int nn = (int)slots.size();
+  const int SD = n->SD, R = n->R;
+  const int CH = std::max(1, std::min(n->B, n->chunk));  // rows per sweep and adjoint
+  if (!n->iga) {
+    n->iga = dalloc_t<float>(c, (size_t)n->B * SD);
+    n->igb = dalloc_t<float>(c, (size_t)n->B * SD);
+    n->ibest = dalloc_t<float>(c, n->rows_cap);
+    n->iorig = dalloc_t<int>(c, n->rows_cap);
+    n->isrc = dalloc_t<int>(c, n->B);
+    n->idst = dalloc_t<int>(c, n->B);
+    n->iseg_cap = 3 * ((size_t)n->B + n->rows_cap / CH + 2);
+    n->iseg = dalloc_t<int>(c, n->iseg_cap);
+  }
+  struct Scratch {
+    mnbab_net* n;
+    std::vector<int> slots;
+    ~Scratch() {
+      for (int s : slots) free_slot(n, s);
+    }
+  } tmp{n, {}};
+  int64_t total = 0;
+  std::vector<float> hl, hu;
+  std::vector<int8_t> hs;
+  for (int t = std::max(2, (int)first_layer); t <= R; ++t) {
+    const int dt = n->nd.d[t], off = n->nd.off[t];
+    hl.resize((size_t)nn * dt);
+    hu.resize((size_t)nn * dt);
+    hs.resize((size_t)nn * dt);
+    for (int k = 0; k < nn; ++k) {
+      const size_t q = (size_t)slots[k] * SD + off;
+      d2h(c, hl.data() + (size_t)k * dt, n->pool.L + q, dt);
+      d2h(c, hu.data() + (size_t)k * dt, n->pool.U + q, dt);
+      d2h(c, hs.data() + (size_t)k * dt, n->pool.S + q, dt);
+    }
+    sync(c);
+    // rows grouped by set: a node's lower rows, then its upper rows
+    std::vector<int> rnode, rj, rorig, src, dst, set_lo, set_hi;
+    std::vector<float> rsign;
+    for (int k = 0; k < nn; ++k) {
+      std::vector<int> idx;
+      for (int j = 0; j < dt; ++j) {
+        const size_t q = (size_t)k * dt + j;
+        if (hl[q] < 0.f && hu[q] > 0.f && hs[q] == 0) idx.push_back(j);
+      }
+      if (idx.empty()) continue;
+      for (int side = 0; side < 2; ++side) {
+        const int ts = alloc_slot(n);
+        tmp.slots.push_back(ts);
+        n->slot_prop[ts] = n->slot_prop[slots[k]];
+        n->slot_row[ts] = n->slot_row[slots[k]];
+        n->slot_split[ts] = R;
+        src.push_back(slots[k]);
+        dst.push_back(ts);
+        set_lo.push_back((int)rnode.size());
+        for (int j : idx) {
+          rnode.push_back(ts);
+          rj.push_back(j);
+          rsign.push_back(side == 0 ? 1.f : -1.f);
+          rorig.push_back(slots[k]);
+        }
+        set_hi.push_back((int)rnode.size());
+      }
+    }
+    const int M = (int)rnode.size(), nsets = (int)dst.size();
+    if (M == 0) continue;
+    if ((size_t)M > n->rows_cap) fail(MNBAB_E_DEVICE, "row scratch too small");
+    // per chunk of rows, the segments of its sets: (set, first row, end row)
+    std::vector<int> seg, seg_at;
+    for (int c0 = 0; c0 < M; c0 += CH) {
+      const int c1 = std::min(M, c0 + CH);
+      seg_at.push_back((int)seg.size() / 3);
+      for (int st = 0; st < nsets; ++st) {
+        const int lo = std::max(set_lo[st], c0), hi = std::min(set_hi[st], c1);
+        if (lo < hi) seg.insert(seg.end(), {st, lo - c0, hi - c0});
+      }
+    }
+    seg_at.push_back((int)seg.size() / 3);
+    if (seg.size() > n->iseg_cap) fail(MNBAB_E_DEVICE, "segment scratch too small");
+    h2d(c, n->row_node, rnode.data(), M);
+    h2d(c, n->row_j, rj.data(), M);
+    h2d(c, n->row_sign, rsign.data(), M);
+    h2d(c, n->iorig, rorig.data(), M);
+    h2d(c, n->isrc, src.data(), nsets);
+    h2d(c, n->idst, dst.data(), nsets);
+    h2d(c, n->iseg, seg.data(), seg.size());
+    {
+      Scope sc(c, C_BOOK, 0.0, 36.0 * nsets * SD);
+      launch_set_init(nsets, n->isrc, n->idst, n->pool, c->st);
+    }
+    SweepOpts o;
+    o.final_mode = true;
+    double b1t = 1.0, b2t = 1.0;
+    for (int step = 0; step <= a.steps; ++step) {
+      const bool grad = step < a.steps;
+      o.store = grad;
+      if (grad) {
+        ck(cudaMemsetAsync(n->iga, 0, (size_t)nsets * SD * sizeof(float), c->st), "memset");
+        ck(cudaMemsetAsync(n->igb, 0, (size_t)nsets * SD * sizeof(float), c->st), "memset");
+      }
+      for (int ci = 0, c0 = 0; c0 < M; ++ci, c0 += CH) {
+        const int Mc = std::min(CH, M - c0);
+        RowsDev r{Mc, n->row_node + c0, n->row_j + c0, n->row_sign + c0};
+        sweep(n, t, r, o);
+        {
+          Scope sc(c, C_BOOK, 0.0, 12.0 * Mc);
+          launch_rows_best(Mc, n->lb, n->ibest + c0, step == 0, c->st);
+        }
+        if (!grad) continue;
+        // the adjoint reads each row's slot from bslots: point it at the chunk's rows
+        int* keep = n->bslots;
+        n->bslots = n->row_node + c0;
+        try {
+          adjoint(n, Mc, false, t - 1);
+        } catch (...) {
+          n->bslots = keep;
+          throw;
+        }
+        n->bslots = keep;
+        const int ns = seg_at[ci + 1] - seg_at[ci];
+        Scope sc(c, C_ADAM, 0.0, 8.0 * (double)Mc * off + 16.0 * ns * off);
+        launch_set_grad(ns, n->iseg + 3 * seg_at[ci], SD, off, n->GA, n->GB, n->iga, n->igb,
+                        c->st);
+      }
+      if (!grad) break;
+      b1t *= a.beta1;
+      b2t *= a.beta2;
+      Scope sc(c, C_ADAM, 0.0, 4.0 * nsets * 2.0 * SD * 8.0, 2);
+      launch_adam(nsets, n->idst, n->pool, c->d_props, SD, n->iga, n->igb, n->GG, n->gmax,
+                  a.grad_floor, a.lr_alpha, a.lr_beta, a.lr_gamma, a.beta1, a.beta2, a.eps,
+                  a.eps_rel, (float)(1.0 - b1t), (float)(1.0 - b2t), c->st);
+    }
+    {
+      Scope sc(c, C_BOOK, 0.0, 20.0 * M);
+      launch_set_update(M, n->iorig, n->row_j, n->row_sign, n->ibest, n->pool, off, c->st);
+    }
+    sync(c);
+    for (int s : tmp.slots) free_slot(n, s);
+    tmp.slots.clear();
+    total += M;
+  }
+  sync(c);
+  return total;
+}
+
 // Starts the given properties (all admitted properties of the network when
 // `only` is null) and bounds every root still pending, in shared launches.
 void ensure_roots(mnbab_net* n, mnbab_prop* const* only = nullptr, int n_only = 0) {
@@ -1116,6 +1272,21 @@ void ensure_roots(mnbab_net* n, mnbab_prop* const* only = nullptr, int n_only = 
   std::vector<int> roots;
   for (auto* p : pend) roots.push_back(p->root_slot);
   rebound(n, roots);
+  // optimised intermediate bounds of the roots that ask for them (Sec. 3.1,
+  // parameter sharing), before the root nodes take the root bounds
+  std::vector<std::pair<int, int>> want;  // (steps, root slot)
+  for (auto* p : pend)
+    if (p->inter_steps > 0) want.push_back({p->inter_steps, p->root_slot});
+  std::sort(want.begin(), want.end());
+  for (size_t i = 0; i < want.size();) {
+    std::vector<int> grp;
+    const int steps = want[i].first;
+    while (i < want.size() && want[i].first == steps && 2 * ((int)grp.size() + 1) <= n->B)
+      grp.push_back(want[i++].second);
+    mnbab_adam a = default_adam();
+    a.steps = steps;
+    optimize_intermediate_impl(n, grp, 2, a);
+  }
   std::vector<int> dst, src, row;
   auto flush = [&]() {
     if (dst.empty()) return;
@@ -1742,6 +1913,8 @@ mnbab_status mnbab_set_mnc(mnbab_ctx* c, mnbab_prop* p, int32_t layer, int32_t n
       !Phat || !pv)))
     fail(MNBAB_E_INVALID_ARG, "bad constraint arguments");
   if (p->mnc_set[layer]) fail(MNBAB_E_INVALID_ARG, "constraints of this layer already set");
+  if (p->inter_steps > 0)
+    fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
   mnbab_net* n = p->net;
   const int d = n->nd.d[layer];
   if (p->pd.E + n_rows > c->EC)
@@ -1978,14 +2151,6 @@ mnbab_status mnbab_optimize(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t nn
   API_END(c)
 }
 
-// Optimised intermediate bounds (Sec. 3.1, parameter sharing).  For ReLU
-// layers t = max(2, first_layer) .. R in order, the unstable unsplit neurons
-// of t of every node give rows +e_j (lower bounds) and -e_j (upper bounds).
-// Each (node, side) has one (alpha, beta) set over the layers below t, held in
-// a scratch slot and shared by its rows.  A step bounds the rows (one sweep
-// per chunk of rows), sums the rows' gradients per set and takes one projected
-// Adam step per set; every row keeps its best bound, and the nodes' bounds of
-// layer t are intersected with them before layer t + 1 is bounded.
 mnbab_status mnbab_optimize_intermediate(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t nn,
                                          int32_t first_layer, const mnbab_adam* cfg,
                                          int64_t* rows_out) {
@@ -1998,147 +2163,18 @@ mnbab_status mnbab_optimize_intermediate(mnbab_ctx* c, const mnbab_node_id* node
   for (int s : slots)
     if (c->props[n->slot_prop[s]]->pd.E > 0)
       fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
-  const int SD = n->SD, R = n->R;
-  const int CH = std::max(1, std::min(n->B, n->chunk));  // rows per sweep and adjoint
-  if (!n->iga) {
-    n->iga = dalloc_t<float>(c, (size_t)n->B * SD);
-    n->igb = dalloc_t<float>(c, (size_t)n->B * SD);
-    n->ibest = dalloc_t<float>(c, n->rows_cap);
-    n->iorig = dalloc_t<int>(c, n->rows_cap);
-    n->isrc = dalloc_t<int>(c, n->B);
-    n->idst = dalloc_t<int>(c, n->B);
-    n->iseg_cap = 3 * ((size_t)n->B + n->rows_cap / CH + 2);
-    n->iseg = dalloc_t<int>(c, n->iseg_cap);
-  }
-  struct Scratch {
-    mnbab_net* n;
-    std::vector<int> slots;
-    ~Scratch() {
-      for (int s : slots) free_slot(n, s);
-    }
-  } tmp{n, {}};
-  int64_t total = 0;
-  std::vector<float> hl, hu;
-  std::vector<int8_t> hs;
-  for (int t = std::max(2, (int)first_layer); t <= R; ++t) {
-    const int dt = n->nd.d[t], off = n->nd.off[t];
-    hl.resize((size_t)nn * dt);
-    hu.resize((size_t)nn * dt);
-    hs.resize((size_t)nn * dt);
-    for (int k = 0; k < nn; ++k) {
-      const size_t q = (size_t)slots[k] * SD + off;
-      d2h(c, hl.data() + (size_t)k * dt, n->pool.L + q, dt);
-      d2h(c, hu.data() + (size_t)k * dt, n->pool.U + q, dt);
-      d2h(c, hs.data() + (size_t)k * dt, n->pool.S + q, dt);
-    }
-    sync(c);
-    // rows grouped by set: a node's lower rows, then its upper rows
-    std::vector<int> rnode, rj, rorig, src, dst, set_lo, set_hi;
-    std::vector<float> rsign;
-    for (int k = 0; k < nn; ++k) {
-      std::vector<int> idx;
-      for (int j = 0; j < dt; ++j) {
-        const size_t q = (size_t)k * dt + j;
-        if (hl[q] < 0.f && hu[q] > 0.f && hs[q] == 0) idx.push_back(j);
-      }
-      if (idx.empty()) continue;
-      for (int side = 0; side < 2; ++side) {
-        const int ts = alloc_slot(n);
-        tmp.slots.push_back(ts);
-        n->slot_prop[ts] = n->slot_prop[slots[k]];
-        n->slot_row[ts] = n->slot_row[slots[k]];
-        n->slot_split[ts] = R;
-        src.push_back(slots[k]);
-        dst.push_back(ts);
-        set_lo.push_back((int)rnode.size());
-        for (int j : idx) {
-          rnode.push_back(ts);
-          rj.push_back(j);
-          rsign.push_back(side == 0 ? 1.f : -1.f);
-          rorig.push_back(slots[k]);
-        }
-        set_hi.push_back((int)rnode.size());
-      }
-    }
-    const int M = (int)rnode.size(), nsets = (int)dst.size();
-    if (M == 0) continue;
-    if ((size_t)M > n->rows_cap) fail(MNBAB_E_DEVICE, "row scratch too small");
-    // per chunk of rows, the segments of its sets: (set, first row, end row)
-    std::vector<int> seg, seg_at;
-    for (int c0 = 0; c0 < M; c0 += CH) {
-      const int c1 = std::min(M, c0 + CH);
-      seg_at.push_back((int)seg.size() / 3);
-      for (int st = 0; st < nsets; ++st) {
-        const int lo = std::max(set_lo[st], c0), hi = std::min(set_hi[st], c1);
-        if (lo < hi) seg.insert(seg.end(), {st, lo - c0, hi - c0});
-      }
-    }
-    seg_at.push_back((int)seg.size() / 3);
-    if (seg.size() > n->iseg_cap) fail(MNBAB_E_DEVICE, "segment scratch too small");
-    h2d(c, n->row_node, rnode.data(), M);
-    h2d(c, n->row_j, rj.data(), M);
-    h2d(c, n->row_sign, rsign.data(), M);
-    h2d(c, n->iorig, rorig.data(), M);
-    h2d(c, n->isrc, src.data(), nsets);
-    h2d(c, n->idst, dst.data(), nsets);
-    h2d(c, n->iseg, seg.data(), seg.size());
-    {
-      Scope sc(c, C_BOOK, 0.0, 36.0 * nsets * SD);
-      launch_set_init(nsets, n->isrc, n->idst, n->pool, c->st);
-    }
-    SweepOpts o;
-    o.final_mode = true;
-    double b1t = 1.0, b2t = 1.0;
-    for (int step = 0; step <= a.steps; ++step) {
-      const bool grad = step < a.steps;
-      o.store = grad;
-      if (grad) {
-        ck(cudaMemsetAsync(n->iga, 0, (size_t)nsets * SD * sizeof(float), c->st), "memset");
-        ck(cudaMemsetAsync(n->igb, 0, (size_t)nsets * SD * sizeof(float), c->st), "memset");
-      }
-      for (int ci = 0, c0 = 0; c0 < M; ++ci, c0 += CH) {
-        const int Mc = std::min(CH, M - c0);
-        RowsDev r{Mc, n->row_node + c0, n->row_j + c0, n->row_sign + c0};
-        sweep(n, t, r, o);
-        {
-          Scope sc(c, C_BOOK, 0.0, 12.0 * Mc);
-          launch_rows_best(Mc, n->lb, n->ibest + c0, step == 0, c->st);
-        }
-        if (!grad) continue;
-        // the adjoint reads each row's slot from bslots: point it at the chunk's rows
-        int* keep = n->bslots;
-        n->bslots = n->row_node + c0;
-        try {
-          adjoint(n, Mc, false, t - 1);
-        } catch (...) {
-          n->bslots = keep;
-          throw;
-        }
-        n->bslots = keep;
-        const int ns = seg_at[ci + 1] - seg_at[ci];
-        Scope sc(c, C_ADAM, 0.0, 8.0 * (double)Mc * off + 16.0 * ns * off);
-        launch_set_grad(ns, n->iseg + 3 * seg_at[ci], SD, off, n->GA, n->GB, n->iga, n->igb,
-                        c->st);
-      }
-      if (!grad) break;
-      b1t *= a.beta1;
-      b2t *= a.beta2;
-      Scope sc(c, C_ADAM, 0.0, 4.0 * nsets * 2.0 * SD * 8.0, 2);
-      launch_adam(nsets, n->idst, n->pool, c->d_props, SD, n->iga, n->igb, n->GG, n->gmax,
-                  a.grad_floor, a.lr_alpha, a.lr_beta, a.lr_gamma, a.beta1, a.beta2, a.eps,
-                  a.eps_rel, (float)(1.0 - b1t), (float)(1.0 - b2t), c->st);
-    }
-    {
-      Scope sc(c, C_BOOK, 0.0, 20.0 * M);
-      launch_set_update(M, n->iorig, n->row_j, n->row_sign, n->ibest, n->pool, off, c->st);
-    }
-    sync(c);
-    for (int s : tmp.slots) free_slot(n, s);
-    tmp.slots.clear();
-    total += M;
-  }
-  sync(c);
+  const int64_t total = optimize_intermediate_impl(n, slots, first_layer, a);
   if (rows_out) *rows_out = total;
+  API_END(c)
+}
+
+mnbab_status mnbab_set_intermediate_steps(mnbab_ctx* c, mnbab_prop* p, int32_t steps) {
+  API_BEGIN(c)
+  if (!p || steps < 0) fail(MNBAB_E_INVALID_ARG, "bad step count");
+  if (p->materialized) fail(MNBAB_E_INVALID_ARG, "property already started");
+  if (steps > 0 && p->pd.E > 0)
+    fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
+  p->inter_steps = steps;
   API_END(c)
 }
 

@@ -123,3 +123,38 @@ def to_params(node, R):
 
 def concat(D, R):
     return np.concatenate([D[i].numpy() for i in range(1, R + 1)])
+
+
+def run_gpu_bab(ctx, props, max_nodes, steps=20):
+    for _ in range(10000):
+        st = ctx.bab_step(props, max_nodes=max_nodes, steps=steps)
+        if st["nodes_bounded"] == 0:
+            break
+
+
+def compare_trace(gtr, ores, max_cmp=None):
+    """Node-by-node agreement up to the first flagged divergence.
+
+    Roots (one optimisation from identical state) must match within TOL.  A
+    child inherits its parent's FP32 parameters, and the piecewise Adam
+    trajectory can amplify rounding differences (the FP64 oracle run in FP32
+    does the same), so the first child outside TOL flags the property and
+    ends the comparison; its bound must still agree within 5e-2."""
+    flagged = 0
+    n = min(len(gtr), len(ores.nodes)) if max_cmp is None else min(max_cmp, len(gtr), len(ores.nodes))
+    for k in range(n):
+        g, o = gtr[k], ores.nodes[k]
+        assert g["seq"] == o.node_id and g["row"] == o.row, (k, g, o)
+        band = TOL * (1 + abs(o.lb))
+        if abs(g["lb"] - o.lb) > band:
+            assert o.depth > 0, ("root bound outside tolerance", k, g["lb"], o.lb)
+            assert abs(g["lb"] - o.lb) <= 5e-2 * (1 + abs(o.lb)), (k, g["lb"], o.lb)
+            return k, flagged + 1
+        if abs(o.lb) <= band:
+            flagged += 1   # margin inside the tolerance band: verdict may differ
+            return k, flagged
+        assert g["verdict"] == o.verdict, (k, g, o)
+        gs = (g["split_layer"], g["split_neuron"]) if g["split_layer"] > 0 else None
+        if gs != o.split:
+            return k, flagged + 1   # tie-band divergence: trees differ from here on
+    return n, flagged

@@ -4,8 +4,10 @@ the FP64 oracle, through the C ABI."""
 import numpy as np
 import pytest
 
-from helpers import TOL, close, concat, conv_case, fc_case, gpu_property, random_node, to_params
-from oracle import core
+import synth
+from helpers import (TOL, close, compare_trace, concat, conv_case, fc_case, gpu_property,
+                     random_node, run_gpu_bab, to_params)
+from oracle import bab, core
 
 pytestmark = pytest.mark.gpu
 
@@ -107,3 +109,39 @@ def test_optimized_intermediate_refuses_constraints(Context):
             ctx.optimize_intermediate([gid])
         after = ctx.export_params(gid)
         assert np.array_equal(before.l, after.l) and np.array_equal(before.u, after.u)
+
+
+def test_root_intermediate_steps_in_bab_match_oracle(Context):
+    """Properties set to optimise their root's intermediate bounds: the GPU's
+    root bounds match the oracle's optimised root bounds, and the BaB trace
+    matches the oracle's verify(inter_steps=20) node by node, under the same
+    trace rules as the plain BaB parity test."""
+    layers = synth.make_network(0)
+    eps = synth.load_eps(0)
+    prs = synth.make_properties(0, layers, n=2, eps=eps, start=50)
+    budget = 16
+    matched = 0
+    with Context(node_capacity=4096) as ctx:
+        for pr in prs:
+            prep = bab.prepare(layers, pr.C, pr.d, pr.lo, pr.hi)
+            net, lo_t, hi_t, l, u, S, m, dense = prep
+            root = bab.root_node(net, 0, l, u, S, None)
+            core.optimize_intermediate(net, root, lo_t, hi_t, core.AdamHP())
+            gnet, prop = gpu_property(ctx, layers, pr.lo, pr.hi, pr.C, pr.d)
+            ctx.set_intermediate_steps(prop, 20)
+            ctx.set_budget(prop, budget)
+            for i in range(1, net.R + 1):
+                gl, gu = ctx.root_bounds(prop, i)
+                assert close(gl, root.l[i].numpy()).all(), f"layer {i} lower root bounds"
+                assert close(gu, root.u[i].numpy()).all(), f"layer {i} upper root bounds"
+            ores = bab.verify(layers, pr.C, pr.d, pr.lo, pr.hi, max_nodes=budget, prepared=prep,
+                              inter_steps=20)
+            run_gpu_bab(ctx, [prop], max_nodes=1)
+            k, flagged = compare_trace(ctx.trace(prop), ores)
+            matched += k
+            if flagged == 0 and k == len(ores.nodes):
+                v, _, _ = ctx.verdict(prop)
+                assert v == ores.verdict
+        with pytest.raises(Exception):
+            ctx.set_intermediate_steps(prop, 5)   # already started
+    assert matched >= 16

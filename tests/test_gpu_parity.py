@@ -11,8 +11,8 @@ import pytest
 import torch
 
 import synth
-from helpers import (TOL, close, concat, conv_case, convbig_spec, fc_case, f32, gpu_property,
-                     random_node, resnet_spec, to_params)
+from helpers import (TOL, close, compare_trace, concat, conv_case, convbig_spec, fc_case, f32,
+                     gpu_property, random_node, resnet_spec, run_gpu_bab, to_params)
 from oracle import bab, core, mnc
 
 pytestmark = pytest.mark.gpu
@@ -267,41 +267,6 @@ def test_acs_choice_matches_oracle(Context, cab):
 # --------------------------------------------------------------------------
 # branch and bound: node-by-node trace against the oracle
 # --------------------------------------------------------------------------
-def _run_gpu_bab(ctx, props, max_nodes, steps=20):
-    for _ in range(10000):
-        st = ctx.bab_step(props, max_nodes=max_nodes, steps=steps)
-        if st["nodes_bounded"] == 0:
-            break
-
-
-def _compare_trace(gtr, ores, max_cmp=None):
-    """Node-by-node agreement up to the first flagged divergence.
-
-    Roots (one optimisation from identical state) must match within TOL.  A
-    child inherits its parent's FP32 parameters, and the piecewise Adam
-    trajectory can amplify rounding differences (the FP64 oracle run in FP32
-    does the same), so the first child outside TOL flags the property and
-    ends the comparison; its bound must still agree within 5e-2."""
-    flagged = 0
-    n = min(len(gtr), len(ores.nodes)) if max_cmp is None else min(max_cmp, len(gtr), len(ores.nodes))
-    for k in range(n):
-        g, o = gtr[k], ores.nodes[k]
-        assert g["seq"] == o.node_id and g["row"] == o.row, (k, g, o)
-        band = TOL * (1 + abs(o.lb))
-        if abs(g["lb"] - o.lb) > band:
-            assert o.depth > 0, ("root bound outside tolerance", k, g["lb"], o.lb)
-            assert abs(g["lb"] - o.lb) <= 5e-2 * (1 + abs(o.lb)), (k, g["lb"], o.lb)
-            return k, flagged + 1
-        if abs(o.lb) <= band:
-            flagged += 1   # margin inside the tolerance band: verdict may differ
-            return k, flagged
-        assert g["verdict"] == o.verdict, (k, g, o)
-        gs = (g["split_layer"], g["split_neuron"]) if g["split_layer"] > 0 else None
-        if gs != o.split:
-            return k, flagged + 1   # tie-band divergence: trees differ from here on
-    return n, flagged
-
-
 def test_bab_trace_matches_oracle_fc_with_mnc(Context):
     layers = synth.make_network(0)
     eps = synth.load_eps(0)
@@ -314,9 +279,9 @@ def test_bab_trace_matches_oracle_fc_with_mnc(Context):
             ores = bab.verify(layers, pr.C, pr.d, pr.lo, pr.hi, max_nodes=budget, prepared=prep)
             gnet, prop = gpu_property(ctx, layers, pr.lo, pr.hi, pr.C, pr.d, prep[6])
             ctx.set_budget(prop, budget)
-            _run_gpu_bab(ctx, [prop], max_nodes=1)
+            run_gpu_bab(ctx, [prop], max_nodes=1)
             gtr = ctx.trace(prop)
-            k, flagged = _compare_trace(gtr, ores)
+            k, flagged = compare_trace(gtr, ores)
             matched += k
             if flagged == 0 and k == len(ores.nodes):
                 v, _, _ = ctx.verdict(prop)
@@ -339,7 +304,7 @@ def test_batched_equals_one_node_per_launch(Context):
                 p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
                 ctx.set_budget(p, 24)
                 props.append(p)
-            _run_gpu_bab(ctx, props, max_nodes=max_nodes, steps=5)
+            run_gpu_bab(ctx, props, max_nodes=max_nodes, steps=5)
             traces.append([ctx.trace(p) for p in props])
     for ta, tb in zip(*traces):
         n = min(len(ta), len(tb))
@@ -365,7 +330,7 @@ def test_conv_full_size_sampled(Context):
         # property 0 against the oracle, node by node (roots and first children)
         ores = bab.verify(layers, prs[0].C, prs[0].d, prs[0].lo, prs[0].hi, max_nodes=12)
         gtr = ctx.trace(props[0])
-        k, flagged = _compare_trace(gtr, ores, max_cmp=12)
+        k, flagged = compare_trace(gtr, ores, max_cmp=12)
         assert k + flagged >= min(9, len(ores.nodes))
         # soundness of root bounds at sampled inputs, counterexamples confirmed in FP64
         rng = np.random.default_rng(0)
@@ -489,6 +454,6 @@ def test_bab_trace_matches_oracle_resnet(Context):
     with Context(node_capacity=1024) as ctx:
         gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
         ctx.set_budget(prop, 14)
-        _run_gpu_bab(ctx, [prop], max_nodes=1)
-        k, flagged = _compare_trace(ctx.trace(prop), ores)
+        run_gpu_bab(ctx, [prop], max_nodes=1)
+        k, flagged = compare_trace(ctx.trace(prop), ores)
         assert k + flagged >= min(8, len(ores.nodes))
