@@ -100,6 +100,10 @@ struct mnbab_net {
   float *iga = nullptr, *igb = nullptr, *ibest = nullptr;
   int *iorig = nullptr, *iseg = nullptr, *isrc = nullptr, *idst = nullptr;
   size_t iseg_cap = 0;
+  // per-row a' checkpoints and gradients [icap][SD] of longer row chunks than
+  // the batch buffers hold (null when icap = B: the batch buffers serve)
+  float *iap = nullptr, *igar = nullptr, *igbr = nullptr;
+  int icap = 0;
 };
 
 struct mnbab_prop {
@@ -1103,16 +1107,46 @@ int64_t optimize_intermediate_impl(mnbab_net* n, const std::vector<int>& slots, 
   mnbab_ctx* c = n->ctx;
   const int nn = (int)slots.size();
   const int SD = n->SD, R = n->R;
-  const int CH = std::max(1, std::min(n->B, n->chunk));  // rows per sweep and adjoint
   if (!n->iga) {
+    // rows per sweep and adjoint: the batch capacity, or more where the
+    // call's own per-row buffers fit in about 1 GB (an eighth of the free
+    // budget at most); fewer, longer chunks mean fewer launches per step
+    const size_t room = std::min<size_t>(1ull << 30, (c->budget - c->used) / 8);
+    const size_t fit = std::min(room / (12 * (size_t)SD), (size_t)n->chunk);
+    n->icap = n->B;
+    if (fit > (size_t)n->B) {
+      n->icap = (int)fit;
+      n->iap = dalloc_t<float>(c, fit * SD);
+      n->igar = dalloc_t<float>(c, fit * SD);
+      n->igbr = dalloc_t<float>(c, fit * SD);
+    }
     n->iga = dalloc_t<float>(c, (size_t)n->B * SD);
     n->igb = dalloc_t<float>(c, (size_t)n->B * SD);
     n->ibest = dalloc_t<float>(c, n->rows_cap);
     n->iorig = dalloc_t<int>(c, n->rows_cap);
     n->isrc = dalloc_t<int>(c, n->B);
     n->idst = dalloc_t<int>(c, n->B);
-    n->iseg_cap = 3 * ((size_t)n->B + n->rows_cap / CH + 2);
+    n->iseg_cap = 3 * ((size_t)n->B + n->rows_cap / std::min(n->icap, n->chunk) + 2);
     n->iseg = dalloc_t<int>(c, n->iseg_cap);
+  }
+  const int CH = std::max(1, std::min(n->icap, n->chunk));
+  // the sweeps and adjoints of this call use the per-row buffers above (and
+  // read each row's slot from bslots); restored on every exit
+  struct Swap {
+    mnbab_net* n;
+    float *ap, *ga, *gb;
+    int* bs;
+    ~Swap() {
+      n->AP = ap;
+      n->GA = ga;
+      n->GB = gb;
+      n->bslots = bs;
+    }
+  } swap{n, n->AP, n->GA, n->GB, n->bslots};
+  if (n->iap) {
+    n->AP = n->iap;
+    n->GA = n->igar;
+    n->GB = n->igbr;
   }
   struct Scratch {
     mnbab_net* n;
@@ -1210,15 +1244,8 @@ int64_t optimize_intermediate_impl(mnbab_net* n, const std::vector<int>& slots, 
         }
         if (!grad) continue;
         // the adjoint reads each row's slot from bslots: point it at the chunk's rows
-        int* keep = n->bslots;
         n->bslots = n->row_node + c0;
-        try {
-          adjoint(n, Mc, false, t - 1);
-        } catch (...) {
-          n->bslots = keep;
-          throw;
-        }
-        n->bslots = keep;
+        adjoint(n, Mc, false, t - 1);
         const int ns = seg_at[ci + 1] - seg_at[ci];
         Scope sc(c, C_ADAM, 0.0, 8.0 * (double)Mc * off + 16.0 * ns * off);
         launch_set_grad(ns, n->iseg + 3 * seg_at[ci], SD, off, n->GA, n->GB, n->iga, n->igb,

@@ -29,18 +29,20 @@ def _case(kind):
     return conv_case(5, 0.05)
 
 
+@pytest.mark.parametrize("row_chunk", [0, 38])
 @pytest.mark.parametrize("kind", ["fc", "conv"])
-def test_optimized_intermediate_bounds_match_oracle(Context, kind):
+def test_optimized_intermediate_bounds_match_oracle(Context, kind, row_chunk):
     """Root and split nodes (float32 start values shared by both sides): after
     20 Adam steps per set, every neuron's bounds match the oracle's within
     1e-4 (1 + |b|), the row counts agree exactly, and the nodes' own
-    parameters are left as they were."""
+    parameters are left as they were.  With row_chunk = 38 the rows run in
+    chunks of 38, so sets span chunk boundaries and the last chunk is ragged."""
     layers, C, d, lo, hi, prep = _case(kind)
     net, lo_t, hi_t, l, u, S, m, dense = prep
     R = net.R
     assert R >= 3
     rng = np.random.default_rng(21)
-    with Context(node_capacity=64) as ctx:
+    with Context(node_capacity=64, row_chunk=row_chunk) as ctx:
         gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
         onodes, gids = [], []
         for k in range(4):
