@@ -188,3 +188,25 @@ def test_linear_set_objective_reaches_its_corner():
         assert bool((got <= torch.maximum(r0, r1) + 1e-12).all())
     # the corner values differ, so the optimum is a real choice
     assert not torch.allclose(best[1][0].sum(), best[1][1].sum())
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_zero_steps_reproduce_deeppoly_root_bounds(seed):
+    """With no Adam step the only iterate is the start point, DeepPoly slopes
+    and beta = 0 (Sec. 3.1 start point), so the root's bounds must stay the
+    DeepPoly root bounds (same rows, same relaxation) to rounding."""
+    prep, lo, hi = _case(seed)
+    net, lo_t, hi_t, l, u, S = prep[0], prep[1], prep[2], prep[3], prep[4], prep[5]
+    node = bab.root_node(net, 0, l, u, S, None)
+    # widen the unstable neurons' bounds of layers >= 2 (they stay unstable), so
+    # that only a recomputation equal to DeepPoly's restores them
+    for i in range(2, net.R + 1):
+        unst = (l[i] < 0) & (u[i] > 0)
+        span = (u[i] - l[i]) + 1.0
+        node.l[i] = torch.where(unst, l[i] - span, l[i])
+        node.u[i] = torch.where(unst, u[i] + span, u[i])
+    rows = core.optimize_intermediate(net, node, lo_t, hi_t, core.AdamHP(steps=0))
+    assert rows > 0
+    for i in range(1, net.R + 1):
+        assert torch.allclose(node.l[i], l[i], rtol=0, atol=1e-12), f"layer {i} lower"
+        assert torch.allclose(node.u[i], u[i], rtol=0, atol=1e-12), f"layer {i} upper"
