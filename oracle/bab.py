@@ -50,6 +50,11 @@ class NodeResult:
     fallback: bool = False
     split_layer: int = 0
     depth: int = 0
+    # with verify(..., conditioning=True): the node bound with the same
+    # optimisation carried out in float32 (core.optimize_in), and the branching
+    # scores {layer: tensor} the split was chosen from
+    lb_f32: float | None = None
+    scores: dict | None = None
 
 
 @dataclass
@@ -77,16 +82,20 @@ def root_node(net, row, l, u, S, mnc, node_id=0) -> Node:
                 split_layer=net.R, depth=0, node_id=node_id)
 
 
-def bound_node(net, node: Node, dense, lo, hi, hp: AdamHP):
-    """Steps 1-4 above; returns (NodeResult, final params, a' at final params)."""
+def bound_node(net, node: Node, dense, lo, hi, hp: AdamHP, conditioning=False):
+    """Steps 1-4 above; returns (NodeResult, final params).  With
+    ``conditioning`` the optimisation is also run in float32 (lb_f32)."""
     core.rebound_node(net, node, lo, hi)
     lb_dp, xs_dp = core.deeppoly_final(net, node, lo, hi)
     lb_dp = float(lb_dp)
     params = (node.alpha, node.beta, node.gamma)
-    aps = None
+    lb32 = None
     if lb_dp > 0:
         lb, xs = lb_dp, xs_dp
+        lb32 = lb_dp
     else:
+        if conditioning:
+            lb32 = max(lb_dp, core.optimize_in(torch.float32, net, node, dense, lo, hi, hp))
         best, bx, a, b, g = core.optimize(net, node, dense, lo, hi, hp)
         params = (a, b, g)
         if best > lb_dp:
@@ -101,7 +110,7 @@ def bound_node(net, node: Node, dense, lo, hi, hp: AdamHP):
     else:
         verdict = UNKNOWN
     res = NodeResult(node.node_id, node.row, lb, lb_dp, f, xs.numpy(), verdict,
-                     split_layer=node.split_layer, depth=node.depth)
+                     split_layer=node.split_layer, depth=node.depth, lb_f32=lb32)
     return res, params
 
 
@@ -113,7 +122,7 @@ def branch(net, node: Node, params, dense, lo, hi, cab=None):
     scores, fb = core.acs_scores(node, g, dense, aps)
     if cab is not None:
         scores = core.cab_scores(scores, cab)
-    return core.pick_split(scores), fb
+    return core.pick_split(scores), fb, scores
 
 
 def children(node: Node, params, split, next_id: int):
@@ -139,12 +148,15 @@ def children(node: Node, params, split, next_id: int):
 
 
 def verify(layers, C, d, lo, hi, max_nodes=256, hp: AdamHP | None = None, mnc_fn=None,
-           rows=None, prepared=None, cab=False, inter_steps=0) -> PropResult:
+           rows=None, prepared=None, cab=False, inter_steps=0,
+           conditioning=False) -> PropResult:
     """BaB on every row of one property; verdict VERIFIED / FALSIFIED / UNKNOWN.
     With ``cab`` the split is chosen by the cost-adjusted ACS score.  With
     ``inter_steps`` > 0 the root's intermediate bounds are first optimised
     (``core.optimize_intermediate``, Sec. 3.1 parameter sharing, that many Adam
-    steps at hp's rates) and shared by every row's root node."""
+    steps at hp's rates) and shared by every row's root node.  With
+    ``conditioning`` every node result also carries its float32 re-run and its
+    branching scores (for the parity tests)."""
     hp = hp or AdamHP()
     net, lo_t, hi_t, l, u, S, mnc, dense = prepared or prepare(layers, C, d, lo, hi, mnc_fn)
     if inter_steps > 0:
@@ -163,11 +175,13 @@ def verify(layers, C, d, lo, hi, max_nodes=256, hp: AdamHP | None = None, mnc_fn
     unknown_leaf = False
     while q and res.n_bounded < max_nodes:
         node = q.popleft()
-        nr, params = bound_node(net, node, dense, lo_t, hi_t, hp)
+        nr, params = bound_node(net, node, dense, lo_t, hi_t, hp, conditioning)
         res.n_bounded += 1
         if nr.verdict == UNKNOWN:
-            split, fb = branch(net, node, params, dense, lo_t, hi_t, costs)
+            split, fb, scores = branch(net, node, params, dense, lo_t, hi_t, costs)
             nr.fallback = fb
+            if conditioning:
+                nr.scores = scores
             if split is None:
                 unknown_leaf = True
             else:

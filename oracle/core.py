@@ -444,7 +444,8 @@ def deeppoly_final(net: Net, node: Node, lo, hi):
 class AdamHP:
     """Projected Adam ascent (Sec. 3.1, projected gradient ascent).  The paper
     names no optimiser or step sizes: parity unpinned, values are this
-    project's choice."""
+    project's choice.  The defaults are standard Adam (eps = 1e-8 in the
+    denominator) with a projection after every step."""
     steps: int = 20
     lr_alpha: float = 0.1
     lr_beta: float = 0.05
@@ -452,13 +453,14 @@ class AdamHP:
     b1: float = 0.9
     b2: float = 0.999
     eps: float = 1e-8
-    # Adam's denominator uses eps_eff = max(eps, eps_rel * G) with G the node's
-    # largest |gradient component|.  Constraints that are tight at the relaxed
-    # point have gradients at rounding level; with a fixed tiny eps, Adam's
-    # per-component normalisation turns that noise into full steps of random
-    # sign.  Scaling eps with G keeps the update continuous in the gradient.
-    eps_rel: float = 1e-3
-    # optional hard dead-zone: components with |g| <= grad_floor * G count as 0
+    # Two named options, both off by default.  With G the node's largest
+    # |gradient component|: eps_rel > 0 makes the denominator use
+    # max(eps, eps_rel * G); grad_floor > 0 counts components with
+    # |g| <= grad_floor * G as zero.  Constraints that are tight at the relaxed
+    # point have gradients at rounding level, which standard Adam's
+    # per-component normalisation turns into full steps of arbitrary sign;
+    # eps_rel keeps the update continuous in the gradient instead.
+    eps_rel: float = 0.0
     grad_floor: float = 0.0
 
 
@@ -520,6 +522,38 @@ def optimize(net, node: Node, dense_mnc, lo, hi, hp: AdamHP):
                 else:
                     P[i] = torch.clamp(P[i], min=0.0)
     return best, best_x, alpha, beta, gamma
+
+
+def cast_net(net: Net, dt) -> Net:
+    """The same network with weights and biases in dtype ``dt``."""
+    edges = [[]] + [[(s, Affine(A.kind, A.W.to(dt), A.b.to(dt), A.stride, A.pad, A.in_shape,
+                                A.out_shape)) for s, A in net.edges[t]]
+                    for t in range(1, len(net.edges))]
+    return Net(edges)
+
+
+def optimize_in(dt, net, node: Node, dense_mnc, lo, hi, hp: AdamHP) -> float:
+    """The best bound of ``optimize`` run with every tensor in dtype ``dt``.
+
+    Used only to decide whether a node's optimised bound is determined to the
+    parity tolerance at a given precision: with dt = float32 this is the same
+    plain iteration carried out in the arithmetic of the GPU path (different
+    rounding of every sum), so a gap to the float64 run measures how strongly
+    the Adam trajectory amplifies rounding at this node.
+    """
+    global DT
+    keep = DT
+    try:
+        DT = dt
+        c = lambda d: {i: d[i].to(dt) if d[i].is_floating_point() else d[i].clone() for i in d}
+        nd = Node(node.row, c(node.l), c(node.u), {i: node.S[i].clone() for i in node.S},
+                  c(node.alpha), c(node.beta), c(node.gamma), node.split_layer, node.depth,
+                  node.node_id)
+        dm = {i: tuple(x.to(dt) for x in dense_mnc[i]) for i in dense_mnc} if dense_mnc else None
+        best, *_ = optimize(cast_net(net, dt), nd, dm, lo.to(dt), hi.to(dt), hp)
+        return float(best)
+    finally:
+        DT = keep
 
 
 # ----------------------------------------------------------------------------

@@ -107,6 +107,43 @@ def test_relu_table_positive_coefficient():
     assert float(a[1][0]) == 0.0
 
 
+@pytest.mark.parametrize("sign", [1, -1])
+def test_standard_adam_closed_form(sign):
+    """Projected Adam (Sec. 3.1, projected gradient ascent) on a split neuron.
+
+    f = relu(x), x in [0.5, 1]; the neuron is split with S = sign.  Then
+    ahat = D + beta S (D = 0 for S = +1, 1 for S = -1) and
+    lb(beta) = min_x (D + beta S) x, whose gradient is constant in beta >= 0:
+    +lo = 0.5 for S = +1 (x* = lo) and -lo for S = -1.
+    With a constant gradient g, bias-corrected Adam has m_hat = g and
+    v_hat = g^2 at every step, so each step is exactly lr g / (|g| + eps):
+    three steps give beta = 3 lr g / (|g| + 1e-8) for S = +1 (the gradient-
+    scaled eps option would give 3 lr / 1.001; no bias correction a first step
+    3x larger), and for S = -1 the projection keeps beta at 0."""
+    L = _one_neuron(1.0, 0.0)
+    net, lo, hi, l, u, S, m, dense = bab.prepare(L, [[1.0]], [0.0], [0.5], [1.0])
+    node = bab.root_node(net, 0, l, u, S, None)
+    node.S[1][0] = sign
+    if sign == 1:
+        node.u[1][0] = 0.0
+    hp = core.AdamHP(steps=3)
+    best, _, _, beta, _ = core.optimize(net, node, None, lo, hi, hp)
+    if sign == 1:
+        g = 0.5
+        expect = 3 * hp.lr_beta * g / (g + 1e-8)
+        assert float(beta[1][0]) == pytest.approx(expect, rel=1e-14)
+        assert best == pytest.approx(0.5 * expect, rel=1e-14)
+        assert abs(float(beta[1][0]) - 3 * hp.lr_beta / 1.001) > 1e-4
+    else:
+        assert float(beta[1][0]) == 0.0
+        assert best == pytest.approx(0.5, abs=1e-15)
+    # the named option changes exactly the denominator
+    _, _, _, beta_r, _ = core.optimize(net, node, None, lo, hi, core.AdamHP(steps=3, eps_rel=1e-3))
+    if sign == 1:
+        assert float(beta_r[1][0]) == pytest.approx(3 * hp.lr_beta * 0.5 / (0.5 + 0.5e-3),
+                                                    rel=1e-12)
+
+
 def test_relu_table_negative_coefficient():
     """f = -2 relu(x) + 5, x in [-1, 2]: the upper line u/(u-l)(x - l) with
     intercept -ul/(u-l) = 2/3 gives the exact minimum 1."""
