@@ -178,18 +178,63 @@ def dominant(stats):
     return max(kern.items(), key=lambda kv: kv[1]["ms"])
 
 
-def roofline(stats, peaks, src, kernels_hash):
-    """Dominant kernel class (largest summed launch time) against its roofline."""
+CONTRACTIONS = ("backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm", "forward_conv",
+                "opt_fused_chain", "backsub_conv_window", "backsub_rows_fused")
+
+
+def tf32x3_peak(peaks, src):
+    """3xTF32 tensor peak: a measured dense TF32 rate / 3 when the peaks file
+    has one, else the measured dense BF16 burst rate x the nominal TF32:BF16
+    ratio 1/2, / 3 (three TF32 products per FP32-accurate product)."""
+    if "tf32_tflops" in peaks:
+        return peaks["tf32_tflops"] / 3.0, f"{src}: MEASURED_PEAKS tf32_tflops / 3"
+    return (peaks["bf16_tflops"] / 2.0 / 3.0,
+            f"derived from {src} bf16_tflops {peaks['bf16_tflops']}: x 1/2 (nominal TF32:BF16) "
+            f"/ 3 (3xTF32 split products)")
+
+
+def chain_macs(layers):
+    """(C, d_R): MACs of one back-substitution row through every affine layer
+    below the objective, and the width of the last ReLU layer."""
+    C, dR = 0.0, 0
+    for L in layers[:-1]:
+        if L["kind"] == "fc":
+            C += L["W"].shape[0] * L["W"].shape[1]
+            dR = L["W"].shape[0]
+        elif L["kind"] == "conv":
+            co, ho, wo = L["out_shape"]
+            C += co * ho * wo * L["W"].shape[1] * L["W"].shape[2] * L["W"].shape[3]
+            dR = co * ho * wo
+    return C, dR
+
+
+def roofline(stats, peaks, src, kernels_hash, layers=None, adam_steps=ADAM_STEPS):
+    """Dominant kernel class (largest summed launch time) against its roofline.
+
+    Back-substitution and adjoint contractions are tensor-core work by the
+    method's shape (dense Lambda W products), so they are measured against the
+    3xTF32 peak whether or not the kernel uses the tensor pipe; their SIMT FP32
+    fraction is reported beside it.  The other classes are HBM-bound."""
     name, st = dominant(stats)
     per_launch_ms = st["ms"] / max(1, st["launches"])
-    simt = name in ("backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm", "forward_conv",
-                    "opt_fused_chain", "backsub_conv_window", "backsub_rows_fused")
-    if simt:
-        # SIMT FP32 FMA: 152 SMs x 128 lanes x 2 flop per cycle at the maximum SM clock
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        ach = st["flops"] / (st["ms"] * 1e-3) / 1e12
-        r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    ach_flops = st["flops"] / (st["ms"] * 1e-3) / 1e12
+    if name in CONTRACTIONS:
+        peak, psrc = tf32x3_peak(peaks, src)
+        r = {"bound": "tensor_3xtf32", "achieved": ach_flops, "peak": peak, "unit": "TFLOP/s",
+             "peak_source": psrc}
+        simt = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        r["simt_fp32"] = {"peak": simt, "frac": ach_flops / simt,
+                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+        if name == "opt_fused_chain" and layers is not None:
+            # the library counts (steps + 1) back-substitution sweeps and steps
+            # adjoint passes (one forward pass of the relaxed network each);
+            # the survey's count is a sweep plus a two-sweep adjoint per step
+            C, dR = chain_macs(layers)
+            ours = (adam_steps + 1) * (C + dR) + adam_steps * C
+            survey = 3.0 * adam_steps * C
+            a2 = ach_flops * survey / ours
+            r["survey_count"] = {"achieved": a2, "frac": a2 / peak,
+                                 "flops_per_row": 2.0 * survey, "library_flops_per_row": 2.0 * ours}
     else:
         peak = peaks["hbm_gbs"]
         ach = st["bytes"] / (st["ms"] * 1e-3) / 1e9
@@ -442,7 +487,7 @@ def run_ours(args):
         finally:
             sctx.close()
     peaks, src = load_peaks()
-    roof = roofline(stats, peaks, src, kernels_sha())
+    roof = roofline(stats, peaks, src, kernels_sha(), layers=layers)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)

@@ -101,13 +101,17 @@ typedef struct {
   int32_t steps;   /* gradient steps; the bound is evaluated steps + 1 times */
   float lr_alpha, lr_beta, lr_gamma;
   float beta1, beta2, eps;
-  /* optional dead-zone: components with |g| <= grad_floor * G count as zero,
-   * G = max_j |g_j| over all of a node's parameters; default 0 (off) */
+  /* Optional, off by default (0 gives standard projected Adam):
+   * grad_floor: components with |g| <= grad_floor * G count as zero;
+   * eps_rel: Adam's denominator uses max(eps, eps_rel * G) instead of eps;
+   * with G = max_j |g_j| over all of a node's parameters.  Constraints that
+   * are tight at the relaxed point have gradients at rounding level; with the
+   * fixed eps, Adam's per-component normalisation turns that noise into steps
+   * of full size and random sign, so FP32 and FP64 runs of the same
+   * optimisation can part by more than 1e-3.  eps_rel = 1e-3 keeps the update
+   * continuous in the gradient (the runs then agree to about 1e-6); it is not
+   * the paper's optimiser, which names only projected gradient ascent. */
   float grad_floor;
-  /* Adam's denominator uses max(eps, eps_rel * G); default 1e-3.  Constraints
-   * tight at the relaxed point have gradients at rounding level, and with a
-   * fixed tiny eps the per-component normalisation turns that noise into full
-   * steps of random sign; scaling eps with G keeps the update continuous. */
   float eps_rel;
 } mnbab_adam;
 
@@ -225,6 +229,14 @@ mnbab_status mnbab_deeppoly_batch(mnbab_ctx* ctx, const mnbab_node_id* nodes, in
 mnbab_status mnbab_bound_grad(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
                               float* lb_out, float* grad_out);
 
+/* Sets the parameters of each node from params, laid out as grad_out of
+ * mnbab_bound_grad: per node alpha[SD], beta[SD], gamma[E] (host floats).  The
+ * values are taken as given: a bound is sound only for 0 <= alpha <= 1 and
+ * beta, gamma >= 0 (Sec. 3.1), so callers that step the parameters project
+ * them.  Bounds and splits of the nodes are unchanged. */
+mnbab_status mnbab_set_params(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
+                              const float* params);
+
 /* cfg->steps projected Adam steps from each node's current parameters
  * (alpha clamped to [0, 1], beta, gamma >= 0).  best_lb_out[i] = the best
  * bound over the steps + 1 evaluated iterates; the node keeps the last
@@ -243,11 +255,14 @@ mnbab_status mnbab_optimize(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t 
  * and the node's bounds of layer t are intersected with them before layer
  * t + 1.  Works on each node's current bounds (re-bound split nodes first,
  * e.g. with mnbab_bound_batch); the nodes' own parameters are unchanged.
- * At most half the context's batch capacity of nodes per call; properties
- * with multi-neuron constraints return MNBAB_E_UNSUPPORTED.  *rows_out
- * (nullable) receives the number of rows bounded.  Scratch node slots are
- * taken from the pool for the duration of the call (MNBAB_E_BUDGET if it is
- * full). */
+ * At most half the context's batch capacity of nodes per call, each listed
+ * once (a repeated node is MNBAB_E_INVALID_ARG); properties with multi-neuron
+ * constraints return MNBAB_E_UNSUPPORTED.  *rows_out (nullable) receives the
+ * number of rows bounded.  Scratch node slots are taken from the pool for the
+ * duration of the call (MNBAB_E_BUDGET if it is full).  The rows of one layer
+ * (2 x unstable neurons x nodes) must fit the network's row scratch
+ * (min(2^26, 2 * SD * batch capacity) rows, at least row_chunk and 2 * SD);
+ * more is MNBAB_E_BUDGET with both counts in the message: pass fewer nodes. */
 mnbab_status mnbab_optimize_intermediate(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
                                          int32_t first_layer, const mnbab_adam* cfg,
                                          int64_t* rows_out);
@@ -256,9 +271,10 @@ mnbab_status mnbab_optimize_intermediate(mnbab_ctx* ctx, const mnbab_node_id* no
  * mnbab_optimize_intermediate with `steps` Adam steps at the default rates:
  * run when the property starts, after its DeepPoly root bounds and before its
  * root nodes take them; 0 (the default) keeps the DeepPoly root bounds.  Call
- * before the property starts (MNBAB_E_INVALID_ARG after); properties with
- * multi-neuron constraints return MNBAB_E_UNSUPPORTED (and mnbab_set_mnc
- * refuses a property with steps > 0). */
+ * before the property starts (MNBAB_E_INVALID_ARG after), on a context whose
+ * batch capacity is at least 2 (node_capacity >= 4; MNBAB_E_INVALID_ARG
+ * otherwise); properties with multi-neuron constraints return
+ * MNBAB_E_UNSUPPORTED (and mnbab_set_mnc refuses a property with steps > 0). */
 mnbab_status mnbab_set_intermediate_steps(mnbab_ctx* ctx, mnbab_prop* prop, int32_t steps);
 
 /* ACS branching score (Sec. 3.2) at each node's current parameters:
@@ -379,9 +395,8 @@ mnbab_status mnbab_queue_size(const mnbab_ctx* ctx, const mnbab_prop* prop, int3
 
 /* DeepPoly lower bounds of query rows of a fully connected ReLU network, for
  * callers that cannot allocate device memory (code running inside another
- * framework's memory pool or allocator hooks, code that must not allocate
- * while a stream capture is active, hosts whose device memory is partitioned
- * up front).  The paper has no counterpart: this is a deployment variant of
+ * framework's memory pool or allocator hooks, hosts whose device memory is
+ * partitioned up front).  The paper has no counterpart: this is a deployment variant of
  * the back-substitution sweep of mnbab_deeppoly_batch, with every scratch
  * buffer taken from a static device array of MNBAB_NOALLOC_SCRATCH_BYTES
  * (16 MiB) that each GPU loading the library holds until the process exits.

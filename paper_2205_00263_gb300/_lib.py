@@ -86,6 +86,7 @@ SIGNATURES = {
     "mnbab_bound_batch": (status, [VP, C.POINTER(node_id), C.c_int32, FP, FP]),
     "mnbab_deeppoly_batch": (status, [VP, C.POINTER(node_id), C.c_int32, FP]),
     "mnbab_bound_grad": (status, [VP, C.POINTER(node_id), C.c_int32, FP, FP]),
+    "mnbab_set_params": (status, [VP, C.POINTER(node_id), C.c_int32, FP]),
     "mnbab_optimize": (status, [VP, C.POINTER(node_id), C.c_int32, C.POINTER(Adam), FP]),
     "mnbab_optimize_intermediate": (status, [VP, C.POINTER(node_id), C.c_int32, C.c_int32,
                                              C.POINTER(Adam), C.POINTER(C.c_int64)]),

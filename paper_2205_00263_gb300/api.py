@@ -245,8 +245,15 @@ class Context:
         g = g.reshape(n, 2 * SD + E)
         return lb, g[:, :SD], g[:, SD:2 * SD], g[:, 2 * SD:]
 
+    def set_params(self, nodes, params):
+        """Writes each node's (alpha, beta, gamma) from one flat float array laid
+        out per node as alpha[SD], beta[SD], gamma[E] (mnbab_set_params)."""
+        ids, n = self._ids(nodes)
+        p = _f32(params).reshape(-1)
+        self._ck(self.lib.mnbab_set_params(self.h, ids, n, _fp(p)))
+
     def optimize(self, nodes, steps=20, lr_alpha=0.1, lr_beta=0.05, lr_gamma=0.05, beta1=0.9,
-                 beta2=0.999, eps=1e-8, grad_floor=0.0, eps_rel=1e-3):
+                 beta2=0.999, eps=1e-8, grad_floor=0.0, eps_rel=0.0):
         ids, n = self._ids(nodes)
         a = L.Adam(steps, lr_alpha, lr_beta, lr_gamma, beta1, beta2, eps, grad_floor, eps_rel)
         best = np.empty(n, np.float32)
@@ -258,7 +265,7 @@ class Context:
         self._ck(self.lib.mnbab_set_intermediate_steps(self.h, prop.h, steps))
 
     def optimize_intermediate(self, nodes, first_layer=2, steps=20, lr_alpha=0.1, lr_beta=0.05,
-                              beta1=0.9, beta2=0.999, eps=1e-8, grad_floor=0.0, eps_rel=1e-3):
+                              beta1=0.9, beta2=0.999, eps=1e-8, grad_floor=0.0, eps_rel=0.0):
         """Optimised intermediate bounds of the nodes (shared per-layer sets);
         returns the number of rows bounded."""
         ids, n = self._ids(nodes)
@@ -280,7 +287,7 @@ class Context:
     def bab_step(self, props, max_nodes: int, steps: int = 20, adam: dict | None = None):
         arr = (C.c_void_p * len(props))(*[p.h.value for p in props])
         a = L.Adam(steps, *(adam or {}).get("rates", (0.1, 0.05, 0.05, 0.9, 0.999, 1e-8, 0.0,
-                                                       1e-3)))
+                                                       0.0)))
         st = L.StepStats()
         self._ck(self.lib.mnbab_bab_step(self.h, arr, len(props), max_nodes, C.byref(a),
                                          C.byref(st)))
@@ -350,7 +357,7 @@ class Context:
         return t.value
 
     def serve_step(self, max_nodes: int, steps: int = 20):
-        a = L.Adam(steps, 0.1, 0.05, 0.05, 0.9, 0.999, 1e-8, 0.0, 1e-3)
+        a = L.Adam(steps, 0.1, 0.05, 0.05, 0.9, 0.999, 1e-8, 0.0, 0.0)
         st = L.ServeStats()
         self._ck(self.lib.mnbab_serve_step(self.h, max_nodes, C.byref(a), C.byref(st)))
         out = {k: getattr(st, k) for k, _ in L.ServeStats._fields_ if k != "step"}

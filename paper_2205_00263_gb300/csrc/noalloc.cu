@@ -1,9 +1,8 @@
 // Allocation-free DeepPoly bound for fully connected ReLU networks.
 //
 // Some callers cannot call cudaMalloc at all: code that runs inside another
-// framework's memory pool or allocator hooks, code that must not allocate
-// while a stream capture is active, or embedded hosts whose device memory is
-// partitioned up front.  For them, mnbab_deeppoly_fc_noalloc runs the same
+// framework's memory pool or allocator hooks, or embedded hosts whose device
+// memory is partitioned up front.  For them, mnbab_deeppoly_fc_noalloc runs the same
 // back-substitution kernels as mnbab_deeppoly_batch, but every scratch buffer
 // (the two coefficient buffers, the per-row partial sums, the row tables and
 // one property descriptor) is carved out of the file-scope array below, which

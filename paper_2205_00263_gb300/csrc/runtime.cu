@@ -878,7 +878,7 @@ mnbab_adam default_adam() {
   a.beta2 = 0.999f;
   a.eps = 1e-8f;
   a.grad_floor = 0.0f;
-  a.eps_rel = 1e-3f;
+  a.eps_rel = 0.0f;  // standard Adam; the gradient-scaled eps is an option
   return a;
 }
 
@@ -1200,7 +1200,11 @@ int64_t optimize_intermediate_impl(mnbab_net* n, const std::vector<int>& slots, 
     }
     const int M = (int)rnode.size(), nsets = (int)dst.size();
     if (M == 0) continue;
-    if ((size_t)M > n->rows_cap) fail(MNBAB_E_DEVICE, "row scratch too small");
+    if ((size_t)M > n->rows_cap)
+      fail(MNBAB_E_BUDGET, "layer " + std::to_string(t) + " needs " + std::to_string(M) +
+                               " intermediate-bound rows, more than the " +
+                               std::to_string(n->rows_cap) +
+                               "-row scratch of this network; pass fewer nodes per call");
     // per chunk of rows, the segments of its sets: (set, first row, end row)
     std::vector<int> seg, seg_at;
     for (int c0 = 0; c0 < M; c0 += CH) {
@@ -1308,7 +1312,10 @@ void ensure_roots(mnbab_net* n, mnbab_prop* const* only = nullptr, int n_only = 
   for (size_t i = 0; i < want.size();) {
     std::vector<int> grp;
     const int steps = want[i].first;
-    while (i < want.size() && want[i].first == steps && 2 * ((int)grp.size() + 1) <= n->B)
+    // two parameter sets (lower, upper) per root; at least one root per group
+    // so that the loop always advances (set_intermediate_steps refuses B < 2)
+    while (i < want.size() && want[i].first == steps &&
+           (grp.empty() || 2 * ((int)grp.size() + 1) <= n->B))
       grp.push_back(want[i++].second);
     mnbab_adam a = default_adam();
     a.steps = steps;
@@ -2125,6 +2132,28 @@ mnbab_status mnbab_deeppoly_batch(mnbab_ctx* c, const mnbab_node_id* nodes, int3
   API_END(c)
 }
 
+mnbab_status mnbab_set_params(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t nn,
+                              const float* params) {
+  API_BEGIN(c)
+  std::vector<int> slots;
+  mnbab_net* n = slots_of(c, nodes, nn, slots);
+  if (!params) fail(MNBAB_E_INVALID_ARG, "null parameter array");
+  const size_t SD = n->SD;
+  size_t at = 0;
+  for (int i = 0; i < nn; ++i) {
+    const int s = slots[i];
+    const int E = c->props[n->slot_prop[s]]->pd.E;
+    h2d(c, n->pool.ALPHA + (size_t)s * SD, params + at, SD);
+    at += SD;
+    h2d(c, n->pool.BETA + (size_t)s * SD, params + at, SD);
+    at += SD;
+    if (E) h2d(c, n->pool.GAM + (size_t)s * c->EC, params + at, E);
+    at += E;
+  }
+  sync(c);
+  API_END(c)
+}
+
 mnbab_status mnbab_bound_grad(mnbab_ctx* c, const mnbab_node_id* nodes, int32_t nn,
                               float* lb_out, float* grad_out) {
   API_BEGIN(c)
@@ -2187,6 +2216,13 @@ mnbab_status mnbab_optimize_intermediate(mnbab_ctx* c, const mnbab_node_id* node
   const mnbab_adam a = cfg ? *cfg : default_adam();
   if (a.steps < 0) fail(MNBAB_E_INVALID_ARG, "negative step count");
   if (2 * nn > n->B) fail(MNBAB_E_INVALID_ARG, "more nodes than half the batch capacity");
+  {
+    // two sets of one node would update the same bounds concurrently
+    std::vector<int> sorted(slots);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      fail(MNBAB_E_INVALID_ARG, "a node is listed twice");
+  }
   for (int s : slots)
     if (c->props[n->slot_prop[s]]->pd.E > 0)
       fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
@@ -2201,6 +2237,9 @@ mnbab_status mnbab_set_intermediate_steps(mnbab_ctx* c, mnbab_prop* p, int32_t s
   if (p->materialized) fail(MNBAB_E_INVALID_ARG, "property already started");
   if (steps > 0 && p->pd.E > 0)
     fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
+  if (steps > 0 && p->net->B < 2)
+    fail(MNBAB_E_INVALID_ARG,
+         "optimised intermediate bounds need a batch capacity of at least 2 (node_capacity >= 4)");
   p->inter_steps = steps;
   API_END(c)
 }

@@ -6,6 +6,7 @@ import pytest
 
 import synth
 from helpers import (TOL, close, compare_trace, concat, conv_case, fc_case, gpu_property,
+                     verdicts_consistent,
                      random_node, run_gpu_bab, to_params)
 from oracle import bab, core
 
@@ -137,13 +138,31 @@ def test_root_intermediate_steps_in_bab_match_oracle(Context):
                 assert close(gl, root.l[i].numpy()).all(), f"layer {i} lower root bounds"
                 assert close(gu, root.u[i].numpy()).all(), f"layer {i} upper root bounds"
             ores = bab.verify(layers, pr.C, pr.d, pr.lo, pr.hi, max_nodes=budget, prepared=prep,
-                              inter_steps=20)
+                              inter_steps=20, conditioning=True)
             run_gpu_bab(ctx, [prop], max_nodes=1)
-            k, flagged = compare_trace(ctx.trace(prop), ores)
+            k, why = compare_trace(ctx.trace(prop), ores)
             matched += k
-            if flagged == 0 and k == len(ores.nodes):
-                v, _, _ = ctx.verdict(prop)
+            v, _, _ = ctx.verdict(prop)
+            if why is None and k == len(ores.nodes):
                 assert v == ores.verdict
+            assert verdicts_consistent(v, ores.verdict)
         with pytest.raises(Exception):
             ctx.set_intermediate_steps(prop, 5)   # already started
     assert matched >= 16
+
+
+def test_small_pool_refuses_intermediate_steps(Context):
+    """A batch capacity of 1 (node_capacity 2) cannot hold a node's two
+    parameter sets: the root option is refused with an error (it used to loop),
+    and a node listed twice in one call is refused as well."""
+    from paper_2205_00263_gb300 import MnbabError
+    layers, C, d, lo, hi, prep = fc_case(31, (12, 9, 8, 4), 0.1)
+    with Context(node_capacity=2) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
+        with pytest.raises(MnbabError):
+            ctx.set_intermediate_steps(prop, 5)
+    with Context(node_capacity=64) as ctx:
+        gnet, prop = gpu_property(ctx, layers, lo, hi, C, d)
+        n0 = ctx.node_root(prop, 0)
+        with pytest.raises(MnbabError):
+            ctx.optimize_intermediate([n0, n0], steps=2)

@@ -2,8 +2,7 @@
 
 mnbab_deeppoly_fc_noalloc exists for callers that cannot allocate device
 memory themselves (code inside another framework's memory pool or allocator
-hooks, code that must not allocate during a stream capture, hosts with device
-memory partitioned up front).  It takes device pointers the caller already
+hooks, hosts with device memory partitioned up front).  It takes device pointers the caller already
 owns and keeps its scratch in a static device array.  This test computes the
 DeepPoly bounds of every property row once through a context
 (mnbab_deeppoly_batch on root nodes) and twice in a row through the
