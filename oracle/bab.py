@@ -24,6 +24,7 @@ project); every node bound is pinned through ``core``.
 """
 from __future__ import annotations
 
+import copy
 import math
 from collections import deque
 from dataclasses import dataclass, field, replace
@@ -50,11 +51,11 @@ class NodeResult:
     fallback: bool = False
     split_layer: int = 0
     depth: int = 0
-    # with verify(..., conditioning=True): the node bound with the same
-    # optimisation carried out in float32 (core.optimize_in), and the branching
-    # scores {layer: tensor} the split was chosen from
-    lb_f32: float | None = None
+    parent: int = -1
+    # with verify(..., record=True): the branching scores {layer: tensor} the
+    # split was chosen from, and the node as queued (before step 1)
     scores: dict | None = None
+    start: Node | None = None
 
 
 @dataclass
@@ -82,20 +83,15 @@ def root_node(net, row, l, u, S, mnc, node_id=0) -> Node:
                 split_layer=net.R, depth=0, node_id=node_id)
 
 
-def bound_node(net, node: Node, dense, lo, hi, hp: AdamHP, conditioning=False):
-    """Steps 1-4 above; returns (NodeResult, final params).  With
-    ``conditioning`` the optimisation is also run in float32 (lb_f32)."""
+def bound_node(net, node: Node, dense, lo, hi, hp: AdamHP):
+    """Steps 1-4 above; returns (NodeResult, final params)."""
     core.rebound_node(net, node, lo, hi)
     lb_dp, xs_dp = core.deeppoly_final(net, node, lo, hi)
     lb_dp = float(lb_dp)
     params = (node.alpha, node.beta, node.gamma)
-    lb32 = None
     if lb_dp > 0:
         lb, xs = lb_dp, xs_dp
-        lb32 = lb_dp
     else:
-        if conditioning:
-            lb32 = max(lb_dp, core.optimize_in(torch.float32, net, node, dense, lo, hi, hp))
         best, bx, a, b, g = core.optimize(net, node, dense, lo, hi, hp)
         params = (a, b, g)
         if best > lb_dp:
@@ -110,7 +106,7 @@ def bound_node(net, node: Node, dense, lo, hi, hp: AdamHP, conditioning=False):
     else:
         verdict = UNKNOWN
     res = NodeResult(node.node_id, node.row, lb, lb_dp, f, xs.numpy(), verdict,
-                     split_layer=node.split_layer, depth=node.depth, lb_f32=lb32)
+                     split_layer=node.split_layer, depth=node.depth, parent=node.parent)
     return res, params
 
 
@@ -143,20 +139,20 @@ def children(node: Node, params, split, next_id: int):
         out.append(Node(row=node.row, l=l, u=u, S=S,
                         alpha={i: a[i].clone() for i in a}, beta=beta,
                         gamma={i: g[i].clone() for i in g},
-                        split_layer=layer, depth=node.depth + 1, node_id=next_id + k))
+                        split_layer=layer, depth=node.depth + 1, node_id=next_id + k,
+                        parent=node.node_id))
     return out
 
 
 def verify(layers, C, d, lo, hi, max_nodes=256, hp: AdamHP | None = None, mnc_fn=None,
-           rows=None, prepared=None, cab=False, inter_steps=0,
-           conditioning=False) -> PropResult:
+           rows=None, prepared=None, cab=False, inter_steps=0, record=False) -> PropResult:
     """BaB on every row of one property; verdict VERIFIED / FALSIFIED / UNKNOWN.
     With ``cab`` the split is chosen by the cost-adjusted ACS score.  With
     ``inter_steps`` > 0 the root's intermediate bounds are first optimised
     (``core.optimize_intermediate``, Sec. 3.1 parameter sharing, that many Adam
-    steps at hp's rates) and shared by every row's root node.  With
-    ``conditioning`` every node result also carries its float32 re-run and its
-    branching scores (for the parity tests)."""
+    steps at hp's rates) and shared by every row's root node.  With ``record``
+    every node result also carries its starting state and its branching
+    scores (for the parity tests)."""
     hp = hp or AdamHP()
     net, lo_t, hi_t, l, u, S, mnc, dense = prepared or prepare(layers, C, d, lo, hi, mnc_fn)
     if inter_steps > 0:
@@ -175,12 +171,14 @@ def verify(layers, C, d, lo, hi, max_nodes=256, hp: AdamHP | None = None, mnc_fn
     unknown_leaf = False
     while q and res.n_bounded < max_nodes:
         node = q.popleft()
-        nr, params = bound_node(net, node, dense, lo_t, hi_t, hp, conditioning)
+        start = copy.deepcopy(node) if record else None
+        nr, params = bound_node(net, node, dense, lo_t, hi_t, hp)
+        nr.start = start
         res.n_bounded += 1
         if nr.verdict == UNKNOWN:
             split, fb, scores = branch(net, node, params, dense, lo_t, hi_t, costs)
             nr.fallback = fb
-            if conditioning:
+            if record:
                 nr.scores = scores
             if split is None:
                 unknown_leaf = True

@@ -374,6 +374,7 @@ class Node:
     split_layer: int            # ReLU layer of the newest split; R for a root
     depth: int = 0
     node_id: int = 0
+    parent: int = -1            # node id of the parent (-1 for a root)
 
 
 def init_params(net: Net, l, u, mnc: dict | None):
@@ -480,11 +481,17 @@ def bound_and_grad(net, node, alpha, beta, gamma, dense_mnc, lo, hi):
     return lb.detach(), xs.detach(), ga, gb, gg
 
 
-def optimize(net, node: Node, dense_mnc, lo, hi, hp: AdamHP):
+def optimize(net, node: Node, dense_mnc, lo, hi, hp: AdamHP, noise=None):
     """hp.steps projected Adam ascent steps from the node's inherited parameters.
 
     Evaluates the bound at theta_0 .. theta_N (N = hp.steps) and returns the
     best bound (first maximiser), its x*, and the final parameters theta_N.
+
+    ``noise = (seed, rel)`` is a test probe, not part of the method: every
+    gradient component that is computed as a sum (alpha of unstable unsplit
+    neurons, beta of split neurons, every gamma) gets an independent uniform
+    perturbation in [-rel G, rel G], G = the node's largest |component|, before
+    the Adam update -- a model of the rounding of an FP32 implementation.
     """
     alpha = {i: node.alpha[i].clone() for i in node.alpha}
     beta = {i: node.beta[i].clone() for i in node.beta}
@@ -503,6 +510,18 @@ def optimize(net, node: Node, dense_mnc, lo, hi, hp: AdamHP):
             break
         t = step + 1
         gmax = max([float(G[i].abs().max()) for G in (ga, gb, gg) for i in G if G[i].numel()] + [0.0])
+        if noise is not None:
+            gen = torch.Generator().manual_seed(noise[0] * 1000 + step)
+            for grp, G in (("a", ga), ("b", gb), ("g", gg)):
+                for i in G:
+                    if grp == "a":
+                        live = (node.l[i] < 0) & (node.u[i] > 0) & (node.S[i] == 0)
+                    elif grp == "b":
+                        live = node.S[i] != 0
+                    else:
+                        live = torch.ones_like(G[i], dtype=torch.bool)
+                    e = (torch.rand(G[i].shape, generator=gen, dtype=DT) * 2 - 1) * noise[1] * gmax
+                    G[i] = G[i] + torch.where(live, e, torch.zeros_like(e))
         floor = hp.grad_floor * gmax
         eps = max(hp.eps, hp.eps_rel * gmax)
         for G in (ga, gb, gg):
@@ -524,36 +543,28 @@ def optimize(net, node: Node, dense_mnc, lo, hi, hp: AdamHP):
     return best, best_x, alpha, beta, gamma
 
 
-def cast_net(net: Net, dt) -> Net:
-    """The same network with weights and biases in dtype ``dt``."""
-    edges = [[]] + [[(s, Affine(A.kind, A.W.to(dt), A.b.to(dt), A.stride, A.pad, A.in_shape,
-                                A.out_shape)) for s, A in net.edges[t]]
-                    for t in range(1, len(net.edges))]
-    return Net(edges)
-
-
-def optimize_in(dt, net, node: Node, dense_mnc, lo, hi, hp: AdamHP) -> float:
-    """The best bound of ``optimize`` run with every tensor in dtype ``dt``.
-
-    Used only to decide whether a node's optimised bound is determined to the
-    parity tolerance at a given precision: with dt = float32 this is the same
-    plain iteration carried out in the arithmetic of the GPU path (different
-    rounding of every sum), so a gap to the float64 run measures how strongly
-    the Adam trajectory amplifies rounding at this node.
-    """
-    global DT
-    keep = DT
-    try:
-        DT = dt
-        c = lambda d: {i: d[i].to(dt) if d[i].is_floating_point() else d[i].clone() for i in d}
-        nd = Node(node.row, c(node.l), c(node.u), {i: node.S[i].clone() for i in node.S},
-                  c(node.alpha), c(node.beta), c(node.gamma), node.split_layer, node.depth,
-                  node.node_id)
-        dm = {i: tuple(x.to(dt) for x in dense_mnc[i]) for i in dense_mnc} if dense_mnc else None
-        best, *_ = optimize(cast_net(net, dt), nd, dm, lo.to(dt), hi.to(dt), hp)
-        return float(best)
-    finally:
-        DT = keep
+def noise_sensitivity(net, node: Node, dense_mnc, lo, hi, hp: AdamHP, seeds=(1, 2, 3),
+                      rel=1e-6, always=False) -> float:
+    """How far the node's optimised bound moves when its gradients carry
+    rounding-level perturbations (``optimize(noise=...)``): the largest
+    |best_perturbed - best| over the seeds, 0 for a node its DeepPoly pass
+    verifies (no optimisation in BaB) unless ``always``.  ``node`` is the node as queued; it is not
+    changed.  A test probe: a bound that moves by more than a small part of the
+    parity tolerance is not determined at FP32 precision."""
+    nd = Node(node.row, {i: node.l[i].clone() for i in node.l},
+              {i: node.u[i].clone() for i in node.u}, {i: node.S[i].clone() for i in node.S},
+              node.alpha, node.beta, node.gamma, node.split_layer, node.depth, node.node_id)
+    rebound_node(net, nd, lo, hi)
+    lb_dp, _ = deeppoly_final(net, nd, lo, hi)
+    if float(lb_dp) > 0 and not always:
+        return 0.0
+    best, *_ = optimize(net, nd, dense_mnc, lo, hi, hp)
+    best = max(best, float(lb_dp))
+    dev = 0.0
+    for sd in seeds:
+        b, *_ = optimize(net, nd, dense_mnc, lo, hi, hp, noise=(sd, rel))
+        dev = max(dev, abs(max(b, float(lb_dp)) - best))
+    return dev
 
 
 # ----------------------------------------------------------------------------

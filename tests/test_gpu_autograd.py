@@ -82,8 +82,12 @@ def test_node_bound_gradient_fd_and_oracle(Context, case):
 
         h = 2e-2
         used = 0
+        lb0 = lb.detach().cpu().numpy()
         for k in range(len(gids)):
-            cand = np.nonzero(np.abs(G[k]) > 1e-3)[0]
+            # FP32 bounds resolve differences down to their spacing: use
+            # coordinates whose bound change over +-h spans >= 2000 spacings
+            ulp = float(np.spacing(np.float32(abs(lb0[k]) + 1.0)))
+            cand = np.nonzero(np.abs(G[k]) / (k + 1) * h >= 2000 * ulp)[0]
             for j in rng.choice(cand, size=min(12, cand.size), replace=False):
                 diffs = []
                 for hh in (h, h / 2):

@@ -6,7 +6,7 @@ import pytest
 
 import synth
 from helpers import (TOL, close, compare_trace, concat, conv_case, fc_case, gpu_property,
-                     verdicts_consistent,
+                     gpu_recompute, oracle_sensitivity, verdicts_consistent,
                      random_node, run_gpu_bab, to_params)
 from oracle import bab, core
 
@@ -138,9 +138,11 @@ def test_root_intermediate_steps_in_bab_match_oracle(Context):
                 assert close(gl, root.l[i].numpy()).all(), f"layer {i} lower root bounds"
                 assert close(gu, root.u[i].numpy()).all(), f"layer {i} upper root bounds"
             ores = bab.verify(layers, pr.C, pr.d, pr.lo, pr.hi, max_nodes=budget, prepared=prep,
-                              inter_steps=20, conditioning=True)
+                              inter_steps=20, record=True)
             run_gpu_bab(ctx, [prop], max_nodes=1)
-            k, why = compare_trace(ctx.trace(prop), ores)
+            k, why = compare_trace(ctx.trace(prop), ores,
+                                   recompute=gpu_recompute(ctx, prop, net.R),
+                                   sensitivity=oracle_sensitivity(prep))
             matched += k
             v, _, _ = ctx.verdict(prop)
             if why is None and k == len(ores.nodes):
