@@ -190,6 +190,47 @@ mnbab_status mnbab_set_mnc(mnbab_ctx* ctx, mnbab_prop* prop, int32_t relu_layer,
                            int32_t k, const int32_t* idx, const float* P, const float* Phat,
                            const float* p);
 
+/* Generates and uploads the multi-neuron constraints of every ReLU layer of a
+ * property (Sec. 3.1, enforcing multi-neuron constraints; the paper takes them
+ * from PRIMA and gives no generator).  This library's construction, from the
+ * property's DeepPoly root bounds (the property is started if it was not):
+ *  - groups: the unstable neurons of the layer in the order of decreasing
+ *    -l u / (u - l) (ties by index), taken as sliding triples (j0, j1, j2),
+ *    (j1, j2, j3), ..., at most max_groups per layer;
+ *  - per group, the DeepPoly lower bounds of d . zhat_G for the 26 directions
+ *    d in {-1, 0, 1}^3 \ {0}, back-substituted on the device;
+ *  - per group, on the host in FP64 (threads over groups), the facets of the
+ *    convex hull of the ReLU graph over that octahedron (mnbab_mnc_group),
+ *    uploaded as with mnbab_set_mnc.
+ * Every layer counts as set afterwards (mnbab_set_mnc then refuses it); call
+ * before bounding any node of the property.  *rows_out (nullable) receives
+ * the number of constraint rows.  MNBAB_E_BUDGET when the rows exceed
+ * mnbab_options.max_mnc_rows (the exact hull gives about 100 to 250 rows per
+ * group). */
+mnbab_status mnbab_generate_mnc(mnbab_ctx* ctx, mnbab_prop* prop, int32_t max_groups,
+                                int64_t* rows_out);
+
+/* Reads back the constraint rows of one ReLU layer of a property (as set by
+ * mnbab_set_mnc or mnbab_generate_mnc, k = 3 neurons a row): idx and P, Phat
+ * [max_rows][3], p [max_rows] (host); *n_out = the number of rows
+ * (MNBAB_E_BUDGET, with *n_out set, when it exceeds max_rows). */
+mnbab_status mnbab_get_mnc(mnbab_ctx* ctx, const mnbab_prop* prop, int32_t relu_layer,
+                           int32_t max_rows, int32_t* idx, float* P, float* Phat, float* p,
+                           int32_t* n_out);
+
+/* The constraint rows of one group of three neurons from its octahedron, on
+ * the host only (no device, no context): oct_lb[26] are lower bounds of
+ * d . zhat_G for d in {-1, 0, 1}^3 \ {0} in lexicographic order of
+ * (d0, d1, d2) (d0 slowest).  Rows are P . relu(zhat_G) + Phat . zhat_G <= p:
+ * the facets of the convex hull of {(relu(x), x) : x in the octahedron} with
+ * unit normals (|(P, Phat)| = 1), offsets at the exact support, and without
+ * facets that involve one neuron only.  P, Phat [max_rows][3] and p
+ * [max_rows] (host, FP64) receive the rows, *n_out their number (0 when the
+ * octahedron is degenerate); MNBAB_E_BUDGET (with *n_out set) when more than
+ * max_rows rows exist. */
+mnbab_status mnbab_mnc_group(const double* oct_lb, int32_t max_rows, double* P, double* Phat,
+                             double* p, int32_t* n_out);
+
 /* ---- nodes ------------------------------------------------------------- */
 /* A fresh root node of property row `row` outside the property's BaB queue
  * (root bounds, DeepPoly slopes, beta = gamma = 0). */

@@ -79,6 +79,10 @@ SIGNATURES = {
     "mnbab_set_property": (status, [VP, VP, FP, FP, FP, FP, C.c_int32, C.POINTER(VP)]),
     "mnbab_get_root_bounds": (status, [VP, VP, C.c_int32, FP, FP]),
     "mnbab_set_mnc": (status, [VP, VP, C.c_int32, C.c_int32, C.c_int32, IP, FP, FP, FP]),
+    "mnbab_generate_mnc": (status, [VP, VP, C.c_int32, C.POINTER(C.c_int64)]),
+    "mnbab_get_mnc": (status, [VP, VP, C.c_int32, C.c_int32, IP, FP, FP, FP, IP]),
+    "mnbab_mnc_group": (status, [C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), IP]),
     "mnbab_node_root": (status, [VP, VP, C.c_int32, C.POINTER(node_id)]),
     "mnbab_node_free": (status, [VP, node_id]),
     "mnbab_export_params": (status, [VP, node_id, VP, C.POINTER(C.c_size_t)]),

@@ -192,6 +192,29 @@ class Context:
         self._ck(self.lib.mnbab_set_mnc(self.h, prop.h, layer, n_rows, k, _ip(idx), _fp(P),
                                         _fp(Ph), _fp(p)))
 
+    def generate_mnc(self, prop: Prop, max_groups: int = 2000) -> int:
+        """Generates and uploads the multi-neuron constraints of every ReLU layer
+        from the property's root bounds (mnbab_generate_mnc); returns the rows."""
+        n = C.c_int64()
+        self._ck(self.lib.mnbab_generate_mnc(self.h, prop.h, max_groups, C.byref(n)))
+        return n.value
+
+    def get_mnc(self, prop: Prop, layer: int):
+        """(idx [e, 3], P [e, 3], Phat [e, 3], p [e]) of one ReLU layer."""
+        n = C.c_int32()
+        st = self.lib.mnbab_get_mnc(self.h, prop.h, layer, 0, None, None, None, None, C.byref(n))
+        if st not in (0, -2):
+            self._ck(st)
+        e = n.value
+        idx = np.zeros((e, 3), np.int32)
+        P = np.zeros((e, 3), np.float32)
+        Ph = np.zeros((e, 3), np.float32)
+        p = np.zeros(e, np.float32)
+        if e:
+            self._ck(self.lib.mnbab_get_mnc(self.h, prop.h, layer, e, _ip(idx), _fp(P), _fp(Ph),
+                                            _fp(p), C.byref(n)))
+        return idx, P, Ph, p
+
     def set_budget(self, prop: Prop, n: int):
         self._ck(self.lib.mnbab_set_budget(self.h, prop.h, n))
 
@@ -375,3 +398,20 @@ class Context:
         self._ck(self.lib.mnbab_request_result(self.h, ticket, C.byref(v), C.byref(w), C.byref(t),
                                                C.byref(n)))
         return dict(verdict=v.value, wait_s=w.value, total_s=t.value, nodes=n.value)
+
+
+def mnc_group(oct_lb, max_rows: int = 4096):
+    """Constraint rows (P [e, 3], Phat [e, 3], p [e]) of one group of three
+    neurons from its 26 octahedral lower bounds (mnbab_mnc_group; host only)."""
+    lib = L.load()
+    ob = np.ascontiguousarray(np.asarray(oct_lb, np.float64).reshape(26))
+    P = np.empty((max_rows, 3))
+    Ph = np.empty((max_rows, 3))
+    p = np.empty(max_rows)
+    n = C.c_int32()
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    st = lib.mnbab_mnc_group(dp(ob), max_rows, dp(P), dp(Ph), dp(p), C.byref(n))
+    if st != 0:
+        raise MnbabError(st, "mnbab_mnc_group failed")
+    k = n.value
+    return P[:k].copy(), Ph[:k].copy(), p[:k].copy()

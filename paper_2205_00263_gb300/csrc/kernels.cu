@@ -44,7 +44,7 @@ __global__ void k_init_rows(NetDev net, int t, int edge, RowsDev rows, float* ou
   const int m = blockIdx.x;
   if (m >= rows.M) return;
   const int n = rows.node[m];
-  const int j = rows.j[m];
+  const int j = rows.j ? rows.j[m] : 0;
   const float sg = rows.sign ? rows.sign[m] : 1.f;
   const int src = edge == 0 ? net.src1[t] : net.src2[t];
   const int width = net.d[src];
@@ -56,7 +56,39 @@ __global__ void k_init_rows(NetDev net, int t, int edge, RowsDev rows, float* ou
                             (e.kind == EPI_CONC && !e.X) || e.kind == EPI_STORE);
   float c0 = 0.f;
   float part = 0.f;
-  if (t == net.R + 1) {
+  if (rows.cidx) {
+    // combination of three neurons of zhat_t: a = sum_k c_k W_t[j_k, :]
+    const LayerDev& L = edge == 0 ? net.aff[t] : net.aff2[t];
+    int jk[3];
+    float ck[3];
+    for (int k = 0; k < 3; ++k) {
+      jk[k] = rows.cidx[3 * m + k];
+      ck[k] = rows.ccoef[3 * m + k];
+      if (edge == 0) {
+        const float bj = net.bfull[t] ? net.bfull[t][jk[k]]
+                                      : (L.kind == 1 ? L.b[jk[k]] : L.b[jk[k] / (L.ho * L.wo)]);
+        c0 += ck[k] * bj;
+      }
+    }
+    const int hw = L.ho * L.wo, ihw = L.hi * L.wi;
+    for (int col = threadIdx.x; col < width; col += blockDim.x) {
+      float a = 0.f;
+      for (int k = 0; k < 3; ++k) {
+        if (ck[k] == 0.f) continue;
+        if (L.kind == 1) {
+          a += ck[k] * L.W[(size_t)jk[k] * width + col];
+        } else {
+          const int co = jk[k] / hw, oh = (jk[k] % hw) / L.wo, ow = jk[k] % L.wo;
+          const int ci = col / ihw, kh = (col % ihw) / L.wi - (oh * L.s - L.p);
+          const int kw = col % L.wi - (ow * L.s - L.p);
+          if (kh >= 0 && kh < L.k && kw >= 0 && kw < L.k)
+            a += ck[k] * L.W[(((size_t)co * L.ci + ci) * L.k + kh) * L.k + kw];
+        }
+      }
+      const float o = epi_apply(e, m, col, a, part);
+      if (out) out[(size_t)m * ld + col] = o;
+    }
+  } else if (t == net.R + 1) {
     const PropDev& P = e.props[e.pool.prop[n]];
     const float* w = P.Wf + (size_t)j * width;
     c0 = P.bf[j];

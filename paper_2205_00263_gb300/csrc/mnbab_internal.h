@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #define MNBAB_MAXR 16
 
 namespace mnbab {
@@ -81,7 +83,20 @@ struct RowsDev {
   const int* node;    // pool slot per row
   const int* j;       // start neuron (intermediate rows) or property row (objective rows)
   const float* sign;  // +1 / -1 (intermediate rows); null for objective rows
+  // combination rows (multi-neuron constraint generation): row m starts at
+  // sum_k ccoef[3 m + k] zhat_{cidx[3 m + k]} instead of sign * zhat_j
+  const int* cidx;
+  const float* ccoef;
 };
+
+// One multi-neuron constraint row of a group of three neurons:
+// P . z_G + Ph . zhat_G <= p.
+struct MncRow {
+  double P[3], Ph[3], p;
+};
+// Rows of one group from the 26 lower bounds of d . zhat_G, d in {-1, 0, 1}^3
+// without 0 in lexicographic order (csrc/mnc_hull.cu); false: no rows.
+bool mnc_group_rows(const double* oct_lb, std::vector<MncRow>& rows);
 
 enum EpiKind { EPI_RELU = 0, EPI_CONC = 1, EPI_ADJ = 2, EPI_FWD_RELU = 3, EPI_STORE = 4 };
 

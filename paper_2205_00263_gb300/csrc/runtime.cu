@@ -17,6 +17,7 @@
 #include <limits>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mnbab.h"
@@ -104,6 +105,10 @@ struct mnbab_net {
   // the batch buffers hold (null when icap = B: the batch buffers serve)
   float *iap = nullptr, *igar = nullptr, *igbr = nullptr;
   int icap = 0;
+  // multi-neuron constraint generation: combination rows of one chunk
+  int* gen_cidx = nullptr;
+  float* gen_coef = nullptr;
+  int gen_cap = 0;
 };
 
 struct mnbab_prop {
@@ -483,13 +488,15 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
   mnbab_ctx* c = n->ctx;
   if (rows.M <= 0) return;
   const NetDev& nd = n->nd;
-  if (!o.final_mode && !o.store && !o.track && t == 1 && nd.n_edge[1] == 1 && nd.src1[1] == 0) {
+  const bool unit = rows.cidx == nullptr;  // the fast paths take rows of one neuron
+  if (unit && !o.final_mode && !o.store && !o.track && t == 1 && nd.n_edge[1] == 1 &&
+      nd.src1[1] == 0) {
     // rows of layer 1: a dot product with the input box per row
     Scope sc(c, C_INIT, 2.0 * rows.M * nd.d[0], 12.0 * rows.M);
     launch_first_rows(nd, n->pool, c->d_props, rows, n->lb, c->st);
     return;
   }
-  if (!o.final_mode && !o.store && !o.track && sweep_chain_supported(nd, t)) {
+  if (unit && !o.final_mode && !o.store && !o.track && sweep_chain_supported(nd, t)) {
     // dense intermediate-bound rows above a chain: persistent fused sweep
     double macs = nd.d[t - 1];
     for (int i = 1; i < t; ++i) macs += layer_macs(nd.aff[i]);
@@ -498,7 +505,7 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
     return;
   }
   WinPlan wp;
-  if (!o.final_mode && !o.store && !o.track && win_plan(nd, t, wp)) {
+  if (unit && !o.final_mode && !o.store && !o.track && win_plan(nd, t, wp)) {
     // intermediate-bound rows of a convolution neuron: receptive-field windows
     double macs = 0.0, elems = (double)nd.aff[t].ci * wp.h[t - 1] * wp.w[t - 1];
     for (int i = t - 1; i >= 1; --i) {
@@ -1345,6 +1352,171 @@ void ensure_roots(mnbab_net* n, mnbab_prop* const* only = nullptr, int n_only = 
   flush();
 }
 
+// Uploads the constraint rows of one ReLU layer of a property (row form and
+// CSR by neuron) and appends them to the property's gamma entries.
+void set_mnc_impl(mnbab_ctx* c, mnbab_prop* p, int layer, int n_rows, int k, const int32_t* idx,
+                  const float* P, const float* Phat, const float* pv) {
+  if (p->mnc_set[layer]) fail(MNBAB_E_INVALID_ARG, "constraints of this layer already set");
+  if (p->inter_steps > 0)
+    fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
+  mnbab_net* n = p->net;
+  const int d = n->nd.d[layer];
+  if (p->pd.E + n_rows > c->EC)
+    fail(MNBAB_E_BUDGET, "more constraint rows than mnbab_options.max_mnc_rows");
+  for (int64_t q = 0; q < (int64_t)n_rows * k; ++q)
+    if (idx[q] < 0 || idx[q] >= d) fail(MNBAB_E_INVALID_ARG, "constraint neuron index out of range");
+  MncDev& m = p->pd.mnc[layer];
+  m.e = n_rows;
+  m.k = k;
+  m.goff = p->pd.E;
+  if (n_rows > 0) {
+    const size_t nk = (size_t)n_rows * k;
+    // CSR by neuron
+    std::vector<int> cnt(d + 1, 0);
+    for (size_t q = 0; q < nk; ++q) cnt[idx[q] + 1]++;
+    for (int j = 0; j < d; ++j) cnt[j + 1] += cnt[j];
+    std::vector<int> ce(nk), pos(cnt.begin(), cnt.end() - 1);
+    std::vector<float> cP(nk), cPh(nk);
+    for (int e = 0; e < n_rows; ++e)
+      for (int kk = 0; kk < k; ++kk) {
+        const size_t q = (size_t)e * k + kk;
+        const int at = pos[idx[q]]++;
+        ce[at] = e;
+        cP[at] = P[q];
+        cPh[at] = Phat[q];
+      }
+    int* didx = dalloc_t<int>(c, nk);
+    float* dP = dalloc_t<float>(c, nk);
+    float* dPh = dalloc_t<float>(c, nk);
+    float* dp = dalloc_t<float>(c, n_rows);
+    int* dcptr = dalloc_t<int>(c, d + 1);
+    int* dce = dalloc_t<int>(c, nk);
+    float* dcP = dalloc_t<float>(c, nk);
+    float* dcPh = dalloc_t<float>(c, nk);
+    h2d(c, didx, idx, nk);
+    h2d(c, dP, P, nk);
+    h2d(c, dPh, Phat, nk);
+    h2d(c, dp, pv, n_rows);
+    h2d(c, dcptr, cnt.data(), d + 1);
+    h2d(c, dce, ce.data(), nk);
+    h2d(c, dcP, cP.data(), nk);
+    h2d(c, dcPh, cPh.data(), nk);
+    m.idx = didx; m.P = dP; m.Ph = dPh; m.p = dp;
+    m.cptr = dcptr; m.ce = dce; m.cP = dcP; m.cPh = dcPh;
+  }
+  p->pd.E += n_rows;
+  p->mnc_set[layer] = 1;
+  update_cab(n, p);
+  upload_prop(c, p->index);
+  sync(c);
+}
+
+// Multi-neuron constraints of every ReLU layer of a property from its root
+// bounds: groups of three unstable neurons (sliding triples in the order of
+// decreasing -l u / (u - l), ties by index, at most max_groups per layer), the
+// DeepPoly lower bounds of the 26 octahedral directions of each group (one
+// combination row each, back-substituted on the device with the root's
+// DeepPoly relaxation of the layers below), then each group's rows from the
+// hull of the lifted ReLU graph on the host (csrc/mnc_hull.cu, in parallel).
+int64_t generate_mnc_impl(mnbab_ctx* c, mnbab_prop* p, int max_groups) {
+  mnbab_net* n = p->net;
+  for (int t = 1; t <= n->R; ++t)
+    if (p->mnc_set[t]) fail(MNBAB_E_INVALID_ARG, "constraints of a layer are already set");
+  if (p->inter_steps > 0)
+    fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
+  mnbab_prop* only[1] = {p};
+  ensure_roots(n, only, 1);
+  if (p->root_slot < 0) fail(MNBAB_E_INVALID_ARG, "property not admitted");
+  const int SD = n->SD, rs = p->root_slot;
+  std::vector<float> hl(SD), hu(SD);
+  d2h(c, hl.data(), n->pool.L + (size_t)rs * SD, SD);
+  d2h(c, hu.data(), n->pool.U + (size_t)rs * SD, SD);
+  sync(c);
+  static const int kDir[26][3] = {
+      {-1, -1, -1}, {-1, -1, 0}, {-1, -1, 1}, {-1, 0, -1}, {-1, 0, 0}, {-1, 0, 1}, {-1, 1, -1},
+      {-1, 1, 0},   {-1, 1, 1},  {0, -1, -1}, {0, -1, 0},  {0, -1, 1}, {0, 0, -1}, {0, 0, 1},
+      {0, 1, -1},   {0, 1, 0},   {0, 1, 1},   {1, -1, -1}, {1, -1, 0}, {1, -1, 1}, {1, 0, -1},
+      {1, 0, 0},    {1, 0, 1},   {1, 1, -1},  {1, 1, 0},   {1, 1, 1}};
+  const int chunk_groups = std::max(1, n->chunk / 26);  // rows per sweep <= the row chunk
+  if (!n->gen_cidx) {
+    n->gen_cap = chunk_groups * 26;
+    n->gen_cidx = dalloc_t<int>(c, 3 * (size_t)n->gen_cap);
+    n->gen_coef = dalloc_t<float>(c, 3 * (size_t)n->gen_cap);
+  }
+  int64_t total = 0;
+  for (int t = 1; t <= n->R; ++t) {
+    const int dt = n->nd.d[t], off = n->nd.off[t];
+    std::vector<int> unst;
+    for (int j = 0; j < dt; ++j)
+      if (hl[off + j] < 0.f && hu[off + j] > 0.f) unst.push_back(j);
+    const int ng = unst.size() >= 3 ? std::min((int)unst.size() - 2, max_groups) : 0;
+    if (ng == 0) {
+      set_mnc_impl(c, p, t, 0, 3, nullptr, nullptr, nullptr, nullptr);
+      continue;
+    }
+    std::vector<double> key(dt, 0.0);
+    for (int j : unst) {
+      const double l = hl[off + j], u = hu[off + j];
+      key[j] = -l * u / (u - l);
+    }
+    std::stable_sort(unst.begin(), unst.end(), [&](int a, int b) {
+      return key[a] != key[b] ? key[a] > key[b] : a < b;
+    });
+    // octahedral bounds: 26 combination rows per group, in chunks
+    std::vector<double> oct((size_t)ng * 26);
+    std::vector<int> cidx, rnode;
+    std::vector<float> coef;
+    std::vector<float> lb;
+    for (int g0 = 0; g0 < ng; g0 += chunk_groups) {
+      const int gn = std::min(chunk_groups, ng - g0), Mc = gn * 26;
+      cidx.resize(3 * (size_t)Mc);
+      coef.resize(3 * (size_t)Mc);
+      rnode.assign(Mc, rs);
+      for (int g = 0; g < gn; ++g)
+        for (int di = 0; di < 26; ++di)
+          for (int k = 0; k < 3; ++k) {
+            const size_t q = 3 * ((size_t)g * 26 + di) + k;
+            cidx[q] = unst[g0 + g + k];
+            coef[q] = (float)kDir[di][k];
+          }
+      h2d(c, n->gen_cidx, cidx.data(), cidx.size());
+      h2d(c, n->gen_coef, coef.data(), coef.size());
+      h2d(c, n->row_node, rnode.data(), rnode.size());
+      RowsDev r{Mc, n->row_node, nullptr, nullptr, n->gen_cidx, n->gen_coef};
+      SweepOpts so;
+      sweep(n, t, r, so);
+      lb.resize(Mc);
+      d2h(c, lb.data(), n->lb, Mc);
+      sync(c);
+      for (int q = 0; q < Mc; ++q) oct[(size_t)g0 * 26 + q] = lb[q];
+    }
+    // hulls on the host, groups spread over the host threads
+    std::vector<std::vector<MncRow>> rows(ng);
+    const int nth = std::max(1, std::min(ng, (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nth; ++w)
+      pool.emplace_back([&, w]() {
+        for (int g = w; g < ng; g += nth) mnc_group_rows(oct.data() + (size_t)g * 26, rows[g]);
+      });
+    for (auto& th : pool) th.join();
+    std::vector<int32_t> idx;
+    std::vector<float> P, Ph, pv;
+    for (int g = 0; g < ng; ++g)
+      for (const MncRow& r : rows[g]) {
+        for (int k = 0; k < 3; ++k) {
+          idx.push_back(unst[g + k]);
+          P.push_back((float)r.P[k]);
+          Ph.push_back((float)r.Ph[k]);
+        }
+        pv.push_back((float)r.p);
+      }
+    const int nr = (int)pv.size();
+    set_mnc_impl(c, p, t, nr, 3, idx.data(), P.data(), Ph.data(), pv.data());
+    total += nr;
+  }
+  return total;
+}
+
 // ---------------------------------------------------------------------------
 // BaB step (Sec. 2.2; Sec. 3.2)
 // ---------------------------------------------------------------------------
@@ -1946,59 +2118,36 @@ mnbab_status mnbab_set_mnc(mnbab_ctx* c, mnbab_prop* p, int32_t layer, int32_t n
   if (!p || layer < 1 || layer > p->net->R || n_rows < 0 || k <= 0 || (n_rows && (!idx || !P ||
       !Phat || !pv)))
     fail(MNBAB_E_INVALID_ARG, "bad constraint arguments");
-  if (p->mnc_set[layer]) fail(MNBAB_E_INVALID_ARG, "constraints of this layer already set");
-  if (p->inter_steps > 0)
-    fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
-  mnbab_net* n = p->net;
-  const int d = n->nd.d[layer];
-  if (p->pd.E + n_rows > c->EC)
-    fail(MNBAB_E_BUDGET, "more constraint rows than mnbab_options.max_mnc_rows");
-  for (int64_t q = 0; q < (int64_t)n_rows * k; ++q)
-    if (idx[q] < 0 || idx[q] >= d) fail(MNBAB_E_INVALID_ARG, "constraint neuron index out of range");
-  MncDev& m = p->pd.mnc[layer];
-  m.e = n_rows;
-  m.k = k;
-  m.goff = p->pd.E;
-  if (n_rows > 0) {
-    const size_t nk = (size_t)n_rows * k;
-    // CSR by neuron
-    std::vector<int> cnt(d + 1, 0);
-    for (size_t q = 0; q < nk; ++q) cnt[idx[q] + 1]++;
-    for (int j = 0; j < d; ++j) cnt[j + 1] += cnt[j];
-    std::vector<int> ce(nk), pos(cnt.begin(), cnt.end() - 1);
-    std::vector<float> cP(nk), cPh(nk);
-    for (int e = 0; e < n_rows; ++e)
-      for (int kk = 0; kk < k; ++kk) {
-        const size_t q = (size_t)e * k + kk;
-        const int at = pos[idx[q]]++;
-        ce[at] = e;
-        cP[at] = P[q];
-        cPh[at] = Phat[q];
-      }
-    int* didx = dalloc_t<int>(c, nk);
-    float* dP = dalloc_t<float>(c, nk);
-    float* dPh = dalloc_t<float>(c, nk);
-    float* dp = dalloc_t<float>(c, n_rows);
-    int* dcptr = dalloc_t<int>(c, d + 1);
-    int* dce = dalloc_t<int>(c, nk);
-    float* dcP = dalloc_t<float>(c, nk);
-    float* dcPh = dalloc_t<float>(c, nk);
-    h2d(c, didx, idx, nk);
-    h2d(c, dP, P, nk);
-    h2d(c, dPh, Phat, nk);
-    h2d(c, dp, pv, n_rows);
-    h2d(c, dcptr, cnt.data(), d + 1);
-    h2d(c, dce, ce.data(), nk);
-    h2d(c, dcP, cP.data(), nk);
-    h2d(c, dcPh, cPh.data(), nk);
-    m.idx = didx; m.P = dP; m.Ph = dPh; m.p = dp;
-    m.cptr = dcptr; m.ce = dce; m.cP = dcP; m.cPh = dcPh;
+  set_mnc_impl(c, p, layer, n_rows, k, idx, P, Phat, pv);
+  API_END(c)
+}
+
+mnbab_status mnbab_get_mnc(mnbab_ctx* c, const mnbab_prop* p, int32_t layer, int32_t max_rows,
+                           int32_t* idx, float* P, float* Phat, float* pv, int32_t* n_out) {
+  API_BEGIN(c)
+  if (!p || layer < 1 || layer > p->net->R || !n_out || max_rows < 0)
+    fail(MNBAB_E_INVALID_ARG, "bad arguments");
+  const MncDev& m = p->pd.mnc[layer];
+  *n_out = m.e;
+  if (m.e > max_rows) fail(MNBAB_E_BUDGET, "more rows than max_rows");
+  if (m.e > 0) {
+    if (!idx || !P || !Phat || !pv) fail(MNBAB_E_INVALID_ARG, "null output");
+    const size_t nk = (size_t)m.e * m.k;
+    d2h(c, idx, m.idx, nk);
+    d2h(c, P, m.P, nk);
+    d2h(c, Phat, m.Ph, nk);
+    d2h(c, pv, m.p, m.e);
+    sync(c);
   }
-  p->pd.E += n_rows;
-  p->mnc_set[layer] = 1;
-  update_cab(n, p);
-  upload_prop(c, p->index);
-  sync(c);
+  API_END(c)
+}
+
+mnbab_status mnbab_generate_mnc(mnbab_ctx* c, mnbab_prop* p, int32_t max_groups,
+                                int64_t* rows_out) {
+  API_BEGIN(c)
+  if (!p || max_groups < 0) fail(MNBAB_E_INVALID_ARG, "bad arguments");
+  const int64_t tot = generate_mnc_impl(c, p, max_groups);
+  if (rows_out) *rows_out = tot;
   API_END(c)
 }
 
