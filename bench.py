@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=None,
                     help="requests of the serving stream (default 24 in the main line, 400 with --serving)")
     ap.add_argument("--serve-rate", type=float, default=4.0)
+    ap.add_argument("--mnc-big-props", type=int, default=32,
+                    help="properties of the conv-big arm with multi-neuron constraints (0 skips it)")
+    ap.add_argument("--mnc-big-groups", type=int, default=24,
+                    help="constraint groups per ReLU layer in the conv-big arm")
     ap.add_argument("--inter-nodes", type=int, default=128,
                     help="root nodes of the optimised-intermediate-bounds arm (0 skips it)")
     return ap.parse_args()
@@ -488,6 +492,10 @@ def run_ours(args):
             sctx.close()
     peaks, src = load_peaks()
     roof = roofline(stats, peaks, src, kernels_sha(), layers=layers)
+    mnc_big = None
+    if world == 1 and args.mnc_big_props > 0:
+        mnc_big = mnc_big_run(local, stream, args.mnc_big_props, 3, args.mnc_big_groups, peaks,
+                              src, kernels_sha())
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -512,6 +520,7 @@ def run_ours(args):
             "nodes_timed": tot_nodes,
             "serving": serving,
             "intermediate": inter,
+            "conv_big_mnc": mnc_big,
             "launches_before_timed": int(launches0),
         }
         print(json.dumps(out), flush=True)
@@ -696,6 +705,79 @@ def intermediate_run(local, stream, layers, eps, start, n_nodes, oracle_nodes):
                              "nodes": oracle_nodes, "cores": torch.get_num_threads(),
                              "kind": "oracle"}
     return out
+
+
+# ----------------------------------------------------------------------------
+# Conv-big (3x32x32, seven ReLU layers) with k = 3 multi-neuron constraints from
+# the library's generator: gamma terms, their gradients and ACS branching run in
+# the timed BaB steps (256 subproblems per step).
+MNC_BIG = ("conv_big_32: 3x32x32 -> conv32 3x3 -> conv32 4x4 s2 -> conv64 3x3 -> conv64 4x4 s2 -> "
+           "FC512 -> FC512 -> FC10, k=3 multi-neuron constraints (library generator)")
+
+
+def mnc_big_run(local, stream, n_props, steps, max_groups, peaks, src, ksha):
+    import torch
+    from paper_2205_00263_gb300 import Context
+    layers2 = synth.make_network(2)
+    props = synth.make_properties(2, layers2, n=n_props, eps=synth.load_eps(2), start=0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ctx = Context(device=local, stream=stream.cuda_stream, node_capacity=4096,
+                  max_mnc_rows=1 << 16)
+    try:
+        net = ctx.load_network(layers2)
+        ps, rows = [], []
+        t0 = time.perf_counter()
+        for pr in props:
+            p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+            ctx.set_budget(p, BUDGET)
+            rows.append(ctx.generate_mnc(p, max_groups))
+            ps.append(p)
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        ctx.bab_step(ps, max_nodes=256, steps=ADAM_STEPS)   # warm-up (roots)
+        ctx.profile(True)
+        ctx.bab_step(ps, max_nodes=256, steps=ADAM_STEPS)   # every class timed: breakdown
+        torch.cuda.synchronize()
+        breakdown, _ = ctx.profile_read()
+        dom_name = dominant(breakdown)[0]
+        ctx.profile(True)
+        ctx.profile_mask([dom_name])
+        nodes, ms, rebound = 0, 0.0, 0
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = ctx.bab_step(ps, max_nodes=256, steps=ADAM_STEPS)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            nodes += st["nodes_bounded"]
+            rebound += st["rows_rebounded"]
+        stats, _ = ctx.profile_read()
+        ctx.profile(False)
+        ctx.profile_mask(None)
+        verd = {"verified": 0, "falsified": 0, "unknown": 0}
+        for p in ps:
+            v, _, _ = ctx.verdict(p)
+            verd["verified" if v == 1 else "falsified" if v == -1 else "unknown"] += 1
+    finally:
+        ctx.close()
+    top = sorted(((k, v["ms"]) for k, v in breakdown.items()
+                  if v["ms"] and not k.startswith(("phase_", "step_"))), key=lambda kv: -kv[1])
+    return {"workload": MNC_BIG, "properties": n_props, "max_groups_per_layer": max_groups,
+            "mnc_rows_per_property": sum(rows) / len(rows),
+            "generate_s_per_property": gen_s / n_props,
+            "value": nodes / (ms * 1e-3) if ms else None, "unit": "nodes/s",
+            "steps": steps, "nodes": nodes, "ms_per_step": ms / max(1, steps),
+            "rows_rebounded": rebound,
+            "roofline": roofline({dom_name: stats[dom_name]}, peaks, src, ksha),
+            "kernel_breakdown_ms": {k: round(v, 3) for k, v in top[:8]},
+            "state_after_timed_steps": verd,
+            "note": "groups per layer capped for the HBM per node (about 150 rows a group); "
+                    "constraint generation is outside the timed steps"}
 
 
 # ----------------------------------------------------------------------------
