@@ -183,7 +183,8 @@ def dominant(stats):
 
 
 CONTRACTIONS = ("backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm", "forward_conv",
-                "opt_fused_chain", "backsub_conv_window", "backsub_rows_fused")
+                "opt_fused_chain", "backsub_conv_window", "backsub_rows_fused", "backsub_conv_tc",
+                "forward_conv_tc")
 
 
 def tf32x3_peak(peaks, src):

@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmnbab.so")
-SOURCES = ["kernels.cu", "runtime.cu", "noalloc.cu", "tc_gemm.cu", "fused.cu", "mnc_hull.cu"]
+SOURCES = ["kernels.cu", "runtime.cu", "noalloc.cu", "tc_gemm.cu", "fused.cu", "mnc_hull.cu",
+           "tc_conv.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC] + ARCH
 

@@ -1384,13 +1384,28 @@ bool conv_supported(const LayerDev& L) {
   return convT_row_smem(L, cbT) <= 40 * 1024 && conv_fwd_row_smem(L, 4) <= 40 * 1024;
 }
 
+// Tensor-core convolutions: always with gemm_path 2, never with 1, and with 0
+// where the SIMT kernels would take the implicit GEMM (large per-row work);
+// dense rows only (rows started at one neuron skip their zero region in the
+// row-resident kernels)
+static bool use_tc_conv(const LayerDev& L, int dir, const Epi& e) {
+  if (e.gemm_path == 1 || !tc_conv_usable(L, dir)) return false;
+  if (dir == 1 && e.sparse_rows) return false;
+  return e.gemm_path == 2 || (double)L.co * L.ho * L.wo * L.ci * L.k * L.k >= 512.0 * 1024.0;
+}
+
+bool conv_tc_chosen(const LayerDev& L, int dir, const Epi& e) {
+  return L.kind == MNBAB_CONV2D && use_tc_conv(L, dir, e);
+}
+
 int backsub_slots(const LayerDev& L) {
   if (L.kind == 1) return (L.d_in + 31) / 32;  // upper bound over the tile shapes
   // upper bound over the implicit-GEMM blocks, the row-resident splits (<= 32
   // CTAs per row, more for large planes) and the fallback tiling (128 positions
   // per CTA)
   const int P = L.hi * L.wi;
-  return std::max(std::max(32 * ((P + 1023) / 1024), (P + 127) / 128), ig_slots(L));
+  return std::max(std::max(std::max(32 * ((P + 1023) / 1024), (P + 127) / 128), ig_slots(L)),
+                  tc_conv_slots(L));
 }
 
 int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
@@ -1403,6 +1418,7 @@ int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* 
                             e, e.err, st);
     return gemm_launch(M, L.d_in, L.d_out, in, ld_in, L.W, L.d_in, nullptr, 1, out, ld_out, e, st);
   }
+  if (use_tc_conv(L, 1, e)) return launch_tc_conv(L, 1, M, in, ld_in, out, ld_out, e, st);
   // dense rows: implicit GEMM per parity class; rows that start at a neuron
   // (nonzero only near it) skip the zero region in the row-resident kernel
   if (!e.sparse_rows && ig_supported(L, 1) && (ig_preferred(L) || !conv_supported(L)))
@@ -1455,6 +1471,10 @@ void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float*
       return;
     }
     gemm_launch(M, L.d_out, L.d_in, in, ld_in, L.Wt, L.d_out, L.b, 1, out, ld_out, e, st);
+    return;
+  }
+  if (use_tc_conv(L, 0, e)) {
+    launch_tc_conv(L, 0, M, in, ld_in, out, ld_out, e, st);
     return;
   }
   if (ig_supported(L, 0) && (ig_preferred(L) || !conv_supported(L))) {

@@ -24,6 +24,7 @@ struct LayerDev {
   const float* b;   // [d_out] (fc) or [co] (conv)
   const float* Wb;  // conv only: [co][kh][kw][ci] (back-substitution layout)
   const float* Wf;  // conv only: [ci][kh][kw][co] (forward layout)
+  const void* tc;   // conv only: host-side tensor-core operands (struct TcConv), or null
 };
 
 // The network as a DAG: node t = 1..R (ReLU layers) and R + 1 (output) sums
@@ -131,6 +132,25 @@ struct Epi {
   int sparse_rows;   // rows started at one neuron and met only convolutions since:
                      // nonzero near it, so conv steps skip the zero region
 };
+
+// ---- tensor-core convolutions (tc_conv.cu) --------------------------------
+// Pre-split TF32 hi / lo weights per stride class with their TMA tensor maps.
+struct TcConv;
+// device floats the layer's pre-split weights take (both directions)
+size_t tc_conv_floats(const LayerDev& L);
+// splits L.W into buf (tc_conv_floats(L) floats, on `st`) and encodes the
+// tensor maps; null when the layer or the driver does not support it
+TcConv* tc_conv_create(const LayerDev& L, float* buf, cudaStream_t st);
+void tc_conv_destroy(TcConv* t);
+// dir 0 forward (channels co), dir 1 transposed (channels ci)
+bool tc_conv_usable(const LayerDev& L, int dir);
+int tc_conv_slots(const LayerDev& L);
+// whether launch_backsub (dir 1) / launch_forward (dir 0) take the tensor-core
+// kernel for this layer and epilogue (kernels.cu)
+bool conv_tc_chosen(const LayerDev& L, int dir, const Epi& e);
+// launches the implicit GEMM; returns the partial-sum slots written (dir 1)
+int launch_tc_conv(const LayerDev& L, int dir, int M, const float* in, int ld_in, float* out,
+                   int ld_out, const Epi& e, cudaStream_t st);
 
 // ---- launchers (kernels.cu, tc_gemm.cu) ----------------------------------
 // Tensor-core 3xTF32 GEMM C = A . Bnk^T (+ bias) with the fused epilogue;

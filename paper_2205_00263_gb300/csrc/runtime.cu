@@ -189,6 +189,7 @@ struct mnbab_ctx {
   struct GraphEntry* cap = nullptr;  // entry being captured (Scope records into it)
   std::vector<struct GraphEntry*> graph_cache;
   std::vector<cudaEvent_t> graph_events;  // events owned by captured graphs
+  std::vector<TcConv*> tc_convs;          // tensor-core convolution operands of all networks
 };
 
 // A captured optimisation loop: its executable graph, the kernel-class work it
@@ -252,7 +253,7 @@ void d2h(mnbab_ctx* c, T* dst, const T* src, size_t n) {
 
 enum Cat {
   C_BACKSUB_FC, C_BACKSUB_CONV, C_FWD_FC, C_FWD_CONV, C_INIT, C_REDUCE, C_GAMMA, C_ADAM, C_ACS,
-  C_BOOK, C_WIN, C_FUSED, C_SWEEP, NKCAT,
+  C_BOOK, C_WIN, C_FUSED, C_SWEEP, C_BACKSUB_CONV_TC, C_FWD_CONV_TC, NKCAT,
   // host wall time of the BaB step phases (stream work included up to their syncs)
   H_ROOTS = NKCAT, H_REBOUND, H_DEEPPOLY, H_OPTIMIZE, H_CONFIRM, H_FINISH,
   // device time of all kernel classes launched within each phase
@@ -263,7 +264,7 @@ const char* CAT_NAMES[NCAT] = {"backsub_fc_gemm", "backsub_conv_transpose", "for
                                "forward_conv",    "init_rows",              "reduce_lb",
                                "gamma_terms",     "adam",                   "acs",
                                "bookkeeping",     "backsub_conv_window",    "opt_fused_chain",
-                               "backsub_rows_fused",
+                               "backsub_rows_fused", "backsub_conv_tc", "forward_conv_tc",
                                "step_roots_wall",        "step_rebound_wall",
                                "step_deeppoly_wall", "step_optimize_wall",  "step_confirm_wall",
                                "step_finish_wall", "phase_roots_gpu",        "phase_rebound_gpu",
@@ -583,7 +584,9 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
         used += 1;
       } else {
         const LayerDev& L = edge_of(n, v, k);
-        Scope sc(c, L.kind == 1 ? C_BACKSUB_FC : C_BACKSUB_CONV, 2.0 * rows.M * layer_macs(L),
+        Scope sc(c, L.kind == 1 ? C_BACKSUB_FC
+                                : (conv_tc_chosen(L, 1, e) ? C_BACKSUB_CONV_TC : C_BACKSUB_CONV),
+                 2.0 * rows.M * layer_macs(L),
                  4.0 * rows.M * (L.d_out + (out ? L.d_in : 0)) + layer_wbytes(L));
         const int sl = launch_backsub(L, rows.M, lam_buf(n, v), nd.d[v], out, nd.d[sidx], e, c->st);
         if (last) used += sl;  // raw contributions write no offset partials
@@ -703,7 +706,8 @@ void adjoint(mnbab_net* n, int M, bool has_gamma, int upto = -1) {
       const float* in = sidx == 0 ? n->X : lam_buf(n, sidx);
       const int ld_in = sidx == 0 ? n->d0 : nd.d[sidx];
       const LayerDev& L = edge_of(n, t, k);
-      Scope sc(c, L.kind == 1 ? C_FWD_FC : C_FWD_CONV, 2.0 * M * layer_macs(L),
+      Scope sc(c, L.kind == 1 ? C_FWD_FC : (conv_tc_chosen(L, 0, e) ? C_FWD_CONV_TC : C_FWD_CONV),
+               2.0 * M * layer_macs(L),
                4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
       launch_forward(L, M, in, ld_in, lam_buf(n, t), nd.d[t], e, c->st);
     }
@@ -851,7 +855,8 @@ void forward_rows(mnbab_net* n, int M, const float* x) {
       const float* in = sidx == 0 ? x : lam_buf(n, sidx);
       const int ld_in = sidx == 0 ? n->d0 : nd.d[sidx];
       const LayerDev& L = edge_of(n, t, k);
-      Scope sc(c, L.kind == 1 ? C_FWD_FC : C_FWD_CONV, 2.0 * M * layer_macs(L),
+      Scope sc(c, L.kind == 1 ? C_FWD_FC : (conv_tc_chosen(L, 0, e) ? C_FWD_CONV_TC : C_FWD_CONV),
+               2.0 * M * layer_macs(L),
                4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
       launch_forward(L, M, in, ld_in, lam_buf(n, t), nd.d[t], e, c->st);
     }
@@ -1855,6 +1860,7 @@ void mnbab_destroy(mnbab_ctx* c) {
   for (auto* r : c->requests) delete r;
   for (auto* n : c->nets) delete n;
   for (auto* p : c->props) delete p;
+  for (auto* t : c->tc_convs) tc_conv_destroy(t);
   if (c->own_stream) cudaStreamDestroy(c->st);
   delete c;
 }
@@ -1902,6 +1908,15 @@ LayerDev upload_affine(mnbab_ctx* c, const HostLayer& h) {
     h2d(c, dWf, Wfw.data(), Wfw.size());
     L.Wb = dWb;
     L.Wf = dWf;
+    // pre-split TF32 weights and TMA tensor maps of the tensor-core convolutions
+    const size_t tcf = tc_conv_floats(L);
+    if (tcf) {
+      TcConv* t = tc_conv_create(L, dalloc_t<float>(c, tcf), c->st);
+      if (t) {
+        c->tc_convs.push_back(t);
+        L.tc = t;
+      }
+    }
   }
   return L;
 }
