@@ -24,7 +24,7 @@ struct LayerDev {
   const float* b;   // [d_out] (fc) or [co] (conv)
   const float* Wb;  // conv only: [co][kh][kw][ci] (back-substitution layout)
   const float* Wf;  // conv only: [ci][kh][kw][co] (forward layout)
-  const void* tc;   // conv only: host-side tensor-core operands (struct TcConv), or null
+  const void* tc;   // host-side tensor-core operands (TcConv for conv, TcFc for FC), or null
 };
 
 // The network as a DAG: node t = 1..R (ReLU layers) and R + 1 (output) sums
@@ -155,9 +155,16 @@ int launch_tc_conv(const LayerDev& L, int dir, int M, const float* in, int ld_in
 // ---- launchers (kernels.cu, tc_gemm.cu) ----------------------------------
 // Tensor-core 3xTF32 GEMM C = A . Bnk^T (+ bias) with the fused epilogue;
 // returns the number of column tiles (partial-sum slots written).
+// With `pre` (the layer's TcFc) the weight operand of direction `dir` (0 W for
+// forward products, 1 W^T for back-substitution) comes pre-split by TMA.
 int launch_gemm_tc(int M, int N, int K, const float* A, int lda, const float* Bnk, int ldb,
                    const float* bias, int bias_div, float* C, int ldc, const Epi& e, int* err,
-                   cudaStream_t st);
+                   cudaStream_t st, const void* pre = nullptr, int dir = 0);
+// Pre-split TF32 weights of an FC layer for the tensor-core GEMM (tc_gemm.cu).
+struct TcFc;
+size_t tc_fc_floats(const LayerDev& L);
+TcFc* tc_fc_create(const LayerDev& L, float* buf, cudaStream_t st);
+void tc_fc_destroy(TcFc* t);
 // Starting rows: a = sign * W_t[j, :] (t <= R) or Wf[row, :] (t = R + 1) on
 // z^(t-1), with c = sign * b_t[j] into slot 0, through epilogue `e`.
 void launch_init_rows(const NetDev& net, int t, int edge, const RowsDev& rows, float* out, int ld,

@@ -190,6 +190,7 @@ struct mnbab_ctx {
   std::vector<struct GraphEntry*> graph_cache;
   std::vector<cudaEvent_t> graph_events;  // events owned by captured graphs
   std::vector<TcConv*> tc_convs;          // tensor-core convolution operands of all networks
+  std::vector<TcFc*> tc_fcs;              // pre-split FC weights of all networks
 };
 
 // A captured optimisation loop: its executable graph, the kernel-class work it
@@ -1861,6 +1862,7 @@ void mnbab_destroy(mnbab_ctx* c) {
   for (auto* n : c->nets) delete n;
   for (auto* p : c->props) delete p;
   for (auto* t : c->tc_convs) tc_conv_destroy(t);
+  for (auto* t : c->tc_fcs) tc_fc_destroy(t);
   if (c->own_stream) cudaStreamDestroy(c->st);
   delete c;
 }
@@ -1889,6 +1891,12 @@ LayerDev upload_affine(mnbab_ctx* c, const HostLayer& h) {
     float* dWt = dalloc_t<float>(c, Wt.size());
     h2d(c, dWt, Wt.data(), Wt.size());
     L.Wt = dWt;
+    // pre-split TF32 weights and TMA tensor maps of the tensor-core GEMM
+    TcFc* t = tc_fc_create(L, dalloc_t<float>(c, tc_fc_floats(L)), c->st);
+    if (t) {
+      c->tc_fcs.push_back(t);
+      L.tc = t;
+    }
   } else {
     if (!conv_supported(L))
       fail(MNBAB_E_UNSUPPORTED, "convolution row does not fit in shared memory");

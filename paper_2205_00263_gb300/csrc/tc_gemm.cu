@@ -19,14 +19,26 @@
 // as the SIMT kernels; each thread owns one row, so the row partial sums of
 // the offset need no cross-thread reduction.
 //
+// The weight operand of an FC layer is constant: it is split into hi / lo once
+// at load_network, arranged as [N/8][K/4][8][4] (core-matrix-major) and loaded
+// per block by TMA (cp.async.bulk.tensor, a 3-D tensor map whose box lands in
+// exactly the canonical layout above); the staging threads then split only
+// the coefficient rows A.  Without pre-split weights both operands are staged.
+//
 // Every wait on the mbarrier is bounded: on timeout the kernel records an
 // error, waits once more (bounded) for its own MMAs, frees its tensor memory
 // and returns.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "epilogue.cuh"
+#include "mnbab.h"
 #include "mnbab_internal.h"
+#include "tc_common.cuh"
 
 namespace mnbab {
 
@@ -163,7 +175,10 @@ __device__ __forceinline__ void tc_stage(const float* __restrict__ X, int ld, in
 }
 
 template <int BN>
-__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, const float* __restrict__ A,
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ CUtensorMap tm_hi,
+                                                 const __grid_constant__ CUtensorMap tm_lo,
+                                                 int use_tma,
+                                                 int M, int N, int K, const float* __restrict__ A,
                                                  int lda, const float* __restrict__ B, int ldb,
                                                  const float* __restrict__ bias, int bias_div,
                                                  float* C, int ldc, Epi e, int* err) {
@@ -172,8 +187,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, con
   constexpr int STAGE = 2 * TBM * TBK * 4 + 2 * BN * TBK * 4;
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * STAGE);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * STAGE);  // mma[2], tma[2]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 4);
+  __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * BN;
@@ -187,9 +203,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, con
                  "r"((uint32_t)BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  const uint32_t tma0 = smem_u32(bar + 2);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1));
+    tc::mbar_init(tma0, 1);
+    tc::mbar_init(tma0 + 8, 1);
+    s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -210,7 +230,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, con
     if (kb >= 2) {
       const bool mine = mbar_wait(bst, (uint32_t)(((kb >> 1) - 1) & 1));
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      ok = __syncthreads_and(mine) != 0;  // uniform across the CTA
+      ok = __syncthreads_and(mine && s_fail == 0) != 0;  // uniform across the CTA
       if (!ok) break;
     }
     unsigned char* a_hi = base + st * STAGE;
@@ -218,12 +238,24 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, con
     unsigned char* b_hi = a_lo + TBM * TBK * 4;
     unsigned char* b_lo = b_hi + BN * TBK * 4;
     const int k0 = kb * TBK;
+    const uint32_t tbar = tma0 + 8 * st;
+    if (use_tma) {
+      if (tid == 0) {
+        // the pre-split weight block [n0 / 8 .. + BN / 8) x [k0 / 4 .. + 8) by TMA;
+        // rows past N read as zeros
+        tc::mbar_expect_tx(tbar, 2 * BN * TBK * 4);
+        tc::tma_load_3d(smem_u32(b_hi), &tm_hi, 0, k0 / 4, n0 / 8, tbar);
+        tc::tma_load_3d(smem_u32(b_lo), &tm_lo, 0, k0 / 4, n0 / 8, tbar);
+      }
+    } else {
+      tc_stage<BN>(B, ldb, N, K, n0, k0, vecB, b_hi, b_lo);
+    }
     tc_stage<TBM>(A, lda, M, K, m0, k0, vecA, a_hi, a_lo);
-    tc_stage<BN>(B, ldb, N, K, n0, k0, vecB, b_hi, b_lo);
     // make the generic-proxy smem writes visible to the tensor core
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && use_tma && !tc::mbar_wait(tbar, (uint32_t)((kb >> 1) & 1))) s_fail = 1;
+    if (tid == 0 && s_fail == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
       const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
@@ -235,18 +267,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, con
         mma_tf32(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
         mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, 1u);
       }
+    }
+    if (tid == 0)  // also when nothing was issued: keeps the phases in step
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               bst)
           : "memory");
-    }
     last = kb;
   }
   if (ok && last >= 0) {
     // the last commit covers every MMA issued before it
     const bool mine = mbar_wait(last & 1 ? bar1 : bar0, (uint32_t)((last >> 1) & 1));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    ok = __syncthreads_and(mine) != 0;
+    ok = __syncthreads_and(mine && s_fail == 0) != 0;
   }
   if (!ok) {
     // record the timeout, then give the MMAs in flight one more bounded wait
@@ -315,10 +348,100 @@ static constexpr int tc_smem_bytes() {
   return 1024 + 2 * (2 * TBM * TBK * 4 + 2 * BN * TBK * 4) + 64;
 }
 
+// Pre-split weight operands of an FC layer: dir 0 B = W [d_out][d_in]
+// (forward), dir 1 B = W^T [d_in][d_out] (back-substitution), each as hi / lo
+// arrays [Np / 8][Kp / 4][8][4] with their tensor maps.
+struct TcFc {
+  bool ok[2] = {false, false};
+  int N[2] = {0, 0}, K[2] = {0, 0};
+  CUtensorMap hi[2], lo[2];
+};
+
+namespace {
+
+__global__ void k_fc_split(const float* __restrict__ B, int N, int K, int Np, int Kp, float* hi,
+                           float* lo) {
+  const size_t total = (size_t)Np * Kp;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int n = (int)(q / Kp), k = (int)(q % Kp);
+    const float w = (n < N && k < K) ? B[(size_t)n * K + k] : 0.f;
+    const uint32_t h = tc::to_tf32(w);
+    const uint32_t l = tc::to_tf32(w - __uint_as_float(h));
+    const size_t o = (((size_t)(n >> 3) * (Kp / 4) + (k >> 2)) * 8 + (n & 7)) * 4 + (k & 3);
+    hi[o] = __uint_as_float(h);
+    lo[o] = __uint_as_float(l);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 fc_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+int fc_np(int N) { return (N + 7) / 8 * 8; }
+int fc_kp(int K) { return (K + TBK - 1) / TBK * TBK; }
+
+}  // namespace
+
+size_t tc_fc_floats(const LayerDev& L) {
+  if (L.kind != MNBAB_FC) return 0;
+  return 2 * ((size_t)fc_np(L.d_out) * fc_kp(L.d_in) + (size_t)fc_np(L.d_in) * fc_kp(L.d_out));
+}
+
+TcFc* tc_fc_create(const LayerDev& L, float* buf, cudaStream_t st) {
+  if (L.kind != MNBAB_FC || !buf || !L.W || !L.Wt) return nullptr;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = fc_encode_fn();
+  if (!enc) return nullptr;
+  TcFc* t = new TcFc();
+  size_t at = 0;
+  for (int dir = 0; dir < 2; ++dir) {
+    const float* B = dir == 0 ? L.W : L.Wt;
+    const int N = dir == 0 ? L.d_out : L.d_in, K = dir == 0 ? L.d_in : L.d_out;
+    const int Np = fc_np(N), Kp = fc_kp(K);
+    float* hi = buf + at;
+    float* lo = hi + (size_t)Np * Kp;
+    at += 2 * (size_t)Np * Kp;
+    const int blocks = (int)std::min<size_t>(4096, ((size_t)Np * Kp + 255) / 256);
+    k_fc_split<<<blocks, 256, 0, st>>>(B, N, K, Np, Kp, hi, lo);
+    // {32 floats = one 8 x 4 core matrix, Kp / 4, Np / 8}; a box is one
+    // K block (8 core matrices along K) of up to 32 row groups (BN <= 256)
+    const cuuint64_t gdim[3] = {32, (cuuint64_t)Kp / 4, (cuuint64_t)Np / 8};
+    const cuuint64_t gstr[2] = {128, (cuuint64_t)(Kp / 4) * 128};
+    bool good = true;
+    const cuuint32_t es[3] = {1, 1, 1};
+    // box height = the tile width launch_gemm_tc takes for this N
+    const int BN = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+    const cuuint32_t box[3] = {32, (cuuint32_t)TBK / 4, (cuuint32_t)BN / 8};
+    for (int part = 0; part < 2 && good; ++part)
+      good = enc(part == 0 ? &t->hi[dir] : &t->lo[dir], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                 part == 0 ? hi : lo, gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (!good) continue;
+    t->ok[dir] = true;
+    t->N[dir] = N;
+    t->K[dir] = K;
+  }
+  return t;
+}
+
+void tc_fc_destroy(TcFc* t) { delete t; }
+
 template <int BN>
-static int launch_bn(int M, int N, int K, const float* A, int lda, const float* B, int ldb,
-                     const float* bias, int bias_div, float* C, int ldc, const Epi& e, int* err,
-                     cudaStream_t st) {
+static int launch_bn(const TcFc* pre, int dir, int M, int N, int K, const float* A, int lda,
+                     const float* B, int ldb, const float* bias, int bias_div, float* C, int ldc,
+                     const Epi& e, int* err, cudaStream_t st) {
   constexpr int smem = tc_smem_bytes<BN>();
   static bool attr = false;
   if (!attr) {
@@ -326,18 +449,25 @@ static int launch_bn(int M, int N, int K, const float* A, int lda, const float* 
     attr = true;
   }
   dim3 grid((N + BN - 1) / BN, (M + TBM - 1) / TBM);
-  k_gemm_tc<BN><<<grid, TC_THREADS, smem, st>>>(M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e, err);
+  // the maps are built for this tile width (N decides BN on both sides)
+  const bool tma = pre && pre->ok[dir] && pre->N[dir] == N && pre->K[dir] == K;
+  static CUtensorMap none{};
+  k_gemm_tc<BN><<<grid, TC_THREADS, smem, st>>>(tma ? pre->hi[dir] : none,
+                                                tma ? pre->lo[dir] : none, tma ? 1 : 0, M, N, K,
+                                                A, lda, B, ldb, bias, bias_div, C, ldc, e, err);
   return grid.x;
 }
 
 // Tile width: the smallest of 64 / 128 / 256 that covers N in one tile, else 256.
 int launch_gemm_tc(int M, int N, int K, const float* A, int lda, const float* Bnk, int ldb,
                    const float* bias, int bias_div, float* C, int ldc, const Epi& e, int* err,
-                   cudaStream_t st) {
-  if (N <= 64) return launch_bn<64>(M, N, K, A, lda, Bnk, ldb, bias, bias_div, C, ldc, e, err, st);
+                   cudaStream_t st, const void* pre, int dir) {
+  const TcFc* p = static_cast<const TcFc*>(pre);
+  if (N <= 64)
+    return launch_bn<64>(p, dir, M, N, K, A, lda, Bnk, ldb, bias, bias_div, C, ldc, e, err, st);
   if (N <= 128)
-    return launch_bn<128>(M, N, K, A, lda, Bnk, ldb, bias, bias_div, C, ldc, e, err, st);
-  return launch_bn<256>(M, N, K, A, lda, Bnk, ldb, bias, bias_div, C, ldc, e, err, st);
+    return launch_bn<128>(p, dir, M, N, K, A, lda, Bnk, ldb, bias, bias_div, C, ldc, e, err, st);
+  return launch_bn<256>(p, dir, M, N, K, A, lda, Bnk, ldb, bias, bias_div, C, ldc, e, err, st);
 }
 
 }  // namespace mnbab
