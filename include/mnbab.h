@@ -149,6 +149,7 @@ typedef struct {
   int32_t split_layer;   /* ReLU layer (1-based) of the chosen split, 0 if none */
   int32_t split_neuron;
   int32_t fallback;      /* 1 if the split came from the intercept fallback score */
+  int32_t leaf;          /* 1 if the node had no unstable unsplit neuron left (a leaf) */
 } mnbab_trace_rec;
 
 /* ---- context ---------------------------------------------------------- */
@@ -341,6 +342,17 @@ mnbab_status mnbab_score_branches(mnbab_ctx* ctx, const mnbab_node_id* nodes, in
  * capacity. */
 mnbab_status mnbab_bab_step(mnbab_ctx* ctx, mnbab_prop* const* props, int32_t n_props,
                             int32_t max_nodes, const mnbab_adam* cfg, mnbab_step_stats* out);
+
+/* Exact completion of fully split leaves (Sec. 3.3: with every unstable
+ * neuron split, the network is affine on the node's region, and the bound
+ * maximised over beta, gamma reaches the region's exact minimum by LP duality).
+ * A node that has no unstable unsplit neuron left and whose bound does not
+ * verify it takes `steps` more projected Adam steps from its parameters: every
+ * iterate's bound is a certified lower bound (> 0 verifies the node), and the
+ * average of the iterates' minimisers over the second half of the steps is
+ * checked in FP64 as a counterexample (< 0 falsifies the property).  A leaf
+ * decided by neither stays UNKNOWN.  0 turns completion off; default 256. */
+mnbab_status mnbab_set_leaf_steps(mnbab_ctx* ctx, mnbab_prop* prop, int32_t steps);
 
 /* Per-property node budget (bounded nodes including roots); default 256. */
 mnbab_status mnbab_set_budget(mnbab_ctx* ctx, mnbab_prop* prop, int32_t max_nodes);

@@ -56,6 +56,7 @@ class NodeResult:
     # split was chosen from, and the node as queued (before step 1)
     scores: dict | None = None
     start: Node | None = None
+    leaf: bool = False              # resolved as a fully split leaf (exact LP)
 
 
 @dataclass
@@ -144,15 +145,31 @@ def children(node: Node, params, split, next_id: int):
     return out
 
 
+def leaf_exact(layers, C, d, node: Node, lo, hi):
+    """Exact minimum of a fully split leaf (Sec. 3.3: with every unstable neuron
+    split the network is affine on the leaf, so its minimum is a linear
+    program; the optimal-beta bound equals it).  Returns (value, argmin) from
+    exact.exact_min over the leaf's splits, FC networks only."""
+    from . import exact
+    splits = {(i, j): int(node.S[i][j]) for i in node.S
+              for j in torch.nonzero(node.S[i]).reshape(-1).tolist()}
+    return exact.exact_min(layers, C, d, node.row, np.asarray(lo), np.asarray(hi),
+                           splits=splits)
+
+
 def verify(layers, C, d, lo, hi, max_nodes=256, hp: AdamHP | None = None, mnc_fn=None,
-           rows=None, prepared=None, cab=False, inter_steps=0, record=False) -> PropResult:
+           rows=None, prepared=None, cab=False, inter_steps=0, record=False,
+           leaf_lp=None) -> PropResult:
     """BaB on every row of one property; verdict VERIFIED / FALSIFIED / UNKNOWN.
     With ``cab`` the split is chosen by the cost-adjusted ACS score.  With
     ``inter_steps`` > 0 the root's intermediate bounds are first optimised
     (``core.optimize_intermediate``, Sec. 3.1 parameter sharing, that many Adam
     steps at hp's rates) and shared by every row's root node.  With ``record``
     every node result also carries its starting state and its branching
-    scores (for the parity tests)."""
+    scores (for the parity tests).  A fully split leaf whose bound does not
+    decide it is resolved by its exact LP (``leaf_exact``) when the network is
+    fully connected (``leaf_lp`` None: whenever it is), else it stays an
+    UNKNOWN leaf."""
     hp = hp or AdamHP()
     net, lo_t, hi_t, l, u, S, mnc, dense = prepared or prepare(layers, C, d, lo, hi, mnc_fn)
     if inter_steps > 0:
@@ -181,7 +198,22 @@ def verify(layers, C, d, lo, hi, max_nodes=256, hp: AdamHP | None = None, mnc_fn
             if record:
                 nr.scores = scores
             if split is None:
-                unknown_leaf = True
+                if leaf_lp is None:
+                    leaf_lp = all(L["kind"] in ("fc", "relu") for L in layers)
+                if leaf_lp:
+                    v, xa = leaf_exact(layers, C, d, node, lo_t, hi_t)
+                    nr.leaf = True
+                    nr.lb = float(v)
+                    if v > 0:
+                        nr.verdict = VERIFIED
+                    else:
+                        fx = float(net.forward(torch.as_tensor(xa, dtype=DT)[None])[0, node.row])
+                        nr.f_xstar = fx
+                        nr.xstar = np.asarray(xa)
+                        nr.verdict = FALSIFIED if fx < 0 else UNKNOWN
+                        unknown_leaf = unknown_leaf or nr.verdict == UNKNOWN
+                else:
+                    unknown_leaf = True
             else:
                 nr.split = (split[0], split[1])
                 for ch in children(node, params, split, nid):

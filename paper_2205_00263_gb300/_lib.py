@@ -63,7 +63,7 @@ class TraceRec(C.Structure):
     _fields_ = [("seq", C.c_int64), ("row", C.c_int32), ("depth", C.c_int32), ("lb", C.c_float),
                 ("lb_deeppoly", C.c_float), ("f_xstar", C.c_float), ("verdict", C.c_int32),
                 ("split_layer", C.c_int32), ("split_neuron", C.c_int32),
-                ("fallback", C.c_int32)]
+                ("fallback", C.c_int32), ("leaf", C.c_int32)]
 
 
 FP = C.POINTER(C.c_float)
@@ -98,6 +98,7 @@ SIGNATURES = {
     "mnbab_bab_step": (status, [VP, C.POINTER(VP), C.c_int32, C.c_int32, C.POINTER(Adam),
                                 C.POINTER(StepStats)]),
     "mnbab_set_budget": (status, [VP, VP, C.c_int32]),
+    "mnbab_set_leaf_steps": (status, [VP, VP, C.c_int32]),
     "mnbab_set_branching": (status, [VP, VP, C.c_int32]),
     "mnbab_set_intermediate_steps": (status, [VP, VP, C.c_int32]),
     "mnbab_get_verdict": (status, [VP, VP, C.c_int32, IP, FP, FP]),

@@ -215,6 +215,10 @@ class Context:
                                             _fp(p), C.byref(n)))
         return idx, P, Ph, p
 
+    def set_leaf_steps(self, prop: Prop, steps: int):
+        """Adam steps of the exact completion of fully split leaves (0: off)."""
+        self._ck(self.lib.mnbab_set_leaf_steps(self.h, prop.h, steps))
+
     def set_budget(self, prop: Prop, n: int):
         self._ck(self.lib.mnbab_set_budget(self.h, prop.h, n))
 

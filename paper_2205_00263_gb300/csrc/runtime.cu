@@ -105,6 +105,7 @@ struct mnbab_net {
   // the batch buffers hold (null when icap = B: the batch buffers serve)
   float *iap = nullptr, *igar = nullptr, *igbr = nullptr;
   int icap = 0;
+  float* xsum = nullptr;  // leaf completion: summed minimisers [B][d0]
   // multi-neuron constraint generation: combination rows of one chunk
   int* gen_cidx = nullptr;
   float* gen_coef = nullptr;
@@ -137,6 +138,7 @@ struct mnbab_prop {
   bool admitted = true;              // false while queued in the request loop
   bool materialized = false;         // node slots allocated
   int inter_steps = 0;               // Adam steps of optimised root intermediate bounds
+  int leaf_steps = 256;              // Adam steps of the exact completion of fully split leaves
 };
 
 // A request of the serving loop.
@@ -928,6 +930,83 @@ void gather_best(mnbab_net* n, int M, float* host_out) {
   d2h(n->ctx, host_out, n->bestb, M);
 }
 
+__global__ void k_acc_rows(size_t n, const float* x, float* acc) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) acc[i] += x[i];
+}
+
+__global__ void k_scale_rows(size_t n, const float* x, float s, float* out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = x[i] * s;
+}
+
+// Exact completion of fully split nodes (Sec. 3.3): with every unstable neuron
+// split, the network is affine on the node's region, so maximising the bound
+// over beta (and gamma) reaches the region's exact minimum by LP duality, and
+// every iterate's bound is a certified lower bound.  `steps` more projected
+// Adam steps from the nodes' parameters (the node keeps the best bound); the
+// average of the iterates' minimisers x* over the second half of the steps
+// converges to a minimiser of the region and is checked in FP64 as a
+// counterexample candidate.  best, f64 (f_r at the average) and xavg [M][d0]
+// come back to the host.
+void leaf_complete(mnbab_net* n, const std::vector<int>& slots, int steps, const mnbab_adam& a,
+                   std::vector<float>& best, std::vector<double>& f64, std::vector<float>& xavg) {
+  mnbab_ctx* c = n->ctx;
+  const int M = (int)slots.size();
+  const size_t nx = (size_t)M * n->d0;
+  if (!n->xsum) n->xsum = dalloc_t<float>(c, (size_t)n->B * n->d0);
+  upload_batch(n, slots);
+  const bool g = batch_has_gamma(n, slots);
+  {
+    Scope sc(c, C_BOOK, 0.0, 16.0 * M * (n->SD + c->EC) + 4.0 * nx);
+    launch_zero_adam(M, n->bslots, n->pool, c->st);
+    launch_fill(n->xsum, nx, 0.f, c->st);
+  }
+  SweepOpts o;
+  o.final_mode = true;
+  o.has_gamma = g;
+  o.store = true;
+  o.track = true;
+  double b1t = 1.0, b2t = 1.0;
+  int cnt = 0;
+  for (int step = 0; step <= steps; ++step) {
+    if (g) {
+      Scope sc(c, C_GAMMA, 0.0, 4.0 * M * (c->EC + 2.0 * n->SD), 2);
+      launch_gamma_proj(M, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+    }
+    sweep(n, n->R + 1, obj_rows(n, M), o);  // x* of this iterate in n->X
+    if (2 * step >= steps) {
+      Scope sc(c, C_BOOK, 0.0, 12.0 * nx);
+      k_acc_rows<<<(unsigned)((nx + 255) / 256), 256, 0, c->st>>>(nx, n->X, n->xsum);
+      ++cnt;
+    }
+    if (step == steps) break;
+    adjoint(n, M, g);
+    b1t *= a.beta1;
+    b2t *= a.beta2;
+    Scope sc(c, C_ADAM, 0.0, 4.0 * M * (2.0 * n->SD + c->EC) * 8.0, 2);
+    launch_adam(M, n->bslots, n->pool, c->d_props, n->SD, n->GA, n->GB, n->GG, n->gmax,
+                a.grad_floor, a.lr_alpha, a.lr_beta, a.lr_gamma, a.beta1, a.beta2, a.eps,
+                a.eps_rel, (float)(1.0 - b1t), (float)(1.0 - b2t), c->st);
+  }
+  {
+    Scope sc(c, C_BOOK, 0.0, 8.0 * nx);
+    k_scale_rows<<<(unsigned)((nx + 255) / 256), 256, 0, c->st>>>(nx, n->xsum, 1.f / cnt, n->Xb);
+  }
+  {
+    Scope sc(c, C_BOOK, 0.0, 8.0 * M * n->maxd, n->R + 2);
+    launch_forward_f64(M, n->bslots, n->pool, c->d_props, n->nd, n->Xb, n->d0, n->f64a,
+                       n->d0 + n->SD, n->f64out, c->st);
+  }
+  f64.resize(M);
+  xavg.resize(nx);
+  d2h(c, f64.data(), n->f64out, M);
+  d2h(c, xavg.data(), n->Xb, nx);
+  best.resize(M);
+  gather_best(n, M, best.data());
+  sync(c);
+}
+
 void setup_net(mnbab_ctx* c, mnbab_net* n) {
   // dims
   n->maxd = n->d0;
@@ -1647,6 +1726,32 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
     std::vector<int> cand_of(Mo, -1);
     for (int k = 0; k < Mc; ++k) cand_of[cand_o[k]] = k;
     ht.lap(H_CONFIRM);
+    // exact completion of fully split leaves the bound does not decide (Sec. 3.3)
+    std::vector<int> leaf_of(Mo, -1);
+    std::vector<double> leaf_f64;
+    std::vector<float> leaf_x;
+    {
+      std::vector<int> lo_idx, ls;
+      int lsteps = 0;
+      for (int o = 0; o < Mo; ++o) {
+        const int i = opt_idx[o];
+        mnbab_prop* p = picked[i].p;
+        const bool cex = cand_of[o] >= 0 && f64[cand_of[o]] < 0.0;
+        if (acs_l[o] == 0 && !(best[i] > 0.f) && !cex && p->leaf_steps > 0 && !p->done) {
+          lo_idx.push_back(o);
+          ls.push_back(oslots[o]);
+          lsteps = std::max(lsteps, p->leaf_steps);
+        }
+      }
+      if (!ls.empty()) {
+        std::vector<float> lbest;
+        leaf_complete(n, ls, lsteps, adam, lbest, leaf_f64, leaf_x);
+        for (size_t k = 0; k < lo_idx.size(); ++k) {
+          leaf_of[lo_idx[k]] = (int)k;
+          best[opt_idx[lo_idx[k]]] = lbest[k];
+        }
+      }
+    }
     // host: verdicts, counterexample confirmation, children
     std::vector<int> par, lay, neu;
     std::vector<int> kidslots;
@@ -1665,6 +1770,7 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
       rec.verdict = MNBAB_UNKNOWN;
       const bool optimised = oi < Mo && opt_idx[oi] == i;
       const int o = optimised ? oi++ : -1;
+      rec.leaf = optimised && acs_l[o] == 0 ? 1 : 0;
       bool release = true;
       if (best[i] > 0.f) {
         rec.verdict = MNBAB_VERIFIED;
@@ -1680,6 +1786,19 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
               fals = true;
               if (!p->done) {
                 p->cex.assign(xc.begin() + (size_t)k * n->d0, xc.begin() + (size_t)(k + 1) * n->d0);
+                p->cex_row = q.row;
+              }
+            }
+          }
+          const int lk = leaf_of[o];
+          if (!fals && lk >= 0) {
+            // a completed leaf: the averaged minimiser, confirmed in FP64
+            rec.f_xstar = (float)leaf_f64[lk];
+            if (leaf_f64[lk] < 0.0) {
+              fals = true;
+              if (!p->done) {
+                p->cex.assign(leaf_x.begin() + (size_t)lk * n->d0,
+                              leaf_x.begin() + (size_t)(lk + 1) * n->d0);
                 p->cex_row = q.row;
               }
             }
@@ -2452,6 +2571,13 @@ mnbab_status mnbab_bab_step(mnbab_ctx* c, mnbab_prop* const* props, int32_t n_pr
   if (!props || !out) fail(MNBAB_E_INVALID_ARG, "null argument");
   const mnbab_adam a = cfg ? *cfg : default_adam();
   bab_step_impl(c, props, n_props, max_nodes, a, out);
+  API_END(c)
+}
+
+mnbab_status mnbab_set_leaf_steps(mnbab_ctx* c, mnbab_prop* p, int32_t steps) {
+  API_BEGIN(c)
+  if (!p || steps < 0) fail(MNBAB_E_INVALID_ARG, "bad step count");
+  p->leaf_steps = steps;
   API_END(c)
 }
 

@@ -186,6 +186,14 @@ def compare_trace(gtr, ores, max_cmp=None, recompute=None, sensitivity=None):
         assert abs(g["lb_deeppoly"] - o.lb_dp) <= dp_band, ("DeepPoly bound", k, g, o.lb_dp)
         band = TOL * (1 + abs(o.lb))
         gs = (g["split_layer"], g["split_neuron"]) if g["split_layer"] > 0 else None
+        if o.leaf:
+            # a fully split leaf: the oracle's exact LP minimum, the GPU's
+            # certified dual bound below it; the verdicts agree
+            assert g["leaf"] == 1 and g["lb"] <= o.lb + band, (k, g, o.lb)
+            if abs(o.lb) <= band:
+                return k, "margin"
+            assert g["verdict"] == o.verdict, (k, g, o.verdict)
+            continue
         bound_ok = abs(g["lb"] - o.lb) <= band
         if bound_ok and abs(o.lb) <= band:
             return k, "margin"

@@ -538,3 +538,32 @@ def test_resnet_soundness_random_parameters(seed):
         node.alpha = {i: _t(rng.uniform(0, 1, l[i].numel())) for i in l}
         lb, _, _ = core.final_bound(net, node, node.alpha, node.beta, node.gamma, None, lo_t, hi_t)
         assert float(lb) <= F[:, node.row].min() + 1e-9
+
+
+def _tiny_problem(seed, eps):
+    layers = synth.tiny_fc_net(seed, [2, 8, 8, 2])
+    x0 = np.random.default_rng(seed + 50).uniform(0.3, 0.7, 2).astype(np.float32)
+    y = synth.net_forward(layers, x0)
+    C, d = synth.property_rows(int(np.argmax(y)), 2)
+    lo, hi = synth.input_box(x0, eps)
+    return layers, C, d, lo, hi
+
+
+# radii within 5% of a critical radius (bisection on the exact minimum), where
+# the DeepPoly bound needs branching down to fully split leaves
+TINY_CASES = [(2, 0.30906), (2, 0.34159), (9, 0.42384), (1, 0.30496), (11, 0.11772)]
+
+
+@pytest.mark.parametrize("seed,eps", TINY_CASES)
+def test_unlimited_bab_with_exact_leaves_is_complete(seed, eps):
+    """Sec. 3.3 completeness: BaB with fully split leaves resolved exactly
+    reproduces the sign of the exact minimum of every property row (pattern
+    enumeration with one LP per pattern), here from the DeepPoly bound alone
+    (no Adam steps) so that leaves are reached."""
+    layers, C, d, lo, hi = _tiny_problem(seed, eps)
+    m = min(exact.exact_min(layers, C, d, r, lo, hi)[0] for r in range(C.shape[0]))
+    assert abs(m) > 1e-3
+    res = bab.verify(layers, C, d, lo, hi, max_nodes=100000, hp=core.AdamHP(steps=0))
+    assert res.verdict == (bab.VERIFIED if m > 0 else bab.FALSIFIED), (m, res.verdict)
+    if seed in (2, 9):
+        assert any(n.leaf for n in res.nodes)
