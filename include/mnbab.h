@@ -439,6 +439,19 @@ mnbab_status mnbab_request_result(mnbab_ctx* ctx, uint64_t ticket, int32_t* verd
 mnbab_status mnbab_attack(mnbab_ctx* ctx, const mnbab_prop* prop, int32_t n_starts, int32_t steps,
                           const float* starts, float* best_out, float* x_out);
 
+/* The pre-attack run when the property starts (Sec. 4, experimental setup:
+ * counterexamples are searched before branch-and-bound): mnbab_attack's sign
+ * steps (`steps` of them) from n_starts starting points, the box centre and
+ * n_starts - 1 points lo + (hi - lo) u with u_{k,j} = the top 53 bits of the
+ * SplitMix64 output at state seed + (i + 1) 0x9E3779B97F4A7C15,
+ * i = (k - 1) d0 + j, over [0, 1).  A row whose best point has a negative
+ * margin in FP64 (host forward pass) falsifies the property before any node is
+ * bounded; otherwise branch-and-bound proceeds as usual.  n_starts = 0 (the
+ * default) turns it off.  Call before the property starts; chain networks
+ * only (MNBAB_E_UNSUPPORTED otherwise). */
+mnbab_status mnbab_set_attack(mnbab_ctx* ctx, mnbab_prop* prop, int32_t n_starts, int32_t steps,
+                              uint64_t seed);
+
 /* Number of open nodes queued for the property. */
 mnbab_status mnbab_queue_size(const mnbab_ctx* ctx, const mnbab_prop* prop, int32_t* n_out);
 

@@ -69,3 +69,39 @@ def attack(layers, C, d, lo, hi, starts: np.ndarray, steps: int):
         best, bx, _ = pgd_row(net, lo, hi, r, starts, steps)
         out.append((best, bx))
     return out
+
+
+def splitmix64(state: int) -> tuple[int, int]:
+    """One output of SplitMix64 (Steele, Lea, Flood 2014; Vigna's reference
+    code): state += 0x9E3779B97F4A7C15, then two xor-shift-multiply rounds and a
+    final xor-shift.  Returns (output, new state)."""
+    m = (1 << 64) - 1
+    state = (state + 0x9E3779B97F4A7C15) & m
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31), state
+
+
+def splitmix_uniform(seed: int, index: int) -> float:
+    """Counter-based uniform in [0, 1): the top 53 bits of the SplitMix64
+    output at state seed + index * 0x9E3779B97F4A7C15 (its (index + 1)-th
+    output from state seed)."""
+    m = (1 << 64) - 1
+    out, _ = splitmix64((seed + index * 0x9E3779B97F4A7C15) & m)
+    return (out >> 11) * (1.0 / (1 << 53))
+
+
+def attack_starts(lo, hi, n_starts: int, seed: int) -> np.ndarray:
+    """Starting points of the pre-attack run inside branch-and-bound: the box
+    centre, then points lo + (hi - lo) u with u = splitmix_uniform(seed,
+    (k - 1) d0 + j) for start k >= 1 and coordinate j."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    d0 = lo.size
+    out = np.empty((n_starts, d0))
+    out[0] = 0.5 * (lo + hi)
+    for k in range(1, n_starts):
+        u = np.array([splitmix_uniform(seed, (k - 1) * d0 + j) for j in range(d0)])
+        out[k] = lo + (hi - lo) * u
+    return out

@@ -105,6 +105,7 @@ SIGNATURES = {
     "mnbab_get_trace": (status, [VP, VP, C.POINTER(TraceRec), C.c_int32, IP]),
     "mnbab_queue_size": (status, [VP, VP, IP]),
     "mnbab_attack": (status, [VP, VP, C.c_int32, C.c_int32, FP, FP, FP]),
+    "mnbab_set_attack": (status, [VP, VP, C.c_int32, C.c_int32, C.c_uint64]),
     "mnbab_profile": (status, [VP, C.c_int32]),
     "mnbab_profile_mask": (status, [VP, C.c_uint64]),
     "mnbab_submit": (status, [VP, VP, C.c_double, C.POINTER(C.c_uint64)]),

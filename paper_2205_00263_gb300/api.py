@@ -339,6 +339,10 @@ class Context:
         self._ck(self.lib.mnbab_queue_size(self.h, prop.h, C.byref(n)))
         return n.value
 
+    def set_attack(self, prop: Prop, n_starts: int, steps: int, seed: int = 0):
+        """Pre-attack when the property starts (box centre plus SplitMix64 starts)."""
+        self._ck(self.lib.mnbab_set_attack(self.h, prop.h, n_starts, steps, seed))
+
     def attack(self, prop: Prop, starts, steps: int):
         """Adversarial pre-attack (sign-step PGD per property row from the given
         starting points [n_starts][d0]); returns (best margin per row, minimisers)."""

@@ -139,6 +139,8 @@ struct mnbab_prop {
   bool materialized = false;         // node slots allocated
   int inter_steps = 0;               // Adam steps of optimised root intermediate bounds
   int leaf_steps = 256;              // Adam steps of the exact completion of fully split leaves
+  int atk_starts = 0, atk_steps = 0;  // pre-attack when the property starts (0: none)
+  uint64_t atk_seed = 0;
 };
 
 // A request of the serving loop.
@@ -1157,12 +1159,132 @@ void update_cab(mnbab_net* n, mnbab_prop* p) {
   }
 }
 
+// Adversarial pre-attack (Sec. 4): sign-step PGD on every property row from
+// n_starts starting points; best_out[r] / x_out[r] the row's smallest FP32
+// margin over all iterates and its first minimiser.
+void attack_impl(mnbab_ctx* c, const mnbab_prop* p, int n_starts, int steps, const float* starts,
+                 float* best_out, float* x_out) {
+  mnbab_net* n = p->net;
+  if (!attack_supported(n->nd))
+    fail(MNBAB_E_UNSUPPORTED, "the attack runs on chain networks whose weights fit in shared memory");
+  const int nr = p->n_rows, d0 = n->d0, nb = nr * n_starts;
+  const size_t need = (size_t)n_starts * d0 + nb + (size_t)nb * d0;
+  if (n->atk_cap < need) {
+    n->atk = dalloc_t<float>(c, need);
+    n->atk_cap = need;
+  }
+  float* dst = n->atk;
+  float* dbest = dst + (size_t)n_starts * d0;
+  float* dbx = dbest + nb;
+  h2d(c, dst, starts, (size_t)n_starts * d0);
+  {
+    Scope sc(c, C_BOOK, 0.0, 4.0 * nb * d0);
+    launch_attack_chain(n->nd, c->d_props, p->index, nr, dst, n_starts, steps, dbest, dbx, c->st);
+  }
+  std::vector<float> hb(nb), hx;
+  d2h(c, hb.data(), dbest, nb);
+  if (x_out) {
+    hx.resize((size_t)nb * d0);
+    d2h(c, hx.data(), dbx, hx.size());
+  }
+  sync(c);
+  for (int r = 0; r < nr; ++r) {
+    int bs = 0;
+    for (int s0 = 1; s0 < n_starts; ++s0)
+      if (hb[(size_t)r * n_starts + s0] < hb[(size_t)r * n_starts + bs]) bs = s0;  // first on ties
+    best_out[r] = hb[(size_t)r * n_starts + bs];
+    if (x_out)
+      std::memcpy(x_out + (size_t)r * d0, hx.data() + ((size_t)r * n_starts + bs) * d0,
+                  (size_t)d0 * sizeof(float));
+  }
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): the output at state
+// seed + index * 0x9E3779B97F4A7C15, top 53 bits as a uniform in [0, 1)
+double splitmix_uniform(uint64_t seed, uint64_t index) {
+  uint64_t z = seed + (index + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// f_r(x) of a chain network in FP64 on the host (counterexample confirmation
+// of the pre-attack): the affine layers of hops, ReLUs, the folded last layer.
+double host_margin(const mnbab_net* n, const mnbab_prop* p, int row, const float* x) {
+  std::vector<double> z(x, x + n->d0), h;
+  for (int t = 1; t <= n->R; ++t) {
+    const HostLayer& L = n->hops[n->eop[t][0]];
+    if (L.kind == MNBAB_FC) {
+      h.assign(L.co, 0.0);
+      for (int o = 0; o < L.co; ++o) {
+        double a = L.b[o];
+        for (int i = 0; i < L.ci; ++i) a += L.W[(size_t)o * L.ci + i] * z[i];
+        h[o] = a;
+      }
+    } else {
+      h.assign((size_t)L.co * L.ho * L.wo, 0.0);
+      for (int co = 0; co < L.co; ++co)
+        for (int oy = 0; oy < L.ho; ++oy)
+          for (int ox = 0; ox < L.wo; ++ox) {
+            double a = L.b[co];
+            for (int ci = 0; ci < L.ci; ++ci)
+              for (int ky = 0; ky < L.k; ++ky)
+                for (int kx = 0; kx < L.k; ++kx) {
+                  const int iy = oy * L.s - L.p + ky, ix = ox * L.s - L.p + kx;
+                  if (iy < 0 || iy >= L.hi || ix < 0 || ix >= L.wi) continue;
+                  a += L.W[(((size_t)co * L.ci + ci) * L.k + ky) * L.k + kx] *
+                       z[((size_t)ci * L.hi + iy) * L.wi + ix];
+                }
+            h[((size_t)co * L.ho + oy) * L.wo + ox] = a;
+          }
+    }
+    for (double& v : h) v = v > 0.0 ? v : 0.0;
+    z.swap(h);
+  }
+  const int dR = (int)z.size();
+  double f = p->bf[row];
+  for (int i = 0; i < dR; ++i) f += p->Wf[(size_t)row * dR + i] * z[i];
+  return f;
+}
+
+// The pre-attack of a property that starts (Sec. 4: counterexamples are
+// searched before branch-and-bound): the box centre and atk_starts - 1
+// SplitMix64 points, atk_steps sign steps; a row whose minimiser has a
+// negative FP64 margin falsifies the property before any node is bounded.
+bool pre_attack(mnbab_ctx* c, mnbab_prop* p) {
+  mnbab_net* n = p->net;
+  const int d0 = n->d0, ns = p->atk_starts;
+  std::vector<float> st((size_t)ns * d0), best(p->n_rows), x((size_t)p->n_rows * d0);
+  for (int j = 0; j < d0; ++j) st[j] = (float)(0.5 * ((double)p->lo[j] + (double)p->hi[j]));
+  for (int k = 1; k < ns; ++k)
+    for (int j = 0; j < d0; ++j) {
+      const double u = splitmix_uniform(p->atk_seed, (uint64_t)(k - 1) * d0 + j);
+      st[(size_t)k * d0 + j] = (float)((double)p->lo[j] + ((double)p->hi[j] - p->lo[j]) * u);
+    }
+  attack_impl(c, p, ns, p->atk_steps, st.data(), best.data(), x.data());
+  for (int r = 0; r < p->n_rows; ++r)
+    if (best[r] < 0.f && host_margin(n, p, r, x.data() + (size_t)r * d0) < 0.0) {
+      p->verdict = MNBAB_FALSIFIED;
+      p->done = true;
+      p->cex.assign(x.begin() + (size_t)r * d0, x.begin() + (size_t)(r + 1) * d0);
+      p->cex_row = r;
+      p->row_fals[r] = 1;
+      return true;
+    }
+  return false;
+}
+
 // Root bounds of every property of the network admitted since the last call,
 // computed together in one re-bounding pass, then their row root nodes.
 // Node slots of a property: the root-bound slot (l = -inf, u = +inf, re-bounded
 // from layer 1 with the next batch of admissions) and one root node per row.
 void materialize(mnbab_net* n, mnbab_prop* p) {
   mnbab_ctx* c = n->ctx;
+  if (p->atk_starts > 0 && pre_attack(c, p)) {
+    p->materialized = true;  // falsified before any node: nothing to bound
+    return;
+  }
   if ((int)n->free_slots.size() < p->n_rows + 1) fail(MNBAB_E_BUDGET, "node pool exhausted");
   const int rs = alloc_slot(n);
   p->root_slot = rs;
@@ -2790,39 +2912,21 @@ mnbab_status mnbab_attack(mnbab_ctx* c, const mnbab_prop* p, int32_t n_starts, i
   API_BEGIN(c)
   if (!p || n_starts <= 0 || steps < 1 || !starts || !best_out)
     fail(MNBAB_E_INVALID_ARG, "bad attack arguments");
-  mnbab_net* n = p->net;
-  if (!attack_supported(n->nd))
+  attack_impl(c, p, n_starts, steps, starts, best_out, x_out);
+  API_END(c)
+}
+
+mnbab_status mnbab_set_attack(mnbab_ctx* c, mnbab_prop* p, int32_t n_starts, int32_t steps,
+                              uint64_t seed) {
+  API_BEGIN(c)
+  if (!p || n_starts < 0 || (n_starts > 0 && steps < 1))
+    fail(MNBAB_E_INVALID_ARG, "bad attack arguments");
+  if (p->materialized) fail(MNBAB_E_INVALID_ARG, "property already started");
+  if (n_starts > 0 && !attack_supported(p->net->nd))
     fail(MNBAB_E_UNSUPPORTED, "the attack runs on chain networks whose weights fit in shared memory");
-  const int nr = p->n_rows, d0 = n->d0, nb = nr * n_starts;
-  const size_t need = (size_t)n_starts * d0 + nb + (size_t)nb * d0;
-  if (n->atk_cap < need) {
-    n->atk = dalloc_t<float>(c, need);
-    n->atk_cap = need;
-  }
-  float* dst = n->atk;
-  float* dbest = dst + (size_t)n_starts * d0;
-  float* dbx = dbest + nb;
-  h2d(c, dst, starts, (size_t)n_starts * d0);
-  {
-    Scope sc(c, C_BOOK, 0.0, 4.0 * nb * d0);
-    launch_attack_chain(n->nd, c->d_props, p->index, nr, dst, n_starts, steps, dbest, dbx, c->st);
-  }
-  std::vector<float> hb(nb), hx;
-  d2h(c, hb.data(), dbest, nb);
-  if (x_out) {
-    hx.resize((size_t)nb * d0);
-    d2h(c, hx.data(), dbx, hx.size());
-  }
-  sync(c);
-  for (int r = 0; r < nr; ++r) {
-    int bs = 0;
-    for (int s = 1; s < n_starts; ++s)
-      if (hb[(size_t)r * n_starts + s] < hb[(size_t)r * n_starts + bs]) bs = s;  // first on ties
-    best_out[r] = hb[(size_t)r * n_starts + bs];
-    if (x_out)
-      std::memcpy(x_out + (size_t)r * d0, hx.data() + ((size_t)r * n_starts + bs) * d0,
-                  (size_t)d0 * sizeof(float));
-  }
+  p->atk_starts = n_starts;
+  p->atk_steps = steps;
+  p->atk_seed = seed;
   API_END(c)
 }
 

@@ -83,3 +83,20 @@ def test_results_are_forward_margins_in_the_box_and_no_worse_than_starts():
         assert best == pytest.approx(y, abs=1e-9)
         f_starts = [attack.margin_and_grad(net, s, r)[0] for s in starts]
         assert best <= min(f_starts) + 1e-12
+
+
+def test_splitmix_starts_follow_the_published_generator():
+    """SplitMix64's first outputs from state 0 are the reference code's
+    0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4, 0x06c45d188009454f; the counter form
+    takes the (i + 1)-th output; starts are the box centre then box points."""
+    s, outs = 0, []
+    for _ in range(3):
+        o, s = attack.splitmix64(s)
+        outs.append(o)
+    assert outs == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert attack.splitmix_uniform(0, 1) == (0x6E789E6AA1B965F4 >> 11) / 2.0 ** 53
+    lo, hi = np.array([0.1, -1.0, 2.0]), np.array([0.3, 1.0, 2.5])
+    st = attack.attack_starts(lo, hi, 4, seed=7)
+    assert np.allclose(st[0], 0.5 * (lo + hi))
+    assert np.all(st >= lo) and np.all(st < hi)
+    assert len({tuple(r) for r in st}) == 4

@@ -11,6 +11,11 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def Context():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
     from paper_2205_00263_gb300 import Context as C
     return C
 
@@ -104,3 +109,90 @@ def test_residual_networks_are_refused(Context):
         p = ctx.set_property(net, lo, hi, C, d)
         with pytest.raises(MnbabError):
             ctx.attack(p, lo[None, :], steps=2)
+
+
+def _well_conditioned(net64, lo, hi, r, start, steps, rel=1e-4):
+    """Whether the FP64 sign-step trajectory of row r from `start` stays away
+    from decisions FP32 could take differently: every gradient component is
+    exactly 0 (no path reaches it, in any precision) or at least rel of the
+    largest, and no iterate at another point has a margin within 1e-4 of the
+    running minimum (the first minimiser is then determined)."""
+    x = np.clip(np.asarray(start, np.float64), lo, hi)
+    alpha = attack.step_size(lo, hi, steps)
+    best, bx = np.inf, None
+    for k in range(steps + 1):
+        f, g = attack.margin_and_grad(net64, x, r)
+        if bx is not None and not np.array_equal(x, bx) and abs(f - best) <= 1e-4 * (1 + abs(best)):
+            return False
+        if f < best:
+            best, bx = f, x.copy()
+        if k == steps:
+            return True
+        ga = np.abs(g)
+        if np.any((ga > 0) & (ga <= rel * ga.max())):
+            return False
+        x = np.clip(x - alpha * np.sign(g), lo, hi)
+
+
+@pytest.mark.parametrize("case", ["fc", "conv"])
+def test_multi_step_attack_matches_oracle(Context, case):
+    """Six sign steps from identical starts give the oracle's best margin and
+    minimiser on every row whose FP64 trajectory is well conditioned."""
+    if case == "fc":
+        layers = synth.tiny_fc_net(11, [12, 16, 9, 4])
+        x0 = np.random.default_rng(12).uniform(0.2, 0.8, 12).astype(np.float32)
+        y = synth.net_forward(layers, x0)
+        C, d = synth.property_rows(int(np.argmax(y)), 4)
+        lo, hi = synth.input_box(x0, 0.1)
+    else:
+        layers, C, d, lo, hi, _ = conv_case(6, 0.05)
+    lo64, hi64 = lo.astype(np.float64), hi.astype(np.float64)
+    net64 = core.fold_property(core.load_net(layers), C, d)
+    rng = np.random.default_rng(21)
+    checked = 0
+    with Context(node_capacity=64) as ctx:
+        net = ctx.load_network(layers)
+        p = ctx.set_property(net, lo, hi, C, d)
+        for _ in range(16):
+            s = (lo + (hi - lo) * rng.uniform(size=lo.size)).astype(np.float32)
+            best, x = ctx.attack(p, s[None, :], steps=6)
+            for r in range(C.shape[0]):
+                if not _well_conditioned(net64, lo64, hi64, r, s.astype(np.float64), 6):
+                    continue
+                rb, rx, _ = attack.pgd_row(net64, lo64, hi64, r, s[None, :].astype(np.float64), 6)
+                assert abs(best[r] - rb) <= TOL * (1 + abs(rb)), (r, best[r], rb)
+                assert np.allclose(x[r], rx, rtol=0, atol=1e-5)
+                checked += 1
+    assert checked >= 4
+
+
+def test_pre_attack_in_bab_falsifies_before_any_node(Context):
+    """mnbab_set_attack: when the property starts, the attack from the box
+    centre and SplitMix64 starts runs first; a property the oracle's attack
+    (same starts) falsifies is FALSIFIED with no node bounded and a
+    counterexample that holds in FP64; one it does not falsify goes on to
+    branch-and-bound."""
+    layers = synth.make_network(1)
+    prs = synth.make_properties(1, layers, n=6, eps=synth.load_eps(1))
+    seen = {True: 0, False: 0}
+    with Context(node_capacity=4096) as ctx:
+        net = ctx.load_network(layers)
+        for k, pr in enumerate(prs):
+            starts = attack.attack_starts(pr.lo, pr.hi, 4, seed=100 + k)
+            ref = attack.attack(layers, pr.C, pr.d, pr.lo, pr.hi, starts, steps=20)
+            o_fals = min(b for b, _ in ref) < -1e-4
+            p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+            ctx.set_attack(p, 4, 20, seed=100 + k)
+            ctx.set_budget(p, 16)
+            ctx.bab_step([p], max_nodes=64, steps=20)
+            v, _, xc = ctx.verdict(p)
+            if o_fals:
+                assert v == -1 and len(ctx.trace(p)) == 0, k
+                assert np.all(xc >= pr.lo) and np.all(xc <= pr.hi)
+                assert (pr.C @ synth.net_forward(layers, xc.astype(np.float64)) + pr.d).min() < 0
+            elif min(b for b, _ in ref) > 1e-4:
+                assert len(ctx.trace(p)) > 0
+            seen[o_fals] += 1
+        with pytest.raises(Exception):
+            ctx.set_attack(p, 4, 20)   # already started
+    assert seen[True] >= 1
