@@ -194,7 +194,9 @@ mnbab_status mnbab_set_mnc(mnbab_ctx* ctx, mnbab_prop* prop, int32_t relu_layer,
 /* Generates and uploads the multi-neuron constraints of every ReLU layer of a
  * property (Sec. 3.1, enforcing multi-neuron constraints; the paper takes them
  * from PRIMA and gives no generator).  This library's construction, from the
- * property's DeepPoly root bounds (the property is started if it was not):
+ * property's root bounds (the property is started if it was not; DeepPoly
+ * bounds, or the optimised ones when mnbab_set_intermediate_steps asked for
+ * them, whose sets then hold no constraints):
  *  - groups: the unstable neurons of the layer in the order of decreasing
  *    -l u / (u - l) (ties by index), taken as sliding triples (j0, j1, j2),
  *    (j1, j2, j3), ..., at most max_groups per layer;
@@ -297,9 +299,11 @@ mnbab_status mnbab_optimize(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t 
  * and the node's bounds of layer t are intersected with them before layer
  * t + 1.  Works on each node's current bounds (re-bound split nodes first,
  * e.g. with mnbab_bound_batch); the nodes' own parameters are unchanged.
+ * With multi-neuron constraints a set also holds gamma (Sec. 3.1: gamma is a
+ * parameter like alpha and beta) for the constraints of the layers below t,
+ * started at 0 and stepped at lr_gamma; the other multipliers stay 0.
  * At most half the context's batch capacity of nodes per call, each listed
- * once (a repeated node is MNBAB_E_INVALID_ARG); properties with multi-neuron
- * constraints return MNBAB_E_UNSUPPORTED.  *rows_out (nullable) receives the
+ * once (a repeated node is MNBAB_E_INVALID_ARG).  *rows_out (nullable) receives the
  * number of rows bounded.  Scratch node slots are taken from the pool for the
  * duration of the call (MNBAB_E_BUDGET if it is full).  The rows of one layer
  * (2 x unstable neurons x nodes) must fit the network's row scratch
@@ -315,8 +319,9 @@ mnbab_status mnbab_optimize_intermediate(mnbab_ctx* ctx, const mnbab_node_id* no
  * root nodes take them; 0 (the default) keeps the DeepPoly root bounds.  Call
  * before the property starts (MNBAB_E_INVALID_ARG after), on a context whose
  * batch capacity is at least 2 (node_capacity >= 4; MNBAB_E_INVALID_ARG
- * otherwise); properties with multi-neuron constraints return
- * MNBAB_E_UNSUPPORTED (and mnbab_set_mnc refuses a property with steps > 0). */
+ * otherwise).  The root's sets use the constraints uploaded by then (none when
+ * mnbab_generate_mnc starts the property: it generates from the optimised
+ * root bounds). */
 mnbab_status mnbab_set_intermediate_steps(mnbab_ctx* ctx, mnbab_prop* prop, int32_t steps);
 
 /* ACS branching score (Sec. 3.2) at each node's current parameters:

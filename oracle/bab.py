@@ -174,7 +174,8 @@ def verify(layers, C, d, lo, hi, max_nodes=256, hp: AdamHP | None = None, mnc_fn
     net, lo_t, hi_t, l, u, S, mnc, dense = prepared or prepare(layers, C, d, lo, hi, mnc_fn)
     if inter_steps > 0:
         root = root_node(net, 0, l, u, S, mnc)
-        core.optimize_intermediate(net, root, lo_t, hi_t, replace(hp, steps=inter_steps))
+        core.optimize_intermediate(net, root, lo_t, hi_t, replace(hp, steps=inter_steps),
+                                   dense_mnc=dense)
         l, u = root.l, root.u
     costs = core.cab_costs(net, {i: m.idx.shape[0] for i, m in mnc.items()} if mnc else None) \
         if cab else None

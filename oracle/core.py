@@ -570,9 +570,11 @@ def noise_sensitivity(net, node: Node, dense_mnc, lo, hi, hp: AdamHP, seeds=(1, 
 # ----------------------------------------------------------------------------
 # Optimised intermediate bounds (Sec. 3.1, parameter sharing)
 # ----------------------------------------------------------------------------
-def intermediate_objective(net: Net, node: Node, t: int, idx, side: int, alpha, beta, lo, hi):
+def intermediate_objective(net: Net, node: Node, t: int, idx, side: int, alpha, beta, lo, hi,
+                           gamma=None, dense_mnc=None):
     """Lower bounds of the rows side * e_j (j in idx) of zhat^(t) with one
-    parameter set (alpha_i, beta_i for i < t) shared by every row.
+    parameter set (alpha_i, beta_i and, with multi-neuron constraints, gamma_i
+    for i < t) shared by every row.
 
     side = +1 gives lower bounds of zhat_j, side = -1 lower bounds of -zhat_j
     (the upper bounds, negated).  Returns the per-row bounds; their sum is the
@@ -580,26 +582,40 @@ def intermediate_objective(net: Net, node: Node, t: int, idx, side: int, alpha, 
     """
     E = torch.zeros(idx.numel(), node.l[t].numel(), dtype=DT)
     E[torch.arange(idx.numel()), idx] = float(side)
-    relax = {i: Relax(node.l[i], node.u[i], node.S[i], alpha[i], beta[i]) for i in range(1, t)}
+    relax = {}
+    for i in range(1, t):
+        GP = GPh = gp0 = None
+        if gamma is not None and dense_mnc and i in dense_mnc and gamma[i].numel() > 0:
+            Pd, Phd, pv = dense_mnc[i]
+            GP, GPh, gp0 = gamma[i] @ Pd, gamma[i] @ Phd, gamma[i] @ pv
+        relax[i] = Relax(node.l[i], node.u[i], node.S[i], alpha[i], beta[i], GP, GPh, gp0)
     lb, _, _ = backsub_rows(net, t, E, relax, lo, hi)
     return lb
 
 
-def intermediate_objective_grad(net: Net, node: Node, t: int, idx, side: int, alpha, beta, lo, hi):
-    """Per-row bounds and the gradient of their sum w.r.t. the shared set."""
+def intermediate_objective_grad(net: Net, node: Node, t: int, idx, side: int, alpha, beta, lo, hi,
+                                gamma=None, dense_mnc=None):
+    """Per-row bounds and the gradient of their sum w.r.t. the shared set
+    (alpha, beta, and gamma when given)."""
     a = {i: alpha[i].detach().clone().requires_grad_(True) for i in alpha}
     b = {i: beta[i].detach().clone().requires_grad_(True) for i in beta}
-    lb = intermediate_objective(net, node, t, idx, side, a, b, lo, hi)
+    g = ({i: gamma[i].detach().clone().requires_grad_(True) for i in gamma}
+         if gamma is not None else None)
+    lb = intermediate_objective(net, node, t, idx, side, a, b, lo, hi, g, dense_mnc)
     keys = list(a.keys())
-    grads = torch.autograd.grad(lb.sum(), [a[k] for k in keys] + [b[k] for k in keys],
-                                allow_unused=True)
+    leaves = [a[k] for k in keys] + [b[k] for k in keys] + ([g[k] for k in keys] if g else [])
+    grads = torch.autograd.grad(lb.sum(), leaves, allow_unused=True)
     n = len(keys)
-    ga = {k: (g if g is not None else torch.zeros_like(a[k])) for k, g in zip(keys, grads[:n])}
-    gb = {k: (g if g is not None else torch.zeros_like(b[k])) for k, g in zip(keys, grads[n:])}
-    return lb.detach(), ga, gb
+    ga = {k: (x if x is not None else torch.zeros_like(a[k])) for k, x in zip(keys, grads[:n])}
+    gb = {k: (x if x is not None else torch.zeros_like(b[k])) for k, x in zip(keys, grads[n:2 * n])}
+    if g is None:
+        return lb.detach(), ga, gb
+    gg = {k: (x if x is not None else torch.zeros_like(g[k])) for k, x in zip(keys, grads[2 * n:])}
+    return lb.detach(), ga, gb, gg
 
 
-def optimize_intermediate(net: Net, node: Node, lo, hi, hp: AdamHP, first_layer: int = 2):
+def optimize_intermediate(net: Net, node: Node, lo, hi, hp: AdamHP, first_layer: int = 2,
+                          dense_mnc=None):
     """Optimised intermediate bounds of a node (Sec. 3.1: intermediate bounds
     come from the same bounding procedure; each layer's neurons share one
     parameter set, with separate sets for lower and upper bounds).
@@ -607,17 +623,18 @@ def optimize_intermediate(net: Net, node: Node, lo, hi, hp: AdamHP, first_layer:
     For t = max(2, first_layer) .. R in order (layer 1 bounds over the box are
     exact already): the rows are the unstable, unsplit neurons j of layer t,
     once with side +1 (lower bounds) and once with side -1 (upper bounds).  Each
-    side has one set (alpha_i, beta_i for the ReLU layers i < t) shared by all
-    its rows, started at DeepPoly slopes and beta = 0, and takes hp.steps
-    projected Adam steps (as in ``optimize``) ascending sum_j lb_j.  Every
-    iterate gives valid bounds, so each row keeps the best bound it reached
-    (the first iterate is the DeepPoly bound); the node's bounds of layer t are
-    intersected with them before layer t + 1 is bounded.  Returns the number of
-    rows bounded.
+    side has one set (alpha_i, beta_i for the ReLU layers i < t, and with
+    multi-neuron constraints gamma_i of those layers' constraints) shared by
+    all its rows, started at DeepPoly slopes, beta = 0 and gamma = 0, and takes
+    hp.steps projected Adam steps (as in ``optimize``) ascending sum_j lb_j.
+    Every iterate gives valid bounds, so each row keeps the best bound it
+    reached (the first iterate is the DeepPoly bound); the node's bounds of
+    layer t are intersected with them before layer t + 1 is bounded.  Returns
+    the number of rows bounded.
     """
     R = net.R
     total = 0
-    lr = {"a": hp.lr_alpha, "b": hp.lr_beta}
+    lr = {"a": hp.lr_alpha, "b": hp.lr_beta, "g": hp.lr_gamma}
     for t in range(max(2, first_layer), R + 1):
         l, u, S = node.l[t], node.u[t], node.S[t]
         idx = torch.nonzero((l < 0) & (u > 0) & (S == 0)).reshape(-1)
@@ -627,23 +644,34 @@ def optimize_intermediate(net: Net, node: Node, lo, hi, hp: AdamHP, first_layer:
         for side in (1, -1):
             alpha = {i: deeppoly_alpha(node.l[i], node.u[i]) for i in range(1, t)}
             beta = {i: torch.zeros_like(node.l[i]) for i in range(1, t)}
-            state = {(g, i): (torch.zeros_like(node.l[i]), torch.zeros_like(node.l[i]))
-                     for g in ("a", "b") for i in range(1, t)}
+            gamma = None
+            if dense_mnc:
+                gamma = {i: torch.zeros(dense_mnc[i][2].numel() if i in dense_mnc else 0, dtype=DT)
+                         for i in range(1, t)}
+            groups = {"a": alpha, "b": beta}
+            if gamma is not None:
+                groups["g"] = gamma
+            state = {(g, i): (torch.zeros_like(P[i]), torch.zeros_like(P[i]))
+                     for g, P in groups.items() for i in P}
             bs = torch.full((idx.numel(),), -math.inf, dtype=DT)
             for step in range(hp.steps + 1):
-                lb, ga, gb = intermediate_objective_grad(net, node, t, idx, side, alpha, beta,
-                                                         lo, hi)
+                out = intermediate_objective_grad(net, node, t, idx, side, alpha, beta, lo, hi,
+                                                  gamma, dense_mnc)
+                lb, grads = out[0], {"a": out[1], "b": out[2]}
+                if gamma is not None:
+                    grads["g"] = out[3]
                 bs = torch.maximum(bs, lb)
                 if step == hp.steps:
                     break
                 k = step + 1
-                gmax = max([float(G[i].abs().max()) for G in (ga, gb) for i in G
+                gmax = max([float(G[i].abs().max()) for G in grads.values() for i in G
                             if G[i].numel()] + [0.0])
                 floor = hp.grad_floor * gmax
                 eps = max(hp.eps, hp.eps_rel * gmax)
-                for grp, P, G in (("a", alpha, ga), ("b", beta, gb)):
+                for grp, P in groups.items():
                     for i in P:
-                        g = torch.where(G[i].abs() <= floor, torch.zeros_like(G[i]), G[i])
+                        g = grads[grp][i]
+                        g = torch.where(g.abs() <= floor, torch.zeros_like(g), g)
                         m, v = state[(grp, i)]
                         m = hp.b1 * m + (1 - hp.b1) * g
                         v = hp.b2 * v + (1 - hp.b2) * g * g

@@ -292,11 +292,13 @@ class Context:
         self._ck(self.lib.mnbab_set_intermediate_steps(self.h, prop.h, steps))
 
     def optimize_intermediate(self, nodes, first_layer=2, steps=20, lr_alpha=0.1, lr_beta=0.05,
-                              beta1=0.9, beta2=0.999, eps=1e-8, grad_floor=0.0, eps_rel=0.0):
-        """Optimised intermediate bounds of the nodes (shared per-layer sets);
-        returns the number of rows bounded."""
+                              beta1=0.9, beta2=0.999, eps=1e-8, grad_floor=0.0, eps_rel=0.0,
+                              lr_gamma=0.05):
+        """Optimised intermediate bounds of the nodes (shared per-layer sets of
+        alpha, beta and, with multi-neuron constraints, gamma); returns the
+        number of rows bounded."""
         ids, n = self._ids(nodes)
-        a = L.Adam(steps, lr_alpha, lr_beta, lr_beta, beta1, beta2, eps, grad_floor, eps_rel)
+        a = L.Adam(steps, lr_alpha, lr_beta, lr_gamma, beta1, beta2, eps, grad_floor, eps_rel)
         rows = C.c_int64()
         self._ck(self.lib.mnbab_optimize_intermediate(self.h, ids, n, first_layer, C.byref(a),
                                                       C.byref(rows)))

@@ -1940,7 +1940,7 @@ void launch_children(int nb, const int* parents, const int* kids, const int* lay
 // set of one (node, target layer, side) lives in a scratch pool slot.
 // ---------------------------------------------------------------------------
 // Set slot dst[b] from node src[b]: bounds and splits, DeepPoly slopes
-// (alpha = 1 if u >= -l else 0), beta = 0, zero Adam moments.
+// (alpha = 1 if u >= -l else 0), beta = 0, gamma = 0, zero Adam moments.
 __global__ void k_set_init(const int* src, const int* dst, PoolDev pool) {
   const int b = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1958,6 +1958,13 @@ __global__ void k_set_init(const int* src, const int* dst, PoolDev pool) {
     pool.MB[qd] = 0.f;
     pool.VB[qd] = 0.f;
   }
+  if (i < pool.EC) {
+    // multi-neuron multipliers start at 0 with zero moments
+    const size_t qd = (size_t)d * pool.EC + i;
+    pool.GAM[qd] = 0.f;
+    pool.MG[qd] = 0.f;
+    pool.VG[qd] = 0.f;
+  }
   if (i == 0) {
     pool.prop[d] = pool.prop[s];
     pool.row[d] = pool.row[s];
@@ -1966,7 +1973,7 @@ __global__ void k_set_init(const int* src, const int* dst, PoolDev pool) {
 
 void launch_set_init(int nsets, const int* src, const int* dst, PoolDev pool, cudaStream_t st) {
   if (nsets <= 0) return;
-  dim3 grid((pool.SD + 255) / 256, nsets);
+  dim3 grid((std::max(pool.SD, pool.EC) + 255) / 256, nsets);
   k_set_init<<<grid, 256, 0, st>>>(src, dst, pool);
 }
 
@@ -2004,6 +2011,33 @@ void launch_set_grad(int nseg, const int* seg, int SD, int lim, const float* GA,
   if (nseg <= 0 || lim <= 0) return;
   dim3 grid((lim + 255) / 256, nseg);
   k_set_grad<<<grid, 256, 0, st>>>(seg, SD, lim, GA, GB, IGA, IGB);
+}
+
+// Adds the per-row gradients GG ([row][EC]) w.r.t. the multi-neuron
+// multipliers of each set's rows to the set's gradient IGG ([set][EC]), rows
+// in order; only constraints of ReLU layers below t (the layers the rows pass)
+// get a gradient, every other entry stays 0 (those multipliers stay 0).
+__global__ void k_set_grad_gamma(const int* seg, const int* set_slot, PoolDev pool,
+                                 const PropDev* props, int t, const float* GG, float* IGG) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = seg[3 * blockIdx.y], r0 = seg[3 * blockIdx.y + 1], r1 = seg[3 * blockIdx.y + 2];
+  const PropDev& P = props[pool.prop[set_slot[s]]];
+  if (e >= P.E) return;
+  bool below = false;
+  for (int i = 1; i < t && i <= MNBAB_MAXR; ++i)
+    if (e >= P.mnc[i].goff && e < P.mnc[i].goff + P.mnc[i].e) below = true;
+  if (!below) return;
+  float g = 0.f;
+  for (int m = r0; m < r1; ++m) g += GG[(size_t)m * pool.EC + e];
+  IGG[(size_t)s * pool.EC + e] += g;
+}
+
+void launch_set_grad_gamma(int nseg, const int* seg, const int* set_slot, PoolDev pool,
+                           const PropDev* props, int t, const float* GG, float* IGG,
+                           cudaStream_t st) {
+  if (nseg <= 0 || pool.EC <= 0) return;
+  dim3 grid((pool.EC + 255) / 256, nseg);
+  k_set_grad_gamma<<<grid, 256, 0, st>>>(seg, set_slot, pool, props, t, GG, IGG);
 }
 
 // Intersects the bounds of neuron j[m] of the layer at offset off of node

@@ -266,6 +266,10 @@ void launch_set_init(int nsets, const int* src, const int* dst, PoolDev pool, cu
 void launch_rows_best(int M, const float* lb, float* best, int first, cudaStream_t st);
 void launch_set_grad(int nseg, const int* seg, int SD, int lim, const float* GA, const float* GB,
                      float* IGA, float* IGB, cudaStream_t st);
+// per-set gradient of the multipliers of constraints in ReLU layers below t
+void launch_set_grad_gamma(int nseg, const int* seg, const int* set_slot, PoolDev pool,
+                           const PropDev* props, int t, const float* GG, float* IGG,
+                           cudaStream_t st);
 void launch_set_update(int M, const int* orig, const int* j, const float* sign, const float* best,
                        PoolDev pool, int off, cudaStream_t st);
 // Root nodes: slots[i] initialised from root-bound slot srcs[i] for row rows[i].

@@ -99,6 +99,7 @@ struct mnbab_net {
   // optimised intermediate bounds (allocated on first use): per-set gradients
   // [B][SD], per-row best bounds and owning nodes, chunk segments, set slots
   float *iga = nullptr, *igb = nullptr, *ibest = nullptr;
+  float* igg = nullptr;  // per-set gradients of the multi-neuron multipliers [B][EC]
   int *iorig = nullptr, *iseg = nullptr, *isrc = nullptr, *idst = nullptr;
   size_t iseg_cap = 0;
   // per-row a' checkpoints and gradients [icap][SD] of longer row chunks than
@@ -1343,7 +1344,13 @@ int64_t optimize_intermediate_impl(mnbab_net* n, const std::vector<int>& slots, 
     n->iseg_cap = 3 * ((size_t)n->B + n->rows_cap / std::min(n->icap, n->chunk) + 2);
     n->iseg = dalloc_t<int>(c, n->iseg_cap);
   }
-  const int CH = std::max(1, std::min(n->icap, n->chunk));
+  // properties with multi-neuron constraints: the sets hold gamma as well, and
+  // the rows' gamma projections and gradients use the batch buffers
+  bool has_g = false;
+  for (int s0 : slots) has_g = has_g || c->props[n->slot_prop[s0]]->pd.E > 0;
+  if (has_g && !n->igg) n->igg = dalloc_t<float>(c, (size_t)n->B * c->EC);
+  const int CH = has_g ? std::max(1, std::min(n->B, n->chunk))
+                       : std::max(1, std::min(n->icap, n->chunk));
   // the sweeps and adjoints of this call use the per-row buffers above (and
   // read each row's slot from bslots); restored on every exit
   struct Swap {
@@ -1357,7 +1364,7 @@ int64_t optimize_intermediate_impl(mnbab_net* n, const std::vector<int>& slots, 
       n->bslots = bs;
     }
   } swap{n, n->AP, n->GA, n->GB, n->bslots};
-  if (n->iap) {
+  if (n->iap && !has_g) {
     n->AP = n->iap;
     n->GA = n->igar;
     n->GB = n->igbr;
@@ -1444,6 +1451,7 @@ int64_t optimize_intermediate_impl(mnbab_net* n, const std::vector<int>& slots, 
     }
     SweepOpts o;
     o.final_mode = true;
+    o.has_gamma = has_g;
     double b1t = 1.0, b2t = 1.0;
     for (int step = 0; step <= a.steps; ++step) {
       const bool grad = step < a.steps;
@@ -1451,10 +1459,17 @@ int64_t optimize_intermediate_impl(mnbab_net* n, const std::vector<int>& slots, 
       if (grad) {
         ck(cudaMemsetAsync(n->iga, 0, (size_t)nsets * SD * sizeof(float), c->st), "memset");
         ck(cudaMemsetAsync(n->igb, 0, (size_t)nsets * SD * sizeof(float), c->st), "memset");
+        if (has_g)
+          ck(cudaMemsetAsync(n->igg, 0, (size_t)nsets * c->EC * sizeof(float), c->st), "memset");
       }
       for (int ci = 0, c0 = 0; c0 < M; ++ci, c0 += CH) {
         const int Mc = std::min(CH, M - c0);
         RowsDev r{Mc, n->row_node + c0, n->row_j + c0, n->row_sign + c0};
+        if (has_g) {
+          // gamma^T P, gamma^T Phat, gamma^T p of each row's set
+          Scope sc(c, C_GAMMA, 0.0, 4.0 * Mc * (c->EC + 2.0 * n->SD), 2);
+          launch_gamma_proj(Mc, r.node, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->gp0, c->st);
+        }
         sweep(n, t, r, o);
         {
           Scope sc(c, C_BOOK, 0.0, 12.0 * Mc);
@@ -1463,17 +1478,21 @@ int64_t optimize_intermediate_impl(mnbab_net* n, const std::vector<int>& slots, 
         if (!grad) continue;
         // the adjoint reads each row's slot from bslots: point it at the chunk's rows
         n->bslots = n->row_node + c0;
-        adjoint(n, Mc, false, t - 1);
+        adjoint(n, Mc, has_g, t - 1);
         const int ns = seg_at[ci + 1] - seg_at[ci];
         Scope sc(c, C_ADAM, 0.0, 8.0 * (double)Mc * off + 16.0 * ns * off);
         launch_set_grad(ns, n->iseg + 3 * seg_at[ci], SD, off, n->GA, n->GB, n->iga, n->igb,
                         c->st);
+        if (has_g)
+          launch_set_grad_gamma(ns, n->iseg + 3 * seg_at[ci], n->idst, n->pool, c->d_props, t,
+                                n->GG, n->igg, c->st);
       }
       if (!grad) break;
       b1t *= a.beta1;
       b2t *= a.beta2;
       Scope sc(c, C_ADAM, 0.0, 4.0 * nsets * 2.0 * SD * 8.0, 2);
-      launch_adam(nsets, n->idst, n->pool, c->d_props, SD, n->iga, n->igb, n->GG, n->gmax,
+      launch_adam(nsets, n->idst, n->pool, c->d_props, SD, n->iga, n->igb,
+                  has_g ? n->igg : n->GG, n->gmax,
                   a.grad_floor, a.lr_alpha, a.lr_beta, a.lr_gamma, a.beta1, a.beta2, a.eps,
                   a.eps_rel, (float)(1.0 - b1t), (float)(1.0 - b2t), c->st);
     }
@@ -1564,8 +1583,6 @@ void ensure_roots(mnbab_net* n, mnbab_prop* const* only = nullptr, int n_only = 
 void set_mnc_impl(mnbab_ctx* c, mnbab_prop* p, int layer, int n_rows, int k, const int32_t* idx,
                   const float* P, const float* Phat, const float* pv) {
   if (p->mnc_set[layer]) fail(MNBAB_E_INVALID_ARG, "constraints of this layer already set");
-  if (p->inter_steps > 0)
-    fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
   mnbab_net* n = p->net;
   const int d = n->nd.d[layer];
   if (p->pd.E + n_rows > c->EC)
@@ -1629,8 +1646,6 @@ int64_t generate_mnc_impl(mnbab_ctx* c, mnbab_prop* p, int max_groups) {
   mnbab_net* n = p->net;
   for (int t = 1; t <= n->R; ++t)
     if (p->mnc_set[t]) fail(MNBAB_E_INVALID_ARG, "constraints of a layer are already set");
-  if (p->inter_steps > 0)
-    fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
   mnbab_prop* only[1] = {p};
   ensure_roots(n, only, 1);
   if (p->root_slot < 0) fail(MNBAB_E_INVALID_ARG, "property not admitted");
@@ -2636,9 +2651,6 @@ mnbab_status mnbab_optimize_intermediate(mnbab_ctx* c, const mnbab_node_id* node
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
       fail(MNBAB_E_INVALID_ARG, "a node is listed twice");
   }
-  for (int s : slots)
-    if (c->props[n->slot_prop[s]]->pd.E > 0)
-      fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
   const int64_t total = optimize_intermediate_impl(n, slots, first_layer, a);
   if (rows_out) *rows_out = total;
   API_END(c)
@@ -2648,8 +2660,6 @@ mnbab_status mnbab_set_intermediate_steps(mnbab_ctx* c, mnbab_prop* p, int32_t s
   API_BEGIN(c)
   if (!p || steps < 0) fail(MNBAB_E_INVALID_ARG, "bad step count");
   if (p->materialized) fail(MNBAB_E_INVALID_ARG, "property already started");
-  if (steps > 0 && p->pd.E > 0)
-    fail(MNBAB_E_UNSUPPORTED, "optimised intermediate bounds take no multi-neuron constraints");
   if (steps > 0 && p->net->B < 2)
     fail(MNBAB_E_INVALID_ARG,
          "optimised intermediate bounds need a batch capacity of at least 2 (node_capacity >= 4)");

@@ -210,3 +210,84 @@ def test_zero_steps_reproduce_deeppoly_root_bounds(seed):
     for i in range(1, net.R + 1):
         assert torch.allclose(node.l[i], l[i], rtol=0, atol=1e-12), f"layer {i} lower"
         assert torch.allclose(node.u[i], u[i], rtol=0, atol=1e-12), f"layer {i} upper"
+
+
+def _mnc_case(seed, dims=(10, 14, 12, 10, 3), eps=0.15):
+    """A case whose layers carry multi-neuron constraints (Sec. 2.3)."""
+    from oracle import mnc
+    L = synth.tiny_fc_net(seed, list(dims))
+    rng = np.random.default_rng(seed + 100)
+    x0 = rng.uniform(0.2, 0.8, dims[0]).astype(np.float32)
+    y = synth.net_forward(L, x0)
+    C, d = synth.property_rows(int(np.argmax(y)), dims[-1])
+    lo, hi = synth.input_box(x0, eps)
+    prep = bab.prepare(L, C, d, lo, hi, mnc.mnc_fn(40))
+    assert prep[7] and any(prep[7][i][2].numel() > 0 for i in prep[7] if i < prep[0].R)
+    return prep, lo, hi
+
+
+@pytest.mark.parametrize("seed", [7, 8])
+def test_gamma_sets_sound_and_zero_steps_give_deeppoly(seed):
+    """With multi-neuron constraints in the shared sets (gamma_i of the layers
+    below t, started at 0), zero Adam steps still give the DeepPoly bounds (the
+    start point has gamma = 0), and optimised bounds contain every sampled
+    pre-activation and are never looser than DeepPoly."""
+    prep, lo, hi = _mnc_case(seed)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    node = bab.root_node(net, 0, l, u, S, m)
+    core.optimize_intermediate(net, node, lo_t, hi_t, core.AdamHP(steps=0), dense_mnc=dense)
+    for i in range(1, net.R + 1):
+        assert torch.allclose(node.l[i], l[i], rtol=0, atol=1e-12)
+        assert torch.allclose(node.u[i], u[i], rtol=0, atol=1e-12)
+    node = bab.root_node(net, 0, l, u, S, m)
+    rows = core.optimize_intermediate(net, node, lo_t, hi_t, core.AdamHP(steps=20), dense_mnc=dense)
+    assert rows > 0
+    for i in node.l:
+        assert bool((node.l[i] >= l[i]).all()) and bool((node.u[i] <= u[i]).all())
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(lo, hi, size=(20000, lo.size))
+    h = _t(X)
+    for i in range(1, net.R + 1):
+        zh = net.aff[i].forward(h)
+        assert bool((zh >= node.l[i] - 1e-9).all()), f"layer {i}: lower bound above a sample"
+        assert bool((zh <= node.u[i] + 1e-9).all()), f"layer {i}: upper bound below a sample"
+        h = torch.clamp(zh, min=0)
+
+
+@pytest.mark.parametrize("side", [1, -1])
+def test_gamma_gradient_matches_finite_differences(side):
+    """The shared set's gradient w.r.t. gamma_i (constraint multipliers of layer
+    i < t) is the derivative of the summed row bounds: autograd against
+    central differences at an interior point (gamma > 0)."""
+    prep, lo, hi = _mnc_case(7)
+    net, lo_t, hi_t, l, u, S, m, dense = prep
+    node = bab.root_node(net, 0, l, u, S, m)
+    t = net.R
+    idx = torch.nonzero((l[t] < 0) & (u[t] > 0)).reshape(-1)
+    if idx.numel() == 0:
+        idx = torch.arange(l[t].numel())
+    rng = np.random.default_rng(3)
+    alpha = {i: _t(rng.uniform(0.2, 0.8, l[i].numel())) for i in range(1, t)}
+    beta = {i: torch.zeros(l[i].numel(), dtype=DT) for i in range(1, t)}
+    gamma = {i: _t(rng.uniform(0.05, 0.3, dense[i][2].numel() if i in dense else 0))
+             for i in range(1, t)}
+    _, _, _, gg = core.intermediate_objective_grad(net, node, t, idx, side, alpha, beta,
+                                                   lo_t, hi_t, gamma, dense)
+
+    def f(g):
+        return float(core.intermediate_objective(net, node, t, idx, side, alpha, beta,
+                                                 lo_t, hi_t, g, dense).sum())
+
+    h = 1e-6
+    checked = nonzero = 0
+    for i in range(1, t):
+        for k in range(0, gamma[i].numel(), max(1, gamma[i].numel() // 12)):
+            gp = {a: v.clone() for a, v in gamma.items()}
+            gm = {a: v.clone() for a, v in gamma.items()}
+            gp[i][k] += h
+            gm[i][k] -= h
+            fd = (f(gp) - f(gm)) / (2 * h)
+            assert abs(fd - float(gg[i][k])) <= 1e-6 * (1 + abs(fd)), (i, k, fd, float(gg[i][k]))
+            checked += 1
+            nonzero += abs(fd) > 1e-9
+    assert checked > 5 and nonzero > 0
