@@ -81,6 +81,11 @@ def parse():
                     help="constraint groups per ReLU layer in the conv-big arm")
     ap.add_argument("--inter-nodes", type=int, default=128,
                     help="root nodes of the optimised-intermediate-bounds arm (0 skips it)")
+    ap.add_argument("--verdicts", default="0,2,3",
+                    help="configurations of the verdicts-at-timeout runs (empty skips them)")
+    ap.add_argument("--verdicts-full", action="store_true",
+                    help="verdicts at the specified sizes (100 / 50 properties, 60 / 120 s "
+                         "timeouts) instead of the bounded default sample; only these runs")
     return ap.parse_args()
 
 
@@ -497,6 +502,10 @@ def run_ours(args):
     if world == 1 and args.mnc_big_props > 0:
         mnc_big = mnc_big_run(local, stream, args.mnc_big_props, 3, args.mnc_big_groups, peaks,
                               src, kernels_sha())
+    verdicts = None
+    if world == 1 and args.verdicts:
+        verdicts = {f"config{c}": verdicts_run(local, stream, int(c), full=False)
+                    for c in args.verdicts.split(",")}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -522,6 +531,7 @@ def run_ours(args):
             "serving": serving,
             "intermediate": inter,
             "conv_big_mnc": mnc_big,
+            "verdicts_at_timeout": verdicts,
             "launches_before_timed": int(launches0),
         }
         print(json.dumps(out), flush=True)
@@ -782,6 +792,126 @@ def mnc_big_run(local, stream, n_props, steps, max_groups, peaks, src, ksha):
 
 
 # ----------------------------------------------------------------------------
+# Verdicts at the timeout: the full method (alpha / beta / gamma with k = 3
+# multi-neuron constraints from the library's generator, ACS branching, FIFO
+# BaB) on the networks of configs 0, 2 and 3.  Config 0 runs in the plain form
+# (one property at a time, one subproblem per launch, <= 256 nodes per
+# property); configs 2 and 3 run a rolling window of at most 16 properties in
+# the batched form (256 / 128 subproblems per step; a finished property's
+# place goes to the next), each property with its own wall-clock timeout from
+# its first step.  The node pool bounds the BaB: the per-property node budget
+# is what the pool holds for the properties that run together (a bounded node
+# frees its slot after its two children take theirs, so a property never holds
+# more than rows + 1 + budget slots, plus one per node of the running step).
+VERDICT_MNC_ROWS = 160_000   # constraint rows a property may hold (configs 2 and 3)
+VERDICT_CFGS = {
+    0: dict(workload="fc_small_784: 784 -> 100 -> 100 -> 10, k=3 multi-neuron constraints",
+            props=16, full_props=16, timeout=0.0, full_timeout=0.0, batch=1, budget=256,
+            capacity=2048, mnc_rows=1 << 16, hbm=16 << 30, plain=True, attack=(8, 20)),
+    2: dict(workload=None, props=8, full_props=100, timeout=20.0,
+            full_timeout=60.0, batch=256, budget=None, capacity=32768, mnc_rows=None,
+            hbm=200 << 30, plain=False, window=16, attack=None),
+    3: dict(workload="resnet_32: 3x32x32 -> conv16 3x3 -> 2 basic blocks (32, 64 ch, s2, 1x1 "
+                     "shortcuts) -> FC100 -> FC10, k=3 multi-neuron constraints",
+            props=8, full_props=50, timeout=20.0, full_timeout=120.0, batch=128, budget=None,
+            capacity=32768, mnc_rows=None, hbm=200 << 30, plain=False, window=16, attack=None),
+}
+
+
+def verdicts_run(local, stream, cfg, full=False, max_groups=2000):
+    import torch
+    from paper_2205_00263_gb300 import Context
+    spec = dict(VERDICT_CFGS[cfg])
+    if cfg == 2:
+        spec["workload"] = MNC_BIG
+    n_props = spec["full_props"] if full else spec["props"]
+    timeout = spec["full_timeout"] if full else spec["timeout"]
+    layers = synth.make_network(cfg)
+    props = synth.make_properties(cfg, layers, n=n_props, eps=synth.load_eps(cfg), start=0)
+    mnc_rows = spec["mnc_rows"] or VERDICT_MNC_ROWS
+    ctx = Context(device=local, stream=stream.cuda_stream, node_capacity=spec["capacity"],
+                  max_mnc_rows=mnc_rows, hbm_budget_bytes=spec["hbm"])
+    try:
+        net = ctx.load_network(layers)
+        ps, rows = [], []
+        t0 = time.perf_counter()
+        for pr in props:
+            p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+            if timeout:
+                ctx.set_timeout(p, timeout)
+            if spec["attack"]:
+                ctx.set_attack(p, spec["attack"][0], spec["attack"][1], seed=len(ps))
+            rows.append(ctx.generate_mnc(p, max_groups))
+            ps.append(p)
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        # node budget: what the pool holds for the properties that run together
+        # (every property's root nodes exist from its constraint generation on)
+        roots = sum(pr.C.shape[0] + 1 for pr in props)
+        together = 1 if spec["plain"] else min(n_props, spec["window"])
+        budget = (spec["capacity"] - 16 - roots - spec["batch"]) // together
+        if budget < 1:
+            raise RuntimeError("node pool too small for the properties' roots")
+        if spec["budget"]:
+            budget = min(budget, spec["budget"])
+        for p in ps:
+            ctx.set_budget(p, budget)
+        ttv, nodes, steps = [], 0, 0
+        t0 = time.perf_counter()
+        if spec["plain"]:
+            for p in ps:
+                while True:
+                    st = ctx.bab_step([p], max_nodes=1, steps=ADAM_STEPS)
+                    nodes += st["nodes_bounded"]
+                    steps += 1
+                    if ctx.queue_size(p) == 0:
+                        break
+                ttv.append(ctx.status(p)[2])
+        else:
+            waiting = list(ps)
+            active = [waiting.pop(0) for _ in range(min(together, len(waiting)))]
+            while active:
+                st = ctx.bab_step(active, max_nodes=spec["batch"], steps=ADAM_STEPS)
+                nodes += st["nodes_bounded"]
+                steps += 1
+                keep = []
+                for p in active:
+                    if ctx.queue_size(p) == 0:
+                        ttv.append(ctx.status(p)[2])
+                    else:
+                        keep.append(p)
+                while waiting and len(keep) < together:
+                    keep.append(waiting.pop(0))
+                active = keep
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        verd = {"verified": 0, "falsified": 0, "unknown": 0, "of_which_timed_out": 0}
+        for p in ps:
+            v, _, _ = ctx.verdict(p)
+            verd["verified" if v == 1 else "falsified" if v == -1 else "unknown"] += 1
+            verd["of_which_timed_out"] += int(ctx.status(p)[1])
+    finally:
+        ctx.close()
+    ttv = np.sort(np.asarray(ttv))
+    return {"workload": spec["workload"], "properties": n_props,
+            "form": ("plain: one property at a time, one subproblem per launch" if spec["plain"]
+                     else f"batched: rolling window of {together} properties, "
+                          f"{spec['batch']} subproblems per step"),
+            "timeout_s": timeout or None, "node_budget_per_property": budget,
+            "max_groups_per_layer": max_groups, "mnc_rows_per_property": float(np.mean(rows)),
+            "generate_s_per_property": gen_s / n_props,
+            "pre_attack": (f"{spec['attack'][0]} starts x {spec['attack'][1]} sign steps"
+                           if spec["attack"] else "none (the attack kernel takes chain networks "
+                           "whose weights fit in shared memory)"),
+            "verdicts": verd,
+            "nodes": nodes, "bab_steps": steps, "wall_s": wall,
+            "nodes_per_s": nodes / wall if wall else None,
+            "time_to_verdict_s": {"p50": float(np.percentile(ttv, 50)),
+                                  "p99": float(np.percentile(ttv, 99))},
+            "sample": "full specified size" if full else "bounded sample (see properties, timeout_s)"}
+
+
+# ----------------------------------------------------------------------------
 def cpu_baseline(seconds: float, start: int = 0):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload:
     BaB on seeded properties of the same net until ~`seconds` of CPU work."""
@@ -893,10 +1023,25 @@ def run_serving(args):
     ctx.close()
 
 
+def run_verdicts_full(args):
+    """Verdicts at the specified sizes: configs 0 (16 properties, plain form), 2
+    (100 properties, 60 s timeout each) and 3 (50 properties, 120 s each), the
+    batched configurations with all properties at once."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    stream = torch.cuda.Stream()
+    out = {f"config{c}": verdicts_run(0, stream, int(c), full=True)
+           for c in (args.verdicts or "0,2,3").split(",")}
+    print(json.dumps({"verdicts_at_timeout": out}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.verdicts_full:
+        run_verdicts_full(a)
     elif a.gemm_tc:
         run_gemm_tc(a)
     elif a.serving:

@@ -206,7 +206,8 @@ mnbab_status mnbab_set_mnc(mnbab_ctx* ctx, mnbab_prop* prop, int32_t relu_layer,
  *    convex hull of the ReLU graph over that octahedron (mnbab_mnc_group),
  *    uploaded as with mnbab_set_mnc.
  * Every layer counts as set afterwards (mnbab_set_mnc then refuses it); call
- * before bounding any node of the property.  *rows_out (nullable) receives
+ * before bounding any node of the property.  A property that its pre-attack
+ * (mnbab_set_attack) falsified when it started gets no rows.  *rows_out (nullable) receives
  * the number of constraint rows.  MNBAB_E_BUDGET when the rows exceed
  * mnbab_options.max_mnc_rows (the exact hull gives about 100 to 250 rows per
  * group). */
@@ -361,6 +362,19 @@ mnbab_status mnbab_set_leaf_steps(mnbab_ctx* ctx, mnbab_prop* prop, int32_t step
 
 /* Per-property node budget (bounded nodes including roots); default 256. */
 mnbab_status mnbab_set_budget(mnbab_ctx* ctx, mnbab_prop* prop, int32_t max_nodes);
+
+/* Per-property wall-clock limit (Sec. 4: each property has a timeout; a
+ * property not decided within it counts as unknown).  The clock starts at the
+ * property's first mnbab_bab_step; a step that ends after the limit with the
+ * property still open sets its verdict to MNBAB_UNKNOWN and frees its queue.
+ * 0 (the default) sets no limit; negative values are MNBAB_E_INVALID_ARG. */
+mnbab_status mnbab_set_timeout(mnbab_ctx* ctx, mnbab_prop* prop, double seconds);
+
+/* Progress of a property: nodes bounded so far, whether its timeout ended it
+ * (1) or not (0), and the seconds since its first BaB step (0 before it);
+ * every output is nullable. */
+mnbab_status mnbab_get_status(const mnbab_ctx* ctx, const mnbab_prop* prop, int32_t* bounded,
+                              int32_t* timed_out, double* elapsed_s);
 
 /* Branching score of a property (Sec. 3.2): mode 0 = ACS; mode 1 = ACS + CAB,
  * the score divided by the cost of the split (App. B): with per-layer costs

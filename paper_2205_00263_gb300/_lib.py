@@ -98,6 +98,8 @@ SIGNATURES = {
     "mnbab_bab_step": (status, [VP, C.POINTER(VP), C.c_int32, C.c_int32, C.POINTER(Adam),
                                 C.POINTER(StepStats)]),
     "mnbab_set_budget": (status, [VP, VP, C.c_int32]),
+    "mnbab_set_timeout": (status, [VP, VP, C.c_double]),
+    "mnbab_get_status": (status, [VP, VP, IP, IP, C.POINTER(C.c_double)]),
     "mnbab_set_leaf_steps": (status, [VP, VP, C.c_int32]),
     "mnbab_set_branching": (status, [VP, VP, C.c_int32]),
     "mnbab_set_intermediate_steps": (status, [VP, VP, C.c_int32]),

@@ -222,6 +222,16 @@ class Context:
     def set_budget(self, prop: Prop, n: int):
         self._ck(self.lib.mnbab_set_budget(self.h, prop.h, n))
 
+    def set_timeout(self, prop: Prop, seconds: float):
+        """Wall-clock limit of the property from its first BaB step (0: none)."""
+        self._ck(self.lib.mnbab_set_timeout(self.h, prop.h, float(seconds)))
+
+    def status(self, prop: Prop):
+        """(nodes bounded, ended by its timeout, seconds since its first step)."""
+        b, t, e = C.c_int32(), C.c_int32(), C.c_double()
+        self._ck(self.lib.mnbab_get_status(self.h, prop.h, C.byref(b), C.byref(t), C.byref(e)))
+        return b.value, bool(t.value), e.value
+
     def set_branching(self, prop: Prop, cab: bool):
         """ACS (cab=False) or cost-adjusted ACS (cab=True) for this property."""
         self._ck(self.lib.mnbab_set_branching(self.h, prop.h, 1 if cab else 0))

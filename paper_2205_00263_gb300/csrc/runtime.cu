@@ -142,7 +142,14 @@ struct mnbab_prop {
   int leaf_steps = 256;              // Adam steps of the exact completion of fully split leaves
   int atk_starts = 0, atk_steps = 0;  // pre-attack when the property starts (0: none)
   uint64_t atk_seed = 0;
+  double timeout_s = 0.0;            // wall-clock limit from its first BaB step (0: none)
+  double t_start = 0.0;              // time of its first BaB step
+  bool timed_out = false;
 };
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 // A request of the serving loop.
 struct Request {
@@ -1648,7 +1655,13 @@ int64_t generate_mnc_impl(mnbab_ctx* c, mnbab_prop* p, int max_groups) {
     if (p->mnc_set[t]) fail(MNBAB_E_INVALID_ARG, "constraints of a layer are already set");
   mnbab_prop* only[1] = {p};
   ensure_roots(n, only, 1);
-  if (p->root_slot < 0) fail(MNBAB_E_INVALID_ARG, "property not admitted");
+  if (!p->materialized) fail(MNBAB_E_INVALID_ARG, "property not admitted");
+  if (p->root_slot < 0) {
+    // decided when it started (its pre-attack found a counterexample): no node
+    // will be bounded, so no constraints are needed
+    for (int t = 1; t <= n->R; ++t) p->mnc_set[t] = 1;
+    return 0;
+  }
   const int SD = n->SD, rs = p->root_slot;
   std::vector<float> hl(SD), hu(SD);
   d2h(c, hl.data(), n->pool.L + (size_t)rs * SD, SD);
@@ -1763,6 +1776,11 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
   HostTimer ht(c);
   ensure_roots(n, props, n_props);
   ht.lap(H_ROOTS);
+  {
+    const double t = now_s();
+    for (int i = 0; i < n_props; ++i)
+      if (props[i]->materialized && props[i]->t_start == 0.0) props[i]->t_start = t;
+  }
   // pop FIFO
   std::vector<Picked> picked;
   for (int i = 0; i < n_props && (int)picked.size() < max_nodes; ++i) {
@@ -2005,9 +2023,15 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
   }
   ht.lap(H_FINISH);
   // property completion
+  const double t_end = now_s();
   for (int i = 0; i < n_props; ++i) {
     mnbab_prop* p = props[i];
     if (!p->materialized) continue;
+    if (!p->done && !p->queue.empty() && p->timeout_s > 0 && t_end - p->t_start > p->timeout_s) {
+      p->verdict = MNBAB_UNKNOWN;
+      p->done = true;
+      p->timed_out = true;
+    }
     if (p->done) {
       for (auto& q : p->queue) free_slot(n, q.slot);
       p->queue.clear();
@@ -2720,6 +2744,24 @@ mnbab_status mnbab_set_budget(mnbab_ctx* c, mnbab_prop* p, int32_t max_nodes) {
   API_END(c)
 }
 
+mnbab_status mnbab_set_timeout(mnbab_ctx* c, mnbab_prop* p, double seconds) {
+  API_BEGIN(c)
+  if (!p || !(seconds >= 0.0)) fail(MNBAB_E_INVALID_ARG, "bad timeout");
+  p->timeout_s = seconds;
+  API_END(c)
+}
+
+mnbab_status mnbab_get_status(const mnbab_ctx* cc, const mnbab_prop* p, int32_t* bounded,
+                              int32_t* timed_out, double* elapsed_s) {
+  mnbab_ctx* c = const_cast<mnbab_ctx*>(cc);
+  API_BEGIN(c)
+  if (!p) fail(MNBAB_E_INVALID_ARG, "null property");
+  if (bounded) *bounded = p->bounded;
+  if (timed_out) *timed_out = p->timed_out ? 1 : 0;
+  if (elapsed_s) *elapsed_s = p->t_start > 0.0 ? now_s() - p->t_start : 0.0;
+  API_END(c)
+}
+
 mnbab_status mnbab_set_branching(mnbab_ctx* c, mnbab_prop* p, int32_t mode) {
   API_BEGIN(c)
   if (!p || mode < 0 || mode > 1) fail(MNBAB_E_INVALID_ARG, "bad branching mode");
@@ -2768,10 +2810,6 @@ mnbab_status mnbab_get_trace(const mnbab_ctx* cc, const mnbab_prop* p, mnbab_tra
   for (int i = 0; i < k; ++i) recs[i] = p->trace[i];
   *n_out = recs ? k : nt;
   API_END(c)
-}
-
-static double now_s() {
-  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 mnbab_status mnbab_submit(mnbab_ctx* c, mnbab_prop* p, double timeout_s, uint64_t* ticket) {

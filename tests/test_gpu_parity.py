@@ -394,6 +394,48 @@ def test_batched_equals_one_node_per_launch(Context):
             assert a["lb"] == b["lb"] or abs(a["lb"] - b["lb"]) <= 1e-6 * (1 + abs(a["lb"]))
 
 
+def test_timeout_ends_open_properties(Context):
+    """A per-property wall-clock limit (Sec. 4) ends a property that is still
+    open after the step in which the limit passed: verdict unknown, queue
+    freed, status reports the timeout; properties decided in that step keep
+    their verdicts, and without a limit the same properties stay open."""
+    layers = synth.make_network(1)
+    prs = synth.make_properties(1, layers, n=24, eps=synth.load_eps(1), start=40)
+    open_without = []
+    with Context(node_capacity=4096) as ctx:
+        net = ctx.load_network(layers)
+        ps = []
+        for pr in prs:
+            p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+            ctx.set_budget(p, 10000)
+            ps.append(p)
+        ctx.bab_step(ps, max_nodes=512, steps=5)
+        open_without = [ctx.queue_size(p) > 0 for p in ps]
+        verd_without = [ctx.verdict(p)[0] for p in ps]
+        for p in ps:
+            b, t, e = ctx.status(p)
+            assert b > 0 and not t and e > 0
+    assert any(open_without), "every property decided at its roots"
+    with Context(node_capacity=4096) as ctx:
+        net = ctx.load_network(layers)
+        ps = []
+        for pr in prs:
+            p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+            ctx.set_budget(p, 10000)
+            ctx.set_timeout(p, 1e-9)
+            ps.append(p)
+        assert ctx.status(ps[0]) == (0, False, 0.0)
+        ctx.bab_step(ps, max_nodes=512, steps=5)
+        for k, p in enumerate(ps):
+            b, t, e = ctx.status(p)
+            assert ctx.queue_size(p) == 0
+            assert t == open_without[k]
+            v = ctx.verdict(p)[0]
+            assert v == (0 if open_without[k] else verd_without[k])
+        with pytest.raises(Exception):
+            ctx.set_timeout(ps[0], -1.0)
+
+
 def test_conv_full_size_sampled(Context):
     """28x28 conv net, 100 properties, 512 subproblems per step (the timed
     configuration): three properties with deep trees agree with the oracle node
