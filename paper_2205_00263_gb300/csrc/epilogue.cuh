@@ -103,6 +103,7 @@ __device__ __forceinline__ float epi_apply(const Epi& e, int m, int j, float v, 
 // the same arithmetic as epi_apply on the loaded values.
 struct EpiIn {
   float acc, l, u, al, be, gp, gph;
+  float cb;  // bias of the consuming affine layer at j (ReLU step)
   int s;
 };
 
@@ -110,8 +111,14 @@ __device__ __forceinline__ const PropDev* epi_prop(const Epi& e, int n) {
   return e.kind == EPI_CONC ? &e.props[e.pool.prop[n]] : nullptr;
 }
 
-__device__ __forceinline__ void epi_load(const Epi& e, int n, const PropDev* P, int m, int j,
-                                         EpiIn& in) {
+// the part of an output's inputs that depends on its column j only
+__device__ __forceinline__ float epi_colbias(const Epi& e, int j) {
+  return e.kind == EPI_RELU ? e.bias[j / e.bias_div] : 0.f;
+}
+
+// every input of output (m, j) except the column bias (in.cb)
+__device__ __forceinline__ void epi_load_row(const Epi& e, int n, const PropDev* P, int m, int j,
+                                             EpiIn& in) {
   in.acc = e.acc_in ? e.acc_in[(size_t)m * e.acc_ld + j] : 0.f;
   in.al = in.be = in.gp = in.gph = 0.f;
   in.s = 0;
@@ -136,6 +143,12 @@ __device__ __forceinline__ void epi_load(const Epi& e, int n, const PropDev* P, 
     in.l = P->lo[j];
     in.u = P->hi[j];
   }
+}
+
+__device__ __forceinline__ void epi_load(const Epi& e, int n, const PropDev* P, int m, int j,
+                                         EpiIn& in) {
+  epi_load_row(e, n, P, m, j, in);
+  in.cb = epi_colbias(e, j);
 }
 
 __device__ __forceinline__ float epi_finish(const Epi& e, int m, int j, float v, const EpiIn& in,
@@ -163,7 +176,7 @@ __device__ __forceinline__ float epi_finish(const Epi& e, int m, int j, float v,
       if (e.final_mode) ah += in.be * (float)s;
       if (e.GPh) ah += in.gph;
       if (e.AP) e.AP[qm] = ap;
-      part += ap * bl + ah * e.bias[j / e.bias_div];
+      part += ap * bl + ah * in.cb;
       return ah;
     }
     case EPI_CONC: {

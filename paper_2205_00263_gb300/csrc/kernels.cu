@@ -1413,9 +1413,11 @@ int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* 
   if (M <= 0) return backsub_slots(L);
   if (L.kind == 1) {
     // Lambda [M][d_out] x W [d_out][d_in]; the tensor-core kernel takes W as [d_in][d_out] = W^T
-    if (use_tc(e, M, L.d_in))
-      return launch_gemm_tc(M, L.d_in, L.d_out, in, ld_in, L.Wt, L.d_out, nullptr, 1, out, ld_out,
-                            e, e.err, st, L.tc, 1);
+    if (use_tc(e, M, L.d_in)) {
+      const int slots =
+          launch_gemm_tc(M, L.d_in, L.d_out, in, ld_in, nullptr, 1, out, ld_out, e, e.err, st, L.tc, 1);
+      if (slots >= 0) return slots;
+    }
     return gemm_launch(M, L.d_in, L.d_out, in, ld_in, L.W, L.d_in, nullptr, 1, out, ld_out, e, st);
   }
   if (use_tc_conv(L, 1, e)) return launch_tc_conv(L, 1, M, in, ld_in, out, ld_out, e, st);
@@ -1466,11 +1468,9 @@ void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float*
   if (M <= 0) return;
   if (L.kind == 1) {
     // G [M][d_in] x W^T + b; the tensor-core kernel takes W [d_out][d_in] as is
-    if (use_tc(e, M, L.d_out)) {
-      launch_gemm_tc(M, L.d_out, L.d_in, in, ld_in, L.W, L.d_in, L.b, 1, out, ld_out, e, e.err, st,
-                     L.tc, 0);
+    if (use_tc(e, M, L.d_out) &&
+        launch_gemm_tc(M, L.d_out, L.d_in, in, ld_in, L.b, 1, out, ld_out, e, e.err, st, L.tc, 0) >= 0)
       return;
-    }
     gemm_launch(M, L.d_out, L.d_in, in, ld_in, L.Wt, L.d_out, L.b, 1, out, ld_out, e, st);
     return;
   }

@@ -153,17 +153,22 @@ int launch_tc_conv(const LayerDev& L, int dir, int M, const float* in, int ld_in
                    int ld_out, const Epi& e, cudaStream_t st);
 
 // ---- launchers (kernels.cu, tc_gemm.cu) ----------------------------------
-// Tensor-core 3xTF32 GEMM C = A . Bnk^T (+ bias) with the fused epilogue;
-// returns the number of column tiles (partial-sum slots written).
-// With `pre` (the layer's TcFc) the weight operand of direction `dir` (0 W for
-// forward products, 1 W^T for back-substitution) comes pre-split by TMA.
-int launch_gemm_tc(int M, int N, int K, const float* A, int lda, const float* Bnk, int ldb,
-                   const float* bias, int bias_div, float* C, int ldc, const Epi& e, int* err,
-                   cudaStream_t st, const void* pre = nullptr, int dir = 0);
+// Tensor-core 3xTF32 GEMM C = A . B^T (+ bias) with the fused epilogue, B the
+// pre-split weight operand of direction `dir` of the layer's TcFc `pre` (0: W
+// for forward products, 1: W^T for back-substitution); A is split into the
+// TcFc's workspace first.  Returns the number of column tiles (partial-sum
+// slots written), or -1 without launching anything when the TcFc cannot serve
+// this product (no tensor maps, other shape, workspace too small).
+int launch_gemm_tc(int M, int N, int K, const float* A, int lda, const float* bias, int bias_div,
+                   float* C, int ldc, const Epi& e, int* err, cudaStream_t st, const void* pre,
+                   int dir);
 // Pre-split TF32 weights of an FC layer for the tensor-core GEMM (tc_gemm.cu).
 struct TcFc;
 size_t tc_fc_floats(const LayerDev& L);
+// workspace floats for coefficient-row products of up to max_rows rows
+size_t tc_fc_workspace_floats(const LayerDev& L, int max_rows);
 TcFc* tc_fc_create(const LayerDev& L, float* buf, cudaStream_t st);
+void tc_fc_set_workspace(TcFc* t, float* ws, size_t floats);
 void tc_fc_destroy(TcFc* t);
 // Starting rows: a = sign * W_t[j, :] (t <= R) or Wf[row, :] (t = R + 1) on
 // z^(t-1), with c = sign * b_t[j] into slot 0, through epilogue `e`.

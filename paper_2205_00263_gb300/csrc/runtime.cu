@@ -1127,6 +1127,25 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
       n->splitk = dalloc_t<float>(c, n->splitk_floats);
     }
   }
+  // tensor-core GEMM: one workspace for the split coefficient rows of every
+  // FC product of up to mrows rows (launches on the stream run in order)
+  {
+    size_t ws = 0;
+    for (int i = 1; i <= n->R + 1; ++i)
+      for (int k = 0; k < n->nd.n_edge[i]; ++k) {
+        const LayerDev& L = k == 0 ? n->nd.aff[i] : n->nd.aff2[i];
+        if (L.kind == 1 && L.tc) ws = std::max(ws, tc_fc_workspace_floats(L, (int)mrows));
+      }
+    if (ws) {
+      float* buf = dalloc_t<float>(c, ws);
+      for (int i = 1; i <= n->R + 1; ++i)
+        for (int k = 0; k < n->nd.n_edge[i]; ++k) {
+          const LayerDev& L = k == 0 ? n->nd.aff[i] : n->nd.aff2[i];
+          if (L.kind == 1 && L.tc)
+            tc_fc_set_workspace(static_cast<TcFc*>(const_cast<void*>(L.tc)), buf, ws);
+        }
+    }
+  }
   n->bslots = dalloc_t<int>(c, B);
   n->brows = dalloc_t<int>(c, B);
   n->acs_layer = dalloc_t<int>(c, B);
