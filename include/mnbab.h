@@ -417,6 +417,7 @@ typedef struct {
   int32_t active;          /* admitted, not finished */
   int32_t queued;          /* waiting for admission */
   mnbab_step_stats step;   /* summed over the networks' BaB steps */
+  int64_t reserved_bytes;  /* HBM held by the active requests' node slots after the pass */
 } mnbab_serve_stats;
 
 /* Queues a property (created by mnbab_set_property and not yet used) as a
@@ -424,15 +425,25 @@ typedef struct {
  * this call to its verdict (UNKNOWN when exceeded). */
 mnbab_status mnbab_submit(mnbab_ctx* ctx, mnbab_prop* prop, double timeout_s, uint64_t* ticket);
 
+/* HBM bytes that the active requests' node slots may hold together, over all
+ * networks of the context; 0 (the default) means the context's HBM budget. */
+mnbab_status mnbab_set_serving_budget(mnbab_ctx* ctx, uint64_t bytes);
+
 /* One pass of the request loop: admits queued requests in FIFO order while
- * their network's node pool (allocated within the HBM budget) can hold their
- * reservation (n_rows + 1 + 2 * node budget slots; a request larger than the
- * pool runs once its network is idle), runs one BaB step per
+ * the HBM of their reservation (n_rows + 1 + 2 * node budget slots, each slot
+ * the per-neuron state, parameters and moments of a node) fits the serving
+ * budget next to the active requests of every network, and their network's
+ * node pool (allocated within the HBM budget) can hold the slots (a request
+ * larger than the pool runs once its network is idle, one larger than the
+ * serving budget once no request is active), runs one BaB step per
  * network over all of its active requests (nodes of different requests share
  * the launches, so requests that arrive while others run join the next
  * batch), and retires requests that reached a verdict, their node budget or
- * their timeout.  Results of a request do not depend on the others it ran
- * with. */
+ * their timeout.  A request's results do not depend on the others it ran
+ * with, except when its root bounds were computed in one pass with other
+ * requests' roots: kernel shapes and reduction splits follow the number of
+ * rows of a launch, so its bounds may then differ at rounding level (and a
+ * branching choice only where two scores tie at that level). */
 mnbab_status mnbab_serve_step(mnbab_ctx* ctx, int32_t max_nodes, const mnbab_adam* cfg,
                               mnbab_serve_stats* out);
 

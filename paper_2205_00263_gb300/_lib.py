@@ -51,7 +51,7 @@ class StepStats(C.Structure):
 
 class ServeStats(C.Structure):
     _fields_ = [("admitted", C.c_int32), ("finished", C.c_int32), ("active", C.c_int32),
-                ("queued", C.c_int32), ("step", StepStats)]
+                ("queued", C.c_int32), ("step", StepStats), ("reserved_bytes", C.c_int64)]
 
 
 class KernelStat(C.Structure):
@@ -112,6 +112,7 @@ SIGNATURES = {
     "mnbab_profile_mask": (status, [VP, C.c_uint64]),
     "mnbab_submit": (status, [VP, VP, C.c_double, C.POINTER(C.c_uint64)]),
     "mnbab_serve_step": (status, [VP, C.c_int32, C.POINTER(Adam), C.POINTER(ServeStats)]),
+    "mnbab_set_serving_budget": (status, [VP, C.c_uint64]),
     "mnbab_poll": (status, [VP, C.c_uint64, IP]),
     "mnbab_request_result": (status, [VP, C.c_uint64, IP, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), IP]),

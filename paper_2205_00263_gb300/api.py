@@ -399,6 +399,10 @@ class Context:
         self._ck(self.lib.mnbab_submit(self.h, prop.h, timeout_s, C.byref(t)))
         return t.value
 
+    def set_serving_budget(self, nbytes: int):
+        """HBM bytes the active requests' node slots may hold (0: the context's budget)."""
+        self._ck(self.lib.mnbab_set_serving_budget(self.h, int(nbytes)))
+
     def serve_step(self, max_nodes: int, steps: int = 20):
         a = L.Adam(steps, 0.1, 0.05, 0.05, 0.9, 0.999, 1e-8, 0.0, 0.0)
         st = L.ServeStats()

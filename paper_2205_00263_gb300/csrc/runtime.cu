@@ -158,6 +158,7 @@ struct Request {
   double t_submit = 0, t_admit = 0, t_done = 0, deadline = 0;
   int state = 0;    // 0 queued, 1 active, 2 done
   int reserve = 0;  // node slots reserved in its network's pool
+  uint64_t bytes = 0;  // HBM of those slots (node state, parameters, moments)
   int timed_out = 0;
 };
 
@@ -196,6 +197,8 @@ struct mnbab_ctx {
   std::vector<Request*> requests;        // by ticket - 1
   std::deque<Request*> req_queue;        // queued, FIFO
   std::vector<int> reserved;             // reserved node slots per network
+  uint64_t serve_budget = 0;             // HBM bytes the active requests may hold (0: budget)
+  uint64_t serve_bytes = 0;              // HBM bytes the active requests hold
   // CUDA graphs of the optimisation loop
   bool graphs = false;
   struct GraphEntry* cap = nullptr;  // entry being captured (Scope records into it)
@@ -2831,6 +2834,14 @@ mnbab_status mnbab_get_trace(const mnbab_ctx* cc, const mnbab_prop* p, mnbab_tra
   API_END(c)
 }
 
+// HBM of one node slot of a network's pool: bounds, splits, slopes, split
+// multipliers and their Adam moments per neuron, multi-neuron multipliers and
+// moments per constraint row, the best minimiser and the slot's scalars
+static uint64_t slot_bytes(const mnbab_net* n) {
+  return (uint64_t)n->SD * (8 * sizeof(float) + 1) + (uint64_t)n->ctx->EC * 3 * sizeof(float) +
+         (uint64_t)n->d0 * sizeof(float) + 3 * sizeof(int);
+}
+
 mnbab_status mnbab_submit(mnbab_ctx* c, mnbab_prop* p, double timeout_s, uint64_t* ticket) {
   API_BEGIN(c)
   if (!p || !ticket) fail(MNBAB_E_INVALID_ARG, "null argument");
@@ -2843,6 +2854,7 @@ mnbab_status mnbab_submit(mnbab_ctx* c, mnbab_prop* p, double timeout_s, uint64_
   r->deadline = timeout_s > 0 ? r->t_submit + timeout_s : 0.0;
   // live nodes never exceed the rows' roots plus two children per bounded node
   r->reserve = std::min(n->cap, p->n_rows + 1 + 2 * p->budget);
+  r->bytes = (uint64_t)r->reserve * slot_bytes(n);
   p->admitted = false;
   c->requests.push_back(r);
   c->req_queue.push_back(r);
@@ -2857,15 +2869,21 @@ mnbab_status mnbab_serve_step(mnbab_ctx* c, int32_t max_nodes, const mnbab_adam*
   std::memset(out, 0, sizeof(*out));
   const mnbab_adam a = cfg ? *cfg : default_adam();
   if (c->reserved.size() < c->nets.size()) c->reserved.resize(c->nets.size(), 0);
-  // admission, FIFO: a request starts once its network's pool can hold its
-  // reservation (the pools are allocated within the context's HBM budget)
+  // admission, FIFO: a request starts once the HBM its node slots take fits
+  // the serving budget next to the active requests of every network, and its
+  // network's pool can hold the slots (the pools are allocated within the
+  // context's HBM budget)
+  const uint64_t hbm = c->serve_budget ? c->serve_budget : c->budget;
   while (!c->req_queue.empty()) {
     Request* r = c->req_queue.front();
     mnbab_net* n = r->p->net;
     const int avail = n->cap - 8;  // the pad slot and a small margin
-    // a request larger than the room still runs once its network is idle
+    // a request larger than the room still runs once its network is idle, and
+    // one larger than the budget once no request is active
     if (c->reserved[n->id] > 0 && c->reserved[n->id] + r->reserve > avail) break;
+    if (c->serve_bytes > 0 && c->serve_bytes + r->bytes > hbm) break;
     c->reserved[n->id] += r->reserve;
+    c->serve_bytes += r->bytes;
     r->p->admitted = true;
     r->state = 1;
     r->t_admit = now_s();
@@ -2907,6 +2925,7 @@ mnbab_status mnbab_serve_step(mnbab_ctx* c, int32_t max_nodes, const mnbab_adam*
       r->state = 2;
       r->t_done = t;
       c->reserved[n->id] -= r->reserve;
+      c->serve_bytes -= r->bytes;
       out->finished++;
     }
   }
@@ -2914,6 +2933,13 @@ mnbab_status mnbab_serve_step(mnbab_ctx* c, int32_t max_nodes, const mnbab_adam*
     if (r->state == 0) out->queued++;
     if (r->state == 1) out->active++;
   }
+  out->reserved_bytes = (int64_t)c->serve_bytes;
+  API_END(c)
+}
+
+mnbab_status mnbab_set_serving_budget(mnbab_ctx* c, uint64_t bytes) {
+  API_BEGIN(c)
+  c->serve_budget = bytes;
   API_END(c)
 }
 
