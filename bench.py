@@ -810,11 +810,11 @@ VERDICT_CFGS = {
             capacity=2048, mnc_rows=1 << 16, hbm=16 << 30, plain=True, attack=(8, 20)),
     2: dict(workload=None, props=8, full_props=100, timeout=20.0,
             full_timeout=60.0, batch=256, budget=None, capacity=32768, mnc_rows=None,
-            hbm=200 << 30, plain=False, window=16, attack=None),
+            hbm=200 << 30, plain=False, window=16, attack=(8, 20)),
     3: dict(workload="resnet_32: 3x32x32 -> conv16 3x3 -> 2 basic blocks (32, 64 ch, s2, 1x1 "
                      "shortcuts) -> FC100 -> FC10, k=3 multi-neuron constraints",
             props=8, full_props=50, timeout=20.0, full_timeout=120.0, batch=128, budget=None,
-            capacity=32768, mnc_rows=None, hbm=200 << 30, plain=False, window=16, attack=None),
+            capacity=32768, mnc_rows=None, hbm=200 << 30, plain=False, window=16, attack=(8, 20)),
 }
 
 
@@ -900,9 +900,7 @@ def verdicts_run(local, stream, cfg, full=False, max_groups=2000):
             "timeout_s": timeout or None, "node_budget_per_property": budget,
             "max_groups_per_layer": max_groups, "mnc_rows_per_property": float(np.mean(rows)),
             "generate_s_per_property": gen_s / n_props,
-            "pre_attack": (f"{spec['attack'][0]} starts x {spec['attack'][1]} sign steps"
-                           if spec["attack"] else "none (the attack kernel takes chain networks "
-                           "whose weights fit in shared memory)"),
+            "pre_attack": f"{spec['attack'][0]} starts x {spec['attack'][1]} sign steps",
             "verdicts": verd,
             "nodes": nodes, "bab_steps": steps, "wall_s": wall,
             "nodes_per_s": nodes / wall if wall else None,

@@ -464,8 +464,14 @@ mnbab_status mnbab_request_result(mnbab_ctx* ctx, uint64_t ticket, int32_t* verd
  * smallest FP32 margin over all iterates of all starts; x_out (host,
  * [n_rows][d0], nullable) its first minimiser (starts in order).  A negative
  * margin is a counterexample candidate: confirm it in higher precision before
- * using it.  Chain networks of FC / convolution layers whose weights fit in
- * shared memory; MNBAB_E_UNSUPPORTED otherwise. */
+ * using it.  Any network the library loads.  Two forms compute it (chosen by
+ * mnbab_set_attack_path): one kernel per (row, start) that keeps the weights
+ * and the iterate in shared memory (chain networks whose weights fit), and
+ * the per-layer form, which runs the bounding path's forward and
+ * back-substitution kernels on scratch node slots whose bounds hold the
+ * iterate's pre-activations (l = u = zhat: the DeepPoly back-substitution of
+ * the objective row is then the margin's gradient, ReLU' = 1 where zhat >= 0);
+ * it takes a node slot per candidate, in chunks of the batch capacity. */
 mnbab_status mnbab_attack(mnbab_ctx* ctx, const mnbab_prop* prop, int32_t n_starts, int32_t steps,
                           const float* starts, float* best_out, float* x_out);
 
@@ -475,12 +481,17 @@ mnbab_status mnbab_attack(mnbab_ctx* ctx, const mnbab_prop* prop, int32_t n_star
  * n_starts - 1 points lo + (hi - lo) u with u_{k,j} = the top 53 bits of the
  * SplitMix64 output at state seed + (i + 1) 0x9E3779B97F4A7C15,
  * i = (k - 1) d0 + j, over [0, 1).  A row whose best point has a negative
- * margin in FP64 (host forward pass) falsifies the property before any node is
- * bounded; otherwise branch-and-bound proceeds as usual.  n_starts = 0 (the
- * default) turns it off.  Call before the property starts; chain networks
- * only (MNBAB_E_UNSUPPORTED otherwise). */
+ * margin in FP64 (a forward pass on the host for the one-kernel form, on the
+ * device for the per-layer form) falsifies the property before any node is
+ * bounded; otherwise branch-and-bound proceeds as usual.  n_starts = 0
+ * (the default) turns it off.  Call before the property starts. */
 mnbab_status mnbab_set_attack(mnbab_ctx* ctx, mnbab_prop* prop, int32_t n_starts, int32_t steps,
                               uint64_t seed);
+
+/* Form of the attack for the whole context: 0 (default) the one-kernel form
+ * where the network allows it, else the per-layer form; 1 the one-kernel form
+ * only (MNBAB_E_UNSUPPORTED on other networks); 2 the per-layer form always. */
+mnbab_status mnbab_set_attack_path(mnbab_ctx* ctx, int32_t path);
 
 /* Number of open nodes queued for the property. */
 mnbab_status mnbab_queue_size(const mnbab_ctx* ctx, const mnbab_prop* prop, int32_t* n_out);

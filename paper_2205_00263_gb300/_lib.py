@@ -113,6 +113,7 @@ SIGNATURES = {
     "mnbab_submit": (status, [VP, VP, C.c_double, C.POINTER(C.c_uint64)]),
     "mnbab_serve_step": (status, [VP, C.c_int32, C.POINTER(Adam), C.POINTER(ServeStats)]),
     "mnbab_set_serving_budget": (status, [VP, C.c_uint64]),
+    "mnbab_set_attack_path": (status, [VP, C.c_int32]),
     "mnbab_poll": (status, [VP, C.c_uint64, IP]),
     "mnbab_request_result": (status, [VP, C.c_uint64, IP, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), IP]),

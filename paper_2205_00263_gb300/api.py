@@ -351,6 +351,10 @@ class Context:
         self._ck(self.lib.mnbab_queue_size(self.h, prop.h, C.byref(n)))
         return n.value
 
+    def set_attack_path(self, path: int):
+        """0 auto, 1 one kernel per (row, start), 2 per-layer kernels."""
+        self._ck(self.lib.mnbab_set_attack_path(self.h, path))
+
     def set_attack(self, prop: Prop, n_starts: int, steps: int, seed: int = 0):
         """Pre-attack when the property starts (box centre plus SplitMix64 starts)."""
         self._ck(self.lib.mnbab_set_attack(self.h, prop.h, n_starts, steps, seed))

@@ -2221,4 +2221,114 @@ void launch_fill(float* p, size_t n, float v, cudaStream_t st) {
   k_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, n, v);
 }
 
+// ---------------------------------------------------------------------------
+// Pre-attack in the per-layer form (Sec. 4, experimental setup): candidate m
+// is a scratch node slot whose bounds hold the pre-activations at its point
+// (l = u = zhat), so that a DeepPoly back-substitution of the objective row
+// through it is the gradient of the margin (ReLU' = 1 where zhat >= 0).
+// ---------------------------------------------------------------------------
+// Slot m of the chunk: no splits, zero parameters, property `prop`, row
+// (q0 + m) / n_starts; its point, start (q0 + m) mod n_starts clipped to the
+// box (starts null: left as is); best margin +inf.
+__global__ void k_attack_init(int M, int q0, int n_starts, const int* slots, PoolDev pool,
+                              int prop, const PropDev* props, const float* starts, float* X,
+                              float* best) {
+  const int m = blockIdx.y;
+  const int slot = slots[m];
+  const int q = q0 + m;
+  const PropDev& P = props[prop];
+  const int lim = max(pool.SD, pool.d0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += gridDim.x * blockDim.x) {
+    if (i < pool.SD) {
+      const size_t o = (size_t)slot * pool.SD + i;
+      pool.L[o] = 0.f;
+      pool.U[o] = 0.f;
+      pool.S[o] = 0;
+      pool.ALPHA[o] = 0.f;
+      pool.BETA[o] = 0.f;
+    }
+    if (starts && i < pool.d0)
+      X[(size_t)m * pool.d0 + i] =
+          fminf(fmaxf(starts[(size_t)(q % n_starts) * pool.d0 + i], P.lo[i]), P.hi[i]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    pool.prop[slot] = prop;
+    pool.row[slot] = q / n_starts;
+    if (best) best[m] = INFINITY;
+  }
+}
+
+void launch_attack_init(int M, int q0, int n_starts, const int* slots, PoolDev pool, int prop,
+                        const PropDev* props, const float* starts, float* X, float* best,
+                        cudaStream_t st) {
+  if (M <= 0) return;
+  const int lim = std::max(pool.SD, pool.d0);
+  dim3 grid((unsigned)std::min(64, (lim + 255) / 256), (unsigned)M);
+  k_attack_init<<<grid, 256, 0, st>>>(M, q0, n_starts, slots, pool, prop, props, starts, X, best);
+}
+
+// z [M][d] holds the pre-activations zhat of ReLU layer (offset off): they go
+// to the bounds of each row's slot (l = u = zhat) and z becomes max(zhat, 0)
+__global__ void k_pattern_relu(int M, const int* slots, PoolDev pool, int off, int d, float* z) {
+  const size_t total = (size_t)M * d;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(i / d), j = (int)(i % d);
+    const float v = z[i];
+    const size_t q = (size_t)slots[m] * pool.SD + off + j;
+    pool.L[q] = v;
+    pool.U[q] = v;
+    z[i] = fmaxf(v, 0.f);
+  }
+}
+
+void launch_pattern_relu(int M, const int* slots, PoolDev pool, int off, int d, float* z,
+                         cudaStream_t st) {
+  if (M <= 0 || d <= 0) return;
+  const size_t total = (size_t)M * d;
+  const int blocks = (int)std::min<size_t>(152 * 8, (total + 255) / 256);
+  k_pattern_relu<<<blocks, 256, 0, st>>>(M, slots, pool, off, d, z);
+}
+
+// best[m] and its point bx[m] <- f[m] and X[m] when f[m] is smaller (the
+// first minimiser is kept on ties; NaN never replaces it)
+__global__ void k_attack_best(const float* f, const float* X, int d0, float* best, float* bx) {
+  const int m = blockIdx.x;
+  const bool better = f[m] < best[m];
+  if (better)
+    for (int j = threadIdx.x; j < d0; j += blockDim.x) bx[(size_t)m * d0 + j] = X[(size_t)m * d0 + j];
+  __syncthreads();
+  if (better && threadIdx.x == 0) best[m] = f[m];
+}
+
+void launch_attack_best(int M, const float* f, const float* X, int d0, float* best, float* bx,
+                        cudaStream_t st) {
+  if (M <= 0) return;
+  k_attack_best<<<M, 128, 0, st>>>(f, X, d0, best, bx);
+}
+
+// x <- clip(x - alpha sign(g), lo, hi), alpha_j = 2.5 (hi_j - lo_j) / (2 steps),
+// sign(0) = 0, with g [M][ld] the margin's gradient
+__global__ void k_attack_step(int M, const float* g, int ld, float* X, int d0,
+                              const PropDev* props, int prop, int steps) {
+  const PropDev& P = props[prop];
+  const size_t total = (size_t)M * d0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(i / d0), j = (int)(i % d0);
+    const float gj = g[(size_t)m * ld + j];
+    const float sg = gj > 0.f ? 1.f : (gj < 0.f ? -1.f : 0.f);
+    const float alpha = 2.5f * (P.hi[j] - P.lo[j]) / (2.0f * (float)steps);
+    X[i] = fminf(fmaxf(X[i] - alpha * sg, P.lo[j]), P.hi[j]);
+  }
+}
+
+void launch_attack_step(int M, const float* g, int ld, float* X, int d0, const PropDev* props,
+                        int prop, int steps, cudaStream_t st) {
+  if (M <= 0) return;
+  const size_t total = (size_t)M * d0;
+  const int blocks = (int)std::min<size_t>(152 * 8, (total + 255) / 256);
+  k_attack_step<<<blocks, 256, 0, st>>>(M, g, ld, X, d0, props, prop, steps);
+}
+
 }  // namespace mnbab

@@ -280,6 +280,19 @@ void launch_set_update(int M, const int* orig, const int* j, const float* sign, 
 // Root nodes: slots[i] initialised from root-bound slot srcs[i] for row rows[i].
 void launch_root_init(int nb, const int* slots, const int* srcs, const int* rows, PoolDev pool,
                       cudaStream_t st);
+// Pre-attack in the per-layer form: candidate slots (no splits, zero
+// parameters, property and row, points clipped from the starts), the
+// pre-activation capture (slot bounds l = u = zhat, z <- max(zhat, 0)), best
+// tracking and the clipped sign step.
+void launch_attack_init(int M, int q0, int n_starts, const int* slots, PoolDev pool, int prop,
+                        const PropDev* props, const float* starts, float* X, float* best,
+                        cudaStream_t st);
+void launch_pattern_relu(int M, const int* slots, PoolDev pool, int off, int d, float* z,
+                         cudaStream_t st);
+void launch_attack_best(int M, const float* f, const float* X, int d0, float* best, float* bx,
+                        cudaStream_t st);
+void launch_attack_step(int M, const float* g, int ld, float* X, int d0, const PropDev* props,
+                        int prop, int steps, cudaStream_t st);
 void launch_final_dot(int M, const int* row_node, PoolDev pool, const PropDev* props,
                       const float* z, int ld, int dR, float* f, cudaStream_t st);
 // Counterexample confirmation in FP64 needs a per-row buffer of d0 + SD doubles.

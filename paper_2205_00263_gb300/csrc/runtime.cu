@@ -168,6 +168,7 @@ struct mnbab_ctx {
   bool own_stream = false;
   uint64_t budget = 0, used = 0;
   int node_cap = 65536, EC = 0, row_chunk = 32768, gemm_path = 0;
+  int attack_path = 0;  // 0 auto, 1 one kernel per (row, start), 2 per-layer kernels
   int* d_err = nullptr;  // device error flag of bounded device waits
   std::string err;
   std::vector<mnbab_net*> nets;
@@ -494,6 +495,7 @@ struct SweepOpts {
   bool has_gamma = false;
   bool store = false;       // keep a' checkpoints and x*
   bool track = false;       // keep best bound / minimiser per node
+  bool keep_a0 = false;     // write the input coefficients a0 to the input buffer
 };
 
 // Back-substitutes rows that all start at zhat^(t) down to the input, node by
@@ -593,7 +595,7 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
       }
       e.slot_base = used;
       e.sparse_rows = conv_only ? 1 : 0;
-      float* out = (sidx >= 1 || !last) ? lam_buf(n, sidx) : nullptr;
+      float* out = (sidx >= 1 || !last || o.keep_a0) ? lam_buf(n, sidx) : nullptr;
       if (v == t) {
         Scope sc(c, C_INIT, 0.0, 4.0 * rows.M * nd.d[sidx]);
         launch_init_rows(nd, t, k, rows, out, nd.d[sidx], e, c->st);
@@ -1192,11 +1194,154 @@ void update_cab(mnbab_net* n, mnbab_prop* p) {
 // Adversarial pre-attack (Sec. 4): sign-step PGD on every property row from
 // n_starts starting points; best_out[r] / x_out[r] the row's smallest FP32
 // margin over all iterates and its first minimiser.
-void attack_impl(mnbab_ctx* c, const mnbab_prop* p, int n_starts, int steps, const float* starts,
-                 float* best_out, float* x_out) {
+// Forward pass of the attack candidates (the batch's slots) from points x:
+// every ReLU layer's pre-activations go to the candidate slot's bounds and the
+// layer buffers hold the activations; the margins land in n->fout.
+void attack_forward(mnbab_net* n, int M, const float* x) {
+  mnbab_ctx* c = n->ctx;
+  const NetDev& nd = n->nd;
+  for (int t = 1; t <= n->R; ++t) {
+    for (int k = 0; k < nd.n_edge[t]; ++k) {
+      const int sidx = src_of(n, t, k);
+      Epi e = base_epi(n, n->bslots);
+      e.part = nullptr;
+      e.kind = EPI_STORE;
+      if (k > 0) {
+        e.acc_in = lam_buf(n, t);
+        e.acc_ld = nd.d[t];
+      }
+      const float* in = sidx == 0 ? x : lam_buf(n, sidx);
+      const int ld_in = sidx == 0 ? n->d0 : nd.d[sidx];
+      const LayerDev& L = edge_of(n, t, k);
+      Scope sc(c, L.kind == 1 ? C_FWD_FC : (conv_tc_chosen(L, 0, e) ? C_FWD_CONV_TC : C_FWD_CONV),
+               2.0 * M * layer_macs(L), 4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
+      launch_forward(L, M, in, ld_in, lam_buf(n, t), nd.d[t], e, c->st);
+    }
+    Scope sc(c, C_BOOK, 0.0, 12.0 * M * nd.d[t]);
+    launch_pattern_relu(M, n->bslots, n->pool, nd.off[t], nd.d[t], lam_buf(n, t), c->st);
+  }
+  const int sR = nd.src1[n->R + 1];
+  const int dR = nd.d[sR];
+  const float* z = sR == 0 ? x : lam_buf(n, sR);
+  Scope sc(c, C_BOOK, 2.0 * M * dR, 8.0 * M * dR);
+  launch_final_dot(M, n->bslots, n->pool, c->d_props, z, sR == 0 ? n->d0 : dR, dR, n->fout, c->st);
+}
+
+// Candidate slots of one chunk, released on every exit.
+struct AttackSlots {
+  mnbab_net* n;
+  std::vector<int> s;
+  ~AttackSlots() {
+    for (int x : s) free_slot(n, x);
+  }
+};
+
+// The pre-attack in the per-layer form, for any network the library loads:
+// candidate q = r n_starts + s (row r, start s) is a scratch node slot; per
+// iterate the forward kernels of the bounding path give the margin and write
+// the pre-activations into the slot's bounds (l = u = zhat), and the DeepPoly
+// back-substitution of the objective row through that slot (ReLU' = 1 where
+// zhat >= 0, no splits or parameters) is the margin's gradient at the input.
+// Candidates run in chunks of the batch capacity.  f64_out (nullable) gets
+// each row's chosen point's margin in FP64 (device forward pass).
+void attack_layers(mnbab_ctx* c, const mnbab_prop* p, int n_starts, int steps, const float* starts,
+                   float* best_out, float* x_out, std::vector<double>* f64_out) {
   mnbab_net* n = p->net;
-  if (!attack_supported(n->nd))
-    fail(MNBAB_E_UNSUPPORTED, "the attack runs on chain networks whose weights fit in shared memory");
+  const int nr = p->n_rows, d0 = n->d0, Q = nr * n_starts;
+  const int Qc = std::min({Q, n->B, n->chunk, (int)n->free_slots.size()});
+  if (Qc < 1) fail(MNBAB_E_BUDGET, "node pool exhausted");
+  const size_t need = (size_t)n_starts * d0 + (size_t)Qc * (2 * (size_t)d0 + 1);
+  if (n->atk_cap < need) {
+    n->atk = dalloc_t<float>(c, need);
+    n->atk_cap = need;
+  }
+  float* dst = n->atk;
+  float* dX = dst + (size_t)n_starts * d0;
+  float* dBx = dX + (size_t)Qc * d0;
+  float* dBest = dBx + (size_t)Qc * d0;
+  h2d(c, dst, starts, (size_t)n_starts * d0);
+  std::vector<float> hb(Q), hx((size_t)Q * d0);
+  for (int q0 = 0; q0 < Q; q0 += Qc) {
+    const int M = std::min(Qc, Q - q0);
+    AttackSlots sl{n, {}};
+    for (int m = 0; m < M; ++m) {
+      const int s = alloc_slot(n);
+      sl.s.push_back(s);
+      n->slot_prop[s] = p->index;
+      n->slot_row[s] = (q0 + m) / n_starts;
+    }
+    upload_batch(n, sl.s);
+    {
+      Scope sc(c, C_BOOK, 0.0, 20.0 * M * n->SD);
+      launch_attack_init(M, q0, n_starts, n->bslots, n->pool, p->index, c->d_props, dst, dX, dBest,
+                         c->st);
+    }
+    for (int k = 0; k <= steps; ++k) {
+      attack_forward(n, M, dX);
+      {
+        Scope sc(c, C_BOOK, 0.0, 8.0 * M * d0);
+        launch_attack_best(M, n->fout, dX, d0, dBest, dBx, c->st);
+      }
+      if (k == steps) break;
+      SweepOpts o;
+      o.keep_a0 = true;
+      sweep(n, n->R + 1, obj_rows(n, M), o);
+      Scope sc(c, C_BOOK, 0.0, 12.0 * M * d0);
+      launch_attack_step(M, lam_buf(n, 0), d0, dX, d0, c->d_props, p->index, steps, c->st);
+    }
+    d2h(c, hb.data() + q0, dBest, M);
+    d2h(c, hx.data() + (size_t)q0 * d0, dBx, (size_t)M * d0);
+    sync(c);
+  }
+  std::vector<float> xr((size_t)nr * d0);
+  for (int r = 0; r < nr; ++r) {
+    int bs = 0;
+    for (int s0 = 1; s0 < n_starts; ++s0)
+      if (hb[(size_t)r * n_starts + s0] < hb[(size_t)r * n_starts + bs]) bs = s0;  // first on ties
+    best_out[r] = hb[(size_t)r * n_starts + bs];
+    std::memcpy(xr.data() + (size_t)r * d0, hx.data() + ((size_t)r * n_starts + bs) * d0,
+                (size_t)d0 * sizeof(float));
+  }
+  if (x_out) std::memcpy(x_out, xr.data(), xr.size() * sizeof(float));
+  if (!f64_out) return;
+  // FP64 margins of the chosen points (row r's point in a slot of row r)
+  f64_out->assign(nr, 0.0);
+  const int Rc = std::min({nr, n->B, (int)n->free_slots.size()});
+  if (Rc < 1) fail(MNBAB_E_BUDGET, "node pool exhausted");
+  for (int r0 = 0; r0 < nr; r0 += Rc) {
+    const int M = std::min(Rc, nr - r0);
+    AttackSlots sl{n, {}};
+    for (int m = 0; m < M; ++m) {
+      const int s = alloc_slot(n);
+      sl.s.push_back(s);
+      n->slot_prop[s] = p->index;
+      n->slot_row[s] = r0 + m;
+    }
+    upload_batch(n, sl.s);
+    launch_attack_init(M, r0, 1, n->bslots, n->pool, p->index, c->d_props, nullptr, nullptr,
+                       nullptr, c->st);
+    h2d(c, n->Xb, xr.data() + (size_t)r0 * d0, (size_t)M * d0);
+    {
+      Scope sc(c, C_BOOK, 2.0 * M * n->SD, 8.0 * M * (d0 + n->SD));
+      launch_forward_f64(M, n->bslots, n->pool, c->d_props, n->nd, n->Xb, d0, n->f64a,
+                         d0 + n->SD, n->f64out, c->st);
+    }
+    d2h(c, f64_out->data() + r0, n->f64out, M);
+    sync(c);
+  }
+}
+
+void attack_impl(mnbab_ctx* c, const mnbab_prop* p, int n_starts, int steps, const float* starts,
+                 float* best_out, float* x_out, std::vector<double>* f64_out = nullptr) {
+  mnbab_net* n = p->net;
+  const bool fused = attack_supported(n->nd);
+  if (c->attack_path == 1 && !fused)
+    fail(MNBAB_E_UNSUPPORTED, "the one-kernel attack takes chain networks whose weights fit in "
+                              "shared memory");
+  if (c->attack_path == 2 || !fused) {
+    attack_layers(c, p, n_starts, steps, starts, best_out, x_out, f64_out);
+    return;
+  }
   const int nr = p->n_rows, d0 = n->d0, nb = nr * n_starts;
   const size_t need = (size_t)n_starts * d0 + nb + (size_t)nb * d0;
   if (n->atk_cap < need) {
@@ -1292,9 +1437,12 @@ bool pre_attack(mnbab_ctx* c, mnbab_prop* p) {
       const double u = splitmix_uniform(p->atk_seed, (uint64_t)(k - 1) * d0 + j);
       st[(size_t)k * d0 + j] = (float)((double)p->lo[j] + ((double)p->hi[j] - p->lo[j]) * u);
     }
-  attack_impl(c, p, ns, p->atk_steps, st.data(), best.data(), x.data());
+  const bool fused = c->attack_path != 2 && attack_supported(n->nd);
+  std::vector<double> f64;
+  attack_impl(c, p, ns, p->atk_steps, st.data(), best.data(), x.data(), fused ? nullptr : &f64);
   for (int r = 0; r < p->n_rows; ++r)
-    if (best[r] < 0.f && host_margin(n, p, r, x.data() + (size_t)r * d0) < 0.0) {
+    if (best[r] < 0.f &&
+        (fused ? host_margin(n, p, r, x.data() + (size_t)r * d0) : f64[r]) < 0.0) {
       p->verdict = MNBAB_FALSIFIED;
       p->done = true;
       p->cex.assign(x.begin() + (size_t)r * d0, x.begin() + (size_t)(r + 1) * d0);
@@ -3009,14 +3157,19 @@ mnbab_status mnbab_attack(mnbab_ctx* c, const mnbab_prop* p, int32_t n_starts, i
   API_END(c)
 }
 
+mnbab_status mnbab_set_attack_path(mnbab_ctx* c, int32_t path) {
+  API_BEGIN(c)
+  if (path < 0 || path > 2) fail(MNBAB_E_INVALID_ARG, "attack path is 0, 1 or 2");
+  c->attack_path = path;
+  API_END(c)
+}
+
 mnbab_status mnbab_set_attack(mnbab_ctx* c, mnbab_prop* p, int32_t n_starts, int32_t steps,
                               uint64_t seed) {
   API_BEGIN(c)
   if (!p || n_starts < 0 || (n_starts > 0 && steps < 1))
     fail(MNBAB_E_INVALID_ARG, "bad attack arguments");
   if (p->materialized) fail(MNBAB_E_INVALID_ARG, "property already started");
-  if (n_starts > 0 && !attack_supported(p->net->nd))
-    fail(MNBAB_E_UNSUPPORTED, "the attack runs on chain networks whose weights fit in shared memory");
   p->atk_starts = n_starts;
   p->atk_steps = steps;
   p->atk_seed = seed;

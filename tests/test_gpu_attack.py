@@ -1,4 +1,7 @@
-"""GPU adversarial pre-attack (mnbab_attack) against the oracle (oracle/attack.py)."""
+"""GPU adversarial pre-attack (mnbab_attack) against the oracle (oracle/attack.py),
+in both forms: one kernel per (row, start) (path 1) and the per-layer kernels
+on scratch node slots (path 2, and the only form for residual networks and
+networks whose weights exceed shared memory)."""
 import numpy as np
 import pytest
 
@@ -24,7 +27,8 @@ def _margin64(layers, C, d, r, x):
     return float(C[r] @ synth.net_forward(layers, np.asarray(x, np.float64)) + d[r])
 
 
-def test_affine_region_reaches_the_closed_form_minimum(Context):
+@pytest.mark.parametrize("path", [1, 2])
+def test_affine_region_reaches_the_closed_form_minimum(Context, path):
     """Every ReLU active on the box: the margin is affine and the sign steps end at
     the minimising corner, so the attack must return the exact minimum."""
     layers = synth.tiny_fc_net(5, [5, 8, 6, 3])
@@ -36,6 +40,7 @@ def test_affine_region_reaches_the_closed_form_minimum(Context):
     starts = (lo + (hi - lo) * np.random.default_rng(1).uniform(size=(2, 5))).astype(np.float32)
     ref = attack.attack(layers, C, d, lo, hi, starts.astype(np.float64), steps=6)
     with Context(node_capacity=64) as ctx:
+        ctx.set_attack_path(path)
         net = ctx.load_network(layers)
         p = ctx.set_property(net, lo, hi, C, d)
         best, x = ctx.attack(p, starts, steps=6)
@@ -44,8 +49,9 @@ def test_affine_region_reaches_the_closed_form_minimum(Context):
         assert abs(_margin64(layers, C, d, r, x[r]) - rb) <= TOL * (1 + abs(rb))
 
 
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("case", ["fc", "conv"])
-def test_one_step_matches_oracle(Context, case):
+def test_one_step_matches_oracle(Context, case, path):
     """From identical starting points, one sign step gives the oracle's iterate and
     margin wherever no gradient component is near zero (there FP32 and FP64 may
     take different signs, so such samples are skipped)."""
@@ -61,6 +67,7 @@ def test_one_step_matches_oracle(Context, case):
     rng = np.random.default_rng(13)
     checked = 0
     with Context(node_capacity=64) as ctx:
+        ctx.set_attack_path(path)
         net = ctx.load_network(layers)
         p = ctx.set_property(net, lo, hi, C, d)
         for _ in range(6):
@@ -101,14 +108,20 @@ def test_full_attack_on_the_conv_net_is_sound(Context):
         assert best[r] <= f_starts + TOL * (1 + abs(f_starts))
 
 
-def test_residual_networks_are_refused(Context):
+def test_one_kernel_form_refuses_residual_networks(Context):
+    """Path 1 (one kernel per row and start) takes chain networks only; the
+    default path runs residual networks in the per-layer form."""
     from paper_2205_00263_gb300 import MnbabError
     layers, C, d, lo, hi, _ = conv_case(4, 0.02, resnet_spec)
     with Context(node_capacity=64) as ctx:
         net = ctx.load_network(layers)
         p = ctx.set_property(net, lo, hi, C, d)
+        ctx.set_attack_path(1)
         with pytest.raises(MnbabError):
             ctx.attack(p, lo[None, :], steps=2)
+        ctx.set_attack_path(0)
+        best, x = ctx.attack(p, lo[None, :], steps=2)
+        assert np.all(np.isfinite(best))
 
 
 def _well_conditioned(net64, lo, hi, r, start, steps, rel=1e-4):
@@ -134,11 +147,15 @@ def _well_conditioned(net64, lo, hi, r, start, steps, rel=1e-4):
         x = np.clip(x - alpha * np.sign(g), lo, hi)
 
 
-@pytest.mark.parametrize("case", ["fc", "conv"])
-def test_multi_step_attack_matches_oracle(Context, case):
+@pytest.mark.parametrize("case,path", [("fc", 1), ("fc", 2), ("conv", 1), ("conv", 2),
+                                       ("resnet", 0)])
+def test_multi_step_attack_matches_oracle(Context, case, path):
     """Six sign steps from identical starts give the oracle's best margin and
-    minimiser on every row whose FP64 trajectory is well conditioned."""
-    if case == "fc":
+    minimiser on every row whose FP64 trajectory is well conditioned (the
+    residual network in the per-layer form)."""
+    if case == "resnet":
+        layers, C, d, lo, hi, _ = conv_case(4, 0.02, resnet_spec)
+    elif case == "fc":
         layers = synth.tiny_fc_net(11, [12, 16, 9, 4])
         x0 = np.random.default_rng(12).uniform(0.2, 0.8, 12).astype(np.float32)
         y = synth.net_forward(layers, x0)
@@ -151,6 +168,7 @@ def test_multi_step_attack_matches_oracle(Context, case):
     rng = np.random.default_rng(21)
     checked = 0
     with Context(node_capacity=64) as ctx:
+        ctx.set_attack_path(path)
         net = ctx.load_network(layers)
         p = ctx.set_property(net, lo, hi, C, d)
         for _ in range(16):
@@ -196,3 +214,51 @@ def test_pre_attack_in_bab_falsifies_before_any_node(Context):
         with pytest.raises(Exception):
             ctx.set_attack(p, 4, 20)   # already started
     assert seen[True] >= 1
+
+
+def test_per_layer_attack_on_conv_big_is_sound(Context):
+    """conv_big_32 (weights beyond shared memory: the per-layer form), 3 starts
+    x 8 steps: every minimiser lies in the box, its FP64 margin is the reported
+    one within the tolerance, and it is no worse than its start."""
+    layers = synth.make_network(2)
+    pr = synth.make_properties(2, layers, n=1, eps=synth.load_eps(2))[0]
+    rng = np.random.default_rng(15)
+    starts = (pr.lo + (pr.hi - pr.lo) * rng.uniform(size=(3, pr.lo.size))).astype(np.float32)
+    with Context(node_capacity=64) as ctx:
+        net = ctx.load_network(layers)
+        p = ctx.set_property(net, pr.lo, pr.hi, pr.C, pr.d)
+        best, x = ctx.attack(p, starts, steps=8)
+    for r in range(pr.C.shape[0]):
+        assert (x[r] >= pr.lo).all() and (x[r] <= pr.hi).all()
+        m = _margin64(layers, pr.C, pr.d, r, x[r])
+        assert abs(m - best[r]) <= TOL * (1 + abs(m))
+        f_starts = min(_margin64(layers, pr.C, pr.d, r, s) for s in starts)
+        assert best[r] <= f_starts + TOL * (1 + abs(f_starts))
+
+
+def test_pre_attack_in_bab_on_a_residual_network(Context):
+    """mnbab_set_attack on a residual network (per-layer form, FP64 check on the
+    device): a property the oracle's attack (same starts) falsifies is
+    FALSIFIED before any node with a counterexample that holds in FP64; one
+    it does not falsify goes on to branch-and-bound."""
+    seen = 0
+    with Context(node_capacity=256) as ctx:
+        for k, (seed, eps) in enumerate(((4, 0.06), (5, 0.06), (6, 0.06), (5, 0.004))):
+            layers, C, d, lo, hi, _ = conv_case(seed, eps, resnet_spec)
+            starts = attack.attack_starts(lo, hi, 3, seed=200 + k)
+            ref = attack.attack(layers, C, d, lo, hi, starts, steps=10)
+            o_best = min(b for b, _ in ref)
+            net = ctx.load_network(layers)
+            p = ctx.set_property(net, lo, hi, C, d)
+            ctx.set_attack(p, 3, 10, seed=200 + k)
+            ctx.set_budget(p, 8)
+            ctx.bab_step([p], max_nodes=64, steps=5)
+            v, _, xc = ctx.verdict(p)
+            if o_best < -1e-4:
+                assert v == -1 and len(ctx.trace(p)) == 0, k
+                assert np.all(xc >= lo) and np.all(xc <= hi)
+                assert (C @ synth.net_forward(layers, xc.astype(np.float64)) + d).min() < 0
+                seen += 1
+            elif o_best > 1e-4:
+                assert len(ctx.trace(p)) > 0
+    assert seen >= 1
