@@ -493,6 +493,48 @@ mnbab_status mnbab_set_attack(mnbab_ctx* ctx, mnbab_prop* prop, int32_t n_starts
  * only (MNBAB_E_UNSUPPORTED on other networks); 2 the per-layer form always. */
 mnbab_status mnbab_set_attack_path(mnbab_ctx* ctx, int32_t path);
 
+/* ---- kernel variants and the autotuner --------------------------------- */
+/* Kernel variants of an affine step (back-substitution through a layer, or
+ * the forward step of the adjoint): */
+#define MNBAB_VARIANT_AUTO 0   /* the built-in choice */
+#define MNBAB_VARIANT_TC 1     /* tensor cores (tcgen05, 3xTF32, TMA-staged weights) */
+#define MNBAB_VARIANT_IGEMM 2  /* SIMT implicit GEMM per stride class (convolutions) */
+#define MNBAB_VARIANT_ROW 3    /* SIMT row-resident kernels (convolutions) */
+#define MNBAB_VARIANT_PLAIN 4  /* SIMT, whole weight tensor in shared memory (convolutions) */
+#define MNBAB_VARIANT_G32 5    /* SIMT GEMM, 32 x 32 tiles (FC) */
+#define MNBAB_VARIANT_G64 6    /* SIMT GEMM, 64 x 64 tiles (FC) */
+#define MNBAB_VARIANT_SPLITK 7 /* SIMT split-K GEMM (FC) */
+
+typedef struct {
+  int32_t node;    /* ReLU layer (1..R) that the affine edge feeds */
+  int32_t edge;    /* 0, or 1 for the second edge of a residual sum */
+  int32_t dir;     /* 0 forward step, 1 back-substitution */
+  int32_t rows;    /* rows of the timed launches */
+  int32_t variant; /* the fastest: the layer's choice for this row bucket */
+  float ms[8];     /* time per launch of each variant (index = variant), -1 if it does not apply */
+} mnbab_tune_rec;
+
+/* Autotuner (a GB300 addition; the paper has no counterpart): for every affine
+ * edge of the network, both directions and the row buckets <= 32, 128, 512,
+ * 2048, 8192 and more (up to min(max_rows, the row scratch)), times each
+ * variant that takes the layer (one untimed and three timed launches with
+ * CUDA events on the context's stream, the fastest counts) with a plain store
+ * epilogue, and makes the fastest the layer's choice for that bucket; larger
+ * buckets take the largest one timed.  Later launches of the network use the
+ * choices (except under a forced mnbab_options.gemm_path, and for
+ * back-substitution rows that the built-in choice sends to the sparse-row
+ * kernels).  The variants compute the same products, with sums in different
+ * orders.  recs (nullable when max_recs = 0) receives up to max_recs records;
+ * *n_out (nullable) their total.  Call between BaB steps. */
+mnbab_status mnbab_autotune(mnbab_ctx* ctx, mnbab_net* net, int32_t max_rows,
+                            mnbab_tune_rec* recs, int32_t max_recs, int32_t* n_out);
+
+/* Fixes the variant of one affine edge and direction for every row bucket
+ * (MNBAB_VARIANT_AUTO restores the built-in choice); a variant that does not
+ * take the layer falls back to the built-in choice at launch. */
+mnbab_status mnbab_set_variant(mnbab_ctx* ctx, mnbab_net* net, int32_t node, int32_t edge,
+                               int32_t dir, int32_t variant);
+
 /* Number of open nodes queued for the property. */
 mnbab_status mnbab_queue_size(const mnbab_ctx* ctx, const mnbab_prop* prop, int32_t* n_out);
 

@@ -54,6 +54,11 @@ class ServeStats(C.Structure):
                 ("queued", C.c_int32), ("step", StepStats), ("reserved_bytes", C.c_int64)]
 
 
+class TuneRec(C.Structure):
+    _fields_ = [("node", C.c_int32), ("edge", C.c_int32), ("dir", C.c_int32),
+                ("rows", C.c_int32), ("variant", C.c_int32), ("ms", C.c_float * 8)]
+
+
 class KernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("ms", C.c_double),
                 ("flops", C.c_double), ("bytes", C.c_double)]
@@ -114,6 +119,8 @@ SIGNATURES = {
     "mnbab_serve_step": (status, [VP, C.c_int32, C.POINTER(Adam), C.POINTER(ServeStats)]),
     "mnbab_set_serving_budget": (status, [VP, C.c_uint64]),
     "mnbab_set_attack_path": (status, [VP, C.c_int32]),
+    "mnbab_autotune": (status, [VP, VP, C.c_int32, C.POINTER(TuneRec), C.c_int32, IP]),
+    "mnbab_set_variant": (status, [VP, VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "mnbab_poll": (status, [VP, C.c_uint64, IP]),
     "mnbab_request_result": (status, [VP, C.c_uint64, IP, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), IP]),

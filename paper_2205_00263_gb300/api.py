@@ -351,6 +351,28 @@ class Context:
         self._ck(self.lib.mnbab_queue_size(self.h, prop.h, C.byref(n)))
         return n.value
 
+    VARIANTS = ("auto", "tc", "igemm", "row", "plain", "g32", "g64", "splitk")
+
+    def autotune(self, net: Net, max_rows: int = 4096):
+        """Times the kernel variants of every affine edge, direction and row
+        bucket and keeps the fastest; returns one dict per (edge, dir, bucket)."""
+        n = C.c_int32()
+        self._ck(self.lib.mnbab_autotune(self.h, net.h, max_rows, None, 0, C.byref(n)))
+        arr = (L.TuneRec * max(1, n.value))()
+        self._ck(self.lib.mnbab_autotune(self.h, net.h, max_rows, arr, n.value, C.byref(n)))
+        out = []
+        for i in range(n.value):
+            r = arr[i]
+            out.append(dict(node=r.node, edge=r.edge, dir=r.dir, rows=r.rows,
+                            variant=self.VARIANTS[r.variant],
+                            ms={self.VARIANTS[v]: r.ms[v] for v in range(8) if r.ms[v] >= 0}))
+        return out
+
+    def set_variant(self, net: Net, node: int, edge: int, direction: int, variant: str):
+        """Fixes the kernel variant of one affine edge and direction ("auto" restores)."""
+        self._ck(self.lib.mnbab_set_variant(self.h, net.h, node, edge, direction,
+                                            self.VARIANTS.index(variant)))
+
     def set_attack_path(self, path: int):
         """0 auto, 1 one kernel per (row, start), 2 per-layer kernels."""
         self._ck(self.lib.mnbab_set_attack_path(self.h, path))

@@ -616,33 +616,53 @@ __global__ void __launch_bounds__(256) k_splitk_epi(int M, int N, int S, const f
 
 // 64 x 64 tiles unless that grid would leave most of the 152 SMs idle; then
 // 32 x 32 tiles, split along K when the K loop is long and the workspace fits.
+// SIMT GEMM variants: V_SPLITK (reduction split over up to 16 CTAs per tile
+// so that small products fill the SMs; -1 when no split is possible), V_G64,
+// V_G32.
+static int gemm_variant(int v, int M, int N, int K, const float* A, int lda, const float* B,
+                        int ldb, const float* bias, int bias_div, float* C, int ldc, const Epi& e,
+                        cudaStream_t st) {
+  if (v == V_SPLITK) {
+    if (K < 256 || !e.ws) return -1;
+    const long small = (long)((N + 31) / 32) * ((M + 31) / 32);
+    int S = (int)std::min<long>(16, std::max<long>(2, (2 * 152 + small - 1) / small));
+    S = std::min(S, K / 64);
+    while (S > 1 && (size_t)S * M * N > e.ws_floats) --S;
+    if (S <= 1) return -1;
+    const int kc = ((K + S - 1) / S + GBK - 1) / GBK * GBK;
+    S = (K + kc - 1) / kc;
+    dim3 g1((N + 31) / 32, (M + 31) / 32, S);
+    k_gemm_splitk<<<g1, 256, 0, st>>>(M, N, K, kc, A, lda, B, ldb, e.ws);
+    dim3 g2((N + 31) / 32, (M + 7) / 8);
+    k_splitk_epi<<<g2, 256, 0, st>>>(M, N, S, e.ws, bias, bias_div, C, ldc, e);
+    return g2.x;
+  }
+  if (v == V_G64) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    k_gemm<64, 64><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e);
+    return grid.x;
+  }
+  if (v == V_G32) {
+    dim3 grid((N + 31) / 32, (M + 31) / 32);
+    k_gemm<32, 32><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e);
+    return grid.x;
+  }
+  return -1;
+}
+
+// built-in choice: split-K when neither tiling fills two waves, else 64 x 64
+// tiles when they do, else 32 x 32
 static int gemm_launch(int M, int N, int K, const float* A, int lda, const float* B, int ldb,
                        const float* bias, int bias_div, float* C, int ldc, const Epi& e,
                        cudaStream_t st) {
   const long big = (long)((N + 63) / 64) * ((M + 63) / 64);
   const long small = (long)((N + 31) / 32) * ((M + 31) / 32);
-  if (big < 2 * 152 && small < 2 * 152 && K >= 256 && e.ws) {
-    int S = (int)std::min<long>(16, std::max<long>(2, (2 * 152 + small - 1) / small));
-    S = std::min(S, K / 64);
-    while (S > 1 && (size_t)S * M * N > e.ws_floats) --S;
-    if (S > 1) {
-      const int kc = ((K + S - 1) / S + GBK - 1) / GBK * GBK;
-      S = (K + kc - 1) / kc;
-      dim3 g1((N + 31) / 32, (M + 31) / 32, S);
-      k_gemm_splitk<<<g1, 256, 0, st>>>(M, N, K, kc, A, lda, B, ldb, e.ws);
-      dim3 g2((N + 31) / 32, (M + 7) / 8);
-      k_splitk_epi<<<g2, 256, 0, st>>>(M, N, S, e.ws, bias, bias_div, C, ldc, e);
-      return g2.x;
-    }
+  if (big < 2 * 152 && small < 2 * 152) {
+    const int r = gemm_variant(V_SPLITK, M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e, st);
+    if (r >= 0) return r;
   }
-  if (big >= 2 * 152) {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    k_gemm<64, 64><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e);
-    return grid.x;
-  }
-  dim3 grid((N + 31) / 32, (M + 31) / 32);
-  k_gemm<32, 32><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, bias, bias_div, C, ldc, e);
-  return grid.x;
+  return gemm_variant(big >= 2 * 152 ? V_G64 : V_G32, M, N, K, A, lda, B, ldb, bias, bias_div, C,
+                      ldc, e, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1394,8 +1414,13 @@ static bool use_tc_conv(const LayerDev& L, int dir, const Epi& e) {
   return e.gemm_path == 2 || (double)L.co * L.ho * L.wo * L.ci * L.k * L.k >= 512.0 * 1024.0;
 }
 
-bool conv_tc_chosen(const LayerDev& L, int dir, const Epi& e) {
-  return L.kind == MNBAB_CONV2D && use_tc_conv(L, dir, e);
+static int tuned_variant(const LayerDev& L, int dir, int M, const Epi& e);
+
+bool conv_tc_chosen(const LayerDev& L, int dir, const Epi& e, int M) {
+  if (L.kind != MNBAB_CONV2D) return false;
+  const int tv = tuned_variant(L, dir, M, e);
+  if (tv > 0) return tv == V_TC && tc_conv_usable(L, dir);
+  return use_tc_conv(L, dir, e);
 }
 
 int backsub_slots(const LayerDev& L) {
@@ -1408,14 +1433,133 @@ int backsub_slots(const LayerDev& L) {
                   tc_conv_slots(L));
 }
 
+// One variant of the transposed convolution (back-substitution, dir 1) or the
+// convolution (forward, dir 0); -1 when it does not take this layer.
+static int conv_variant(int v, int dir, const LayerDev& L, int M, const float* in, int ld_in,
+                        float* out, int ld_out, const Epi& e, cudaStream_t st) {
+  if (v == V_TC) {
+    if (!tc_conv_usable(L, dir) || (dir == 1 && e.sparse_rows)) return -1;
+    const int slots = launch_tc_conv(L, dir, M, in, ld_in, out, ld_out, e, st);
+    return dir == 1 ? slots : 0;
+  }
+  if (v == V_IG) {
+    if (!ig_supported(L, dir) || (dir == 1 && e.sparse_rows)) return -1;
+    const int slots = launch_ig(L, dir, M, in, ld_in, out, ld_out, e, st);
+    return dir == 1 ? slots : 0;
+  }
+  if (v == V_ROW && dir == 1) {
+    const int CBv = L.ci <= 1 ? 1 : (L.ci <= 4 ? 4 : 8);
+    const ConvSplit cs = conv_split(M, L.hi * L.wi, (L.ci + CBv - 1) / CBv, CBv,
+                                    [&](int cw) { return convT_row_smem(L, cw); }, 40 * 1024);
+    const int rsm = convT_row_smem(L, cs.bpg * CBv) * 4;
+    if (rsm > 160 * 1024 || !L.Wb || cs.npc * cs.ngrp > backsub_slots(L)) return -1;
+    dim3 grid(cs.npc * cs.ngrp, M);
+    if (CBv == 1) {
+      set_smem(k_convT_row<1>, rsm);
+      k_convT_row<1><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
+    } else if (CBv == 4) {
+      set_smem(k_convT_row<4>, rsm);
+      k_convT_row<4><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
+    } else {
+      set_smem(k_convT_row<8>, rsm);
+      k_convT_row<8><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
+    }
+    return grid.x;
+  }
+  if (v == V_ROW && dir == 0) {
+    const int CBv = (L.co % 8 == 0 && L.ho * L.wo >= 64) ? 8 : 4;
+    const ConvSplit cs = conv_split(M, L.ho * L.wo, (L.co + CBv - 1) / CBv, CBv,
+                                    [&](int cw) { return conv_fwd_row_smem(L, cw); }, 40 * 1024);
+    const int rsm = conv_fwd_row_smem(L, cs.bpg * CBv) * 4;
+    if (rsm > 160 * 1024 || !L.Wf) return -1;
+    dim3 grid(cs.npc * cs.ngrp, M);
+    if (CBv == 8) {
+      set_smem(k_conv_fwd_row<8>, rsm);
+      k_conv_fwd_row<8><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
+    } else {
+      set_smem(k_conv_fwd_row<4>, rsm);
+      k_conv_fwd_row<4><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
+    }
+    return 0;
+  }
+  if (v == V_PLAIN) {
+    const int smem = L.co * L.ci * L.k * L.k * 4;
+    if (smem > 200 * 1024) return -1;
+    if (dir == 1) {
+      dim3 grid((L.hi * L.wi + 127) / 128, M);
+      if (L.ci <= 1) {
+        set_smem(k_convT<1>, smem);
+        k_convT<1><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+      } else if (L.ci <= 4) {
+        set_smem(k_convT<4>, smem);
+        k_convT<4><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+      } else if (L.ci <= 16) {
+        set_smem(k_convT<16>, smem);
+        k_convT<16><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+      } else {
+        set_smem(k_convT<32>, smem);
+        k_convT<32><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+      }
+      return grid.x;
+    }
+    const int Pout = L.ho * L.wo;
+    const int rows_per = Pout >= 128 ? 1 : 128 / Pout;
+    dim3 grid(rows_per == 1 ? (Pout + 127) / 128 : 1, (M + rows_per - 1) / rows_per);
+    if (L.co <= 16) {
+      set_smem(k_conv_fwd<16>, smem);
+      k_conv_fwd<16><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+    } else {
+      set_smem(k_conv_fwd<32>, smem);
+      k_conv_fwd<32><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
+    }
+    return 0;
+  }
+  return -1;
+}
+
+int launch_affine_variant(int v, int dir, const LayerDev& L, int M, const float* in, int ld_in,
+                          float* out, int ld_out, const Epi& e, cudaStream_t st) {
+  if (M <= 0) return -1;
+  if (L.kind == 1) {
+    if (v == V_TC) {
+      const int slots =
+          dir == 1 ? launch_gemm_tc(M, L.d_in, L.d_out, in, ld_in, nullptr, 1, out, ld_out, e,
+                                    e.err, st, L.tc, 1)
+                   : launch_gemm_tc(M, L.d_out, L.d_in, in, ld_in, L.b, 1, out, ld_out, e, e.err,
+                                    st, L.tc, 0);
+      return slots < 0 ? -1 : (dir == 1 ? slots : 0);
+    }
+    // back-substitution Lambda [M][d_out] x W [d_out][d_in]; forward G [M][d_in] x W^T + b
+    const int slots =
+        dir == 1 ? gemm_variant(v, M, L.d_in, L.d_out, in, ld_in, L.W, L.d_in, nullptr, 1, out,
+                                ld_out, e, st)
+                 : gemm_variant(v, M, L.d_out, L.d_in, in, ld_in, L.Wt, L.d_out, L.b, 1, out,
+                                ld_out, e, st);
+    return slots < 0 ? -1 : (dir == 1 ? slots : 0);
+  }
+  return conv_variant(v, dir, L, M, in, ld_in, out, ld_out, e, st);
+}
+
+// the autotuner's variant for this launch, if it applies: not under a forced
+// GEMM path, and not for rows that the built-in choice serves with the
+// sparse-row kernels
+static int tuned_variant(const LayerDev& L, int dir, int M, const Epi& e) {
+  if (e.gemm_path != 0 || (dir == 1 && e.sparse_rows && L.kind != 1)) return 0;
+  return L.tune[dir][tune_bucket(M)];
+}
+
 int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
                    const Epi& e, cudaStream_t st) {
   if (M <= 0) return backsub_slots(L);
+  const int tv = tuned_variant(L, 1, M, e);
+  if (tv > 0) {
+    const int slots = launch_affine_variant(tv, 1, L, M, in, ld_in, out, ld_out, e, st);
+    if (slots >= 0) return slots;
+  }
   if (L.kind == 1) {
     // Lambda [M][d_out] x W [d_out][d_in]; the tensor-core kernel takes W as [d_in][d_out] = W^T
     if (use_tc(e, M, L.d_in)) {
-      const int slots =
-          launch_gemm_tc(M, L.d_in, L.d_out, in, ld_in, nullptr, 1, out, ld_out, e, e.err, st, L.tc, 1);
+      const int slots = launch_affine_variant(V_TC, 1, L, M, in, ld_in, out, ld_out, e, st);
       if (slots >= 0) return slots;
     }
     return gemm_launch(M, L.d_in, L.d_out, in, ld_in, L.W, L.d_in, nullptr, 1, out, ld_out, e, st);
@@ -1425,51 +1569,20 @@ int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* 
   // (nonzero only near it) skip the zero region in the row-resident kernel
   if (!e.sparse_rows && ig_supported(L, 1) && (ig_preferred(L) || !conv_supported(L)))
     return launch_ig(L, 1, M, in, ld_in, out, ld_out, e, st);
-  {
-    const int CBv = L.ci <= 1 ? 1 : (L.ci <= 4 ? 4 : 8);
-    const ConvSplit cs = conv_split(M, L.hi * L.wi, (L.ci + CBv - 1) / CBv, CBv,
-                                    [&](int cw) { return convT_row_smem(L, cw); }, 40 * 1024);
-    const int rsm = convT_row_smem(L, cs.bpg * CBv) * 4;
-    if (rsm <= 160 * 1024 && L.Wb && cs.npc * cs.ngrp <= backsub_slots(L)) {
-      dim3 grid(cs.npc * cs.ngrp, M);
-      if (CBv == 1) {
-        set_smem(k_convT_row<1>, rsm);
-        k_convT_row<1><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
-      } else if (CBv == 4) {
-        set_smem(k_convT_row<4>, rsm);
-        k_convT_row<4><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
-      } else {
-        set_smem(k_convT_row<8>, rsm);
-        k_convT_row<8><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
-      }
-      return grid.x;
-    }
-  }
-  const int smem = L.co * L.ci * L.k * L.k * 4;
-  dim3 grid((L.hi * L.wi + 127) / 128, M);
-  if (L.ci <= 1) {
-    set_smem(k_convT<1>, smem);
-    k_convT<1><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
-  } else if (L.ci <= 4) {
-    set_smem(k_convT<4>, smem);
-    k_convT<4><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
-  } else if (L.ci <= 16) {
-    set_smem(k_convT<16>, smem);
-    k_convT<16><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
-  } else {
-    set_smem(k_convT<32>, smem);
-    k_convT<32><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
-  }
-  return grid.x;
+  const int slots = conv_variant(V_ROW, 1, L, M, in, ld_in, out, ld_out, e, st);
+  if (slots >= 0) return slots;
+  return conv_variant(V_PLAIN, 1, L, M, in, ld_in, out, ld_out, e, st);
 }
 
 void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
                     const Epi& e, cudaStream_t st) {
   if (M <= 0) return;
+  const int tv = tuned_variant(L, 0, M, e);
+  if (tv > 0 && launch_affine_variant(tv, 0, L, M, in, ld_in, out, ld_out, e, st) >= 0) return;
   if (L.kind == 1) {
     // G [M][d_in] x W^T + b; the tensor-core kernel takes W [d_out][d_in] as is
     if (use_tc(e, M, L.d_out) &&
-        launch_gemm_tc(M, L.d_out, L.d_in, in, ld_in, L.b, 1, out, ld_out, e, e.err, st, L.tc, 0) >= 0)
+        launch_affine_variant(V_TC, 0, L, M, in, ld_in, out, ld_out, e, st) >= 0)
       return;
     gemm_launch(M, L.d_out, L.d_in, in, ld_in, L.Wt, L.d_out, L.b, 1, out, ld_out, e, st);
     return;
@@ -1482,34 +1595,8 @@ void launch_forward(const LayerDev& L, int M, const float* in, int ld_in, float*
     launch_ig(L, 0, M, in, ld_in, out, ld_out, e, st);
     return;
   }
-  {
-    const int CBv = (L.co % 8 == 0 && L.ho * L.wo >= 64) ? 8 : 4;
-    const ConvSplit cs = conv_split(M, L.ho * L.wo, (L.co + CBv - 1) / CBv, CBv,
-                                    [&](int cw) { return conv_fwd_row_smem(L, cw); }, 40 * 1024);
-    const int rsm = conv_fwd_row_smem(L, cs.bpg * CBv) * 4;
-    if (rsm <= 160 * 1024 && L.Wf) {
-      dim3 grid(cs.npc * cs.ngrp, M);
-      if (CBv == 8) {
-        set_smem(k_conv_fwd_row<8>, rsm);
-        k_conv_fwd_row<8><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
-      } else {
-        set_smem(k_conv_fwd_row<4>, rsm);
-        k_conv_fwd_row<4><<<grid, 128, rsm, st>>>(M, in, ld_in, out, ld_out, L, e, cs);
-      }
-      return;
-    }
-  }
-  const int smem = L.co * L.ci * L.k * L.k * 4;
-  const int Pout = L.ho * L.wo;
-  const int rows_per = Pout >= 128 ? 1 : 128 / Pout;
-  dim3 grid(rows_per == 1 ? (Pout + 127) / 128 : 1, (M + rows_per - 1) / rows_per);
-  if (L.co <= 16) {
-    set_smem(k_conv_fwd<16>, smem);
-    k_conv_fwd<16><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
-  } else {
-    set_smem(k_conv_fwd<32>, smem);
-    k_conv_fwd<32><<<grid, 128, smem, st>>>(M, in, ld_in, out, ld_out, L, e);
-  }
+  if (conv_variant(V_ROW, 0, L, M, in, ld_in, out, ld_out, e, st) >= 0) return;
+  conv_variant(V_PLAIN, 0, L, M, in, ld_in, out, ld_out, e, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -25,7 +25,30 @@ struct LayerDev {
   const float* Wb;  // conv only: [co][kh][kw][ci] (back-substitution layout)
   const float* Wf;  // conv only: [ci][kh][kw][co] (forward layout)
   const void* tc;   // host-side tensor-core operands (TcConv for conv, TcFc for FC), or null
+  // kernel variant per direction (0 forward, 1 back-substitution) and row
+  // bucket (tune_bucket), set by the autotuner; 0 = the built-in choice
+  signed char tune[2][6];
 };
+
+// Kernel variants of an affine step (the autotuner times them).
+enum KernelVariant {
+  V_AUTO = 0,    // built-in choice
+  V_TC = 1,      // tensor cores (tcgen05, 3xTF32)
+  V_IG = 2,      // SIMT implicit GEMM per stride class (conv)
+  V_ROW = 3,     // SIMT row-resident kernels (conv)
+  V_PLAIN = 4,   // SIMT kernels with the whole weight tensor in shared memory (conv)
+  V_G32 = 5,     // SIMT GEMM, 32 x 32 tiles (FC)
+  V_G64 = 6,     // SIMT GEMM, 64 x 64 tiles (FC)
+  V_SPLITK = 7,  // SIMT split-K GEMM (FC)
+  NVARIANT = 8
+};
+// row bucket of a launch of M rows: <= 32, 128, 512, 2048, 8192, more
+inline int tune_bucket(int M) {
+  int b = 0;
+  for (int lim = 32; b < 5 && M > lim; lim *= 4) ++b;
+  return b;
+}
+constexpr int TUNE_ROWS[6] = {32, 128, 512, 2048, 8192, 32768};
 
 // The network as a DAG: node t = 1..R (ReLU layers) and R + 1 (output) sums
 // one or two affine edges, zhat_t = A1(z_src1) + A2(z_src2) (+ biases), with
@@ -147,7 +170,7 @@ bool tc_conv_usable(const LayerDev& L, int dir);
 int tc_conv_slots(const LayerDev& L);
 // whether launch_backsub (dir 1) / launch_forward (dir 0) take the tensor-core
 // kernel for this layer and epilogue (kernels.cu)
-bool conv_tc_chosen(const LayerDev& L, int dir, const Epi& e);
+bool conv_tc_chosen(const LayerDev& L, int dir, const Epi& e, int M);
 // launches the implicit GEMM; returns the partial-sum slots written (dir 1)
 int launch_tc_conv(const LayerDev& L, int dir, int M, const float* in, int ld_in, float* out,
                    int ld_out, const Epi& e, cudaStream_t st);
@@ -227,6 +250,11 @@ void launch_attack_chain(const NetDev& net, const PropDev* props, int prop, int 
                          float* bx_out, cudaStream_t st);
 // Back-substitution through affine layer i: in [M][d_i] -> out [M][d_{i-1}].
 // Returns the number of partial-sum slots used.
+// One kernel variant of the back-substitution (dir 1) or forward (dir 0) step
+// through layer L: the partial-sum slots written (back-substitution) or 0, or
+// -1 without launching when the variant does not take this layer.
+int launch_affine_variant(int variant, int dir, const LayerDev& L, int M, const float* in,
+                          int ld_in, float* out, int ld_out, const Epi& e, cudaStream_t st);
 int launch_backsub(const LayerDev& L, int M, const float* in, int ld_in, float* out, int ld_out,
                    const Epi& e, cudaStream_t st);
 int backsub_slots(const LayerDev& L);

@@ -603,7 +603,7 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
       } else {
         const LayerDev& L = edge_of(n, v, k);
         Scope sc(c, L.kind == 1 ? C_BACKSUB_FC
-                                : (conv_tc_chosen(L, 1, e) ? C_BACKSUB_CONV_TC : C_BACKSUB_CONV),
+                                : (conv_tc_chosen(L, 1, e, rows.M) ? C_BACKSUB_CONV_TC : C_BACKSUB_CONV),
                  2.0 * rows.M * layer_macs(L),
                  4.0 * rows.M * (L.d_out + (out ? L.d_in : 0)) + layer_wbytes(L));
         const int sl = launch_backsub(L, rows.M, lam_buf(n, v), nd.d[v], out, nd.d[sidx], e, c->st);
@@ -724,7 +724,7 @@ void adjoint(mnbab_net* n, int M, bool has_gamma, int upto = -1) {
       const float* in = sidx == 0 ? n->X : lam_buf(n, sidx);
       const int ld_in = sidx == 0 ? n->d0 : nd.d[sidx];
       const LayerDev& L = edge_of(n, t, k);
-      Scope sc(c, L.kind == 1 ? C_FWD_FC : (conv_tc_chosen(L, 0, e) ? C_FWD_CONV_TC : C_FWD_CONV),
+      Scope sc(c, L.kind == 1 ? C_FWD_FC : (conv_tc_chosen(L, 0, e, M) ? C_FWD_CONV_TC : C_FWD_CONV),
                2.0 * M * layer_macs(L),
                4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
       launch_forward(L, M, in, ld_in, lam_buf(n, t), nd.d[t], e, c->st);
@@ -873,7 +873,7 @@ void forward_rows(mnbab_net* n, int M, const float* x) {
       const float* in = sidx == 0 ? x : lam_buf(n, sidx);
       const int ld_in = sidx == 0 ? n->d0 : nd.d[sidx];
       const LayerDev& L = edge_of(n, t, k);
-      Scope sc(c, L.kind == 1 ? C_FWD_FC : (conv_tc_chosen(L, 0, e) ? C_FWD_CONV_TC : C_FWD_CONV),
+      Scope sc(c, L.kind == 1 ? C_FWD_FC : (conv_tc_chosen(L, 0, e, M) ? C_FWD_CONV_TC : C_FWD_CONV),
                2.0 * M * layer_macs(L),
                4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
       launch_forward(L, M, in, ld_in, lam_buf(n, t), nd.d[t], e, c->st);
@@ -1213,7 +1213,7 @@ void attack_forward(mnbab_net* n, int M, const float* x) {
       const float* in = sidx == 0 ? x : lam_buf(n, sidx);
       const int ld_in = sidx == 0 ? n->d0 : nd.d[sidx];
       const LayerDev& L = edge_of(n, t, k);
-      Scope sc(c, L.kind == 1 ? C_FWD_FC : (conv_tc_chosen(L, 0, e) ? C_FWD_CONV_TC : C_FWD_CONV),
+      Scope sc(c, L.kind == 1 ? C_FWD_FC : (conv_tc_chosen(L, 0, e, M) ? C_FWD_CONV_TC : C_FWD_CONV),
                2.0 * M * layer_macs(L), 4.0 * M * (L.d_in + L.d_out) + layer_wbytes(L));
       launch_forward(L, M, in, ld_in, lam_buf(n, t), nd.d[t], e, c->st);
     }
@@ -1225,6 +1225,87 @@ void attack_forward(mnbab_net* n, int M, const float* x) {
   const float* z = sR == 0 ? x : lam_buf(n, sR);
   Scope sc(c, C_BOOK, 2.0 * M * dR, 8.0 * M * dR);
   launch_final_dot(M, n->bslots, n->pool, c->d_props, z, sR == 0 ? n->d0 : dR, dR, n->fout, c->st);
+}
+
+// Autotuner: for every affine edge, direction and row bucket up to max_rows,
+// each kernel variant that takes the layer runs once untimed and three times
+// timed (CUDA events on the context's stream, the fastest counts) on the
+// network's coefficient buffers filled with 0.5, with a plain store
+// epilogue; the fastest variant becomes the layer's choice for that bucket
+// (larger buckets take the largest one timed).
+int64_t autotune_impl(mnbab_net* n, int max_rows, std::vector<mnbab_tune_rec>& recs) {
+  mnbab_ctx* c = n->ctx;
+  NetDev& nd = n->nd;
+  const int top = std::max(1, std::min(max_rows, std::max(n->chunk, n->B)));
+  cudaEvent_t e0, e1;
+  ck(cudaEventCreate(&e0), "cudaEventCreate");
+  ck(cudaEventCreate(&e1), "cudaEventCreate");
+  struct Ev {
+    cudaEvent_t a, b;
+    ~Ev() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } ev{e0, e1};
+  for (int t = 1; t <= n->R; ++t)
+    for (int k = 0; k < nd.n_edge[t]; ++k) {
+      LayerDev& L = k == 0 ? nd.aff[t] : nd.aff2[t];
+      const int sidx = src_of(n, t, k);
+      for (int dir = 1; dir >= 0; --dir) {
+        int last = 0;
+        for (int b = 0; b < 6; ++b) {
+          if (b > 0 && TUNE_ROWS[b - 1] >= top) {
+            L.tune[dir][b] = (signed char)last;
+            continue;
+          }
+          const int M = std::min(TUNE_ROWS[b], top);
+          float* in = dir == 1 ? lam_buf(n, t) : lam_buf(n, sidx);
+          const int ld_in = dir == 1 ? nd.d[t] : nd.d[sidx];
+          float* out = dir == 1 ? lam_buf(n, sidx) : lam_buf(n, t);
+          const int ld_out = dir == 1 ? nd.d[sidx] : nd.d[t];
+          launch_fill(in, (size_t)M * ld_in, 0.5f, c->st);
+          Epi e = base_epi(n, n->bslots);
+          e.part = nullptr;
+          e.kind = EPI_STORE;
+          e.slot_base = 0;
+          e.sparse_rows = 0;
+          e.gemm_path = 0;
+          mnbab_tune_rec rec{};
+          rec.node = t;
+          rec.edge = k;
+          rec.dir = dir;
+          rec.rows = M;
+          float best = INFINITY;
+          int bv = 0;
+          for (int v = 0; v < NVARIANT; ++v) rec.ms[v] = -1.f;
+          for (int v = 1; v < NVARIANT; ++v) {
+            if (launch_affine_variant(v, dir, L, M, in, ld_in, out, ld_out, e, c->st) < 0) continue;
+            sync(c);
+            float ms = INFINITY;
+            for (int rep = 0; rep < 3; ++rep) {
+              ck(cudaEventRecord(e0, c->st), "cudaEventRecord");
+              launch_affine_variant(v, dir, L, M, in, ld_in, out, ld_out, e, c->st);
+              ck(cudaEventRecord(e1, c->st), "cudaEventRecord");
+              ck(cudaEventSynchronize(e1), "cudaEventSynchronize");
+              float x = 0.f;
+              ck(cudaEventElapsedTime(&x, e0, e1), "cudaEventElapsedTime");
+              ms = std::min(ms, x);
+            }
+            rec.ms[v] = ms;
+            if (ms < best) {
+              best = ms;
+              bv = v;
+            }
+          }
+          sync(c);  // raises the device error flag of the bounded waits, if set
+          rec.variant = bv;
+          L.tune[dir][b] = (signed char)bv;
+          last = bv;
+          recs.push_back(rec);
+        }
+      }
+    }
+  return (int64_t)recs.size();
 }
 
 // Candidate slots of one chunk, released on every exit.
@@ -3154,6 +3235,30 @@ mnbab_status mnbab_attack(mnbab_ctx* c, const mnbab_prop* p, int32_t n_starts, i
   if (!p || n_starts <= 0 || steps < 1 || !starts || !best_out)
     fail(MNBAB_E_INVALID_ARG, "bad attack arguments");
   attack_impl(c, p, n_starts, steps, starts, best_out, x_out);
+  API_END(c)
+}
+
+mnbab_status mnbab_autotune(mnbab_ctx* c, mnbab_net* n, int32_t max_rows, mnbab_tune_rec* recs,
+                            int32_t max_recs, int32_t* n_out) {
+  API_BEGIN(c)
+  if (!n || n->ctx != c || max_rows < 1 || max_recs < 0 || (max_recs > 0 && !recs))
+    fail(MNBAB_E_INVALID_ARG, "bad autotune arguments");
+  std::vector<mnbab_tune_rec> all;
+  autotune_impl(n, max_rows, all);
+  const int k = std::min((int)all.size(), max_recs);
+  if (k > 0) std::memcpy(recs, all.data(), (size_t)k * sizeof(mnbab_tune_rec));
+  if (n_out) *n_out = (int)all.size();
+  API_END(c)
+}
+
+mnbab_status mnbab_set_variant(mnbab_ctx* c, mnbab_net* n, int32_t node, int32_t edge, int32_t dir,
+                               int32_t variant) {
+  API_BEGIN(c)
+  if (!n || n->ctx != c || node < 1 || node > n->R || edge < 0 || edge >= n->nd.n_edge[node] ||
+      dir < 0 || dir > 1 || variant < 0 || variant >= NVARIANT)
+    fail(MNBAB_E_INVALID_ARG, "bad variant arguments");
+  LayerDev& L = edge == 0 ? n->nd.aff[node] : n->nd.aff2[node];
+  for (int b = 0; b < 6; ++b) L.tune[dir][b] = (signed char)variant;
   API_END(c)
 }
 

@@ -74,8 +74,11 @@ def conv_case(seed, eps, spec_fn=None):
     return layers, C, d, lo, hi, prep
 
 
-def gpu_property(ctx, layers, lo, hi, C, d, mncs=None):
-    net = ctx.load_network(layers)
+def gpu_property(ctx, layers, lo, hi, C, d, mncs=None, net=None):
+    """A property on `net` (a new copy of `layers` when None) with its
+    multi-neuron constraints."""
+    if net is None:
+        net = ctx.load_network(layers)
     prop = ctx.set_property(net, lo, hi, C, d)
     if mncs:
         for i in sorted(mncs):

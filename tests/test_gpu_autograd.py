@@ -69,7 +69,7 @@ def test_node_bound_gradient_fd_and_oracle(Context, case):
         for k, on in enumerate(onodes):
             ref, _, oa, ob, og = core.bound_and_grad(net, on, on.alpha, on.beta, on.gamma, dense,
                                                      lo_t, hi_t)
-            assert abs(float(lb[k]) - float(ref)) <= TOL * (1 + abs(float(ref)))
+            assert abs(float(lb[k].detach()) - float(ref)) <= TOL * (1 + abs(float(ref)))
             o = np.concatenate([concat(oa, net.R), concat(ob, net.R)]
                                + ([np.concatenate([og[i].numpy() for i in sorted(og)
                                                    if og[i].numel()])] if E else []))

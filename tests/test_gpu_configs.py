@@ -72,7 +72,7 @@ def test_fc_mnc_verdicts_at_budget(Context):
             gnet = ctx.load_network(layers)
             for pr in prs:
                 prep = bab.prepare(layers, pr.C, pr.d, pr.lo, pr.hi, omnc.mnc_fn())
-                _, prop = gpu_property(ctx, layers, pr.lo, pr.hi, pr.C, pr.d, prep[6])
+                _, prop = gpu_property(ctx, layers, pr.lo, pr.hi, pr.C, pr.d, prep[6], net=gnet)
                 ctx.set_budget(prop, budget)
                 for _ in range(100000):
                     if ctx.bab_step([prop], max_nodes=1, steps=20)["nodes_bounded"] == 0:
