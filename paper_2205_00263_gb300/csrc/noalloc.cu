@@ -36,6 +36,12 @@ __global__ void k_iota(int* p, int n) {
   if (i < n) p[i] = i;
 }
 
+// The property descriptor travels as a kernel argument and is stored by the
+// device, so no host buffer has to outlive the call.
+__global__ void k_store_prop(PropDev* dst, PropDev pd) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dst = pd;
+}
+
 void set_err(char* buf, size_t len, const char* msg) {
   if (buf && len) {
     std::strncpy(buf, msg, len - 1);
@@ -154,7 +160,8 @@ extern "C" mnbab_status mnbab_deeppoly_fc_noalloc(int32_t n_affine, const int32_
   float* d_B = reinterpret_cast<float*>(base + o_B);
   float* d_part = reinterpret_cast<float*>(base + o_part);
   // the array keeps the previous call's contents: set everything that is read
-  cudaError_t e = cudaMemcpyAsync(d_prop, &pd, sizeof(PropDev), cudaMemcpyHostToDevice, st);
+  k_store_prop<<<1, 1, 0, st>>>(d_prop, pd);
+  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemsetAsync(d_pidx, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_S, 0, std::max(1, off), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_node, 0, M * sizeof(int), st);
