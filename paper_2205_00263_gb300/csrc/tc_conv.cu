@@ -55,6 +55,7 @@ namespace {
 
 constexpr int KC = 32;    // reduction values per staged block
 constexpr int TROWS = 4;  // objective rows per CTA (one warp each)
+constexpr int TC_KMAX = 1024;  // longest reduction (padded to KC) the kernel takes
 
 struct ConvClass {
   int P, K;            // positions and reduction length of the class
@@ -137,10 +138,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const __grid_constant__ 
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * STAGE);  // tma[2], mma[2]
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 4);
-  // reduction table of a K block: source offset (channel plane + tap shift),
-  // tap shifts for the bounds check (dy = dx = -1000: padding of the block)
-  __shared__ int t_delta[2][KC], t_dy[2][KC], t_dx[2][KC];
+  // reduction table of the whole K range, computed once: source offset
+  // (channel plane + tap shift) and tap shifts for the bounds check
+  // (dy = dx = -1000: padding past K)
+  __shared__ int t_delta[TC_KMAX];
+  __shared__ short2 t_dd[TC_KMAX];
   __shared__ int s_fail;
+  __shared__ float s_part[2][TROWS];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rq = warp & 3;         // objective row of this warp (TMEM lane quarter)
@@ -191,36 +195,51 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const __grid_constant__ 
   constexpr uint32_t idesc = tc::idesc_tf32_m128(NP);
 
   const int nk = (c.K + KC - 1) / KC;
+  for (int kidx = tid; kidx < nk * KC; kidx += TC_THREADS) {
+    int delta = 0, dy = -1000, dx = -1000;
+    if (kidx < c.K) {
+      int off;
+      if (dir == 0) {
+        const int kk2 = L.k * L.k;
+        off = (kidx / kk2) * L.hi * L.wi;
+        dy = (kidx / L.k) % L.k;
+        dx = kidx % L.k;
+      } else {
+        const int nab = c.na * c.nb;
+        off = (kidx / nab) * L.ho * L.wo;
+        dy = -((kidx / c.nb) % c.na);
+        dx = -(kidx % c.nb);
+      }
+      delta = off + dy * Wsrc + dx;
+    }
+    t_delta[kidx] = delta;
+    t_dd[kidx] = make_short2((short)dy, (short)dx);
+  }
+  __syncthreads();
+  // implicit im2col: the 16 reduction values of this thread's GEMM row in K
+  // block kb (half kh of the block)
+  auto gather = [&](int kb, float (&v)[16]) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int kk = kb * KC + kh * 16 + u;
+      const short2 dd = t_dd[kk];
+      const int yy = gy + dd.x, xx = gx + dd.y;
+      const bool in_b = pv && yy >= 0 && yy < Hs && xx >= 0 && xx < Wsrc;
+      v[u] = in_b ? __ldg(src + t_delta[kk]) : 0.f;
+    }
+  };
   bool ok = true;
   int last = -1;
+  float vn[16];
+  if (nk > 0) gather(0, vn);
   for (int kb = 0; kb < nk; ++kb) {
     const int st = kb & 1;
     const uint32_t tbar = tma0 + 8 * st, mbar = mma0 + 8 * st;
-    // the reduction table of this block (every thread finished reading the
-    // other table copy before the previous block's MMA barrier)
-    const int k0 = kb * KC, kcn = min(KC, c.K - k0);
-    if (tid < KC) {
-      int delta = 0, dy = -1000, dx = -1000;
-      if (tid < kcn) {
-        const int kidx = k0 + tid;
-        int off;
-        if (dir == 0) {
-          const int kk2 = L.k * L.k;
-          off = (kidx / kk2) * L.hi * L.wi;
-          dy = (kidx / L.k) % L.k;
-          dx = kidx % L.k;
-        } else {
-          const int nab = c.na * c.nb;
-          off = (kidx / nab) * L.ho * L.wo;
-          dy = -((kidx / c.nb) % c.na);
-          dx = -(kidx % c.nb);
-        }
-        delta = off + dy * Wsrc + dx;
-      }
-      t_delta[st][tid] = delta;
-      t_dy[st][tid] = dy;
-      t_dx[st][tid] = dx;
-    }
+    float v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v[u] = vn[u];
+    // the next block's loads are in flight while this block is staged and issued
+    if (kb + 1 < nk) gather(kb + 1, vn);
     if (kb >= 2) {
       // the MMAs of block kb - 2 read this stage: wait for them
       const bool mine = tc::mbar_wait(mbar, (uint32_t)(((kb >> 1) - 1) & 1));
@@ -240,17 +259,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const __grid_constant__ 
       tc::tma_load_3d(tc::smem_u32(b_hi), &tm_hi, 0, kb * (KC / 4), cls, tbar);
       tc::tma_load_3d(tc::smem_u32(b_lo), &tm_lo, 0, kb * (KC / 4), cls, tbar);
     }
-    // implicit im2col: 16 reduction values of this thread's GEMM row, all
-    // loads in flight before the split into hi / lo
     const int r = rq * 32 + lane;
-    float v[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int kk = kh * 16 + u;
-      const int yy = gy + t_dy[st][kk], xx = gx + t_dx[st][kk];
-      const bool in_b = pv && yy >= 0 && yy < Hs && xx >= 0 && xx < Wsrc;
-      v[u] = in_b ? __ldg(src + t_delta[st][kk]) : 0.f;
-    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       uint4 h, l;
@@ -305,16 +314,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const __grid_constant__ 
     }
     __syncthreads();
   }
-  if (ok && kh == 0) {
-    // epilogue: warps 0-3, each its TMEM lane quarter = its objective row
+  if (ok) {
+    // epilogue: every warp reads its TMEM lane quarter (objective row rq); warp
+    // group kh takes the 16-column chunks 16 (2 i + kh).  The inputs of four
+    // outputs are loaded together before any of them is finished.
     float part = 0.f;
     const int y = dir == 0 ? iy : c.y0 + L.s * iy;
     const int x = dir == 0 ? ix : c.x0 + L.s * ix;
     const int plane = dir == 0 ? L.ho * L.wo : L.hi * L.wi;
     const int W2 = dir == 0 ? L.wo : L.wi;
+    const int pj = y * W2 + x;
     const uint32_t trow = tmem + ((uint32_t)(rq * 32) << 16);
-#pragma unroll
-    for (int c0 = 0; c0 < NP; c0 += 16) {
+    const int nrow = pv ? e.row_node[m] : 0;
+    const PropDev* Pp = pv ? epi_prop(e, nrow) : nullptr;
+    for (int c0 = 16 * kh; c0 < NP; c0 += 32) {
       float v[16];
       if (nk > 0) {
         tc::tmem_ld16(trow + (uint32_t)c0, v);
@@ -324,25 +337,37 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const __grid_constant__ 
       }
       if (pv) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int n = c0 + i;
-          if (n < N) {
-            const int j = n * plane + y * W2 + x;
-            float val = v[i];
-            if (dir == 0) val += L.b[n];
-            const float o = epi_apply(e, m, j, val, part);
-            if (out) out[(size_t)m * ld_out + j] = o;
+        for (int g = 0; g < 16; g += 4) {
+          EpiIn in[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int n = c0 + g + i;
+            if (n < N) epi_load(e, nrow, Pp, m, n * plane + pj, in[i]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int n = c0 + g + i;
+            if (n < N) {
+              const int j = n * plane + pj;
+              float val = v[g + i];
+              if (dir == 0) val += L.b[n];
+              const float o = epi_finish(e, m, j, val, in[i], part);
+              if (out) out[(size_t)m * ld_out + j] = o;
+            }
           }
         }
       }
     }
     if (has_part) {
       for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (lane == 0 && rowv) e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = part;
+      if (lane == 0) s_part[kh][rq] = part;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  // a row's offset partial: the two warp groups' sums, in that order
+  if (ok && has_part && kh == 0 && lane == 0 && rowv)
+    e.part[(size_t)m * e.nslot + e.slot_base + blockIdx.x] = s_part[0][rq] + s_part[1][rq];
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
@@ -381,7 +406,7 @@ size_t tc_conv_floats(const LayerDev& L) {
     int K = 0;
     for (int cl = 0; cl < ncls; ++cl) K = std::max(K, conv_class(L, dir, cl).K);
     const int Kp = std::max(KC, (K + KC - 1) / KC * KC);
-    if (N < 8 || NP > 64) continue;
+    if (N < 8 || NP > 64 || Kp > TC_KMAX) continue;
     tot += 2 * (size_t)ncls * Kp * NP;
   }
   return tot;
@@ -404,7 +429,8 @@ TcConv* tc_conv_create(const LayerDev& L, float* buf, cudaStream_t st) {
       pmax = std::max(pmax, c.P);
     }
     const int Kp = std::max(KC, (K + KC - 1) / KC * KC);
-    if (N < 8 || NP > 64) continue;  // too few or too many channels for these tiles
+    // too few or too many channels for these tiles, or a reduction longer than the table
+    if (N < 8 || NP > 64 || Kp > TC_KMAX) continue;
     float* hi = buf + at;
     float* lo = hi + (size_t)ncls * Kp * NP;
     at += 2 * (size_t)ncls * Kp * NP;
