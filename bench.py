@@ -192,12 +192,39 @@ CONTRACTIONS = ("backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm", 
                 "forward_conv_tc")
 
 
+def measure_tf32(n=8192, reps=5):
+    """Dense TF32 rate of cuBLAS on this GPU (torch.matmul of two n x n FP32
+    matrices with TF32 allowed), best of `reps` after a warm-up, CUDA events."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        c = a @ b
+        best = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c = a @ b
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del a, b, c
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def tf32x3_peak(peaks, src):
-    """3xTF32 tensor peak: a measured dense TF32 rate / 3 when the peaks file
-    has one, else the measured dense BF16 burst rate x the nominal TF32:BF16
-    ratio 1/2, / 3 (three TF32 products per FP32-accurate product)."""
+    """3xTF32 tensor peak: a measured dense TF32 rate / 3 when there is one
+    (bench.py measures cuBLAS TF32 in the run), else the measured dense BF16
+    burst rate x the nominal TF32:BF16 ratio 1/2, / 3 (three TF32 products per
+    FP32-accurate product)."""
     if "tf32_tflops" in peaks:
-        return peaks["tf32_tflops"] / 3.0, f"{src}: MEASURED_PEAKS tf32_tflops / 3"
+        return peaks["tf32_tflops"] / 3.0, peaks.get("tf32_source", f"{src}: tf32_tflops") + " / 3"
     return (peaks["bf16_tflops"] / 2.0 / 3.0,
             f"derived from {src} bf16_tflops {peaks['bf16_tflops']}: x 1/2 (nominal TF32:BF16) "
             f"/ 3 (3xTF32 split products)")
@@ -497,6 +524,11 @@ def run_ours(args):
         finally:
             sctx.close()
     peaks, src = load_peaks()
+    if "tf32_tflops" not in peaks:
+        tf = measure_tf32()
+        peaks["tf32_tflops"] = tf
+        peaks["tf32_source"] = (f"measured in this run: cuBLAS TF32 GEMM 8192^3, best of 5 "
+                                f"({tf:.1f} TFLOP/s)")
     roof = roofline(stats, peaks, src, kernels_sha(), layers=layers)
     mnc_big = None
     if world == 1 and args.mnc_big_props > 0:
@@ -1017,9 +1049,10 @@ def run_gemm_tc(args):
                       "tflops": g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] else None}
         ctx.close()
     peaks, src = load_peaks()
-    tf32 = peaks["bf16_tflops"] / 2.0
-    out["peak_3xtf32_tflops"] = tf32 / 3.0
-    out["peak_source"] = f"{src} bf16_tflops x 1/2 (nominal TF32/BF16 ratio) / 3 (three MMAs)"
+    if "tf32_tflops" not in peaks:
+        peaks["tf32_tflops"] = measure_tf32()
+        peaks["tf32_source"] = "measured in this run: cuBLAS TF32 GEMM 8192^3, best of 5"
+    out["peak_3xtf32_tflops"], out["peak_source"] = tf32x3_peak(peaks, src)
     t = out["tcgen05_3xtf32"]["tflops"]
     out["frac_of_3xtf32"] = t / out["peak_3xtf32_tflops"] if t else None
     out["workload"] = ("conv_big_32 root bounding, 4 properties: FC back-substitution GEMMs "

@@ -1708,19 +1708,59 @@ __device__ __forceinline__ int layer_of(const NetDev& net, int f) {
 }
 
 // gamma^T P and gamma^T Phat per neuron (CSR by neuron), gamma^T p per row.
-__global__ void k_gamma_proj(int M, const int* row_node, PoolDev pool, const PropDev* props,
-                             NetDev net, float* GP, float* GPh) {
+// A CTA serves one row: its node and its property's per-layer CSR pointers are
+// looked up once into shared memory; a thread takes one neuron and keeps eight
+// of its entries' loads in flight at a time (the sums keep entry order).
+struct MncCsr {
+  const int* cptr;
+  const int* ce;
+  const float* cP;
+  const float* cPh;
+  int goff, e;
+};
+
+__global__ void k_gamma_proj(int M, const int* __restrict__ row_node, PoolDev pool,
+                             const PropDev* __restrict__ props, NetDev net, float* __restrict__ GP,
+                             float* __restrict__ GPh) {
   const int m = blockIdx.y;
+  __shared__ int s_n;
+  __shared__ MncCsr s_mc[MNBAB_MAXR + 1];
+  if (threadIdx.x == 0) s_n = row_node[m];
+  __syncthreads();
+  const int n = s_n;
+  if (threadIdx.x >= 1 && threadIdx.x <= net.R) {
+    const MncDev& mc = props[pool.prop[n]].mnc[threadIdx.x];
+    s_mc[threadIdx.x] = MncCsr{mc.cptr, mc.ce, mc.cP, mc.cPh, mc.goff, mc.e};
+  }
+  __syncthreads();
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= net.SD) return;
-  const int n = row_node[m];
   const int i = layer_of(net, f);
-  const int j = f - net.off[i];
-  const MncDev& mc = props[pool.prop[n]].mnc[i];
+  const MncCsr& mc = s_mc[i];
   float gp = 0.f, gph = 0.f;
   if (mc.e > 0) {
+    const int j = f - net.off[i];
     const float* gam = pool.GAM + (size_t)n * pool.EC + mc.goff;
-    for (int q = mc.cptr[j]; q < mc.cptr[j + 1]; ++q) {
+    const int q1 = mc.cptr[j + 1];
+    int q = mc.cptr[j];
+    for (; q + 8 <= q1; q += 8) {
+      int ce[8];
+      float g[8], cp[8], cph[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        ce[k] = mc.ce[q + k];
+        cp[k] = mc.cP[q + k];
+        cph[k] = mc.cPh[q + k];
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) g[k] = gam[ce[k]];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        gp = fmaf(g[k], cp[k], gp);
+        gph = fmaf(g[k], cph[k], gph);
+      }
+    }
+    for (; q < q1; ++q) {
       const float g = gam[mc.ce[q]];
       gp = fmaf(g, mc.cP[q], gp);
       gph = fmaf(g, mc.cPh[q], gph);
@@ -1730,18 +1770,37 @@ __global__ void k_gamma_proj(int M, const int* row_node, PoolDev pool, const Pro
   GPh[(size_t)m * net.SD + f] = gph;
 }
 
-__global__ void k_gamma_p(int M, const int* row_node, PoolDev pool, const PropDev* props,
-                          NetDev net, float* gp0) {
+// gamma^T p of one row: GP_THREADS threads, four independent partial sums a
+// thread (fixed order, so the value does not depend on the launch)
+constexpr int GP_THREADS = 512;
+
+__global__ void __launch_bounds__(GP_THREADS) k_gamma_p(int M, const int* row_node, PoolDev pool,
+                                                        const PropDev* props, NetDev net,
+                                                        float* gp0) {
   const int m = blockIdx.x;
   const int n = row_node[m];
   const PropDev& P = props[pool.prop[n]];
-  float acc = 0.f;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
   for (int i = 1; i <= net.R; ++i) {
     const MncDev& mc = P.mnc[i];
     const float* gam = pool.GAM + (size_t)n * pool.EC + mc.goff;
-    for (int e = threadIdx.x; e < mc.e; e += blockDim.x) acc = fmaf(gam[e], mc.p[e], acc);
+    const int e1 = mc.e;
+    int e = threadIdx.x;
+    for (; e + 3 * GP_THREADS < e1; e += 4 * GP_THREADS) {
+      float g[4], p[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        g[u] = gam[e + u * GP_THREADS];
+        p[u] = mc.p[e + u * GP_THREADS];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fmaf(g[u], p[u], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u, e += GP_THREADS)
+      if (e < e1) acc[u] = fmaf(gam[e], mc.p[e], acc[u]);
   }
-  const float tot = block_sum(acc);
+  const float tot = block_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
   if (threadIdx.x == 0) gp0[m] = tot;
 }
 
@@ -1750,39 +1809,75 @@ void launch_gamma_proj(int M, const int* row_node, PoolDev pool, const PropDev* 
   if (M <= 0) return;
   dim3 grid((net.SD + 255) / 256, M);
   k_gamma_proj<<<grid, 256, 0, st>>>(M, row_node, pool, props, net, GP, GPh);
-  k_gamma_p<<<M, 256, 0, st>>>(M, row_node, pool, props, net, gp0);
+  k_gamma_p<<<M, GP_THREADS, 0, st>>>(M, row_node, pool, props, net, gp0);
 }
 
-// d lb / d gamma_e = sum_k P_ek (d lb / d a')_idx + Phat_ek (d lb / d ahat)_idx - p_e
-__global__ void k_gamma_grad(int M, const int* row_node, PoolDev pool, const PropDev* props,
-                             NetDev net, const float* Gz, const float* Hz, float* GG) {
+// d lb / d gamma_e = sum_k P_ek (d lb / d a')_idx + Phat_ek (d lb / d ahat)_idx - p_e.
+constexpr int GAMMA_NPT = 4;
+// A CTA serves one row (node and property looked up once); each thread takes
+// GAMMA_NPT constraint rows, loading every row's entries before the gathers.
+__global__ void k_gamma_grad(int M, const int* __restrict__ row_node, PoolDev pool,
+                             const PropDev* __restrict__ props, NetDev net,
+                             const float* __restrict__ Gz, const float* __restrict__ Hz,
+                             float* __restrict__ GG) {
   const int m = blockIdx.y;
-  const int ef = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = row_node[m];
-  const PropDev& P = props[pool.prop[n]];
-  if (ef >= P.E) return;
-  int i = 0;
-  for (int t = 1; t <= net.R; ++t)
-    if (P.mnc[t].e > 0 && ef >= P.mnc[t].goff && ef < P.mnc[t].goff + P.mnc[t].e) i = t;
-  if (i == 0) return;
-  const MncDev& mc = P.mnc[i];
-  const int e = ef - mc.goff;
-  const float* gz = Gz + (size_t)m * net.SD + net.off[i];
-  const float* hz = Hz + (size_t)m * net.SD + net.off[i];
-  float g = -mc.p[e];
-  for (int k = 0; k < mc.k; ++k) {
-    const int j = mc.idx[(size_t)e * mc.k + k];
-    g = fmaf(mc.P[(size_t)e * mc.k + k], gz[j], g);
-    g = fmaf(mc.Ph[(size_t)e * mc.k + k], hz[j], g);
+  __shared__ const PropDev* s_P;
+  __shared__ int s_goff[MNBAB_MAXR + 1], s_e[MNBAB_MAXR + 1];
+  if (threadIdx.x == 0) s_P = props + pool.prop[row_node[m]];
+  __syncthreads();
+  const PropDev& P = *s_P;
+  if (threadIdx.x <= net.R) {
+    s_goff[threadIdx.x] = threadIdx.x >= 1 ? P.mnc[threadIdx.x].goff : 0;
+    s_e[threadIdx.x] = threadIdx.x >= 1 ? P.mnc[threadIdx.x].e : 0;
   }
-  GG[(size_t)m * pool.EC + ef] = g;
+  __syncthreads();
+  const int E = P.E;
+  const int e0 = blockIdx.x * (blockDim.x * GAMMA_NPT) + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < GAMMA_NPT; ++u) {
+    const int ef = e0 + u * blockDim.x;
+    if (ef >= E) break;
+    int i = 0;
+    for (int t = 1; t <= net.R; ++t)
+      if (s_e[t] > 0 && ef >= s_goff[t] && ef < s_goff[t] + s_e[t]) i = t;
+    if (i == 0) continue;
+    const MncDev& mc = P.mnc[i];
+    const int e = ef - s_goff[i];
+    const float* gz = Gz + (size_t)m * net.SD + net.off[i];
+    const float* hz = Hz + (size_t)m * net.SD + net.off[i];
+    const int k = mc.k;
+    float g = -mc.p[e];
+    if (k == 3) {
+      const int j0 = mc.idx[(size_t)e * 3], j1 = mc.idx[(size_t)e * 3 + 1],
+                j2 = mc.idx[(size_t)e * 3 + 2];
+      const float p0 = mc.P[(size_t)e * 3], p1 = mc.P[(size_t)e * 3 + 1],
+                  p2 = mc.P[(size_t)e * 3 + 2];
+      const float h0 = mc.Ph[(size_t)e * 3], h1 = mc.Ph[(size_t)e * 3 + 1],
+                  h2 = mc.Ph[(size_t)e * 3 + 2];
+      const float z0 = gz[j0], z1 = gz[j1], z2 = gz[j2];
+      const float y0 = hz[j0], y1 = hz[j1], y2 = hz[j2];
+      g = fmaf(p0, z0, g);
+      g = fmaf(h0, y0, g);
+      g = fmaf(p1, z1, g);
+      g = fmaf(h1, y1, g);
+      g = fmaf(p2, z2, g);
+      g = fmaf(h2, y2, g);
+    } else {
+      for (int kk = 0; kk < k; ++kk) {
+        const int j = mc.idx[(size_t)e * k + kk];
+        g = fmaf(mc.P[(size_t)e * k + kk], gz[j], g);
+        g = fmaf(mc.Ph[(size_t)e * k + kk], hz[j], g);
+      }
+    }
+    GG[(size_t)m * pool.EC + ef] = g;
+  }
 }
 
 void launch_gamma_grad(int M, const int* row_node, PoolDev pool, const PropDev* props,
                        const NetDev& net, const float* Gz, const float* Hz, float* GG,
                        cudaStream_t st) {
   if (M <= 0 || pool.EC <= 0) return;
-  dim3 grid((pool.EC + 255) / 256, M);
+  dim3 grid((pool.EC + 256 * GAMMA_NPT - 1) / (256 * GAMMA_NPT), M);
   k_gamma_grad<<<grid, 256, 0, st>>>(M, row_node, pool, props, net, Gz, Hz, GG);
 }
 
@@ -1817,18 +1912,27 @@ __global__ void k_grad_max(int SD, int EC, const int* row_node, const PoolDev po
   }
 }
 
-__global__ void k_adam(int M, const int* row_node, PoolDev pool, const PropDev* props, int SD,
-                       const float* GA, const float* GB, const float* GG, const float* gmax,
-                       float floor, float lr_a, float lr_b, float lr_g, float b1, float b2,
-                       float eps_abs, float eps_rel, float bc1, float bc2) {
+// The alpha of a neuron that is not unstable and unsplit, and the beta of an
+// unsplit one, have a zero gradient at every step of an optimisation (its
+// bounds and splits are fixed), and their moments start at zero: their
+// updates are identities and are skipped.  gmax is read only when the
+// dead-zone or the gradient-scaled eps is on (use_gmax).
+__global__ void k_adam(int M, const int* __restrict__ row_node, PoolDev pool,
+                       const PropDev* __restrict__ props, int SD, const float* __restrict__ GA,
+                       const float* __restrict__ GB, const float* __restrict__ GG,
+                       const float* __restrict__ gmax, int use_gmax, float floor, float lr_a,
+                       float lr_b, float lr_g, float b1, float b2, float eps_abs, float eps_rel,
+                       float bc1, float bc2) {
   const int m = blockIdx.y;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = row_node[m];
-  const float thr = floor * gmax[m];
-  const float eps = fmaxf(eps_abs, eps_rel * gmax[m]);
+  const float gm = use_gmax ? gmax[m] : 0.f;
+  const float thr = floor * gm;
+  const float eps = fmaxf(eps_abs, eps_rel * gm);
   auto dz = [thr](float g) { return fabsf(g) <= thr ? 0.f : g; };
   if (idx < SD) {
     const size_t q = (size_t)n * SD + idx;
+    if (pool.S[q] != 0 || !(pool.L[q] < 0.f) || !(pool.U[q] > 0.f)) return;
     float th = pool.ALPHA[q], mo = pool.MA[q], ve = pool.VA[q];
     adam1(th, mo, ve, dz(GA[(size_t)m * SD + idx]), lr_a, b1, b2, eps, bc1, bc2);
     pool.ALPHA[q] = fminf(fmaxf(th, 0.f), 1.f);
@@ -1836,6 +1940,7 @@ __global__ void k_adam(int M, const int* row_node, PoolDev pool, const PropDev* 
   } else if (idx < 2 * SD) {
     const int f = idx - SD;
     const size_t q = (size_t)n * SD + f;
+    if (pool.S[q] == 0) return;
     float th = pool.BETA[q], mo = pool.MB[q], ve = pool.VB[q];
     adam1(th, mo, ve, dz(GB[(size_t)m * SD + f]), lr_b, b1, b2, eps, bc1, bc2);
     pool.BETA[q] = fmaxf(th, 0.f);
@@ -1856,11 +1961,13 @@ void launch_adam(int M, const int* row_node, PoolDev pool, const PropDev* props,
                  float lr_a, float lr_b, float lr_g, float b1, float b2, float eps, float eps_rel,
                  float bc1, float bc2, cudaStream_t st) {
   if (M <= 0) return;
-  k_grad_max<<<M, 256, 0, st>>>(SD, pool.EC, row_node, pool, props, GA, GB, GG, gmax);
+  const int use_gmax = (floor != 0.f || eps_rel != 0.f) ? 1 : 0;
+  if (use_gmax)
+    k_grad_max<<<M, 256, 0, st>>>(SD, pool.EC, row_node, pool, props, GA, GB, GG, gmax);
   const int tot = 2 * SD + pool.EC;
   dim3 grid((tot + 255) / 256, M);
-  k_adam<<<grid, 256, 0, st>>>(M, row_node, pool, props, SD, GA, GB, GG, gmax, floor, lr_a, lr_b,
-                               lr_g, b1, b2, eps, eps_rel, bc1, bc2);
+  k_adam<<<grid, 256, 0, st>>>(M, row_node, pool, props, SD, GA, GB, GG, gmax, use_gmax, floor,
+                               lr_a, lr_b, lr_g, b1, b2, eps, eps_rel, bc1, bc2);
 }
 
 __global__ void k_zero_adam(const int* row_node, PoolDev pool) {
