@@ -75,6 +75,11 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=None,
                     help="requests of the serving stream (default 24 in the main line, 400 with --serving)")
     ap.add_argument("--serve-rate", type=float, default=4.0)
+    ap.add_argument("--mnc-big-only", action="store_true",
+                    help="run only the conv_big_32 arm with multi-neuron constraints")
+    ap.add_argument("--mnc-big-capacity", type=int, default=4096,
+                    help="node slots of the conv_big_32 arm's context")
+    ap.add_argument("--mnc-big-steps", type=int, default=3)
     ap.add_argument("--mnc-big-props", type=int, default=32,
                     help="properties of the conv-big arm with multi-neuron constraints (0 skips it)")
     ap.add_argument("--mnc-big-groups", type=int, default=2000,
@@ -287,7 +292,9 @@ def roofline(stats, peaks, src, kernels_hash, layers=None, adam_steps=ADAM_STEPS
             t = json.load(f)
         # DRAM bytes per row from one capture, scaled by the rows of an average
         # launch (its algorithmic flops over the flops of one row)
-        if (t.get("kernels_sha") == kernels_hash and name in t.get("dram_bytes_per_row", {})
+        sha = t.get("kernels_sha", {})
+        if (isinstance(sha, dict) and sha.get(name) == kernels_sha(name)
+                and name in t.get("dram_bytes_per_row", {})
                 and name in t.get("flops_per_row", {})):
             rows = st["flops"] / max(1, st["launches"]) / t["flops_per_row"][name]
             r["traffic"] = t["dram_bytes_per_row"][name] * rows
@@ -296,11 +303,20 @@ def roofline(stats, peaks, src, kernels_hash, layers=None, adam_steps=ADAM_STEPS
     return r
 
 
-def kernels_sha():
+# sources a kernel class's code lives in (the traffic record of a class stays
+# valid while these files are unchanged); other classes hash every source
+KERNEL_SOURCES = {
+    "opt_fused_chain": ("fused.cu", "epilogue.cuh", "mnbab_internal.h"),
+    "backsub_conv_tc": ("tc_conv.cu", "tc_common.cuh", "epilogue.cuh", "mnbab_internal.h"),
+    "forward_conv_tc": ("tc_conv.cu", "tc_common.cuh", "epilogue.cuh", "mnbab_internal.h"),
+}
+
+
+def kernels_sha(kernel=None):
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2205_00263_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(KERNEL_SOURCES.get(kernel) or os.listdir(d)):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -532,7 +548,8 @@ def run_ours(args):
     roof = roofline(stats, peaks, src, kernels_sha(), layers=layers)
     mnc_big = None
     if world == 1 and args.mnc_big_props > 0:
-        mnc_big = mnc_big_run(local, stream, args.mnc_big_props, 3, args.mnc_big_groups, peaks,
+        mnc_big = mnc_big_run(local, stream, args.mnc_big_props, args.mnc_big_steps,
+                              args.mnc_big_groups, peaks,
                               src, kernels_sha())
     verdicts = None
     if world == 1 and args.verdicts:
@@ -758,13 +775,14 @@ MNC_BIG = ("conv_big_32: 3x32x32 -> conv32 3x3 -> conv32 4x4 s2 -> conv64 3x3 ->
            "FC512 -> FC512 -> FC10, k=3 multi-neuron constraints (library generator)")
 
 
-def mnc_big_run(local, stream, n_props, steps, max_groups, peaks, src, ksha):
+def mnc_big_run(local, stream, n_props, steps, max_groups, peaks, src, ksha, capacity=4096,
+                batch=256):
     import torch
     from paper_2205_00263_gb300 import Context
     layers2 = synth.make_network(2)
     props = synth.make_properties(2, layers2, n=n_props, eps=synth.load_eps(2), start=0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ctx = Context(device=local, stream=stream.cuda_stream, node_capacity=4096,
+    ctx = Context(device=local, stream=stream.cuda_stream, node_capacity=capacity,
                   max_mnc_rows=VERDICT_MNC_ROWS, hbm_budget_bytes=64 << 30)
     try:
         net = ctx.load_network(layers2)
@@ -777,9 +795,9 @@ def mnc_big_run(local, stream, n_props, steps, max_groups, peaks, src, ksha):
             ps.append(p)
         torch.cuda.synchronize()
         gen_s = time.perf_counter() - t0
-        ctx.bab_step(ps, max_nodes=256, steps=ADAM_STEPS)   # warm-up (roots)
+        ctx.bab_step(ps, max_nodes=batch, steps=ADAM_STEPS)   # warm-up (roots)
         ctx.profile(True)
-        ctx.bab_step(ps, max_nodes=256, steps=ADAM_STEPS)   # every class timed: breakdown
+        ctx.bab_step(ps, max_nodes=batch, steps=ADAM_STEPS)   # every class timed: breakdown
         torch.cuda.synchronize()
         breakdown, _ = ctx.profile_read()
         dom_name = dominant(breakdown)[0]
@@ -793,7 +811,7 @@ def mnc_big_run(local, stream, n_props, steps, max_groups, peaks, src, ksha):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = ctx.bab_step(ps, max_nodes=256, steps=ADAM_STEPS)
+            st = ctx.bab_step(ps, max_nodes=batch, steps=ADAM_STEPS)
             e1.record(stream)
             e1.synchronize()
             ms += e0.elapsed_time(e1)
@@ -814,7 +832,7 @@ def mnc_big_run(local, stream, n_props, steps, max_groups, peaks, src, ksha):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = ctx.bab_step(ps, max_nodes=256, steps=ADAM_STEPS)
+            st = ctx.bab_step(ps, max_nodes=batch, steps=ADAM_STEPS)
             e1.record(stream)
             e1.synchronize()
             t_ms += e0.elapsed_time(e1)
@@ -836,6 +854,7 @@ def mnc_big_run(local, stream, n_props, steps, max_groups, peaks, src, ksha):
     top = sorted(((k, v["ms"]) for k, v in breakdown.items()
                   if v["ms"] and not k.startswith(("phase_", "step_"))), key=lambda kv: -kv[1])
     return {"workload": MNC_BIG, "properties": n_props, "max_groups_per_layer": max_groups,
+            "subproblems_per_step": batch, "node_capacity": capacity,
             "mnc_rows_per_property": sum(rows) / len(rows),
             "generate_s_per_property": gen_s / n_props,
             "value": nodes / (ms * 1e-3) if ms else None, "unit": "nodes/s",
@@ -1060,6 +1079,20 @@ def run_gemm_tc(args):
     print(json.dumps(out), flush=True)
 
 
+def run_mnc_big(args):
+    """The conv_big_32 arm alone (multi-neuron constraints from the library's
+    generator, alpha / beta / gamma, ACS), e.g. for profiling on a small pool."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    stream = torch.cuda.Stream()
+    peaks, src = load_peaks()
+    cap = args.mnc_big_capacity
+    out = mnc_big_run(0, stream, args.mnc_big_props, args.mnc_big_steps, args.mnc_big_groups,
+                      peaks, src, kernels_sha(), capacity=cap, batch=min(256, cap // 4))
+    print(json.dumps({"conv_big_mnc": out}), flush=True)
+
+
 def run_serving(args):
     """Config 4: Poisson stream (rate 4/s, 400 requests, seed 4) over the
     calibrated networks of configs 1-3, 60 s timeout, continuous batching."""
@@ -1102,5 +1135,7 @@ if __name__ == "__main__":
         run_gemm_tc(a)
     elif a.serving:
         run_serving(a)
+    elif a.mnc_big_only:
+        run_mnc_big(a)
     else:
         run_ours(a)
