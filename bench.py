@@ -194,7 +194,7 @@ def dominant(stats):
 
 CONTRACTIONS = ("backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm", "forward_conv",
                 "opt_fused_chain", "backsub_conv_window", "backsub_rows_fused", "backsub_conv_tc",
-                "forward_conv_tc")
+                "forward_conv_tc", "opt_fused_chain_tc")
 
 
 def measure_tf32(n=8192, reps=5):
@@ -267,7 +267,7 @@ def roofline(stats, peaks, src, kernels_hash, layers=None, adam_steps=ADAM_STEPS
         simt = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         r["simt_fp32"] = {"peak": simt, "frac": ach_flops / simt,
                           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
-        if name == "opt_fused_chain" and layers is not None:
+        if name in ("opt_fused_chain", "opt_fused_chain_tc") and layers is not None:
             # the library counts (steps + 1) back-substitution sweeps and steps
             # adjoint passes (one forward pass of the relaxed network each);
             # the survey's count is a sweep plus a two-sweep adjoint per step
@@ -307,6 +307,7 @@ def roofline(stats, peaks, src, kernels_hash, layers=None, adam_steps=ADAM_STEPS
 # valid while these files are unchanged); other classes hash every source
 KERNEL_SOURCES = {
     "opt_fused_chain": ("fused.cu", "epilogue.cuh", "mnbab_internal.h"),
+    "opt_fused_chain_tc": ("fused.cu", "epilogue.cuh", "mnbab_internal.h", "tc_common.cuh"),
     "backsub_conv_tc": ("tc_conv.cu", "tc_common.cuh", "epilogue.cuh", "mnbab_internal.h"),
     "forward_conv_tc": ("tc_conv.cu", "tc_common.cuh", "epilogue.cuh", "mnbab_internal.h"),
 }

@@ -25,6 +25,7 @@
 #include "epilogue.cuh"
 #include "mnbab.h"
 #include "mnbab_internal.h"
+#include "tc_common.cuh"
 
 namespace mnbab {
 
@@ -379,26 +380,215 @@ __device__ void f_conv_fwd(const LayerDev& L, const float* g, float* h, const fl
 }
 
 
+// ---- transposed convolution of one conv layer on the tensor cores --------------
+// The back-substitution step through conv layer T (Sec. 3.1: the affine step
+// through a convolution is its transposed convolution) as one small GEMM per
+// sweep plus a gather:
+//   Z[(c, kh, kw), (oy, ox)] = sum over o of W[o, c, kh, kw] Lambda[o, oy, ox]
+//   nxt[c, y, x] = sum over taps with y = oy s - p + kh, x = ox s - p + kw of Z.
+// A = W viewed as [ci k k][co] stays in tensor memory for the whole launch
+// (TF32 hi and lo parts, written once).  The layer's back-substitution weight
+// region of shared memory (which the SIMT step no longer needs) holds, per
+// sweep, first B = Lambda as [ho wo][co] (hi and lo) and then Z: D = Z
+// accumulates in tensor memory with 3xTF32 split products (lo.hi + hi.lo +
+// hi.hi, FP32 accumulation), is copied to that region once the MMAs are done
+// and gathered into nxt in a fixed tap order.
+constexpr int FTC_TAPS = 4;  // taps per dimension and stride class (k <= 4 s)
+
+struct FusedTc {
+  int t = 0;           // the layer (0: none)
+  int RK = 0;          // rows of A: ci k k
+  int P = 0;           // output positions ho wo
+  int Mt = 0, Kp = 0, Np = 0;  // 128-row tiles, co padded to 8, P padded to 16
+  int zs = 0;          // row stride of Z in shared memory (odd: no bank conflicts)
+  int dcol = 0;        // first tensor-memory column of D
+  uint32_t ncols = 0;  // tensor-memory columns allocated
+};
+
+// shared-memory floats of layer t's first weight region: the staged Wb, or
+// for the tensor-core layer its B tile (hi and lo) and later its Z
+__host__ __device__ inline int ftc_wb_region(const LayerDev& L, int t, const FusedTc& ft) {
+  const int wb = f_wb_floats(L);
+  if (t != ft.t) return wb;
+  const int z = (ft.RK * ft.zs + 3) / 4 * 4, b = 2 * ft.Np * ft.Kp;
+  const int m = z > b ? z : b;
+  return wb > m ? wb : m;
+}
+
+// A (hi and lo) into tensor memory: warp w writes lanes 32 (w mod 4) .. + 31
+// of 8-column chunks; called by every thread
+__device__ void ftc_load_a(const FusedTc& ft, const LayerDev& L, uint32_t tmem) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3, g = warp >> 2;
+  const int nch = ft.Kp / 8, ntask = ft.Mt * 2 * nch;
+  for (int task = g; task < ntask; task += FT / 128) {
+    const int i = task / (2 * nch), h = (task / nch) & 1, cc = task % nch;
+    const int r = i * 128 + q * 32 + lane;
+    uint32_t v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int o = cc * 8 + j;
+      const float w = (r < ft.RK && o < L.co) ? __ldg(L.W + (size_t)o * ft.RK + r) : 0.f;
+      const uint32_t hi = tc::to_tf32(w);
+      v[j] = h == 0 ? hi : tc::to_tf32(w - __uint_as_float(hi));
+    }
+    tc::tmem_st8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(i * 2 * ft.Kp + h * ft.Kp + cc * 8),
+                 v);
+  }
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// cur [co][ho][wo] -> nxt [ci][hi][wi]; the B tile and then Z in the region
+// `Z` of shared memory.  Returns false (the same in every thread) when the MMAs
+// did not complete within the bounded wait; the error flag is then set.
+__device__ bool ftc_back(const FusedTc& ft, const LayerDev& L, const float* cur, float* nxt,
+                         float* Z, uint32_t tmem, uint32_t bar, uint32_t& phase, int* err) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // B [Np][Kp] in the no-swizzle K-major canonical layout: core matrices of 8
+  // positions x 4 channels, 128 B apart along K, Kp / 4 x 128 B apart along N
+  const uint32_t sbo = (uint32_t)(ft.Kp / 4) * 128u;
+  unsigned char* bhi = reinterpret_cast<unsigned char*>(Z);
+  unsigned char* blo = bhi + (size_t)ft.Np * ft.Kp * 4;
+  for (int o = warp; o < ft.Kp; o += FT / 32)
+    for (int n = lane; n < ft.Np; n += 32) {
+      const float v = (o < L.co && n < ft.P) ? cur[o * ft.P + n] : 0.f;
+      const uint32_t h = tc::to_tf32(v);
+      const uint32_t l = tc::to_tf32(v - __uint_as_float(h));
+      const uint32_t off = (uint32_t)(n >> 3) * sbo + (uint32_t)(o >> 2) * 128u + (n & 7) * 16u +
+                           (o & 3) * 4u;
+      *reinterpret_cast<uint32_t*>(bhi + off) = h;
+      *reinterpret_cast<uint32_t*>(blo + off) = l;
+    }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t idesc = tc::idesc_tf32_m128(ft.Np);
+    const uint32_t bh = tc::smem_u32(bhi), bl = tc::smem_u32(blo);
+    for (int i = 0; i < ft.Mt; ++i) {
+      const uint32_t d = tmem + (uint32_t)(ft.dcol + i * ft.Np);
+      for (int ks = 0; ks < ft.Kp / 8; ++ks) {
+        const uint32_t ah = tmem + (uint32_t)(i * 2 * ft.Kp + ks * 8);
+        const uint32_t bo = (uint32_t)ks * 256u;
+        tc::mma_tf32_tmem_a(d, ah + (uint32_t)ft.Kp, tc::smem_desc(bh + bo, 128, sbo), idesc,
+                            ks > 0 ? 1u : 0u);
+        tc::mma_tf32_tmem_a(d, ah, tc::smem_desc(bl + bo, 128, sbo), idesc, 1u);
+        tc::mma_tf32_tmem_a(d, ah, tc::smem_desc(bh + bo, 128, sbo), idesc, 1u);
+      }
+    }
+    tc::mma_commit(bar);
+  }
+  // every warp waits for the MMAs itself, then copies its lane quarter of D
+  // (16-column chunks split over the four warps of a quarter) to Z
+  const bool mine = __all_sync(0xffffffffu, tc::mbar_wait(bar, phase));
+  if (mine) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int q = warp & 3, g = warp >> 2, nc = ft.Np / 16;
+    for (int task = g; task < ft.Mt * nc; task += FT / 128) {
+      const int i = task / nc, c = task % nc;
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ft.dcol + i * ft.Np + c * 16), v);
+      const int r = i * 128 + q * 32 + lane;
+      if (r < ft.RK) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c * 16 + j < ft.P) Z[r * ft.zs + c * 16 + j] = v[j];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  if (!__syncthreads_and(mine)) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, 1);
+      tc::mbar_wait(bar, phase);  // one more bounded wait before the memory is released
+    }
+    return false;
+  }
+  phase ^= 1u;
+  // gather: one item per (channel, input row, column residue mod s); its
+  // columns share the row taps (kh, oy) and the column taps kw with ox = base + i
+  // for the i-th column of the residue class.  Taps are summed in (kh, kw) order.
+  const int S = L.s, HW = L.hi * L.wi, kk = L.k * L.k;
+  const int items = L.ci * L.hi * S;
+  for (int it = threadIdx.x; it < items; it += FT) {
+    const int rx = it % S, y = (it / S) % L.hi, c = it / (S * L.hi);
+    // row taps kh = kh0 + a s (valid: inside the kernel, oy in range) and
+    // column taps kw = kw0 + b s
+    const int kh0 = (y + L.p) % S, kw0 = (rx + L.p) % S;
+    int zrow[FTC_TAPS], kwz[FTC_TAPS], base[FTC_TAPS];
+    bool rv[FTC_TAPS], cv[FTC_TAPS];
+#pragma unroll
+    for (int a = 0; a < FTC_TAPS; ++a) {
+      const int kh = kh0 + a * S, ty = y + L.p - kh;
+      rv[a] = kh < L.k && ty >= 0 && ty / S < L.ho;
+      zrow[a] = (c * kk + kh * L.k) * ft.zs + (rv[a] ? (ty / S) * L.wo : 0);
+      const int kw = kw0 + a * S;
+      cv[a] = kw < L.k;
+      kwz[a] = kw * ft.zs;
+      base[a] = (rx + L.p - kw) / S;  // exact: rx + p - kw is a multiple of s
+    }
+    float* out = nxt + c * HW + y * L.wi;
+    for (int x = rx, i = 0; x < L.wi; x += S, ++i) {
+      float acc = 0.f;
+#pragma unroll
+      for (int a = 0; a < FTC_TAPS; ++a) {
+#pragma unroll
+        for (int b = 0; b < FTC_TAPS; ++b) {
+          const int ox = base[b] + i;
+          if (rv[a] && cv[b] && ox >= 0 && ox < L.wo) acc += Z[zrow[a] + kwz[b] + ox];
+        }
+      }
+      out[x] = acc;
+    }
+  }
+  return true;
+}
+
 }  // namespace
 
 // two CTAs per SM: at most 64 registers a thread
 __global__ void __launch_bounds__(FT, 2) k_opt_chain(NetDev net, PoolDev pool, const PropDev* props,
                                                   const int* row_node, const int* row_j,
                                                   FusedHP hp, float* AP_out, float* GB_out,
-                                                  int maxw) {
+                                                  int maxw, FusedTc ft, int* err) {
   extern __shared__ __align__(16) float fsm[];
   __shared__ float red[32];
   __shared__ int improved;
+  __shared__ __align__(8) uint64_t tc_bar;
+  __shared__ uint32_t tc_holder;
   const int SD = pool.SD, d0 = pool.d0, R = net.R;
-  // conv weights of every layer, staged once: Wb then Wf per conv layer
+  // conv weights of every layer, staged once: Wb then Wf per conv layer (the
+  // Wb region of the tensor-core layer holds its Z instead)
   int wtot = 0;
   for (int t = 1; t <= R; ++t) {
     const LayerDev& L = net.aff[t];
     if (L.kind != MNBAB_CONV2D) continue;
-    f_stage(fsm + wtot, L.Wb, L.co, L.k * L.k * L.ci, f_wb_stride(L), FT);
-    f_stage(fsm + wtot + f_wb_floats(L), L.Wf, L.ci, L.k * L.k * L.co, f_wf_stride(L), FT);
-    wtot += f_conv_wfloats(L);
+    const int wbr = ftc_wb_region(L, t, ft);
+    if (t != ft.t) f_stage(fsm + wtot, L.Wb, L.co, L.k * L.k * L.ci, f_wb_stride(L), FT);
+    f_stage(fsm + wtot + wbr, L.Wf, L.ci, L.k * L.k * L.co, f_wf_stride(L), FT);
+    wtot += wbr + f_wf_floats(L);
   }
+  uint32_t tmem = 0, phase = 0;
+  const uint32_t bar = tc::smem_u32(&tc_bar);
+  if (ft.t) {
+    if ((threadIdx.x >> 5) == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       tc::smem_u32(&tc_holder)),
+                   "r"(ft.ncols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+      tc::mbar_init(bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem = tc_holder;
+    ftc_load_a(ft, net.aff[ft.t], tmem);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  bool abort = false;
   const int SDp = (SD + 3) & ~3;  // 16-byte aligned sub-buffers
   float* B0 = fsm + wtot;
   float* B1 = B0 + maxw;
@@ -410,7 +600,9 @@ __global__ void __launch_bounds__(FT, 2) k_opt_chain(NetDev net, PoolDev pool, c
   unsigned char* code = reinterpret_cast<unsigned char*>(Xs + ((d0 + 3) & ~3));
   auto wsm = [&](int t) {  // staged weights of conv layer t
     int o = 0;
-    for (int u = 1; u < t; ++u) o += f_conv_wfloats(net.aff[u]);
+    for (int u = 1; u < t; ++u)
+      if (net.aff[u].kind == MNBAB_CONV2D)
+        o += ftc_wb_region(net.aff[u], u, ft) + f_wf_floats(net.aff[u]);
     return fsm + o;
   };
   const int m = blockIdx.x;
@@ -464,13 +656,22 @@ __global__ void __launch_bounds__(FT, 2) k_opt_chain(NetDev net, PoolDev pool, c
       }
       __syncthreads();
       const LayerDev& L = net.aff[t];
-      if (L.kind == MNBAB_FC) f_fc_back(L, cur, nxt);
-      else f_conv_back(L, cur, nxt, wsm(t));
+      if (L.kind == MNBAB_FC) {
+        f_fc_back(L, cur, nxt);
+      } else if (t == ft.t) {
+        if (!ftc_back(ft, L, cur, nxt, wsm(t), tmem, bar, phase, err)) {
+          abort = true;
+          break;
+        }
+      } else {
+        f_conv_back(L, cur, nxt, wsm(t));
+      }
       __syncthreads();
       float* tmp = cur;
       cur = nxt;
       nxt = tmp;
     }
+    if (abort) break;
     for (int j = threadIdx.x; j < d0; j += FT) {
       const float a = cur[j];
       const float x = a >= 0.f ? P.lo[j] : P.hi[j];
@@ -499,7 +700,7 @@ __global__ void __launch_bounds__(FT, 2) k_opt_chain(NetDev net, PoolDev pool, c
       __syncthreads();
       const LayerDev& L = net.aff[t];
       if (L.kind == MNBAB_FC) f_fc_fwd(L, g, h);
-      else f_conv_fwd(L, g, h, wsm(t) + f_wb_floats(L));
+      else f_conv_fwd(L, g, h, wsm(t) + ftc_wb_region(L, t, ft));
       __syncthreads();
       const int dt = net.d[t], off = net.off[t];
       for (int j = threadIdx.x; j < dt; j += FT) {
@@ -558,6 +759,15 @@ __global__ void __launch_bounds__(FT, 2) k_opt_chain(NetDev net, PoolDev pool, c
         pool.MB[q] = mo;
         pool.VB[q] = ve;
       }
+    }
+  }
+  if (ft.t) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(ft.ncols));
     }
   }
 }
@@ -893,9 +1103,11 @@ static int fused_maxw(const NetDev& net, int d0) {
   return (maxw + 3) / 4 * 4;
 }
 
-static int fused_smem_floats(const NetDev& net, int SD, int d0) {
+static int fused_smem_floats(const NetDev& net, int SD, int d0, const FusedTc& ft = FusedTc()) {
   int w = 0;
-  for (int t = 1; t <= net.R; ++t) w += f_conv_wfloats(net.aff[t]);
+  for (int t = 1; t <= net.R; ++t)
+    if (net.aff[t].kind == MNBAB_CONV2D)
+      w += ftc_wb_region(net.aff[t], t, ft) + f_wf_floats(net.aff[t]);
   return w + 2 * fused_maxw(net, d0) + (SD + 3) / 4 * 4 + (d0 + 3) / 4 * 4 + (SD + 3) / 4;
 }
 
@@ -911,16 +1123,57 @@ bool fused_supported(const NetDev& net, int SD, int d0, int steps) {
   return fused_smem_floats(net, SD, d0) * (int)sizeof(float) <= 200 * 1024;
 }
 
+// The conv layer whose transposed convolution runs on the tensor cores: the one
+// with the most multiply-adds among those whose operands fit (A and D in 256
+// tensor-memory columns, the whole shared-memory layout with B and Z within the
+// fused kernel's limit); t = 0 when none fits.
+static FusedTc fused_tc_plan(const NetDev& net, int SD, int d0) {
+  constexpr int kTwoPerSm = 112 * 1024;  // dynamic shared memory of two CTAs per SM
+  const int simt = fused_smem_floats(net, SD, d0) * (int)sizeof(float);
+  FusedTc best;
+  double best_macs = 0.0;
+  for (int t = 1; t <= net.R; ++t) {
+    const LayerDev& L = net.aff[t];
+    if (L.kind != MNBAB_CONV2D || !L.W || L.k > FTC_TAPS * L.s) continue;
+    FusedTc f;
+    f.t = t;
+    f.RK = L.ci * L.k * L.k;
+    f.P = L.ho * L.wo;
+    f.Mt = (f.RK + 127) / 128;
+    f.Kp = (L.co + 7) / 8 * 8;
+    f.Np = std::max(16, (f.P + 15) / 16 * 16);
+    f.zs = f.P | 1;
+    f.dcol = f.Mt * 2 * f.Kp;
+    const int cols = f.dcol + f.Mt * f.Np;
+    // a larger Z region must not cost the second CTA per SM
+    const int bytes = fused_smem_floats(net, SD, d0, f) * (int)sizeof(float);
+    if (f.Np > 256 || cols > 256 || bytes > 200 * 1024 ||
+        (simt <= kTwoPerSm && bytes > kTwoPerSm))
+      continue;
+    f.ncols = 32;
+    while ((int)f.ncols < cols) f.ncols <<= 1;
+    const double macs = (double)L.co * f.P * f.RK;
+    if (macs > best_macs) {
+      best_macs = macs;
+      best = f;
+    }
+  }
+  return best;
+}
+
+int fused_tc_layer(const NetDev& net, int SD, int d0) { return fused_tc_plan(net, SD, d0).t; }
+
 void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropDev* props,
                       const int* row_node, const int* row_j, const FusedHP& hp, float* AP_out,
-                      float* GB_out,
-                      cudaStream_t st) {
+                      float* GB_out, bool allow_tc, int* err, cudaStream_t st) {
   if (M <= 0) return;
-  const int smem = fused_smem_floats(net, pool.SD, pool.d0) * (int)sizeof(float);
+  const FusedTc ft = allow_tc && err ? fused_tc_plan(net, pool.SD, pool.d0) : FusedTc();
+  const int smem = fused_smem_floats(net, pool.SD, pool.d0, ft) * (int)sizeof(float);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_opt_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_opt_chain<<<M, FT, smem, st>>>(net, pool, props, row_node, row_j, hp, AP_out, GB_out,
-                                  fused_maxw(net, pool.d0));
+  const int maxw = fused_maxw(net, pool.d0);
+  k_opt_chain<<<M, FT, smem, st>>>(net, pool, props, row_node, row_j, hp, AP_out, GB_out, maxw, ft,
+                                  err);
 }
 
 bool sweep_chain_supported(const NetDev& net, int t0) {

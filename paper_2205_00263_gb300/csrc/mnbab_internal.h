@@ -231,10 +231,14 @@ bool fused_supported(const NetDev& net, int SD, int d0, int steps);
 // rows m < M: node row_node[m], objective row row_j[m]; a' of the final sweep
 // goes to AP_out [M][SD]; GB_out [M][SD] is row scratch for d lb / d beta;
 // BEST / BESTX of the node track the best iterate.
+// allow_tc: the largest conv layer whose operands fit takes its transposed
+// convolution on the tensor cores (3xTF32); err is the device error flag of
+// its bounded waits (null: SIMT only).
 void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropDev* props,
                       const int* row_node, const int* row_j, const FusedHP& hp, float* AP_out,
-                      float* GB_out,
-                      cudaStream_t st);
+                      float* GB_out, bool allow_tc, int* err, cudaStream_t st);
+// the layer launch_opt_chain(allow_tc = true) runs on the tensor cores (0: none)
+int fused_tc_layer(const NetDev& net, int SD, int d0);
 // Intermediate-bound rows that start at a fully connected neuron of zhat_t0
 // above a chain of FC / conv layers: one persistent CTA loop, each row carried
 // to the input in shared memory with DeepPoly epilogues; lower bounds to lb[m].

@@ -270,18 +270,20 @@ void d2h(mnbab_ctx* c, T* dst, const T* src, size_t n) {
 
 enum Cat {
   C_BACKSUB_FC, C_BACKSUB_CONV, C_FWD_FC, C_FWD_CONV, C_INIT, C_REDUCE, C_GAMMA, C_ADAM, C_ACS,
-  C_BOOK, C_WIN, C_FUSED, C_SWEEP, C_BACKSUB_CONV_TC, C_FWD_CONV_TC, NKCAT,
+  C_BOOK, C_WIN, C_FUSED, C_SWEEP, C_BACKSUB_CONV_TC, C_FWD_CONV_TC, C_FUSED_TC, NKCAT,
   // host wall time of the BaB step phases (stream work included up to their syncs)
   H_ROOTS = NKCAT, H_REBOUND, H_DEEPPOLY, H_OPTIMIZE, H_CONFIRM, H_FINISH,
   // device time of all kernel classes launched within each phase
   G_ROOTS, G_REBOUND, G_DEEPPOLY, G_OPTIMIZE, G_CONFIRM, G_FINISH, NCAT
 };
 constexpr int NPHASE = 6;
+static_assert(NCAT <= 32, "profile arrays hold 32 classes");
 const char* CAT_NAMES[NCAT] = {"backsub_fc_gemm", "backsub_conv_transpose", "forward_fc_gemm",
                                "forward_conv",    "init_rows",              "reduce_lb",
                                "gamma_terms",     "adam",                   "acs",
                                "bookkeeping",     "backsub_conv_window",    "opt_fused_chain",
                                "backsub_rows_fused", "backsub_conv_tc", "forward_conv_tc",
+                               "opt_fused_chain_tc",
                                "step_roots_wall",        "step_rebound_wall",
                                "step_deeppoly_wall", "step_optimize_wall",  "step_confirm_wall",
                                "step_finish_wall", "phase_roots_gpu",        "phase_rebound_gpu",
@@ -822,11 +824,14 @@ void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a)
     }
     double macs = 0.0;
     for (int t = 1; t <= n->R; ++t) macs += layer_macs(n->nd.aff[t]);
-    Scope sc(c, C_FUSED,
+    // one conv layer's transposed convolution on the tensor cores (class
+    // opt_fused_chain_tc) unless the SIMT path is forced
+    const bool tc = c->gemm_path != 1 && fused_tc_layer(n->nd, n->SD, n->d0) > 0;
+    Scope sc(c, tc ? C_FUSED_TC : C_FUSED,
              2.0 * M * ((a.steps + 1.0) * (macs + n->nd.d[n->R]) + a.steps * macs),
              (double)M * (a.steps + 1.0) * n->SD * 66.0);
-    launch_opt_chain(M, n->nd, n->pool, c->d_props, n->bslots, n->brows, hp, n->AP, n->GB,
-                     c->st);
+    launch_opt_chain(M, n->nd, n->pool, c->d_props, n->bslots, n->brows, hp, n->AP, n->GB, tc,
+                     c->d_err, c->st);
     return;
   }
   {

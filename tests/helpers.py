@@ -41,6 +41,14 @@ def conv_spec(seed):
                         ("fc", 13), ("relu",), ("fc", 4)])
 
 
+def conv_small_spec(seed):
+    """The conv_small_28 layer pattern: 1x28x28 -> conv16 4x4 s2 -> conv32 4x4 s2
+    -> FC100 -> FC10."""
+    return dict(seed=seed, in_shape=(1, 28, 28),
+                layers=[("conv", 16, 4, 2, 0), ("relu",), ("conv", 32, 4, 2, 0), ("relu",),
+                        ("fc", 100), ("relu",), ("fc", 10)])
+
+
 def convbig_spec(seed):
     """The conv-big layer pattern (3x3 s1 p1, 4x4 s2 p1; 32 and 64 channels) on
     a 3x12x12 input: the 64 -> 64 4x4 layer's weights (256 KB) exceed shared

@@ -11,7 +11,8 @@ import pytest
 import torch
 
 import synth
-from helpers import (ACS_TIE, COND, TOL, close, compare_trace, concat, conv_case, convbig_spec, fc_case,
+from helpers import (ACS_TIE, COND, TOL, close, compare_trace, concat, conv_case, conv_small_spec,
+                     convbig_spec, fc_case,
                      f32, gpu_property, gpu_recompute, oracle_sensitivity, random_node, resnet_spec,
                      run_gpu_bab, to_params, verdicts_consistent)
 from oracle import bab, core, mnc
@@ -241,16 +242,22 @@ def test_optimized_bound_eps_rel_option(Context, path):
             _assert_close(best[k], ref, f"node {k} optimised bound")
 
 
-@pytest.mark.parametrize("path", [1, 2])
-@pytest.mark.parametrize("case", ["fc", "conv"])
+@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("case", ["fc", "conv", "conv_small"])
 def test_optimized_bound_without_constraints(Context, case, path):
     """Without multi-neuron constraints the optimisation loop of a chain network
-    runs in one fused launch (path 1) or as separate sweeps, adjoints and Adam
-    steps (path 2, tensor-core GEMMs); both match the oracle's 20-step Adam."""
+    runs in one fused launch (path 0: the largest conv layer's transposed
+    convolution on the tensor cores; path 1: SIMT only) or as separate sweeps,
+    adjoints and Adam steps (path 2, tensor-core GEMMs); all match the oracle's
+    20-step Adam."""
     if case == "fc":
         layers, C, d, lo, hi, prep = fc_case(9, (37, 53, 29, 7), 0.12)
-    else:
+    elif case == "conv":
         layers, C, d, lo, hi, prep = conv_case(5, 0.05)
+    else:
+        # the conv_small_28 layer pattern (conv16 4x4 s2, conv32 4x4 s2, FC100) on a
+        # 1x28x28 input, seeded like the other cases
+        layers, C, d, lo, hi, prep = conv_case(6, 0.02, conv_small_spec)
     net, lo_t, hi_t, l, u, S, m, dense = prep
     rng = np.random.default_rng(9)
     with Context(node_capacity=128, gemm_path=path) as ctx:
@@ -266,7 +273,10 @@ def test_optimized_bound_without_constraints(Context, case, path):
             gids.append(gid)
         best = ctx.optimize(gids, steps=20)
         stats, _ = ctx.profile_read()
-        assert (stats["opt_fused_chain"]["launches"] > 0) == (path == 1)
+        fused = stats["opt_fused_chain"]["launches"]
+        fused_tc = stats["opt_fused_chain_tc"]["launches"]
+        assert (fused > 0) == (path == 1 or (path == 0 and case == "fc"))
+        assert (fused_tc > 0) == (path == 0 and case != "fc")
         for k, on in enumerate(onodes):
             ref, *_ = core.optimize(net, on, dense, lo_t, hi_t, core.AdamHP())
             _assert_close(best[k], ref, f"node {k} optimised bound")
