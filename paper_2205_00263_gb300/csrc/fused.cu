@@ -550,12 +550,16 @@ __device__ bool ftc_back(const FusedTc& ft, const LayerDev& L, const float* cur,
 __global__ void __launch_bounds__(FT, 2) k_opt_chain(NetDev net, PoolDev pool, const PropDev* props,
                                                   const int* row_node, const int* row_j,
                                                   FusedHP hp, float* AP_out, float* GB_out,
-                                                  int maxw, FusedTc ft, int* err) {
+                                                  int maxw, FusedTc ft, int* err,
+                                                  const float* __restrict__ skip_lb) {
   extern __shared__ __align__(16) float fsm[];
   __shared__ float red[32];
   __shared__ int improved;
   __shared__ __align__(8) uint64_t tc_bar;
   __shared__ uint32_t tc_holder;
+  // a row whose DeepPoly bound (skip_lb, by batch row) already verifies its node
+  // is not optimised: the node keeps its state and its DeepPoly best bound
+  if (skip_lb && skip_lb[blockIdx.x] > 0.f) return;
   const int SD = pool.SD, d0 = pool.d0, R = net.R;
   // conv weights of every layer, staged once: Wb then Wf per conv layer (the
   // Wb region of the tensor-core layer holds its Z instead)
@@ -1165,7 +1169,8 @@ int fused_tc_layer(const NetDev& net, int SD, int d0) { return fused_tc_plan(net
 
 void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropDev* props,
                       const int* row_node, const int* row_j, const FusedHP& hp, float* AP_out,
-                      float* GB_out, bool allow_tc, int* err, cudaStream_t st) {
+                      float* GB_out, bool allow_tc, int* err, cudaStream_t st,
+                      const float* skip_lb) {
   if (M <= 0) return;
   const FusedTc ft = allow_tc && err ? fused_tc_plan(net, pool.SD, pool.d0) : FusedTc();
   const int smem = fused_smem_floats(net, pool.SD, pool.d0, ft) * (int)sizeof(float);
@@ -1173,7 +1178,7 @@ void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropD
     cudaFuncSetAttribute(k_opt_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int maxw = fused_maxw(net, pool.d0);
   k_opt_chain<<<M, FT, smem, st>>>(net, pool, props, row_node, row_j, hp, AP_out, GB_out, maxw, ft,
-                                  err);
+                                  err, skip_lb);
 }
 
 bool sweep_chain_supported(const NetDev& net, int t0) {

@@ -2335,16 +2335,20 @@ __device__ double f64_edge(const LayerDev& L, const double* z, int o) {
 // FP64 forward pass of counterexample candidates (Sec. 3.1, upper bounding):
 // one launch per layer, one thread per (candidate, neuron), then the objective
 // row per candidate.
-__global__ void k_f64_input(int M, const float* X, int ldx, double* buf, int ldb, int d0) {
+// With dcount set, only the first *dcount of the M rows are live (a count the
+// device computed; the grid covers M).
+__global__ void k_f64_input(int M, const int* dcount, const float* X, int ldx, double* buf, int ldb,
+                            int d0) {
   const int m = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (dcount && m >= *dcount) return;
   if (m < M && k < d0) buf[(size_t)m * ldb + k] = (double)X[(size_t)m * ldx + k];
 }
 
-__global__ void k_f64_layer(int M, NetDev net, int t, double* buf, int ldb) {
+__global__ void k_f64_layer(int M, const int* dcount, NetDev net, int t, double* buf, int ldb) {
   const int m = blockIdx.y;
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M || o >= net.d[t]) return;
+  if (m >= M || o >= net.d[t] || (dcount && m >= *dcount)) return;
   double* z = buf + (size_t)m * ldb;
   const int d0 = net.d[0];
   auto seg = [&](int s) { return s == 0 ? z : z + d0 + net.off[s]; };
@@ -2353,9 +2357,11 @@ __global__ void k_f64_layer(int M, NetDev net, int t, double* buf, int ldb) {
   seg(t)[o] = v > 0.0 ? v : 0.0;
 }
 
-__global__ void k_f64_objective(int M, const int* row_node, PoolDev pool, const PropDev* props,
-                                NetDev net, const double* buf, int ldb, double* fout) {
+__global__ void k_f64_objective(int M, const int* dcount, const int* row_node, PoolDev pool,
+                                const PropDev* props, NetDev net, const double* buf, int ldb,
+                                double* fout) {
   const int m = blockIdx.x;
+  if (dcount && m >= *dcount) return;
   const double* z = buf + (size_t)m * ldb;
   const int n = row_node[m];
   const PropDev& P = props[pool.prop[n]];
@@ -2378,12 +2384,54 @@ __global__ void k_f64_objective(int M, const int* row_node, PoolDev pool, const 
 
 void launch_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev* props,
                         const NetDev& net, const float* X, int ldx, double* buf, int ldb,
-                        double* fout, cudaStream_t st) {
+                        double* fout, cudaStream_t st, const int* dcount) {
   if (M <= 0) return;
-  k_f64_input<<<dim3((net.d[0] + 255) / 256, M), 256, 0, st>>>(M, X, ldx, buf, ldb, net.d[0]);
+  k_f64_input<<<dim3((net.d[0] + 255) / 256, M), 256, 0, st>>>(M, dcount, X, ldx, buf, ldb,
+                                                                net.d[0]);
   for (int t = 1; t <= net.R; ++t)
-    k_f64_layer<<<dim3((net.d[t] + 127) / 128, M), 128, 0, st>>>(M, net, t, buf, ldb);
-  k_f64_objective<<<M, 256, 0, st>>>(M, row_node, pool, props, net, buf, ldb, fout);
+    k_f64_layer<<<dim3((net.d[t] + 127) / 128, M), 128, 0, st>>>(M, dcount, net, t, buf, ldb);
+  k_f64_objective<<<M, 256, 0, st>>>(M, dcount, row_node, pool, props, net, buf, ldb, fout);
+}
+
+// Counterexample candidates of a batch (Sec. 3.1, upper bounding), in batch
+// order: rows m < M whose FP32 objective at the node's best minimiser is
+// negative and whose best bound is not positive.  One CTA of up to 1024
+// threads, a thread per row and rounds of 1024 rows; writes the rows' batch
+// indices and slots and their count.
+__global__ void __launch_bounds__(1024) k_select_cand(int M, const float* __restrict__ fout,
+                                                      const int* __restrict__ slots,
+                                                      const float* __restrict__ best,
+                                                      int* cand_idx, int* cand_slot, int* count) {
+  __shared__ int warp_tot[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int m0 = 0; m0 < M; m0 += blockDim.x) {
+    const int m = m0 + threadIdx.x;
+    bool c = false;
+    if (m < M) c = fout[m] < 0.f && !(best[slots[m]] > 0.f);
+    const unsigned bal = __ballot_sync(0xffffffffu, c);
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    int before = base;
+    for (int w = 0; w < warp; ++w) before += warp_tot[w];
+    before += __popc(bal & ((1u << lane) - 1u));
+    if (c) {
+      cand_idx[before] = m;
+      cand_slot[before] = slots[m];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int w = 0; w < nw; ++w) base += warp_tot[w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base;
+}
+
+void launch_select_cand(int M, const float* fout, const int* slots, const float* best,
+                        int* cand_idx, int* cand_slot, int* count, cudaStream_t st) {
+  const int thr = std::max(32, std::min(1024, (M + 31) / 32 * 32));
+  k_select_cand<<<1, thr, 0, st>>>(M, fout, slots, best, cand_idx, cand_slot, count);
 }
 
 __global__ void k_fill(float* p, size_t n, float v) {

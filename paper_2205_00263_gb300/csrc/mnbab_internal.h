@@ -233,10 +233,12 @@ bool fused_supported(const NetDev& net, int SD, int d0, int steps);
 // BEST / BESTX of the node track the best iterate.
 // allow_tc: the largest conv layer whose operands fit takes its transposed
 // convolution on the tensor cores (3xTF32); err is the device error flag of
-// its bounded waits (null: SIMT only).
+// its bounded waits (null: SIMT only).  skip_lb (optional, by row): rows whose
+// value is positive (verified by the DeepPoly pass) are not optimised.
 void launch_opt_chain(int M, const NetDev& net, const PoolDev& pool, const PropDev* props,
                       const int* row_node, const int* row_j, const FusedHP& hp, float* AP_out,
-                      float* GB_out, bool allow_tc, int* err, cudaStream_t st);
+                      float* GB_out, bool allow_tc, int* err, cudaStream_t st,
+                      const float* skip_lb = nullptr);
 // the layer launch_opt_chain(allow_tc = true) runs on the tensor cores (0: none)
 int fused_tc_layer(const NetDev& net, int SD, int d0);
 // Intermediate-bound rows that start at a fully connected neuron of zhat_t0
@@ -336,6 +338,10 @@ void launch_root_slot_init(int nb, const int* slots, const int* prop, PoolDev po
 // FP64 forward pass f_r(x) of rows of X (counterexample confirmation).
 void launch_forward_f64(int M, const int* row_node, PoolDev pool, const PropDev* props,
                         const NetDev& net, const float* X, int ldx, double* buf, int ldb,
-                        double* fout, cudaStream_t st);
+                        double* fout, cudaStream_t st, const int* dcount = nullptr);
+// batch rows with a negative FP32 objective and a non-positive best bound, in
+// batch order: cand_idx / cand_slot [count], count on the device
+void launch_select_cand(int M, const float* fout, const int* slots, const float* best,
+                        int* cand_idx, int* cand_slot, int* count, cudaStream_t st);
 
 }  // namespace mnbab

@@ -93,6 +93,10 @@ struct mnbab_net {
   float* splitk = nullptr;
   size_t splitk_floats = 0;
   int* cslots = nullptr;
+  int *cand_idx = nullptr, *cand_count = nullptr;  // counterexample candidates picked on the device
+  // the last fused optimisation launch: its profiling class and per-row work
+  int fused_cat = -1;
+  double fused_row_flops = 0.0, fused_row_bytes = 0.0;
   int *bslots = nullptr, *brows = nullptr, *acs_layer = nullptr, *acs_neuron = nullptr,
       *acs_fb = nullptr, *kid_parent = nullptr, *kid_slots = nullptr, *kid_layer = nullptr,
       *kid_neuron = nullptr;
@@ -182,6 +186,9 @@ struct mnbab_ctx {
   // every full stream synchronisation (all earlier transfers are done)
   unsigned char* pin = nullptr;
   size_t pin_cap = 0, pin_used = 0;
+  // pinned landing area of the BaB step's device-to-host reads (Readback)
+  unsigned char* rb = nullptr;
+  size_t rb_cap = 0;
   std::vector<std::pair<void*, size_t>> allocs;
   // profiling: kernel-class timing with CUDA events, launch and copy counters
   bool prof = false;
@@ -267,6 +274,41 @@ void d2h(mnbab_ctx* c, T* dst, const T* src, size_t n) {
   c->d2h_bytes += (int64_t)(n * sizeof(T));
   if (n) ck(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToHost, c->st), "D2H");
 }
+
+// Device-to-host reads that do not block the host: a copy into pageable memory
+// returns only once it has completed, so the reads of a step land in the
+// context's pinned area and finish() moves them to their destinations after the
+// next stream synchronisation.  Without room (or without the area) a read falls
+// back to a direct, blocking copy.
+struct Readback {
+  mnbab_ctx* c;
+  struct Item {
+    void* dst;
+    size_t off, bytes;
+  };
+  std::vector<Item> items;
+  size_t used = 0;
+  explicit Readback(mnbab_ctx* c_) : c(c_) {}
+  template <typename T>
+  void add(T* dst, const T* src, size_t n) {
+    const size_t b = n * sizeof(T);
+    if (!b) return;
+    if (!c->rb || used + b > c->rb_cap) {
+      d2h(c, dst, src, n);
+      return;
+    }
+    c->d2h_bytes += (int64_t)b;
+    ck(cudaMemcpyAsync(c->rb + used, src, b, cudaMemcpyDeviceToHost, c->st), "D2H");
+    items.push_back({dst, used, b});
+    used += (b + 15) & ~size_t(15);
+  }
+  // after a synchronisation of the stream
+  void finish() {
+    for (const Item& it : items) std::memcpy(it.dst, c->rb + it.off, it.bytes);
+    items.clear();
+    used = 0;
+  }
+};
 
 enum Cat {
   C_BACKSUB_FC, C_BACKSUB_CONV, C_FWD_FC, C_FWD_CONV, C_INIT, C_REDUCE, C_GAMMA, C_ADAM, C_ACS,
@@ -738,15 +780,31 @@ void adjoint(mnbab_net* n, int M, bool has_gamma, int upto = -1) {
   }
 }
 
-void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a);
+void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a,
+                       const float* skip_lb = nullptr);
+
+// Whether run_optimize takes the fused one-launch loop for this batch.
+bool fused_path(mnbab_net* n, bool has_gamma, int steps) {
+  return !has_gamma && n->ctx->gemm_path != 2 && fused_supported(n->nd, n->SD, n->d0, steps);
+}
+
+// Takes work back out of a kernel class's algorithmic counts (rows a launch was
+// sized for that its kernel skipped).
+void prof_sub(mnbab_ctx* c, int cat, double flops, double bytes) {
+  c->acc_flops[cat] -= flops;
+  c->acc_bytes[cat] -= bytes;
+}
 
 // The optimisation loop, replayed from a CUDA graph: the row count is padded up
 // to a multiple of 64 with rows that point at the network's pad slot (its state
 // is scratch: nothing reads it), so a handful of graphs cover every batch size.
-void run_optimize(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
+// skip_lb (fused path without graphs only): rows whose DeepPoly bound is positive
+// are not optimised.
+void run_optimize(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a,
+                  const float* skip_lb = nullptr) {
   mnbab_ctx* c = n->ctx;
   if (!c->graphs || n->pad_slot < 0) {
-    run_optimize_body(n, M, has_gamma, a);
+    run_optimize_body(n, M, has_gamma, a, skip_lb);
     return;
   }
   const int Mb = std::min(n->B, (M + 63) / 64 * 64);
@@ -802,9 +860,10 @@ void run_optimize(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
   for (auto& pr : g->pairs) c->pending.push_back({(1 << 16) | pr.first, pr.second});
 }
 
-void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a) {
+void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a,
+                       const float* skip_lb) {
   mnbab_ctx* c = n->ctx;
-  if (!has_gamma && c->gemm_path != 2 && fused_supported(n->nd, n->SD, n->d0, a.steps)) {
+  if (fused_path(n, has_gamma, a.steps)) {
     // the whole loop in one launch, one CTA per row
     FusedHP hp{};
     hp.steps = a.steps;
@@ -827,11 +886,12 @@ void run_optimize_body(mnbab_net* n, int M, bool has_gamma, const mnbab_adam& a)
     // one conv layer's transposed convolution on the tensor cores (class
     // opt_fused_chain_tc) unless the SIMT path is forced
     const bool tc = c->gemm_path != 1 && fused_tc_layer(n->nd, n->SD, n->d0) > 0;
-    Scope sc(c, tc ? C_FUSED_TC : C_FUSED,
-             2.0 * M * ((a.steps + 1.0) * (macs + n->nd.d[n->R]) + a.steps * macs),
-             (double)M * (a.steps + 1.0) * n->SD * 66.0);
+    n->fused_cat = tc ? C_FUSED_TC : C_FUSED;
+    n->fused_row_flops = 2.0 * ((a.steps + 1.0) * (macs + n->nd.d[n->R]) + a.steps * macs);
+    n->fused_row_bytes = (a.steps + 1.0) * n->SD * 66.0;
+    Scope sc(c, n->fused_cat, M * n->fused_row_flops, M * n->fused_row_bytes);
     launch_opt_chain(M, n->nd, n->pool, c->d_props, n->bslots, n->brows, hp, n->AP, n->GB, tc,
-                     c->d_err, c->st);
+                     c->d_err, c->st, skip_lb);
     return;
   }
   {
@@ -898,6 +958,16 @@ __global__ void k_gather_rows(int M, const int* idx, const float* src, int ld_sr
   for (int k = threadIdx.x; k < w; k += blockDim.x) dst[(size_t)m * ld_dst + k] = s[k];
 }
 
+// the same for the first *count rows (a count on the device; the grid covers the
+// largest possible count)
+__global__ void k_gather_rows_n(const int* count, const int* idx, const float* src, int ld_src,
+                                float* dst, int ld_dst, int w) {
+  const int m = blockIdx.x;
+  if (m >= *count) return;
+  const float* s = src + (size_t)idx[m] * ld_src;
+  for (int k = threadIdx.x; k < w; k += blockDim.x) dst[(size_t)m * ld_dst + k] = s[k];
+}
+
 __global__ void k_gather1(int M, const int* idx, const float* src, float* dst) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m < M) dst[m] = src[idx[m]];
@@ -942,12 +1012,13 @@ mnbab_net* slots_of(mnbab_ctx* c, const mnbab_node_id* nodes, int nn, std::vecto
   return net;
 }
 
-void gather_best(mnbab_net* n, int M, float* host_out) {
+void gather_best(mnbab_net* n, int M, float* host_out, Readback* rb = nullptr) {
   {
     Scope sc(n->ctx, C_BOOK, 0.0, 12.0 * M);
     k_gather1<<<(M + 255) / 256, 256, 0, n->ctx->st>>>(M, n->bslots, n->pool.BEST, n->bestb);
   }
-  d2h(n->ctx, host_out, n->bestb, M);
+  if (rb) rb->add(host_out, n->bestb, M);
+  else d2h(n->ctx, host_out, n->bestb, M);
 }
 
 __global__ void k_acc_rows(size_t n, const float* x, float* acc) {
@@ -1124,6 +1195,8 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   n->f64a = dalloc_t<double>(c, B * (size_t)(n->d0 + n->SD));
   n->f64out = dalloc_t<double>(c, B);
   n->cslots = dalloc_t<int>(c, B);
+  n->cand_idx = dalloc_t<int>(c, B);
+  n->cand_count = dalloc_t<int>(c, 1);
   // split-K workspace: 16 splits of a B x (widest FC layer) product
   {
     size_t wmax = 0;
@@ -2067,75 +2140,115 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
     SweepOpts dp;
     dp.track = true;
     sweep(n, n->R + 1, obj_rows(n, M), dp);
+    Readback rb(c);
     std::vector<float> lb_dp(M);
-    d2h(c, lb_dp.data(), n->lb, M);
-    sync(c);
+    rb.add(lb_dp.data(), n->lb, M);
+    // On the fused path without graphs the whole batch goes to the optimiser,
+    // whose kernel skips the rows the DeepPoly pass verified (read on the
+    // device); the step then synchronises once for all of its results.
+    const bool all_rows = !c->graphs && fused_path(n, batch_has_gamma(n, slots), adam.steps);
+    if (!all_rows) {
+      sync(c);
+      rb.finish();
+    }
     ht.lap(H_DEEPPOLY);
-    // 3. projected Adam on the nodes DeepPoly does not verify
-    std::vector<int> opt_idx;
+    // 3. projected Adam on the nodes DeepPoly does not verify; dev lists the
+    // batch rows of the device arrays
+    std::vector<int> dev;
     for (int i = 0; i < M; ++i)
-      if (!(lb_dp[i] > 0.f)) opt_idx.push_back(i);
-    std::vector<int> oslots(opt_idx.size());
-    for (size_t i = 0; i < opt_idx.size(); ++i) oslots[i] = slots[opt_idx[i]];
-    const int Mo = (int)oslots.size();
-    std::vector<int> acs_l(Mo), acs_n(Mo), acs_fb(Mo);
+      if (all_rows || !(lb_dp[i] > 0.f)) dev.push_back(i);
+    std::vector<int> dslots(dev.size());
+    for (size_t k = 0; k < dev.size(); ++k) dslots[k] = slots[dev[k]];
+    const int Md = (int)dslots.size();
+    std::vector<int> acs_ld(Md), acs_nd(Md), acs_fbd(Md), cand_d(Md);
+    std::vector<float> f32d(Md);
+    std::vector<double> f64(Md);
     std::vector<float> best(M);
-    std::vector<float> f32(Mo);
-    if (Mo > 0) {
-      upload_batch(n, oslots);
-      const bool g = batch_has_gamma(n, oslots);
-      run_optimize(n, Mo, g, adam);
+    int n_cand = 0;
+    if (Md > 0) {
+      if (!all_rows) upload_batch(n, dslots);
+      const bool g = batch_has_gamma(n, dslots);
+      run_optimize(n, Md, g, adam, all_rows ? n->lb : nullptr);
       // 5. ACS at the final parameters (a' and gamma^T P of the last sweep)
       {
-        Scope sc(c, C_ACS, 0.0, 4.0 * Mo * n->SD * (g ? 5.0 : 4.0));
-        launch_acs(Mo, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0,
-                   n->acs_layer,
-                   n->acs_neuron, n->score, n->acs_fb, c->st);
+        Scope sc(c, C_ACS, 0.0, 4.0 * Md * n->SD * (g ? 5.0 : 4.0));
+        launch_acs(Md, n->bslots, n->pool, c->d_props, n->nd, n->GP, n->GPh, n->AP, g ? 1 : 0,
+                   n->acs_layer, n->acs_neuron, n->score, n->acs_fb, c->st);
       }
-      // 4. counterexample check at the best minimiser
+      // 4. counterexample check at the best minimiser: FP32 forward pass of every
+      // row, then the candidates (picked on the device) in FP64
       {
-        Scope sc(c, C_BOOK, 0.0, 8.0 * Mo * n->d0);
-        k_gather_rows<<<Mo, 128, 0, c->st>>>(Mo, n->bslots, n->pool.BESTX, n->d0, n->Xb, n->d0,
+        Scope sc(c, C_BOOK, 0.0, 8.0 * Md * n->d0);
+        k_gather_rows<<<Md, 128, 0, c->st>>>(Md, n->bslots, n->pool.BESTX, n->d0, n->Xb, n->d0,
                                              n->d0);
       }
-      forward_rows(n, Mo, n->Xb);
-      d2h(c, f32.data(), n->fout, Mo);
-      d2h(c, acs_l.data(), n->acs_layer, Mo);
-      d2h(c, acs_n.data(), n->acs_neuron, Mo);
-      d2h(c, acs_fb.data(), n->acs_fb, Mo);
+      forward_rows(n, Md, n->Xb);
+      {
+        Scope sc(c, C_BOOK, 0.0, 16.0 * Md);
+        launch_select_cand(Md, n->fout, n->bslots, n->pool.BEST, n->cand_idx, n->cslots,
+                           n->cand_count, c->st);
+      }
+      {
+        Scope sc(c, C_BOOK, 0.0, 8.0 * Md * n->d0);
+        k_gather_rows_n<<<Md, 128, 0, c->st>>>(n->cand_count, n->cslots, n->pool.BESTX, n->d0,
+                                               n->Xb, n->d0, n->d0);
+      }
+      {
+        Scope sc(c, C_BOOK, 0.0, 8.0 * Md * n->maxd, n->R + 2);
+        launch_forward_f64(Md, n->cslots, n->pool, c->d_props, n->nd, n->Xb, n->d0, n->f64a,
+                           n->d0 + n->SD, n->f64out, c->st, n->cand_count);
+      }
+      rb.add(f32d.data(), n->fout, Md);
+      rb.add(acs_ld.data(), n->acs_layer, Md);
+      rb.add(acs_nd.data(), n->acs_neuron, Md);
+      rb.add(acs_fbd.data(), n->acs_fb, Md);
+      rb.add(&n_cand, n->cand_count, 1);
+      rb.add(cand_d.data(), n->cand_idx, Md);
+      rb.add(f64.data(), n->f64out, Md);
     }
     // best bound of every node (DeepPoly value for the verified ones)
-    upload_batch(n, slots);
-    gather_best(n, M, best.data());
+    if (!all_rows) upload_batch(n, slots);
+    gather_best(n, M, best.data(), &rb);
     sync(c);
+    rb.finish();
     ht.lap(H_OPTIMIZE);
-    // FP64 confirmation of every FP32 counterexample candidate, in one batch
-    std::vector<int> cand_o;
-    for (int o = 0; o < Mo; ++o)
-      if (f32[o] < 0.f && !(best[opt_idx[o]] > 0.f)) cand_o.push_back(o);
-    const int Mc = (int)cand_o.size();
-    std::vector<double> f64(Mc);
-    std::vector<float> xc((size_t)Mc * n->d0);
-    if (Mc > 0) {
-      std::vector<int> cs(Mc);
-      for (int k = 0; k < Mc; ++k) cs[k] = oslots[cand_o[k]];
-      h2d(c, n->cslots, cs.data(), Mc);
-      {
-        Scope sc(c, C_BOOK, 0.0, 8.0 * Mc * n->d0);
-        k_gather_rows<<<Mc, 128, 0, c->st>>>(Mc, n->cslots, n->pool.BESTX, n->d0, n->Xb, n->d0,
-                                             n->d0);
-      }
-      {
-        Scope sc(c, C_BOOK, 0.0, 8.0 * Mc * n->maxd, n->R + 2);
-        launch_forward_f64(Mc, n->cslots, n->pool, c->d_props, n->nd, n->Xb, n->d0, n->f64a,
-                           n->d0 + n->SD, n->f64out, c->st);
-      }
-      d2h(c, f64.data(), n->f64out, Mc);
-      d2h(c, xc.data(), n->Xb, (size_t)Mc * n->d0);
-      sync(c);
+    // the optimised rows (batch indices) and their device rows
+    std::vector<int> opt_idx, d_of;
+    std::vector<int> o_of_d(Md, -1);
+    for (int k = 0; k < Md; ++k) {
+      if (all_rows && lb_dp[dev[k]] > 0.f) continue;
+      o_of_d[k] = (int)opt_idx.size();
+      opt_idx.push_back(dev[k]);
+      d_of.push_back(k);
     }
+    const int Mo = (int)opt_idx.size();
+    if (all_rows && Md > Mo && n->fused_cat >= 0)
+      prof_sub(c, n->fused_cat, (Md - Mo) * n->fused_row_flops, (Md - Mo) * n->fused_row_bytes);
+    std::vector<int> oslots(Mo), acs_l(Mo), acs_n(Mo), acs_fb(Mo);
+    std::vector<float> f32(Mo);
+    for (int o = 0; o < Mo; ++o) {
+      oslots[o] = slots[opt_idx[o]];
+      acs_l[o] = acs_ld[d_of[o]];
+      acs_n[o] = acs_nd[d_of[o]];
+      acs_fb[o] = acs_fbd[d_of[o]];
+      f32[o] = f32d[d_of[o]];
+    }
+    // FP64-confirmed candidates; the inputs of the falsifying ones are read back
+    // only when there are any
     std::vector<int> cand_of(Mo, -1);
-    for (int k = 0; k < Mc; ++k) cand_of[cand_o[k]] = k;
+    bool any_neg = false;
+    for (int k = 0; k < n_cand; ++k) {
+      const int o = o_of_d[cand_d[k]];
+      if (o >= 0) cand_of[o] = k;
+      any_neg = any_neg || f64[k] < 0.0;
+    }
+    std::vector<float> xc;
+    if (any_neg) {
+      xc.resize((size_t)n_cand * n->d0);
+      rb.add(xc.data(), n->Xb, xc.size());
+      sync(c);
+      rb.finish();
+    }
     ht.lap(H_CONFIRM);
     // exact completion of fully split leaves the bound does not decide (Sec. 3.3)
     std::vector<int> leaf_of(Mo, -1);
@@ -2273,7 +2386,8 @@ void bab_step_impl(mnbab_ctx* c, mnbab_prop* const* props, int n_props, int max_
           pk.p->row_open[pk.q.row]++;
         }
       }
-      sync(c);
+      // no synchronisation: a freed parent slot is reused only by later work on
+      // the same stream, after the children have copied it
       for (int b = 0; b < nb; ++b) free_slot(n, par[b]);
     }
   }
@@ -2368,6 +2482,13 @@ mnbab_status mnbab_create(const mnbab_options* opt, mnbab_ctx** out) {
     } else {
       cudaGetLastError();  // unpinned copies instead
     }
+    void* rb = nullptr;
+    if (cudaHostAlloc(&rb, (size_t)1 << 20, cudaHostAllocDefault) == cudaSuccess) {
+      c->rb = static_cast<unsigned char*>(rb);
+      c->rb_cap = (size_t)1 << 20;
+    } else {
+      cudaGetLastError();  // blocking reads instead
+    }
     ck(cudaMemset(c->d_err, 0, sizeof(int)), "memset");
   } catch (const Err& e) {
     mnbab_destroy(c);
@@ -2394,6 +2515,7 @@ void mnbab_destroy(mnbab_ctx* c) {
   for (auto e : c->graph_events) cudaEventDestroy(e);
   for (auto& a : c->allocs) cudaFree(a.first);
   if (c->pin) cudaFreeHost(c->pin);
+  if (c->rb) cudaFreeHost(c->rb);
   for (auto* r : c->requests) delete r;
   for (auto* n : c->nets) delete n;
   for (auto* p : c->props) delete p;
