@@ -667,8 +667,10 @@ void sweep(mnbab_net* n, int t, const RowsDev& rows, const SweepOpts& o) {
 // Re-bounds ReLU layers t > split layer of each node (Sec. 3.2, enforcing
 // splits); rows are the node's unstable unsplit neurons, both sides.  The rows
 // of every layer are collected up front (a layer's row set depends only on its
-// own current bounds), so a pass costs one host synchronisation.
-int64_t rebound(mnbab_net* n, const std::vector<int>& slots) {
+// own current bounds), so a pass costs one host synchronisation.  For fresh
+// root slots (`fresh`: every bound infinite, nothing split) every neuron is a
+// row, so the counts are known on the host and the pass does not synchronise.
+int64_t rebound(mnbab_net* n, const std::vector<int>& slots, bool fresh = false) {
   mnbab_ctx* c = n->ctx;
   const int R = n->R;
   int64_t total = 0;
@@ -698,8 +700,12 @@ int64_t rebound(mnbab_net* n, const std::vector<int>& slots) {
       at += 2 * lay.size() * (size_t)n->nd.d[t];
     }
     int M[MNBAB_MAXR + 2] = {0};
-    d2h(c, M, n->counter, R + 1);
-    sync(c);
+    if (fresh) {
+      for (int t = 1; t <= R; ++t) M[t] = 2 * cnt[t] * n->nd.d[t];
+    } else {
+      d2h(c, M, n->counter, R + 1);
+      sync(c);
+    }
     for (int t = 1; t <= R; ++t) {
       if (!cnt[t] || !M[t]) continue;
       total += M[t];
@@ -1171,6 +1177,9 @@ void setup_net(mnbab_ctx* c, mnbab_net* n) {
   n->rows_cap = std::max(n->rows_cap, (size_t)2 * SD);
   n->row_node = dalloc_t<int>(c, n->rows_cap);
   n->row_j = dalloc_t<int>(c, n->rows_cap);
+  // valid indices everywhere from the start (slot 0, neuron 0)
+  ck(cudaMemsetAsync(n->row_node, 0, n->rows_cap * sizeof(int), c->st), "memset");
+  ck(cudaMemsetAsync(n->row_j, 0, n->rows_cap * sizeof(int), c->st), "memset");
   n->row_sign = dalloc_t<float>(c, n->rows_cap);
   n->counter = dalloc_t<int>(c, MNBAB_MAXR + 2);
   n->rb_nodes = dalloc_t<int>(c, (size_t)(MNBAB_MAXR + 2) * B);
@@ -1871,7 +1880,7 @@ void ensure_roots(mnbab_net* n, mnbab_prop* const* only = nullptr, int n_only = 
   if (pend.empty()) return;
   std::vector<int> roots;
   for (auto* p : pend) roots.push_back(p->root_slot);
-  rebound(n, roots);
+  rebound(n, roots, true);
   // optimised intermediate bounds of the roots that ask for them (Sec. 3.1,
   // parameter sharing), before the root nodes take the root bounds
   std::vector<std::pair<int, int>> want;  // (steps, root slot)
@@ -1898,7 +1907,7 @@ void ensure_roots(mnbab_net* n, mnbab_prop* const* only = nullptr, int n_only = 
     h2d(c, n->ri_row, row.data(), row.size());
     Scope sc(c, C_BOOK, 0.0, 25.0 * dst.size() * n->SD);
     launch_root_init((int)dst.size(), n->ri_dst, n->ri_src, n->ri_row, n->pool, c->st);
-    sync(c);
+    // the index vectors were staged when they were enqueued: they can be reused
     dst.clear(); src.clear(); row.clear();
   };
   for (auto* p : pend) {
