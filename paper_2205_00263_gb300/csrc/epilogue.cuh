@@ -145,6 +145,38 @@ __device__ __forceinline__ void epi_load_row(const Epi& e, int n, const PropDev*
   }
 }
 
+// epi_load_row in two parts: the inputs that depend on the node and column only
+// (bounds, split, slope, multiplier; the input box), which rows of one node can
+// share, and those of the row itself
+__device__ __forceinline__ void epi_load_node(const Epi& e, int n, const PropDev* P, int j,
+                                              EpiIn& in) {
+  in.al = in.be = 0.f;
+  in.s = 0;
+  if (e.kind == EPI_RELU || e.kind == EPI_ADJ) {
+    const size_t q = (size_t)n * e.SD + e.off + j;
+    in.l = e.pool.L[q];
+    in.u = e.pool.U[q];
+    in.s = e.pool.S[q];
+    if (e.kind == EPI_ADJ || e.final_mode) in.al = e.pool.ALPHA[q];
+    if (e.kind == EPI_RELU && e.final_mode) in.be = e.pool.BETA[q];
+  } else if (e.kind == EPI_CONC) {
+    in.l = P->lo[j];
+    in.u = P->hi[j];
+  }
+}
+
+__device__ __forceinline__ void epi_load_own(const Epi& e, int m, int j, EpiIn& in) {
+  in.acc = e.acc_in ? e.acc_in[(size_t)m * e.acc_ld + j] : 0.f;
+  in.gp = in.gph = 0.f;
+  const size_t qm = (size_t)m * e.SD + e.off + j;
+  if (e.kind == EPI_RELU) {
+    if (e.GP) in.gp = e.GP[qm];
+    if (e.GPh) in.gph = e.GPh[qm];
+  } else if (e.kind == EPI_ADJ) {
+    in.gp = e.AP[qm];
+  }
+}
+
 __device__ __forceinline__ void epi_load(const Epi& e, int n, const PropDev* P, int m, int j,
                                          EpiIn& in) {
   epi_load_row(e, n, P, m, j, in);

@@ -224,19 +224,30 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     int my_nd = 0;
     if (per_node && lane < RPW && m0 + warp + 16 * lane < M)
       my_nd = e.row_node[m0 + warp + 16 * lane];
+    // a warp's rows of one node (consecutive rows of a batch usually are) share
+    // the node's per-column inputs: they are loaded when the node changes
+    EpiIn in[PER];
+    int have = -1;
 #pragma unroll 1
     for (int t = 0; t < RPW; ++t) {
       const int rr = warp + 16 * t, m = m0 + rr;
       const int nd = __shfl_sync(0xffffffffu, my_nd, t);
       if (m >= M) break;  // rows ascend with t
-      const PropDev* Pp = epi_prop(e, nd);
       // every global load of the row's outputs in flight before the arithmetic
-      EpiIn in[PER];
+      if (nd != have || !per_node) {
+        const PropDev* Pp = epi_prop(e, nd);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+          const int n = n0 + lane + 32 * i;
+          if (n < N) epi_load_node(e, nd, Pp, n, in[i]);
+          in[i].cb = cb[i];
+        }
+        have = nd;
+      }
 #pragma unroll
       for (int i = 0; i < PER; ++i) {
         const int n = n0 + lane + 32 * i;
-        if (n < N) epi_load_row(e, nd, Pp, m, n, in[i]);
-        in[i].cb = cb[i];
+        if (n < N) epi_load_own(e, m, n, in[i]);
       }
       float part = 0.f;
 #pragma unroll
