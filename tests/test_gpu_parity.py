@@ -41,13 +41,15 @@ def _assert_close(g, o, what, tol=TOL):
 # --------------------------------------------------------------------------
 # root bounds (DeepPoly back-substitution of every neuron, both sides)
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("path", [1, 2])
-@pytest.mark.parametrize("case", ["ragged_fc", "conv", "convbig", "resnet", "cfg0"])
+@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("case", ["ragged_fc", "conv", "conv_small", "convbig", "resnet", "cfg0"])
 def test_root_bounds(Context, case, path):
     if case == "ragged_fc":
         layers, C, d, lo, hi, prep = fc_case(1, (37, 53, 29, 7), 0.1)
     elif case == "conv":
         layers, C, d, lo, hi, prep = conv_case(2, 0.05)
+    elif case == "conv_small":
+        layers, C, d, lo, hi, prep = conv_case(6, 0.02, conv_small_spec)
     elif case == "convbig":
         layers, C, d, lo, hi, prep = conv_case(3, 0.01, convbig_spec)
     elif case == "resnet":
@@ -68,10 +70,13 @@ def test_root_bounds(Context, case, path):
         stats, _ = ctx.profile_read()
         # rows of convolution neurons above a convolution chain take the
         # receptive-field window kernel; the others the full-width sweep
-        if case in ("conv", "convbig", "resnet"):
+        if case in ("conv", "conv_small", "convbig", "resnet"):
             assert stats["backsub_conv_window"]["launches"] > 0
         else:
             assert stats["backsub_conv_window"]["launches"] == 0
+        # dense rows above a conv chain: the fused sweep
+        if case in ("conv", "conv_small"):
+            assert stats["backsub_rows_fused"]["launches"] > 0
 
 
 # --------------------------------------------------------------------------
