@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--plain-nodes", type=int, default=48)
+    ap.add_argument("--plain-nodes", type=int, default=512,
+                    help="nodes of the plain one-subproblem-per-launch arm")
     ap.add_argument("--e2e-steps", type=int, default=2,
                     help="cold solves of the e2e arm (0 skips the e2e arm)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -469,6 +470,7 @@ def run_ours(args):
         e1.synchronize()
         pms = e0.elapsed_time(e1)
         plain = {"value": pn / (pms * 1e-3), "unit": "nodes/s", "nodes": pn,
+                 "properties": win2.next,
                  "form": "one subproblem per launch (max_nodes=1), same kernels, no graph"}
 
     # e2e: the same rolling-window workload through the public API, every step
