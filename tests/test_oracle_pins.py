@@ -144,6 +144,57 @@ def test_standard_adam_closed_form(sign):
                                                     rel=1e-12)
 
 
+def test_adam_returns_the_best_iterate():
+    """The optimiser reports the best bound over its iterates (Sec. 3.1: every
+    parameter setting gives a valid bound).  f = relu(x) - 0.375 x on [-1, 1],
+    the linear part through a stable neuron z2 = x + 2:
+    lb(alpha) = -|alpha - 0.375|, maximal inside (0, 1).  From alpha = 1
+    Adam's first steps have a constant gradient, so each is lr = 0.1 long;
+    the sixth reaches alpha = 0.4 (lb = -0.025) and momentum then carries
+    alpha past the optimum.  The reported bound is at least -0.025, longer
+    runs never report less, and none exceeds the exact minimum 0."""
+    L = [_fc([[1.0], [1.0]], [0.0, 2.0]), RELU, _fc([[1.0, -0.375]], [0.75])]
+    net, lo, hi, l, u, S, _, _ = bab.prepare(L, [[1.0]], [0.0], [-1.0], [1.0])
+    assert float(l[1][1]) > 0 and float(l[1][0]) < 0 < float(u[1][0])
+    node = bab.root_node(net, 0, l, u, S, None)
+    for a in (0.0, 0.375, 0.8):
+        lb, _, _ = core.final_bound(net, node, {1: _t([a, 1.0])}, {1: _t([0.0, 0.0])},
+                                    {1: torch.zeros(0, dtype=DT)}, None, lo, hi)
+        assert float(lb) == pytest.approx(-abs(a - 0.375), abs=1e-12)
+    prev = -math.inf
+    for steps in (6, 12, 20, 30):
+        best, *_ = core.optimize(net, node, None, lo, hi, core.AdamHP(steps=steps))
+        assert best >= -0.025 - 1e-7  # steps are lr / (1 + eps / |g|) long
+        assert best <= 1e-12
+        assert best >= prev
+        prev = best
+
+
+def test_multi_neuron_terms_by_hand():
+    """The gamma terms of the ReLU step (Sec. 3.1, enforcing multi-neuron
+    constraints) by hand.  x in [-1, 1], zhat = x, y = relu(x), f = w y, one
+    constraint y - 0.5 zhat - 0.5 <= 0 (the triangle's upper facet) with
+    multiplier g.  The bound adds g (y - 0.5 zhat - 0.5) to f, so the
+    coefficient on y is a' = w + g, the one on zhat gains -0.5 g and the offset
+    -0.5 g.  With a' >= 0 the lower slope alpha applies:
+    lb = -|a' alpha - 0.5 g| - 0.5 g; with a' < 0 the upper line (slope 1/2,
+    intercept 1/2) applies: lb = -|0.5 a' - 0.5 g| + 0.5 a' - 0.5 g."""
+    m = core.MNC(np.array([[0]]), np.array([[1.0]]), np.array([[-0.5]]), np.array([0.5]))
+    dense = {1: m.dense(1)}
+    for w in (1.0, -1.0):
+        net, lo, hi, l, u, S, _, _ = bab.prepare(_one_neuron(w, 0.0), [[1.0]], [0.0], [-1.0], [1.0])
+        node = bab.root_node(net, 0, l, u, S, None)
+        for a, g in ((0.5, 1.0), (0.25, 2.0), (0.8, 0.3), (0.1, 0.0)):
+            lb, _, _ = core.final_bound(net, node, {1: _t([a])}, {1: _t([0.0])}, {1: _t([g])},
+                                        dense, lo, hi)
+            ap = w + g
+            if ap >= 0:
+                ref = -abs(ap * a - 0.5 * g) - 0.5 * g
+            else:
+                ref = -abs(0.5 * ap - 0.5 * g) + 0.5 * ap - 0.5 * g
+            assert float(lb) == pytest.approx(ref, abs=1e-12), (w, a, g)
+
+
 def test_relu_table_negative_coefficient():
     """f = -2 relu(x) + 5, x in [-1, 2]: the upper line u/(u-l)(x - l) with
     intercept -ul/(u-l) = 2/3 gives the exact minimum 1."""
@@ -411,6 +462,31 @@ def test_acs_scores_by_hand():
     sc, fb = core.acs_scores(node, gamma, dense, aps)
     assert fb and np.allclose(sc[1].numpy()[:3], [0.5, 1.5, 0.25])
     assert core.pick_split(sc)[:2] == (1, 1)
+    # the fallback's intercept -l u / (u - l) with l != -1: 2/3, 3/4, 3/4
+    node3 = core.Node(0, {1: _t([-2, -1, -3, 1]), 2: _t([-1, -1])},
+                      {1: _t([1, 3, 1, 2]), 2: _t([1, 1])}, S, {}, {}, {}, split_layer=2)
+    sc, fb = core.acs_scores(node3, gamma, dense, aps)
+    assert fb and np.allclose(sc[1].numpy()[:3], [2.0 / 3.0, 2.25, 0.375])
+    # ties: within 1e-5 (relative) of the maximum the lowest (layer, index)
+    # wins; beyond the band the maximum does
+    assert core.pick_split({1: _t([0.5, 0.5 * (1 + 1e-6)])})[:2] == (1, 0)
+    assert core.pick_split({1: _t([0.5, 0.5 * (1 + 1e-4)])})[:2] == (1, 1)
+    assert core.pick_split({1: _t([0.1]), 2: _t([0.1 * (1 + 1e-6)])})[:2] == (1, 0)
+
+
+def test_folded_property_is_the_margin():
+    """Folding C f(x) + d into the last affine layer (Sec. 2.1) gives a network
+    whose outputs are the margins, by the generator's own numpy forward pass;
+    the last layer's bias is large here so that a dropped C b shows."""
+    L = synth.tiny_fc_net(12, [5, 7, 4])
+    L[-1]["b"] = np.array([1.0, -2.0, 0.5, 3.0], np.float32)
+    C, d = synth.property_rows(2, 4)
+    d = d + np.array([0.25, -0.5, 1.0], np.float32)
+    folded = core.fold_property(core.load_net(L), C, d)
+    X = np.random.default_rng(12).uniform(-1, 1, size=(20, 5))
+    got = folded.forward(_t(X)).numpy()
+    ref = np.stack([C.astype(np.float64) @ synth.net_forward(L, x) + d for x in X])
+    assert np.allclose(got, ref, atol=1e-10)
 
 
 def test_counterexamples_are_real():
@@ -447,6 +523,28 @@ def test_children_keep_earlier_bounds():
         assert bool((ch.l[2] >= l[2] - 1e-12).all()) and bool((ch.u[2] <= u[2] + 1e-12).all())
     assert float(kids[0].u[1][j]) == 0.0 and int(kids[0].S[1][j]) == 1
     assert float(kids[1].l[1][j]) == 0.0 and int(kids[1].S[1][j]) == -1
+
+
+def test_rebound_after_split_is_exact_on_single_neurons():
+    """Re-bounding after a split (Sec. 3.2) by hand: x in [-1, 1], z1 = x,
+    z2 = relu(z1) - 0.5, f = relu(z2).  At the root DeepPoly gives
+    z2 in [-1.5, 0.5] (lower slope 1 since u1 = -l1; upper line (x + 1) / 2).
+    Splitting z1 <= 0 makes relu(z1) = 0, so the re-bounded z2 is exactly
+    -0.5; splitting z1 >= 0 makes the ReLU the identity, and with beta = 0
+    the re-bounding sees z1 = x over the whole box: z2 in [-1.5, 0.5]."""
+    L = [_fc([[1.0]], [0.0]), RELU, _fc([[1.0]], [-0.5]), RELU, _fc([[1.0]], [0.0])]
+    net, lo, hi, l, u, S, _, _ = bab.prepare(L, [[1.0]], [0.0], [-1.0], [1.0])
+    assert (float(l[1][0]), float(u[1][0])) == (-1.0, 1.0)
+    assert float(l[2][0]) == pytest.approx(-1.5, abs=1e-12)
+    assert float(u[2][0]) == pytest.approx(0.5, abs=1e-12)
+    node = bab.root_node(net, 0, l, u, S, None)
+    neg, pos = bab.children(node, (node.alpha, node.beta, node.gamma), (1, 0, 0.0), 1)
+    for ch in (neg, pos):
+        core.rebound_node(net, ch, lo, hi)
+    assert float(neg.l[2][0]) == pytest.approx(-0.5, abs=1e-12)
+    assert float(neg.u[2][0]) == pytest.approx(-0.5, abs=1e-12)
+    assert float(pos.l[2][0]) == pytest.approx(-1.5, abs=1e-12)
+    assert float(pos.u[2][0]) == pytest.approx(0.5, abs=1e-12)
 
 
 def test_cab_costs_by_hand():
