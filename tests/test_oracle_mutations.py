@@ -17,7 +17,7 @@ import textwrap
 
 import pytest
 
-from oracle import attack, bab, core, mnc
+from oracle import attack, bab, core, exact, mnc
 
 import test_attack_pins as apins
 import test_oracle_intermediate as ipins
@@ -53,6 +53,9 @@ REBOUND_EXACT = (pins.test_rebound_after_split_is_exact_on_single_neurons, ())
 ADAM_BEST = (pins.test_adam_returns_the_best_iterate, ())
 MNC_TERMS = (pins.test_multi_neuron_terms_by_hand, ())
 FOLD = (pins.test_folded_property_is_the_margin, ())
+BAB_ROOT = (pins.test_bab_root_verdict_uses_the_optimised_bound, ())
+LEAF_LP = (pins.test_fully_split_leaf_reaches_lp_optimum, (5,))
+COMPLETE = (pins.test_unlimited_bab_with_exact_leaves_is_complete, (2, 0.30906))
 MNC_SOUND = (pins.test_mnc_rows_are_sound_per_orthant, ())
 ACS = (pins.test_acs_scores_by_hand, ())
 CEX = (pins.test_counterexamples_are_real, ())
@@ -162,6 +165,17 @@ CASES = [
      "2.0 * net.width(t) * C[t]", "net.width(t) * C[t]", [CAB]),
     ("cab_conv_cost_as_weights", core, "cab_costs",
      "A.d_out * A.W.shape[2] * A.W.shape[3]", "A.W.numel()", [CAB]),
+    ("octahedron_direction_negated", mnc, "octahedron_bounds",
+     "E[gi * len(DIRS) + di, G[k]] += dv[k]", "E[gi * len(DIRS) + di, G[k]] -= dv[k]",
+     [MNC_SOUND]),
+    # the BaB step (Sec. 3.2, Sec. 3.3)
+    ("optimised_bound_ignored", bab, "bound_node",
+     "if best > lb_dp:", "if False:", [BAB_ROOT]),
+    ("counterexample_checked_on_row_0", bab, "bound_node",
+     "[0, node.row])", "[0, 0])", [CEX]),
+    ("exact_minimum_active_sign_flipped", exact, "exact_min",
+     "A_ub.append(-Z[j]); b_ub.append(zc[j])", "A_ub.append(Z[j]); b_ub.append(-zc[j])",
+     [BELOW_EXACT, BELOW_EXACT_4, LEAF_LP, COMPLETE]),
     # the property and counterexamples (Sec. 2.1, Sec. 4)
     ("property_offset_dropped", core, "fold_property",
      "Ct @ last.b + dt", "dt", [FOLD]),

@@ -489,6 +489,18 @@ def test_folded_property_is_the_margin():
     assert np.allclose(got, ref, atol=1e-10)
 
 
+def test_bab_root_verdict_uses_the_optimised_bound():
+    """f = 3 relu(x) + 1 on [-1, 2]: DeepPoly gives -2 and the optimised slope 0
+    the exact 1 > 0, so BaB verifies at the root with one node bounded; it
+    branches only when the optimised bound does not decide (Sec. 3.1, then
+    Sec. 3.2)."""
+    res = bab.verify(_one_neuron(3.0, 1.0), np.array([[1.0]]), np.array([0.0]),
+                     np.array([-1.0]), np.array([2.0]), max_nodes=10)
+    assert res.verdict == bab.VERIFIED and res.n_bounded == 1
+    assert res.nodes[0].lb_dp == pytest.approx(-2.0, abs=1e-12)
+    assert res.nodes[0].lb == pytest.approx(1.0, abs=1e-12)
+
+
 def test_counterexamples_are_real():
     """Every FALSIFIED verdict carries x* in the box with f_r(x*) < 0 under an
     independent float64 forward pass (Sec. 3.1, upper bounding)."""
@@ -500,6 +512,10 @@ def test_counterexamples_are_real():
         C, d = synth.property_rows(int(np.argmax(y)), 4)
         lo, hi = synth.input_box(x0, 0.25)
         r = bab.verify(L, C, d, lo, hi, max_nodes=20, hp=core.AdamHP(steps=5))
+        # every node's f(x*) is its own row's margin at its x*
+        for nd in r.nodes:
+            m = C.astype(np.float64) @ synth.net_forward(L, nd.xstar) + d
+            assert nd.f_xstar == pytest.approx(m[nd.row], abs=1e-6 * (1 + abs(m[nd.row])))
         if r.verdict == bab.FALSIFIED:
             n_fals += 1
             nr = r.nodes[-1]
@@ -507,6 +523,17 @@ def test_counterexamples_are_real():
             m = C @ synth.net_forward(L, nr.xstar) + d
             assert m[nr.row] < 0
     assert n_fals >= 1
+    # the check at x* uses the node's own row, on every row of a property
+    x0 = np.random.default_rng(210).uniform(0.2, 0.8, 16).astype(np.float32)
+    C, d = synth.property_rows(int(np.argmax(synth.net_forward(L, x0))), 4)
+    lo, hi = synth.input_box(x0, 0.05)
+    net, lo_t, hi_t, l, u, S, m_, dense = bab.prepare(L, C, d, lo, hi)
+    for row in range(C.shape[0]):
+        nr, _ = bab.bound_node(net, bab.root_node(net, row, l, u, S, None), None, lo_t, hi_t,
+                               core.AdamHP(steps=2))
+        m = C.astype(np.float64) @ synth.net_forward(L, nr.xstar) + d
+        assert nr.row == row
+        assert nr.f_xstar == pytest.approx(m[row], abs=1e-6 * (1 + abs(m[row])))
 
 
 def test_children_keep_earlier_bounds():
