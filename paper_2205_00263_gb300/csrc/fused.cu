@@ -32,6 +32,8 @@ namespace mnbab {
 namespace {
 
 constexpr int FT = 512;  // threads per CTA (two CTAs per SM)
+constexpr int FU = 3;    // neurons per thread whose node-state loads overlap (ReLU steps)
+constexpr int FA = 4;    // parameters per thread whose loads overlap (Adam)
 
 __device__ __forceinline__ float f_block_sum(float v, float* red) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -635,28 +637,48 @@ __global__ void __launch_bounds__(FT, 2) k_opt_chain(NetDev net, PoolDev pool, c
     for (int t = R; t >= 1; --t) {
       const int dt = net.d[t], off = net.off[t];
       const float* bias = net.bfull[t];
-      for (int j = threadIdx.x; j < dt; j += FT) {
-        const int cd = code[off + j];
-        const float ap = cur[j];
-        float D, bl = 0.f, bt = 0.f;
-        if (cd == 2) {
+      // FU neurons per thread at a time: their node-state loads (slope, or
+      // bounds, or beta) are all issued before the first is used
+      for (int j0 = threadIdx.x; j0 < dt; j0 += FU * FT) {
+        int cd[FU];
+        float ap[FU], v0[FU], v1[FU];
+#pragma unroll
+        for (int k = 0; k < FU; ++k) {
+          const int j = j0 + k * FT;
+          cd[k] = j < dt ? code[off + j] : 0;
+          ap[k] = j < dt ? cur[j] : 0.f;
+          v0[k] = v1[k] = 0.f;
           const size_t q = nb + off + j;
-          if (ap >= 0.f) {
-            D = pool.ALPHA[q];
-          } else {
-            const float l = pool.L[q], u = pool.U[q];
-            const float den = u - l;
-            D = u / den;
-            bl = (-u * l) / den;
+          if (cd[k] == 2) {
+            v0[k] = ap[k] >= 0.f ? pool.ALPHA[q] : pool.L[q];
+            if (ap[k] < 0.f) v1[k] = pool.U[q];
+          } else if (cd[k] >= 3) {
+            v0[k] = pool.BETA[q];
           }
-        } else {
-          D = (cd == 1 || cd == 3) ? 1.f : 0.f;
-          if (cd >= 3) bt = pool.BETA[nb + off + j] * (cd == 3 ? -1.f : 1.f);
         }
-        const float ah = ap * D + bt;
-        APs[off + j] = ap;
-        part += ap * bl + ah * bias[j];
-        cur[j] = ah;
+#pragma unroll
+        for (int k = 0; k < FU; ++k) {
+          const int j = j0 + k * FT;
+          if (j >= dt) break;
+          float D, bl = 0.f, bt = 0.f;
+          if (cd[k] == 2) {
+            if (ap[k] >= 0.f) {
+              D = v0[k];
+            } else {
+              const float l = v0[k], u = v1[k];
+              const float den = u - l;
+              D = u / den;
+              bl = (-u * l) / den;
+            }
+          } else {
+            D = (cd[k] == 1 || cd[k] == 3) ? 1.f : 0.f;
+            if (cd[k] >= 3) bt = v0[k] * (cd[k] == 3 ? -1.f : 1.f);
+          }
+          const float ah = ap[k] * D + bt;
+          APs[off + j] = ap[k];
+          part += ap[k] * bl + ah * bias[j];
+          cur[j] = ah;
+        }
       }
       __syncthreads();
       const LayerDev& L = net.aff[t];
@@ -707,32 +729,50 @@ __global__ void __launch_bounds__(FT, 2) k_opt_chain(NetDev net, PoolDev pool, c
       else f_conv_fwd(L, g, h, wsm(t) + ftc_wb_region(L, t, ft));
       __syncthreads();
       const int dt = net.d[t], off = net.off[t];
-      for (int j = threadIdx.x; j < dt; j += FT) {
-        const int cd = code[off + j];
-        const float ap = APs[off + j];
-        const float hv = h[j];
-        float D, bl = 0.f, ga = 0.f, gb = 0.f;
-        if (cd == 2) {
-          const size_t q = nb + off + j;
-          if (ap >= 0.f) {
-            D = pool.ALPHA[q];
-            ga = hv * ap;
-          } else {
-            const float l = pool.L[q], u = pool.U[q];
-            const float den = u - l;
-            D = u / den;
-            bl = (-u * l) / den;
-          }
-        } else {
-          D = (cd == 1 || cd == 3) ? 1.f : 0.f;
-          if (cd >= 3) {
-            gb = hv * (cd == 3 ? -1.f : 1.f);
-            GBs[off + j] = gb;  // row scratch in global memory (L2-resident)
+      for (int j0 = threadIdx.x; j0 < dt; j0 += FU * FT) {
+        int cdk[FU];
+        float apk[FU], v0[FU], v1[FU];
+#pragma unroll
+        for (int k = 0; k < FU; ++k) {
+          const int j = j0 + k * FT;
+          cdk[k] = j < dt ? code[off + j] : 0;
+          apk[k] = j < dt ? APs[off + j] : 0.f;
+          v0[k] = v1[k] = 0.f;
+          if (cdk[k] == 2) {
+            const size_t q = nb + off + j;
+            v0[k] = apk[k] >= 0.f ? pool.ALPHA[q] : pool.L[q];
+            if (apk[k] < 0.f) v1[k] = pool.U[q];
           }
         }
-        APs[off + j] = ga;
-        gm = fmaxf(gm, fmaxf(fabsf(ga), fabsf(gb)));
-        h[j] = hv * D + bl;
+#pragma unroll
+        for (int k = 0; k < FU; ++k) {
+          const int j = j0 + k * FT;
+          if (j >= dt) break;
+          const int cd = cdk[k];
+          const float ap = apk[k];
+          const float hv = h[j];
+          float D, bl = 0.f, ga = 0.f, gb = 0.f;
+          if (cd == 2) {
+            if (ap >= 0.f) {
+              D = v0[k];
+              ga = hv * ap;
+            } else {
+              const float l = v0[k], u = v1[k];
+              const float den = u - l;
+              D = u / den;
+              bl = (-u * l) / den;
+            }
+          } else {
+            D = (cd == 1 || cd == 3) ? 1.f : 0.f;
+            if (cd >= 3) {
+              gb = hv * (cd == 3 ? -1.f : 1.f);
+              GBs[off + j] = gb;  // row scratch in global memory (L2-resident)
+            }
+          }
+          APs[off + j] = ga;
+          gm = fmaxf(gm, fmaxf(fabsf(ga), fabsf(gb)));
+          h[j] = hv * D + bl;
+        }
       }
       g = h;
     }
@@ -743,25 +783,46 @@ __global__ void __launch_bounds__(FT, 2) k_opt_chain(NetDev net, PoolDev pool, c
     const float bc1 = hp.bc1[step], bc2 = hp.bc2[step];
     // the alpha of a stable or split neuron and the beta of an unsplit one have a
     // zero gradient at every step, so their (zero-moment) updates are identities
-    for (int i = threadIdx.x; i < SD; i += FT) {
-      const int cd = code[i];
-      const size_t q = nb + i;
-      if (cd == 2) {
-        float ga = APs[i];
-        if (fabsf(ga) <= thr) ga = 0.f;
-        float th = pool.ALPHA[q], mo = pool.MA[q], ve = pool.VA[q];
-        f_adam(th, mo, ve, ga, hp.lr_a, hp.b1, hp.b2, eps, bc1, bc2);
-        pool.ALPHA[q] = fminf(fmaxf(th, 0.f), 1.f);
-        pool.MA[q] = mo;
-        pool.VA[q] = ve;
-      } else if (cd >= 3) {
-        float gb = GBs[i];
-        if (fabsf(gb) <= thr) gb = 0.f;
-        float th = pool.BETA[q], mo = pool.MB[q], ve = pool.VB[q];
-        f_adam(th, mo, ve, gb, hp.lr_b, hp.b1, hp.b2, eps, bc1, bc2);
-        pool.BETA[q] = fmaxf(th, 0.f);
-        pool.MB[q] = mo;
-        pool.VB[q] = ve;
+    // FA parameters per thread at a time: all their loads (parameter, both
+    // moments, gradient) are issued before the first update
+    for (int i0 = threadIdx.x; i0 < SD; i0 += FA * FT) {
+      int cd[FA];
+      float th[FA], mo[FA], ve[FA], gr[FA];
+#pragma unroll
+      for (int k = 0; k < FA; ++k) {
+        const int i = i0 + k * FT;
+        cd[k] = i < SD ? code[i] : 0;
+        th[k] = mo[k] = ve[k] = gr[k] = 0.f;
+        const size_t q = nb + i;
+        if (cd[k] == 2) {
+          th[k] = pool.ALPHA[q];
+          mo[k] = pool.MA[q];
+          ve[k] = pool.VA[q];
+          gr[k] = APs[i];
+        } else if (cd[k] >= 3) {
+          th[k] = pool.BETA[q];
+          mo[k] = pool.MB[q];
+          ve[k] = pool.VB[q];
+          gr[k] = GBs[i];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < FA; ++k) {
+        if (cd[k] < 2) continue;
+        const size_t q = nb + i0 + k * FT;
+        float g = gr[k];
+        if (fabsf(g) <= thr) g = 0.f;
+        if (cd[k] == 2) {
+          f_adam(th[k], mo[k], ve[k], g, hp.lr_a, hp.b1, hp.b2, eps, bc1, bc2);
+          pool.ALPHA[q] = fminf(fmaxf(th[k], 0.f), 1.f);
+          pool.MA[q] = mo[k];
+          pool.VA[q] = ve[k];
+        } else {
+          f_adam(th[k], mo[k], ve[k], g, hp.lr_b, hp.b1, hp.b2, eps, bc1, bc2);
+          pool.BETA[q] = fmaxf(th[k], 0.f);
+          pool.MB[q] = mo[k];
+          pool.VB[q] = ve[k];
+        }
       }
     }
   }
