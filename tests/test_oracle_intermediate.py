@@ -158,6 +158,26 @@ def _one_unstable_net():
     return net, lo, hi, l, u, S
 
 
+def test_each_row_keeps_its_best_iterate():
+    """Every iterate of a set gives valid bounds, so each row keeps the best it
+    reached (Sec. 3.1).  x in [-1, 1]; layer 1 is x and x + 2 (stable), and
+    z2 = relu(x) - 0.375 (x + 2) + 0.75 = relu(x) - 0.375 x.  Its lower bound
+    with the first neuron's shared slope alpha is -|alpha - 0.375| (DeepPoly,
+    alpha = 1: -0.625).  From alpha = 1 Adam's first steps are lr = 0.1 long and
+    reach alpha = 0.4 (-0.025) before momentum carries alpha past the optimum,
+    so the optimised lower bound is at least -0.025 and at most the exact
+    minimum 0."""
+    L = [_fc([[1.0], [1.0]], [0.0, 2.0]), RELU, _fc([[1.0, -0.375]], [0.75]), RELU,
+         _fc([[1.0]], [0.0])]
+    net, lo, hi, l, u, S, _, _ = bab.prepare(L, [[1.0]], [0.0], [-1.0], [1.0])
+    assert float(l[2][0]) == pytest.approx(-0.625, abs=1e-12)
+    assert float(u[2][0]) == pytest.approx(0.625, abs=1e-12)
+    node = bab.root_node(net, 0, l, u, S, None)
+    core.optimize_intermediate(net, node, lo, hi, core.AdamHP(steps=20))
+    assert float(node.l[2][0]) >= -0.025 - 1e-7
+    assert float(node.l[2][0]) <= 1e-12
+
+
 def test_linear_set_objective_reaches_its_corner():
     """With one unstable neuron below the target layer, every row bound is
     linear in that neuron's shared slope, so the set objective is maximised at

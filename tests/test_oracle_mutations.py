@@ -56,6 +56,11 @@ FOLD = (pins.test_folded_property_is_the_margin, ())
 BAB_ROOT = (pins.test_bab_root_verdict_uses_the_optimised_bound, ())
 LEAF_LP = (pins.test_fully_split_leaf_reaches_lp_optimum, (5,))
 COMPLETE = (pins.test_unlimited_bab_with_exact_leaves_is_complete, (2, 0.30906))
+UNDECIDED_LEAF = (pins.test_bab_without_leaf_completion_never_verifies_an_undecided_leaf, ())
+INTER_GAMMA = (ipins.test_gamma_sets_sound_and_zero_steps_give_deeppoly, (7,))
+INTER_GAMMA_FD = (ipins.test_gamma_gradient_matches_finite_differences, (1,))
+INTER_LOOSER = (ipins.test_optimised_bounds_sound_and_never_looser, (1, 0))
+INTER_BEST = (ipins.test_each_row_keeps_its_best_iterate, ())
 MNC_SOUND = (pins.test_mnc_rows_are_sound_per_orthant, ())
 ACS = (pins.test_acs_scores_by_hand, ())
 CEX = (pins.test_counterexamples_are_real, ())
@@ -143,6 +148,13 @@ CASES = [
      "alpha = {i: torch.ones_like(node.l[i]) for i in range(1, t)}", [INTER_ZERO]),
     ("inter_descends", core, "optimize_intermediate",
      "P[i] = P[i] + lr[grp] * mh", "P[i] = P[i] - lr[grp] * mh", [INTER_CORNER]),
+    ("inter_last_iterate_kept", core, "optimize_intermediate",
+     "bs = torch.maximum(bs, lb)", "bs = lb", [INTER_BEST]),
+    ("inter_gamma_dropped", core, "intermediate_objective",
+     "GP, GPh, gp0 = gamma[i] @ Pd, gamma[i] @ Phd, gamma[i] @ pv",
+     "GP, GPh, gp0 = None, None, None", [INTER_GAMMA, INTER_GAMMA_FD]),
+    ("undecided_leaf_closes_the_property", bab, "verify",
+     "if not q and not unknown_leaf:", "if not q:", [UNDECIDED_LEAF]),
     ("inter_side_ignored", core, "intermediate_objective",
      "= float(side)", "= 1.0", [INTER_SOUND]),
     # multi-neuron constraints (Sec. 2.3, Sec. 3.1)

@@ -665,6 +665,21 @@ def test_resnet_soundness_random_parameters(seed):
         assert float(lb) <= F[:, node.row].min() + 1e-9
 
 
+def test_bab_without_leaf_completion_never_verifies_an_undecided_leaf():
+    """With exact leaf completion off, a fully split leaf that its bound does
+    not decide stays UNKNOWN, and so does its property (Sec. 3.3: only a
+    decided leaf closes a branch).  On a near-critical 2-8-8-2 problem whose
+    exact minimum is negative, DeepPoly-only BaB ends with undecided leaves
+    and never reports VERIFIED."""
+    layers, C, d, lo, hi = _tiny_problem(2, 0.34159)
+    m = min(exact.exact_min(layers, C, d, r, lo, hi)[0] for r in range(C.shape[0]))
+    assert m < 0
+    res = bab.verify(layers, C, d, lo, hi, max_nodes=100000, hp=core.AdamHP(steps=0),
+                     leaf_lp=False)
+    assert any(n.split is None and n.verdict == bab.UNKNOWN for n in res.nodes)
+    assert res.verdict != bab.VERIFIED
+
+
 def _tiny_problem(seed, eps):
     layers = synth.tiny_fc_net(seed, [2, 8, 8, 2])
     x0 = np.random.default_rng(seed + 50).uniform(0.3, 0.7, 2).astype(np.float32)
