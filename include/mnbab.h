@@ -65,7 +65,11 @@ typedef struct {
   int32_t row_chunk;           /* max back-substitution rows per launch; 0 = 32768, at most 65534 */
   int32_t gemm_path;           /* dense FC steps: 0 = auto (tcgen05 3xTF32 when a launch fills
                                   two waves of 128-row tiles, else SIMT FP32), 1 = SIMT FP32
-                                  only, 2 = tcgen05 3xTF32 always */
+                                  only, 2 = tcgen05 3xTF32 always.  It also picks the form of
+                                  the optimisation loop of chain networks without multi-neuron
+                                  constraints: 0 = one fused launch per batch whose largest
+                                  conv layer's transposed convolution runs on tcgen05, 1 = the
+                                  fused launch in SIMT FP32 only, 2 = per-layer launches */
   int32_t use_graphs;          /* 1 = replay the optimisation loop from captured CUDA graphs
                                   (rows padded to multiples of 64, one graph per padded size);
                                   0 = launch it kernel by kernel (default) */
@@ -285,7 +289,9 @@ mnbab_status mnbab_set_params(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_
 /* cfg->steps projected Adam steps from each node's current parameters
  * (alpha clamped to [0, 1], beta, gamma >= 0).  best_lb_out[i] = the best
  * bound over the steps + 1 evaluated iterates; the node keeps the last
- * iterate's parameters.  Nodes must already be re-bounded. */
+ * iterate's parameters.  Nodes must already be re-bounded.  For a chain of
+ * FC / CONV2D layers without multi-neuron constraints the whole loop runs in
+ * one launch, one CTA per node (see mnbab_options.gemm_path). */
 mnbab_status mnbab_optimize(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
                             const mnbab_adam* cfg, float* best_lb_out);
 
