@@ -323,9 +323,11 @@ __device__ void f_conv_back(const LayerDev& L, const float* cur, float* nxt, con
 }
 
 // Forward convolution through L (+ bias) with its weights in shared memory as
-// Wf [ci][kh][kw][co]: g [ci][hi][wi] -> h [co][ho][wo].
-__device__ void f_conv_fwd(const LayerDev& L, const float* g, float* h, const float* Wf) {
-  const int CB = (L.co & 3) == 0 ? 4 : 1;
+// Wf [ci][kh][kw][co]: g [ci][hi][wi] -> h [co][ho][wo].  A thread group takes
+// CB output channels of one position: each input load serves CB channels (the
+// weight loads of a warp are mostly broadcasts, the input loads are not).
+template <int CB>
+__device__ void f_conv_fwd_cb(const LayerDev& L, const float* g, float* h, const float* Wf) {
   const int ngr = L.co / CB, P = L.ho * L.wo, hwi = L.hi * L.wi;
   const int items = P * ngr;
   const int ks = f_split(items);
@@ -334,7 +336,9 @@ __device__ void f_conv_fwd(const LayerDev& L, const float* g, float* h, const fl
     const int b = rr * FT + threadIdx.x;
     const int it = b / ks, k0 = b % ks;
     const bool act = it < items;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    float a[CB];
+#pragma unroll
+    for (int u = 0; u < CB; ++u) a[u] = 0.f;
     int grp = 0, pos = 0;
     if (act) {
       grp = it / P;
@@ -351,34 +355,35 @@ __device__ void f_conv_fwd(const LayerDev& L, const float* g, float* h, const fl
           for (int kw = kw_lo; kw < kw_hi; ++kw) {
             const float v = gp[(ih0 + kh) * L.wi + iw0 + kw];
             const float* wp = wc + (size_t)(kh * L.k + kw) * L.co;
-            if (CB == 4) {
-              const float4 w = *reinterpret_cast<const float4*>(wp);
-              a0 = fmaf(v, w.x, a0);
-              a1 = fmaf(v, w.y, a1);
-              a2 = fmaf(v, w.z, a2);
-              a3 = fmaf(v, w.w, a3);
+            if (CB >= 4) {
+#pragma unroll
+              for (int q = 0; q < CB / 4; ++q) {
+                const float4 w = *reinterpret_cast<const float4*>(wp + 4 * q);
+                a[4 * q] = fmaf(v, w.x, a[4 * q]);
+                a[4 * q + 1] = fmaf(v, w.y, a[4 * q + 1]);
+                a[4 * q + 2] = fmaf(v, w.z, a[4 * q + 2]);
+                a[4 * q + 3] = fmaf(v, w.w, a[4 * q + 3]);
+              }
             } else {
-              a0 = fmaf(v, wp[0], a0);
+              a[0] = fmaf(v, wp[0], a[0]);
             }
           }
       }
     }
-    a0 = f_group_sum(a0, ks);
-    if (CB == 4) {
-      a1 = f_group_sum(a1, ks);
-      a2 = f_group_sum(a2, ks);
-      a3 = f_group_sum(a3, ks);
-    }
+#pragma unroll
+    for (int u = 0; u < CB; ++u) a[u] = f_group_sum(a[u], ks);
     if (act && k0 == 0) {
       const int c = grp * CB;
-      h[c * P + pos] = a0 + L.b[c];
-      if (CB == 4) {
-        h[(c + 1) * P + pos] = a1 + L.b[c + 1];
-        h[(c + 2) * P + pos] = a2 + L.b[c + 2];
-        h[(c + 3) * P + pos] = a3 + L.b[c + 3];
-      }
+#pragma unroll
+      for (int u = 0; u < CB; ++u) h[(c + u) * P + pos] = a[u] + L.b[c + u];
     }
   }
+}
+
+__device__ void f_conv_fwd(const LayerDev& L, const float* g, float* h, const float* Wf) {
+  if ((L.co & 7) == 0) f_conv_fwd_cb<8>(L, g, h, Wf);
+  else if ((L.co & 3) == 0) f_conv_fwd_cb<4>(L, g, h, Wf);
+  else f_conv_fwd_cb<1>(L, g, h, Wf);
 }
 
 
