@@ -428,7 +428,9 @@ typedef struct {
 
 /* Queues a property (created by mnbab_set_property and not yet used) as a
  * request of the context's request loop; timeout_s > 0 limits its time from
- * this call to its verdict (UNKNOWN when exceeded). */
+ * this call to its verdict (UNKNOWN when exceeded).  A finished request's
+ * record stays in the context, readable by its ticket, until mnbab_destroy;
+ * its node slots and HBM reservation are released when it finishes. */
 mnbab_status mnbab_submit(mnbab_ctx* ctx, mnbab_prop* prop, double timeout_s, uint64_t* ticket);
 
 /* HBM bytes that the active requests' node slots may hold together, over all
