@@ -36,13 +36,14 @@ def test_roofline_fields_follow_from_the_stats():
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["avg_launch_us"] == pytest.approx(17.6 / 8 * 1e3)
     assert r["simt_fp32"]["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
-    # the survey's count per row (a sweep plus a two-sweep adjoint per Adam step)
-    # against the library's ((steps + 1) sweeps with the objective row, steps adjoints)
+    # the three-sweep count per row (a sweep plus a two-sweep adjoint per Adam
+    # step) against the library's ((steps + 1) sweeps with the objective row,
+    # steps adjoints)
     C, dR = bench.chain_macs(layers)
-    ours, survey = 21 * (C + dR) + 20 * C, 3 * 20 * C
-    assert r["survey_count"]["achieved"] == pytest.approx(r["achieved"] * survey / ours)
-    assert r["survey_count"]["flops_per_row"] == 2 * survey
-    assert r["survey_count"]["library_flops_per_row"] == 2 * ours
+    ours, three = 21 * (C + dR) + 20 * C, 3 * 20 * C
+    assert r["three_sweep_count"]["achieved"] == pytest.approx(r["achieved"] * three / ours)
+    assert r["three_sweep_count"]["flops_per_row"] == 2 * three
+    assert r["three_sweep_count"]["library_flops_per_row"] == 2 * ours
 
 
 def test_hbm_bound_class_and_derived_peak():
