@@ -23,7 +23,7 @@
  *  - Errors: MNBAB_E_INVALID_ARG for bad handles, sizes or shapes;
  *    MNBAB_E_BUDGET when the HBM budget or a pool capacity would be exceeded;
  *    MNBAB_E_DEVICE for CUDA errors; MNBAB_E_UNSUPPORTED for layer kinds or
- *    shapes this build does not handle.  mnbab_last_error() gives the text.
+ *    shapes the library does not handle.  mnbab_last_error() gives the text.
  */
 #ifndef MNBAB_H
 #define MNBAB_H
