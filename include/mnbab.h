@@ -182,7 +182,8 @@ mnbab_status mnbab_set_property(mnbab_ctx* ctx, const mnbab_net* net, const floa
                                 const float* x_hi, const float* C, const float* d,
                                 int32_t n_rows, mnbab_prop** out);
 
-/* Root bounds l, u of ReLU layer relu_layer (1-based), d_i floats each. */
+/* Root bounds l, u of ReLU layer relu_layer (1-based), d_i floats each: the
+ * intermediate bounds of Sec. 3.1 at the property's root. */
 mnbab_status mnbab_get_root_bounds(const mnbab_ctx* ctx, const mnbab_prop* prop,
                                    int32_t relu_layer, float* l_out, float* u_out);
 
@@ -241,7 +242,8 @@ mnbab_status mnbab_mnc_group(const double* oct_lb, int32_t max_rows, double* P, 
 
 /* ---- nodes ------------------------------------------------------------- */
 /* A fresh root node of property row `row` outside the property's BaB queue
- * (root bounds, DeepPoly slopes, beta = gamma = 0). */
+ * (the root subproblem of Sec. 2.2: root bounds, DeepPoly slopes,
+ * beta = gamma = 0). */
 mnbab_status mnbab_node_root(mnbab_ctx* ctx, mnbab_prop* prop, int32_t row, mnbab_node_id* out);
 mnbab_status mnbab_node_free(mnbab_ctx* ctx, mnbab_node_id node);
 
@@ -267,13 +269,15 @@ mnbab_status mnbab_import_params(mnbab_ctx* ctx, mnbab_node_id node, const void*
 mnbab_status mnbab_bound_batch(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
                                float* lb_out, float* ub_out);
 
-/* The DeepPoly pass of each node's objective (slopes from the area
- * heuristic, beta = gamma = 0); nodes must already be re-bounded. */
+/* The DeepPoly pass of each node's objective (Sec. 4, experimental setup:
+ * DeepPoly before the optimisation; slopes from the area heuristic,
+ * beta = gamma = 0); nodes must already be re-bounded. */
 mnbab_status mnbab_deeppoly_batch(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
                                   float* lb_out);
 
 /* The objective bound at the node's parameters and its gradient w.r.t.
- * (alpha, beta, gamma) from the adjoint back-substitution: grad_out holds
+ * (alpha, beta, gamma) from the adjoint back-substitution (Sec. 3.1: the bound
+ * is optimised by gradient ascent in these parameters): grad_out holds
  * n * (2 * SD + E) floats, per node alpha[SD], beta[SD], gamma[E]. */
 mnbab_status mnbab_bound_grad(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
                               float* lb_out, float* grad_out);
@@ -286,8 +290,8 @@ mnbab_status mnbab_bound_grad(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_
 mnbab_status mnbab_set_params(mnbab_ctx* ctx, const mnbab_node_id* nodes, int32_t n,
                               const float* params);
 
-/* cfg->steps projected Adam steps from each node's current parameters
- * (alpha clamped to [0, 1], beta, gamma >= 0).  best_lb_out[i] = the best
+/* cfg->steps projected Adam steps (Sec. 3.1, projected gradient ascent) from
+ * each node's current parameters (alpha clamped to [0, 1], beta, gamma >= 0).  best_lb_out[i] = the best
  * bound over the steps + 1 evaluated iterates; the node keeps the last
  * iterate's parameters.  Nodes must already be re-bounded.  For a chain of
  * FC / CONV2D layers without multi-neuron constraints the whole loop runs in
@@ -391,7 +395,9 @@ mnbab_status mnbab_get_status(const mnbab_ctx* ctx, const mnbab_prop* prop, int3
  * layer's cost is positive). */
 mnbab_status mnbab_set_branching(mnbab_ctx* ctx, mnbab_prop* prop, int32_t mode);
 
-/* Verdict of a property (row < 0) or of one row.  lb (nullable) = the lowest
+/* Verdict of a property (row < 0) or of one row (Sec. 2.2: VERIFIED when every
+ * subproblem's lower bound is positive, FALSIFIED by a concrete input with a
+ * negative margin).  lb (nullable) = the lowest
  * open or leaf lower bound seen (+inf if verified).  x_cex (nullable, d0
  * floats) receives the counterexample when FALSIFIED. */
 mnbab_status mnbab_get_verdict(const mnbab_ctx* ctx, const mnbab_prop* prop, int32_t row,
