@@ -56,3 +56,30 @@ def test_hbm_bound_class_and_derived_peak():
     # without a measured TF32 rate the 3xTF32 peak is BF16 x 1/2 / 3
     p, src = bench.tf32x3_peak(peaks, "measured")
     assert p == pytest.approx(1945.8 / 2 / 3) and "derived" in src
+
+
+def test_reference_arm_line():
+    """--impl reference times the FP64 oracle on the host cores (no GPU) and
+    prints one JSON line with the same metric and unit, impl "reference", a
+    cpu_baseline block and an e2e block without host-device copies; under a
+    multi-process launch only rank 0 prints."""
+    import json
+    import os
+    import subprocess
+    import sys
+    cmd = [sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+           "--steps", "1", "--warmup", "0", "--cpu-seconds", "0.5"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "nodes/s"
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "nodes/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    other = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=env)
+    assert other.returncode == 0 and other.stdout.strip() == ""
