@@ -17,8 +17,8 @@ are timed with CUDA events on the library's stream; L2 is flushed (256 MiB
 write) between timed steps, outside the timed spans.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload instead (the only place besides the cpu_baseline leg where this file
-runs the oracle).
+workload instead.  Besides that arm, this file runs the oracle only in its CPU
+baseline legs: the line's cpu_baseline and the intermediate-bounds block's.
 """
 from __future__ import annotations
 
@@ -765,9 +765,10 @@ def intermediate_run(local, stream, layers, eps, start, n_nodes, oracle_nodes):
             rows_or += core.optimize_intermediate(net_o, node, lo_t, hi_t,
                                                   core.AdamHP(steps=ADAM_STEPS))
             t_or += time.perf_counter() - t1
-        out["cpu_oracle"] = {"nodes_per_s": oracle_nodes / t_or, "rows": rows_or,
-                             "nodes": oracle_nodes, "cores": torch.get_num_threads(),
-                             "kind": "oracle"}
+        # the block's CPU baseline: the FP64 oracle, as it stands, on a few of the roots
+        out["cpu_baseline"] = {"value": oracle_nodes / t_or, "unit": "nodes/s",
+                               "rows": rows_or, "nodes": oracle_nodes,
+                               "cores": torch.get_num_threads(), "kind": "oracle"}
     return out
 
 

@@ -1,4 +1,6 @@
-"""Calibrate the L-inf radius of each synthetic workload (writes synth/eps.json).
+"""Calibrate the L-inf radius of each synthetic workload (writes synth/eps.json)
+-- test infrastructure only: the stored radii are inputs of the tests and the
+bench; the product path never runs this script.
 
 For every property the largest radius eps_p at which a single DeepPoly pass
 (root intermediate bounds, DeepPoly objective bound of every margin row, no
