@@ -35,6 +35,25 @@ def test_header_declares_the_boundary():
         assert n in names
 
 
+def test_boundary_calls_cite_the_paper():
+    """Each call of the method's boundary is documented with the passage that
+    defines it: the comment text between the previous declaration and its
+    own (its group heading included) names a section or appendix."""
+    txt = open(os.path.join(ROOT, "include", "mnbab.h")).read()
+    decl = [(m.start(), m.group(1)) for m in
+            re.finditer(r"\nmnbab_status\s+(mnbab_\w+)\s*\(", txt)]
+    prev_end = {}
+    for k, (pos, name) in enumerate(decl):
+        start = txt.index(";", decl[k - 1][0]) if k else 0
+        prev_end[name] = txt[start:pos]
+    for name in ("mnbab_load_network", "mnbab_set_property", "mnbab_set_mnc",
+                 "mnbab_bound_batch", "mnbab_deeppoly_batch", "mnbab_bound_grad",
+                 "mnbab_optimize", "mnbab_score_branches", "mnbab_bab_step",
+                 "mnbab_get_verdict", "mnbab_get_root_bounds", "mnbab_node_root",
+                 "mnbab_optimize_intermediate", "mnbab_attack", "mnbab_set_branching"):
+        assert re.search(r"Sec\. \d|App\. [A-Z]", prev_end[name]), name
+
+
 def test_library_exports_every_declared_symbol(lib_path):
     lib = ctypes.CDLL(lib_path)
     missing = [n for n in _declared() if not hasattr(lib, n)]
